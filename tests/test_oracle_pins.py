@@ -1,0 +1,401 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test names the passage of arXiv 2602.21242 (or the textbook fact) that
+fixes the expected value: closed forms derived from the paper's formulas,
+special cases that reduce to textbook lattice Boltzmann, library routines
+(np.roll, math.fsum, np.fft), and the conservation laws the paper states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_21242_gb300 import flows
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
+THETAS = [0.25, 1.0 / 3.0, 0.4, 0.5]
+
+
+def moments_np(f):
+    """Moments written directly with numpy: rho, u, full second-moment tensor."""
+    rho = f.sum()
+    jx, jy = (CX * f).sum(), (CY * f).sum()
+    return rho, jx / rho, jy / rho, (CX * CX * f).sum(), (CY * CY * f).sum(), (CX * CY * f).sum()
+
+
+def random_node(g, theta, spread=0.3):
+    """A positive non-equilibrium population set with velocity well inside the GEq positivity range."""
+    base = np.array([16, 4, 4, 4, 4, 1, 1, 1, 1], float) / 36
+    f = base * (1 + spread * g.uniform(-1, 1, 9)) * g.uniform(0.8, 1.2)
+    return f
+
+
+def neq_tensor(f, theta):
+    """N_d = (Pi^neq_xx - Pi^neq_yy)/2, N_xy = Pi^neq_xy with Pi^eq = rho(uu + theta I) (Eq. 4)."""
+    rho, ux, uy, pxx, pyy, pxy = moments_np(f)
+    nxx = pxx - rho * (ux * ux + theta)
+    nyy = pyy - rho * (uy * uy + theta)
+    nxy = pxy - rho * ux * uy
+    return rho, ux, uy, 0.5 * (nxx - nyy), nxy
+
+
+def mu(theta, u):
+    """Eq. 13b, diagonal entry: (theta - u^2)(1 - theta - u^2) / (2 theta^2)."""
+    return (theta - u * u) * (1 - theta - u * u) / (2 * theta * theta)
+
+
+# --------------------------------------------------------------------------- GEq (Eq. 10)
+
+def test_geq_reduces_to_textbook_weights(oracle):
+    """At theta = 1/3, u = 0 the GEq is the standard D2Q9 weight set 16/36, 4/36, 1/36."""
+    for rho in (1.0, 0.7):
+        feq = oracle.geq(rho, 0.0, 0.0, 1.0 / 3.0)
+        np.testing.assert_allclose(feq, rho * np.array([16, 4, 4, 4, 4, 1, 1, 1, 1]) / 36.0,
+                                   rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("theta", THETAS + [0.6])
+def test_geq_six_moments(oracle, theta):
+    """Eqs. 3-4: sum f^eq = rho, sum c f^eq = rho u, sum cc f^eq = rho(uu + theta I)."""
+    g = flows.rng(11)
+    for _ in range(50):
+        rho = g.uniform(0.5, 2.0)
+        ux, uy = g.uniform(-0.3, 0.3, 2)
+        feq = oracle.geq(rho, ux, uy, theta)
+        r, mx, my, pxx, pyy, pxy = moments_np(feq)
+        np.testing.assert_allclose([r, mx, my], [rho, ux, uy], rtol=0, atol=2e-15)
+        np.testing.assert_allclose([pxx, pyy, pxy],
+                                   [rho * (ux * ux + theta), rho * (uy * uy + theta), rho * ux * uy],
+                                   rtol=0, atol=4e-15)
+
+
+def test_geq_agrees_with_polynomial_equilibrium_to_second_order(oracle):
+    """At theta = 1/3 the GEq and the textbook polynomial equilibrium
+    w rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2) differ only at O(u^3)."""
+    w = np.array([16, 4, 4, 4, 4, 1, 1, 1, 1]) / 36.0
+    d = np.array([0.6, -0.8])
+    errs = []
+    for s in (0.04, 0.02, 0.01):
+        u = s * d
+        cu = CX * u[0] + CY * u[1]
+        poly = w * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (u @ u))
+        errs.append(np.abs(oracle.geq(1.0, u[0], u[1], 1.0 / 3.0) - poly).max())
+    assert errs[0] / errs[1] == pytest.approx(8.0, rel=0.05)
+    assert errs[1] / errs[2] == pytest.approx(8.0, rel=0.05)
+
+
+def test_geq_literal_product_signs(oracle):
+    """Eq. 10 factor by factor: Phi(0) = 1 - theta - u^2 and Phi(+-1) = (theta + u^2 +- u)/2."""
+    theta, ux, uy, rho = 0.37, 0.11, -0.07, 1.3
+    phi = lambda c, u: (1 - theta - u * u) if c == 0 else (theta + u * u + c * u) / 2
+    expect = np.array([rho * phi(cx, ux) * phi(cy, uy) for cx, cy in zip(CX, CY)])
+    np.testing.assert_allclose(oracle.geq(rho, ux, uy, theta), expect, rtol=1e-15, atol=0)
+
+
+# --------------------------------------------------------------------------- OReg (Eq. 2)
+
+@pytest.mark.parametrize("theta", THETAS)
+def test_oreg_moment_identities(oracle, theta):
+    """Closed forms of the moments of f^OReg (from Eq. 2 with the GEq of Eq. 10):
+    sum f^OReg = 0; psi_x = u_x(1-3theta-u_x^2) N_d/(2theta^2), psi_y = -u_y(1-3theta-u_y^2) N_d/(2theta^2);
+    sum c_x^2 f^OReg = mu_xx N_d, sum c_y^2 f^OReg = -mu_yy N_d (mu of Eq. 13);
+    sum c_x c_y f^OReg = N_xy + u_x u_y (u_y^2 - u_x^2) N_d / (2 theta^2)."""
+    g = flows.rng(7)
+    for _ in range(40):
+        f = random_node(g, theta)
+        rho, ux, uy, Nd, Nxy = neq_tensor(f, theta)
+        t = oracle.node_terms(f, theta)
+        fo = t["foreg"]
+        scale = abs(Nd) + abs(Nxy)
+        k = Nd / (2 * theta * theta)
+        assert abs(fo.sum()) <= 1e-15 * max(scale, 1e-3) + 1e-17
+        np.testing.assert_allclose((CX * fo).sum(), ux * (1 - 3 * theta - ux * ux) * k, rtol=1e-11, atol=1e-16)
+        np.testing.assert_allclose((CY * fo).sum(), -uy * (1 - 3 * theta - uy * uy) * k, rtol=1e-11, atol=1e-16)
+        np.testing.assert_allclose((CX * CX * fo).sum(), mu(theta, ux) * Nd, rtol=1e-11, atol=1e-16)
+        np.testing.assert_allclose((CY * CY * fo).sum(), -mu(theta, uy) * Nd, rtol=1e-11, atol=1e-16)
+        np.testing.assert_allclose((CX * CY * fo).sum(), Nxy + ux * uy * (uy * uy - ux * ux) * k,
+                                   rtol=1e-11, atol=1e-16)
+        # psi is reported as the moment (Eq. 6a)
+        np.testing.assert_allclose(t["psi"], [(CX * fo).sum(), (CY * fo).sum()], rtol=0,
+                                   atol=1e-15 * np.abs(fo).max())
+
+
+def test_oreg_reduces_to_regularised_lbm(oracle):
+    """u = 0, theta = 1/3: f^OReg_i = w_i / (2 c_s^4) c_ia c_ib S_ab, the textbook regularised
+    non-equilibrium built from the traceless part S of Pi^neq (c_s^2 = 1/3)."""
+    g = flows.rng(3)
+    w = np.array([16, 4, 4, 4, 4, 1, 1, 1, 1]) / 36.0
+    for _ in range(20):
+        rho = g.uniform(0.8, 1.2)
+        feq = rho * w
+        f = feq + 0.01 * g.standard_normal(9)
+        pneq = np.array([[(CX * CX * (f - feq)).sum(), (CX * CY * (f - feq)).sum()],
+                         [(CX * CY * (f - feq)).sum(), (CY * CY * (f - feq)).sum()]])
+        S = pneq - 0.5 * np.trace(pneq) * np.eye(2)
+        cs2 = 1.0 / 3.0
+        expect = np.array([w[i] / (2 * cs2 * cs2) * np.array([CX[i], CY[i]]) @ S @ np.array([CX[i], CY[i]])
+                           for i in range(9)])
+        got = oracle.oreg_node(f, feq, rho, 0.0, 0.0, 1.0 / 3.0)
+        np.testing.assert_allclose(got, expect, rtol=1e-12, atol=1e-18)
+
+
+def test_oreg_vanishes_at_equilibrium(oracle):
+    """f = f^eq gives f^neq = 0, hence f^OReg = psi = Pi~ = Psi = 0 (Eqs. 2, 12, 14, 15)."""
+    for theta in THETAS:
+        f = oracle.geq(1.05, 0.08, -0.05, theta)
+        t = oracle.node_terms(f, theta)
+        for key in ("foreg", "psi", "pitilde", "PsiP", "PsiC"):
+            assert np.abs(t[key]).max() < 1e-16, key
+
+
+# --------------------------------------------------------------------------- corrections
+
+@pytest.mark.parametrize("theta", THETAS)
+def test_corrections_satisfy_eq8(oracle, theta):
+    """Eq. 8: sum {1, c, cc} Psi^C = -{0, psi, Pi~}; the partial form (Eq. 14) removes psi only."""
+    g = flows.rng(5)
+    for _ in range(30):
+        f = random_node(g, theta)
+        t = oracle.node_terms(f, theta)
+        psi, pit = t["psi"], t["pitilde"]  # pit = (xx, yy, xy)
+        for Psi, second in ((t["PsiC"], pit), (t["PsiP"], np.zeros(3))):
+            m = [Psi.sum(), (CX * Psi).sum(), (CY * Psi).sum(),
+                 (CX * CX * Psi).sum(), (CY * CY * Psi).sum(), (CX * CY * Psi).sum()]
+            expect = [0.0, -psi[0], -psi[1], -second[0], -second[1], -second[2]]
+            np.testing.assert_allclose(m, expect, rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("theta", THETAS)
+def test_pref_and_pitilde_closed_forms(oracle, theta):
+    """Eq. 12 evaluated on f^OReg gives pref = -(mu_xx + mu_yy) N_d / (4 theta^2). With the
+    exact local stress pref* = -N_d/(2 theta^2) in place of pref, the printed Eq. 11b equals
+    sum cc f^OReg - Pi^NS with Pi^NS = (N_d, -N_d, N_xy): this fixes the signs of Eq. 11b."""
+    g = flows.rng(9)
+    for _ in range(30):
+        f = random_node(g, theta)
+        rho, ux, uy, Nd, Nxy = neq_tensor(f, theta)
+        t = oracle.node_terms(f, theta)
+        np.testing.assert_allclose(t["pref"], -(mu(theta, ux) + mu(theta, uy)) * Nd / (4 * theta ** 2),
+                                   rtol=1e-11, atol=1e-17)
+        if abs(t["pref"]) < 1e-12:
+            continue
+        pit_star = t["pitilde"] * (-Nd / (2 * theta ** 2)) / t["pref"]
+        fo = t["foreg"]
+        resid = np.array([(CX * CX * fo).sum() - Nd, (CY * CY * fo).sum() + Nd, (CX * CY * fo).sum() - Nxy])
+        np.testing.assert_allclose(pit_star, resid, rtol=1e-10, atol=1e-16)
+
+
+# --------------------------------------------------------------------------- collision (Eq. 1a)
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("theta", THETAS)
+def test_collision_conservation(oracle, model, theta):
+    """Mass is conserved by every model; momentum by LBGK, partial and complete; the uncorrected
+    model changes momentum by exactly (1 - 1/tau) psi (the compatibility violation, Sec. 2)."""
+    g = flows.rng(13 + model)
+    tau = 0.8
+    for _ in range(20):
+        f = random_node(g, theta)
+        fs = oracle.collide_node(f, theta, tau, model)
+        t = oracle.node_terms(f, theta)
+        rho = f.sum()
+        np.testing.assert_allclose(fs.sum(), rho, rtol=2e-15, atol=0)
+        dj = np.array([(CX * (fs - f)).sum(), (CY * (fs - f)).sum()])
+        expect = (1 - 1 / tau) * t["psi"] if model == 1 else np.zeros(2)
+        np.testing.assert_allclose(dj, expect, rtol=0, atol=2e-16)
+
+
+@pytest.mark.parametrize("theta", THETAS)
+def test_collision_second_moments(oracle, theta):
+    """Post-collision stress: LBGK relaxes Pi^neq by (1 - 1/tau); partial leaves sum cc f^OReg
+    (Psi^P has no second moments); complete gives (1 - 1/tau)(sum cc f^OReg - Pi~) (Eqs. 1a, 8)."""
+    g = flows.rng(17)
+    tau = 0.65
+    wp = 1 - 1 / tau
+    for _ in range(20):
+        f = random_node(g, theta)
+        rho, ux, uy, pxx, pyy, pxy = moments_np(f)
+        t = oracle.node_terms(f, theta)
+        fo = t["foreg"]
+        peq = np.array([rho * (ux * ux + theta), rho * (uy * uy + theta), rho * ux * uy])
+        so = np.array([(CX * CX * fo).sum(), (CY * CY * fo).sum(), (CX * CY * fo).sum()])
+        pneq = np.array([pxx, pyy, pxy]) - peq
+        for model, expect in ((0, wp * pneq), (1, wp * so), (2, wp * so), (3, wp * (so - t["pitilde"]))):
+            fs = oracle.collide_node(f, theta, tau, model)
+            got = np.array([(CX * CX * fs).sum(), (CY * CY * fs).sum(), (CX * CY * fs).sum()]) - peq
+            np.testing.assert_allclose(got, expect, rtol=0, atol=4e-15 * np.abs(f).sum())
+
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_equilibrium_is_fixed_point(oracle, model):
+    """f = f^eq is left unchanged by every collision (f^neq = 0 => g = 0)."""
+    for theta in THETAS:
+        feq = oracle.geq(0.95, -0.06, 0.09, theta)
+        np.testing.assert_allclose(oracle.collide_node(feq, theta, 0.57, model), feq, rtol=0, atol=1e-15)
+
+
+def test_lbgk_is_bgk_relaxation(oracle):
+    """Model 0 is f* = f + (f^eq - f)/tau (Eq. 1a with f^neq = f - f^eq)."""
+    g = flows.rng(19)
+    for _ in range(10):
+        f = random_node(g, 0.35)
+        rho, ux, uy, *_ = moments_np(f)
+        feq = oracle.geq(rho, ux, uy, 0.35)
+        np.testing.assert_allclose(oracle.collide_node(f, 0.35, 0.9, 0), f + (feq - f) / 0.9, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------- streaming (Eq. 1b)
+
+def test_streaming_is_a_shift(oracle):
+    """With the collision switched off, one step moves plane i by c_i (np.roll)."""
+    f = flows.random_populations(7, 5, seed=1)
+    out = oracle.run(f, 1 / 3, 0.6, oracle.NO_COLLISION, 1)
+    for i in range(9):
+        np.testing.assert_array_equal(out[i], np.roll(f[i], shift=(int(CY[i]), int(CX[i])), axis=(0, 1)))
+
+
+def test_streaming_period(oracle):
+    """Streaming alone is a permutation with period lcm(nx, ny) on the periodic grid."""
+    nx, ny = 6, 4
+    f = flows.random_populations(nx, ny, seed=2)
+    out = oracle.run(f, 1 / 3, 0.6, oracle.NO_COLLISION, math.lcm(nx, ny))
+    np.testing.assert_array_equal(out, f)
+
+
+# --------------------------------------------------------------------------- init, diagnostics
+
+def test_init_and_moments_roundtrip(oracle):
+    rho, ux, uy = flows.taylor_green(16, 12, 0.05, 0.4)
+    f = oracle.init(rho, ux, uy, 0.4)
+    r2, ux2, uy2 = oracle.moments(f)
+    np.testing.assert_allclose(r2, rho, rtol=1e-15)
+    np.testing.assert_allclose(ux2, ux, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(uy2, uy, rtol=0, atol=1e-16)
+
+
+def test_diagnostics_against_fsum(oracle):
+    """Diagnostics are compensated sums: equal to math.fsum of per-node values to roundoff."""
+    f = flows.random_populations(33, 17, seed=4)
+    rho = f.sum(0)
+    jx = np.tensordot(CX, f, 1)
+    jy = np.tensordot(CY, f, 1)
+    ke = 0.5 * (jx * jx + jy * jy) / rho
+    d = oracle.diagnostics(f)
+    for got, vals in zip(d[:4], (rho, jx, jy, ke)):
+        assert got == pytest.approx(math.fsum(vals.ravel()), rel=1e-15, abs=1e-15)
+    assert d[4] == 0
+    f[3, 2, 5] = np.nan
+    f[0, 9, 1] = np.inf
+    assert oracle.diagnostics(f)[4] == 2
+
+
+# --------------------------------------------------------------------------- dynamics
+
+def _mode_amplitude(field, kx_idx, ky_idx):
+    return np.abs(np.fft.fft2(field)[ky_idx, kx_idx]) / field.size
+
+
+@pytest.mark.parametrize("model", [0, 3])
+def test_taylor_green_decay(oracle, model):
+    """theta = 1/3: velocity of a Taylor-Green vortex decays as exp(-2 nu k^2 t) with
+    nu = theta (tau - 1/2) (Eq. 1 with the viscosity reading of Sec. 1 / Eq. 5)."""
+    n, theta, nu, u0, steps = 32, 1.0 / 3.0, 0.02, 0.005, 400
+    tau = oracle.tau_from_nu(nu, theta)
+    rho, ux, uy = flows.taylor_green(n, n, u0, theta)
+    # the initial state carries no non-equilibrium part: skip the start-up transient
+    f = oracle.run(oracle.init(rho, ux, uy, theta), theta, tau, model, 50)
+    a0 = _mode_amplitude(oracle.moments(f)[2], 1, 1)
+    f = oracle.run(f, theta, tau, model, steps)
+    a1 = _mode_amplitude(oracle.moments(f)[2], 1, 1)
+    k = 2 * math.pi / n
+    rate = -math.log(a1 / a0) / steps
+    assert rate == pytest.approx(2 * nu * k * k, rel=0.003)
+
+
+@pytest.mark.parametrize("U", [0.0, 0.1])
+def test_shear_wave_decay_and_advection(oracle, U):
+    """Completely corrected model: a transverse shear wave decays as exp(-nu k^2 t) and its
+    phase is carried at the background velocity U (Galilean invariance, Sec. 5.1)."""
+    nx, ny, theta, nu, steps = 48, 2, 1.0 / 3.0, 0.02, 240
+    tau = oracle.tau_from_nu(nu, theta)
+    rho, ux, uy = flows.shear_wave(nx, ny, U=U, amp=0.005)
+    f = oracle.run(oracle.init(rho, ux, uy, theta), theta, tau, 3, 40)  # past the start-up transient
+    c0 = np.fft.fft(oracle.moments(f)[2][0])[1]
+    f = oracle.run(f, theta, tau, 3, steps)
+    c1 = np.fft.fft(oracle.moments(f)[2][0])[1]
+    k = 2 * math.pi / nx
+    assert -math.log(abs(c1) / abs(c0)) / steps == pytest.approx(nu * k * k, rel=0.003)
+    # u_y(x - U t): the Fourier phase of mode 1 turns by -k U t
+    dphase = np.angle(c1 / c0)
+    assert dphase == pytest.approx(-k * U * steps, abs=1e-4)
+
+
+def _acoustic_run(oracle, theta, model, nu=0.01, nx=64, steps=2000):
+    """Standing acoustic wave u_x = 1e-4 sin(kx): returns the decay rate of the mode energy
+    |u_k|^2 + theta |rho_k|^2 (linear isothermal acoustics) and whether the run stayed finite."""
+    tau = oracle.tau_from_nu(nu, theta)
+    x = np.arange(nx)[None, :]
+    ux = np.broadcast_to(1e-4 * np.sin(2 * np.pi * x / nx), (2, nx)).copy()
+    f = oracle.init(np.ones((2, nx)), ux, np.zeros_like(ux), theta)
+
+    def energy(f):
+        r, u, _ = oracle.moments(f)
+        return abs(np.fft.fft(u[0])[1]) ** 2 + theta * abs(np.fft.fft(r[0])[1]) ** 2
+
+    f = oracle.run(f, theta, tau, model, 50)
+    e1 = energy(f)
+    f = oracle.run(f, theta, tau, model, steps)
+    e2 = energy(f)
+    k = 2 * math.pi / nx
+    if not np.isfinite(f).all() or not np.isfinite(e2):
+        return float("inf"), False
+    return -math.log(e2 / e1) / (2 * steps) / (nu * k * k / 2), True
+
+
+@pytest.mark.parametrize("theta", [0.25, 1.0 / 3.0, 0.4])
+def test_lbgk_acoustic_damping(oracle, theta):
+    """LBGK on the GEq: the lattice's third moment sum c_x^3 f^eq = rho u_x (instead of
+    3 theta rho u_x) gives a first-order stress -tau (1 - theta) rho d_x u_x in a 1D wave, i.e.
+    sound damped at 2 mu_0 times nu k^2/2 with mu_0 = (1 - theta)/(2 theta) -- the u -> 0
+    value of Eq. 13's mu. Pins the LBGK reading and the theta dependence of the GEq."""
+    ratio, ok = _acoustic_run(oracle, theta, 0)
+    assert ok
+    assert ratio == pytest.approx(2 * (1 - theta) / (2 * theta), rel=0.02)
+
+
+def test_normal_stress_amplification_decides_stability(oracle):
+    """Eq. 13 at u -> 0: the uncorrected and partial models carry sum c_x^2 f^OReg = mu_0 N_d, so
+    the normal-stress mode is multiplied by (1 - 1/tau) mu_0 each step. At theta = 0.25,
+    tau = 0.54 that factor is -1.27: a resting acoustic wave grows (the paper reports the
+    uncorrected model unstable at theta = 0.25, Sec. 5.1). The complete model's factor,
+    (1 - 1/tau) mu_0 (5 theta - 1)/(2 theta) = -0.64 (Eqs. 11b, 12, 15), stays below 1."""
+    theta, tau = 0.25, 0.01 / 0.25 + 0.5
+    mu0 = (1 - theta) / (2 * theta)
+    wp = 1 - 1 / tau
+    assert abs(wp * mu0) > 1 > abs(wp * mu0 * (5 * theta - 1) / (2 * theta))
+    for model in (1, 2):
+        assert not _acoustic_run(oracle, theta, model, steps=600)[1]
+    assert _acoustic_run(oracle, theta, 3, steps=600)[1]
+
+
+# --------------------------------------------------------------------------- complex step
+
+def test_complex_step_matches_finite_difference(oracle):
+    """The complex instantiation gives d f*/d f_j equal to a central difference of the real one."""
+    g = flows.rng(23)
+    f = random_node(g, 0.4)
+    for model in (0, 1, 2, 3):
+        for j in (0, 5):
+            h = 1e-30
+            fz = f.astype(complex)
+            fz[j] += 1j * h
+            d_cs = oracle.collide_node_cplx(fz, 0.4, 0.7, model).imag / h
+            e = 1e-6
+            fp, fm = f.copy(), f.copy()
+            fp[j] += e
+            fm[j] -= e
+            d_fd = (oracle.collide_node(fp, 0.4, 0.7, model) - oracle.collide_node(fm, 0.4, 0.7, model)) / (2 * e)
+            np.testing.assert_allclose(d_cs, d_fd, rtol=1e-6, atol=1e-9)
+            np.testing.assert_allclose(oracle.collide_node_cplx(fz, 0.4, 0.7, model).real,
+                                       oracle.collide_node(f, 0.4, 0.7, model), rtol=1e-15)
