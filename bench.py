@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Throughput of the fused D2Q9 OReg-GEq step (arXiv 2602.21242, Eq. 1) on GB300.
+
+One benchmark step = one pass of the whole hot path over the lattice: pull
+streaming, moments, guided equilibrium, Onsager-regularised non-equilibrium,
+compatibility and stress corrections, relaxation, store, and the fused FP64
+diagnostics reduction (mass, momentum, kinetic energy, non-finite count).
+
+Workload (default): 4096 x 4096 doubly periodic advected shear wave,
+u_y = 0.01 sin(2 pi x / nx) on u_x = U = 0.1, rho = 1, theta = 1/3, nu = 0.005,
+completely corrected model, FP64 storage and arithmetic. Inputs are larger than
+L2 (two 1.2 GB population buffers vs 129 MB).
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline, D2Q9 OReg-GEq; FP32 vs FP64 at stated error"
+BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}
+# Algorithmic FP64 FLOP per node of one collision (FMA = 2 FLOP), counted from the
+# product-form collision ("Roofline"): moments, 1/rho, per-axis
+# GEq factors, model terms and the 9 relaxed populations.
+FLOP_PER_NODE = {"lbgk": 73, "oreg": 150, "partial": 164, "complete": 205}
+FALLBACK_HBM_GBS = 6800.0
+MODEL_NAMES = ["lbgk", "oreg", "partial", "complete"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096, help="lattice side (nx = ny)")
+    ap.add_argument("--model", default="complete", choices=MODEL_NAMES)
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the per-model / per-precision sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=50, help="lattice steps per end-to-end call")
+    ap.add_argument("--e2e-calls", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload(n: int):
+    theta, nu, U = 1.0 / 3.0, 0.005, 0.1
+    return {"nx": n, "ny": n, "theta": theta, "nu": nu, "tau": nu / theta + 0.5, "U": U, "amp": 0.01}
+
+
+def workload_name(w, model, prec):
+    return (f"advected shear wave {w['nx']}x{w['ny']} periodic, u_y=0.01 sin(2 pi x/nx), U={w['U']}, "
+            f"theta=1/3, nu={w['nu']}, {model} model, {prec} storage, diagnostics every step")
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_mlups(w, model, target_s=12.0, nx=None, ny=None):
+    """Time the FP64 oracle (all host cores) on the workload's flow; returns (mlups, cores, sample)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2602_21242_gb300 import flows
+
+    cores = O.set_threads(os.cpu_count() or 1)
+    nx = nx or w["nx"]
+    ny = ny or w["ny"]
+    m = MODEL_NAMES.index(model)
+    rho, ux, uy = flows.shear_wave(nx, ny, U=w["U"], amp=w["amp"])
+    f = O.init(rho, ux, uy, w["theta"])
+    del rho, ux, uy
+    t0 = time.perf_counter()
+    f = O.run(f, w["theta"], w["tau"], m, 1)  # calibration step
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    f = O.run(f, w["theta"], w["tau"], m, steps)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(f[:, :2, :2]).all()
+    sample = f"{nx}x{ny} grid of the same flow, {steps} oracle steps of the {model} model, {dt:.1f} s"
+    return nx * ny * steps / dt / 1e6, cores, sample
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_21242_gb300 import capi, flows
+    from paper_2602_21242_gb300.lattice import Lattice
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    capi.load()
+    stream = torch.cuda.current_stream(dev)
+
+    w = workload(args.n)
+    n = w["nx"] * w["ny"]
+    rho, ux, uy = flows.shear_wave(w["nx"], w["ny"], U=w["U"], amp=w["amp"])
+    fields = [torch.from_numpy(a).to(dev) for a in (rho, ux, uy)]
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    # ---- headline: timed region
+    lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], args.model, args.prec, device=dev, stream=stream)
+    lat.init(*fields)
+    lat.set_diagnostics_interval(1)
+    for _ in range(args.warmup):
+        lat.step(1)
+    lat.sync()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
+        gpu_id = "GPU-" + gpu_id
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    with ClockSampler(gpu_id) as clocks:
+        events[0].record(stream)
+        for k in range(args.steps):
+            lat.step(1)
+            events[k + 1].record(stream)
+        barrier()
+    total_ms = events[0].elapsed_time(events[-1])
+    per_step = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
+    diag, t_diag, status = lat.step_diagnostics()
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    mlups = world * n * args.steps / (total_ms * 1e-3) / 1e6
+    step_ms = statistics.mean(per_step)
+
+    # ---- roofline of the step kernel (fused step + its tiny diagnostics finalisation)
+    peak_hbm, hbm_src = hbm_peak()
+    bytes_step = BYTES_PER_NODE[args.prec] * n
+    hbm_gbs = bytes_step / (step_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
+            "frac": round(hbm_gbs / peak_hbm, 4), "traffic": None,
+            "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
+            else "profiling-recipe fallback 6.8 TB/s",
+            "kernel": f"step_kernel<{args.model},{args.prec},diag>", "ms_per_launch": round(step_ms, 4)}
+    alu = None
+    if args.prec == "f64":
+        peak_f64 = capi.lbm_measure_peak(0)
+        flops = FLOP_PER_NODE[args.model] * n / (step_ms * 1e-3)
+        alu = {"bound": "alu", "achieved": round(flops / 1e12, 4), "peak": round(peak_f64 / 1e12, 4),
+               "unit": "TFLOP/s", "frac": round(flops / peak_f64, 4), "traffic": None,
+               "peak_source": "FP64 FMA rate measured live on this GPU (lbm_measure_peak)",
+               "flop_per_node": FLOP_PER_NODE[args.model],
+               "kernel": roof["kernel"], "ms_per_launch": round(step_ms, 4)}
+        if alu["frac"] > roof["frac"]:
+            roof, alu = alu, roof
+    lat.close()
+    del lat
+
+    out = {"metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else "f32",
+           "data": "synthetic",
+           "config": {"workload": workload_name(w, args.model, args.prec), "nx": w["nx"], "ny": w["ny"],
+                      "collision": args.model, "storage": args.prec, "theta": w["theta"], "nu": w["nu"],
+                      "tau": w["tau"], "U": w["U"],
+                      "l2": f"inputs larger than L2: two {lat_bytes(args.prec, n)/1e9:.2f} GB population buffers",
+                      "parallelism": f"one independent lattice per GPU (replicas), {world} GPU(s)"},
+           "roofline": roof, "roofline_other": alu,
+           "gpu_launches": 2 * args.steps,
+           "gpu_launches_note": "per step: 1 fused step kernel + 1 diagnostics finalisation kernel",
+           "clocks": clocks.summary(),
+           "final_diagnostics": {"t": t_diag, "mass": diag[0], "mom_x": diag[1], "mom_y": diag[2],
+                                 "kinetic": diag[3], "nonfinite": diag[4]}}
+
+    # ---- end to end through the host-buffer entry point
+    if rank == 0 or world > 1:
+        host = [torch.from_numpy(a).pin_memory() for a in (rho, ux, uy)]
+        res = [torch.empty((w["ny"], w["nx"]), dtype=torch.float64).pin_memory() for _ in range(3)]
+        lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], args.model, args.prec, device=dev, stream=stream)
+        lat.set_diagnostics_interval(1)
+        ptrs = [h.data_ptr() for h in host] + [r.data_ptr() for r in res]
+        capi.lbm_run_host(lat.ctx, *ptrs[:3], 2, *ptrs[3:], want_diag=True)  # warm-up (staging allocation)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_calls):
+            capi.lbm_run_host(lat.ctx, *ptrs[:3], args.e2e_steps, *ptrs[3:], want_diag=True)
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        lat.close()
+        out["e2e"] = {"value": round(world * n * args.e2e_steps * args.e2e_calls / dt / 1e6, 2), "unit": "MLUPS",
+                      "h2d_bytes_per_step": round(3 * 8 * n / args.e2e_steps),
+                      "d2h_bytes_per_step": round((3 * 8 * n + 5 * 8) / args.e2e_steps),
+                      "call": f"lbm_run_host: upload rho0,u0 (pinned) -> init -> {args.e2e_steps} steps with "
+                              f"diagnostics -> download rho,u and diagnostics; {args.e2e_calls} calls timed"}
+
+    # ---- per-model / per-precision sweep on the same flow
+    if not args.no_forms:
+        out["forms"] = forms_sweep(w, fields, dev, stream, peak_hbm)
+
+    # ---- CPU baseline (oracle) on rank 0 at N = 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_mlups(w, args.model)
+        out["cpu_baseline"] = {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                               "sample": sample}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def lat_bytes(prec, n):
+    return BYTES_PER_NODE[prec] // 2 * n
+
+
+def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=200):
+    """MLUPS of every model in FP64 and of the complete model in the shifted FP32 / FP16 forms,
+    with the velocity error of the shifted forms against FP64 after err_steps steps."""
+    import torch
+
+    from paper_2602_21242_gb300.lattice import Lattice
+
+    n = w["nx"] * w["ny"]
+    res = {}
+
+    def timed(model, prec):
+        lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], model, prec, device=dev, stream=stream)
+        lat.init(*fields)
+        lat.set_diagnostics_interval(1)
+        lat.step(warm)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        lat.sync()
+        ms = e0.elapsed_time(e1) / steps
+        lat.close()
+        mlups = n / (ms * 1e-3) / 1e6
+        gbs = BYTES_PER_NODE[prec] * n / (ms * 1e-3) / 1e9
+        return {"mlups": round(mlups, 1), "ms_per_step": round(ms, 4), "hbm_gbs": round(gbs, 1),
+                "hbm_frac": round(gbs / peak_hbm, 4)}
+
+    for model in MODEL_NAMES:
+        res[f"{model}/f64"] = timed(model, "f64")
+    for prec in ("f32", "f16"):
+        res[f"complete/{prec}"] = timed("complete", prec)
+
+    # velocity error of the shifted forms against FP64 on the same flow
+    finals = {}
+    for prec in ("f64", "f32", "f16"):
+        lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], "complete", prec, device=dev, stream=stream)
+        lat.init(*fields)
+        lat.step(err_steps)
+        finals[prec] = [t.clone() for t in lat.moments()]
+        lat.close()
+    for prec in ("f32", "f16"):
+        du = max(float((finals[prec][k] - finals["f64"][k]).abs().max()) for k in (1, 2))
+        dr = float((finals[prec][0] - finals["f64"][0]).abs().max())
+        res[f"complete/{prec}"]["error_vs_f64"] = {
+            "steps": err_steps, "max_abs_du_over_U": du / w["U"], "max_abs_drho": dr}
+    return res
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, timed on the host cores (the reference arm)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2602_21242_gb300 import flows
+
+    w = workload(args.n)
+    cores = O.set_threads(os.cpu_count() or 1)
+    m = MODEL_NAMES.index(args.model)
+    # bounded sample per step: a band of rows of the same flow, sized to ~1 s of oracle work
+    band = min(w["ny"], 256)
+    rho, ux, uy = flows.shear_wave(w["nx"], band, U=w["U"], amp=w["amp"])
+    f = O.init(rho, ux, uy, w["theta"])
+    t0 = time.perf_counter()
+    f = O.run(f, w["theta"], w["tau"], m, 1)
+    t1 = time.perf_counter() - t0
+    band = max(8, min(w["ny"], int(band * 1.0 / max(t1, 1e-6))))
+    rho, ux, uy = flows.shear_wave(w["nx"], band, U=w["U"], amp=w["amp"])
+    f = O.init(rho, ux, uy, w["theta"])
+    for _ in range(args.warmup):
+        f = O.run(f, w["theta"], w["tau"], m, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.run(f, w["theta"], w["tau"], m, 1)
+    dt = time.perf_counter() - t0
+    nodes = w["nx"] * band
+    mlups = nodes * args.steps / dt / 1e6
+    sample = f"per step: one oracle step on a {w['nx']}x{band} periodic band of the same flow"
+    out = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": workload_name(w, args.model, "f64"), "nx": w["nx"], "ny": w["ny"],
+                      "collision": args.model, "storage": "f64", "theta": w["theta"], "nu": w["nu"],
+                      "tau": w["tau"], "U": w["U"]},
+           "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * lbm.h -- C ABI of the GB300 D2Q9 generalized Onsager-regularised lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * Method: arXiv 2602.21242 ("Generalized Onsager-Regularized Lattice Boltzmann
+ * Method for error-free Navier-Stokes models on standard lattices"). One time
+ * step is the lattice Boltzmann equation, Eq. 1: collide every node,
+ *   f*_i = f^eq_i + (1 - 1/tau) g_i                                  (Eq. 1a)
+ * then propagate f*_i(x, t) -> f_i(x + c_i, t + 1)                   (Eq. 1b)
+ * on a doubly periodic nx x ny D2Q9 grid (velocities numbered as in Fig. 1a),
+ * with f^eq the guided equilibrium (Eq. 10) and g chosen by the model:
+ *   LBM_LBGK           g = f - f^eq                         (Eq. 1a, Sec. 1)
+ *   LBM_OREG           g = f^OReg                            (Eq. 2)
+ *   LBM_OREG_PARTIAL   g = f^OReg + Psi^P                    (Eqs. 7, 14)
+ *   LBM_OREG_COMPLETE  g = f^OReg + Psi^C, with Pi~ from Eqs. 11b and 12 (Eqs. 7, 15)
+ *
+ * Conventions shared by every call:
+ *   - Fields are row-major [y][x] (x fastest), nx * ny doubles, unpadded.
+ *     Population arrays are [i][y][x], 9 * nx * ny doubles, i in Fig. 1a order:
+ *     c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1) c5=(1,1) c6=(-1,1) c7=(-1,-1) c8=(1,-1).
+ *   - The STATE of a lattice at time t is its pre-collision populations f(x, t).
+ *     lbm_init sets f(x, 0) = f^eq(rho0(x), u0(x)); lbm_step advances t.
+ *   - theta is the reduced lattice temperature, tau the relaxation time. The
+ *     lattice viscosity is nu = theta (tau - 1/2): the paper prints tau = nu/theta
+ *     (Sec. 1); the 1/2 follows from the (1 - dt/2tau) factors of Eq. 5 at dt = 1.
+ *   - Pointers named d_* are DEVICE pointers, h_* are HOST pointers; all are
+ *     owned by the caller and must stay valid until the call's work completes
+ *     on the lattice's stream (calls are asynchronous unless stated).
+ *   - Every call returns an lbm_status. On failure, lbm_last_error(ctx) holds a
+ *     one-line message. A call that fails leaves the lattice's state unchanged
+ *     unless stated otherwise.
+ *   - A lattice is bound to the CUDA device that was current at creation; call
+ *     with the same device current. Calls on one lattice are not thread-safe.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Collision models (Sec. 4). */
+enum lbm_model {
+  LBM_LBGK = 0,
+  LBM_OREG = 1,
+  LBM_OREG_PARTIAL = 2,
+  LBM_OREG_COMPLETE = 3
+};
+
+/* Storage / arithmetic forms.
+ *   LBM_F64        populations stored in FP64, all arithmetic in FP64.
+ *   LBM_F32_SHIFT  stored as deviations f_i - rho_ref w_i(theta) in FP32, where
+ *                  w_i(theta) is the rest GEq (Eq. 10 at u = 0) and rho_ref = 1;
+ *                  collision arithmetic in FP32, reductions in FP64.
+ *   LBM_F16_SHIFT  as LBM_F32_SHIFT with the deviations stored in IEEE FP16. */
+enum lbm_prec {
+  LBM_F64 = 0,
+  LBM_F32_SHIFT = 1,
+  LBM_F16_SHIFT = 2
+};
+
+enum lbm_status {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,     /* an argument is out of range or a pointer is NULL      */
+  LBM_ENOMEM = -2,     /* device or host allocation failed                       */
+  LBM_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed            */
+  LBM_ENONFINITE = -4, /* a diagnostics pass found non-finite populations        */
+  LBM_ETIMEOUT = -5,   /* a bounded device-side wait gave up                     */
+  LBM_ESTATE = -6      /* call out of order (e.g. stepping before lbm_init)      */
+};
+
+/* Library version, (major << 16) | minor. */
+int lbm_version(void);
+
+/*
+ * Device memory layout of one population buffer for (nx, ny, prec): each of the
+ * 9 planes has ny rows of *pitch elements (pitch >= nx, rows 128-byte aligned) and
+ * planes are *plane elements apart (256-byte aligned). *state_bytes is the size
+ * of ONE buffer; a lattice holds two (ping-pong). Any output pointer may be NULL.
+ * Errors: LBM_EINVAL for nx, ny < 1, sizes whose buffers exceed 2^40 bytes, or an
+ * unknown prec.
+ */
+int lbm_layout(int nx, int ny, int prec, long long* pitch, long long* plane,
+               long long* state_bytes);
+
+/*
+ * Create a lattice for the problem of Sec. 1 / Eq. 1: nx x ny periodic grid,
+ * temperature theta, relaxation time tau and collision model (enum lbm_model),
+ * FP64 storage, on the legacy default stream, library-owned buffers.
+ * Errors: LBM_EINVAL unless nx, ny >= 1, 0 < theta < 1, tau > 1/2 and model in
+ * range; LBM_ENOMEM; LBM_ECUDA (e.g. no device). *out is set only on success.
+ */
+int lbm_create(int nx, int ny, double theta, double tau, int model, lbm_ctx** out);
+
+/*
+ * As lbm_create with a storage form (enum lbm_prec), a CUDA stream (a
+ * cudaStream_t cast to void*, NULL = legacy default stream) and, optionally,
+ * caller-owned population memory: d_pop_buffers, if not NULL, is a device
+ * pointer to 2 * state_bytes bytes (see lbm_layout), 256-byte aligned, that the
+ * caller keeps alive until lbm_destroy; the library never frees it.
+ */
+int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
+                  void* stream, void* d_pop_buffers, lbm_ctx** out);
+
+/* Release the lattice and the device memory it owns. NULL is accepted. Synchronises its stream. */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Rebind the lattice to another stream (cudaStream_t as void*, NULL = legacy default). */
+int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/*
+ * Initial state f(x, 0) = f^eq(rho0(x), u0(x)), the guided equilibrium of Eq. 10,
+ * at every node; resets the step counter to 0. d_rho, d_ux, d_uy: device arrays
+ * of nx * ny doubles. GEq populations are positive only where
+ * 1 - theta - u^2 > 0 and theta + u^2 > |u| per axis; the call does not check.
+ */
+int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double* d_uy);
+
+/*
+ * Advance the state by n >= 0 time steps of Eq. 1 (fused pull-stream + collide).
+ * Asynchronous. If a diagnostics interval M > 0 is set, every step whose start
+ * time t is a multiple of M also reduces the diagnostics of f(x, t) (see
+ * lbm_diagnostics) on the device; lbm_sync / lbm_step_diagnostics report them.
+ * Errors: LBM_ESTATE before lbm_init or lbm_set_state; LBM_EINVAL for n < 0.
+ */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Fused diagnostics interval M (0 = off, the default). */
+int lbm_set_diagnostics_interval(lbm_ctx* ctx, int every);
+
+/*
+ * Latest diagnostics reduced inside lbm_step: h_out5 as in lbm_diagnostics,
+ * *h_time = the time t they describe (-1 if none yet). Synchronises the stream.
+ * Returns LBM_ENONFINITE if any fused pass so far met a non-finite population.
+ */
+int lbm_step_diagnostics(lbm_ctx* ctx, double* h_out5, long long* h_time);
+
+/*
+ * Moments of the current state (Sec. 1): rho = sum_i f_i and u = sum_i c_i f_i / rho,
+ * written to device arrays of nx * ny doubles.
+ */
+int lbm_moments(lbm_ctx* ctx, double* d_rho, double* d_ux, double* d_uy);
+
+/*
+ * Global diagnostics of the current state, reduced on the device in a fixed
+ * order (deterministic for a given size) in FP64, written to the HOST array
+ * h_out5 = { sum rho, sum rho u_x, sum rho u_y, sum rho |u|^2 / 2,
+ * number of nodes with a non-finite population } (sums skip those nodes).
+ * Synchronises. Returns LBM_ENONFINITE when out5[4] > 0 (out5 is still written).
+ */
+int lbm_diagnostics(lbm_ctx* ctx, double* h_out5);
+
+/* Copy the state f(x, t) to / from a device array of 9 * nx * ny doubles ([i][y][x]). */
+int lbm_get_state(lbm_ctx* ctx, double* d_f);
+int lbm_set_state(lbm_ctx* ctx, const double* d_f);
+
+/* Current time t (steps since lbm_init / lbm_set_state). */
+int lbm_time(const lbm_ctx* ctx, long long* h_t);
+
+/*
+ * End-to-end call on HOST memory: copy rho0, u0 (host, nx * ny doubles each;
+ * page-locked memory recommended) to the device, lbm_init, run n steps, copy the
+ * final moments to h_rho, h_ux, h_uy (host, may be NULL to skip) and the final
+ * diagnostics to h_diag5 (host, may be NULL). Synchronous. Device staging
+ * memory is allocated on the first call and kept by the lattice.
+ */
+int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const double* h_uy0,
+                 int n, double* h_rho, double* h_ux, double* h_uy, double* h_diag5);
+
+/* Wait for the lattice's stream; report a pending CUDA error (LBM_ECUDA) or a
+ * non-finite population seen by a fused diagnostics pass (LBM_ENONFINITE). */
+int lbm_sync(lbm_ctx* ctx);
+
+/*
+ * Measured arithmetic ceiling of the current device (no counterpart in the
+ * paper; used as the roofline denominator of ALU-bound kernels): kind 0 = FP64,
+ * kind 1 = FP32, as FLOP/s of fused multiply-adds (2 FLOP each) from independent
+ * FMA chains on 8 blocks per SM, best of 3 timed launches. Synchronous, runs on
+ * the legacy default stream and allocates a small scratch buffer.
+ */
+int lbm_measure_peak(int kind, double* h_flops);
+
+/* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,194 @@
+"""ctypes binding of liblbm.so -- the C ABI of include/lbm.h, same names.
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels. If the library cannot be found or built, loading raises
+``RuntimeError``; there is no Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LBM_LBGK, LBM_OREG, LBM_OREG_PARTIAL, LBM_OREG_COMPLETE = 0, 1, 2, 3
+LBM_F64, LBM_F32_SHIFT, LBM_F16_SHIFT = 0, 1, 2
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_ENONFINITE",
+                -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
+MODELS = {"lbgk": LBM_LBGK, "oreg": LBM_OREG, "partial": LBM_OREG_PARTIAL, "complete": LBM_OREG_COMPLETE}
+PRECS = {"f64": LBM_F64, "f32": LBM_F32_SHIFT, "f16": LBM_F16_SHIFT}
+
+_lock = threading.Lock()
+_lib = None
+
+_i, _d, _p, _ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+_pll = ctypes.POINTER(ctypes.c_longlong)
+_pd = ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "lbm_version": ([], _i),
+    "lbm_layout": ([_i, _i, _i, _pll, _pll, _pll], _i),
+    "lbm_create": ([_i, _i, _d, _d, _i, ctypes.POINTER(_p)], _i),
+    "lbm_create_ex": ([_i, _i, _d, _d, _i, _i, _p, _p, ctypes.POINTER(_p)], _i),
+    "lbm_destroy": ([_p], _i),
+    "lbm_set_stream": ([_p, _p], _i),
+    "lbm_init": ([_p, _p, _p, _p], _i),
+    "lbm_step": ([_p, _i], _i),
+    "lbm_set_diagnostics_interval": ([_p, _i], _i),
+    "lbm_step_diagnostics": ([_p, _pd, _pll], _i),
+    "lbm_moments": ([_p, _p, _p, _p], _i),
+    "lbm_diagnostics": ([_p, _pd], _i),
+    "lbm_get_state": ([_p, _p], _i),
+    "lbm_set_state": ([_p, _p], _i),
+    "lbm_time": ([_p, _pll], _i),
+    "lbm_run_host": ([_p, _p, _p, _p, _i, _p, _p, _p, _pd], _i),
+    "lbm_sync": ([_p], _i),
+    "lbm_measure_peak": ([_i, _pd], _i),
+    "lbm_last_error": ([_p], ctypes.c_char_p),
+}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load liblbm.so (building it first if it is absent or stale and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            try:
+                path = _build.build()
+            except RuntimeError:
+                if not os.path.exists(path):
+                    raise
+        if not os.path.exists(path):
+            raise RuntimeError(f"liblbm.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def last_error(ctx=None) -> str:
+    msg = load().lbm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def check(status: int, ctx=None) -> int:
+    if status != LBM_OK:
+        raise LBMError(status, last_error(ctx))
+    return status
+
+
+# ---------------------------------------------------------------- thin wrappers (same names as the ABI)
+
+def lbm_version() -> int:
+    return load().lbm_version()
+
+
+def lbm_layout(nx: int, ny: int, prec: int):
+    pitch, plane, nbytes = _ll(), _ll(), _ll()
+    check(load().lbm_layout(nx, ny, prec, ctypes.byref(pitch), ctypes.byref(plane), ctypes.byref(nbytes)))
+    return pitch.value, plane.value, nbytes.value
+
+
+def lbm_create(nx: int, ny: int, theta: float, tau: float, model: int):
+    ctx = _p()
+    check(load().lbm_create(nx, ny, theta, tau, model, ctypes.byref(ctx)))
+    return ctx
+
+
+def lbm_create_ex(nx: int, ny: int, theta: float, tau: float, model: int, prec: int, stream: int = 0,
+                  pop_buffers: int = 0):
+    ctx = _p()
+    check(load().lbm_create_ex(nx, ny, theta, tau, model, prec, stream or None, pop_buffers or None,
+                               ctypes.byref(ctx)))
+    return ctx
+
+
+def lbm_destroy(ctx) -> None:
+    check(load().lbm_destroy(ctx))
+
+
+def lbm_set_stream(ctx, stream: int) -> None:
+    check(load().lbm_set_stream(ctx, stream or None), ctx)
+
+
+def lbm_init(ctx, d_rho: int, d_ux: int, d_uy: int) -> None:
+    check(load().lbm_init(ctx, d_rho, d_ux, d_uy), ctx)
+
+
+def lbm_step(ctx, n: int) -> None:
+    check(load().lbm_step(ctx, n), ctx)
+
+
+def lbm_set_diagnostics_interval(ctx, every: int) -> None:
+    check(load().lbm_set_diagnostics_interval(ctx, every), ctx)
+
+
+def lbm_step_diagnostics(ctx, raise_nonfinite: bool = True):
+    out = (ctypes.c_double * 5)()
+    t = _ll()
+    s = load().lbm_step_diagnostics(ctx, out, ctypes.byref(t))
+    if s != LBM_OK and (raise_nonfinite or s != LBM_ENONFINITE):
+        check(s, ctx)
+    return list(out), t.value, s
+
+
+def lbm_moments(ctx, d_rho: int, d_ux: int, d_uy: int) -> None:
+    check(load().lbm_moments(ctx, d_rho, d_ux, d_uy), ctx)
+
+
+def lbm_diagnostics(ctx, raise_nonfinite: bool = True):
+    out = (ctypes.c_double * 5)()
+    s = load().lbm_diagnostics(ctx, out)
+    if s != LBM_OK and (raise_nonfinite or s != LBM_ENONFINITE):
+        check(s, ctx)
+    return list(out), s
+
+
+def lbm_get_state(ctx, d_f: int) -> None:
+    check(load().lbm_get_state(ctx, d_f), ctx)
+
+
+def lbm_set_state(ctx, d_f: int) -> None:
+    check(load().lbm_set_state(ctx, d_f), ctx)
+
+
+def lbm_time(ctx) -> int:
+    t = _ll()
+    check(load().lbm_time(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def lbm_run_host(ctx, h_rho0: int, h_ux0: int, h_uy0: int, n: int, h_rho: int = 0, h_ux: int = 0, h_uy: int = 0,
+                 want_diag: bool = False):
+    diag = (ctypes.c_double * 5)() if want_diag else None
+    check(load().lbm_run_host(ctx, h_rho0, h_ux0, h_uy0, n, h_rho or None, h_ux or None, h_uy or None, diag), ctx)
+    return list(diag) if want_diag else None
+
+
+def lbm_sync(ctx) -> None:
+    check(load().lbm_sync(ctx), ctx)
+
+
+def lbm_measure_peak(kind: int) -> float:
+    """FLOP/s ceiling of the current device: kind 0 = FP64 FMA, 1 = FP32 FMA."""
+    v = ctypes.c_double()
+    check(load().lbm_measure_peak(kind, ctypes.byref(v)))
+    return v.value

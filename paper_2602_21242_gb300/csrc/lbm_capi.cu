@@ -1,0 +1,411 @@
+// lbm_capi.cu -- implementation of the C ABI declared in include/lbm.h.
+//
+// A lattice (lbm_ctx) owns two population buffers (ping-pong), the per-block
+// diagnostics partials and a few device scalars. Each call validates its
+// arguments on the host, enqueues kernels on the lattice's stream and returns a
+// status; only the calls documented as synchronous wait for the device.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "lbm.h"
+#include "lbm_launch.h"
+
+struct lbm_ctx {
+  int device = 0;
+  int nx = 0, ny = 0, model = 0, prec = 0;
+  double theta = 0, tau = 0, rho_ref = 0;
+  olbm::Geometry g{};
+  long long state_bytes = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;  // buffer holding the current state
+  bool own_buffers = true;
+  bool initialised = false;
+  cudaStream_t stream = nullptr;
+  double* d_partials = nullptr;
+  long long nparts = 0;
+  double* d_diag = nullptr;      // [6] latest fused diagnostics (out5 + time)
+  double* d_diag_now = nullptr;  // [6] scratch of lbm_diagnostics
+  unsigned long long* d_sticky = nullptr;
+  int diag_every = 0;
+  long long t = 0;
+  long long last_diag_t = -1;
+  double* d_stage = nullptr;  // lbm_run_host staging, 6 * nodes doubles
+  char err[320] = {0};
+};
+
+namespace {
+
+thread_local char g_create_err[320] = "";
+
+int fail(lbm_ctx* ctx, int status, const char* fmt, ...) {
+  char* dst = ctx ? ctx->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, sizeof(g_create_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+long long elem_size(int prec) { return prec == LBM_F64 ? 8 : (prec == LBM_F32_SHIFT ? 4 : 2); }
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+bool layout_of(int nx, int ny, int prec, long long* pitch, long long* plane, long long* bytes) {
+  if (nx < 1 || ny < 1 || prec < LBM_F64 || prec > LBM_F16_SHIFT) return false;
+  const long long es = elem_size(prec);
+  const long long p = round_up(nx, 128 / es);         // 128-byte rows
+  const long long pl = round_up(p * (long long)ny, 256 / es);  // 256-byte planes
+  const long long b = 9 * pl * es;
+  if (p > (1LL << 31) || b > (1LL << 40)) return false;
+  if (pitch) *pitch = p;
+  if (plane) *plane = pl;
+  if (bytes) *bytes = b;
+  return true;
+}
+
+long long nodes_of(const lbm_ctx* c) { return (long long)c->nx * c->ny; }
+
+cudaError_t launch_step(const olbm::StepArgs& a, int prec, cudaStream_t st) {
+  switch (prec) {
+    case LBM_F64: return olbm::launch_step_f64(a, st);
+    case LBM_F32_SHIFT: return olbm::launch_step_f32(a, st);
+    default: return olbm::launch_step_f16(a, st);
+  }
+}
+
+cudaError_t launch_diag(const lbm_ctx* c, cudaStream_t st) {
+  const void* src = c->buf[c->cur];
+  switch (c->prec) {
+    case LBM_F64: return olbm::launch_diag_f64(src, c->g, c->rho_ref, c->d_partials, st);
+    case LBM_F32_SHIFT: return olbm::launch_diag_f32(src, c->g, c->rho_ref, c->d_partials, st);
+    default: return olbm::launch_diag_f16(src, c->g, c->rho_ref, c->d_partials, st);
+  }
+}
+
+int check_ctx(lbm_ctx* ctx) {
+  if (!ctx) return LBM_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device)
+    return fail(ctx, LBM_EINVAL, "the current CUDA device (%d) is not the lattice's device (%d)", dev, ctx->device);
+  return LBM_OK;
+}
+
+void free_ctx(lbm_ctx* c) {
+  if (!c) return;
+  if (c->own_buffers) {
+    cudaFree(c->buf[0]);
+    cudaFree(c->buf[1]);
+  }
+  cudaFree(c->d_partials);
+  cudaFree(c->d_diag);
+  cudaFree(c->d_diag_now);
+  cudaFree(c->d_sticky);
+  cudaFree(c->d_stage);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_version(void) { return (1 << 16) | 0; }
+
+int lbm_layout(int nx, int ny, int prec, long long* pitch, long long* plane, long long* state_bytes) {
+  return layout_of(nx, ny, prec, pitch, plane, state_bytes) ? LBM_OK : LBM_EINVAL;
+}
+
+int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec, void* stream,
+                  void* d_pop_buffers, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  long long pitch, plane, bytes;
+  if (!layout_of(nx, ny, prec, &pitch, &plane, &bytes))
+    return fail(nullptr, LBM_EINVAL, "invalid size or precision (nx=%d ny=%d prec=%d)", nx, ny, prec);
+  if (!(theta > 0.0 && theta < 1.0)) return fail(nullptr, LBM_EINVAL, "theta must lie in (0, 1), got %g", theta);
+  if (!(tau > 0.5) || !std::isfinite(tau))
+    return fail(nullptr, LBM_EINVAL, "tau must exceed 1/2 (positive viscosity), got %g", tau);
+  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE)
+    return fail(nullptr, LBM_EINVAL, "unknown collision model %d", model);
+  if (d_pop_buffers && (reinterpret_cast<uintptr_t>(d_pop_buffers) % 256) != 0)
+    return fail(nullptr, LBM_EINVAL, "population buffers must be 256-byte aligned");
+
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, LBM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  c->nx = nx;
+  c->ny = ny;
+  c->model = model;
+  c->prec = prec;
+  c->theta = theta;
+  c->tau = tau;
+  c->rho_ref = (prec == LBM_F64) ? 0.0 : 1.0;
+  c->g = olbm::Geometry{nx, ny, pitch, plane};
+  c->state_bytes = bytes;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->nparts = olbm::node_blocks(c->g);
+
+  if (d_pop_buffers) {
+    c->own_buffers = false;
+    c->buf[0] = d_pop_buffers;
+    c->buf[1] = static_cast<char*>(d_pop_buffers) + bytes;
+  } else {
+    for (int k = 0; k < 2; ++k) {
+      e = cudaMalloc(&c->buf[k], (size_t)bytes);
+      if (e != cudaSuccess) {
+        free_ctx(c);
+        cudaGetLastError();
+        return fail(nullptr, LBM_ENOMEM, "cudaMalloc of %lld bytes: %s", bytes, cudaGetErrorString(e));
+      }
+    }
+  }
+  if ((e = cudaMalloc(&c->d_partials, sizeof(double) * 5 * (size_t)c->nparts)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_diag, sizeof(double) * 6)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_diag_now, sizeof(double) * 6)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, LBM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+  }
+  // Defined contents everywhere, including row and plane padding.
+  if ((e = cudaMemsetAsync(c->buf[0], 0, (size_t)bytes, c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->buf[1], 0, (size_t)bytes, c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_diag, 0, sizeof(double) * 6, c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_sticky, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess) {
+    free_ctx(c);
+    return fail(nullptr, LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, double theta, double tau, int model, lbm_ctx** out) {
+  return lbm_create_ex(nx, ny, theta, tau, model, LBM_F64, nullptr, nullptr, out);
+}
+
+int lbm_destroy(lbm_ctx* ctx) {
+  if (!ctx) return LBM_OK;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx* ctx, void* stream) {
+  if (!ctx) return LBM_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double* d_uy) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!d_rho || !d_ux || !d_uy) return fail(ctx, LBM_EINVAL, "lbm_init: NULL field pointer");
+  cudaError_t e;
+  void* dst = ctx->buf[ctx->cur];
+  switch (ctx->prec) {
+    case LBM_F64: e = olbm::launch_init_f64(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+    case LBM_F32_SHIFT: e = olbm::launch_init_f32(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+    default: e = olbm::launch_init_f16(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_init launch");
+  e = cudaMemsetAsync(ctx->d_sticky, 0, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_init reset");
+  ctx->initialised = true;
+  ctx->t = 0;
+  ctx->last_diag_t = -1;
+  return LBM_OK;
+}
+
+int lbm_set_diagnostics_interval(lbm_ctx* ctx, int every) {
+  if (!ctx) return LBM_EINVAL;
+  if (every < 0) return fail(ctx, LBM_EINVAL, "diagnostics interval must be >= 0");
+  ctx->diag_every = every;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* ctx, int n) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n must be >= 0");
+  if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_step before lbm_init / lbm_set_state");
+  olbm::StepArgs a;
+  a.model = ctx->model;
+  a.g = ctx->g;
+  a.theta = ctx->theta;
+  a.tau = ctx->tau;
+  a.rho_ref = ctx->rho_ref;
+  a.partials = ctx->d_partials;
+  for (int k = 0; k < n; ++k) {
+    a.diag = ctx->diag_every > 0 && (ctx->t % ctx->diag_every) == 0;
+    a.src = ctx->buf[ctx->cur];
+    a.dst = ctx->buf[ctx->cur ^ 1];
+    cudaError_t e = launch_step(a, ctx->prec, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step launch");
+    if (a.diag) {
+      e = olbm::launch_finalize(ctx->d_partials, (int)ctx->nparts, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
+                                ctx->d_sticky, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step diagnostics launch");
+      ctx->last_diag_t = ctx->t;
+    }
+    ctx->cur ^= 1;
+    ctx->t += 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_step_diagnostics(lbm_ctx* ctx, double* h_out5, long long* h_time) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!h_out5) return fail(ctx, LBM_EINVAL, "lbm_step_diagnostics: NULL output");
+  double d[6];
+  unsigned long long bad = 0;
+  cudaError_t e = cudaMemcpyAsync(d, ctx->d_diag, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_sticky, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step_diagnostics");
+  for (int k = 0; k < 5; ++k) h_out5[k] = ctx->last_diag_t >= 0 ? d[k] : 0.0;
+  if (h_time) *h_time = ctx->last_diag_t;
+  if (bad > 0) return fail(ctx, LBM_ENONFINITE, "%llu non-finite node(s) met by fused diagnostics", bad);
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* ctx, double* d_rho, double* d_ux, double* d_uy) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!d_rho || !d_ux || !d_uy) return fail(ctx, LBM_EINVAL, "lbm_moments: NULL field pointer");
+  if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_moments before lbm_init / lbm_set_state");
+  const void* src = ctx->buf[ctx->cur];
+  cudaError_t e;
+  switch (ctx->prec) {
+    case LBM_F64: e = olbm::launch_moments_f64(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
+    case LBM_F32_SHIFT: e = olbm::launch_moments_f32(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
+    default: e = olbm::launch_moments_f16(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
+  }
+  return e == cudaSuccess ? LBM_OK : cuda_fail(ctx, e, "lbm_moments launch");
+}
+
+int lbm_diagnostics(lbm_ctx* ctx, double* h_out5) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!h_out5) return fail(ctx, LBM_EINVAL, "lbm_diagnostics: NULL output");
+  if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_diagnostics before lbm_init / lbm_set_state");
+  cudaError_t e = launch_diag(ctx, ctx->stream);
+  if (e == cudaSuccess)
+    e = olbm::launch_finalize(ctx->d_partials, (int)ctx->nparts, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag_now,
+                              nullptr, ctx->stream);
+  double d[6];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, ctx->d_diag_now, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_diagnostics");
+  for (int k = 0; k < 5; ++k) h_out5[k] = d[k];
+  if (d[4] > 0) return fail(ctx, LBM_ENONFINITE, "%.0f node(s) hold non-finite populations", d[4]);
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx* ctx, double* d_f) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!d_f) return fail(ctx, LBM_EINVAL, "lbm_get_state: NULL pointer");
+  if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_get_state before lbm_init / lbm_set_state");
+  const void* src = ctx->buf[ctx->cur];
+  cudaError_t e;
+  switch (ctx->prec) {
+    case LBM_F64: e = olbm::launch_get_state_f64(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
+    case LBM_F32_SHIFT: e = olbm::launch_get_state_f32(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
+    default: e = olbm::launch_get_state_f16(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
+  }
+  return e == cudaSuccess ? LBM_OK : cuda_fail(ctx, e, "lbm_get_state launch");
+}
+
+int lbm_set_state(lbm_ctx* ctx, const double* d_f) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!d_f) return fail(ctx, LBM_EINVAL, "lbm_set_state: NULL pointer");
+  void* dst = ctx->buf[ctx->cur];
+  cudaError_t e;
+  switch (ctx->prec) {
+    case LBM_F64: e = olbm::launch_set_state_f64(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+    case LBM_F32_SHIFT: e = olbm::launch_set_state_f32(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+    default: e = olbm::launch_set_state_f16(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_state launch");
+  e = cudaMemsetAsync(ctx->d_sticky, 0, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_state reset");
+  ctx->initialised = true;
+  ctx->t = 0;
+  ctx->last_diag_t = -1;
+  return LBM_OK;
+}
+
+int lbm_time(const lbm_ctx* ctx, long long* h_t) {
+  if (!ctx || !h_t) return LBM_EINVAL;
+  *h_t = ctx->t;
+  return LBM_OK;
+}
+
+int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const double* h_uy0, int n, double* h_rho,
+                 double* h_ux, double* h_uy, double* h_diag5) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!h_rho0 || !h_ux0 || !h_uy0) return fail(ctx, LBM_EINVAL, "lbm_run_host: NULL input");
+  if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_run_host: n must be >= 0");
+  const size_t N = (size_t)nodes_of(ctx);
+  cudaError_t e;
+  if (!ctx->d_stage) {
+    e = cudaMalloc(&ctx->d_stage, sizeof(double) * 6 * N);
+    if (e != cudaSuccess) {
+      ctx->d_stage = nullptr;
+      cudaGetLastError();
+      return fail(ctx, LBM_ENOMEM, "lbm_run_host staging: %s", cudaGetErrorString(e));
+    }
+  }
+  double* in = ctx->d_stage;
+  double* outp = ctx->d_stage + 3 * N;
+  const size_t fb = sizeof(double) * N;
+  if ((e = cudaMemcpyAsync(in, h_rho0, fb, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(in + N, h_ux0, fb, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(in + 2 * N, h_uy0, fb, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "lbm_run_host upload");
+  if ((s = lbm_init(ctx, in, in + N, in + 2 * N)) != LBM_OK) return s;
+  if ((s = lbm_step(ctx, n)) != LBM_OK) return s;
+  if (h_rho || h_ux || h_uy) {
+    if ((s = lbm_moments(ctx, outp, outp + N, outp + 2 * N)) != LBM_OK) return s;
+    if (h_rho && (e = cudaMemcpyAsync(h_rho, outp, fb, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "lbm_run_host download");
+    if (h_ux && (e = cudaMemcpyAsync(h_ux, outp + N, fb, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "lbm_run_host download");
+    if (h_uy && (e = cudaMemcpyAsync(h_uy, outp + 2 * N, fb, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "lbm_run_host download");
+  }
+  if (h_diag5) return lbm_diagnostics(ctx, h_diag5);  // synchronises
+  e = cudaStreamSynchronize(ctx->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(ctx, e, "lbm_run_host sync");
+}
+
+int lbm_sync(lbm_ctx* ctx) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_sync");
+  unsigned long long bad = 0;
+  e = cudaMemcpyAsync(&bad, ctx->d_sticky, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_sync flag read");
+  if (bad > 0) return fail(ctx, LBM_ENONFINITE, "%llu non-finite node(s) met by fused diagnostics", bad);
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err : g_create_err; }
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+// lbm_device.cuh -- device-side building blocks of the D2Q9 OReg-GEq step
+// (arXiv 2602.21242): storage forms, per-run coefficients, the per-node
+// collision of Eq. 1a for the four models, the guided equilibrium of Eq. 10,
+// and the fixed-order block reduction used by the diagnostics.
+//
+// Product form. The guided equilibrium factorises per axis (Eq. 10):
+//   f^eq_(a,b) = rho * P_x(a) * P_y(b),  P(0) = 1 - theta - u^2,
+//   P(+-1) = (theta + u^2 +- u)/2,        a, b in {-1, 0, 1},
+// and, with C = c - u, so does every term of the Onsager-regularised
+// non-equilibrium of Eq. 2 (traceless second-moment contraction, D = 2):
+//   f^OReg_(a,b) = K1 [Q_x(a) P_y(b) - P_x(a) Q_y(b)] + K2 R_x(a) R_y(b)
+// with R(a) = P(a) C(a), Q(a) = P(a) C(a)^2, K1 = N_d / (2 theta^2),
+// K2 = N_xy / theta^2, N_d = (Pi^neq_xx - Pi^neq_yy)/2, N_xy = Pi^neq_xy.
+// The moments of f^OReg that the corrections need follow in closed form from
+// sum_a P = 1, sum_a a P = u, sum_a a^2 P = theta + u^2 (exact identities of
+// Eq. 10, not the Chapman-Enskog estimates of Eq. 11a):
+//   psi_x = K1 u_x (1 - 3 theta - u_x^2),  psi_y = -K1 u_y (1 - 3 theta - u_y^2)    (Eq. 6a)
+//   sum_i (c_ix^2 - c_iy^2) f^OReg_i = 2 theta^2 K1 (mu_xx + mu_yy)
+//   => pref = -(K1/2)(mu_xx + mu_yy),  mu_aa = (theta - u_a^2)(1 - theta - u_a^2)/(2 theta^2)  (Eqs. 12, 13b)
+// so no population-level moment sums are needed beyond those of f itself.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace olbm {
+
+// ---------------------------------------------------------------- storage forms
+// PREC 0: FP64 absolute populations. PREC 1: FP32 deviations from the rest
+// state rho_ref * W(a) W(b). PREC 2: FP16 deviations, FP32 arithmetic.
+template <int PREC> struct Form;
+template <> struct Form<0> {
+  using S = double;
+  using T = double;
+  static constexpr bool kShift = false;
+};
+template <> struct Form<1> {
+  using S = float;
+  using T = float;
+  static constexpr bool kShift = true;
+};
+template <> struct Form<2> {
+  using S = __half;
+  using T = float;
+  static constexpr bool kShift = true;
+};
+
+__device__ __forceinline__ double ld_t(const double* p, double) { return __ldg(p); }
+__device__ __forceinline__ float ld_t(const float* p, float) { return __ldg(p); }
+__device__ __forceinline__ float ld_t(const __half* p, float) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void st_t(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st_t(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_t(__half* p, float v) { *p = __float2half_rn(v); }
+
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(__half v) { return (double)__half2float(v); }
+
+template <typename S> __device__ __forceinline__ S from_double(double v);
+template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __half from_double<__half>(double v) {
+  return __float2half_rn((float)v);
+}
+
+// ---------------------------------------------------------------- lattice
+// Population index of velocity (a, b), a, b in {-1, 0, 1}: IDX[a + 1][b + 1]
+// (Fig. 1a numbering: c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1) c5=(1,1) c6=(-1,1)
+// c7=(-1,-1) c8=(1,-1)).
+__host__ __device__ constexpr int pop_index(int a, int b) {
+  return (a == -1) ? (b == -1 ? 7 : (b == 0 ? 3 : 6))
+                   : (a == 0 ? (b == -1 ? 4 : (b == 0 ? 0 : 2)) : (b == -1 ? 8 : (b == 0 ? 1 : 5)));
+}
+__host__ __device__ constexpr int cx_of(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+
+// Geometry of one population buffer.
+struct Geometry {
+  int nx, ny;
+  long long pitch;  // elements between rows
+  long long plane;  // elements between planes
+};
+
+// Per-run coefficients, computed once on the host in FP64 and rounded to T.
+template <typename T> struct Coef {
+  T theta;        // theta
+  T one_m_theta;  // 1 - theta            (P(0) at u = 0)
+  T half_theta;   // theta / 2            (P(+-1) at u = 0)
+  T omega;        // 1 / tau
+  T one_m_omega;  // 1 - 1/tau            (omega')
+  T k1;           // omega' / (4 theta^2): omega' K1 = k1 * (D - rho (u_x^2 - u_y^2))
+  T k2;           // omega' / theta^2:     omega' K2 = k2 * N_xy
+  T c3;           // 1 - 3 theta
+  T tt;           // theta (1 - 3 theta)
+  T inv2t2;       // 1 / (2 theta^2)
+  T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
+  T w[3];         // rho_ref * rest weights per axis pair are W(a) W(b); W(-1) = W(1) = theta/2, W(0) = 1 - theta
+};
+
+template <typename T> __host__ Coef<T> make_coef(double theta, double tau, double rho_ref) {
+  Coef<T> c;
+  const double om = 1.0 / tau, omp = 1.0 - om;
+  c.theta = (T)theta;
+  c.one_m_theta = (T)(1.0 - theta);
+  c.half_theta = (T)(0.5 * theta);
+  c.omega = (T)om;
+  c.one_m_omega = (T)omp;
+  c.k1 = (T)(omp / (4.0 * theta * theta));
+  c.k2 = (T)(omp / (theta * theta));
+  c.c3 = (T)(1.0 - 3.0 * theta);
+  c.tt = (T)(theta * (1.0 - 3.0 * theta));
+  c.inv2t2 = (T)(1.0 / (2.0 * theta * theta));
+  c.rho_ref = (T)rho_ref;
+  c.w[0] = (T)(0.5 * theta);
+  c.w[1] = (T)(1.0 - theta);
+  c.w[2] = (T)(0.5 * theta);
+  return c;
+}
+
+// Moments of one node kept for the diagnostics.
+template <typename T> struct NodeMoments {
+  T m0;  // sum of stored values: rho (absolute) or rho - rho_ref (shifted)
+  T jx, jy, ux, uy;
+};
+
+// ---------------------------------------------------------------- collision
+// In-place collision of one node (Eq. 1a). f holds the stored values of the
+// pulled pre-collision populations (absolute, or deviations from the rest
+// state in the shifted forms); on return it holds the post-collision values
+// in the same representation.
+template <int MODEL, bool SHIFT, typename T>
+__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments<T>& mom) {
+  // Moments (Sec. 1). The rest state has zero momentum, zero
+  // sum (c_x^2 - c_y^2) W and zero sum c_x c_y W, so these sums are the same for
+  // absolute and shifted values.
+  const T s13 = f[1] + f[3], d13 = f[1] - f[3];
+  const T s24 = f[2] + f[4], d24 = f[2] - f[4];
+  const T s57 = f[5] + f[7], d57 = f[5] - f[7];
+  const T s68 = f[6] + f[8], d68 = f[6] - f[8];
+  const T m0 = f[0] + (s13 + s24) + (s57 + s68);
+  const T jx = d13 + (d57 - d68);
+  const T jy = d24 + (d57 + d68);
+  const T rho = SHIFT ? c.rho_ref + m0 : m0;
+  const T inv_rho = T(1) / rho;
+  const T ux = jx * inv_rho, uy = jy * inv_rho;
+  mom.m0 = m0;
+  mom.jx = jx;
+  mom.jy = jy;
+  mom.ux = ux;
+  mom.uy = uy;
+
+  const T ux2 = ux * ux, uy2 = uy * uy;
+  // Per-axis GEq factors P(a) (Eq. 10), a = -1, 0, +1.
+  const T hx = fma(T(0.5), ux2, c.half_theta), hux = T(0.5) * ux;
+  const T hy = fma(T(0.5), uy2, c.half_theta), huy = T(0.5) * uy;
+  const T px[3] = {hx - hux, c.one_m_theta - ux2, hx + hux};
+  const T py[3] = {hy - huy, c.one_m_theta - uy2, hy + huy};
+
+  if constexpr (MODEL == 0) {
+    // LBGK: f* = f + (f^eq - f)/tau = (1 - 1/tau) f + (1/tau) f^eq.
+    if constexpr (!SHIFT) {
+      const T orho = c.omega * rho;
+      const T e[3] = {orho * px[0], orho * px[1], orho * px[2]};
+#pragma unroll
+      for (int a = -1; a <= 1; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+          const int i = pop_index(a, b);
+          f[i] = fma(e[a + 1], py[b + 1], c.one_m_omega * f[i]);
+        }
+    } else {
+      // Shifted: f^eq - rho_ref W W = m0 W_a W_b + rho (dP_x(a) P_y(b) + W_a dP_y(b)),
+      // dP = P - W formed directly (dP(0) = -u^2, dP(+-1) = (u^2 +- u)/2), so no
+      // O(1) terms cancel.
+      const T dx[3] = {fma(T(0.5), ux2, -hux), -ux2, fma(T(0.5), ux2, hux)};
+      const T dy[3] = {fma(T(0.5), uy2, -huy), -uy2, fma(T(0.5), uy2, huy)};
+#pragma unroll
+      for (int a = -1; a <= 1; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+          const int i = pop_index(a, b);
+          const T feq = fma(m0 * c.w[a + 1], c.w[b + 1],
+                            rho * fma(dx[a + 1], py[b + 1], c.w[a + 1] * dy[b + 1]));
+          f[i] = fma(c.omega, feq - f[i], f[i]);
+        }
+    }
+  } else {
+    // Onsager-regularised models (Eq. 2) with corrections (Eqs. 14, 15).
+    // Non-equilibrium stress (Eq. 4 gives Pi^eq = rho (u u + theta I) exactly):
+    //   2 N_d = sum (c_x^2 - c_y^2) f - rho (u_x^2 - u_y^2),  N_xy = sum c_x c_y f - rho u_x u_y.
+    const T Dxy = s13 - s24;
+    const T Pxy = s57 - s68;
+    const T A1 = c.k1 * fma(-rho, ux2 - uy2, Dxy);  // omega' K1
+    const T A2 = c.k2 * fma(-jx, uy, Pxy);          // omega' K2
+    const T cxm[3] = {T(-1) - ux, -ux, T(1) - ux};  // C_x(a) = a - u_x
+    const T cym[3] = {T(-1) - uy, -uy, T(1) - uy};
+    T rx[3], qx[3], ry[3], qy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      rx[k] = px[k] * cxm[k];
+      qx[k] = rx[k] * cxm[k];
+      ry[k] = py[k] * cym[k];
+      qy[k] = ry[k] * cym[k];
+    }
+    // omega' Psi per population (Eqs. 14, 15), from closed-form psi and Pi~.
+    T cor[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cor[i] = T(0);
+    if constexpr (MODEL >= 2) {
+      const T wpsx = A1 * ux * (c.c3 - ux2);   // omega' psi_x
+      const T wpsy = -A1 * uy * (c.c3 - uy2);  // omega' psi_y
+      if constexpr (MODEL == 2) {
+        // Psi^P: -1/2 c_ia psi_a on the axis populations.
+        cor[1] = T(-0.5) * wpsx;
+        cor[3] = T(0.5) * wpsx;
+        cor[2] = T(-0.5) * wpsy;
+        cor[4] = T(0.5) * wpsy;
+      } else {
+        // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12 (evaluated on f^OReg).
+        const T muxx = (c.theta - ux2) * px[1] * c.inv2t2;
+        const T muyy = (c.theta - uy2) * py[1] * c.inv2t2;
+        const T wpref = T(-0.5) * A1 * (muxx + muyy);         // omega' pref
+        const T wPxx = -wpref * fma(ux2, ux2 - T(1), c.tt);  // omega' Pi~_xx
+        const T wPyy = wpref * fma(uy2, uy2 - T(1), c.tt);   // omega' Pi~_yy
+        const T wPxy = wpref * (ux * uy) * (ux2 - uy2);      // omega' Pi~_xy
+        cor[1] = T(0.5) * (wPyy - wpsx);
+        cor[3] = T(0.5) * (wPyy + wpsx);
+        cor[2] = T(0.5) * (wPxx - wpsy);
+        cor[4] = T(0.5) * (wPxx + wpsy);
+        const T dsum = T(-0.25) * (wPxx + wPyy);
+        const T dxy = T(0.25) * wPxy;
+        cor[5] = dsum - dxy;  // c_x c_y = +1
+        cor[7] = dsum - dxy;
+        cor[6] = dsum + dxy;  // c_x c_y = -1
+        cor[8] = dsum + dxy;
+      }
+    }
+    // f*_(a,b) = f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] + omega' Psi
+    //          = E(a) P_y(b) - B(a) Q_y(b) + G(a) R_y(b) + omega' Psi.
+    T E[3], B[3], G[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      B[k] = A1 * px[k];
+      G[k] = A2 * rx[k];
+    }
+    if constexpr (!SHIFT) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) E[k] = fma(A1, qx[k], rho * px[k]);
+#pragma unroll
+      for (int a = -1; a <= 1; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+          const int i = pop_index(a, b);
+          f[i] = fma(E[a + 1], py[b + 1], fma(-B[a + 1], qy[b + 1], fma(G[a + 1], ry[b + 1], cor[i])));
+        }
+    } else {
+      const T dx[3] = {fma(T(0.5), ux2, -hux), -ux2, fma(T(0.5), ux2, hux)};
+      const T dy[3] = {fma(T(0.5), uy2, -huy), -uy2, fma(T(0.5), uy2, huy)};
+      T rw[3], mw[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        E[k] = fma(A1, qx[k], rho * dx[k]);
+        rw[k] = rho * c.w[k];
+        mw[k] = m0 * c.w[k];
+      }
+#pragma unroll
+      for (int a = -1; a <= 1; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+          const int i = pop_index(a, b);
+          const T base = fma(mw[a + 1], c.w[b + 1], fma(rw[a + 1], dy[b + 1], cor[i]));
+          f[i] = fma(E[a + 1], py[b + 1], fma(-B[a + 1], qy[b + 1], fma(G[a + 1], ry[b + 1], base)));
+        }
+    }
+  }
+}
+
+// Guided equilibrium (Eq. 10) in FP64, product form; used by lbm_init.
+__device__ __forceinline__ void geq_f64(double rho, double ux, double uy, double theta, double (&feq)[9]) {
+  const double px[3] = {0.5 * (theta + ux * ux - ux), 1.0 - theta - ux * ux, 0.5 * (theta + ux * ux + ux)};
+  const double py[3] = {0.5 * (theta + uy * uy - uy), 1.0 - theta - uy * uy, 0.5 * (theta + uy * uy + uy)};
+#pragma unroll
+  for (int a = -1; a <= 1; ++a)
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) feq[pop_index(a, b)] = rho * px[a + 1] * py[b + 1];
+}
+
+// Rest-state value of population i for the shifted forms: rho_ref W(c_ix) W(c_iy).
+__device__ __forceinline__ double rest_value(int i, double theta, double rho_ref) {
+  const double wx = cx_of(i) == 0 ? 1.0 - theta : 0.5 * theta;
+  const double wy = cy_of(i) == 0 ? 1.0 - theta : 0.5 * theta;
+  return rho_ref * wx * wy;
+}
+
+// ---------------------------------------------------------------- reductions
+// Sum NV doubles over a block of NT threads in a fixed order: xor-butterfly in
+// each warp, then warp totals in warp order by thread 0. The result is valid in
+// thread 0 only. Deterministic for a fixed block shape.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (&out)[NV]) {
+  static_assert(NT % 32 == 0, "block size must be a multiple of 32");
+  constexpr int NW = NT / 32;
+  __shared__ double red[NW][NV];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[tid >> 5][k] = v[k];
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += red[w][k];
+      out[k] = s;
+    }
+  }
+}
+
+}  // namespace olbm

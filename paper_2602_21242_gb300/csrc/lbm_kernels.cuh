@@ -1,0 +1,319 @@
+// lbm_kernels.cuh -- CUDA kernels of the fused D2Q9 step (arXiv 2602.21242,
+// Eq. 1) and its companions, templated on the collision model and the storage
+// form. Included by one translation unit per storage form (lbm_f64.cu,
+// lbm_f32.cu, lbm_f16.cu), each of which instantiates the launchers declared in
+// lbm_launch.h.
+//
+// Buffer convention. A population buffer B holds, at node x, the
+// post-collision values of the previous step still at their source node:
+//   B_i(x) = f*_i(x, t - 1) = f_i(x + c_i, t)        (Eq. 1b)
+// so one step is a pure pull:  f_i(x, t) = B_i(x - c_i)  (periodic wrap),
+// collide at x (Eq. 1a), write f*_i(x, t) to B'_i(x). lbm_init and set_state
+// write the push-shifted image of the pre-collision state; get_state and the
+// moments pull it back.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_launch.h"
+
+namespace olbm {
+
+constexpr int kBX = 32;  // threads along x (one warp = 32 consecutive nodes of a row)
+constexpr int kBY = 8;   // rows per block
+constexpr int kNT = kBX * kBY;
+constexpr int kNDiag = 5;  // partial sums per block: m0, jx, jy, ke, non-finite nodes
+
+// Source offsets of the pull f_i(x) = B_i(x - c_i) inside one plane.
+__device__ __forceinline__ void pull_offsets(int x, int y, const Geometry& g, long long (&o)[9]) {
+  const int xm = (x == 0) ? g.nx - 1 : x - 1;
+  const int xp = (x == g.nx - 1) ? 0 : x + 1;
+  const int ym = (y == 0) ? g.ny - 1 : y - 1;
+  const int yp = (y == g.ny - 1) ? 0 : y + 1;
+  const long long r = (long long)y * g.pitch, rm = (long long)ym * g.pitch, rp = (long long)yp * g.pitch;
+  o[0] = r + x;    // c0 = ( 0, 0)
+  o[1] = r + xm;   // c1 = ( 1, 0)
+  o[2] = rm + x;   // c2 = ( 0, 1)
+  o[3] = r + xp;   // c3 = (-1, 0)
+  o[4] = rp + x;   // c4 = ( 0,-1)
+  o[5] = rm + xm;  // c5 = ( 1, 1)
+  o[6] = rm + xp;  // c6 = (-1, 1)
+  o[7] = rp + xp;  // c7 = (-1,-1)
+  o[8] = rp + xm;  // c8 = ( 1,-1)
+}
+
+// Offsets of the push x -> x + c_i (inverse of the pull).
+__device__ __forceinline__ void push_offsets(int x, int y, const Geometry& g, long long (&o)[9]) {
+  const int xm = (x == 0) ? g.nx - 1 : x - 1;
+  const int xp = (x == g.nx - 1) ? 0 : x + 1;
+  const int ym = (y == 0) ? g.ny - 1 : y - 1;
+  const int yp = (y == g.ny - 1) ? 0 : y + 1;
+  const long long r = (long long)y * g.pitch, rm = (long long)ym * g.pitch, rp = (long long)yp * g.pitch;
+  o[0] = r + x;
+  o[1] = r + xp;
+  o[2] = rp + x;
+  o[3] = r + xm;
+  o[4] = rm + x;
+  o[5] = rp + xp;
+  o[6] = rp + xm;
+  o[7] = rm + xm;
+  o[8] = rm + xp;
+}
+
+template <typename T> __device__ __forceinline__ bool finite_t(T v) { return isfinite(v); }
+
+// ------------------------------------------------------------------ fused step
+// One thread per node. Pull (Eq. 1b), collide (Eq. 1a), store. With DIAG, the
+// block also reduces mass, momentum, kinetic energy and the count of nodes with
+// a non-finite pulled population into partials[block * 5 + k].
+template <int MODEL, int PREC, bool DIAG>
+__global__ void __launch_bounds__(kNT) step_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                   typename Form<PREC>::S* __restrict__ dst, Geometry g,
+                                                   Coef<typename Form<PREC>::T> c, double* __restrict__ partials) {
+  using S = typename Form<PREC>::S;
+  using T = typename Form<PREC>::T;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  const bool active = (x < g.nx) && (y < g.ny);
+  double acc[kNDiag] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (active) {
+    long long o[9];
+    pull_offsets(x, y, g, o);
+    T f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ld_t(src + i * g.plane + o[i], T());
+    bool ok = true;
+    if constexpr (DIAG) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) ok = ok && finite_t(f[i]);
+    }
+    NodeMoments<T> m;
+    collide<MODEL, Form<PREC>::kShift, T>(f, c, m);
+    const long long here = (long long)y * g.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st_t(dst + i * g.plane + here, f[i]);
+    if constexpr (DIAG) {
+      if (ok) {
+        acc[0] = (double)m.m0;
+        acc[1] = (double)m.jx;
+        acc[2] = (double)m.jy;
+        acc[3] = 0.5 * ((double)m.jx * (double)m.ux + (double)m.jy * (double)m.uy);
+      } else {
+        acc[4] = 1.0;
+      }
+    }
+  }
+  if constexpr (DIAG) {
+    double tot[kNDiag];
+    block_sum<kNDiag, kNT>(acc, tot);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      double* p = partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * kNDiag;
+#pragma unroll
+      for (int k = 0; k < kNDiag; ++k) p[k] = tot[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ diagnostics of the state
+// Pull only (no collision): FP64 moments of f(x, t), block partials as above.
+template <int PREC>
+__global__ void __launch_bounds__(kNT) diag_kernel(const typename Form<PREC>::S* __restrict__ src, Geometry g,
+                                                   double rho_ref, double* __restrict__ partials) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  double acc[kNDiag] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (x < g.nx && y < g.ny) {
+    long long o[9];
+    pull_offsets(x, y, g, o);
+    double m0 = 0.0, jx = 0.0, jy = 0.0;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const double v = to_double(src[i * g.plane + o[i]]);
+      ok = ok && isfinite(v);
+      m0 += v;
+      jx += (double)cx_of(i) * v;
+      jy += (double)cy_of(i) * v;
+    }
+    if (ok) {
+      acc[0] = m0;
+      acc[1] = jx;
+      acc[2] = jy;
+      acc[3] = 0.5 * (jx * jx + jy * jy) / (rho_ref + m0);
+    } else {
+      acc[4] = 1.0;
+    }
+  }
+  double tot[kNDiag];
+  block_sum<kNDiag, kNT>(acc, tot);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double* p = partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * kNDiag;
+#pragma unroll
+    for (int k = 0; k < kNDiag; ++k) p[k] = tot[k];
+  }
+}
+
+// ------------------------------------------------------------------ init, moments, state copies
+// B_i(x) = f^eq_i(rho0(x + c_i), u0(x + c_i)) - rest_i: the buffer whose pull is f^eq(rho0, u0).
+template <int PREC>
+__global__ void __launch_bounds__(kNT) init_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
+                                                   const double* __restrict__ uy, Geometry g, double theta,
+                                                   double rho_ref, typename Form<PREC>::S* __restrict__ dst) {
+  using S = typename Form<PREC>::S;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long long here = (long long)y * g.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    int xs = x + cx_of(i), ys = y + cy_of(i);  // node x + c_i, periodic
+    xs = (xs < 0) ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
+    ys = (ys < 0) ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+    const long long n = (long long)ys * g.nx + xs;
+    double feq[9];
+    geq_f64(rho[n], ux[n], uy[n], theta, feq);
+    dst[i * g.plane + here] = from_double<S>(feq[i] - rest_value(i, theta, rho_ref));
+  }
+}
+
+// (rho, u) of f(x, t) in FP64, unpadded [y][x] output.
+template <int PREC>
+__global__ void __launch_bounds__(kNT) moments_kernel(const typename Form<PREC>::S* __restrict__ src, Geometry g,
+                                                      double rho_ref, double* __restrict__ rho,
+                                                      double* __restrict__ ux, double* __restrict__ uy) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  long long o[9];
+  pull_offsets(x, y, g, o);
+  double m0 = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double v = to_double(src[i * g.plane + o[i]]);
+    m0 += v;
+    jx += (double)cx_of(i) * v;
+    jy += (double)cy_of(i) * v;
+  }
+  const double r = rho_ref + m0;
+  const long long n = (long long)y * g.nx + x;
+  rho[n] = r;
+  ux[n] = jx / r;
+  uy[n] = jy / r;
+}
+
+// out_i(x) = B_i(x - c_i) + rest_i  (pre-collision f(x, t), FP64, unpadded [i][y][x]).
+template <int PREC>
+__global__ void __launch_bounds__(kNT) get_state_kernel(const typename Form<PREC>::S* __restrict__ src, Geometry g,
+                                                        double theta, double rho_ref, double* __restrict__ out) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  long long o[9];
+  pull_offsets(x, y, g, o);
+  const long long nodes = (long long)g.nx * g.ny;
+  const long long n = (long long)y * g.nx + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) out[i * nodes + n] = to_double(src[i * g.plane + o[i]]) + rest_value(i, theta, rho_ref);
+}
+
+// B_i(x + c_i) = in_i(x) - rest_i.
+template <int PREC>
+__global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict__ in, Geometry g, double theta,
+                                                        double rho_ref, typename Form<PREC>::S* __restrict__ dst) {
+  using S = typename Form<PREC>::S;
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  long long o[9];
+  push_offsets(x, y, g, o);
+  const long long nodes = (long long)g.nx * g.ny;
+  const long long n = (long long)y * g.nx + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dst[i * g.plane + o[i]] = from_double<S>(in[i * nodes + n] - rest_value(i, theta, rho_ref));
+}
+
+// ------------------------------------------------------------------ launchers
+inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
+
+template <int PREC> struct Launch {
+  using S = typename Form<PREC>::S;
+  using T = typename Form<PREC>::T;
+
+  template <int MODEL>
+  static cudaError_t step_m(bool diag, const void* src, void* dst, const Geometry& g, const Coef<T>& c,
+                            double* partials, cudaStream_t st) {
+    const dim3 grid = grid_of(g), block(kBX, kBY);
+    if (diag)
+      step_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)src, (S*)dst, g, c, partials);
+    else
+      step_kernel<MODEL, PREC, false><<<grid, block, 0, st>>>((const S*)src, (S*)dst, g, c, partials);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step(const StepArgs& a, cudaStream_t st) {
+    const Coef<T> c = make_coef<T>(a.theta, a.tau, a.rho_ref);
+    switch (a.model) {
+      case 0: return step_m<0>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
+      case 1: return step_m<1>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
+      case 2: return step_m<2>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
+      case 3: return step_m<3>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+
+  static cudaError_t diag(const void* src, const Geometry& g, double rho_ref, double* partials, cudaStream_t st) {
+    diag_kernel<PREC><<<grid_of(g), dim3(kBX, kBY), 0, st>>>((const S*)src, g, rho_ref, partials);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t init(const double* rho, const double* ux, const double* uy, const Geometry& g, double theta,
+                          double rho_ref, void* dst, cudaStream_t st) {
+    init_kernel<PREC><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(rho, ux, uy, g, theta, rho_ref, (S*)dst);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t moments(const void* src, const Geometry& g, double rho_ref, double* rho, double* ux,
+                             double* uy, cudaStream_t st) {
+    moments_kernel<PREC><<<grid_of(g), dim3(kBX, kBY), 0, st>>>((const S*)src, g, rho_ref, rho, ux, uy);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t get_state(const void* src, const Geometry& g, double theta, double rho_ref, double* out,
+                               cudaStream_t st) {
+    get_state_kernel<PREC><<<grid_of(g), dim3(kBX, kBY), 0, st>>>((const S*)src, g, theta, rho_ref, out);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t set_state(const double* in, const Geometry& g, double theta, double rho_ref, void* dst,
+                               cudaStream_t st) {
+    set_state_kernel<PREC><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(in, g, theta, rho_ref, (S*)dst);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace olbm
+
+// Defines the C++ entry points of lbm_launch.h for one storage form.
+#define OLBM_DEFINE_LAUNCHERS(PREC, SUFFIX)                                                                      \
+  namespace olbm {                                                                                               \
+  cudaError_t launch_step_##SUFFIX(const StepArgs& a, cudaStream_t st) { return Launch<PREC>::step(a, st); }     \
+  cudaError_t launch_diag_##SUFFIX(const void* src, const Geometry& g, double rho_ref, double* partials,         \
+                                   cudaStream_t st) {                                                            \
+    return Launch<PREC>::diag(src, g, rho_ref, partials, st);                                                    \
+  }                                                                                                              \
+  cudaError_t launch_init_##SUFFIX(const double* rho, const double* ux, const double* uy, const Geometry& g,     \
+                                   double theta, double rho_ref, void* dst, cudaStream_t st) {                   \
+    return Launch<PREC>::init(rho, ux, uy, g, theta, rho_ref, dst, st);                                          \
+  }                                                                                                              \
+  cudaError_t launch_moments_##SUFFIX(const void* src, const Geometry& g, double rho_ref, double* rho,           \
+                                      double* ux, double* uy, cudaStream_t st) {                                 \
+    return Launch<PREC>::moments(src, g, rho_ref, rho, ux, uy, st);                                              \
+  }                                                                                                              \
+  cudaError_t launch_get_state_##SUFFIX(const void* src, const Geometry& g, double theta, double rho_ref,        \
+                                        double* out, cudaStream_t st) {                                          \
+    return Launch<PREC>::get_state(src, g, theta, rho_ref, out, st);                                             \
+  }                                                                                                              \
+  cudaError_t launch_set_state_##SUFFIX(const double* in, const Geometry& g, double theta, double rho_ref,       \
+                                        void* dst, cudaStream_t st) {                                            \
+    return Launch<PREC>::set_state(in, g, theta, rho_ref, dst, st);                                              \
+  }                                                                                                              \
+  }

@@ -1,0 +1,45 @@
+// lbm_launch.h -- host-side entry points into the kernels of one storage form
+// (internal to liblbm.so; the public ABI is include/lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace olbm {
+
+struct StepArgs {
+  int model;         // 0..3, enum lbm_model
+  bool diag;         // fuse the diagnostics reduction into this step
+  const void* src;   // buffer holding f*(t - 1) at source nodes
+  void* dst;         // buffer receiving f*(t)
+  Geometry g;
+  double theta, tau;
+  double rho_ref;    // 0 for absolute storage, 1 for the shifted forms
+  double* partials;  // grid blocks * 5 doubles when diag
+};
+
+// Number of thread blocks of the node-parallel kernels (= diagnostics partials).
+long long node_blocks(const Geometry& g);
+
+#define OLBM_DECLARE_LAUNCHERS(SUFFIX)                                                                        \
+  cudaError_t launch_step_##SUFFIX(const StepArgs& a, cudaStream_t st);                                       \
+  cudaError_t launch_diag_##SUFFIX(const void* src, const Geometry& g, double rho_ref, double* partials,      \
+                                   cudaStream_t st);                                                          \
+  cudaError_t launch_init_##SUFFIX(const double* rho, const double* ux, const double* uy, const Geometry& g,  \
+                                   double theta, double rho_ref, void* dst, cudaStream_t st);                 \
+  cudaError_t launch_moments_##SUFFIX(const void* src, const Geometry& g, double rho_ref, double* rho,        \
+                                      double* ux, double* uy, cudaStream_t st);                               \
+  cudaError_t launch_get_state_##SUFFIX(const void* src, const Geometry& g, double theta, double rho_ref,     \
+                                        double* out, cudaStream_t st);                                        \
+  cudaError_t launch_set_state_##SUFFIX(const double* in, const Geometry& g, double theta, double rho_ref,    \
+                                        void* dst, cudaStream_t st);
+
+OLBM_DECLARE_LAUNCHERS(f64)
+OLBM_DECLARE_LAUNCHERS(f32)
+OLBM_DECLARE_LAUNCHERS(f16)
+
+cudaError_t launch_finalize(const double* partials, int nparts, double rho_ref, long long nodes, long long t,
+                            double* out, unsigned long long* sticky, cudaStream_t st);
+
+}  // namespace olbm

@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads,
+exports every entry point include/*.h declares, and rejects bad arguments
+before touching the device."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2602_21242_gb300 import build, capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments",
+                     "lbm_diagnostics", "lbm_get_state", "lbm_set_state", "lbm_destroy", "lbm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = capi.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(lbm_\w+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+
+
+def test_build_targets_sm_103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_layout():
+    pitch, plane, nbytes = capi.lbm_layout(4096, 4096, capi.LBM_F64)
+    assert pitch == 4096 and plane == 4096 * 4096 and nbytes == 9 * 4096 * 4096 * 8
+    pitch, plane, nbytes = capi.lbm_layout(33, 7, capi.LBM_F64)
+    assert pitch == 48 and (pitch * 8) % 128 == 0 and (plane * 8) % 256 == 0 and plane >= pitch * 7
+    pitch, plane, nbytes = capi.lbm_layout(33, 7, capi.LBM_F16_SHIFT)
+    assert pitch == 64 and nbytes == 9 * plane * 2
+    with pytest.raises(capi.LBMError):
+        capi.lbm_layout(0, 5, capi.LBM_F64)
+    with pytest.raises(capi.LBMError):
+        capi.lbm_layout(5, 5, 7)
+
+
+@pytest.mark.parametrize("args,fragment", [
+    ((0, 8, 1 / 3, 0.6, 3), "invalid size"),
+    ((8, 8, 1.2, 0.6, 3), "theta"),
+    ((8, 8, 0.0, 0.6, 3), "theta"),
+    ((8, 8, 1 / 3, 0.5, 3), "tau"),
+    ((8, 8, 1 / 3, float("nan"), 3), "tau"),
+    ((8, 8, 1 / 3, 0.6, 4), "model"),
+])
+def test_create_rejects_bad_arguments(args, fragment):
+    with pytest.raises(capi.LBMError) as e:
+        capi.lbm_create(*args)
+    assert e.value.status == capi.LBM_EINVAL
+    assert fragment in str(e.value)
+
+
+def test_calls_reject_null_context():
+    lib = capi.load()
+    assert lib.lbm_step(None, 1) == capi.LBM_EINVAL
+    assert lib.lbm_init(None, None, None, None) == capi.LBM_EINVAL
+    assert lib.lbm_destroy(None) == capi.LBM_OK
+    assert isinstance(capi.last_error(None), str)
+    assert capi.lbm_version() >> 16 == 1
