@@ -169,6 +169,17 @@ int lbm_time(const lbm_ctx* ctx, long long* h_t);
 int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const double* h_uy0,
                  int n, double* h_rho, double* h_ux, double* h_uy, double* h_diag5);
 
+/*
+ * Launch shape of the fused step kernel (no counterpart in the paper): blocks of
+ * bx x by threads (bx a multiple of 32, bx * by <= 512), each thread updating
+ * `rows` nodes of one column (1 <= rows <= 64). Results do not depend on the
+ * shape except for the order of the diagnostics sums. Each storage form starts
+ * from a default measured on GB300; lbm_set_launch may reallocate the small
+ * diagnostics buffer (it then synchronises the stream). Errors: LBM_EINVAL.
+ */
+int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows);
+int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
+
 /* Wait for the lattice's stream; report a pending CUDA error (LBM_ECUDA) or a
  * non-finite population seen by a fused diagnostics pass (LBM_ENONFINITE). */
 int lbm_sync(lbm_ctx* ctx);

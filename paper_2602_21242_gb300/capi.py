@@ -46,6 +46,8 @@ _SIGNATURES = {
     "lbm_run_host": ([_p, _p, _p, _p, _i, _p, _p, _p, _pd], _i),
     "lbm_sync": ([_p], _i),
     "lbm_measure_peak": ([_i, _pd], _i),
+    "lbm_set_launch": ([_p, _i, _i, _i], _i),
+    "lbm_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "lbm_last_error": ([_p], ctypes.c_char_p),
 }
 
@@ -192,3 +194,13 @@ def lbm_measure_peak(kind: int) -> float:
     v = ctypes.c_double()
     check(load().lbm_measure_peak(kind, ctypes.byref(v)))
     return v.value
+
+
+def lbm_set_launch(ctx, bx: int, by: int, rows: int) -> None:
+    check(load().lbm_set_launch(ctx, bx, by, rows), ctx)
+
+
+def lbm_get_launch(ctx):
+    bx, by, rows = _i(), _i(), _i()
+    check(load().lbm_get_launch(ctx, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(rows)), ctx)
+    return bx.value, by.value, rows.value

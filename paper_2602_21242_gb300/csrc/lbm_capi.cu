@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "lbm.h"
@@ -25,8 +26,10 @@ struct lbm_ctx {
   bool own_buffers = true;
   bool initialised = false;
   cudaStream_t stream = nullptr;
+  olbm::LaunchCfg cfg{};
   double* d_partials = nullptr;
-  long long nparts = 0;
+  long long nparts = 0;      // partials the step kernel writes under cfg
+  long long parts_cap = 0;   // partials allocated
   double* d_diag = nullptr;      // [6] latest fused diagnostics (out5 + time)
   double* d_diag_now = nullptr;  // [6] scratch of lbm_diagnostics
   unsigned long long* d_sticky = nullptr;
@@ -72,6 +75,18 @@ bool layout_of(int nx, int ny, int prec, long long* pitch, long long* plane, lon
 }
 
 long long nodes_of(const lbm_ctx* c) { return (long long)c->nx * c->ny; }
+
+// Default launch shapes of the step kernel per storage form, chosen by timing on
+// GB300 at the 4096^2 benchmark size; lbm_set_launch overrides them per lattice.
+olbm::LaunchCfg default_cfg(int prec) {
+  olbm::LaunchCfg k;
+  if (prec == LBM_F64) {
+    k.bx = 32, k.by = 8, k.rows = 4;
+  } else {
+    k.bx = 128, k.by = 2, k.rows = 4;
+  }
+  return k;
+}
 
 cudaError_t launch_step(const olbm::StepArgs& a, int prec, cudaStream_t st) {
   switch (prec) {
@@ -153,7 +168,9 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   c->g = olbm::Geometry{nx, ny, pitch, plane};
   c->state_bytes = bytes;
   c->stream = static_cast<cudaStream_t>(stream);
-  c->nparts = olbm::node_blocks(c->g);
+  c->cfg = default_cfg(prec);
+  c->nparts = olbm::step_blocks(c->g, c->cfg);
+  c->parts_cap = std::max(c->nparts, olbm::node_blocks(c->g));
 
   if (d_pop_buffers) {
     c->own_buffers = false;
@@ -169,7 +186,7 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
       }
     }
   }
-  if ((e = cudaMalloc(&c->d_partials, sizeof(double) * 5 * (size_t)c->nparts)) != cudaSuccess ||
+  if ((e = cudaMalloc(&c->d_partials, sizeof(double) * 5 * (size_t)c->parts_cap)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag_now, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess) {
@@ -245,6 +262,7 @@ int lbm_step(lbm_ctx* ctx, int n) {
   a.tau = ctx->tau;
   a.rho_ref = ctx->rho_ref;
   a.partials = ctx->d_partials;
+  a.cfg = ctx->cfg;
   for (int k = 0; k < n; ++k) {
     a.diag = ctx->diag_every > 0 && (ctx->t % ctx->diag_every) == 0;
     a.src = ctx->buf[ctx->cur];
@@ -301,8 +319,8 @@ int lbm_diagnostics(lbm_ctx* ctx, double* h_out5) {
   if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_diagnostics before lbm_init / lbm_set_state");
   cudaError_t e = launch_diag(ctx, ctx->stream);
   if (e == cudaSuccess)
-    e = olbm::launch_finalize(ctx->d_partials, (int)ctx->nparts, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag_now,
-                              nullptr, ctx->stream);
+    e = olbm::launch_finalize(ctx->d_partials, (int)olbm::node_blocks(ctx->g), ctx->rho_ref, nodes_of(ctx), ctx->t,
+                              ctx->d_diag_now, nullptr, ctx->stream);
   double d[6];
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, ctx->d_diag_now, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -390,6 +408,43 @@ int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const 
   if (h_diag5) return lbm_diagnostics(ctx, h_diag5);  // synchronises
   e = cudaStreamSynchronize(ctx->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(ctx, e, "lbm_run_host sync");
+}
+
+int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  olbm::LaunchCfg k;
+  k.bx = bx;
+  k.by = by;
+  k.rows = rows;
+  if (!olbm::valid_cfg(k))
+    return fail(ctx, LBM_EINVAL, "launch shape %dx%d x %d rows invalid (bx a multiple of 32, bx*by <= 512, rows 1..64)",
+                bx, by, rows);
+  const long long need = olbm::step_blocks(ctx->g, k);
+  if (need > ctx->parts_cap) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_launch sync");
+    double* p = nullptr;
+    e = cudaMalloc(&p, sizeof(double) * 5 * (size_t)need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, LBM_ENOMEM, "lbm_set_launch: %s", cudaGetErrorString(e));
+    }
+    cudaFree(ctx->d_partials);
+    ctx->d_partials = p;
+    ctx->parts_cap = need;
+  }
+  ctx->cfg = k;
+  ctx->nparts = need;
+  return LBM_OK;
+}
+
+int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows) {
+  if (!ctx || !bx || !by || !rows) return LBM_EINVAL;
+  *bx = ctx->cfg.bx;
+  *by = ctx->cfg.by;
+  *rows = ctx->cfg.rows;
+  return LBM_OK;
 }
 
 int lbm_sync(lbm_ctx* ctx) {

@@ -125,14 +125,40 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
 // Moments of one node kept for the diagnostics.
 template <typename T> struct NodeMoments {
   T m0;  // sum of stored values: rho (absolute) or rho - rho_ref (shifted)
-  T jx, jy, ux, uy;
+  T jx, jy;
+  T ke;  // rho |u|^2 / 2
 };
+
+// 1 / x. FP64: a single-precision seed (rcp.approx, relative error < 2^-22 after
+// rounding x to FP32) refined by one cubic Newton step r = r0 (1 + e + e^2),
+// e = 1 - x r0, which leaves a relative error O(e^3) < 2^-64 before the final
+// rounding: 3 FP64 operations instead of a full IEEE division. Valid for
+// |x| in the FP32 normal range; other x (rho <= 0 or non-finite) give a
+// non-finite or meaningless result, which the diagnostics report.
+__device__ __forceinline__ float rcp_seed(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double recip(double x) {
+  const double r0 = (double)rcp_seed((float)x);
+  const double e = fma(-x, r0, 1.0);
+  return fma(r0, fma(e, e, e), r0);
+}
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
 // ---------------------------------------------------------------- collision
 // In-place collision of one node (Eq. 1a). f holds the stored values of the
 // pulled pre-collision populations (absolute, or deviations from the rest
 // state in the shifted forms); on return it holds the post-collision values
 // in the same representation.
+//
+// With P(b), C(b) = b - u the per-axis factors, every post-collision
+// population of the Onsager-regularised models is written as
+//   f*_(a,b) = P_y(b) [E(a) + C_y(b) (G(a) - B(a) C_y(b))] + omega' Psi_(a,b)
+// where E(a) = P_x(a) (rho + A1 C_x(a)^2), B(a) = A1 P_x(a), G(a) = A2 P_x(a) C_x(a),
+// A1 = omega' K1, A2 = omega' K2: the expansion of
+// f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] at three FMAs per population.
 template <int MODEL, bool SHIFT, typename T>
 __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments<T>& mom) {
   // Moments (Sec. 1). The rest state has zero momentum, zero
@@ -146,20 +172,21 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
   const T jx = d13 + (d57 - d68);
   const T jy = d24 + (d57 + d68);
   const T rho = SHIFT ? c.rho_ref + m0 : m0;
-  const T inv_rho = T(1) / rho;
+  const T inv_rho = recip(rho);
   const T ux = jx * inv_rho, uy = jy * inv_rho;
   mom.m0 = m0;
   mom.jx = jx;
   mom.jy = jy;
-  mom.ux = ux;
-  mom.uy = uy;
+  mom.ke = T(0.5) * fma(jx, ux, jy * uy);
 
   const T ux2 = ux * ux, uy2 = uy * uy;
-  // Per-axis GEq factors P(a) (Eq. 10), a = -1, 0, +1.
-  const T hx = fma(T(0.5), ux2, c.half_theta), hux = T(0.5) * ux;
-  const T hy = fma(T(0.5), uy2, c.half_theta), huy = T(0.5) * uy;
-  const T px[3] = {hx - hux, c.one_m_theta - ux2, hx + hux};
-  const T py[3] = {hy - huy, c.one_m_theta - uy2, hy + huy};
+  // Per-axis GEq factors P(a) (Eq. 10), a = -1, 0, +1, and their deviations
+  // dP = P - W from the rest values (dP(0) = -u^2, dP(+-1) = (u^2 +- u)/2).
+  const T hux = T(0.5) * ux, huy = T(0.5) * uy;
+  const T dx[3] = {fma(T(0.5), ux2, -hux), -ux2, fma(T(0.5), ux2, hux)};
+  const T dy[3] = {fma(T(0.5), uy2, -huy), -uy2, fma(T(0.5), uy2, huy)};
+  const T px[3] = {c.half_theta + dx[0], c.one_m_theta - ux2, c.half_theta + dx[2]};
+  const T py[3] = {c.half_theta + dy[0], c.one_m_theta - uy2, c.half_theta + dy[2]};
 
   if constexpr (MODEL == 0) {
     // LBGK: f* = f + (f^eq - f)/tau = (1 - 1/tau) f + (1/tau) f^eq.
@@ -175,10 +202,7 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
         }
     } else {
       // Shifted: f^eq - rho_ref W W = m0 W_a W_b + rho (dP_x(a) P_y(b) + W_a dP_y(b)),
-      // dP = P - W formed directly (dP(0) = -u^2, dP(+-1) = (u^2 +- u)/2), so no
-      // O(1) terms cancel.
-      const T dx[3] = {fma(T(0.5), ux2, -hux), -ux2, fma(T(0.5), ux2, hux)};
-      const T dy[3] = {fma(T(0.5), uy2, -huy), -uy2, fma(T(0.5), uy2, huy)};
+      // so no O(1) terms cancel.
 #pragma unroll
       for (int a = -1; a <= 1; ++a)
 #pragma unroll
@@ -199,14 +223,6 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
     const T A2 = c.k2 * fma(-jx, uy, Pxy);          // omega' K2
     const T cxm[3] = {T(-1) - ux, -ux, T(1) - ux};  // C_x(a) = a - u_x
     const T cym[3] = {T(-1) - uy, -uy, T(1) - uy};
-    T rx[3], qx[3], ry[3], qy[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      rx[k] = px[k] * cxm[k];
-      qx[k] = rx[k] * cxm[k];
-      ry[k] = py[k] * cym[k];
-      qy[k] = ry[k] * cym[k];
-    }
     // omega' Psi per population (Eqs. 14, 15), from closed-form psi and Pi~.
     T cor[9];
 #pragma unroll
@@ -222,61 +238,44 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
         cor[4] = T(0.5) * wpsy;
       } else {
         // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12 (evaluated on f^OReg).
-        const T muxx = (c.theta - ux2) * px[1] * c.inv2t2;
-        const T muyy = (c.theta - uy2) * py[1] * c.inv2t2;
-        const T wpref = T(-0.5) * A1 * (muxx + muyy);         // omega' pref
-        const T wPxx = -wpref * fma(ux2, ux2 - T(1), c.tt);  // omega' Pi~_xx
-        const T wPyy = wpref * fma(uy2, uy2 - T(1), c.tt);   // omega' Pi~_yy
-        const T wPxy = wpref * (ux * uy) * (ux2 - uy2);      // omega' Pi~_xy
-        cor[1] = T(0.5) * (wPyy - wpsx);
-        cor[3] = T(0.5) * (wPyy + wpsx);
-        cor[2] = T(0.5) * (wPxx - wpsy);
-        cor[4] = T(0.5) * (wPxx + wpsy);
-        const T dsum = T(-0.25) * (wPxx + wPyy);
-        const T dxy = T(0.25) * wPxy;
-        cor[5] = dsum - dxy;  // c_x c_y = +1
-        cor[7] = dsum - dxy;
-        cor[6] = dsum + dxy;  // c_x c_y = -1
-        cor[8] = dsum + dxy;
+        const T muxx = (c.theta - ux2) * px[1];  // 2 theta^2 mu_xx
+        const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
+        const T hwpref = T(-0.25) * c.inv2t2 * A1 * (muxx + muyy);  // omega' pref / 2
+        const T hPxx = -hwpref * fma(ux2, ux2 - T(1), c.tt);       // omega' Pi~_xx / 2
+        const T hPyy = hwpref * fma(uy2, uy2 - T(1), c.tt);        // omega' Pi~_yy / 2
+        const T qPxy = T(0.5) * hwpref * (ux * uy) * (ux2 - uy2);  // omega' Pi~_xy / 4
+        const T hpsx = T(0.5) * wpsx, hpsy = T(0.5) * wpsy;
+        cor[1] = hPyy - hpsx;
+        cor[3] = hPyy + hpsx;
+        cor[2] = hPxx - hpsy;
+        cor[4] = hPxx + hpsy;
+        const T dsum = T(-0.5) * (hPxx + hPyy);
+        cor[5] = dsum - qPxy;  // c_x c_y = +1
+        cor[7] = dsum - qPxy;
+        cor[6] = dsum + qPxy;  // c_x c_y = -1
+        cor[8] = dsum + qPxy;
       }
     }
-    // f*_(a,b) = f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] + omega' Psi
-    //          = E(a) P_y(b) - B(a) Q_y(b) + G(a) R_y(b) + omega' Psi.
     T E[3], B[3], G[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+      const T base = SHIFT ? rho * dx[k] : rho * px[k];  // f^eq part carried by P_y(b)
+      E[k] = fma(A1 * px[k], cxm[k] * cxm[k], base);
       B[k] = A1 * px[k];
-      G[k] = A2 * rx[k];
+      G[k] = A2 * (px[k] * cxm[k]);
     }
-    if constexpr (!SHIFT) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) E[k] = fma(A1, qx[k], rho * px[k]);
+    for (int a = -1; a <= 1; ++a)
 #pragma unroll
-      for (int a = -1; a <= 1; ++a)
-#pragma unroll
-        for (int b = -1; b <= 1; ++b) {
-          const int i = pop_index(a, b);
-          f[i] = fma(E[a + 1], py[b + 1], fma(-B[a + 1], qy[b + 1], fma(G[a + 1], ry[b + 1], cor[i])));
+      for (int b = -1; b <= 1; ++b) {
+        const int i = pop_index(a, b);
+        T rest = cor[i];
+        if constexpr (SHIFT) {
+          // remaining f^eq deviation: m0 W_a W_b + rho W_a dP_y(b)
+          rest = fma(m0 * c.w[a + 1], c.w[b + 1], fma(rho * c.w[a + 1], dy[b + 1], rest));
         }
-    } else {
-      const T dx[3] = {fma(T(0.5), ux2, -hux), -ux2, fma(T(0.5), ux2, hux)};
-      const T dy[3] = {fma(T(0.5), uy2, -huy), -uy2, fma(T(0.5), uy2, huy)};
-      T rw[3], mw[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        E[k] = fma(A1, qx[k], rho * dx[k]);
-        rw[k] = rho * c.w[k];
-        mw[k] = m0 * c.w[k];
+        f[i] = fma(py[b + 1], fma(cym[b + 1], fma(-B[a + 1], cym[b + 1], G[a + 1]), E[a + 1]), rest);
       }
-#pragma unroll
-      for (int a = -1; a <= 1; ++a)
-#pragma unroll
-        for (int b = -1; b <= 1; ++b) {
-          const int i = pop_index(a, b);
-          const T base = fma(mw[a + 1], c.w[b + 1], fma(rw[a + 1], dy[b + 1], cor[i]));
-          f[i] = fma(E[a + 1], py[b + 1], fma(-B[a + 1], qy[b + 1], fma(G[a + 1], ry[b + 1], base)));
-        }
-    }
   }
 }
 

@@ -18,8 +18,8 @@
 
 namespace olbm {
 
-constexpr int kBX = 32;  // threads along x (one warp = 32 consecutive nodes of a row)
-constexpr int kBY = 8;   // rows per block
+constexpr int kBX = 32;  // threads along x of the auxiliary kernels (init, moments, state copies, diagnostics)
+constexpr int kBY = 8;   // rows per block of the auxiliary kernels
 constexpr int kNT = kBX * kBY;
 constexpr int kNDiag = 5;  // partial sums per block: m0, jx, jy, ke, non-finite nodes
 
@@ -41,75 +41,100 @@ __device__ __forceinline__ void pull_offsets(int x, int y, const Geometry& g, lo
   o[8] = rp + xm;  // c8 = ( 1,-1)
 }
 
-// Offsets of the push x -> x + c_i (inverse of the pull).
-__device__ __forceinline__ void push_offsets(int x, int y, const Geometry& g, long long (&o)[9]) {
-  const int xm = (x == 0) ? g.nx - 1 : x - 1;
-  const int xp = (x == g.nx - 1) ? 0 : x + 1;
-  const int ym = (y == 0) ? g.ny - 1 : y - 1;
-  const int yp = (y == g.ny - 1) ? 0 : y + 1;
-  const long long r = (long long)y * g.pitch, rm = (long long)ym * g.pitch, rp = (long long)yp * g.pitch;
-  o[0] = r + x;
-  o[1] = r + xp;
-  o[2] = rp + x;
-  o[3] = r + xm;
-  o[4] = rm + x;
-  o[5] = rp + xp;
-  o[6] = rp + xm;
-  o[7] = rm + xm;
-  o[8] = rm + xp;
+// Finite test on the bit pattern (integer pipe, no FP64 compare): exponent not all ones.
+__device__ __forceinline__ bool finite_bits(double v) {
+  return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
+__device__ __forceinline__ bool finite_bits(float v) {
+  return (__float_as_int(v) & 0x7f800000) != 0x7f800000;
 }
 
-template <typename T> __device__ __forceinline__ bool finite_t(T v) { return isfinite(v); }
+// Block-wide sum of per-thread diagnostics: the four moment sums are reduced
+// across each warp in the compute type T (an xor butterfly, identical in every
+// lane), then the warp totals are added in FP64 in warp order by thread 0. The
+// non-finite count is reduced as an integer. Deterministic for a given block
+// shape. Blocks have at most kMaxWarps warps.
+constexpr int kMaxWarps = 16;
+template <typename T>
+__device__ __forceinline__ void block_diag(T (&v)[4], int bad, double* __restrict__ out5) {
+  __shared__ double red[kMaxWarps][5];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[tid >> 5][k] = (double)v[k];
+    red[tid >> 5][4] = (double)bad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < 5; ++k) {
+      double acc = 0.0;
+      for (int w = 0; w < nw; ++w) acc += red[w][k];
+      out5[k] = acc;
+    }
+  }
+}
 
 // ------------------------------------------------------------------ fused step
-// One thread per node. Pull (Eq. 1b), collide (Eq. 1a), store. With DIAG, the
-// block also reduces mass, momentum, kinetic energy and the count of nodes with
-// a non-finite pulled population into partials[block * 5 + k].
+// Block (bx, by) threads, bx a multiple of 32, bx * by <= 512; each thread
+// updates `rows` nodes of one column x, at rows y0 + r * by (r < rows), so at
+// every iteration a block covers by consecutive rows. Pull (Eq. 1b), collide
+// (Eq. 1a), store. With DIAG, per-block sums of mass (as the stored deviation
+// m0), momentum, kinetic energy and the number of nodes whose pulled
+// populations do not sum to a finite value go to partials[block * 5 + k].
 template <int MODEL, int PREC, bool DIAG>
-__global__ void __launch_bounds__(kNT) step_kernel(const typename Form<PREC>::S* __restrict__ src,
+__global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S* __restrict__ src,
                                                    typename Form<PREC>::S* __restrict__ dst, Geometry g,
-                                                   Coef<typename Form<PREC>::T> c, double* __restrict__ partials) {
-  using S = typename Form<PREC>::S;
+                                                   Coef<typename Form<PREC>::T> c, double* __restrict__ partials,
+                                                   int rows) {
   using T = typename Form<PREC>::T;
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  const bool active = (x < g.nx) && (y < g.ny);
-  double acc[kNDiag] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (active) {
-    long long o[9];
-    pull_offsets(x, y, g, o);
-    T f[9];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y0 = blockIdx.y * blockDim.y * rows + threadIdx.y;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  int bad = 0;
+  if (x < g.nx) {
+    const int xm = (x == 0) ? g.nx - 1 : x - 1;
+    const int xp = (x == g.nx - 1) ? 0 : x + 1;
+    for (int r = 0; r < rows; ++r) {
+      const int y = y0 + r * (int)blockDim.y;
+      if (y >= g.ny) break;
+      const int ym = (y == 0) ? g.ny - 1 : y - 1;
+      const int yp = (y == g.ny - 1) ? 0 : y + 1;
+      const long long rc = (long long)y * g.pitch, rm = (long long)ym * g.pitch, rp = (long long)yp * g.pitch;
+      T f[9];
+      f[0] = ld_t(src + rc + x, T());
+      f[1] = ld_t(src + 1 * g.plane + rc + xm, T());
+      f[2] = ld_t(src + 2 * g.plane + rm + x, T());
+      f[3] = ld_t(src + 3 * g.plane + rc + xp, T());
+      f[4] = ld_t(src + 4 * g.plane + rp + x, T());
+      f[5] = ld_t(src + 5 * g.plane + rm + xm, T());
+      f[6] = ld_t(src + 6 * g.plane + rm + xp, T());
+      f[7] = ld_t(src + 7 * g.plane + rp + xp, T());
+      f[8] = ld_t(src + 8 * g.plane + rp + xm, T());
+      NodeMoments<T> m;
+      collide<MODEL, Form<PREC>::kShift, T>(f, c, m);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = ld_t(src + i * g.plane + o[i], T());
-    bool ok = true;
-    if constexpr (DIAG) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) ok = ok && finite_t(f[i]);
-    }
-    NodeMoments<T> m;
-    collide<MODEL, Form<PREC>::kShift, T>(f, c, m);
-    const long long here = (long long)y * g.pitch + x;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) st_t(dst + i * g.plane + here, f[i]);
-    if constexpr (DIAG) {
-      if (ok) {
-        acc[0] = (double)m.m0;
-        acc[1] = (double)m.jx;
-        acc[2] = (double)m.jy;
-        acc[3] = 0.5 * ((double)m.jx * (double)m.ux + (double)m.jy * (double)m.uy);
-      } else {
-        acc[4] = 1.0;
+      for (int i = 0; i < 9; ++i) st_t(dst + i * g.plane + rc + x, f[i]);
+      if constexpr (DIAG) {
+        if (finite_bits(m.m0)) {
+          acc[0] += m.m0;
+          acc[1] += m.jx;
+          acc[2] += m.jy;
+          acc[3] += m.ke;
+        } else {
+          ++bad;
+        }
       }
     }
   }
   if constexpr (DIAG) {
-    double tot[kNDiag];
-    block_sum<kNDiag, kNT>(acc, tot);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double* p = partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * kNDiag;
-#pragma unroll
-      for (int k = 0; k < kNDiag; ++k) p[k] = tot[k];
-    }
+    block_diag<T>(acc, bad, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
   }
 }
 
@@ -125,16 +150,14 @@ __global__ void __launch_bounds__(kNT) diag_kernel(const typename Form<PREC>::S*
     long long o[9];
     pull_offsets(x, y, g, o);
     double m0 = 0.0, jx = 0.0, jy = 0.0;
-    bool ok = true;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const double v = to_double(src[i * g.plane + o[i]]);
-      ok = ok && isfinite(v);
       m0 += v;
       jx += (double)cx_of(i) * v;
       jy += (double)cy_of(i) * v;
     }
-    if (ok) {
+    if (finite_bits(m0)) {
       acc[0] = m0;
       acc[1] = jx;
       acc[2] = jy;
@@ -215,7 +238,7 @@ __global__ void __launch_bounds__(kNT) get_state_kernel(const typename Form<PREC
   for (int i = 0; i < 9; ++i) out[i * nodes + n] = to_double(src[i * g.plane + o[i]]) + rest_value(i, theta, rho_ref);
 }
 
-// B_i(x + c_i) = in_i(x) - rest_i.
+// B_i(x - c_i) = in_i(x) - rest_i: the inverse of get_state (each element written once).
 template <int PREC>
 __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict__ in, Geometry g, double theta,
                                                         double rho_ref, typename Form<PREC>::S* __restrict__ dst) {
@@ -224,7 +247,7 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
   const int y = blockIdx.y * kBY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
   long long o[9];
-  push_offsets(x, y, g, o);
+  pull_offsets(x, y, g, o);
   const long long nodes = (long long)g.nx * g.ny;
   const long long n = (long long)y * g.nx + x;
 #pragma unroll
@@ -233,29 +256,35 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 
 // ------------------------------------------------------------------ launchers
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
+inline dim3 step_grid(const Geometry& g, const LaunchCfg& k) {
+  return dim3((g.nx + k.bx - 1) / k.bx, (g.ny + k.by * k.rows - 1) / (k.by * k.rows));
+}
 
 template <int PREC> struct Launch {
   using S = typename Form<PREC>::S;
   using T = typename Form<PREC>::T;
 
   template <int MODEL>
-  static cudaError_t step_m(bool diag, const void* src, void* dst, const Geometry& g, const Coef<T>& c,
-                            double* partials, cudaStream_t st) {
-    const dim3 grid = grid_of(g), block(kBX, kBY);
-    if (diag)
-      step_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)src, (S*)dst, g, c, partials);
+  static cudaError_t step_m(const StepArgs& a, const Coef<T>& c, cudaStream_t st) {
+    const dim3 block(a.cfg.bx, a.cfg.by);
+    const dim3 grid = step_grid(a.g, a.cfg);
+    if (a.diag)
+      step_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                              a.cfg.rows);
     else
-      step_kernel<MODEL, PREC, false><<<grid, block, 0, st>>>((const S*)src, (S*)dst, g, c, partials);
+      step_kernel<MODEL, PREC, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                               a.cfg.rows);
     return cudaGetLastError();
   }
 
   static cudaError_t step(const StepArgs& a, cudaStream_t st) {
+    if (!valid_cfg(a.cfg)) return cudaErrorInvalidConfiguration;
     const Coef<T> c = make_coef<T>(a.theta, a.tau, a.rho_ref);
     switch (a.model) {
-      case 0: return step_m<0>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
-      case 1: return step_m<1>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
-      case 2: return step_m<2>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
-      case 3: return step_m<3>(a.diag, a.src, a.dst, a.g, c, a.partials, st);
+      case 0: return step_m<0>(a, c, st);
+      case 1: return step_m<1>(a, c, st);
+      case 2: return step_m<2>(a, c, st);
+      case 3: return step_m<3>(a, c, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -8,6 +8,16 @@
 
 namespace olbm {
 
+// Launch shape of the step kernel: bx x by threads (bx a multiple of 32,
+// bx * by <= 512), each thread updating `rows` nodes of one column.
+struct LaunchCfg {
+  int bx = 32, by = 8, rows = 1;
+};
+
+inline bool valid_cfg(const LaunchCfg& k) {
+  return k.bx >= 32 && k.bx % 32 == 0 && k.by >= 1 && k.bx * k.by <= 512 && k.rows >= 1 && k.rows <= 64;
+}
+
 struct StepArgs {
   int model;         // 0..3, enum lbm_model
   bool diag;         // fuse the diagnostics reduction into this step
@@ -17,10 +27,13 @@ struct StepArgs {
   double theta, tau;
   double rho_ref;    // 0 for absolute storage, 1 for the shifted forms
   double* partials;  // grid blocks * 5 doubles when diag
+  LaunchCfg cfg;
 };
 
-// Number of thread blocks of the node-parallel kernels (= diagnostics partials).
+// Number of thread blocks of the auxiliary node-parallel kernels and of the
+// step kernel under a launch shape (= diagnostics partials they write).
 long long node_blocks(const Geometry& g);
+long long step_blocks(const Geometry& g, const LaunchCfg& k);
 
 #define OLBM_DECLARE_LAUNCHERS(SUFFIX)                                                                        \
   cudaError_t launch_step_##SUFFIX(const StepArgs& a, cudaStream_t st);                                       \

@@ -10,6 +10,11 @@ long long node_blocks(const Geometry& g) {
   return (long long)gr.x * gr.y;
 }
 
+long long step_blocks(const Geometry& g, const LaunchCfg& k) {
+  const dim3 gr = step_grid(g, k);
+  return (long long)gr.x * gr.y;
+}
+
 // Fixed-order final sum of the block partials: out[0..4] as in lbm_diagnostics
 // (mass gets rho_ref for every finite node), out[5] = t; non-finite nodes are
 // added to *sticky.
