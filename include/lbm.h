@@ -193,6 +193,36 @@ int lbm_sync(lbm_ctx* ctx);
  */
 int lbm_measure_peak(int kind, double* h_flops);
 
+/*
+ * One fused FP64 step with diagnostics that allocates no device memory (no
+ * counterpart in the paper). For callers that cannot call cudaMalloc: code
+ * whose device memory must all come from its own pool or arena, loops where an
+ * allocation's implicit synchronisation would stall the GPU, or work recorded
+ * into a CUDA graph. It needs no lattice object: the caller passes every input
+ * and output, and the only scratch, the per-block diagnostics sums, lives in a
+ * fixed static device array of 320 KiB (8192 blocks x 5 doubles) that every
+ * GPU which loads the library holds until the process exits.
+ *
+ *   d_src   device buffer in the FP64 layout of lbm_layout(nx, ny, LBM_F64)
+ *           holding the state at time t as the library keeps it: plane i, node y
+ *           holds f_i(y + c_i, t) (periodic), the population that node y + c_i
+ *           pulls from y; read only.
+ *   d_dst   a second such buffer (not aliasing d_src); receives the state at t + 1
+ *           in the same convention.
+ *   d_diag5 device array of 5 doubles: diagnostics of f(x, t) as in lbm_diagnostics.
+ *   stream  cudaStream_t as void* (NULL = legacy default stream).
+ *
+ * Asynchronous. The first call on a device resolves the scratch array's device
+ * address (a cudaGetSymbolAddress on that device, which must be current); make
+ * that first call before any stream capture. All calls on a device share the
+ * scratch: calls whose work overlaps on the GPU race on it. Lattices that need
+ * more than 8192 blocks of 32 x 8 threads with up to 64 rows per thread (for
+ * example a 16384 x 16384 grid; 8192 x 8192 fits) are rejected with LBM_EINVAL.
+ * On failure, lbm_last_error(NULL) describes the error.
+ */
+int lbm_step_noalloc(int nx, int ny, double theta, double tau, int model, const double* d_src,
+                     double* d_dst, double* d_diag5, void* stream);
+
 /* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -47,6 +47,7 @@ _SIGNATURES = {
     "lbm_sync": ([_p], _i),
     "lbm_measure_peak": ([_i, _pd], _i),
     "lbm_set_launch": ([_p, _i, _i, _i], _i),
+    "lbm_step_noalloc": ([_i, _i, _d, _d, _i, _p, _p, _p, _p], _i),
     "lbm_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "lbm_last_error": ([_p], ctypes.c_char_p),
 }
@@ -204,3 +205,9 @@ def lbm_get_launch(ctx):
     bx, by, rows = _i(), _i(), _i()
     check(load().lbm_get_launch(ctx, ctypes.byref(bx), ctypes.byref(by), ctypes.byref(rows)), ctx)
     return bx.value, by.value, rows.value
+
+
+def lbm_step_noalloc(nx: int, ny: int, theta: float, tau: float, model: int, d_src: int, d_dst: int,
+                     d_diag5: int, stream: int = 0) -> None:
+    """One fused FP64 step + diagnostics on caller buffers, with no device allocation."""
+    check(load().lbm_step_noalloc(nx, ny, theta, tau, model, d_src, d_dst, d_diag5, stream or None))

@@ -129,6 +129,14 @@ void free_ctx(lbm_ctx* c) {
 
 }  // namespace
 
+int olbm::set_thread_error(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_create_err, sizeof(g_create_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
 extern "C" {
 
 int lbm_version(void) { return (1 << 16) | 0; }

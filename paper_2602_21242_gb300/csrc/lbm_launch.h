@@ -52,6 +52,9 @@ OLBM_DECLARE_LAUNCHERS(f64)
 OLBM_DECLARE_LAUNCHERS(f32)
 OLBM_DECLARE_LAUNCHERS(f16)
 
+// Record a message for lbm_last_error(NULL) on this thread; returns status.
+int set_thread_error(int status, const char* fmt, ...);
+
 cudaError_t launch_finalize(const double* partials, int nparts, double rho_ref, long long nodes, long long t,
                             double* out, unsigned long long* sticky, cudaStream_t st);
 
