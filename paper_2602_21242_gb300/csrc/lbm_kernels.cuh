@@ -49,15 +49,17 @@ __device__ __forceinline__ bool finite_bits(float v) {
   return (__float_as_int(v) & 0x7f800000) != 0x7f800000;
 }
 
-// Block-wide sum of per-thread diagnostics: the four moment sums are reduced
-// across each warp in the compute type T (an xor butterfly, identical in every
-// lane), then the warp totals are added in FP64 in warp order by thread 0. The
-// non-finite count is reduced as an integer. Deterministic for a given block
-// shape. Blocks have at most kMaxWarps warps.
+// Block-wide sum of per-thread diagnostics, entirely in the compute type T
+// (FP64 for the FP64 form, FP32 for the shifted forms, whose per-node values are
+// small deviations): an xor butterfly in each warp (identical in every lane),
+// then the warp totals in warp order by thread 0, which converts the four sums
+// to FP64 for the global reduction. The non-finite count is an integer.
+// Deterministic for a given block shape; at most kMaxWarps warps per block.
 constexpr int kMaxWarps = 16;
 template <typename T>
 __device__ __forceinline__ void block_diag(T (&v)[4], int bad, double* __restrict__ out5) {
-  __shared__ double red[kMaxWarps][5];
+  __shared__ T red[kMaxWarps][4];
+  __shared__ int redbad[kMaxWarps];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -68,16 +70,21 @@ __device__ __forceinline__ void block_diag(T (&v)[4], int bad, double* __restric
   const int nw = (blockDim.x * blockDim.y) >> 5;
   if ((tid & 31) == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[tid >> 5][k] = (double)v[k];
-    red[tid >> 5][4] = (double)bad;
+    for (int k = 0; k < 4; ++k) red[tid >> 5][k] = v[k];
+    redbad[tid >> 5] = bad;
   }
   __syncthreads();
   if (tid == 0) {
-    for (int k = 0; k < 5; ++k) {
-      double acc = 0.0;
-      for (int w = 0; w < nw; ++w) acc += red[w][k];
-      out5[k] = acc;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    int nb = 0;
+    for (int w = 0; w < nw; ++w) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += red[w][k];
+      nb += redbad[w];
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out5[k] = (double)acc[k];
+    out5[4] = (double)nb;
   }
 }
 
@@ -101,13 +108,12 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
   if (x < g.nx) {
     const int xm = (x == 0) ? g.nx - 1 : x - 1;
     const int xp = (x == g.nx - 1) ? 0 : x + 1;
-    for (int r = 0; r < rows; ++r) {
-      const int y = y0 + r * (int)blockDim.y;
-      if (y >= g.ny) break;
+    const int dy = (int)blockDim.y;
+    // Pull of node (x, y): f_i(x, y) = B_i(x - c_ix, y - c_iy), periodic.
+    auto pull = [&](int y, T (&f)[9]) {
       const int ym = (y == 0) ? g.ny - 1 : y - 1;
       const int yp = (y == g.ny - 1) ? 0 : y + 1;
       const long long rc = (long long)y * g.pitch, rm = (long long)ym * g.pitch, rp = (long long)yp * g.pitch;
-      T f[9];
       f[0] = ld_t(src + rc + x, T());
       f[1] = ld_t(src + 1 * g.plane + rc + xm, T());
       f[2] = ld_t(src + 2 * g.plane + rm + x, T());
@@ -117,8 +123,18 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
       f[6] = ld_t(src + 6 * g.plane + rm + xp, T());
       f[7] = ld_t(src + 7 * g.plane + rp + xp, T());
       f[8] = ld_t(src + 8 * g.plane + rp + xm, T());
+    };
+    T f[9], fn[9];
+    int y = y0;
+    if (y < g.ny) pull(y, f);
+    for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
+      // Loads of the next row are issued before this row's arithmetic, so each
+      // thread keeps 18 loads in flight.
+      const bool more = (r + 1 < rows) && (y + dy < g.ny);
+      if (more) pull(y + dy, fn);
       NodeMoments<T> m;
       collide<MODEL, Form<PREC>::kShift, T>(f, c, m);
+      const long long rc = (long long)y * g.pitch;
 #pragma unroll
       for (int i = 0; i < 9; ++i) st_t(dst + i * g.plane + rc + x, f[i]);
       if constexpr (DIAG) {
@@ -130,6 +146,10 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
         } else {
           ++bad;
         }
+      }
+      if (more) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fn[i];
       }
     }
   }

@@ -1,0 +1,110 @@
+"""Shifted-storage forms (FP32 and FP16 deviations from the rest state, FP32
+arithmetic) against the FP64 oracle, at stated error bounds.
+
+Bound derivation (absolute error per population after n steps, flows with
+|f - rho_ref W| <= d): each step rounds every stored deviation once (half an ulp
+of d: 2^-24 d in FP32, 2^-11 d in FP16) and the FP32 collision adds at most a few
+ulps of its O(d) intermediate terms; errors in the conserved moments persist,
+those in the other moments relax. A linear worst case over n steps is
+n * (2^-24 * 16 d) for FP32 and n * (2^-11 d) for FP16 storage, the form of the
+bounds asserted below with d the largest initial deviation.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2602_21242_gb300 import flows
+from paper_2602_21242_gb300.lattice import Lattice
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 100
+
+
+def rest_state(theta):
+    w0, w1 = 1 - theta, theta / 2
+    wx = np.array([w0, w1, w0, w1, w0, w1, w1, w1, w1])
+    wy = np.array([w0, w0, w1, w0, w1, w1, w1, w1, w1])
+    return wx * wy
+
+
+def bound(prec, d, steps=STEPS):
+    return steps * (2.0 ** -24 * 16 * d if prec == "f32" else 2.0 ** -11 * d)
+
+
+def run_form(f0, theta, tau, model, prec, steps=STEPS):
+    _, ny, nx = f0.shape
+    with Lattice(nx, ny, theta, tau, model, prec) as lat:
+        lat.set_state(torch.from_numpy(f0).cuda())
+        lat.step(steps)
+        lat.sync()
+        return lat.state().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_taylor_green_forms(oracle, prec, model):
+    n, theta, nu, u0 = 64, 1.0 / 3.0, 0.01, 0.05
+    tau = oracle.tau_from_nu(nu, theta)
+    f0 = oracle.init(*flows.taylor_green(n, n, u0, theta), theta)
+    d = np.abs(f0 - rest_state(theta)[:, None, None]).max()
+    ref = oracle.run(f0, theta, tau, model, STEPS)
+    got = run_form(f0, theta, tau, model, prec)
+    err = np.abs(got - ref).max()
+    assert err <= bound(prec, d), f"{prec} model {model}: max abs err {err:.3e} > bound {bound(prec, d):.3e}"
+    # velocity error relative to the flow amplitude
+    du = max(np.abs(a - b).max() for a, b in zip(oracle.moments(got)[1:], oracle.moments(ref)[1:]))
+    assert du / u0 <= (2e-5 if prec == "f32" else 5e-2)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("theta", [0.25, 0.4])
+def test_advected_shear_wave_forms(oracle, prec, theta):
+    nx, ny, U = 96, 10, 0.1
+    tau = oracle.tau_from_nu(0.005, theta)
+    f0 = oracle.init(*flows.shear_wave(nx, ny, U=U, amp=0.01), theta)
+    d = np.abs(f0 - rest_state(theta)[:, None, None]).max()
+    ref = oracle.run(f0, theta, tau, 3, STEPS)
+    got = run_form(f0, theta, tau, 3, prec)
+    err = np.abs(got - ref).max()
+    assert err <= bound(prec, d), f"{prec} theta {theta}: max abs err {err:.3e} > bound {bound(prec, d):.3e}"
+
+
+@pytest.mark.parametrize("model", [0, 3])
+def test_random_state_f32(oracle, model):
+    """Generic non-equilibrium populations (deviations up to ~0.2 rho w) in the FP32 form."""
+    nx, ny, theta, tau = 45, 19, 0.35, 0.8
+    f0 = flows.random_populations(nx, ny, seed=700 + model, spread=0.2)
+    d = np.abs(f0 - rest_state(theta)[:, None, None]).max()
+    ref = oracle.run(f0, theta, tau, model, STEPS)
+    got = run_form(f0, theta, tau, model, "f32")
+    err = np.abs(got - ref).max()
+    assert err <= bound("f32", d), f"model {model}: max abs err {err:.3e} > bound {bound('f32', d):.3e}"
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_forms_diagnostics(oracle, prec):
+    """FP64 global reductions of the shifted forms against the oracle's compensated sums of
+    the same (rounded) state; total mass over 100 steps within what storage rounding allows
+    (rounding a stored deviation does not conserve mass: relative drift ~ 1e-8 in FP32,
+    ~1e-4 in FP16 for this flow)."""
+    n, theta = 48, 1.0 / 3.0
+    tau = oracle.tau_from_nu(0.01, theta)
+    f0 = oracle.init(*flows.taylor_green(n, n, 0.05, theta), theta)
+    with Lattice(n, n, theta, tau, "complete", prec) as lat:
+        lat.set_state(torch.from_numpy(f0).cuda())
+        s0 = lat.state().cpu().numpy()
+        np.testing.assert_allclose(lat.diagnostics(), oracle.diagnostics(s0), rtol=1e-12, atol=1e-12)
+        lat.set_diagnostics_interval(10)
+        lat.step(STEPS)
+        st = lat.state().cpu().numpy()
+        lat.step(1)  # fused pass at t = STEPS
+        fused, t, status = lat.step_diagnostics()
+    assert t == STEPS and status == 0
+    ref = oracle.diagnostics(st)
+    # fused sums (FP32 within a block for the shifted forms, FP64 across blocks)
+    np.testing.assert_allclose(fused[0], ref[0], rtol=1e-12)
+    np.testing.assert_allclose(fused[1:4], ref[1:4], rtol=1e-5, atol=1e-9)
+    drift = abs(ref[0] - oracle.diagnostics(f0)[0]) / ref[0]
+    assert drift <= (1e-8 if prec == "f32" else 1e-4)
