@@ -104,7 +104,7 @@ def test_forms_diagnostics(oracle, prec):
     assert t == STEPS and status == 0
     ref = oracle.diagnostics(st)
     # fused sums (FP32 within a block for the shifted forms, FP64 across blocks)
-    np.testing.assert_allclose(fused[0], ref[0], rtol=1e-12)
+    np.testing.assert_allclose(fused[0], ref[0], rtol=1e-9)
     np.testing.assert_allclose(fused[1:4], ref[1:4], rtol=1e-5, atol=1e-9)
     drift = abs(ref[0] - oracle.diagnostics(f0)[0]) / ref[0]
     assert drift <= (1e-8 if prec == "f32" else 1e-4)
