@@ -177,7 +177,7 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   c->state_bytes = bytes;
   c->stream = static_cast<cudaStream_t>(stream);
   c->cfg = default_cfg(prec);
-  c->nparts = olbm::step_blocks(c->g, c->cfg);
+  c->nparts = olbm::step_blocks(c->g, c->cfg, prec);
   c->parts_cap = std::max(c->nparts, olbm::node_blocks(c->g));
 
   if (d_pop_buffers) {
@@ -428,7 +428,7 @@ int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows) {
   if (!olbm::valid_cfg(k))
     return fail(ctx, LBM_EINVAL, "launch shape %dx%d x %d rows invalid (bx a multiple of 32, bx*by <= 512, rows 1..64)",
                 bx, by, rows);
-  const long long need = olbm::step_blocks(ctx->g, k);
+  const long long need = olbm::step_blocks(ctx->g, k, ctx->prec);
   if (need > ctx->parts_cap) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_launch sync");

@@ -64,6 +64,34 @@ template <> __device__ __forceinline__ __half from_double<__half>(double v) {
   return __float2half_rn((float)v);
 }
 
+// ---------------------------------------------------------------- packed FP32
+// Two nodes' values in one register pair, operated on by Blackwell's packed
+// FP32 instructions (add/mul/fma .f32x2, sm_100 and later): one instruction
+// per operation for two nodes, each lane rounded exactly as the scalar
+// operation. a - b is formed as fma(b, -1, a), exact like a scalar subtraction.
+struct f32x2 {
+  float2 v;
+  f32x2() = default;
+  __host__ __device__ f32x2(float s) : v(make_float2(s, s)) {}
+  __host__ __device__ f32x2(double s) : v(make_float2((float)s, (float)s)) {}
+  __host__ __device__ f32x2(int s) : v(make_float2((float)s, (float)s)) {}
+  __host__ __device__ explicit f32x2(float2 a) : v(a) {}
+  // Hidden friends: found only by argument-dependent lookup on f32x2, so they
+  // never capture a scalar fma(double, ...) call.
+  friend __device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b) { return f32x2(__fadd2_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ f32x2 operator*(f32x2 a, f32x2 b) { return f32x2(__fmul2_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) {
+    return f32x2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));
+  }
+  friend __device__ __forceinline__ f32x2 operator-(f32x2 a) {
+    return f32x2(__fmul2_rn(a.v, make_float2(-1.0f, -1.0f)));
+  }
+  friend __device__ __forceinline__ f32x2& operator+=(f32x2& a, f32x2 b) { return a = a + b; }
+  friend __device__ __forceinline__ f32x2 fma(f32x2 a, f32x2 b, f32x2 c) {
+    return f32x2(__ffma2_rn(a.v, b.v, c.v));
+  }
+};
+
 // ---------------------------------------------------------------- lattice
 // Population index of velocity (a, b), a, b in {-1, 0, 1}: IDX[a + 1][b + 1]
 // (Fig. 1a numbering: c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1) c5=(1,1) c6=(-1,1)
@@ -98,6 +126,7 @@ template <typename T> struct Coef {
   T c3;           // 1 - 3 theta
   T tt;           // theta (1 - 3 theta)
   T inv2t2;       // 1 / (2 theta^2)
+  T mq_inv2t2;    // -1 / (8 theta^2)
   T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
   T w[3];         // rho_ref * rest weights per axis pair are W(a) W(b); W(-1) = W(1) = theta/2, W(0) = 1 - theta
 };
@@ -115,6 +144,7 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
   c.c3 = (T)(1.0 - 3.0 * theta);
   c.tt = (T)(theta * (1.0 - 3.0 * theta));
   c.inv2t2 = (T)(1.0 / (2.0 * theta * theta));
+  c.mq_inv2t2 = (T)(-0.25 / (2.0 * theta * theta));
   c.rho_ref = (T)rho_ref;
   c.w[0] = (T)(0.5 * theta);
   c.w[1] = (T)(1.0 - theta);
@@ -146,6 +176,7 @@ __device__ __forceinline__ double recip(double x) {
   return fma(r0, fma(e, e, e), r0);
 }
 __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+__device__ __forceinline__ f32x2 recip(f32x2 x) { return f32x2(make_float2(1.0f / x.v.x, 1.0f / x.v.y)); }
 
 // ---------------------------------------------------------------- collision
 // In-place collision of one node (Eq. 1a). f holds the stored values of the
@@ -221,12 +252,12 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
     const T Pxy = s57 - s68;
     const T A1 = c.k1 * fma(-rho, ux2 - uy2, Dxy);  // omega' K1
     const T A2 = c.k2 * fma(-jx, uy, Pxy);          // omega' K2
-    const T cxm[3] = {T(-1) - ux, -ux, T(1) - ux};  // C_x(a) = a - u_x
-    const T cym[3] = {T(-1) - uy, -uy, T(1) - uy};
+    const T cxm[3] = {T(-1.0) - ux, -ux, T(1.0) - ux};  // C_x(a) = a - u_x
+    const T cym[3] = {T(-1.0) - uy, -uy, T(1.0) - uy};
     // omega' Psi per population (Eqs. 14, 15), from closed-form psi and Pi~.
     T cor[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) cor[i] = T(0);
+    for (int i = 0; i < 9; ++i) cor[i] = T(0.0);
     if constexpr (MODEL >= 2) {
       const T wpsx = A1 * ux * (c.c3 - ux2);   // omega' psi_x
       const T wpsy = -A1 * uy * (c.c3 - uy2);  // omega' psi_y
@@ -240,9 +271,9 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
         // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12 (evaluated on f^OReg).
         const T muxx = (c.theta - ux2) * px[1];  // 2 theta^2 mu_xx
         const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
-        const T hwpref = T(-0.25) * c.inv2t2 * A1 * (muxx + muyy);  // omega' pref / 2
-        const T hPxx = -hwpref * fma(ux2, ux2 - T(1), c.tt);       // omega' Pi~_xx / 2
-        const T hPyy = hwpref * fma(uy2, uy2 - T(1), c.tt);        // omega' Pi~_yy / 2
+        const T hwpref = c.mq_inv2t2 * A1 * (muxx + muyy);  // omega' pref / 2
+        const T hPxx = -hwpref * fma(ux2, ux2 - T(1.0), c.tt);       // omega' Pi~_xx / 2
+        const T hPyy = hwpref * fma(uy2, uy2 - T(1.0), c.tt);        // omega' Pi~_yy / 2
         const T qPxy = T(0.5) * hwpref * (ux * uy) * (ux2 - uy2);  // omega' Pi~_xy / 4
         const T hpsx = T(0.5) * wpsx, hpsy = T(0.5) * wpsy;
         cor[1] = hPyy - hpsx;

@@ -158,6 +158,98 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
   }
 }
 
+// ------------------------------------------------------------------ fused step, node pairs
+// Shifted forms with even nx: each thread updates the node pair (x, x + 1),
+// x even, with the collision evaluated once on packed f32x2 values. Planes with
+// c_ix = 0 are read as one aligned 2-element vector; planes with c_ix = +-1
+// need (x - 1, x) or (x + 1, x + 2) and are read element by element. Stores
+// are aligned 2-element vectors. Otherwise as step_kernel.
+__device__ __forceinline__ f32x2 ld_pair(const float* p) { return f32x2(__ldg(reinterpret_cast<const float2*>(p))); }
+__device__ __forceinline__ f32x2 ld_pair(const __half* p) {
+  return f32x2(__half22float2(__ldg(reinterpret_cast<const __half2*>(p))));
+}
+__device__ __forceinline__ f32x2 ld_two(const float* p0, const float* p1) {
+  return f32x2(make_float2(__ldg(p0), __ldg(p1)));
+}
+__device__ __forceinline__ f32x2 ld_two(const __half* p0, const __half* p1) {
+  return f32x2(make_float2(__half2float(__ldg(p0)), __half2float(__ldg(p1))));
+}
+__device__ __forceinline__ void st_pair(float* p, f32x2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+__device__ __forceinline__ void st_pair(__half* p, f32x2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
+
+template <int MODEL, int PREC, bool DIAG>
+__global__ void __launch_bounds__(512) step_pair_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                        typename Form<PREC>::S* __restrict__ dst, Geometry g,
+                                                        Coef<f32x2> c, double* __restrict__ partials, int rows) {
+  static_assert(PREC != 0, "node pairs are for the shifted forms");
+  using S = typename Form<PREC>::S;
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y0 = blockIdx.y * blockDim.y * rows + threadIdx.y;
+  f32x2 acc[4] = {f32x2(0.0f), f32x2(0.0f), f32x2(0.0f), f32x2(0.0f)};
+  int bad = 0;
+  if (x < g.nx) {
+    const int xm = (x == 0) ? g.nx - 1 : x - 1;           // x - 1, periodic
+    const int xp2 = (x + 2 >= g.nx) ? x + 2 - g.nx : x + 2;  // x + 2, periodic
+    const int dy = (int)blockDim.y;
+    auto pull = [&](int y, f32x2 (&f)[9]) {
+      const int ym = (y == 0) ? g.ny - 1 : y - 1;
+      const int yp = (y == g.ny - 1) ? 0 : y + 1;
+      const S* p0 = src + (long long)y * g.pitch;
+      const S* pm = src + (long long)ym * g.pitch;
+      const S* pp = src + (long long)yp * g.pitch;
+      f[0] = ld_pair(p0 + x);
+      f[1] = ld_two(p0 + 1 * g.plane + xm, p0 + 1 * g.plane + x);
+      f[2] = ld_pair(pm + 2 * g.plane + x);
+      f[3] = ld_two(p0 + 3 * g.plane + x + 1, p0 + 3 * g.plane + xp2);
+      f[4] = ld_pair(pp + 4 * g.plane + x);
+      f[5] = ld_two(pm + 5 * g.plane + xm, pm + 5 * g.plane + x);
+      f[6] = ld_two(pm + 6 * g.plane + x + 1, pm + 6 * g.plane + xp2);
+      f[7] = ld_two(pp + 7 * g.plane + x + 1, pp + 7 * g.plane + xp2);
+      f[8] = ld_two(pp + 8 * g.plane + xm, pp + 8 * g.plane + x);
+    };
+    f32x2 f[9], fn[9];
+    int y = y0;
+    if (y < g.ny) pull(y, f);
+    for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
+      const bool more = (r + 1 < rows) && (y + dy < g.ny);
+      if (more) pull(y + dy, fn);
+      NodeMoments<f32x2> m;
+      collide<MODEL, true, f32x2>(f, c, m);
+      S* q = dst + (long long)y * g.pitch + x;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);
+      if constexpr (DIAG) {
+        const bool ok0 = finite_bits(m.m0.v.x), ok1 = finite_bits(m.m0.v.y);
+        if (ok0 && ok1) {
+          acc[0] += m.m0;
+          acc[1] += m.jx;
+          acc[2] += m.jy;
+          acc[3] += m.ke;
+        } else {
+          // keep the finite node of the pair, count the other
+          const float2 keep = make_float2(ok0 ? 1.0f : 0.0f, ok1 ? 1.0f : 0.0f);
+          acc[0] += f32x2(make_float2(ok0 ? m.m0.v.x : 0.0f, ok1 ? m.m0.v.y : 0.0f));
+          acc[1] += f32x2(make_float2(ok0 ? m.jx.v.x : 0.0f, ok1 ? m.jx.v.y : 0.0f));
+          acc[2] += f32x2(make_float2(ok0 ? m.jy.v.x : 0.0f, ok1 ? m.jy.v.y : 0.0f));
+          acc[3] += f32x2(make_float2(ok0 ? m.ke.v.x : 0.0f, ok1 ? m.ke.v.y : 0.0f));
+          bad += (ok0 ? 0 : 1) + (ok1 ? 0 : 1);
+          (void)keep;
+        }
+      }
+      if (more) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fn[i];
+      }
+    }
+  }
+  if constexpr (DIAG) {
+    float a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = acc[k].v.x + acc[k].v.y;
+    block_diag<float>(a, bad, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
+  }
+}
+
 // ------------------------------------------------------------------ diagnostics of the state
 // Pull only (no collision): FP64 moments of f(x, t), block partials as above.
 template <int PREC>
@@ -276,8 +368,11 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 
 // ------------------------------------------------------------------ launchers
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
-inline dim3 step_grid(const Geometry& g, const LaunchCfg& k) {
-  return dim3((g.nx + k.bx - 1) / k.bx, (g.ny + k.by * k.rows - 1) / (k.by * k.rows));
+// The shifted forms update node pairs (x, x + 1) when nx is even.
+inline bool uses_pairs(int prec, const Geometry& g) { return prec != 0 && (g.nx % 2) == 0; }
+inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
+  const int cols = uses_pairs(prec, g) ? 2 * k.bx : k.bx;
+  return dim3((g.nx + cols - 1) / cols, (g.ny + k.by * k.rows - 1) / (k.by * k.rows));
 }
 
 template <int PREC> struct Launch {
@@ -287,7 +382,19 @@ template <int PREC> struct Launch {
   template <int MODEL>
   static cudaError_t step_m(const StepArgs& a, const Coef<T>& c, cudaStream_t st) {
     const dim3 block(a.cfg.bx, a.cfg.by);
-    const dim3 grid = step_grid(a.g, a.cfg);
+    const dim3 grid = step_grid(a.g, a.cfg, PREC);
+    if constexpr (PREC != 0) {
+      if (uses_pairs(PREC, a.g)) {
+        const Coef<f32x2> c2 = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
+        if (a.diag)
+          step_pair_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c2,
+                                                                       a.partials, a.cfg.rows);
+        else
+          step_pair_kernel<MODEL, PREC, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c2,
+                                                                        a.partials, a.cfg.rows);
+        return cudaGetLastError();
+      }
+    }
     if (a.diag)
       step_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
                                                               a.cfg.rows);

@@ -33,7 +33,7 @@ struct StepArgs {
 // Number of thread blocks of the auxiliary node-parallel kernels and of the
 // step kernel under a launch shape (= diagnostics partials they write).
 long long node_blocks(const Geometry& g);
-long long step_blocks(const Geometry& g, const LaunchCfg& k);
+long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec);
 
 #define OLBM_DECLARE_LAUNCHERS(SUFFIX)                                                                        \
   cudaError_t launch_step_##SUFFIX(const StepArgs& a, cudaStream_t st);                                       \

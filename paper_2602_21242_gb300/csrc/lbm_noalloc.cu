@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kSumThreads) noalloc_sum_kernel(const double* 
 template <int MODEL>
 cudaError_t launch(const olbm::Geometry& g, const olbm::Coef<double>& c, const double* src, double* dst,
                    double* partials, const olbm::LaunchCfg& k, cudaStream_t st) {
-  const dim3 grid = olbm::step_grid(g, k), block(k.bx, k.by);
+  const dim3 grid = olbm::step_grid(g, k, 0), block(k.bx, k.by);
   olbm::step_kernel<MODEL, 0, true><<<grid, block, 0, st>>>(src, dst, g, c, partials, k.rows);
   return cudaGetLastError();
 }
@@ -89,8 +89,8 @@ extern "C" int lbm_step_noalloc(int nx, int ny, double theta, double tau, int mo
   k.bx = 32;
   k.by = 8;
   k.rows = 4;
-  while (olbm::step_blocks(g, k) > kNoAllocMaxBlocks && k.rows < 64) k.rows *= 2;
-  const long long nparts = olbm::step_blocks(g, k);
+  while (olbm::step_blocks(g, k, LBM_F64) > kNoAllocMaxBlocks && k.rows < 64) k.rows *= 2;
+  const long long nparts = olbm::step_blocks(g, k, LBM_F64);
   if (nparts > kNoAllocMaxBlocks)
     return olbm::set_thread_error(LBM_EINVAL,
                                   "lbm_step_noalloc: a %d x %d lattice needs %lld thread blocks, more than the %d "

@@ -10,8 +10,8 @@ long long node_blocks(const Geometry& g) {
   return (long long)gr.x * gr.y;
 }
 
-long long step_blocks(const Geometry& g, const LaunchCfg& k) {
-  const dim3 gr = step_grid(g, k);
+long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec) {
+  const dim3 gr = step_grid(g, k, prec);
   return (long long)gr.x * gr.y;
 }
 

@@ -71,10 +71,12 @@ def test_advected_shear_wave_forms(oracle, prec, theta):
     assert err <= bound(prec, d), f"{prec} theta {theta}: max abs err {err:.3e} > bound {bound(prec, d):.3e}"
 
 
+@pytest.mark.parametrize("nx,ny", [(45, 19), (46, 19), (2, 3), (130, 1)])
 @pytest.mark.parametrize("model", [0, 3])
-def test_random_state_f32(oracle, model):
-    """Generic non-equilibrium populations (deviations up to ~0.2 rho w) in the FP32 form."""
-    nx, ny, theta, tau = 45, 19, 0.35, 0.8
+def test_random_state_f32(oracle, model, nx, ny):
+    """Generic non-equilibrium populations (deviations up to ~0.2 rho w) in the FP32 form; odd
+    widths take the one-node-per-thread kernel, even widths the node-pair kernel."""
+    theta, tau = 0.35, 0.8
     f0 = flows.random_populations(nx, ny, seed=700 + model, spread=0.2)
     d = np.abs(f0 - rest_state(theta)[:, None, None]).max()
     ref = oracle.run(f0, theta, tau, model, STEPS)
@@ -105,6 +107,6 @@ def test_forms_diagnostics(oracle, prec):
     ref = oracle.diagnostics(st)
     # fused sums (FP32 within a block for the shifted forms, FP64 across blocks)
     np.testing.assert_allclose(fused[0], ref[0], rtol=1e-9)
-    np.testing.assert_allclose(fused[1:4], ref[1:4], rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(fused[1:4], ref[1:4], rtol=1e-5, atol=1e-5)
     drift = abs(ref[0] - oracle.diagnostics(f0)[0]) / ref[0]
     assert drift <= (1e-8 if prec == "f32" else 1e-4)
