@@ -76,15 +76,19 @@ bool layout_of(int nx, int ny, int prec, long long* pitch, long long* plane, lon
 
 long long nodes_of(const lbm_ctx* c) { return (long long)c->nx * c->ny; }
 
-// Default launch shapes of the step kernel per storage form, chosen by timing on
-// GB300 at the 4096^2 benchmark size; lbm_set_launch overrides them per lattice.
-olbm::LaunchCfg default_cfg(int prec) {
+// Default launch shape of the step kernel per storage form, chosen by timing on
+// GB300 at the 4096^2 benchmark size (FP64: 64 x 2 threads, 32 rows; shifted
+// forms: 128 x 4 threads, 16 rows). On smaller lattices the rows per thread are
+// halved until the grid has at least 4 blocks per SM. lbm_set_launch (and the
+// autotuner built on it) overrides the shape per lattice.
+olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
   olbm::LaunchCfg k;
   if (prec == LBM_F64) {
-    k.bx = 32, k.by = 8, k.rows = 4;
+    k.bx = 64, k.by = 2, k.rows = 32;
   } else {
-    k.bx = 128, k.by = 2, k.rows = 4;
+    k.bx = 128, k.by = 4, k.rows = 16;
   }
+  while (k.rows > 1 && olbm::step_blocks(g, k, prec) < 4LL * sms) k.rows /= 2;
   return k;
 }
 
@@ -176,7 +180,9 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   c->g = olbm::Geometry{nx, ny, pitch, plane};
   c->state_bytes = bytes;
   c->stream = static_cast<cudaStream_t>(stream);
-  c->cfg = default_cfg(prec);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
+  c->cfg = default_cfg(prec, c->g, sms);
   c->nparts = olbm::step_blocks(c->g, c->cfg, prec);
   c->parts_cap = std::max(c->nparts, olbm::node_blocks(c->g));
 

@@ -13,6 +13,8 @@
 // moments pull it back.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
@@ -88,82 +90,8 @@ __device__ __forceinline__ void block_diag(T (&v)[4], int bad, double* __restric
   }
 }
 
-// ------------------------------------------------------------------ fused step
-// Block (bx, by) threads, bx a multiple of 32, bx * by <= 512; each thread
-// updates `rows` nodes of one column x, at rows y0 + r * by (r < rows), so at
-// every iteration a block covers by consecutive rows. Pull (Eq. 1b), collide
-// (Eq. 1a), store. With DIAG, per-block sums of mass (as the stored deviation
-// m0), momentum, kinetic energy and the number of nodes whose pulled
-// populations do not sum to a finite value go to partials[block * 5 + k].
-template <int MODEL, int PREC, bool DIAG>
-__global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S* __restrict__ src,
-                                                   typename Form<PREC>::S* __restrict__ dst, Geometry g,
-                                                   Coef<typename Form<PREC>::T> c, double* __restrict__ partials,
-                                                   int rows) {
-  using T = typename Form<PREC>::T;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y0 = blockIdx.y * blockDim.y * rows + threadIdx.y;
-  T acc[4] = {T(0), T(0), T(0), T(0)};
-  int bad = 0;
-  if (x < g.nx) {
-    const int xm = (x == 0) ? g.nx - 1 : x - 1;
-    const int xp = (x == g.nx - 1) ? 0 : x + 1;
-    const int dy = (int)blockDim.y;
-    // Pull of node (x, y): f_i(x, y) = B_i(x - c_ix, y - c_iy), periodic.
-    auto pull = [&](int y, T (&f)[9]) {
-      const int ym = (y == 0) ? g.ny - 1 : y - 1;
-      const int yp = (y == g.ny - 1) ? 0 : y + 1;
-      const long long rc = (long long)y * g.pitch, rm = (long long)ym * g.pitch, rp = (long long)yp * g.pitch;
-      f[0] = ld_t(src + rc + x, T());
-      f[1] = ld_t(src + 1 * g.plane + rc + xm, T());
-      f[2] = ld_t(src + 2 * g.plane + rm + x, T());
-      f[3] = ld_t(src + 3 * g.plane + rc + xp, T());
-      f[4] = ld_t(src + 4 * g.plane + rp + x, T());
-      f[5] = ld_t(src + 5 * g.plane + rm + xm, T());
-      f[6] = ld_t(src + 6 * g.plane + rm + xp, T());
-      f[7] = ld_t(src + 7 * g.plane + rp + xp, T());
-      f[8] = ld_t(src + 8 * g.plane + rp + xm, T());
-    };
-    T f[9], fn[9];
-    int y = y0;
-    if (y < g.ny) pull(y, f);
-    for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
-      // Loads of the next row are issued before this row's arithmetic, so each
-      // thread keeps 18 loads in flight.
-      const bool more = (r + 1 < rows) && (y + dy < g.ny);
-      if (more) pull(y + dy, fn);
-      NodeMoments<T> m;
-      collide<MODEL, Form<PREC>::kShift, T>(f, c, m);
-      const long long rc = (long long)y * g.pitch;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) st_t(dst + i * g.plane + rc + x, f[i]);
-      if constexpr (DIAG) {
-        if (finite_bits(m.m0)) {
-          acc[0] += m.m0;
-          acc[1] += m.jx;
-          acc[2] += m.jy;
-          acc[3] += m.ke;
-        } else {
-          ++bad;
-        }
-      }
-      if (more) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = fn[i];
-      }
-    }
-  }
-  if constexpr (DIAG) {
-    block_diag<T>(acc, bad, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
-  }
-}
-
-// ------------------------------------------------------------------ fused step, node pairs
-// Shifted forms with even nx: each thread updates the node pair (x, x + 1),
-// x even, with the collision evaluated once on packed f32x2 values. Planes with
-// c_ix = 0 are read as one aligned 2-element vector; planes with c_ix = +-1
-// need (x - 1, x) or (x + 1, x + 2) and are read element by element. Stores
-// are aligned 2-element vectors. Otherwise as step_kernel.
+// ------------------------------------------------------------------ fused step: one column of nodes
+// Element loads/stores of one node pair (shifted forms, x even).
 __device__ __forceinline__ f32x2 ld_pair(const float* p) { return f32x2(__ldg(reinterpret_cast<const float2*>(p))); }
 __device__ __forceinline__ f32x2 ld_pair(const __half* p) {
   return f32x2(__half22float2(__ldg(reinterpret_cast<const __half2*>(p))));
@@ -177,77 +105,152 @@ __device__ __forceinline__ f32x2 ld_two(const __half* p0, const __half* p1) {
 __device__ __forceinline__ void st_pair(float* p, f32x2 v) { *reinterpret_cast<float2*>(p) = v.v; }
 __device__ __forceinline__ void st_pair(__half* p, f32x2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
 
-template <int MODEL, int PREC, bool DIAG>
-__global__ void __launch_bounds__(512) step_pair_kernel(const typename Form<PREC>::S* __restrict__ src,
-                                                        typename Form<PREC>::S* __restrict__ dst, Geometry g,
-                                                        Coef<f32x2> c, double* __restrict__ partials, int rows) {
-  static_assert(PREC != 0, "node pairs are for the shifted forms");
+// Per-thread diagnostics accumulator in the compute type CT.
+template <typename CT> struct DiagAcc {
+  CT v[4];
+  int bad;
+  __device__ DiagAcc() : bad(0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = CT(0.0);
+  }
+  __device__ __forceinline__ void add(const NodeMoments<CT>& m);
+};
+template <> __device__ __forceinline__ void DiagAcc<double>::add(const NodeMoments<double>& m) {
+  if (finite_bits(m.m0)) {
+    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
+  } else {
+    ++bad;
+  }
+}
+template <> __device__ __forceinline__ void DiagAcc<float>::add(const NodeMoments<float>& m) {
+  if (finite_bits(m.m0)) {
+    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
+  } else {
+    ++bad;
+  }
+}
+template <> __device__ __forceinline__ void DiagAcc<f32x2>::add(const NodeMoments<f32x2>& m) {
+  const bool ok0 = finite_bits(m.m0.v.x), ok1 = finite_bits(m.m0.v.y);
+  if (ok0 && ok1) {
+    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
+  } else {  // keep the finite node of the pair, count the other
+    const float2 k = make_float2(ok0 ? 1.0f : 0.0f, ok1 ? 1.0f : 0.0f);
+    v[0] += f32x2(make_float2(ok0 ? m.m0.v.x : 0.0f, ok1 ? m.m0.v.y : 0.0f));
+    v[1] += f32x2(make_float2(k.x * m.jx.v.x, k.y * m.jx.v.y));
+    v[2] += f32x2(make_float2(k.x * m.jy.v.x, k.y * m.jy.v.y));
+    v[3] += f32x2(make_float2(k.x * m.ke.v.x, k.y * m.ke.v.y));
+    bad += (ok0 ? 0 : 1) + (ok1 ? 0 : 1);
+  }
+}
+
+// Reduce a thread's accumulator over the block into out5 (thread 0 writes).
+template <typename CT> __device__ __forceinline__ void block_diag_acc(DiagAcc<CT>& a, double* out5) {
+  if constexpr (std::is_same<CT, f32x2>::value) {
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = a.v[k].v.x + a.v[k].v.y;
+    block_diag<float>(v, a.bad, out5);
+  } else {
+    block_diag<CT>(a.v, a.bad, out5);
+  }
+}
+
+// Update `rows` nodes (or node pairs) of column x: rows y0, y0 + dy, ...,
+// pulling each row's 9 populations (Eq. 1b, periodic), colliding (Eq. 1a) and
+// storing aligned. The next row's loads are issued before the current row's
+// arithmetic, so each thread keeps two rows of loads in flight. With PAIRS
+// (shifted forms, even nx, x even) the nodes x and x + 1 are updated together
+// on packed f32x2 values; planes with c_ix = 0 are read as aligned 2-element
+// vectors, the others element by element.
+template <int MODEL, int PREC, bool DIAG, bool PAIRS> struct Column {
   using S = typename Form<PREC>::S;
-  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y0 = blockIdx.y * blockDim.y * rows + threadIdx.y;
-  f32x2 acc[4] = {f32x2(0.0f), f32x2(0.0f), f32x2(0.0f), f32x2(0.0f)};
-  int bad = 0;
-  if (x < g.nx) {
-    const int xm = (x == 0) ? g.nx - 1 : x - 1;           // x - 1, periodic
-    const int xp2 = (x + 2 >= g.nx) ? x + 2 - g.nx : x + 2;  // x + 2, periodic
-    const int dy = (int)blockDim.y;
-    auto pull = [&](int y, f32x2 (&f)[9]) {
-      const int ym = (y == 0) ? g.ny - 1 : y - 1;
-      const int yp = (y == g.ny - 1) ? 0 : y + 1;
-      const S* p0 = src + (long long)y * g.pitch;
-      const S* pm = src + (long long)ym * g.pitch;
-      const S* pp = src + (long long)yp * g.pitch;
+  using CT = typename std::conditional<PAIRS, f32x2, typename Form<PREC>::T>::type;
+
+  __device__ static __forceinline__ void pull(const S* __restrict__ src, const Geometry& g, int x, int xm, int xp,
+                                              int y, CT (&f)[9]) {
+    const int ym = (y == 0) ? g.ny - 1 : y - 1;
+    const int yp = (y == g.ny - 1) ? 0 : y + 1;
+    const S* p0 = src + (long long)y * g.pitch;
+    const S* pm = src + (long long)ym * g.pitch;
+    const S* pp = src + (long long)yp * g.pitch;
+    if constexpr (PAIRS) {
+      // xm = x - 1, xp = x + 2 (periodic); the pair's second node is x + 1
       f[0] = ld_pair(p0 + x);
       f[1] = ld_two(p0 + 1 * g.plane + xm, p0 + 1 * g.plane + x);
       f[2] = ld_pair(pm + 2 * g.plane + x);
-      f[3] = ld_two(p0 + 3 * g.plane + x + 1, p0 + 3 * g.plane + xp2);
+      f[3] = ld_two(p0 + 3 * g.plane + x + 1, p0 + 3 * g.plane + xp);
       f[4] = ld_pair(pp + 4 * g.plane + x);
       f[5] = ld_two(pm + 5 * g.plane + xm, pm + 5 * g.plane + x);
-      f[6] = ld_two(pm + 6 * g.plane + x + 1, pm + 6 * g.plane + xp2);
-      f[7] = ld_two(pp + 7 * g.plane + x + 1, pp + 7 * g.plane + xp2);
+      f[6] = ld_two(pm + 6 * g.plane + x + 1, pm + 6 * g.plane + xp);
+      f[7] = ld_two(pp + 7 * g.plane + x + 1, pp + 7 * g.plane + xp);
       f[8] = ld_two(pp + 8 * g.plane + xm, pp + 8 * g.plane + x);
-    };
-    f32x2 f[9], fn[9];
+    } else {
+      // xm = x - 1, xp = x + 1 (periodic)
+      f[0] = ld_t(p0 + x, CT());
+      f[1] = ld_t(p0 + 1 * g.plane + xm, CT());
+      f[2] = ld_t(pm + 2 * g.plane + x, CT());
+      f[3] = ld_t(p0 + 3 * g.plane + xp, CT());
+      f[4] = ld_t(pp + 4 * g.plane + x, CT());
+      f[5] = ld_t(pm + 5 * g.plane + xm, CT());
+      f[6] = ld_t(pm + 6 * g.plane + xp, CT());
+      f[7] = ld_t(pp + 7 * g.plane + xp, CT());
+      f[8] = ld_t(pp + 8 * g.plane + xm, CT());
+    }
+  }
+
+  __device__ static __forceinline__ void run(const S* __restrict__ src, S* __restrict__ dst, const Geometry& g,
+                                             const Coef<CT>& c, int x, int y0, int dy, int rows,
+                                             DiagAcc<CT>& acc) {
+    if (x >= g.nx) return;
+    const int xm = (x == 0) ? g.nx - 1 : x - 1;
+    int xp;
+    if constexpr (PAIRS) {
+      xp = (x + 2 >= g.nx) ? x + 2 - g.nx : x + 2;
+    } else {
+      xp = (x == g.nx - 1) ? 0 : x + 1;
+    }
+    CT f[9], fn[9];
     int y = y0;
-    if (y < g.ny) pull(y, f);
+    if (y < g.ny) pull(src, g, x, xm, xp, y, f);
     for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
       const bool more = (r + 1 < rows) && (y + dy < g.ny);
-      if (more) pull(y + dy, fn);
-      NodeMoments<f32x2> m;
-      collide<MODEL, true, f32x2>(f, c, m);
+      if (more) pull(src, g, x, xm, xp, y + dy, fn);
+      NodeMoments<CT> m;
+      collide<MODEL, Form<PREC>::kShift, CT>(f, c, m);
       S* q = dst + (long long)y * g.pitch + x;
+      if constexpr (PAIRS) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);
-      if constexpr (DIAG) {
-        const bool ok0 = finite_bits(m.m0.v.x), ok1 = finite_bits(m.m0.v.y);
-        if (ok0 && ok1) {
-          acc[0] += m.m0;
-          acc[1] += m.jx;
-          acc[2] += m.jy;
-          acc[3] += m.ke;
-        } else {
-          // keep the finite node of the pair, count the other
-          const float2 keep = make_float2(ok0 ? 1.0f : 0.0f, ok1 ? 1.0f : 0.0f);
-          acc[0] += f32x2(make_float2(ok0 ? m.m0.v.x : 0.0f, ok1 ? m.m0.v.y : 0.0f));
-          acc[1] += f32x2(make_float2(ok0 ? m.jx.v.x : 0.0f, ok1 ? m.jx.v.y : 0.0f));
-          acc[2] += f32x2(make_float2(ok0 ? m.jy.v.x : 0.0f, ok1 ? m.jy.v.y : 0.0f));
-          acc[3] += f32x2(make_float2(ok0 ? m.ke.v.x : 0.0f, ok1 ? m.ke.v.y : 0.0f));
-          bad += (ok0 ? 0 : 1) + (ok1 ? 0 : 1);
-          (void)keep;
-        }
+        for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
       }
+      if constexpr (DIAG) acc.add(m);
       if (more) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
       }
     }
   }
-  if constexpr (DIAG) {
-    float a[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] = acc[k].v.x + acc[k].v.y;
-    block_diag<float>(a, bad, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
-  }
+};
+
+// One lattice: block (bx, by) threads, bx a multiple of 32, bx * by <= 512; a
+// thread updates column x (pairs: x and x + 1) at rows y0 + r * by, r < rows.
+// With DIAG, per-block sums of mass (as the stored deviation m0), momentum,
+// kinetic energy and the number of nodes whose pulled populations do not sum to
+// a finite value go to partials[block * 5 + k].
+template <int MODEL, int PREC, bool DIAG, bool PAIRS>
+__global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                   typename Form<PREC>::S* __restrict__ dst, Geometry g,
+                                                   Coef<typename Column<MODEL, PREC, DIAG, PAIRS>::CT> c,
+                                                   double* __restrict__ partials, int rows) {
+  using Col = Column<MODEL, PREC, DIAG, PAIRS>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = PAIRS ? 2 * t : t;
+  const int y0 = blockIdx.y * blockDim.y * rows + threadIdx.y;
+  DiagAcc<typename Col::CT> acc;
+  Col::run(src, dst, g, c, x, y0, (int)blockDim.y, rows, acc);
+  if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
 }
 
 // ------------------------------------------------------------------ diagnostics of the state
@@ -379,39 +382,36 @@ template <int PREC> struct Launch {
   using S = typename Form<PREC>::S;
   using T = typename Form<PREC>::T;
 
-  template <int MODEL>
-  static cudaError_t step_m(const StepArgs& a, const Coef<T>& c, cudaStream_t st) {
+  template <int MODEL, bool PAIRS>
+  static cudaError_t step_p(const StepArgs& a, cudaStream_t st) {
+    using CT = typename Column<MODEL, PREC, false, PAIRS>::CT;
+    const Coef<CT> c = make_coef<CT>(a.theta, a.tau, a.rho_ref);
     const dim3 block(a.cfg.bx, a.cfg.by);
     const dim3 grid = step_grid(a.g, a.cfg, PREC);
-    if constexpr (PREC != 0) {
-      if (uses_pairs(PREC, a.g)) {
-        const Coef<f32x2> c2 = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
-        if (a.diag)
-          step_pair_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c2,
-                                                                       a.partials, a.cfg.rows);
-        else
-          step_pair_kernel<MODEL, PREC, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c2,
-                                                                        a.partials, a.cfg.rows);
-        return cudaGetLastError();
-      }
-    }
     if (a.diag)
-      step_kernel<MODEL, PREC, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
-                                                              a.cfg.rows);
+      step_kernel<MODEL, PREC, true, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                                     a.cfg.rows);
     else
-      step_kernel<MODEL, PREC, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
-                                                               a.cfg.rows);
+      step_kernel<MODEL, PREC, false, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                                      a.cfg.rows);
     return cudaGetLastError();
+  }
+
+  template <int MODEL>
+  static cudaError_t step_m(const StepArgs& a, cudaStream_t st) {
+    if constexpr (PREC != 0) {
+      if (uses_pairs(PREC, a.g)) return step_p<MODEL, true>(a, st);
+    }
+    return step_p<MODEL, false>(a, st);
   }
 
   static cudaError_t step(const StepArgs& a, cudaStream_t st) {
     if (!valid_cfg(a.cfg)) return cudaErrorInvalidConfiguration;
-    const Coef<T> c = make_coef<T>(a.theta, a.tau, a.rho_ref);
     switch (a.model) {
-      case 0: return step_m<0>(a, c, st);
-      case 1: return step_m<1>(a, c, st);
-      case 2: return step_m<2>(a, c, st);
-      case 3: return step_m<3>(a, c, st);
+      case 0: return step_m<0>(a, st);
+      case 1: return step_m<1>(a, st);
+      case 2: return step_m<2>(a, st);
+      case 3: return step_m<3>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }

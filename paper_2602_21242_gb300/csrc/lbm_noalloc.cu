@@ -68,7 +68,7 @@ template <int MODEL>
 cudaError_t launch(const olbm::Geometry& g, const olbm::Coef<double>& c, const double* src, double* dst,
                    double* partials, const olbm::LaunchCfg& k, cudaStream_t st) {
   const dim3 grid = olbm::step_grid(g, k, 0), block(k.bx, k.by);
-  olbm::step_kernel<MODEL, 0, true><<<grid, block, 0, st>>>(src, dst, g, c, partials, k.rows);
+  olbm::step_kernel<MODEL, 0, true, false><<<grid, block, 0, st>>>(src, dst, g, c, partials, k.rows);
   return cudaGetLastError();
 }
 
