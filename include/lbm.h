@@ -180,6 +180,60 @@ int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const 
 int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows);
 int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent doubly periodic lattices of uneven size,
+ * each with its own theta and tau, sharing one collision model and storage
+ * form, advanced together (Eq. 1 per domain). Domain k's fields are packed
+ * one after another (domain 0 first), each row-major [y][x] with nx[k] * ny[k]
+ * doubles. The ABI conventions above apply.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+enum lbm_batch_mode {
+  LBM_BATCH_GRAPH = 0,      /* one tile-kernel launch per step, n steps captured into one CUDA graph */
+  LBM_BATCH_PERSISTENT = 1  /* one cooperative launch for all n steps, bounded-wait grid barrier per step */
+};
+
+/* Create n >= 1 domains (arrays of length n). Errors: LBM_EINVAL for a domain
+ * outside the lbm_create ranges; LBM_ENOMEM; LBM_ECUDA. Message: lbm_last_error(NULL). */
+int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, const double* tau,
+                     int model, int prec, void* stream, lbm_batch** out);
+int lbm_batch_destroy(lbm_batch* b);
+
+/* Tile shape: blocks of bx x by threads (bx a multiple of 32, bx * by <= 512) updating
+ * tiles of bx (node pairs: 2 bx) columns x by * rows rows. Rebuilds the tile list. */
+int lbm_batch_set_launch(lbm_batch* b, int bx, int by, int rows);
+int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* ntiles);
+int lbm_batch_set_mode(lbm_batch* b, int mode);  /* enum lbm_batch_mode; default LBM_BATCH_GRAPH */
+/* Fused per-domain diagnostics every M steps in LBM_BATCH_GRAPH mode (0 = off). */
+int lbm_batch_set_diagnostics_interval(lbm_batch* b, int every);
+
+/* f(x, 0) = f^eq(rho0, u0) (Eq. 10) for every domain, from packed device fields. */
+int lbm_batch_init(lbm_batch* b, const double* d_rho, const double* d_ux, const double* d_uy);
+/* Domain k's state f(x, t) to / from a device array of 9 * nx[k] * ny[k] doubles ([i][y][x]). */
+int lbm_batch_get_state(lbm_batch* b, int k, double* d_f);
+int lbm_batch_set_state(lbm_batch* b, int k, const double* d_f);
+/* Moments of every domain into packed device fields (asynchronous). */
+int lbm_batch_moments(lbm_batch* b, double* d_rho, double* d_ux, double* d_uy);
+
+/*
+ * Advance every domain by n steps. LBM_BATCH_GRAPH: asynchronous; the n launches
+ * are captured once into a graph (re-captured when n, the buffer parity or the
+ * diagnostics phase changes) and replayed. LBM_BATCH_PERSISTENT: one cooperative
+ * launch; synchronises and returns LBM_ETIMEOUT if a grid barrier waited longer
+ * than about a second (the state is then undefined).
+ */
+int lbm_batch_step(lbm_batch* b, int n);
+/* Latest fused diagnostics, h_out[5 * k + j] as lbm_diagnostics for domain k; *h_time
+ * the time they describe (-1 if none). Synchronises; LBM_ENONFINITE if any pass met one. */
+int lbm_batch_step_diagnostics(lbm_batch* b, double* h_out, long long* h_time);
+/* Diagnostics of every domain's current state into h_out[5 * n] (host). Synchronises. */
+int lbm_batch_diagnostics(lbm_batch* b, double* h_out);
+/* Total nodes, bytes of the population arena, current time. */
+int lbm_batch_info(const lbm_batch* b, long long* total_nodes, long long* arena_bytes, long long* t);
+int lbm_batch_sync(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Wait for the lattice's stream; report a pending CUDA error (LBM_ECUDA) or a
  * non-finite population seen by a fused diagnostics pass (LBM_ENONFINITE). */
 int lbm_sync(lbm_ctx* ctx);

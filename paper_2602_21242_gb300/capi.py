@@ -50,7 +50,24 @@ _SIGNATURES = {
     "lbm_step_noalloc": ([_i, _i, _d, _d, _i, _p, _p, _p, _p], _i),
     "lbm_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "lbm_last_error": ([_p], ctypes.c_char_p),
+    "lbm_batch_create": ([_i, _p, _p, _p, _p, _i, _i, _p, ctypes.POINTER(_p)], _i),
+    "lbm_batch_destroy": ([_p], _i),
+    "lbm_batch_set_launch": ([_p, _i, _i, _i], _i),
+    "lbm_batch_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "lbm_batch_set_mode": ([_p, _i], _i),
+    "lbm_batch_set_diagnostics_interval": ([_p, _i], _i),
+    "lbm_batch_init": ([_p, _p, _p, _p], _i),
+    "lbm_batch_get_state": ([_p, _i, _p], _i),
+    "lbm_batch_set_state": ([_p, _i, _p], _i),
+    "lbm_batch_moments": ([_p, _p, _p, _p], _i),
+    "lbm_batch_step": ([_p, _i], _i),
+    "lbm_batch_step_diagnostics": ([_p, _pd, _pll], _i),
+    "lbm_batch_diagnostics": ([_p, _pd], _i),
+    "lbm_batch_info": ([_p, _pll, _pll, _pll], _i),
+    "lbm_batch_sync": ([_p], _i),
+    "lbm_batch_last_error": ([_p], ctypes.c_char_p),
 }
+LBM_BATCH_GRAPH, LBM_BATCH_PERSISTENT = 0, 1
 
 
 class LBMError(RuntimeError):
@@ -211,3 +228,96 @@ def lbm_step_noalloc(nx: int, ny: int, theta: float, tau: float, model: int, d_s
                      d_diag5: int, stream: int = 0) -> None:
     """One fused FP64 step + diagnostics on caller buffers, with no device allocation."""
     check(load().lbm_step_noalloc(nx, ny, theta, tau, model, d_src, d_dst, d_diag5, stream or None))
+
+
+# ---------------------------------------------------------------- batched form
+
+def batch_last_error(b) -> str:
+    msg = load().lbm_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def bcheck(status: int, b=None) -> int:
+    if status != LBM_OK:
+        raise LBMError(status, batch_last_error(b) if b else last_error(None))
+    return status
+
+
+def lbm_batch_create(nx, ny, theta, tau, model: int, prec: int, stream: int = 0):
+    n = len(nx)
+    a_nx = (ctypes.c_int * n)(*[int(v) for v in nx])
+    a_ny = (ctypes.c_int * n)(*[int(v) for v in ny])
+    a_th = (ctypes.c_double * n)(*[float(v) for v in theta])
+    a_tau = (ctypes.c_double * n)(*[float(v) for v in tau])
+    b = _p()
+    bcheck(load().lbm_batch_create(n, a_nx, a_ny, a_th, a_tau, model, prec, stream or None, ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_destroy(b) -> None:
+    bcheck(load().lbm_batch_destroy(b))
+
+
+def lbm_batch_set_launch(b, bx: int, by: int, rows: int) -> None:
+    bcheck(load().lbm_batch_set_launch(b, bx, by, rows), b)
+
+
+def lbm_batch_get_launch(b):
+    v = [_i() for _ in range(4)]
+    bcheck(load().lbm_batch_get_launch(b, *[ctypes.byref(x) for x in v]), b)
+    return tuple(x.value for x in v)
+
+
+def lbm_batch_set_mode(b, mode: int) -> None:
+    bcheck(load().lbm_batch_set_mode(b, mode), b)
+
+
+def lbm_batch_set_diagnostics_interval(b, every: int) -> None:
+    bcheck(load().lbm_batch_set_diagnostics_interval(b, every), b)
+
+
+def lbm_batch_init(b, d_rho: int, d_ux: int, d_uy: int) -> None:
+    bcheck(load().lbm_batch_init(b, d_rho, d_ux, d_uy), b)
+
+
+def lbm_batch_get_state(b, k: int, d_f: int) -> None:
+    bcheck(load().lbm_batch_get_state(b, k, d_f), b)
+
+
+def lbm_batch_set_state(b, k: int, d_f: int) -> None:
+    bcheck(load().lbm_batch_set_state(b, k, d_f), b)
+
+
+def lbm_batch_moments(b, d_rho: int, d_ux: int, d_uy: int) -> None:
+    bcheck(load().lbm_batch_moments(b, d_rho, d_ux, d_uy), b)
+
+
+def lbm_batch_step(b, n: int) -> None:
+    bcheck(load().lbm_batch_step(b, n), b)
+
+
+def lbm_batch_step_diagnostics(b, n_domains: int, raise_nonfinite: bool = True):
+    out = (ctypes.c_double * (5 * n_domains))()
+    t = _ll()
+    s = load().lbm_batch_step_diagnostics(b, out, ctypes.byref(t))
+    if s != LBM_OK and (raise_nonfinite or s != LBM_ENONFINITE):
+        bcheck(s, b)
+    return [list(out[5 * k:5 * k + 5]) for k in range(n_domains)], t.value, s
+
+
+def lbm_batch_diagnostics(b, n_domains: int, raise_nonfinite: bool = True):
+    out = (ctypes.c_double * (5 * n_domains))()
+    s = load().lbm_batch_diagnostics(b, out)
+    if s != LBM_OK and (raise_nonfinite or s != LBM_ENONFINITE):
+        bcheck(s, b)
+    return [list(out[5 * k:5 * k + 5]) for k in range(n_domains)], s
+
+
+def lbm_batch_info(b):
+    v = [_ll() for _ in range(3)]
+    bcheck(load().lbm_batch_info(b, *[ctypes.byref(x) for x in v]), b)
+    return tuple(x.value for x in v)
+
+
+def lbm_batch_sync(b) -> None:
+    bcheck(load().lbm_batch_sync(b), b)

@@ -102,6 +102,24 @@ __device__ __forceinline__ f32x2 ld_two(const float* p0, const float* p1) {
 __device__ __forceinline__ f32x2 ld_two(const __half* p0, const __half* p1) {
   return f32x2(make_float2(__half2float(__ldg(p0)), __half2float(__ldg(p1))));
 }
+// L2-coherent variants (ld.global.cg) for kernels that read data written by
+// other blocks of the same launch (the persistent batched kernel).
+__device__ __forceinline__ double ld_cg(const double* p, double) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p, float) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const __half* p, float) {
+  return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ f32x2 ld_pair_cg(const float* p) { return f32x2(__ldcg(reinterpret_cast<const float2*>(p))); }
+__device__ __forceinline__ f32x2 ld_pair_cg(const __half* p) {
+  const unsigned u = __ldcg(reinterpret_cast<const unsigned*>(p));
+  return f32x2(__half22float2(*reinterpret_cast<const __half2*>(&u)));
+}
+__device__ __forceinline__ f32x2 ld_two_cg(const float* p0, const float* p1) {
+  return f32x2(make_float2(__ldcg(p0), __ldcg(p1)));
+}
+__device__ __forceinline__ f32x2 ld_two_cg(const __half* p0, const __half* p1) {
+  return f32x2(make_float2(ld_cg(p0, 0.0f), ld_cg(p1, 0.0f)));
+}
 __device__ __forceinline__ void st_pair(float* p, f32x2 v) { *reinterpret_cast<float2*>(p) = v.v; }
 __device__ __forceinline__ void st_pair(__half* p, f32x2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
 
@@ -161,8 +179,9 @@ template <typename CT> __device__ __forceinline__ void block_diag_acc(DiagAcc<CT
 // arithmetic, so each thread keeps two rows of loads in flight. With PAIRS
 // (shifted forms, even nx, x even) the nodes x and x + 1 are updated together
 // on packed f32x2 values; planes with c_ix = 0 are read as aligned 2-element
-// vectors, the others element by element.
-template <int MODEL, int PREC, bool DIAG, bool PAIRS> struct Column {
+// vectors, the others element by element. With CG the loads bypass L1 (for
+// data written earlier in the same launch by other blocks).
+template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Column {
   using S = typename Form<PREC>::S;
   using CT = typename std::conditional<PAIRS, f32x2, typename Form<PREC>::T>::type;
 
@@ -175,26 +194,29 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS> struct Column {
     const S* pp = src + (long long)yp * g.pitch;
     if constexpr (PAIRS) {
       // xm = x - 1, xp = x + 2 (periodic); the pair's second node is x + 1
-      f[0] = ld_pair(p0 + x);
-      f[1] = ld_two(p0 + 1 * g.plane + xm, p0 + 1 * g.plane + x);
-      f[2] = ld_pair(pm + 2 * g.plane + x);
-      f[3] = ld_two(p0 + 3 * g.plane + x + 1, p0 + 3 * g.plane + xp);
-      f[4] = ld_pair(pp + 4 * g.plane + x);
-      f[5] = ld_two(pm + 5 * g.plane + xm, pm + 5 * g.plane + x);
-      f[6] = ld_two(pm + 6 * g.plane + x + 1, pm + 6 * g.plane + xp);
-      f[7] = ld_two(pp + 7 * g.plane + x + 1, pp + 7 * g.plane + xp);
-      f[8] = ld_two(pp + 8 * g.plane + xm, pp + 8 * g.plane + x);
+      auto P = [](const S* q) { return CG ? ld_pair_cg(q) : ld_pair(q); };
+      auto T2 = [](const S* q0, const S* q1) { return CG ? ld_two_cg(q0, q1) : ld_two(q0, q1); };
+      f[0] = P(p0 + x);
+      f[1] = T2(p0 + 1 * g.plane + xm, p0 + 1 * g.plane + x);
+      f[2] = P(pm + 2 * g.plane + x);
+      f[3] = T2(p0 + 3 * g.plane + x + 1, p0 + 3 * g.plane + xp);
+      f[4] = P(pp + 4 * g.plane + x);
+      f[5] = T2(pm + 5 * g.plane + xm, pm + 5 * g.plane + x);
+      f[6] = T2(pm + 6 * g.plane + x + 1, pm + 6 * g.plane + xp);
+      f[7] = T2(pp + 7 * g.plane + x + 1, pp + 7 * g.plane + xp);
+      f[8] = T2(pp + 8 * g.plane + xm, pp + 8 * g.plane + x);
     } else {
       // xm = x - 1, xp = x + 1 (periodic)
-      f[0] = ld_t(p0 + x, CT());
-      f[1] = ld_t(p0 + 1 * g.plane + xm, CT());
-      f[2] = ld_t(pm + 2 * g.plane + x, CT());
-      f[3] = ld_t(p0 + 3 * g.plane + xp, CT());
-      f[4] = ld_t(pp + 4 * g.plane + x, CT());
-      f[5] = ld_t(pm + 5 * g.plane + xm, CT());
-      f[6] = ld_t(pm + 6 * g.plane + xp, CT());
-      f[7] = ld_t(pp + 7 * g.plane + xp, CT());
-      f[8] = ld_t(pp + 8 * g.plane + xm, CT());
+      auto L = [](const S* q) { return CG ? ld_cg(q, CT()) : ld_t(q, CT()); };
+      f[0] = L(p0 + x);
+      f[1] = L(p0 + 1 * g.plane + xm);
+      f[2] = L(pm + 2 * g.plane + x);
+      f[3] = L(p0 + 3 * g.plane + xp);
+      f[4] = L(pp + 4 * g.plane + x);
+      f[5] = L(pm + 5 * g.plane + xm);
+      f[6] = L(pm + 6 * g.plane + xp);
+      f[7] = L(pp + 7 * g.plane + xp);
+      f[8] = L(pp + 8 * g.plane + xm);
     }
   }
 

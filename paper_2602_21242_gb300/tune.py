@@ -1,0 +1,129 @@
+"""Autotuner for the launch shape of the step kernels.
+
+For a lattice (or a batch) it times candidate shapes (threads bx x by, rows per
+thread) with CUDA events on the object's own stream, keeps the fastest, and
+caches it in a JSON file keyed by GPU name, kind, size class, storage form and
+collision model, so the measurement runs once per configuration class.
+
+Cache file: $OLBM_TUNE_CACHE, else ~/.cache/olbm/tune.json.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+import threading
+
+import torch
+
+from . import capi
+
+_lock = threading.Lock()
+
+LATTICE_CANDIDATES = [(bx, by, rows) for (bx, by), rows in itertools.product(
+    [(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)], [4, 8, 16, 32])]
+BATCH_CANDIDATES = [(bx, by, rows) for (bx, by), rows in itertools.product(
+    [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)], [2, 4, 8, 16])]
+
+
+def cache_path() -> str:
+    return os.environ.get("OLBM_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "olbm", "tune.json")
+
+
+def _load_cache(path: str) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path: str, key: str, value) -> None:
+    with _lock:
+        data = _load_cache(path)
+        data[key] = value
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def _key(kind: str, nodes: int, prec: int, model: int, extra: str = "") -> str:
+    gpu = torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+    size_class = int(round(math.log2(max(nodes, 1))))
+    return f"{gpu}|{kind}|2^{size_class}{extra}|prec{prec}|model{model}"
+
+
+def _time(step, sync, stream, steps: int) -> float:
+    step(steps)  # warm-up with the same count (a batch captures its graph here)
+    sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(steps)
+    e1.record(stream)
+    sync()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, path: str | None = None):
+    """Pick and apply the fastest launch shape for `lat` (a Lattice). Timing runs on a
+    temporary lattice of the same size, storage and model started at rest, so `lat`'s
+    state is untouched. Returns ((bx, by, rows), ms_per_step or None if cached)."""
+    from .lattice import Lattice
+
+    path = path or cache_path()
+    key = _key("lattice", lat.nx * lat.ny, lat.prec, lat.model)
+    if use_cache:
+        hit = _load_cache(path).get(key)
+        if hit:
+            capi.lbm_set_launch(lat.ctx, *hit["shape"])
+            return tuple(hit["shape"]), None
+    best = None
+    with Lattice(lat.nx, lat.ny, lat.theta, lat.tau, lat.model, lat.prec, device=lat.device,
+                 stream=lat.stream) as tmp:
+        ones = torch.ones((lat.ny, lat.nx), dtype=torch.float64, device=lat.device)
+        zeros = torch.zeros_like(ones)
+        tmp.init(ones, zeros, zeros)
+        tmp.set_diagnostics_interval(1)
+        for shape in candidates or LATTICE_CANDIDATES:
+            try:
+                capi.lbm_set_launch(tmp.ctx, *shape)
+            except capi.LBMError:
+                continue
+            ms = _time(tmp.step, tmp.sync, tmp.stream, steps)
+            if best is None or ms < best[1]:
+                best = (shape, ms)
+    capi.lbm_set_launch(lat.ctx, *best[0])
+    _store(path, key, {"shape": list(best[0]), "ms_per_step": best[1]})
+    return tuple(best[0]), best[1]
+
+
+def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, path: str | None = None):
+    """Pick and apply the fastest tile shape for `batch` (a Batch). The timing steps the
+    batch itself from a rest state (rho = 1, u = 0): call it before Batch.init.
+    Returns ((bx, by, rows), ms_per_step or None if cached)."""
+    path = path or cache_path()
+    key = _key("batch", batch.total_nodes, batch.prec, batch.model, f"|n{batch.n}")
+    if use_cache:
+        hit = _load_cache(path).get(key)
+        if hit:
+            batch.set_launch(*hit["shape"])
+            return tuple(hit["shape"]), None
+    rest = [torch.ones((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
+    zero = [torch.zeros((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
+    best = None
+    for shape in candidates or BATCH_CANDIDATES:
+        try:
+            batch.set_launch(*shape)
+        except capi.LBMError:
+            continue
+        batch.init(rest, zero, zero)
+        ms = _time(batch.step, batch.sync, batch.stream, steps)
+        if best is None or ms < best[1]:
+            best = (shape, ms)
+    batch.set_launch(*best[0])
+    batch.init(rest, zero, zero)
+    _store(path, key, {"shape": list(best[0]), "ms_per_step": best[1]})
+    return tuple(best[0]), best[1]

@@ -1,0 +1,122 @@
+"""Batched form: independent lattices of uneven size, theta and tau in one launch.
+
+Each domain of a batch must be bit-identical to a single lattice run of the
+same storage form (the per-node arithmetic is shared), in both execution modes,
+and the FP64 batch must match the oracle at 1e-12 per node.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2602_21242_gb300 import capi, flows, tune
+from paper_2602_21242_gb300.batch import Batch
+from paper_2602_21242_gb300.lattice import Lattice
+
+pytestmark = pytest.mark.gpu
+
+DOMAINS = [(37, 23, 0.30, 0.70), (64, 64, 0.25, 0.80), (100, 3, 0.40, 0.60), (1, 5, 1 / 3, 0.90),
+           (48, 31, 0.35, 0.75), (130, 9, 0.28, 0.65)]
+
+
+def states(seed, domains=DOMAINS):
+    return [flows.random_populations(nx, ny, seed=seed + k, spread=0.15) for k, (nx, ny, _, _) in enumerate(domains)]
+
+
+def single_run(f0, nx, ny, theta, tau, model, prec, steps):
+    with Lattice(nx, ny, theta, tau, model, prec) as lat:
+        lat.set_state(torch.from_numpy(f0).cuda())
+        lat.step(steps)
+        return lat.state().cpu().numpy()
+
+
+def make_batch(model, prec, mode, domains=DOMAINS):
+    return Batch([d[0] for d in domains], [d[1] for d in domains], [d[2] for d in domains],
+                 [d[3] for d in domains], model, prec, mode=mode)
+
+
+@pytest.mark.parametrize("mode", ["graph", "persistent"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("model", [0, 3])
+def test_batch_bit_identical_to_single_lattices(model, prec, mode):
+    f0 = states(100 + model)
+    steps = 13
+    with make_batch(model, prec, mode) as b:
+        for k, f in enumerate(f0):
+            b.set_state(k, f)
+        b.step(steps)
+        b.sync()
+        got = [b.state(k).cpu().numpy() for k in range(b.n)]
+    for k, (nx, ny, theta, tau) in enumerate(DOMAINS):
+        want = single_run(f0[k], nx, ny, theta, tau, model, prec, steps)
+        np.testing.assert_array_equal(got[k], want, err_msg=f"domain {k} ({nx}x{ny})")
+
+
+@pytest.mark.parametrize("model", [1, 2, 3])
+def test_batch_f64_oracle_parity(oracle, model):
+    f0 = states(200 + model)
+    with make_batch(model, "f64", "graph") as b:
+        for k, f in enumerate(f0):
+            b.set_state(k, f)
+        b.step(50)
+        for k, (nx, ny, theta, tau) in enumerate(DOMAINS):
+            ref = oracle.run(f0[k], theta, tau, model, 50)
+            got = b.state(k).cpu().numpy()
+            err = np.max(np.abs(got - ref) / np.abs(ref).max(axis=0))
+            assert err <= 1e-12, f"domain {k}: {err:.3e}"
+
+
+def test_batch_graph_recapture_and_parity_changes(oracle):
+    """Odd step counts flip the buffer parity; each call still advances every domain."""
+    f0 = states(300)
+    with make_batch(3, "f64", "graph") as b:
+        for k, f in enumerate(f0):
+            b.set_state(k, f)
+        for n in (3, 5, 3, 0, 1):
+            b.step(n)
+        b.sync()
+        assert capi.lbm_batch_info(b.handle)[2] == 12
+        for k, (nx, ny, theta, tau) in enumerate(DOMAINS):
+            ref = oracle.run(f0[k], theta, tau, 3, 12)
+            np.testing.assert_allclose(b.state(k).cpu().numpy(), ref, rtol=1e-12)
+
+
+def test_batch_init_moments_and_diagnostics(oracle):
+    doms = [(40, 40, 1 / 3, 0.56), (64, 32, 0.3, 0.6), (33, 17, 0.38, 0.7)]
+    rho, ux, uy = zip(*[flows.taylor_green(nx, ny, 0.05, th) for nx, ny, th, _ in doms])
+    with make_batch(3, "f64", "graph", doms) as b:
+        b.init(rho, ux, uy)
+        b.set_diagnostics_interval(4)
+        b.step(9)  # fused passes at t = 0, 4, 8
+        fused, t, status = b.step_diagnostics()
+        now = b.diagnostics()
+        mom = b.moments()
+        for k, (nx, ny, th, tau) in enumerate(doms):
+            f8 = oracle.run(oracle.init(rho[k], ux[k], uy[k], th), th, tau, 3, 8)
+            f9 = oracle.run(f8, th, tau, 3, 1)
+            np.testing.assert_allclose(fused[k], oracle.diagnostics(f8), rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(now[k], oracle.diagnostics(f9), rtol=1e-12, atol=1e-12)
+            for got, want in zip(mom[k], oracle.moments(f9)):
+                np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-12, atol=1e-14)
+    assert t == 8 and status == capi.LBM_OK
+
+
+def test_batch_rejects_bad_domains():
+    with pytest.raises(capi.LBMError) as e:
+        Batch([16, 0], [16, 16], [0.3, 0.3], [0.6, 0.6], "complete", "f32")
+    assert e.value.status == capi.LBM_EINVAL
+    with pytest.raises(capi.LBMError):
+        Batch([16], [16], [0.3], [0.5], "complete", "f32")
+
+
+def test_tuners(tmp_path):
+    path = str(tmp_path / "tune.json")
+    with Lattice(256, 256, 1 / 3, 0.56, "complete", "f32") as lat:
+        shape, ms = tune.tune_lattice(lat, candidates=[(64, 2, 4), (128, 4, 8)], steps=4, path=path)
+        assert shape in [(64, 2, 4), (128, 4, 8)] and ms > 0
+        assert capi.lbm_get_launch(lat.ctx) == shape
+        again, cached = tune.tune_lattice(lat, path=path)
+        assert again == shape and cached is None
+    with make_batch(3, "f32", "graph") as b:
+        shape, ms = tune.tune_batch(b, candidates=[(32, 4, 4), (64, 2, 8)], steps=4, path=path)
+        assert b.launch()[:3] == shape
