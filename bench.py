@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50, help="lattice steps per end-to-end call")
     ap.add_argument("--e2e-calls", type=int, default=3)
+    ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 256-domain batched workload")
     return ap.parse_args()
 
 
@@ -278,9 +279,10 @@ def run_gpu(args):
                       "call": f"lbm_run_host: upload rho0,u0 (pinned) -> init -> {args.e2e_steps} steps with "
                               f"diagnostics -> download rho,u and diagnostics; {args.e2e_calls} calls timed"}
 
-    # ---- per-model / per-precision sweep on the same flow
+    # ---- per-model / per-precision sweep on the same flow, and the batched workload
     if not args.no_forms:
         out["forms"] = forms_sweep(w, fields, dev, stream, peak_hbm)
+        out["forms"].update(batch_sweep(dev, stream, peak_hbm, steps=args.batch_steps))
 
     # ---- CPU baseline (oracle) on rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -344,6 +346,49 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
         dr = float((finals[prec][0] - finals["f64"][0]).abs().max())
         res[f"complete/{prec}"]["error_vs_f64"] = {
             "steps": err_steps, "max_abs_du_over_U": du / w["U"], "max_abs_drho": dr}
+    return res
+
+
+def batch_sweep(dev, stream, peak_hbm, steps=1000):
+    """Batched workload: 256 independent Taylor-Green domains, N ~ U{64..512}, theta ~ U[0.25, 0.4],
+    nu ~ U[0.002, 0.02], u0 ~ U[0.02, 0.1], completely corrected model, FP32 shifted storage, `steps`
+    steps per call; tile shape from the autotuner; graph mode (fused per-domain diagnostics every
+    step) and persistent mode (one cooperative launch, no fused diagnostics)."""
+    import torch
+
+    from paper_2602_21242_gb300 import flows, tune
+    from paper_2602_21242_gb300.batch import Batch
+
+    doms = flows.batch_domains(256)
+    ns = [d.n for d in doms]
+    thetas = [d.theta for d in doms]
+    taus = [d.nu / d.theta + 0.5 for d in doms]
+    fields = [flows.taylor_green(d.n, d.n, d.u0, d.theta) for d in doms]
+    rho, ux, uy = ([f[j] for f in fields] for j in range(3))
+    res = {}
+    with Batch(ns, ns, thetas, taus, "complete", "f32", device=dev, stream=stream) as b:
+        shape, _ = tune.tune_batch(b, steps=10, use_cache=False)
+        nodes = b.total_nodes
+        for mode in ("graph", "persistent"):
+            b.set_mode(mode)
+            b.set_diagnostics_interval(1 if mode == "graph" else 0)
+            b.init(rho, ux, uy)
+            b.step(steps)  # warm-up (graph capture)
+            b.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(steps)
+            e1.record(stream)
+            b.sync()
+            ms = e0.elapsed_time(e1) / steps
+            d = b.diagnostics()
+            mass = sum(x[0] for x in d)
+            res[f"batch256/complete/f32/{mode}"] = {
+                "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
+                "hbm_gbs": round(72 * nodes / (ms * 1e-3) / 1e9, 1),
+                "hbm_frac": round(72 * nodes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
+                "domains": 256, "nodes": nodes, "steps": steps, "tile": list(shape),
+                "fused_diagnostics": mode == "graph", "mass_rel_drift": abs(mass - sum(rho_k.sum() for rho_k in rho)) / mass}
     return res
 
 
