@@ -156,6 +156,26 @@ int lbm_diagnostics(lbm_ctx* ctx, double* h_out5);
 int lbm_get_state(lbm_ctx* ctx, double* d_f);
 int lbm_set_state(lbm_ctx* ctx, const double* d_f);
 
+/*
+ * Reverse-mode derivative (vector-Jacobian product) of n steps of Eq. 1 started
+ * from the guided equilibrium f(x, 0) = f^eq(rho0(x), u0(x)) (Eq. 10), with
+ * respect to the initial fields. Given the cotangents g_rho, g_ux, g_uy of the
+ * final moments (rho, u)(x, n) (device arrays of nx * ny doubles; any may be
+ * NULL = 0), writes the cotangents of (rho0, u0) to g_rho0, g_ux0, g_uy0 (device,
+ * nx * ny doubles; any may be NULL to skip).
+ * Method: a forward pass from d_rho0, d_ux0, d_uy0 (device) storing a checkpoint
+ * every ckpt_every steps, then per segment, last first, a recomputation of its
+ * states and the adjoint steps lambda(t) = J_C(f(t))^T S^T lambda(t + 1), where S^T
+ * reads lambda_i(t + 1) at x + c_i and J_C^T is the hand-derived transposed
+ * Jacobian of the model's collision. FP64 and FP32 storage (the FP32 form's
+ * adjoint runs in FP32); LBM_EINVAL for FP16. Device work memory of
+ * (ceil(n / ckpt_every) + ckpt_every + 2) population buffers is kept by the
+ * lattice. Asynchronous; on return the lattice holds f(x, n) of this run.
+ */
+int lbm_vjp(lbm_ctx* ctx, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+            const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
+            double* g_rho0, double* g_ux0, double* g_uy0);
+
 /* Current time t (steps since lbm_init / lbm_set_state). */
 int lbm_time(const lbm_ctx* ctx, long long* h_t);
 

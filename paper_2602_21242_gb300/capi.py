@@ -46,6 +46,7 @@ _SIGNATURES = {
     "lbm_run_host": ([_p, _p, _p, _p, _i, _p, _p, _p, _pd], _i),
     "lbm_sync": ([_p], _i),
     "lbm_measure_peak": ([_i, _pd], _i),
+    "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "lbm_set_launch": ([_p, _i, _i, _i], _i),
     "lbm_step_noalloc": ([_i, _i, _d, _d, _i, _p, _p, _p, _p], _i),
     "lbm_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
@@ -321,3 +322,10 @@ def lbm_batch_info(b):
 
 def lbm_batch_sync(b) -> None:
     bcheck(load().lbm_batch_sync(b), b)
+
+
+def lbm_vjp(ctx, n: int, ckpt_every: int, d_rho0: int, d_ux0: int, d_uy0: int, g_rho: int = 0, g_ux: int = 0,
+            g_uy: int = 0, g_rho0: int = 0, g_ux0: int = 0, g_uy0: int = 0) -> None:
+    """Cotangents of (rho0, u0) for cotangents of the moments after n steps (device pointers, 0 = NULL)."""
+    check(load().lbm_vjp(ctx, n, ckpt_every, d_rho0, d_ux0, d_uy0, g_rho or None, g_ux or None, g_uy or None,
+                         g_rho0 or None, g_ux0 or None, g_uy0 or None), ctx)

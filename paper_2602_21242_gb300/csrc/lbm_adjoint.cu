@@ -1,0 +1,254 @@
+// lbm_adjoint.cu -- lbm_vjp: reverse-mode derivative of n LBE steps
+// (arXiv 2602.21242, Eq. 1) started from the guided equilibrium (Eq. 10).
+//
+// Forward map: f(0) = f^eq(rho0, u0); f(t + 1) = S C f(t) (C: collision at every
+// node, S: streaming); outputs (rho, u)(x, n) = moments of f(n). Reverse:
+//   lambda(n)_i  = g_rho + (c_ix - u_x) g_ux / rho + (c_iy - u_y) g_uy / rho
+//   lambda(t)(x) = J_C(f(x, t))^T mu(x),  mu_i(x) = lambda_i(t + 1)(x + c_i)   (S^T: a push-read)
+//   g_rho0 = sum_i lambda_i(0) df^eq_i/drho0, g_u0 likewise.
+// States are recomputed in segments of K steps from checkpoints taken every K
+// steps (memory: ceil(n/K) checkpoints + K recomputed states + 2 adjoint fields).
+#include <algorithm>
+#include <cstdio>
+
+#include "lbm.h"
+#include "lbm_adjoint.cuh"
+#include "lbm_ctx.h"
+#include "lbm_kernels.cuh"
+
+namespace olbm {
+
+constexpr int kABX = 32, kABY = 8;
+
+// lambda(n) from the cotangents of the final moments (any may be NULL = 0).
+template <int PREC>
+__global__ void __launch_bounds__(kABX* kABY) adj_seed_kernel(const typename Form<PREC>::S* __restrict__ fbuf,
+                                                              Geometry g, double rho_ref,
+                                                              const double* __restrict__ g_rho,
+                                                              const double* __restrict__ g_ux,
+                                                              const double* __restrict__ g_uy,
+                                                              typename Form<PREC>::T* __restrict__ lam) {
+  using T = typename Form<PREC>::T;
+  const int x = blockIdx.x * kABX + threadIdx.x, y = blockIdx.y * kABY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  long long o[9];
+  pull_offsets(x, y, g, o);
+  double m0 = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double v = to_double(fbuf[i * g.plane + o[i]]);
+    m0 += v;
+    jx += (double)cx_of(i) * v;
+    jy += (double)cy_of(i) * v;
+  }
+  const double rho = rho_ref + m0, ux = jx / rho, uy = jy / rho;
+  const long long n = (long long)y * g.nx + x;
+  const double gr = g_rho ? g_rho[n] : 0.0, gx = g_ux ? g_ux[n] / rho : 0.0, gy = g_uy ? g_uy[n] / rho : 0.0;
+  const long long here = (long long)y * g.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    lam[i * g.plane + here] = (T)(gr + ((double)cx_of(i) - ux) * gx + ((double)cy_of(i) - uy) * gy);
+}
+
+// lambda(t)(x) = J_C(f(x, t))^T mu(x), mu_i(x) = lambda_i(t + 1)(x + c_i).
+template <int MODEL, int PREC>
+__global__ void __launch_bounds__(kABX* kABY) adj_step_kernel(const typename Form<PREC>::S* __restrict__ fbuf,
+                                                              const typename Form<PREC>::T* __restrict__ lam_next,
+                                                              typename Form<PREC>::T* __restrict__ lam, Geometry g,
+                                                              Coef<typename Form<PREC>::T> c) {
+  using T = typename Form<PREC>::T;
+  const int x = blockIdx.x * kABX + threadIdx.x, y = blockIdx.y * kABY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  long long o[9];
+  pull_offsets(x, y, g, o);
+  T f[9], mu[9], out[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = ld_t(fbuf + i * g.plane + o[i], T());
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    int xd = x + cx_of(i), yd = y + cy_of(i);  // x + c_i, periodic
+    xd = xd < 0 ? xd + g.nx : (xd >= g.nx ? xd - g.nx : xd);
+    yd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
+    mu[i] = lam_next[i * g.plane + (long long)yd * g.pitch + xd];
+  }
+  collide_vjp<MODEL, Form<PREC>::kShift, T>(f, mu, c, out);
+  const long long here = (long long)y * g.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) lam[i * g.plane + here] = out[i];
+}
+
+// Cotangents of (rho0, u0) from lambda(0), through f(x, 0) = f^eq(rho0(x), u0(x)).
+template <int PREC>
+__global__ void __launch_bounds__(kABX* kABY) adj_final_kernel(const typename Form<PREC>::T* __restrict__ lam,
+                                                               Geometry g, double theta,
+                                                               const double* __restrict__ rho0,
+                                                               const double* __restrict__ ux0,
+                                                               const double* __restrict__ uy0,
+                                                               double* __restrict__ g_rho0,
+                                                               double* __restrict__ g_ux0,
+                                                               double* __restrict__ g_uy0) {
+  const int x = blockIdx.x * kABX + threadIdx.x, y = blockIdx.y * kABY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long long n = (long long)y * g.nx + x, here = (long long)y * g.pitch + x;
+  const double rho = rho0[n], ux = ux0[n], uy = uy0[n];
+  const double px[3] = {0.5 * (theta + ux * ux - ux), 1.0 - theta - ux * ux, 0.5 * (theta + ux * ux + ux)};
+  const double py[3] = {0.5 * (theta + uy * uy - uy), 1.0 - theta - uy * uy, 0.5 * (theta + uy * uy + uy)};
+  const double dpx[3] = {ux - 0.5, -2.0 * ux, ux + 0.5};
+  const double dpy[3] = {uy - 0.5, -2.0 * uy, uy + 0.5};
+  double gr = 0.0, gx = 0.0, gy = 0.0;
+#pragma unroll
+  for (int a = -1; a <= 1; ++a)
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+      const double l = (double)lam[pop_index(a, b) * g.plane + here];
+      gr += l * px[a + 1] * py[b + 1];
+      gx += l * dpx[a + 1] * py[b + 1];
+      gy += l * px[a + 1] * dpy[b + 1];
+    }
+  if (g_rho0) g_rho0[n] = gr;
+  if (g_ux0) g_ux0[n] = rho * gx;
+  if (g_uy0) g_uy0[n] = rho * gy;
+}
+
+inline dim3 adj_grid(const Geometry& g) { return dim3((g.nx + kABX - 1) / kABX, (g.ny + kABY - 1) / kABY); }
+
+template <int PREC> struct Adjoint {
+  using S = typename Form<PREC>::S;
+  using T = typename Form<PREC>::T;
+
+  static cudaError_t seed(const void* fbuf, const Geometry& g, double rho_ref, const double* gr, const double* gx,
+                          const double* gy, void* lam, cudaStream_t st) {
+    adj_seed_kernel<PREC><<<adj_grid(g), dim3(kABX, kABY), 0, st>>>((const S*)fbuf, g, rho_ref, gr, gx, gy, (T*)lam);
+    return cudaGetLastError();
+  }
+
+  template <int MODEL>
+  static cudaError_t step_m(const void* fbuf, const void* lam_next, void* lam, const Geometry& g, const Coef<T>& c,
+                            cudaStream_t st) {
+    adj_step_kernel<MODEL, PREC><<<adj_grid(g), dim3(kABX, kABY), 0, st>>>((const S*)fbuf, (const T*)lam_next,
+                                                                          (T*)lam, g, c);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step(int model, const void* fbuf, const void* lam_next, void* lam, const Geometry& g,
+                          double theta, double tau, double rho_ref, cudaStream_t st) {
+    const Coef<T> c = make_coef<T>(theta, tau, rho_ref);
+    switch (model) {
+      case 0: return step_m<0>(fbuf, lam_next, lam, g, c, st);
+      case 1: return step_m<1>(fbuf, lam_next, lam, g, c, st);
+      case 2: return step_m<2>(fbuf, lam_next, lam, g, c, st);
+      default: return step_m<3>(fbuf, lam_next, lam, g, c, st);
+    }
+  }
+
+  static cudaError_t final_(const void* lam, const Geometry& g, double theta, const double* r0, const double* u0,
+                            const double* v0, double* gr, double* gx, double* gy, cudaStream_t st) {
+    adj_final_kernel<PREC><<<adj_grid(g), dim3(kABX, kABY), 0, st>>>((const T*)lam, g, theta, r0, u0, v0, gr, gx,
+                                                                     gy);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace olbm
+
+namespace {
+
+int vfail(lbm_ctx* c, int status, const char* msg, cudaError_t e = cudaSuccess) {
+  if (e != cudaSuccess)
+    snprintf(c->err, sizeof(c->err), "%s: %s", msg, cudaGetErrorString(e));
+  else
+    snprintf(c->err, sizeof(c->err), "%s", msg);
+  return status;
+}
+
+cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
+  olbm::StepArgs a;
+  a.model = c->model;
+  a.diag = false;
+  a.src = src;
+  a.dst = dst;
+  a.g = c->g;
+  a.theta = c->theta;
+  a.tau = c->tau;
+  a.rho_ref = c->rho_ref;
+  a.partials = c->d_partials;
+  a.cfg = c->cfg;
+  return c->prec == LBM_F64 ? olbm::launch_step_f64(a, c->stream) : olbm::launch_step_f32(a, c->stream);
+}
+
+}  // namespace
+
+extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+                       const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
+                       double* g_rho0, double* g_ux0, double* g_uy0) {
+  if (!c) return LBM_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return vfail(c, LBM_EINVAL, "lbm_vjp: the current CUDA device is not the lattice's device");
+  if (n < 0 || ckpt_every < 1) return vfail(c, LBM_EINVAL, "lbm_vjp: need n >= 0 and ckpt_every >= 1");
+  if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp: NULL initial field");
+  if (c->prec == LBM_F16_SHIFT) return vfail(c, LBM_EINVAL, "lbm_vjp: FP64 and FP32 storage only");
+  const int K = std::min(ckpt_every, std::max(n, 1));
+  const int nseg = (n + K - 1) / K;
+  const size_t sb = (size_t)c->state_bytes;  // one state, and one adjoint field in the same layout
+  const size_t need = sb * ((size_t)nseg + (size_t)K + 2);
+  cudaError_t e;
+  if (need > c->vjp_bytes) {
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp sync", e);
+    cudaFree(c->d_vjp);
+    c->d_vjp = nullptr;
+    c->vjp_bytes = 0;
+    if ((e = cudaMalloc(&c->d_vjp, need)) != cudaSuccess) {
+      cudaGetLastError();
+      return vfail(c, LBM_ENOMEM, "lbm_vjp work memory", e);
+    }
+    c->vjp_bytes = need;
+  }
+  char* base = static_cast<char*>(c->d_vjp);
+  auto ckpt = [&](int s) { return base + sb * (size_t)s; };
+  auto ring = [&](int j) { return base + sb * ((size_t)nseg + (size_t)j); };
+  void* lam[2] = {base + sb * ((size_t)nseg + K), base + sb * ((size_t)nseg + K + 1)};
+
+  // forward: init, then n steps with a checkpoint at the start of every segment
+  int s = lbm_init(c, d_rho0, d_ux0, d_uy0);
+  if (s != LBM_OK) return s;
+  for (int seg = 0; seg < nseg; ++seg) {
+    if ((e = cudaMemcpyAsync(ckpt(seg), c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+      return vfail(c, LBM_ECUDA, "lbm_vjp checkpoint", e);
+    const int len = std::min(K, n - seg * K);
+    for (int k = 0; k < len; ++k) {
+      if ((e = fwd_step(c, c->buf[c->cur], c->buf[c->cur ^ 1])) != cudaSuccess)
+        return vfail(c, LBM_ECUDA, "lbm_vjp forward", e);
+      c->cur ^= 1;
+      c->t += 1;
+    }
+  }
+  // seed lambda(n)
+  int li = 0;
+  e = c->prec == LBM_F64 ? olbm::Adjoint<0>::seed(c->buf[c->cur], c->g, c->rho_ref, g_rho, g_ux, g_uy, lam[li], c->stream)
+                         : olbm::Adjoint<1>::seed(c->buf[c->cur], c->g, c->rho_ref, g_rho, g_ux, g_uy, lam[li], c->stream);
+  if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp seed", e);
+  // backward over segments: recompute the segment's states, then reverse them
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int len = std::min(K, n - seg * K);
+    const void* prev = ckpt(seg);
+    for (int j = 1; j < len; ++j) {
+      if ((e = fwd_step(c, prev, ring(j))) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp recompute", e);
+      prev = ring(j);
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      const void* fbuf = j == 0 ? ckpt(seg) : ring(j);
+      e = c->prec == LBM_F64
+              ? olbm::Adjoint<0>::step(c->model, fbuf, lam[li], lam[li ^ 1], c->g, c->theta, c->tau, c->rho_ref, c->stream)
+              : olbm::Adjoint<1>::step(c->model, fbuf, lam[li], lam[li ^ 1], c->g, c->theta, c->tau, c->rho_ref, c->stream);
+      if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp adjoint step", e);
+      li ^= 1;
+    }
+  }
+  // through the equilibrium initialisation
+  e = c->prec == LBM_F64
+          ? olbm::Adjoint<0>::final_(lam[li], c->g, c->theta, d_rho0, d_ux0, d_uy0, g_rho0, g_ux0, g_uy0, c->stream)
+          : olbm::Adjoint<1>::final_(lam[li], c->g, c->theta, d_rho0, d_ux0, d_uy0, g_rho0, g_ux0, g_uy0, c->stream);
+  if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp final", e);
+  return LBM_OK;
+}

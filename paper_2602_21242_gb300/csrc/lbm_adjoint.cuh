@@ -1,0 +1,144 @@
+// lbm_adjoint.cuh -- transposed Jacobian of one collision (Eq. 1a) for the
+// hand-written adjoint of the D2Q9 OReg-GEq step (arXiv 2602.21242).
+//
+// Every model's post-collision populations are a function of five node
+// quantities z = (rho, u_x, u_y, A1, A2) (and, for LBGK, of f itself):
+//   f*_(a,b) = P_x(a) P_y(b) [rho + A1 (C_x(a)^2 - C_y(b)^2) + A2 C_x(a) C_y(b)] + omega' Psi_(a,b)
+//   (OReg models; omega' Psi depends on A1 and u only), and
+//   f*_i = (1 - omega) f_i + omega rho P_x(a) P_y(b)   (LBGK),
+// with u = j / rho, A1 = omega'/(4 theta^2) (D - rho (u_x^2 - u_y^2)),
+// A2 = omega'/theta^2 (Pi_xy - rho u_x u_y), and (rho, j, D, Pi_xy) linear in f
+// (D = sum (c_x^2 - c_y^2) f). Given mu = dL/df*, the reverse sweep forms
+// dL/dz, pushes it through A1, A2 and u = j / rho onto the five moments, and
+// expands lambda_i = dL/df_i = rho~ + c_ix jx~ + c_iy jy~ + (c_ix^2 - c_iy^2) D~
+// + c_ix c_iy Pi~_xy (plus (1 - omega) mu_i for LBGK).
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace olbm {
+
+template <int MODEL, bool SHIFT, typename T>
+__device__ __forceinline__ void collide_vjp(const T (&f)[9], const T (&mu)[9], const Coef<T>& c, T (&lam)[9]) {
+  // ---- forward intermediates, as in collide()
+  const T s13 = f[1] + f[3], d13 = f[1] - f[3];
+  const T s24 = f[2] + f[4], d24 = f[2] - f[4];
+  const T s57 = f[5] + f[7], d57 = f[5] - f[7];
+  const T s68 = f[6] + f[8], d68 = f[6] - f[8];
+  const T m0 = f[0] + (s13 + s24) + (s57 + s68);
+  const T jx = d13 + (d57 - d68);
+  const T jy = d24 + (d57 + d68);
+  const T rho = SHIFT ? c.rho_ref + m0 : m0;
+  const T r = recip(rho);
+  const T ux = jx * r, uy = jy * r;
+  const T ux2 = ux * ux, uy2 = uy * uy;
+  const T hux = T(0.5) * ux, huy = T(0.5) * uy;
+  const T px[3] = {c.half_theta + fma(T(0.5), ux2, -hux), c.one_m_theta - ux2, c.half_theta + fma(T(0.5), ux2, hux)};
+  const T py[3] = {c.half_theta + fma(T(0.5), uy2, -huy), c.one_m_theta - uy2, c.half_theta + fma(T(0.5), uy2, huy)};
+  // dP/du: P(0) = 1 - theta - u^2 -> -2u; P(+-1) = (theta + u^2 +- u)/2 -> u +- 1/2
+  const T dpx[3] = {ux - T(0.5), T(-2.0) * ux, ux + T(0.5)};
+  const T dpy[3] = {uy - T(0.5), T(-2.0) * uy, uy + T(0.5)};
+
+  T rb = T(0.0), uxb = T(0.0), uyb = T(0.0);  // adjoints of rho (at fixed u), u_x, u_y
+  if constexpr (MODEL == 0) {
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const T w = mu[pop_index(a, b)];
+        rb = fma(w, px[a + 1] * py[b + 1], rb);
+        uxb = fma(w, dpx[a + 1] * py[b + 1], uxb);
+        uyb = fma(w, px[a + 1] * dpy[b + 1], uyb);
+      }
+    rb = c.omega * rb;
+    uxb = c.omega * rho * uxb;
+    uyb = c.omega * rho * uyb;
+    const T jxb = uxb * r, jyb = uyb * r;
+    rb = rb - (uxb * ux + uyb * uy) * r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      lam[i] = fma(c.one_m_omega, mu[i], rb + T((double)cx_of(i)) * jxb + T((double)cy_of(i)) * jyb);
+  } else {
+    const T Dxy = s13 - s24;
+    const T Pxy = s57 - s68;
+    const T A1 = c.k1 * fma(-rho, ux2 - uy2, Dxy);
+    const T A2 = c.k2 * fma(-jx, uy, Pxy);
+    const T cxm[3] = {T(-1.0) - ux, -ux, T(1.0) - ux};
+    const T cym[3] = {T(-1.0) - uy, -uy, T(1.0) - uy};
+    T A1b = T(0.0), A2b = T(0.0);
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const T w = mu[pop_index(a, b)];
+        const T cx = cxm[a + 1], cy = cym[b + 1];
+        const T Q = px[a + 1] * py[b + 1];
+        const T dc2 = cx * cx - cy * cy;
+        const T S = fma(A1, dc2, fma(A2, cx * cy, rho));
+        const T wQ = w * Q;
+        rb = rb + wQ;
+        A1b = fma(wQ, dc2, A1b);
+        A2b = fma(wQ, cx * cy, A2b);
+        // dS/du_x = -2 A1 C_x - A2 C_y; dS/du_y = 2 A1 C_y - A2 C_x
+        uxb = fma(w * py[b + 1], fma(dpx[a + 1], S, -px[a + 1] * fma(T(2.0) * A1, cx, A2 * cy)), uxb);
+        uyb = fma(w * px[a + 1], fma(dpy[b + 1], S, py[b + 1] * fma(T(2.0) * A1, cy, -(A2 * cx))), uyb);
+      }
+    if constexpr (MODEL == 2) {
+      // Psi^P: omega' Psi_1,3 = -+ psi'_x / 2, omega' Psi_2,4 = -+ psi'_y / 2,
+      // psi'_x = A1 u_x (c3 - u_x^2), psi'_y = -A1 u_y (c3 - u_y^2)
+      const T Mx = T(-0.5) * (mu[1] - mu[3]);
+      const T My = T(-0.5) * (mu[2] - mu[4]);
+      A1b = A1b + Mx * ux * (c.c3 - ux2) - My * uy * (c.c3 - uy2);
+      uxb = fma(Mx * A1, c.c3 - T(3.0) * ux2, uxb);
+      uyb = uyb - My * A1 * (c.c3 - T(3.0) * uy2);
+    } else if constexpr (MODEL == 3) {
+      // Psi^C through h = omega' pref / 2 = mq A1 (mu_xx' + mu_yy'), the halved
+      // Pi~ terms hPxx = -h Fx, hPyy = h Fy, qPxy = h G / 2 and hps = psi' / 2.
+      const T muxx = (c.theta - ux2) * px[1];
+      const T muyy = (c.theta - uy2) * py[1];
+      const T h = c.mq_inv2t2 * A1 * (muxx + muyy);
+      const T Fx = fma(ux2, ux2 - T(1.0), c.tt), Fy = fma(uy2, uy2 - T(1.0), c.tt);
+      const T G = ux * uy * (ux2 - uy2);
+      const T Sd = (mu[5] + mu[7]) + (mu[6] + mu[8]);
+      const T hPyyb = mu[1] + mu[3] - T(0.5) * Sd;
+      const T hPxxb = mu[2] + mu[4] - T(0.5) * Sd;
+      const T qPxyb = (mu[6] + mu[8]) - (mu[5] + mu[7]);
+      const T wpsxb = T(0.5) * (mu[3] - mu[1]);
+      const T wpsyb = T(0.5) * (mu[4] - mu[2]);
+      // psi'_x = A1 u_x (c3 - u_x^2), psi'_y = -A1 u_y (c3 - u_y^2)
+      A1b = A1b + wpsxb * ux * (c.c3 - ux2) - wpsyb * uy * (c.c3 - uy2);
+      uxb = fma(wpsxb * A1, c.c3 - T(3.0) * ux2, uxb);
+      uyb = uyb - wpsyb * A1 * (c.c3 - T(3.0) * uy2);
+      // through Fx, Fy, G at fixed h
+      const T dFx = T(2.0) * ux * fma(T(2.0), ux2, T(-1.0));
+      const T dFy = T(2.0) * uy * fma(T(2.0), uy2, T(-1.0));
+      const T dGx = uy * fma(T(3.0), ux2, -uy2);
+      const T dGy = ux * fma(T(-3.0), uy2, ux2);
+      uxb = uxb + h * (T(0.5) * qPxyb * dGx - hPxxb * dFx);
+      uyb = uyb + h * (hPyyb * dFy + T(0.5) * qPxyb * dGy);
+      // through h = mq A1 (mu_xx' + mu_yy'), d mu_aa'/du_a = -2 u_a (1 - 2 u_a^2)
+      const T hb = hPyyb * Fy - hPxxb * Fx + T(0.5) * qPxyb * G;
+      A1b = fma(hb * c.mq_inv2t2, muxx + muyy, A1b);
+      const T hA = hb * c.mq_inv2t2 * A1;
+      uxb = fma(hA * T(-2.0) * ux, fma(T(-2.0), ux2, T(1.0)), uxb);
+      uyb = fma(hA * T(-2.0) * uy, fma(T(-2.0), uy2, T(1.0)), uyb);
+    }
+    // through A1 = k1 (D - rho (u_x^2 - u_y^2)) and A2 = k2 (Pi_xy - rho u_x u_y)
+    const T Db = c.k1 * A1b;
+    const T Pb = c.k2 * A2b;
+    rb = rb - c.k1 * (ux2 - uy2) * A1b - c.k2 * ux * uy * A2b;
+    uxb = uxb - T(2.0) * c.k1 * rho * ux * A1b - c.k2 * rho * uy * A2b;
+    uyb = uyb + T(2.0) * c.k1 * rho * uy * A1b - c.k2 * rho * ux * A2b;
+    // through u = j / rho
+    const T jxb = uxb * r, jyb = uyb * r;
+    rb = rb - (uxb * ux + uyb * uy) * r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int cx = cx_of(i), cy = cy_of(i);
+      lam[i] = rb + T((double)cx) * jxb + T((double)cy) * jyb + T((double)(cx * cx - cy * cy)) * Db +
+               T((double)(cx * cy)) * Pb;
+    }
+  }
+}
+
+}  // namespace olbm

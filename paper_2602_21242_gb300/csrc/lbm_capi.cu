@@ -13,32 +13,8 @@
 #include <new>
 
 #include "lbm.h"
+#include "lbm_ctx.h"
 #include "lbm_launch.h"
-
-struct lbm_ctx {
-  int device = 0;
-  int nx = 0, ny = 0, model = 0, prec = 0;
-  double theta = 0, tau = 0, rho_ref = 0;
-  olbm::Geometry g{};
-  long long state_bytes = 0;
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;  // buffer holding the current state
-  bool own_buffers = true;
-  bool initialised = false;
-  cudaStream_t stream = nullptr;
-  olbm::LaunchCfg cfg{};
-  double* d_partials = nullptr;
-  long long nparts = 0;      // partials the step kernel writes under cfg
-  long long parts_cap = 0;   // partials allocated
-  double* d_diag = nullptr;      // [6] latest fused diagnostics (out5 + time)
-  double* d_diag_now = nullptr;  // [6] scratch of lbm_diagnostics
-  unsigned long long* d_sticky = nullptr;
-  int diag_every = 0;
-  long long t = 0;
-  long long last_diag_t = -1;
-  double* d_stage = nullptr;  // lbm_run_host staging, 6 * nodes doubles
-  char err[320] = {0};
-};
 
 namespace {
 
@@ -128,6 +104,7 @@ void free_ctx(lbm_ctx* c) {
   cudaFree(c->d_diag_now);
   cudaFree(c->d_sticky);
   cudaFree(c->d_stage);
+  cudaFree(c->d_vjp);
   delete c;
 }
 

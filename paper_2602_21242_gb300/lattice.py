@@ -130,3 +130,37 @@ class Lattice:
     def diagnostics(self, raise_nonfinite: bool = True):
         with torch.cuda.device(self.device):
             return capi.lbm_diagnostics(self._ctx, raise_nonfinite)[0]
+
+
+class _Run(torch.autograd.Function):
+    """(rho0, u0) -> (rho, u) after n steps; backward through lbm_vjp (hand-written adjoint)."""
+
+    @staticmethod
+    def forward(fctx, rho0, ux0, uy0, lattice, n, ckpt_every):
+        shape = (lattice.ny, lattice.nx)
+        r0, u0, v0 = (_dev_f64(t.detach(), shape, nm) for t, nm in ((rho0, "rho0"), (ux0, "ux0"), (uy0, "uy0")))
+        lattice.init(r0, u0, v0)
+        lattice.step(n)
+        rho, ux, uy = lattice.moments()
+        fctx.save_for_backward(r0, u0, v0)
+        fctx.lattice, fctx.n, fctx.k = lattice, n, ckpt_every
+        return rho.clone(), ux.clone(), uy.clone()
+
+    @staticmethod
+    def backward(fctx, g_rho, g_ux, g_uy):
+        r0, u0, v0 = fctx.saved_tensors
+        lat = fctx.lattice
+        grads = [torch.empty_like(r0) for _ in range(3)]
+        gs = [g.contiguous().to(torch.float64) if g is not None else None for g in (g_rho, g_ux, g_uy)]
+        with torch.cuda.device(lat.device):
+            capi.lbm_vjp(lat.ctx, fctx.n, fctx.k, r0.data_ptr(), u0.data_ptr(), v0.data_ptr(),
+                         *[g.data_ptr() if g is not None else 0 for g in gs],
+                         *[g.data_ptr() for g in grads])
+            lat.stream.synchronize()
+        return grads[0], grads[1], grads[2], None, None, None
+
+
+def run(lattice: Lattice, rho0, ux0, uy0, n: int, ckpt_every: int = 50):
+    """Differentiable run: returns (rho, u_x, u_y) after n steps from f^eq(rho0, u0); gradients
+    with respect to rho0, ux0, uy0 come from the library's adjoint (lbm_vjp)."""
+    return _Run.apply(rho0, ux0, uy0, lattice, int(n), int(ckpt_every))

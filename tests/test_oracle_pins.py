@@ -399,3 +399,28 @@ def test_complex_step_matches_finite_difference(oracle):
             np.testing.assert_allclose(d_cs, d_fd, rtol=1e-6, atol=1e-9)
             np.testing.assert_allclose(oracle.collide_node_cplx(fz, 0.4, 0.7, model).real,
                                        oracle.collide_node(f, 0.4, 0.7, model), rtol=1e-15)
+
+
+def test_complex_step_run_matches_finite_difference(oracle):
+    """Complex-step directional derivative of init + n steps + moments (the oracle-side reference
+    gradient) agrees with a central difference of the real oracle."""
+    n, theta, tau, steps = 10, 0.37, 0.7, 12
+    g = flows.rng(41)
+    rho, ux, uy = flows.taylor_green(n, n, 0.04, theta)
+    v = [g.standard_normal((n, n)) * s for s in (1e-2, 1e-2, 1e-2)]
+    w = [g.standard_normal((n, n)) for _ in range(3)]
+    for model in (0, 3):
+        def loss(eps, cplx):
+            args = [a + eps * d for a, d in zip((rho, ux, uy), v)]
+            if cplx:
+                f = oracle.run_cplx(oracle.init_cplx(*args, theta), theta, tau, model, steps)
+                m = oracle.moments_cplx(f)
+            else:
+                f = oracle.run(oracle.init(*args, theta), theta, tau, model, steps)
+                m = oracle.moments(f)
+            return sum((wk * mk).sum() for wk, mk in zip(w, m))
+        h = 1e-30
+        d_cs = loss(1j * h, True).imag / h
+        e = 1e-6
+        d_fd = (loss(e, False) - loss(-e, False)) / (2 * e)
+        assert d_cs == pytest.approx(d_fd, rel=1e-6)
