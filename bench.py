@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16"])
     ap.add_argument("--no-forms", action="store_true", help="skip the per-model / per-precision sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--e2e-steps", type=int, default=50, help="lattice steps per end-to-end call")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 256-domain batched workload")
@@ -257,7 +258,7 @@ def run_gpu(args):
                                  "kinetic": diag[3], "nonfinite": diag[4]}}
 
     # ---- end to end through the host-buffer entry point
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         host = [torch.from_numpy(a).pin_memory() for a in (rho, ux, uy)]
         res = [torch.empty((w["ny"], w["nx"]), dtype=torch.float64).pin_memory() for _ in range(3)]
         lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], args.model, args.prec, device=dev, stream=stream)
