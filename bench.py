@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the per-model / per-precision sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="run the 8192^2 shear-layer precision study instead of the benchmark")
+    ap.add_argument("--study-steps", type=int, default=5000)
     ap.add_argument("--e2e-steps", type=int, default=50, help="lattice steps per end-to-end call")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 256-domain batched workload")
@@ -211,11 +214,8 @@ def run_gpu(args):
     total_ms = events[0].elapsed_time(events[-1])
     per_step = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
     diag, t_diag, status = lat.step_diagnostics()
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    mlups = world * n * args.steps / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(total_ms, world, dev)
+    mlups = aggregate_mlups(n, args.steps, total_ms, world)
     step_ms = statistics.mean(per_step)
 
     # ---- roofline of the step kernel (fused step + its tiny diagnostics finalisation)
@@ -270,11 +270,7 @@ def run_gpu(args):
         for _ in range(args.e2e_calls):
             capi.lbm_run_host(lat.ctx, *ptrs[:3], args.e2e_steps, *ptrs[3:], want_diag=True)
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
         lat.close()
         out["e2e"] = {"value": round(world * n * args.e2e_steps * args.e2e_calls / dt / 1e6, 2), "unit": "MLUPS",
                       "h2d_bytes_per_step": round(3 * 8 * n / args.e2e_steps),
@@ -286,6 +282,7 @@ def run_gpu(args):
     if not args.no_forms:
         out["forms"] = forms_sweep(w, fields, dev, stream, peak_hbm)
         out["forms"].update(batch_sweep(dev, stream, peak_hbm, steps=args.batch_steps))
+        out["forms"].update(vjp_sweep(dev, stream))
 
     # ---- CPU baseline (oracle) on rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -297,6 +294,23 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value of x over the ranks of the default process group (x itself when world == 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes_per_rank: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job MLUPS: every rank advances its own lattice (weak scaling), timed by the slowest rank."""
+    return world * nodes_per_rank * steps / (max_ms * 1e-3) / 1e6
 
 
 def lat_bytes(prec, n):
@@ -395,6 +409,51 @@ def batch_sweep(dev, stream, peak_hbm, steps=1000):
     return res
 
 
+def vjp_sweep(dev, stream, n=1024, steps=500, ckpt=50):
+    """Differentiation workload: 1024^2 periodic, initial velocity from random Fourier modes
+    |k| <= 8 scaled to max |u| = 0.02, theta = 1/3, nu = 0.01, 500 steps, completely corrected
+    model; loss = 1/2 sum (rho_T - rho_target)^2 against a target run from the next seed;
+    gradient with respect to (rho0, u0) through lbm_vjp with checkpoints every 50 steps, in
+    FP64 and in the FP32 form, with the FP32 gradient's relative error against FP64."""
+    import torch
+
+    from paper_2602_21242_gb300 import flows
+    from paper_2602_21242_gb300.lattice import Lattice, run
+
+    theta, nu = 1.0 / 3.0, 0.01
+    tau = nu / theta + 0.5
+    x0 = [torch.from_numpy(a).to(dev) for a in flows.random_modes(n, seed=flows.SEED_BASE + 4)]
+    tgt = [torch.from_numpy(a).to(dev) for a in flows.random_modes(n, seed=flows.SEED_BASE + 5)]
+    with Lattice(n, n, theta, tau, "complete", "f64", device=dev, stream=stream) as lat:
+        lat.init(*tgt)
+        lat.step(steps)
+        rho_t = lat.moments()[0].clone()
+    res, grads = {}, {}
+    for prec in ("f64", "f32"):
+        with Lattice(n, n, theta, tau, "complete", prec, device=dev, stream=stream) as lat:
+            for rep in range(2):  # first pass allocates the work memory
+                x = [t.clone().requires_grad_(True) for t in x0]
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                rho, _, _ = run(lat, *x, steps, ckpt_every=ckpt)
+                loss = 0.5 * ((rho - rho_t) ** 2).sum()
+                e1.record(stream)
+                loss.backward()
+                e2.record(stream)
+                torch.cuda.synchronize(dev)
+            fwd_ms, bwd_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+            grads[prec] = [t.grad.detach() for t in x]
+            res[f"vjp1024/complete/{prec}"] = {
+                "forward_ms": round(fwd_ms, 2), "backward_ms": round(bwd_ms, 2), "loss": float(loss),
+                "gradient_mlups": round(n * n * steps / ((fwd_ms + bwd_ms) * 1e-3) / 1e6, 1),
+                "steps": steps, "ckpt_every": ckpt,
+                "note": "backward = forward recompute with checkpoints + segment recomputes + adjoint steps"}
+    num = sum(float(((a - b) ** 2).sum()) for a, b in zip(grads["f32"], grads["f64"]))
+    den = sum(float((b ** 2).sum()) for b in grads["f64"])
+    res["vjp1024/complete/f32"]["grad_rel_l2_error_vs_f64"] = (num / den) ** 0.5
+    return res
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -441,8 +500,53 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def precision_study(args):
+    """8192^2 doubly periodic shear layer (u_x = 0.1 tanh((y - ny/4)/80), mirrored; u_y = 0.005
+    sin(2 pi x / nx)), theta = 0.3, nu = 1e-3, completely corrected model, `--study-steps` steps in
+    FP64, FP32-shifted and FP16-shifted storage; prints the velocity and density error of the
+    shifted forms against FP64 and each form's throughput. LBGK is run in FP64 alongside to record
+    whether it stays finite at this Reynolds number (U N / nu = 8.2e5)."""
+    import torch
+
+    from paper_2602_21242_gb300 import flows
+    from paper_2602_21242_gb300.lattice import Lattice
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, theta, nu, U = 8192, 0.3, 1e-3, 0.1
+    tau = nu / theta + 0.5
+    fields = [torch.from_numpy(a).to(dev) for a in flows.shear_layer(n, n, U=U, width=80.0, delta_amp=0.005)]
+    res, final = {}, {}
+    for model, prec in (("complete", "f64"), ("complete", "f32"), ("complete", "f16"), ("lbgk", "f64")):
+        with Lattice(n, n, theta, tau, model, prec, device=dev, stream=stream) as lat:
+            lat.init(*fields)
+            lat.set_diagnostics_interval(100)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(args.study_steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            d, t, status = lat.step_diagnostics(raise_nonfinite=False)
+            if model == "complete":
+                final[prec] = [x.clone() for x in lat.moments()]
+            res[f"{model}/{prec}"] = {"mlups": round(n * n * args.study_steps / (ms * 1e-3) / 1e6, 1),
+                                      "finite": status == 0 and d[4] == 0, "mass": d[0], "t_diag": t}
+    for prec in ("f32", "f16"):
+        du = max(float((final[prec][k] - final["f64"][k]).abs().max()) for k in (1, 2))
+        du_rms = max(float(((final[prec][k] - final["f64"][k]) ** 2).mean().sqrt()) for k in (1, 2))
+        dr = float((final[prec][0] - final["f64"][0]).abs().max())
+        res[f"complete/{prec}"].update({"max_abs_du_over_U": du / U, "rms_du_over_U": du_rms / U,
+                                         "max_abs_drho": dr})
+    print(json.dumps({"study": "shear-layer precision, 8192^2, theta=0.3, nu=1e-3, U=0.1",
+                      "steps": args.study_steps, "results": res}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.precision_study:
+        precision_study(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
