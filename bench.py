@@ -38,6 +38,10 @@ BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}
 # diagnostics (7). The FP64 form is bound by the FP64 pipe on GB300.
 FP64_OPS_PER_NODE = {"lbgk": 64, "oreg": 98, "partial": 108, "complete": 131}
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per node of one step-kernel launch from the ncu capture of
+# the current kernel (profiles/step_kernel_<prec>_complete_2048.md, 2048^2, scaled to the
+# lattice by node count since traffic grows with it). Keyed by (storage, model).
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.7, ("f32", "complete"): 60.7}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete"]
 
 
@@ -222,8 +226,10 @@ def run_gpu(args):
     peak_hbm, hbm_src = hbm_peak()
     bytes_step = BYTES_PER_NODE[args.prec] * n
     hbm_gbs = bytes_step / (step_ms * 1e-3) / 1e9
+    tpn = PROFILED_TRAFFIC_B_PER_NODE.get((args.prec, args.model))
+    traffic = round(tpn * n) if tpn is not None else None
     roof = {"bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
-            "frac": round(hbm_gbs / peak_hbm, 4), "traffic": None,
+            "frac": round(hbm_gbs / peak_hbm, 4), "traffic": traffic,
             "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
             else "profiling-recipe fallback 6.8 TB/s",
             "kernel": f"step_kernel<{args.model},{args.prec},diag>", "ms_per_launch": round(step_ms, 4)}
@@ -232,7 +238,7 @@ def run_gpu(args):
         peak_ops = capi.lbm_measure_peak(0) / 2.0  # FMA instructions per second (2 FLOP each)
         ops = FP64_OPS_PER_NODE[args.model] * n / (step_ms * 1e-3)
         alu = {"bound": "alu", "achieved": round(ops / 1e12, 4), "peak": round(peak_ops / 1e12, 4),
-               "unit": "Top/s (FP64 add/mul/fma)", "frac": round(ops / peak_ops, 4), "traffic": None,
+               "unit": "Top/s (FP64 add/mul/fma)", "frac": round(ops / peak_ops, 4), "traffic": traffic,
                "peak_source": "FP64 FMA issue rate measured live on this GPU (lbm_measure_peak / 2)",
                "ops_per_node": FP64_OPS_PER_NODE[args.model],
                "kernel": roof["kernel"], "ms_per_launch": round(step_ms, 4)}
