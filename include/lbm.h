@@ -200,6 +200,19 @@ int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const 
 int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows);
 int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
 
+/*
+ * Step-kernel selection (no counterpart in the paper). kind 0: the column kernel
+ * of lbm_set_launch. kind 1 (shifted FP32/FP16 forms with nx a multiple of 8;
+ * other lattices keep kind 0's kernel): a producer warp streams each output
+ * row's nine plane segments into a shared-memory ring with TMA bulk copies and
+ * mbarrier transaction counts while consumer warps collide node pairs; one CTA
+ * per strip of 256 (FP32) or 512 (FP16) columns and `rows` rows (1..4096;
+ * bx, by ignored). Its waits are bounded: a wait that gives up makes lbm_sync
+ * return LBM_ETIMEOUT. Same results as kind 0 except the diagnostics' summation order.
+ */
+int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows);
+int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows);
+
 /* ------------------------------------------------------------------------
  * Batched form: many independent doubly periodic lattices of uneven size,
  * each with its own theta and tau, sharing one collision model and storage

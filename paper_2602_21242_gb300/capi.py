@@ -48,6 +48,8 @@ _SIGNATURES = {
     "lbm_measure_peak": ([_i, _pd], _i),
     "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "lbm_set_launch": ([_p, _i, _i, _i], _i),
+    "lbm_set_launch_ex": ([_p, _i, _i, _i, _i], _i),
+    "lbm_get_launch_ex": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "lbm_step_noalloc": ([_i, _i, _d, _d, _i, _p, _p, _p, _p], _i),
     "lbm_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "lbm_last_error": ([_p], ctypes.c_char_p),
@@ -329,3 +331,13 @@ def lbm_vjp(ctx, n: int, ckpt_every: int, d_rho0: int, d_ux0: int, d_uy0: int, g
     """Cotangents of (rho0, u0) for cotangents of the moments after n steps (device pointers, 0 = NULL)."""
     check(load().lbm_vjp(ctx, n, ckpt_every, d_rho0, d_ux0, d_uy0, g_rho or None, g_ux or None, g_uy or None,
                          g_rho0 or None, g_ux0 or None, g_uy0 or None), ctx)
+
+
+def lbm_set_launch_ex(ctx, kind: int, bx: int, by: int, rows: int) -> None:
+    check(load().lbm_set_launch_ex(ctx, kind, bx, by, rows), ctx)
+
+
+def lbm_get_launch_ex(ctx):
+    v = [_i() for _ in range(4)]
+    check(load().lbm_get_launch_ex(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return tuple(x.value for x in v)

@@ -103,6 +103,7 @@ void free_ctx(lbm_ctx* c) {
   cudaFree(c->d_diag);
   cudaFree(c->d_diag_now);
   cudaFree(c->d_sticky);
+  cudaFree(c->d_err);
   cudaFree(c->d_stage);
   cudaFree(c->d_vjp);
   delete c;
@@ -180,7 +181,8 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   if ((e = cudaMalloc(&c->d_partials, sizeof(double) * 5 * (size_t)c->parts_cap)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag_now, sizeof(double) * 6)) != cudaSuccess ||
-      (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess) {
+      (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
     return fail(nullptr, LBM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
@@ -189,7 +191,8 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   if ((e = cudaMemsetAsync(c->buf[0], 0, (size_t)bytes, c->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->buf[1], 0, (size_t)bytes, c->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->d_diag, 0, sizeof(double) * 6, c->stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->d_sticky, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess) {
+      (e = cudaMemsetAsync(c->d_sticky, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess) {
     free_ctx(c);
     return fail(nullptr, LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
@@ -254,6 +257,7 @@ int lbm_step(lbm_ctx* ctx, int n) {
   a.rho_ref = ctx->rho_ref;
   a.partials = ctx->d_partials;
   a.cfg = ctx->cfg;
+  a.err = ctx->d_err;
   for (int k = 0; k < n; ++k) {
     a.diag = ctx->diag_every > 0 && (ctx->t % ctx->diag_every) == 0;
     a.src = ctx->buf[ctx->cur];
@@ -278,10 +282,13 @@ int lbm_step_diagnostics(lbm_ctx* ctx, double* h_out5, long long* h_time) {
   if (!h_out5) return fail(ctx, LBM_EINVAL, "lbm_step_diagnostics: NULL output");
   double d[6];
   unsigned long long bad = 0;
+  int timed_out = 0;
   cudaError_t e = cudaMemcpyAsync(d, ctx->d_diag, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_sticky, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&timed_out, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step_diagnostics");
+  if (timed_out) return fail(ctx, LBM_ETIMEOUT, "a bounded device-side wait of the step kernel gave up");
   for (int k = 0; k < 5; ++k) h_out5[k] = ctx->last_diag_t >= 0 ? d[k] : 0.0;
   if (h_time) *h_time = ctx->last_diag_t;
   if (bad > 0) return fail(ctx, LBM_ENONFINITE, "%llu non-finite node(s) met by fused diagnostics", bad);
@@ -401,16 +408,21 @@ int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const 
   return e == cudaSuccess ? LBM_OK : cuda_fail(ctx, e, "lbm_run_host sync");
 }
 
-int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows) {
+int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows) { return lbm_set_launch_ex(ctx, 0, bx, by, rows); }
+
+int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows) {
   int s = check_ctx(ctx);
   if (s != LBM_OK) return s;
   olbm::LaunchCfg k;
+  k.kind = kind;
   k.bx = bx;
   k.by = by;
   k.rows = rows;
   if (!olbm::valid_cfg(k))
-    return fail(ctx, LBM_EINVAL, "launch shape %dx%d x %d rows invalid (bx a multiple of 32, bx*by <= 512, rows 1..64)",
-                bx, by, rows);
+    return fail(ctx, LBM_EINVAL,
+                "launch kind %d shape %dx%d x %d rows invalid (kind 0: bx a multiple of 32, bx*by <= 512, rows 1..64; "
+                "kind 1: rows 1..4096)",
+                kind, bx, by, rows);
   const long long need = olbm::step_blocks(ctx->g, k, ctx->prec);
   if (need > ctx->parts_cap) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -430,6 +442,12 @@ int lbm_set_launch(lbm_ctx* ctx, int bx, int by, int rows) {
   return LBM_OK;
 }
 
+int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows) {
+  if (!ctx || !kind) return LBM_EINVAL;
+  *kind = ctx->cfg.kind;
+  return lbm_get_launch(ctx, bx, by, rows);
+}
+
 int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows) {
   if (!ctx || !bx || !by || !rows) return LBM_EINVAL;
   *bx = ctx->cfg.bx;
@@ -445,9 +463,12 @@ int lbm_sync(lbm_ctx* ctx) {
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_sync");
   unsigned long long bad = 0;
+  int timed_out = 0;
   e = cudaMemcpyAsync(&bad, ctx->d_sticky, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&timed_out, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_sync flag read");
+  if (timed_out) return fail(ctx, LBM_ETIMEOUT, "a bounded device-side wait of the step kernel gave up");
   if (bad > 0) return fail(ctx, LBM_ENONFINITE, "%llu non-finite node(s) met by fused diagnostics", bad);
   return LBM_OK;
 }

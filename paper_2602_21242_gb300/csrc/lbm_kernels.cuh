@@ -275,6 +275,16 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
 }
 
+}  // namespace olbm
+
+#include "lbm_stream.cuh"
+
+namespace olbm {
+
+// Pipeline shapes per storage form: consumer threads (node pairs) and ring slots.
+constexpr int kStreamNC32 = 128, kStreamNC16 = 256, kStreamStages = 8;
+inline int stream_width(int prec) { return 2 * (prec == 1 ? kStreamNC32 : kStreamNC16); }
+
 // ------------------------------------------------------------------ diagnostics of the state
 // Pull only (no collision): FP64 moments of f(x, t), block partials as above.
 template <int PREC>
@@ -395,7 +405,15 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
 // The shifted forms update node pairs (x, x + 1) when nx is even.
 inline bool uses_pairs(int prec, const Geometry& g) { return prec != 0 && (g.nx % 2) == 0; }
+// The pipeline kernel applies to the shifted forms with nx a multiple of 8.
+inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
+  return k.kind == 1 && prec != 0 && (g.nx % 8) == 0;
+}
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
+  if (uses_stream(prec, g, k)) {
+    const int w = stream_width(prec);
+    return dim3((g.nx + w - 1) / w, (g.ny + k.rows - 1) / k.rows);
+  }
   const int cols = uses_pairs(prec, g) ? 2 * k.bx : k.bx;
   return dim3((g.nx + cols - 1) / cols, (g.ny + k.by * k.rows - 1) / (k.by * k.rows));
 }
@@ -419,9 +437,28 @@ template <int PREC> struct Launch {
     return cudaGetLastError();
   }
 
+  template <int MODEL, bool DIAG>
+  static cudaError_t stream_d(const StepArgs& a, cudaStream_t st) {
+    constexpr int NC = PREC == 1 ? kStreamNC32 : kStreamNC16;
+    using Shape = StreamShape<PREC, NC, kStreamStages>;
+    auto kernel = step_stream_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
+    static bool configured = false;  // per instantiation: opt in to the large shared-memory carve-out once
+    if (!configured) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
+    kernel<<<step_grid(a.g, a.cfg, PREC), NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c,
+                                                                           a.partials, a.cfg.rows, a.err);
+    return cudaGetLastError();
+  }
+
   template <int MODEL>
   static cudaError_t step_m(const StepArgs& a, cudaStream_t st) {
     if constexpr (PREC != 0) {
+      if (uses_stream(PREC, a.g, a.cfg)) return a.diag ? stream_d<MODEL, true>(a, st) : stream_d<MODEL, false>(a, st);
       if (uses_pairs(PREC, a.g)) return step_p<MODEL, true>(a, st);
     }
     return step_p<MODEL, false>(a, st);

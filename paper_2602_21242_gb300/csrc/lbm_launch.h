@@ -8,14 +8,18 @@
 
 namespace olbm {
 
-// Launch shape of the step kernel: bx x by threads (bx a multiple of 32,
-// bx * by <= 512), each thread updating `rows` nodes of one column.
+// Launch shape of the step kernel. kind 0: bx x by threads (bx a multiple of
+// 32, bx * by <= 512), each thread updating `rows` nodes of one column.
+// kind 1 (shifted forms, nx a multiple of 8): the bulk-copy pipeline, one CTA
+// per strip of kStreamW(prec) columns and `rows` rows (bx, by unused).
 struct LaunchCfg {
-  int bx = 32, by = 8, rows = 1;
+  int bx = 32, by = 8, rows = 1, kind = 0;
 };
 
 inline bool valid_cfg(const LaunchCfg& k) {
-  return k.bx >= 32 && k.bx % 32 == 0 && k.by >= 1 && k.bx * k.by <= 512 && k.rows >= 1 && k.rows <= 64;
+  if (k.kind == 1) return k.rows >= 1 && k.rows <= 4096;
+  return k.kind == 0 && k.bx >= 32 && k.bx % 32 == 0 && k.by >= 1 && k.bx * k.by <= 512 && k.rows >= 1 &&
+         k.rows <= 64;
 }
 
 struct StepArgs {
@@ -28,6 +32,7 @@ struct StepArgs {
   double rho_ref;    // 0 for absolute storage, 1 for the shifted forms
   double* partials;  // grid blocks * 5 doubles when diag
   LaunchCfg cfg;
+  int* err = nullptr;  // device flag set by a bounded wait that gave up (pipeline kernel)
 };
 
 // Number of thread blocks of the auxiliary node-parallel kernels and of the
