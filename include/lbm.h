@@ -205,10 +205,12 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * of lbm_set_launch. kind 1 (shifted FP32/FP16 forms with nx a multiple of 8;
  * other lattices keep kind 0's kernel): a producer warp streams each output
  * row's nine plane segments into a shared-memory ring with TMA bulk copies and
- * mbarrier transaction counts while consumer warps collide node pairs; one CTA
- * per strip of 256 (FP32) or 512 (FP16) columns and `rows` rows (1..4096;
- * bx, by ignored). Its waits are bounded: a wait that gives up makes lbm_sync
- * return LBM_ETIMEOUT. Same results as kind 0 except the diagnostics' summation order.
+ * mbarrier transaction counts while consumer warps collide node pairs; the
+ * lattice is cut into tiles of 256 (FP32) or 512 (FP16) columns by `rows` rows
+ * (1..4096; bx, by ignored) that a persistent grid of resident CTAs takes round
+ * robin. Its waits are bounded: a wait that gives up makes lbm_sync and
+ * lbm_step_diagnostics return LBM_ETIMEOUT. Same results as kind 0 except the
+ * diagnostics' summation order.
  */
 int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows);
 int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows);

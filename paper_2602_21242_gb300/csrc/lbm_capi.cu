@@ -258,14 +258,17 @@ int lbm_step(lbm_ctx* ctx, int n) {
   a.partials = ctx->d_partials;
   a.cfg = ctx->cfg;
   a.err = ctx->d_err;
+  long long used = ctx->nparts;
+  a.parts_used = &used;
   for (int k = 0; k < n; ++k) {
     a.diag = ctx->diag_every > 0 && (ctx->t % ctx->diag_every) == 0;
     a.src = ctx->buf[ctx->cur];
     a.dst = ctx->buf[ctx->cur ^ 1];
+    used = ctx->nparts;
     cudaError_t e = launch_step(a, ctx->prec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step launch");
     if (a.diag) {
-      e = olbm::launch_finalize(ctx->d_partials, (int)ctx->nparts, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
+      e = olbm::launch_finalize(ctx->d_partials, (int)used, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
                                 ctx->d_sticky, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step diagnostics launch");
       ctx->last_diag_t = ctx->t;

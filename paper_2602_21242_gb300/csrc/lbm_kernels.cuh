@@ -13,6 +13,7 @@
 // moments pull it back.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "lbm_device.cuh"
@@ -412,7 +413,8 @@ inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   if (uses_stream(prec, g, k)) {
     const int w = stream_width(prec);
-    return dim3((g.nx + w - 1) / w, (g.ny + k.rows - 1) / k.rows);
+    const long long tiles = (long long)((g.nx + w - 1) / w) * ((g.ny + k.rows - 1) / k.rows);
+    return dim3((unsigned)(k.cap > 0 ? std::min<long long>(tiles, k.cap) : tiles));
   }
   const int cols = uses_pairs(prec, g) ? 2 * k.bx : k.bx;
   return dim3((g.nx + cols - 1) / cols, (g.ny + k.by * k.rows - 1) / (k.by * k.rows));
@@ -442,16 +444,26 @@ template <int PREC> struct Launch {
     constexpr int NC = PREC == 1 ? kStreamNC32 : kStreamNC16;
     using Shape = StreamShape<PREC, NC, kStreamStages>;
     auto kernel = step_stream_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
-    static bool configured = false;  // per instantiation: opt in to the large shared-memory carve-out once
-    if (!configured) {
-      const cudaError_t e =
-          cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
+    // Per instantiation, once: opt in to the large shared-memory carve-out and
+    // size the persistent grid (resident CTAs per SM x SMs).
+    static int resident = 0;
+    if (resident == 0) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
+      int dev = 0, sms = 0, per_sm = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NC + 32, Shape::kSmemBytes);
       if (e != cudaSuccess) return e;
-      configured = true;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      resident = per_sm * sms;
     }
+    LaunchCfg k = a.cfg;
+    k.cap = resident;
+    const dim3 grid = step_grid(a.g, k, PREC);
+    if (a.parts_used) *a.parts_used = grid.x;
     const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
-    kernel<<<step_grid(a.g, a.cfg, PREC), NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c,
-                                                                           a.partials, a.cfg.rows, a.err);
+    kernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
+                                                     a.err);
     return cudaGetLastError();
   }
 

@@ -14,6 +14,7 @@ namespace olbm {
 // per strip of kStreamW(prec) columns and `rows` rows (bx, by unused).
 struct LaunchCfg {
   int bx = 32, by = 8, rows = 1, kind = 0;
+  int cap = 0;  // kind 1: most CTAs launched (a multiple of the SM count); 0 = one CTA per tile
 };
 
 inline bool valid_cfg(const LaunchCfg& k) {
@@ -33,6 +34,7 @@ struct StepArgs {
   double* partials;  // grid blocks * 5 doubles when diag
   LaunchCfg cfg;
   int* err = nullptr;  // device flag set by a bounded wait that gave up (pipeline kernel)
+  long long* parts_used = nullptr;  // out: diagnostics partials the launch wrote (its grid size)
 };
 
 // Number of thread blocks of the auxiliary node-parallel kernels and of the

@@ -1,0 +1,95 @@
+"""The paper's benchmark experiments (arXiv 2602.21242, Sec. 5) run on the GPU path.
+
+* Rotated decaying shear wave (Sec. 5.1, Fig. 2): numerical viscosity nu~/nu
+  against Mach number for the four models and several temperatures. The printed
+  set-up (a 1 x 200 grid with sin[sqrt(2) pi (-x + y)/N]) is not periodic as
+  written; here the wave runs along (-1, 1) on a square N x N periodic grid,
+  u_x = u_y = Ma/sqrt(6) + A0 sin(2 pi (-x + y)/N), so the mean flow (Ma/sqrt(6))
+  (1, 1) is perpendicular to the wave vector and the perturbation is a pure shear
+  wave. nu~ comes from the exponential decay of the wave's Fourier coefficient in
+  the velocity component along (1, 1) between two times (k^2 = 2 (2 pi/N)^2).
+  Runs that become non-finite are reported as nu~ = 0 (the paper's convention for
+  catastrophic instability).
+* Doubly periodic shear layer (Sec. 5.3): the paper's initial condition
+  (kappa = 80, delta = 0.05, u0 = 0.04, Re = u0 N / nu = 3e4) run to one turnover
+  time N / u0; reports whether each model stays finite and the vorticity field.
+
+All computation runs in liblbm.so; this module sets up inputs and reads moments.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import flows
+from .lattice import Lattice, tau_from_nu
+
+
+def rotated_shear_wave_fields(n: int, ma: float, a0: float = 1e-3):
+    x = np.arange(n, dtype=np.float64)[None, :]
+    y = np.arange(n, dtype=np.float64)[:, None]
+    pert = a0 * np.sin(2 * math.pi * (-x + y) / n)
+    u = ma / math.sqrt(6.0) + pert
+    u = np.broadcast_to(u, (n, n)).copy()
+    return np.ones((n, n)), u, u.copy()
+
+
+def _mode(ux: torch.Tensor, uy: torch.Tensor, n: int) -> complex:
+    """Fourier coefficient of (u_x + u_y)/sqrt(2) on the wave vector (2 pi / n)(-1, 1)."""
+    s = ((ux + uy) / math.sqrt(2.0)).cpu().numpy()
+    return complex(np.fft.fft2(s)[1, n - 1])  # index (k_y, k_x) = (1, -1)
+
+
+def rotated_shear_wave_viscosity(model: str, theta: float, ma: float, n: int = 200, nu: float = 1e-3,
+                                 steps: int = 1200, t_fit: int = 200, a0: float = 1e-3, prec: str = "f64",
+                                 device=None):
+    """Numerical viscosity ratio nu~/nu of the rotated shear wave (0.0 if the run became non-finite)."""
+    tau = tau_from_nu(nu, theta)
+    rho, ux, uy = rotated_shear_wave_fields(n, ma, a0)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    with Lattice(n, n, theta, tau, model, prec, device=dev) as lat:
+        lat.init(*(torch.from_numpy(a).to(dev) for a in (rho, ux, uy)))
+        lat.step(t_fit)
+        _, u1, v1 = lat.moments()
+        a1 = abs(_mode(u1, v1, n))
+        lat.step(steps - t_fit)
+        r2, u2, v2 = lat.moments()
+        if not (torch.isfinite(r2).all() and torch.isfinite(u2).all() and torch.isfinite(v2).all()):
+            return 0.0
+        a2 = abs(_mode(u2, v2, n))
+    if not (a2 > 0 and a1 > 0) or a2 > 10 * a1:
+        return 0.0
+    k2 = 2.0 * (2 * math.pi / n) ** 2
+    nu_num = -math.log(a2 / a1) / ((steps - t_fit) * k2)
+    return nu_num / nu
+
+
+def shear_layer_run(model: str, theta: float, n: int, u0: float = 0.04, kappa: float = 80.0, delta: float = 0.05,
+                    re: float = 3.0e4, turnovers: float = 1.0, prec: str = "f64", device=None):
+    """Paper's doubly periodic shear layer to `turnovers` x N/u0 steps. Returns (finite, steps,
+    vorticity (ny, nx) float64 numpy array or None)."""
+    nu = u0 * n / re
+    tau = tau_from_nu(nu, theta)
+    y = np.arange(n, dtype=np.float64)[:, None]
+    x = np.arange(n, dtype=np.float64)[None, :]
+    ux = np.where(y <= n / 2, u0 * np.tanh(kappa * (y / n - 0.25)), u0 * np.tanh(kappa * (0.75 - y / n)))
+    ux = np.broadcast_to(ux, (n, n)).copy()
+    uy = np.broadcast_to(delta * u0 * np.sin(2 * math.pi * (x / n + 0.25)), (n, n)).copy()
+    rho = np.ones((n, n))
+    steps = int(round(turnovers * n / u0))
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    with Lattice(n, n, theta, tau, model, prec, device=dev) as lat:
+        lat.init(*(torch.from_numpy(a).to(dev) for a in (rho, ux, uy)))
+        lat.step(steps)
+        r, u, v = (t.cpu().numpy() for t in lat.moments())
+    finite = bool(np.isfinite(r).all() and np.isfinite(u).all() and np.isfinite(v).all())
+    if not finite:
+        return False, steps, None
+    # vorticity by periodic central differences (lattice units)
+    w = (np.roll(v, -1, axis=1) - np.roll(v, 1, axis=1)) / 2 - (np.roll(u, -1, axis=0) - np.roll(u, 1, axis=0)) / 2
+    return True, steps, w
+
+
+__all__ = ["rotated_shear_wave_fields", "rotated_shear_wave_viscosity", "shear_layer_run", "flows"]
