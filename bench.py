@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--precision-study", action="store_true",
                     help="run the 8192^2 shear-layer precision study instead of the benchmark")
     ap.add_argument("--study-steps", type=int, default=5000)
+    ap.add_argument("--experiments", action="store_true",
+                    help="run the paper's rotated-shear-wave and shear-layer experiments instead of the benchmark")
     ap.add_argument("--e2e-steps", type=int, default=50, help="lattice steps per end-to-end call")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 256-domain batched workload")
@@ -548,8 +550,40 @@ def precision_study(args):
                       "steps": args.study_steps, "results": res}), flush=True)
 
 
+def paper_experiments(args):
+    """Sec. 5.1: nu~/nu of the rotated decaying shear wave (N = 200, nu = 1e-3, 1200 steps) for the four
+    models, theta in {0.25, 1/3, 0.4, 0.5}, Ma = 0.1 .. 1.0 (0 = the run became non-finite).
+    Sec. 5.3: the doubly periodic shear layer (kappa = 80, delta = 0.05, u0 = 0.04, Re = 3e4) to one
+    turnover time for N in {128, 256, 512}, theta in {0.4, 0.6}: whether each model stays finite."""
+    import torch
+
+    from paper_2602_21242_gb300 import experiments
+
+    torch.cuda.set_device(0)
+    models = ["lbgk", "oreg", "partial", "complete"]
+    mas = [round(0.1 * k, 1) for k in range(1, 11)]
+    table = {}
+    for theta in (0.25, 1.0 / 3.0, 0.4, 0.5):
+        for model in models:
+            table[f"{model}/theta={theta:.3f}"] = [
+                round(experiments.rotated_shear_wave_viscosity(model, theta, ma), 4) for ma in mas]
+    layer = {}
+    for theta in (0.4, 0.6):
+        for n in (128, 256, 512):
+            for model in models:
+                finite, steps, w = experiments.shear_layer_run(model, theta, n)
+                layer[f"{model}/theta={theta}/N={n}"] = {
+                    "finite": finite, "steps": steps,
+                    "max_abs_vorticity": None if w is None else float(abs(w).max())}
+    print(json.dumps({"experiments": "paper Sec. 5.1 and 5.3", "rotated_shear_wave": {"Ma": mas, "nu_ratio": table},
+                      "shear_layer": layer}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.experiments:
+        paper_experiments(args)
+        return
     if args.precision_study:
         precision_study(args)
         return

@@ -312,6 +312,16 @@ int lbm_measure_peak(int kind, double* h_flops);
 int lbm_step_noalloc(int nx, int ny, double theta, double tau, int model, const double* d_src,
                      double* d_dst, double* d_diag5, void* stream);
 
+/*
+ * Self-test of the bounded device-side waits (no counterpart in the paper):
+ * which = 0 waits on an mbarrier phase that never completes (the wait routine of
+ * the kind-1 step kernel), which = 1 on a grid barrier one block never reaches
+ * (the routine of the persistent batched kernel). Each wait gives up after about
+ * a second; the call returns LBM_ETIMEOUT and the elapsed host time in
+ * *h_seconds, and the context stays usable. Synchronous (cudaDeviceSynchronize).
+ */
+int lbm_selftest_timeout(int which, double* h_seconds);
+
 /* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

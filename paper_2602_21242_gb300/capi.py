@@ -46,6 +46,7 @@ _SIGNATURES = {
     "lbm_run_host": ([_p, _p, _p, _p, _i, _p, _p, _p, _pd], _i),
     "lbm_sync": ([_p], _i),
     "lbm_measure_peak": ([_i, _pd], _i),
+    "lbm_selftest_timeout": ([_i, _pd], _i),
     "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "lbm_set_launch": ([_p, _i, _i, _i], _i),
     "lbm_set_launch_ex": ([_p, _i, _i, _i, _i], _i),
@@ -341,3 +342,10 @@ def lbm_get_launch_ex(ctx):
     v = [_i() for _ in range(4)]
     check(load().lbm_get_launch_ex(ctx, *[ctypes.byref(x) for x in v]), ctx)
     return tuple(x.value for x in v)
+
+
+def lbm_selftest_timeout(which: int):
+    """Run a wait that must give up; returns (status, seconds)."""
+    secs = ctypes.c_double()
+    s = load().lbm_selftest_timeout(which, ctypes.byref(secs))
+    return s, secs.value

@@ -96,49 +96,6 @@ __global__ void __launch_bounds__(512) batch_step_kernel(const Desc<typename For
   update_tile<MODEL, PREC, DIAG, false>(d, tl.y, tl.z, parity, rows, partials + (long long)blockIdx.x * 5);
 }
 
-// Grid barrier with bounded waits. count/gen/err live in device memory zeroed
-// before the launch. Returns false (in every thread of the block) once any
-// block has given up.
-struct GridBarrier {
-  unsigned count;
-  unsigned gen;
-  int err;
-  int pad;
-};
-constexpr long long kBarrierCycles = 2000000000LL;  // ~1 s at GB300 clocks
-
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    ok = 1;
-    volatile unsigned* vgen = &b->gen;
-    volatile int* verr = &b->err;
-    const unsigned g = *vgen;  // generation before this block arrives
-    __threadfence();           // this block's stores before its arrival
-    const unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      b->count = 0;
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
-        if (*verr != 0 || clock64() - t0 > kBarrierCycles) {
-          atomicExch(&b->err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    if (*verr != 0) ok = 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 // n steps of every domain in one launch; tiles strided over the grid.
 template <int MODEL, int PREC>
 __global__ void __launch_bounds__(512) batch_persistent_kernel(const Desc<typename Form<PREC>::T>* __restrict__ desc,

@@ -1,0 +1,55 @@
+// lbm_selftest.cu -- makes the library's bounded device-side waits run out on
+// purpose and reports how the host sees it, so that the timeout paths are
+// exercised without faulting or hanging the GPU: each kernel waits on a
+// condition that nothing will satisfy, using the same wait routines as the
+// pipelined step kernel (mbarrier phase) and the persistent batched kernel
+// (grid barrier); each wait gives up after about a second and sets a flag.
+#include <chrono>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+// One block waits for an mbarrier phase that needs two arrivals and gets none.
+__global__ void stuck_mbarrier_kernel(int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    olbm::mbar_init(&bar, 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  olbm::mbar_wait(&bar, 0u, err);
+}
+
+// Two blocks, one of which leaves without arriving: the other waits at the grid barrier.
+__global__ void stuck_grid_barrier_kernel(olbm::GridBarrier* b) {
+  if (blockIdx.x == 0) return;
+  olbm::grid_sync(b, gridDim.x);
+}
+
+}  // namespace
+
+extern "C" int lbm_selftest_timeout(int which, double* h_seconds) {
+  if (which != 0 && which != 1) return LBM_EINVAL;
+  int* d = nullptr;
+  const size_t bytes = which == 0 ? sizeof(int) : sizeof(olbm::GridBarrier);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return LBM_ENOMEM;
+  cudaMemset(d, 0, bytes);
+  const auto t0 = std::chrono::steady_clock::now();
+  if (which == 0)
+    stuck_mbarrier_kernel<<<1, 32>>>(d);
+  else
+    stuck_grid_barrier_kernel<<<2, 32>>>(reinterpret_cast<olbm::GridBarrier*>(d));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int flag = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&flag, which == 0 ? d : &reinterpret_cast<olbm::GridBarrier*>(d)->err, sizeof(int),
+                   cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (h_seconds) *h_seconds = secs;
+  if (e != cudaSuccess) return LBM_ECUDA;
+  return flag ? LBM_ETIMEOUT : LBM_OK;
+}

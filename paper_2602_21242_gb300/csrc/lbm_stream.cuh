@@ -63,6 +63,49 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Grid barrier with bounded waits. count/gen/err live in device memory zeroed
+// before the launch. Returns false (in every thread of the block) once any
+// block has given up.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad;
+};
+constexpr long long kBarrierCycles = 2000000000LL;  // ~1 s at GB300 clocks
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &b->gen;
+    volatile int* verr = &b->err;
+    const unsigned g = *vgen;  // generation before this block arrives
+    __threadfence();           // this block's stores before its arrival
+    const unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
+    if (arrived == nblocks) {
+      b->count = 0;
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*verr != 0 || clock64() - t0 > kBarrierCycles) {
+          atomicExch(&b->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (*verr != 0) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 __device__ __forceinline__ f32x2 lds_pair(const float* p) { return f32x2(*reinterpret_cast<const float2*>(p)); }
 __device__ __forceinline__ f32x2 lds_pair(const __half* p) {
   return f32x2(__half22float2(*reinterpret_cast<const __half2*>(p)));
