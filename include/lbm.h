@@ -207,8 +207,9 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * row's nine plane segments into a shared-memory ring with TMA bulk copies and
  * mbarrier transaction counts while consumer warps collide node pairs; the
  * lattice is cut into tiles of 256 (FP32) or 512 (FP16) columns by `rows` rows
- * (1..4096; bx, by ignored) that a persistent grid of resident CTAs takes round
- * robin. Its waits are bounded: a wait that gives up makes lbm_sync and
+ * (1..4096); bx = 0 launches one CTA per tile, bx = k > 0 a persistent grid of k
+ * CTAs per SM (capped at the resident count) that takes the tiles round robin
+ * (by ignored). Its waits are bounded: a wait that gives up makes lbm_sync and
  * lbm_step_diagnostics return LBM_ETIMEOUT. Same results as kind 0 except the
  * diagnostics' summation order.
  */

@@ -446,7 +446,7 @@ template <int PREC> struct Launch {
     auto kernel = step_stream_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
     // Per instantiation, once: opt in to the large shared-memory carve-out and
     // size the persistent grid (resident CTAs per SM x SMs).
-    static int resident = 0;
+    static int resident = 0, sms_seen = 1;
     if (resident == 0) {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
       int dev = 0, sms = 0, per_sm = 0;
@@ -456,9 +456,12 @@ template <int PREC> struct Launch {
       if (e != cudaSuccess) return e;
       if (per_sm < 1) return cudaErrorInvalidConfiguration;
       resident = per_sm * sms;
+      sms_seen = sms;
     }
+    // bx > 0: a persistent grid of bx CTAs per SM (at most the resident count);
+    // bx == 0: one CTA per tile.
     LaunchCfg k = a.cfg;
-    k.cap = resident;
+    k.cap = a.cfg.bx > 0 ? std::min(resident, a.cfg.bx * sms_seen) : 0;
     const dim3 grid = step_grid(a.g, k, PREC);
     if (a.parts_used) *a.parts_used = grid.x;
     const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);

@@ -10,15 +10,17 @@ namespace olbm {
 
 // Launch shape of the step kernel. kind 0: bx x by threads (bx a multiple of
 // 32, bx * by <= 512), each thread updating `rows` nodes of one column.
-// kind 1 (shifted forms, nx a multiple of 8): the bulk-copy pipeline, one CTA
-// per strip of kStreamW(prec) columns and `rows` rows (bx, by unused).
+// kind 1 (shifted forms, nx a multiple of 8): the bulk-copy pipeline over
+// tiles of stream_width(prec) columns by `rows` rows; bx = 0 launches one CTA
+// per tile, bx > 0 a persistent grid of bx CTAs per SM (at most the resident
+// count) looping over the tiles; by unused.
 struct LaunchCfg {
   int bx = 32, by = 8, rows = 1, kind = 0;
   int cap = 0;  // kind 1: most CTAs launched (a multiple of the SM count); 0 = one CTA per tile
 };
 
 inline bool valid_cfg(const LaunchCfg& k) {
-  if (k.kind == 1) return k.rows >= 1 && k.rows <= 4096;
+  if (k.kind == 1) return k.rows >= 1 && k.rows <= 4096 && k.bx >= 0 && k.bx <= 64;
   return k.kind == 0 && k.bx >= 32 && k.bx % 32 == 0 && k.by >= 1 && k.bx * k.by <= 512 && k.rows >= 1 &&
          k.rows <= 64;
 }

@@ -21,8 +21,11 @@ from . import capi
 
 _lock = threading.Lock()
 
-LATTICE_CANDIDATES = [(bx, by, rows) for (bx, by), rows in itertools.product(
+# (kind, bx, by, rows): kind 0 = column kernel; kind 1 = bulk-copy pipeline (shifted forms,
+# nx a multiple of 8) with bx = CTAs per SM (0 = one CTA per tile)
+LATTICE_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)], [4, 8, 16, 32])]
+PIPELINE_CANDIDATES = [(1, ctas, 1, rows) for ctas in (0, 1, 2) for rows in (4, 8, 16, 32, 64)]
 BATCH_CANDIDATES = [(bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)], [2, 4, 8, 16])]
 
@@ -68,18 +71,23 @@ def _time(step, sync, stream, steps: int) -> float:
 
 
 def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, path: str | None = None):
-    """Pick and apply the fastest launch shape for `lat` (a Lattice). Timing runs on a
-    temporary lattice of the same size, storage and model started at rest, so `lat`'s
-    state is untouched. Returns ((bx, by, rows), ms_per_step or None if cached)."""
+    """Pick and apply the fastest launch (kind, bx, by, rows) for `lat` (a Lattice). Timing
+    runs on a temporary lattice of the same size, storage and model started at rest, so
+    `lat`'s state is untouched. Candidates may be given as (bx, by, rows) for kind 0 or as
+    (kind, bx, by, rows). Returns ((kind, bx, by, rows), ms_per_step or None if cached)."""
     from .lattice import Lattice
 
     path = path or cache_path()
-    key = _key("lattice", lat.nx * lat.ny, lat.prec, lat.model)
+    key = _key("lattice", lat.nx * lat.ny, lat.prec, lat.model, f"|nx%8={lat.nx % 8}")
     if use_cache:
         hit = _load_cache(path).get(key)
         if hit:
-            capi.lbm_set_launch(lat.ctx, *hit["shape"])
+            capi.lbm_set_launch_ex(lat.ctx, *hit["shape"])
             return tuple(hit["shape"]), None
+    if candidates is None:
+        candidates = list(LATTICE_CANDIDATES)
+        if lat.prec != capi.LBM_F64 and lat.nx % 8 == 0:
+            candidates += PIPELINE_CANDIDATES
     best = None
     with Lattice(lat.nx, lat.ny, lat.theta, lat.tau, lat.model, lat.prec, device=lat.device,
                  stream=lat.stream) as tmp:
@@ -87,15 +95,16 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
         zeros = torch.zeros_like(ones)
         tmp.init(ones, zeros, zeros)
         tmp.set_diagnostics_interval(1)
-        for shape in candidates or LATTICE_CANDIDATES:
+        for shape in candidates:
+            shape = tuple(shape) if len(shape) == 4 else (0,) + tuple(shape)
             try:
-                capi.lbm_set_launch(tmp.ctx, *shape)
+                capi.lbm_set_launch_ex(tmp.ctx, *shape)
             except capi.LBMError:
                 continue
             ms = _time(tmp.step, tmp.sync, tmp.stream, steps)
             if best is None or ms < best[1]:
                 best = (shape, ms)
-    capi.lbm_set_launch(lat.ctx, *best[0])
+    capi.lbm_set_launch_ex(lat.ctx, *best[0])
     _store(path, key, {"shape": list(best[0]), "ms_per_step": best[1]})
     return tuple(best[0]), best[1]
 

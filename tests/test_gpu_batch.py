@@ -112,9 +112,10 @@ def test_batch_rejects_bad_domains():
 def test_tuners(tmp_path):
     path = str(tmp_path / "tune.json")
     with Lattice(256, 256, 1 / 3, 0.56, "complete", "f32") as lat:
-        shape, ms = tune.tune_lattice(lat, candidates=[(64, 2, 4), (128, 4, 8)], steps=4, path=path)
-        assert shape in [(64, 2, 4), (128, 4, 8)] and ms > 0
-        assert capi.lbm_get_launch(lat.ctx) == shape
+        shape, ms = tune.tune_lattice(lat, candidates=[(64, 2, 4), (128, 4, 8), (1, 0, 1, 16)], steps=4, path=path)
+        assert shape in [(0, 64, 2, 4), (0, 128, 4, 8), (1, 0, 1, 16)] and ms > 0
+        assert capi.lbm_get_launch_ex(lat.ctx)[0] == shape[0]
+        assert capi.lbm_get_launch_ex(lat.ctx)[3] == shape[3]
         again, cached = tune.tune_lattice(lat, path=path)
         assert again == shape and cached is None
     with make_batch(3, "f32", "graph") as b:

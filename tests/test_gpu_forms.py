@@ -113,12 +113,14 @@ def test_forms_diagnostics(oracle, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("nx,ny,rows", [(64, 40, 7), (264, 17, 5), (520, 9, 4), (8, 5, 2), (1024, 33, 64)])
+@pytest.mark.parametrize("nx,ny,rows,ctas", [(64, 40, 7, 0), (264, 17, 5, 0), (520, 9, 4, 0), (8, 5, 2, 0),
+                                             (1024, 33, 64, 0), (1032, 65, 3, 1), (2048, 40, 4, 2)])
 @pytest.mark.parametrize("model", [0, 3])
-def test_pipeline_kernel_matches_column_kernel(prec, nx, ny, rows, model):
+def test_pipeline_kernel_matches_column_kernel(prec, nx, ny, rows, ctas, model):
     """The bulk-copy pipeline (launch kind 1) and the column kernel share the per-node
     arithmetic: populations bit-identical, diagnostics equal to FP32 summation order.
-    Sizes cover full and partial column strips, partial row blocks and the periodic edges."""
+    Sizes cover full and partial column strips, partial row blocks, the periodic edges, and
+    both one CTA per tile (ctas = 0) and persistent grids (ctas CTAs per SM)."""
     theta, tau = 0.33, 0.7
     f0 = flows.random_populations(nx, ny, seed=900 + nx + ny, spread=0.1)
     out = {}
@@ -126,8 +128,10 @@ def test_pipeline_kernel_matches_column_kernel(prec, nx, ny, rows, model):
         with Lattice(nx, ny, theta, tau, model, prec) as lat:
             from paper_2602_21242_gb300 import capi
             if kind == 1:
-                capi.lbm_set_launch_ex(lat.ctx, 1, 0, 0, rows)
+                capi.lbm_set_launch_ex(lat.ctx, 1, ctas, 0, rows)
                 assert capi.lbm_get_launch_ex(lat.ctx)[0] == 1
+            else:
+                capi.lbm_set_launch_ex(lat.ctx, 0, 128, 4, 16)
             lat.set_state(torch.from_numpy(f0).cuda())
             lat.set_diagnostics_interval(1)
             lat.step(6)
