@@ -413,7 +413,9 @@ inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   if (uses_stream(prec, g, k)) {
     const int w = stream_width(prec);
-    const long long tiles = (long long)((g.nx + w - 1) / w) * ((g.ny + k.rows - 1) / k.rows);
+    const int sx = (g.nx + w - 1) / w, sy = (g.ny + k.rows - 1) / k.rows;
+    if (k.bx == 0) return dim3(sx, sy);  // one CTA per tile
+    const long long tiles = (long long)sx * sy;
     return dim3((unsigned)(k.cap > 0 ? std::min<long long>(tiles, k.cap) : tiles));
   }
   const int cols = uses_pairs(prec, g) ? 2 * k.bx : k.bx;
@@ -444,15 +446,18 @@ template <int PREC> struct Launch {
     constexpr int NC = PREC == 1 ? kStreamNC32 : kStreamNC16;
     using Shape = StreamShape<PREC, NC, kStreamStages>;
     auto kernel = step_stream_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
+    auto pkernel = step_stream_persistent_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
     // Per instantiation, once: opt in to the large shared-memory carve-out and
     // size the persistent grid (resident CTAs per SM x SMs).
     static int resident = 0, sms_seen = 1;
     if (resident == 0) {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pkernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
       int dev = 0, sms = 0, per_sm = 0;
       if (e == cudaSuccess) e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NC + 32, Shape::kSmemBytes);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pkernel, NC + 32, Shape::kSmemBytes);
       if (e != cudaSuccess) return e;
       if (per_sm < 1) return cudaErrorInvalidConfiguration;
       resident = per_sm * sms;
@@ -463,10 +468,14 @@ template <int PREC> struct Launch {
     LaunchCfg k = a.cfg;
     k.cap = a.cfg.bx > 0 ? std::min(resident, a.cfg.bx * sms_seen) : 0;
     const dim3 grid = step_grid(a.g, k, PREC);
-    if (a.parts_used) *a.parts_used = grid.x;
+    if (a.parts_used) *a.parts_used = (long long)grid.x * grid.y;
     const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
-    kernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
-                                                     a.err);
+    if (a.cfg.bx == 0)
+      kernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
+                                                       a.err);
+    else
+      pkernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
+                                                        a.err);
     return cudaGetLastError();
   }
 

@@ -128,7 +128,7 @@ template <int PREC, int NC, int STAGES> struct StreamShape {
 };
 
 template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32) step_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
+__global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const typename Form<PREC>::S* __restrict__ src,
                                                              typename Form<PREC>::S* __restrict__ dst, Geometry g,
                                                              Coef<f32x2> c, double* __restrict__ partials, int H,
                                                              int* __restrict__ err) {
@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(NC + 32) step_stream_kernel(const typename For
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes);
   unsigned long long* empty = full + STAGES;
 
-  // Tiles: strips of W columns x blocks of H rows, numbered strip-fastest. CTA b
-  // takes tiles b, b + gridDim.x, ...; the ring's item counter runs on across
-  // tiles, so a CTA fills the pipeline once.
+  // Persistent form. Tiles: strips of W columns x blocks of H rows, numbered
+  // strip-fastest. CTA b takes tiles b, b + gridDim.x, ...; the ring's item
+  // counter runs on across tiles, so a CTA fills the pipeline once.
   const int nstrips = (g.nx + Shape::kW - 1) / Shape::kW;
   const int ntiles = nstrips * ((g.ny + H - 1) / H);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -249,6 +249,122 @@ __global__ void __launch_bounds__(NC + 32) step_stream_kernel(const typename For
     }
   }
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)blockIdx.x * 5);
+}
+
+// One CTA per tile: strip blockIdx.x of W columns, rows [blockIdx.y H, + H).
+// (Measured faster than the persistent form when registers allow only two
+// resident CTAs per SM: overlapping CTA lifetimes hide the ring's fill.)
+template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
+__global__ void __launch_bounds__(NC + 32) step_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                             typename Form<PREC>::S* __restrict__ dst, Geometry g,
+                                                             Coef<f32x2> c, double* __restrict__ partials, int H,
+                                                             int* __restrict__ err) {
+  using S = typename Form<PREC>::S;
+  using Shape = StreamShape<PREC, NC, STAGES>;
+  constexpr int CH = Shape::kChunk, SEG = Shape::kSeg;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S* ring = reinterpret_cast<S*>(smem);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes);
+  unsigned long long* empty = full + STAGES;
+
+  const int x0 = blockIdx.x * Shape::kW;
+  const int y0 = blockIdx.y * H;
+  const int w = min(Shape::kW, g.nx - x0);       // nodes of this strip (a multiple of 8)
+  const int rows = min(H, g.ny - y0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kConsumerWarps = NC / 32;
+  const bool producer = warp == kConsumerWarps;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  DiagAcc<f32x2> acc;
+  if (producer) {
+    // Copy plan per plane: main segment [x0, x0 + w) always; the left chunk (ending
+    // at x0 - 1, periodic) for c_ix = +1, the right chunk (starting at x0 + w) for c_ix = -1.
+    const int xl = (x0 == 0) ? g.nx - CH : x0 - CH;
+    const int xr = (x0 + w >= g.nx) ? 0 : x0 + w;
+    const unsigned main_bytes = (unsigned)(w * sizeof(S));
+    const unsigned stage_bytes = 9u * main_bytes + 6u * 16u;
+    bool ok = true;
+    int issued = 0;
+    for (int k = 0; k < rows && ok; ++k) {
+      const int s = k % STAGES;
+      if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
+      ok = __all_sync(0xffffffffu, ok);  // the whole warp leaves together
+      if (!ok) break;
+      const int y = y0 + k;
+      S* slot = ring + (size_t)s * 9 * SEG;
+      if (lane == 0) mbar_expect_tx_arrive(&full[s], stage_bytes);
+      __syncwarp();
+      // lanes 0..8: main segments; lanes 9..14: edge chunks of the planes with c_ix != 0
+      if (lane < 15) {
+        int i, part;  // part 0: main, 1: left chunk, 2: right chunk
+        if (lane < 9) {
+          i = lane;
+          part = 0;
+        } else {
+          const int e = lane - 9;  // planes 1, 5, 8 take the left chunk; 3, 6, 7 the right one
+          const int planes[6] = {1, 5, 8, 3, 6, 7};
+          i = planes[e];
+          part = e < 3 ? 1 : 2;
+        }
+        int ys = y - cy_of(i);
+        ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+        const S* row = src + i * g.plane + (long long)ys * g.pitch;
+        S* seg = slot + i * SEG;
+        if (part == 0)
+          bulk_g2s(seg + CH, row + x0, main_bytes, &full[s]);
+        else if (part == 1)
+          bulk_g2s(seg, row + xl, 16u, &full[s]);
+        else
+          bulk_g2s(seg + CH + w, row + xr, 16u, &full[s]);
+      }
+      ++issued;
+    }
+    // Before leaving, every copy issued must have landed (bounded).
+    for (int k = (issued > STAGES ? issued - STAGES : 0); k < issued; ++k)
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[k % STAGES], (unsigned)((k / STAGES) & 1), err))) break;
+  } else if (threadIdx.x < NC) {
+    const int t = threadIdx.x;
+    const int xl = 2 * t;  // local node index of the pair's first node
+    const bool active = xl < w;
+    for (int k = 0; k < rows; ++k) {
+      const int s = k % STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err))) break;
+      const S* slot = ring + (size_t)s * 9 * SEG;
+      f32x2 f[9];
+      if (active) {
+        // plane i, node x0 + xl + q: element CH + xl + q - c_ix of the plane's segment
+        f[0] = lds_pair(slot + 0 * SEG + CH + xl);
+        f[1] = lds_two(slot + 1 * SEG + CH + xl - 1, slot + 1 * SEG + CH + xl);
+        f[2] = lds_pair(slot + 2 * SEG + CH + xl);
+        f[3] = lds_two(slot + 3 * SEG + CH + xl + 1, slot + 3 * SEG + CH + xl + 2);
+        f[4] = lds_pair(slot + 4 * SEG + CH + xl);
+        f[5] = lds_two(slot + 5 * SEG + CH + xl - 1, slot + 5 * SEG + CH + xl);
+        f[6] = lds_two(slot + 6 * SEG + CH + xl + 1, slot + 6 * SEG + CH + xl + 2);
+        f[7] = lds_two(slot + 7 * SEG + CH + xl + 1, slot + 7 * SEG + CH + xl + 2);
+        f[8] = lds_two(slot + 8 * SEG + CH + xl - 1, slot + 8 * SEG + CH + xl);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (active) {
+        NodeMoments<f32x2> m;
+        collide<MODEL, true, f32x2>(f, c, m);
+        S* q = dst + (long long)(y0 + k) * g.pitch + x0 + xl;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);
+        if constexpr (DIAG) acc.add(m);
+      }
+    }
+  }
+  if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
 }
 
 }  // namespace olbm

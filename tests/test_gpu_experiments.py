@@ -14,30 +14,55 @@ from paper_2602_21242_gb300.lattice import tau_from_nu
 pytestmark = pytest.mark.gpu
 
 
-def oracle_nu_ratio(oracle, model, theta, ma, n, nu, steps, t_fit):
+def oracle_nu_ratio(oracle, model, theta, ma, n, nu, steps, t_fit, orientation):
     m = {"lbgk": 0, "oreg": 1, "partial": 2, "complete": 3}[model]
     tau = tau_from_nu(nu, theta)
-    rho, ux, uy = experiments.rotated_shear_wave_fields(n, ma)
+    rho, ux, uy = experiments.rotated_shear_wave_fields(n, ma, orientation=orientation)
     f = oracle.run(oracle.init(rho, ux, uy, theta), theta, tau, m, t_fit)
     _, u1, v1 = oracle.moments(f)
     f = oracle.run(f, theta, tau, m, steps - t_fit)
     _, u2, v2 = oracle.moments(f)
-    mode = lambda u, v: abs(np.fft.fft2((u + v) / math.sqrt(2.0))[1, n - 1])
-    k2 = 2.0 * (2 * math.pi / n) ** 2
-    return -math.log(mode(u2, v2) / mode(u1, v1)) / ((steps - t_fit) * k2) / nu
+    a1 = abs(experiments.shear_mode(u1, v1, n, orientation))
+    a2 = abs(experiments.shear_mode(u2, v2, n, orientation))
+    return -math.log(a2 / a1) / ((steps - t_fit) * experiments.shear_k2(n, orientation)) / nu
 
 
+@pytest.mark.parametrize("orientation", ["axis", "diagonal"])
 @pytest.mark.parametrize("model", ["lbgk", "oreg", "partial", "complete"])
-def test_rotated_shear_wave_measurement_matches_oracle(oracle, model):
+def test_rotated_shear_wave_measurement_matches_oracle(oracle, model, orientation):
     n, theta, ma, nu, steps, t_fit = 32, 0.4, 0.3, 0.005, 300, 50
-    got = experiments.rotated_shear_wave_viscosity(model, theta, ma, n=n, nu=nu, steps=steps, t_fit=t_fit)
-    want = oracle_nu_ratio(oracle, model, theta, ma, n, nu, steps, t_fit)
+    got = experiments.rotated_shear_wave_viscosity(model, theta, ma, n=n, nu=nu, steps=steps, t_fit=t_fit,
+                                                   orientation=orientation)
+    want = oracle_nu_ratio(oracle, model, theta, ma, n, nu, steps, t_fit, orientation)
     assert got == pytest.approx(want, rel=1e-8)
 
 
-def test_complete_model_viscosity_is_accurate_at_theta0():
-    """Sec. 5.1: at theta = 1/3 the corrected models recover the imposed viscosity over the
-    Mach range (paper: up to Ma = 1)."""
-    for ma in (0.1, 0.5):
-        r = experiments.rotated_shear_wave_viscosity("complete", 1.0 / 3.0, ma, n=200, nu=1e-3)
-        assert r == pytest.approx(1.0, abs=0.05), (ma, r)
+def test_corrected_models_recover_the_viscosity():
+    """Sec. 5.1: the partially and completely corrected models recover nu over the Mach range
+    (paper: up to Ma = 1, 0.9, 0.4 at theta = 1/3, 0.4, 0.5), the complete one also at
+    theta = 0.25 over the whole range."""
+    cases = [(1.0 / 3.0, (0.1, 0.5, 0.9), ("partial", "complete")), (0.4, (0.1, 0.5, 0.9), ("partial", "complete")),
+             (0.5, (0.1, 0.4), ("partial", "complete")), (0.25, (0.1, 0.5, 0.9), ("complete",))]
+    for theta, mas, models in cases:
+        for model in models:
+            for ma in mas:
+                r = experiments.rotated_shear_wave_viscosity(model, theta, ma)
+                assert r == pytest.approx(1.0, abs=0.03), (model, theta, ma, r)
+
+
+def test_uncorrected_model_degrades_with_mach_and_temperature():
+    """Sec. 5.1: the uncorrected model recovers nu only at small Ma, over a range that shrinks as
+    theta grows, and is not stable at theta = 0.25."""
+    assert experiments.rotated_shear_wave_viscosity("oreg", 1.0 / 3.0, 0.1) == pytest.approx(1.0, abs=0.03)
+    assert abs(experiments.rotated_shear_wave_viscosity("oreg", 1.0 / 3.0, 0.7) - 1.0) > 0.5
+    assert abs(experiments.rotated_shear_wave_viscosity("oreg", 0.4, 0.5) - 1.0) > 0.5
+    assert experiments.rotated_shear_wave_viscosity("oreg", 0.25, 0.1) == 0.0
+
+
+def test_shear_layer_lbgk_fails_where_oreg_holds():
+    """Sec. 5.3: at theta = 0.6 LBGK does not give a physical shear layer on N = 128 while the
+    corrected OReg model stays bounded."""
+    ok_l, _, w_l = experiments.shear_layer_run("lbgk", 0.6, 128)
+    ok_c, _, w_c = experiments.shear_layer_run("complete", 0.6, 128)
+    assert ok_c and np.abs(w_c).max() < 0.05
+    assert (not ok_l) or np.abs(w_l).max() > 1.0

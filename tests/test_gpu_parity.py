@@ -215,3 +215,39 @@ def test_full_size_sampled_parity_f64(oracle, model):
         assert d[0] == pytest.approx(n * n, rel=1e-13)            # mass conserved
         assert d[1] == pytest.approx(0.1 * n * n, rel=1e-12)      # momentum conserved (models 0, 3)
         _one_step_sample_check(oracle, lat, theta, tau, model, 512, 77 + model, 1e-13)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_checkpoint_resume(prec):
+    """lbm_get_state / lbm_set_state as checkpoint and resume: a run split at t = 7 and resumed
+    in a new lattice equals the uninterrupted run (the FP32 form after its own first rounding)."""
+    n, theta, tau = 48, 1 / 3, 0.6
+    rho, ux, uy = flows.taylor_green(n, n, 0.05, theta)
+    fields = [torch.from_numpy(a).cuda() for a in (rho, ux, uy)]
+    with Lattice(n, n, theta, tau, "complete", prec) as a:
+        a.init(*fields)
+        a.step(7)
+        ckpt = a.state()
+        a.step(13)
+        want = a.state().cpu().numpy()
+    with Lattice(n, n, theta, tau, "complete", prec) as b:
+        b.set_state(ckpt)
+        assert b.time == 0
+        b.step(13)
+        got = b.state().cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+
+
+def test_vjp_and_batch_argument_errors():
+    with Lattice(16, 16, 1 / 3, 0.6, "complete", "f16") as lat:
+        z = torch.zeros((16, 16), dtype=torch.float64, device="cuda")
+        with pytest.raises(capi.LBMError) as e:
+            capi.lbm_vjp(lat.ctx, 4, 2, z.data_ptr(), z.data_ptr(), z.data_ptr())
+        assert e.value.status == capi.LBM_EINVAL
+    with Lattice(16, 16, 1 / 3, 0.6, "complete", "f64") as lat:
+        with pytest.raises(capi.LBMError):
+            capi.lbm_vjp(lat.ctx, 4, 0, z.data_ptr(), z.data_ptr(), z.data_ptr())
+        with pytest.raises(capi.LBMError):
+            capi.lbm_set_launch_ex(lat.ctx, 0, 48, 4, 4)  # bx not a multiple of 32
+        with pytest.raises(capi.LBMError):
+            capi.lbm_set_launch_ex(lat.ctx, 2, 32, 4, 4)  # unknown kind
