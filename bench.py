@@ -33,10 +33,10 @@ METRIC = "MLUPS and % of HBM roofline, D2Q9 OReg-GEq; FP32 vs FP64 at stated err
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}
 # Algorithmic FP64 operations per node of one fused step (each add, mul or FMA is
 # one operation, i.e. one FP64 pipe issue), counted from the product-form
-# collision: 35 shared (moments 16, 1/rho 3, u 2, u^2 2, u/2 2, dP 4, P 6), the
+# collision: 33 shared (moments 16, 1/rho 3, u 2, u^2 2, u/2 2, P 8), the
 # model part (LBGK 22, OReg 56, partial 66, complete 89) and the fused
 # diagnostics (7). The FP64 form is bound by the FP64 pipe on GB300.
-FP64_OPS_PER_NODE = {"lbgk": 64, "oreg": 98, "partial": 108, "complete": 131}
+FP64_OPS_PER_NODE = {"lbgk": 62, "oreg": 96, "partial": 106, "complete": 129}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch from the ncu capture of
 # the current kernel (profiles/step_kernel_<prec>_complete_2048.md, 2048^2, scaled to the

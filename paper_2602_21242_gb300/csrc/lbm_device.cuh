@@ -214,10 +214,19 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
   // Per-axis GEq factors P(a) (Eq. 10), a = -1, 0, +1, and their deviations
   // dP = P - W from the rest values (dP(0) = -u^2, dP(+-1) = (u^2 +- u)/2).
   const T hux = T(0.5) * ux, huy = T(0.5) * uy;
-  const T dx[3] = {fma(T(0.5), ux2, -hux), -ux2, fma(T(0.5), ux2, hux)};
-  const T dy[3] = {fma(T(0.5), uy2, -huy), -uy2, fma(T(0.5), uy2, huy)};
-  const T px[3] = {c.half_theta + dx[0], c.one_m_theta - ux2, c.half_theta + dx[2]};
-  const T py[3] = {c.half_theta + dy[0], c.one_m_theta - uy2, c.half_theta + dy[2]};
+  // Shifted forms need dP exactly (no cancellation against W); the absolute form
+  // only needs P, one operation cheaper per axis.
+  T dx[3], dy[3], px[3], py[3];
+  if constexpr (SHIFT) {
+    dx[0] = fma(T(0.5), ux2, -hux), dx[1] = -ux2, dx[2] = fma(T(0.5), ux2, hux);
+    dy[0] = fma(T(0.5), uy2, -huy), dy[1] = -uy2, dy[2] = fma(T(0.5), uy2, huy);
+    px[0] = c.half_theta + dx[0], px[1] = c.one_m_theta - ux2, px[2] = c.half_theta + dx[2];
+    py[0] = c.half_theta + dy[0], py[1] = c.one_m_theta - uy2, py[2] = c.half_theta + dy[2];
+  } else {
+    const T hx = fma(T(0.5), ux2, c.half_theta), hy = fma(T(0.5), uy2, c.half_theta);
+    px[0] = hx - hux, px[1] = c.one_m_theta - ux2, px[2] = hx + hux;
+    py[0] = hy - huy, py[1] = c.one_m_theta - uy2, py[2] = hy + huy;
+  }
 
   if constexpr (MODEL == 0) {
     // LBGK: f* = f + (f^eq - f)/tau = (1 - 1/tau) f + (1/tau) f^eq.
