@@ -34,15 +34,17 @@ BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}
 # Algorithmic FP64 operations per node of one fused step (each add, mul or FMA is
 # one operation, i.e. one FP64 pipe issue), counted from the product-form
 # collision: 33 shared (moments 16, 1/rho 3, u 2, u^2 2, u/2 2, P 8), the
-# model part (LBGK 22, OReg 56, partial 66, complete 89) and the fused
-# diagnostics (7). The FP64 form is bound by the FP64 pipe on GB300.
-FP64_OPS_PER_NODE = {"lbgk": 62, "oreg": 96, "partial": 106, "complete": 129}
+# model part (LBGK 22, OReg 56, partial 66, complete 89; complete with the Eq. 12
+# prefactor from f^neq 83) and the fused diagnostics (7). The FP64 form is bound by
+# the FP64 pipe on GB300.
+FP64_OPS_PER_NODE = {"lbgk": 62, "oreg": 96, "partial": 106, "complete": 129, "complete_neq": 123}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch from the ncu capture of
-# the current kernel (profiles/step_kernel_<prec>_complete_2048.md, 2048^2, scaled to the
+# the current kernels (profiles/step_kernel_f64_complete_2048.md and
+# profiles/step_stream_kernel_f32_complete_2048.md, 2048^2, scaled to the
 # lattice by node count since traffic grows with it). Keyed by (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.7, ("f32", "complete"): 60.7}
-MODEL_NAMES = ["lbgk", "oreg", "partial", "complete"]
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.7, ("f32", "complete"): 60.3}
+MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 
 
 def parse_args():
@@ -560,7 +562,7 @@ def paper_experiments(args):
     from paper_2602_21242_gb300 import experiments
 
     torch.cuda.set_device(0)
-    models = ["lbgk", "oreg", "partial", "complete"]
+    models = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
     mas = [round(0.1 * k, 1) for k in range(1, 11)]
     table = {}
     for theta in (0.25, 1.0 / 3.0, 0.4, 0.5):

@@ -13,6 +13,9 @@
  *   LBM_OREG           g = f^OReg                            (Eq. 2)
  *   LBM_OREG_PARTIAL   g = f^OReg + Psi^P                    (Eqs. 7, 14)
  *   LBM_OREG_COMPLETE  g = f^OReg + Psi^C, with Pi~ from Eqs. 11b and 12 (Eqs. 7, 15)
+ *   LBM_OREG_COMPLETE_NEQ  as LBM_OREG_COMPLETE with Eq. 12's strain estimate taken
+ *                      from f^neq instead of f^OReg (pref = -N_d / (2 theta^2)), with
+ *                      which the corrected stress equals Pi^NS exactly (Eq. 7)
  *
  * Conventions shared by every call:
  *   - Fields are row-major [y][x] (x fastest), nx * ny doubles, unpadded.
@@ -41,12 +44,13 @@ extern "C" {
 
 typedef struct lbm_ctx lbm_ctx;
 
-/* Collision models (Sec. 4). */
+/* Collision models (Sec. 4; model 4 is the f^neq variant of Eq. 12's prefactor). */
 enum lbm_model {
   LBM_LBGK = 0,
   LBM_OREG = 1,
   LBM_OREG_PARTIAL = 2,
-  LBM_OREG_COMPLETE = 3
+  LBM_OREG_COMPLETE = 3,
+  LBM_OREG_COMPLETE_NEQ = 4
 };
 
 /* Storage / arithmetic forms.

@@ -137,7 +137,8 @@ template <int PREC> struct Adjoint {
       case 0: return step_m<0>(fbuf, lam_next, lam, g, c, st);
       case 1: return step_m<1>(fbuf, lam_next, lam, g, c, st);
       case 2: return step_m<2>(fbuf, lam_next, lam, g, c, st);
-      default: return step_m<3>(fbuf, lam_next, lam, g, c, st);
+      case 3: return step_m<3>(fbuf, lam_next, lam, g, c, st);
+      default: return step_m<4>(fbuf, lam_next, lam, g, c, st);
     }
   }
 

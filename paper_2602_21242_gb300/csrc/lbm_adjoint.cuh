@@ -91,12 +91,12 @@ __device__ __forceinline__ void collide_vjp(const T (&f)[9], const T (&mu)[9], c
       A1b = A1b + Mx * ux * (c.c3 - ux2) - My * uy * (c.c3 - uy2);
       uxb = fma(Mx * A1, c.c3 - T(3.0) * ux2, uxb);
       uyb = uyb - My * A1 * (c.c3 - T(3.0) * uy2);
-    } else if constexpr (MODEL == 3) {
-      // Psi^C through h = omega' pref / 2 = mq A1 (mu_xx' + mu_yy'), the halved
-      // Pi~ terms hPxx = -h Fx, hPyy = h Fy, qPxy = h G / 2 and hps = psi' / 2.
+    } else if constexpr (MODEL >= 3) {
+      // Psi^C through h = omega' pref / 2 (model 3: mq A1 (mu_xx' + mu_yy'); model 4:
+      // -A1 / 2), the halved Pi~ terms hPxx = -h Fx, hPyy = h Fy, qPxy = h G / 2 and hps = psi' / 2.
       const T muxx = (c.theta - ux2) * px[1];
       const T muyy = (c.theta - uy2) * py[1];
-      const T h = c.mq_inv2t2 * A1 * (muxx + muyy);
+      const T h = MODEL == 3 ? c.mq_inv2t2 * A1 * (muxx + muyy) : T(-0.5) * A1;
       const T Fx = fma(ux2, ux2 - T(1.0), c.tt), Fy = fma(uy2, uy2 - T(1.0), c.tt);
       const T G = ux * uy * (ux2 - uy2);
       const T Sd = (mu[5] + mu[7]) + (mu[6] + mu[8]);
@@ -116,12 +116,17 @@ __device__ __forceinline__ void collide_vjp(const T (&f)[9], const T (&mu)[9], c
       const T dGy = ux * fma(T(-3.0), uy2, ux2);
       uxb = uxb + h * (T(0.5) * qPxyb * dGx - hPxxb * dFx);
       uyb = uyb + h * (hPyyb * dFy + T(0.5) * qPxyb * dGy);
-      // through h = mq A1 (mu_xx' + mu_yy'), d mu_aa'/du_a = -2 u_a (1 - 2 u_a^2)
+      // through h: model 3, h = mq A1 (mu_xx' + mu_yy') with d mu_aa'/du_a = -2 u_a (1 - 2 u_a^2);
+      // model 4, h = -A1 / 2
       const T hb = hPyyb * Fy - hPxxb * Fx + T(0.5) * qPxyb * G;
-      A1b = fma(hb * c.mq_inv2t2, muxx + muyy, A1b);
-      const T hA = hb * c.mq_inv2t2 * A1;
-      uxb = fma(hA * T(-2.0) * ux, fma(T(-2.0), ux2, T(1.0)), uxb);
-      uyb = fma(hA * T(-2.0) * uy, fma(T(-2.0), uy2, T(1.0)), uyb);
+      if constexpr (MODEL == 3) {
+        A1b = fma(hb * c.mq_inv2t2, muxx + muyy, A1b);
+        const T hA = hb * c.mq_inv2t2 * A1;
+        uxb = fma(hA * T(-2.0) * ux, fma(T(-2.0), ux2, T(1.0)), uxb);
+        uyb = fma(hA * T(-2.0) * uy, fma(T(-2.0), uy2, T(1.0)), uyb);
+      } else {
+        A1b = fma(T(-0.5), hb, A1b);
+      }
     }
     // through A1 = k1 (D - rho (u_x^2 - u_y^2)) and A2 = k2 (Pi_xy - rho u_x u_y)
     const T Db = c.k1 * A1b;

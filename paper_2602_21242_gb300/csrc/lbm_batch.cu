@@ -337,7 +337,8 @@ cudaError_t launch_batch_step_p(const lbm_batch* b, bool diag, int parity, cudaS
     case 0: return launch_batch_step<PREC, 0>(b, diag, parity, st);
     case 1: return launch_batch_step<PREC, 1>(b, diag, parity, st);
     case 2: return launch_batch_step<PREC, 2>(b, diag, parity, st);
-    default: return launch_batch_step<PREC, 3>(b, diag, parity, st);
+    case 3: return launch_batch_step<PREC, 3>(b, diag, parity, st);
+    default: return launch_batch_step<PREC, 4>(b, diag, parity, st);
   }
 }
 
@@ -380,7 +381,8 @@ cudaError_t launch_persistent_p(lbm_batch* b, int n, int parity0, cudaStream_t s
     case 0: return launch_persistent<PREC, 0>(b, n, parity0, st);
     case 1: return launch_persistent<PREC, 1>(b, n, parity0, st);
     case 2: return launch_persistent<PREC, 2>(b, n, parity0, st);
-    default: return launch_persistent<PREC, 3>(b, n, parity0, st);
+    case 3: return launch_persistent<PREC, 3>(b, n, parity0, st);
+    default: return launch_persistent<PREC, 4>(b, n, parity0, st);
   }
 }
 
@@ -401,7 +403,7 @@ extern "C" {
 int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, const double* tau, int model,
                      int prec, void* stream, lbm_batch** out) {
   if (!out || n < 1 || !nx || !ny || !theta || !tau) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: bad arguments");
-  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE) return bfail(nullptr, LBM_EINVAL, "unknown model %d", model);
+  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ) return bfail(nullptr, LBM_EINVAL, "unknown model %d", model);
   if (prec < LBM_F64 || prec > LBM_F16_SHIFT) return bfail(nullptr, LBM_EINVAL, "unknown storage form %d", prec);
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation failed");

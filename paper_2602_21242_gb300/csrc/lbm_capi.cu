@@ -125,7 +125,7 @@ int olbm::set_thread_error(int status, const char* fmt, ...) {
 
 extern "C" {
 
-int lbm_version(void) { return (1 << 16) | 0; }
+int lbm_version(void) { return (1 << 16) | 1; }
 
 int lbm_layout(int nx, int ny, int prec, long long* pitch, long long* plane, long long* state_bytes) {
   return layout_of(nx, ny, prec, pitch, plane, state_bytes) ? LBM_OK : LBM_EINVAL;
@@ -140,7 +140,7 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   if (!(theta > 0.0 && theta < 1.0)) return fail(nullptr, LBM_EINVAL, "theta must lie in (0, 1), got %g", theta);
   if (!(tau > 0.5) || !std::isfinite(tau))
     return fail(nullptr, LBM_EINVAL, "tau must exceed 1/2 (positive viscosity), got %g", tau);
-  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE)
+  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ)
     return fail(nullptr, LBM_EINVAL, "unknown collision model %d", model);
   if (d_pop_buffers && (reinterpret_cast<uintptr_t>(d_pop_buffers) % 256) != 0)
     return fail(nullptr, LBM_EINVAL, "population buffers must be 256-byte aligned");

@@ -277,10 +277,16 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
         cor[2] = T(-0.5) * wpsy;
         cor[4] = T(0.5) * wpsy;
       } else {
-        // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12 (evaluated on f^OReg).
-        const T muxx = (c.theta - ux2) * px[1];  // 2 theta^2 mu_xx
-        const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
-        const T hwpref = c.mq_inv2t2 * A1 * (muxx + muyy);  // omega' pref / 2
+        // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12, evaluated on f^OReg (model 3):
+        // pref = -(K1/2)(mu_xx + mu_yy); or on f^neq (model 4): pref = -K1.
+        T hwpref;  // omega' pref / 2
+        if constexpr (MODEL == 3) {
+          const T muxx = (c.theta - ux2) * px[1];  // 2 theta^2 mu_xx
+          const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
+          hwpref = c.mq_inv2t2 * A1 * (muxx + muyy);
+        } else {
+          hwpref = T(-0.5) * A1;
+        }
         const T hPxx = -hwpref * fma(ux2, ux2 - T(1.0), c.tt);       // omega' Pi~_xx / 2
         const T hPyy = hwpref * fma(uy2, uy2 - T(1.0), c.tt);        // omega' Pi~_yy / 2
         const T qPxy = T(0.5) * hwpref * (ux * uy) * (ux2 - uy2);  // omega' Pi~_xy / 4

@@ -495,6 +495,7 @@ template <int PREC> struct Launch {
       case 1: return step_m<1>(a, st);
       case 2: return step_m<2>(a, st);
       case 3: return step_m<3>(a, st);
+      case 4: return step_m<4>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }

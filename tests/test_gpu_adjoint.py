@@ -49,7 +49,7 @@ def dot(grads, v):
     return sum(float((gk * vk).sum()) for gk, vk in zip(grads, v))
 
 
-@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("theta", [1.0 / 3.0, 0.4])
 def test_vjp_matches_oracle_complex_step(oracle, model, theta):
     n, steps, k = 20, 30, 7  # segments of 7, 7, 7, 7, 2 steps
@@ -60,7 +60,7 @@ def test_vjp_matches_oracle_complex_step(oracle, model, theta):
     assert dot(grads, v) == pytest.approx(want, rel=1e-10)
 
 
-@pytest.mark.parametrize("model", [0, 3])
+@pytest.mark.parametrize("model", [0, 3, 4])
 def test_vjp_every_component_small_grid(oracle, model):
     """Full gradient on a 4 x 3 grid, each input component by its own complex step."""
     nx, ny, theta, steps = 4, 3, 0.35, 9

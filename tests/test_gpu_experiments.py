@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 
 def oracle_nu_ratio(oracle, model, theta, ma, n, nu, steps, t_fit, orientation):
-    m = {"lbgk": 0, "oreg": 1, "partial": 2, "complete": 3}[model]
+    m = {"lbgk": 0, "oreg": 1, "partial": 2, "complete": 3, "complete_neq": 4}[model]
     tau = tau_from_nu(nu, theta)
     rho, ux, uy = experiments.rotated_shear_wave_fields(n, ma, orientation=orientation)
     f = oracle.run(oracle.init(rho, ux, uy, theta), theta, tau, m, t_fit)
@@ -28,7 +28,7 @@ def oracle_nu_ratio(oracle, model, theta, ma, n, nu, steps, t_fit, orientation):
 
 
 @pytest.mark.parametrize("orientation", ["axis", "diagonal"])
-@pytest.mark.parametrize("model", ["lbgk", "oreg", "partial", "complete"])
+@pytest.mark.parametrize("model", ["lbgk", "oreg", "partial", "complete", "complete_neq"])
 def test_rotated_shear_wave_measurement_matches_oracle(oracle, model, orientation):
     n, theta, ma, nu, steps, t_fit = 32, 0.4, 0.3, 0.005, 300, 50
     got = experiments.rotated_shear_wave_viscosity(model, theta, ma, n=n, nu=nu, steps=steps, t_fit=t_fit,

@@ -52,7 +52,7 @@ SIZES = [(37, 23), (64, 64), (100, 3), (1, 5), (5, 1), (1, 1), (33, 9)]
 
 
 @pytest.mark.parametrize("nx,ny", SIZES)
-@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("theta", [0.25, 1.0 / 3.0, 0.4])
 def test_random_state_parity_f64(oracle, nx, ny, model, theta):
     """Generic non-equilibrium populations, 100 steps, tau = 0.8."""
@@ -62,7 +62,7 @@ def test_random_state_parity_f64(oracle, nx, ny, model, theta):
     assert_rel(got, ref, REL_F64, f"{nx}x{ny} model {model} theta {theta:.3f}")
 
 
-@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 def test_taylor_green_parity_f64(oracle, model):
     """Taylor-Green at 64^2, theta = 1/3, nu = 0.01, u0 = 0.05, through lbm_init and lbm_moments."""
     n, theta, nu, u0 = 64, 1.0 / 3.0, 0.01, 0.05

@@ -424,3 +424,25 @@ def test_complex_step_run_matches_finite_difference(oracle):
         e = 1e-6
         d_fd = (loss(e, False) - loss(-e, False)) / (2 * e)
         assert d_cs == pytest.approx(d_fd, rel=1e-6)
+
+
+@pytest.mark.parametrize("theta", THETAS + [0.6])
+def test_complete_neq_variant_recovers_the_ns_stress_exactly(oracle, theta):
+    """Model 4 takes Eq. 12's strain estimate from f^neq: pref = -N_d/(2 theta^2), with which
+    Eq. 11b makes sum cc f^GOReg = Pi^NS = (N_d, -N_d, N_xy) exactly (Eq. 7), so the post-collision
+    stress is (1 - 1/tau) times the traceless Pi^neq at any theta; mass and momentum are conserved."""
+    g = flows.rng(51)
+    tau = 0.7
+    for _ in range(20):
+        f = random_node(g, theta)
+        rho, ux, uy, pxx, pyy, pxy = moments_np(f)
+        _, _, _, Nd, Nxy = neq_tensor(f, theta)
+        fs = oracle.collide_node(f, theta, tau, 4)
+        peq = np.array([rho * (ux * ux + theta), rho * (uy * uy + theta), rho * ux * uy])
+        got = np.array([(CX * CX * fs).sum(), (CY * CY * fs).sum(), (CX * CY * fs).sum()]) - peq
+        np.testing.assert_allclose(got, (1 - 1 / tau) * np.array([Nd, -Nd, Nxy]), rtol=0, atol=4e-15 * f.sum())
+        np.testing.assert_allclose(fs.sum(), rho, rtol=2e-15)
+        np.testing.assert_allclose([(CX * (fs - f)).sum(), (CY * (fs - f)).sum()], 0.0, atol=2e-16)
+    # equilibrium is a fixed point
+    feq = oracle.geq(0.95, -0.06, 0.09, theta)
+    np.testing.assert_allclose(oracle.collide_node(feq, theta, 0.57, 4), feq, rtol=0, atol=1e-15)

@@ -29,7 +29,7 @@ def _interior(buf, nx, ny, pitch, plane):
     return buf.reshape(9, plane)[:, : pitch * ny].reshape(9, ny, pitch)[:, :, :nx]
 
 
-@pytest.mark.parametrize("model,nx,ny", [(3, 96, 40), (0, 37, 23), (2, 300, 70)])
+@pytest.mark.parametrize("model,nx,ny", [(3, 96, 40), (0, 37, 23), (2, 300, 70), (4, 64, 33)])
 def test_noalloc_matches_regular_step_twice(model, nx, ny):
     if not torch.cuda.is_available():
         pytest.fail("GPU test needs a CUDA device")
