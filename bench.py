@@ -556,7 +556,9 @@ def paper_experiments(args):
     """Sec. 5.1: nu~/nu of the rotated decaying shear wave (N = 200, nu = 1e-3, 1200 steps) for the four
     models, theta in {0.25, 1/3, 0.4, 0.5}, Ma = 0.1 .. 1.0 (0 = the run became non-finite).
     Sec. 5.3: the doubly periodic shear layer (kappa = 80, delta = 0.05, u0 = 0.04, Re = 3e4) to one
-    turnover time for N in {128, 256, 512}, theta in {0.4, 0.6}: whether each model stays finite."""
+    turnover time for N in {128, 256, 512}, theta in {0.4, 0.6}: whether each model stays finite.
+    Sec. 5.2: the isothermal shocktube (800 x 1, bounce-back walls, 400 steps) at (theta, nu) =
+    (0.4, 1e-12) and (0.55, 1e-9) against the exact isothermal Riemann solution."""
     import torch
 
     from paper_2602_21242_gb300 import experiments
@@ -577,8 +579,17 @@ def paper_experiments(args):
                 layer[f"{model}/theta={theta}/N={n}"] = {
                     "finite": finite, "steps": steps,
                     "max_abs_vorticity": None if w is None else float(abs(w).max())}
-    print(json.dumps({"experiments": "paper Sec. 5.1 and 5.3", "rotated_shear_wave": {"Ma": mas, "nu_ratio": table},
-                      "shear_layer": layer}), flush=True)
+    tube = {}
+    for theta, nu in ((0.4, 1e-12), (0.55, 1e-9)):
+        for model in models:
+            r = experiments.shocktube_run(model, theta, nu)
+            tube[f"{model}/theta={theta}/nu={nu:g}"] = {
+                k: r[k] for k in ("finite", "l1_rho", "l1_ux", "plateau_rho", "plateau_ux", "rho_star", "u_star",
+                                  "tv_excess") if k in r}
+    print(json.dumps({"experiments": "paper Sec. 5.1, 5.2 and 5.3",
+                      "rotated_shear_wave": {"Ma": mas, "nu_ratio": table}, "shear_layer": layer,
+                      "shocktube": {"grid": "800 x 1, fullway bounce-back walls at x = 0 and 799, 400 steps",
+                                    "rho_l_rho_r": list(experiments.SHOCKTUBE_RHO), "runs": tube}}), flush=True)
 
 
 def main():

@@ -135,6 +135,21 @@ int lbm_step(lbm_ctx* ctx, int n);
 int lbm_set_diagnostics_interval(lbm_ctx* ctx, int every);
 
 /*
+ * Fullway bounce-back walls (the wall treatment of Sec. 5.2's shocktube). h_mask:
+ * HOST array of nx * ny bytes, row-major [y][x]; a nonzero byte makes that node
+ * a wall: in every later step (lbm_step, lbm_run_host, the forward and reverse
+ * sweeps of lbm_vjp) the node does not collide but returns each population the
+ * way it came, f*_i = f_ibar with c_ibar = -c_i. NULL removes all walls (the
+ * default: doubly periodic). Wall nodes keep populations; moments, state copies
+ * and diagnostics cover them like any node (bounce-back conserves each node's
+ * mass, so total mass stays conserved; momentum does not). *h_count (may be
+ * NULL) receives the number of wall nodes. Synchronous: waits for the lattice's
+ * stream, then uploads the list. The mask is copied; the caller keeps it.
+ * Errors: LBM_ENOMEM, LBM_ECUDA; the previous walls are gone after a failure.
+ */
+int lbm_set_walls(lbm_ctx* ctx, const unsigned char* h_mask, long long* h_count);
+
+/*
  * Latest diagnostics reduced inside lbm_step: h_out5 as in lbm_diagnostics,
  * *h_time = the time t they describe (-1 if none yet). Synchronises the stream.
  * Returns LBM_ENONFINITE if any fused pass so far met a non-finite population.

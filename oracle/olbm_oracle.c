@@ -12,6 +12,9 @@
  *     c4=(0,-1), c5=(1,1), c6=(-1,1), c7=(-1,-1), c8=(1,-1).
  *   - Fields are stored [i][y][x], x fastest, doubly periodic, node-centred
  *     coordinates x = 0..nx-1, y = 0..ny-1.
+ *   - Optional wall nodes (a byte mask [y][x]) use fullway bounce-back, the
+ *     wall treatment of the shocktube (Sec. 5.2): they reverse every population
+ *     instead of colliding.
  *   - The state is the set of PRE-collision populations f_i(x, t). One step is
  *     collide everywhere (Eq. 1a), then propagate f*_i(x) to x + c_i (Eq. 1b).
  *   - Initial state: f(x, 0) = f^eq(rho0(x), u0(x)) (Eq. 10).
@@ -55,7 +58,7 @@ static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 /* Exported entry points (called through ctypes by oracle/oracle.py).        */
 /* ------------------------------------------------------------------------- */
 
-int oracle_version(void) { return 1; }
+int oracle_version(void) { return 2; }
 
 int oracle_set_threads(int n) {
 #ifdef _OPENMP
@@ -114,15 +117,16 @@ void oracle_init(int nx, int ny, double theta, const double* rho, const double* 
 
 /*
  * nsteps LBE steps (Eq. 1) in place on f (9 * nx * ny pre-collision values);
- * work is caller scratch of the same size.
+ * work is caller scratch of the same size. walls: NULL, or nx * ny flags
+ * (nonzero = fullway bounce-back node).
  */
-void oracle_run(int nx, int ny, double theta, double tau, int model, int nsteps, double* f,
-                double* work) {
+void oracle_run_walls(int nx, int ny, double theta, double tau, int model, int nsteps,
+                      const unsigned char* walls, double* f, double* work) {
   const size_t n9 = (size_t)9 * nx * ny;
   double* a = f;
   double* b = work;
   for (int s = 0; s < nsteps; ++s) {
-    r_step(a, b, nx, ny, theta, tau, model);
+    r_step(a, b, nx, ny, theta, tau, model, walls);
     double* t = a;
     a = b;
     b = t;
@@ -130,20 +134,30 @@ void oracle_run(int nx, int ny, double theta, double tau, int model, int nsteps,
   if (a != f) memcpy(f, a, n9 * sizeof(double));
 }
 
-/* Complex-step twin of oracle_run: f and work are interleaved (re, im) pairs. */
-void oracle_run_cplx(int nx, int ny, double theta, double tau, int model, int nsteps,
-                     double* f_ri, double* work_ri) {
+void oracle_run(int nx, int ny, double theta, double tau, int model, int nsteps, double* f,
+                double* work) {
+  oracle_run_walls(nx, ny, theta, tau, model, nsteps, NULL, f, work);
+}
+
+/* Complex-step twin of oracle_run_walls: f and work are interleaved (re, im) pairs. */
+void oracle_run_walls_cplx(int nx, int ny, double theta, double tau, int model, int nsteps,
+                           const unsigned char* walls, double* f_ri, double* work_ri) {
   const size_t n9 = (size_t)9 * nx * ny;
   double _Complex* a = (double _Complex*)f_ri;
   double _Complex* b = (double _Complex*)work_ri;
   double _Complex* f = a;
   for (int s = 0; s < nsteps; ++s) {
-    z_step(a, b, nx, ny, theta, tau, model);
+    z_step(a, b, nx, ny, theta, tau, model, walls);
     double _Complex* t = a;
     a = b;
     b = t;
   }
   if (a != f) memcpy(f, a, n9 * sizeof(double _Complex));
+}
+
+void oracle_run_cplx(int nx, int ny, double theta, double tau, int model, int nsteps,
+                     double* f_ri, double* work_ri) {
+  oracle_run_walls_cplx(nx, ny, theta, tau, model, nsteps, NULL, f_ri, work_ri);
 }
 
 /* Complex-step twin of oracle_init (inputs and output interleaved re, im). */

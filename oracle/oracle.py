@@ -67,6 +67,8 @@ def _load():
             "oracle_init": ([i, i, d, p, p, p, p], None),
             "oracle_run": ([i, i, d, d, i, i, p, p], None),
             "oracle_run_cplx": ([i, i, d, d, i, i, p, p], None),
+            "oracle_run_walls": ([i, i, d, d, i, i, p, p, p], None),
+            "oracle_run_walls_cplx": ([i, i, d, d, i, i, p, p, p], None),
             "oracle_init_cplx": ([i, i, d, p, p, p, p], None),
             "oracle_collide_node_cplx": ([p, d, d, i, p], None),
             "oracle_moments_field": ([i, i, p, p, p, p], None),
@@ -166,23 +168,37 @@ def init(rho, ux, uy, theta: float) -> np.ndarray:
     return f
 
 
-def run(f, theta: float, tau: float, model: int, nsteps: int) -> np.ndarray:
-    """Advance pre-collision populations (9, ny, nx) by nsteps LBE steps (Eq. 1); returns a new array."""
+def _walls(walls, ny, nx):
+    if walls is None:
+        return None, None
+    w = np.ascontiguousarray(np.asarray(walls) != 0, dtype=np.uint8)
+    if w.shape != (ny, nx):
+        raise ValueError(f"walls must have shape {(ny, nx)}, got {w.shape}")
+    return w, _ptr(w)
+
+
+def run(f, theta: float, tau: float, model: int, nsteps: int, walls=None) -> np.ndarray:
+    """Advance pre-collision populations (9, ny, nx) by nsteps LBE steps (Eq. 1); returns a new array.
+
+    walls: optional (ny, nx) flags; a nonzero node is a fullway bounce-back wall (Sec. 5.2)."""
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     if f.ndim != 3 or f.shape[0] != 9:
         raise ValueError("populations must have shape (9, ny, nx)")
     _, ny, nx = f.shape
     work = np.empty_like(f)
-    _load().oracle_run(nx, ny, float(theta), float(tau), int(model), int(nsteps), _ptr(f), _ptr(work))
+    w, wp = _walls(walls, ny, nx)
+    _load().oracle_run_walls(nx, ny, float(theta), float(tau), int(model), int(nsteps), wp, _ptr(f), _ptr(work))
     return f
 
 
-def run_cplx(f, theta: float, tau: float, model: int, nsteps: int) -> np.ndarray:
+def run_cplx(f, theta: float, tau: float, model: int, nsteps: int, walls=None) -> np.ndarray:
     """Complex-step twin of run() (complex128 populations)."""
     f = np.array(f, dtype=np.complex128, order="C", copy=True)
     _, ny, nx = f.shape
     work = np.empty_like(f)
-    _load().oracle_run_cplx(nx, ny, float(theta), float(tau), int(model), int(nsteps), _ptr(f), _ptr(work))
+    w, wp = _walls(walls, ny, nx)
+    _load().oracle_run_walls_cplx(nx, ny, float(theta), float(tau), int(model), int(nsteps), wp, _ptr(f),
+                                  _ptr(work))
     return f
 
 

@@ -10,6 +10,8 @@ import ctypes
 import os
 import threading
 
+import numpy as np
+
 from . import build as _build
 
 LBM_LBGK, LBM_OREG, LBM_OREG_PARTIAL, LBM_OREG_COMPLETE, LBM_OREG_COMPLETE_NEQ = 0, 1, 2, 3, 4
@@ -38,6 +40,7 @@ _SIGNATURES = {
     "lbm_init": ([_p, _p, _p, _p], _i),
     "lbm_step": ([_p, _i], _i),
     "lbm_set_diagnostics_interval": ([_p, _i], _i),
+    "lbm_set_walls": ([_p, _p, _pll], _i),
     "lbm_step_diagnostics": ([_p, _pd, _pll], _i),
     "lbm_moments": ([_p, _p, _p, _p], _i),
     "lbm_diagnostics": ([_p, _pd], _i),
@@ -164,6 +167,18 @@ def lbm_step(ctx, n: int) -> None:
 
 def lbm_set_diagnostics_interval(ctx, every: int) -> None:
     check(load().lbm_set_diagnostics_interval(ctx, every), ctx)
+
+
+def lbm_set_walls(ctx, mask) -> int:
+    """Fullway bounce-back wall nodes from a host (ny, nx) mask (nonzero = wall); None removes them.
+    Returns the number of wall nodes."""
+    n = _ll()
+    if mask is None:
+        check(load().lbm_set_walls(ctx, None, ctypes.byref(n)), ctx)
+        return int(n.value)
+    m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+    check(load().lbm_set_walls(ctx, m.ctypes.data, ctypes.byref(n)), ctx)
+    return int(n.value)
 
 
 def lbm_step_diagnostics(ctx, raise_nonfinite: bool = True):

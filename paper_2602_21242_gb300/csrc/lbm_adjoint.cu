@@ -15,6 +15,7 @@
 #include "lbm_adjoint.cuh"
 #include "lbm_ctx.h"
 #include "lbm_kernels.cuh"
+#include "lbm_walls.h"
 
 namespace olbm {
 
@@ -174,7 +175,10 @@ cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
   a.rho_ref = c->rho_ref;
   a.partials = c->d_partials;
   a.cfg = c->cfg;
-  return c->prec == LBM_F64 ? olbm::launch_step_f64(a, c->stream) : olbm::launch_step_f32(a, c->stream);
+  cudaError_t e = c->prec == LBM_F64 ? olbm::launch_step_f64(a, c->stream) : olbm::launch_step_f32(a, c->stream);
+  if (e == cudaSuccess && c->n_walls > 0)
+    e = olbm::launch_walls(c->prec == LBM_F64 ? 8 : 4, src, dst, c->g, c->d_walls, c->n_walls, c->stream);
+  return e;
 }
 
 }  // namespace
@@ -242,6 +246,9 @@ extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, 
       e = c->prec == LBM_F64
               ? olbm::Adjoint<0>::step(c->model, fbuf, lam[li], lam[li ^ 1], c->g, c->theta, c->tau, c->rho_ref, c->stream)
               : olbm::Adjoint<1>::step(c->model, fbuf, lam[li], lam[li ^ 1], c->g, c->theta, c->tau, c->rho_ref, c->stream);
+      if (e == cudaSuccess && c->n_walls > 0)
+        e = olbm::launch_walls_adjoint(c->prec == LBM_F64 ? 8 : 4, lam[li], lam[li ^ 1], c->g, c->d_walls,
+                                       c->n_walls, c->stream);
       if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp adjoint step", e);
       li ^= 1;
     }

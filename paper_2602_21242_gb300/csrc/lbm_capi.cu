@@ -15,6 +15,7 @@
 #include "lbm.h"
 #include "lbm_ctx.h"
 #include "lbm_launch.h"
+#include "lbm_walls.h"
 
 namespace {
 
@@ -110,6 +111,7 @@ void free_ctx(lbm_ctx* c) {
   cudaFree(c->d_err);
   cudaFree(c->d_stage);
   cudaFree(c->d_vjp);
+  cudaFree(c->d_walls);
   delete c;
 }
 
@@ -241,6 +243,50 @@ int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double
   return LBM_OK;
 }
 
+int lbm_set_walls(lbm_ctx* ctx, const unsigned char* h_mask, long long* h_count) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  const long long nodes = nodes_of(ctx);
+  long long n = 0;
+  int2* list = nullptr;
+  if (h_mask) {
+    for (long long k = 0; k < nodes; ++k) n += h_mask[k] != 0;
+    if (n > 0) {
+      list = new (std::nothrow) int2[n];
+      if (!list) return fail(ctx, LBM_ENOMEM, "lbm_set_walls: host list");
+      long long j = 0;
+      for (int y = 0; y < ctx->ny; ++y)
+        for (int x = 0; x < ctx->nx; ++x)
+          if (h_mask[(long long)y * ctx->nx + x]) list[j++] = make_int2(x, y);
+    }
+  }
+  // the previous list may still be read by queued steps
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    delete[] list;
+    return cuda_fail(ctx, e, "lbm_set_walls sync");
+  }
+  cudaFree(ctx->d_walls);
+  ctx->d_walls = nullptr;
+  ctx->n_walls = 0;
+  if (n > 0) {
+    e = cudaMalloc(&ctx->d_walls, sizeof(int2) * (size_t)n);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ctx->d_walls, list, sizeof(int2) * (size_t)n, cudaMemcpyHostToDevice);
+    delete[] list;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ctx->d_walls);
+      ctx->d_walls = nullptr;
+      return fail(ctx, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "lbm_set_walls: %s",
+                  cudaGetErrorString(e));
+    }
+    ctx->n_walls = n;
+  }
+  if (h_count) *h_count = n;
+  return LBM_OK;
+}
+
 int lbm_set_diagnostics_interval(lbm_ctx* ctx, int every) {
   if (!ctx) return LBM_EINVAL;
   if (every < 0) return fail(ctx, LBM_EINVAL, "diagnostics interval must be >= 0");
@@ -271,6 +317,11 @@ int lbm_step(lbm_ctx* ctx, int n) {
     used = ctx->nparts;
     cudaError_t e = launch_step(a, ctx->prec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step launch");
+    if (ctx->n_walls > 0) {
+      e = olbm::launch_walls((int)elem_size(ctx->prec), a.src, a.dst, ctx->g, ctx->d_walls, ctx->n_walls,
+                             ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step walls launch");
+    }
     if (a.diag) {
       e = olbm::launch_finalize(ctx->d_partials, (int)used, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
                                 ctx->d_sticky, ctx->stream);

@@ -32,6 +32,9 @@ struct lbm_ctx {
   // lbm_vjp work memory: checkpoints, recompute ring, adjoint fields (grown on demand)
   void* d_vjp = nullptr;
   size_t vjp_bytes = 0;
+  // fullway bounce-back wall nodes (x, y), applied after every step (lbm_set_walls)
+  int2* d_walls = nullptr;
+  long long n_walls = 0;
   char err[320] = {0};
 };
 

@@ -10,6 +10,7 @@ Example::
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import capi
@@ -106,6 +107,17 @@ class Lattice:
 
     def set_diagnostics_interval(self, every: int) -> None:
         capi.lbm_set_diagnostics_interval(self._ctx, int(every))
+
+    def set_walls(self, mask) -> int:
+        """Fullway bounce-back wall nodes, (ny, nx) host mask (numpy or CPU tensor; nonzero = wall),
+        None = doubly periodic. Returns the number of wall nodes."""
+        if mask is not None:
+            if isinstance(mask, torch.Tensor):
+                mask = mask.detach().cpu().numpy()
+            if tuple(np.shape(mask)) != (self.ny, self.nx):
+                raise ValueError(f"wall mask must have shape {(self.ny, self.nx)}")
+        with torch.cuda.device(self.device):
+            return capi.lbm_set_walls(self._ctx, mask)
 
     def step_diagnostics(self, raise_nonfinite: bool = True):
         with torch.cuda.device(self.device):

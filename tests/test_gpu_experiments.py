@@ -66,3 +66,23 @@ def test_shear_layer_lbgk_fails_where_oreg_holds():
     ok_c, _, w_c = experiments.shear_layer_run("complete", 0.6, 128)
     assert ok_c and np.abs(w_c).max() < 0.05
     assert (not ok_l) or np.abs(w_l).max() > 1.0
+
+
+def test_shocktube_matches_the_paper_statements():
+    """Sec. 5.2, (theta, nu) = (0.4, 1e-12): LBGK shows large oscillations; the uncorrected model is
+    free of them but its middle-state density is low while its velocity is right; the partially and
+    completely corrected models recover the exact middle state. (0.55, 1e-9): LBGK is unphysical; the
+    uncorrected model keeps its deficiency; the corrected ones stay accurate, oscillations small."""
+    r = {m: experiments.shocktube_run(m, 0.4, 1e-12) for m in ("lbgk", "oreg", "partial", "complete")}
+    rs, us = r["oreg"]["rho_star"], r["oreg"]["u_star"]
+    assert r["lbgk"]["tv_excess"] > 1.0
+    assert r["oreg"]["tv_excess"] < 0.02
+    assert rs - r["oreg"]["plateau_rho"] > 2e-3 and abs(r["oreg"]["plateau_ux"] - us) < 1e-3
+    for m in ("partial", "complete"):
+        assert abs(r[m]["plateau_rho"] - rs) < 2e-4 and abs(r[m]["plateau_ux"] - us) < 2e-4
+        assert r[m]["tv_excess"] < 0.02 and r[m]["l1_rho"] < 0.5 * r["oreg"]["l1_rho"]
+    r = {m: experiments.shocktube_run(m, 0.55, 1e-9) for m in ("lbgk", "oreg", "partial", "complete")}
+    assert (not r["lbgk"]["finite"]) or r["lbgk"]["l1_rho"] > 1.0
+    assert rs - r["oreg"]["plateau_rho"] > 2e-3
+    for m in ("partial", "complete"):
+        assert abs(r[m]["plateau_rho"] - rs) < 2e-4 and r[m]["tv_excess"] < 0.2

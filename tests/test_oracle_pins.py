@@ -188,7 +188,7 @@ def test_pref_and_pitilde_closed_forms(oracle, theta):
 
 # --------------------------------------------------------------------------- collision (Eq. 1a)
 
-@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("theta", THETAS)
 def test_collision_conservation(oracle, model, theta):
     """Mass is conserved by every model; momentum by LBGK, partial and complete; the uncorrected
@@ -227,7 +227,7 @@ def test_collision_second_moments(oracle, theta):
             np.testing.assert_allclose(got, expect, rtol=0, atol=4e-15 * np.abs(f).sum())
 
 
-@pytest.mark.parametrize("model", [0, 1, 2, 3])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 def test_equilibrium_is_fixed_point(oracle, model):
     """f = f^eq is left unchanged by every collision (f^neq = 0 => g = 0)."""
     for theta in THETAS:
@@ -446,3 +446,67 @@ def test_complete_neq_variant_recovers_the_ns_stress_exactly(oracle, theta):
     # equilibrium is a fixed point
     feq = oracle.geq(0.95, -0.06, 0.09, theta)
     np.testing.assert_allclose(oracle.collide_node(feq, theta, 0.57, 4), feq, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- fullway bounce-back walls (Sec. 5.2)
+
+def _mirror_x(f):
+    """Reflect pre-collision populations x -> nx - 1 - x: population i goes to the one with c_x negated."""
+    perm = [int(np.flatnonzero((CX == -CX[i]) & (CY == CY[i]))[0]) for i in range(9)]
+    return f[perm][:, :, ::-1].copy()
+
+
+@pytest.mark.parametrize("i,start", [(1, 2), (3, 5), (5, 3)])
+def test_bounce_back_returns_a_pulse_reversed(oracle, i, start):
+    """Streaming only (no collision in the fluid): a pulse travelling along c_i reaches the wall
+    column after d steps, is sent back along -c_i and is at its start node, reversed, after 2 d."""
+    nx, ny = 9, 4
+    walls = np.zeros((ny, nx), dtype=np.uint8)
+    walls[:, 0] = walls[:, nx - 1] = 1
+    f = np.zeros((9, ny, nx))
+    f[i, 1, start] = 1.0
+    cx, cy = int(CX[i]), int(CY[i])
+    d = (nx - 1 - start) if cx > 0 else start  # steps to the wall column
+    out = oracle.run(f, 1 / 3, 0.7, oracle.NO_COLLISION, 2 * d, walls=walls)
+    ibar = int(np.flatnonzero((CX == -cx) & (CY == -cy))[0])
+    want = np.zeros_like(f)
+    want[ibar, 1, start] = 1.0  # the y drift of a diagonal pulse cancels on the way back
+    np.testing.assert_array_equal(out, want)
+
+
+@pytest.mark.parametrize("model", [0, 1, 3, 4])
+def test_closed_box_conserves_mass_and_keeps_rest(oracle, model):
+    """Walls on all four sides of a random state: bounce-back and collision both conserve each
+    node's mass, so the total over all nodes (fluid and wall) stays fixed; a fluid at rest stays at
+    rest exactly (f^eq(rho, 0) is symmetric under c -> -c)."""
+    nx, ny, theta = 14, 11, 0.4
+    walls = np.zeros((ny, nx), dtype=np.uint8)
+    walls[0, :] = walls[-1, :] = walls[:, 0] = walls[:, -1] = 1
+    g = flows.rng(61)
+    f = np.stack([random_node(g, theta, 0.2) for _ in range(nx * ny)], axis=1).reshape(9, ny, nx)
+    out = oracle.run(f, theta, 0.6, model, 60, walls=walls)
+    assert math.fsum(out.ravel()) == pytest.approx(math.fsum(f.ravel()), rel=1e-13)
+    rest = oracle.init(np.full((ny, nx), 1.1), np.zeros((ny, nx)), np.zeros((ny, nx)), theta)
+    np.testing.assert_allclose(oracle.run(rest, theta, 0.6, model, 25, walls=walls), rest, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("model", [0, 2, 3])
+def test_walls_commute_with_mirror_reflection(oracle, model):
+    """A mirror-symmetric wall layout: running the reflected state equals reflecting the run."""
+    nx, ny, theta = 16, 5, 0.35
+    walls = np.zeros((ny, nx), dtype=np.uint8)
+    walls[:, 0] = walls[:, nx - 1] = 1
+    walls[2, 4] = walls[2, nx - 5] = 1
+    g = flows.rng(62)
+    f = np.stack([random_node(g, theta, 0.2) for _ in range(nx * ny)], axis=1).reshape(9, ny, nx)
+    a = oracle.run(f, theta, 0.8, model, 30, walls=walls)
+    b = oracle.run(_mirror_x(f), theta, 0.8, model, 30, walls=walls)
+    np.testing.assert_allclose(_mirror_x(a), b, rtol=1e-12, atol=0)
+
+
+def test_walls_absent_equals_periodic_run(oracle):
+    """An all-zero wall mask is the periodic step."""
+    g = flows.rng(63)
+    f = np.stack([random_node(g, 0.3) for _ in range(6 * 7)], axis=1).reshape(9, 7, 6)
+    np.testing.assert_array_equal(oracle.run(f, 0.3, 0.7, 3, 5, walls=np.zeros((7, 6))),
+                                  oracle.run(f, 0.3, 0.7, 3, 5))
