@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=50, help="lattice steps per end-to-end call")
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 256-domain batched workload")
+    ap.add_argument("--batch-tile", default="", help="kind,bx,by,rows (or bx,by,rows for kind 0) of the batched tiles (default: autotuned)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the 256-domain batched workload (graph and persistent modes) and print its JSON")
     return ap.parse_args()
 
 
@@ -376,7 +379,7 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
     return res
 
 
-def batch_sweep(dev, stream, peak_hbm, steps=1000):
+def batch_sweep(dev, stream, peak_hbm, steps=1000, tile=None):
     """Batched workload: 256 independent Taylor-Green domains, N ~ U{64..512}, theta ~ U[0.25, 0.4],
     nu ~ U[0.002, 0.02], u0 ~ U[0.02, 0.1], completely corrected model, FP32 shifted storage, `steps`
     steps per call; tile shape from the autotuner; graph mode (fused per-domain diagnostics every
@@ -394,7 +397,11 @@ def batch_sweep(dev, stream, peak_hbm, steps=1000):
     rho, ux, uy = ([f[j] for f in fields] for j in range(3))
     res = {}
     with Batch(ns, ns, thetas, taus, "complete", "f32", device=dev, stream=stream) as b:
-        shape, _ = tune.tune_batch(b, steps=10, use_cache=False)
+        if tile is None:
+            shape, _ = tune.tune_batch(b, steps=10, use_cache=False)
+        else:
+            shape = tuple(tile)
+            b.set_launch(*shape)
         nodes = b.total_nodes
         for mode in ("graph", "persistent"):
             b.set_mode(mode)
@@ -599,6 +606,15 @@ def main():
         return
     if args.precision_study:
         precision_study(args)
+        return
+    if args.batch_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        tile = tuple(int(v) for v in args.batch_tile.split(",")) if args.batch_tile else None
+        print(json.dumps(batch_sweep(torch.device("cuda", 0), stream, hbm_peak()[0], args.batch_steps, tile)),
+              flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -221,16 +221,18 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
 
 /*
  * Step-kernel selection (no counterpart in the paper). kind 0: the column kernel
- * of lbm_set_launch. kind 1 (shifted FP32/FP16 forms with nx a multiple of 8;
- * other lattices keep kind 0's kernel): a producer warp streams each output
+ * of lbm_set_launch. kind 1 (shifted FP32/FP16 forms, any nx; FP64 lattices
+ * keep kind 0's kernel): a producer warp streams each output
  * row's nine plane segments into a shared-memory ring with TMA bulk copies and
  * mbarrier transaction counts while consumer warps collide node pairs; the
  * lattice is cut into tiles of 256 (FP32) or 512 (FP16) columns by `rows` rows
  * (1..4096); bx = 0 launches one CTA per tile, bx = k > 0 a persistent grid of k
  * CTAs per SM (capped at the resident count) that takes the tiles round robin
  * (by ignored). Its waits are bounded: a wait that gives up makes lbm_sync and
- * lbm_step_diagnostics return LBM_ETIMEOUT. Same results as kind 0 except the
- * diagnostics' summation order.
+ * lbm_step_diagnostics return LBM_ETIMEOUT. Same results as kind 0 for even nx
+ * (FP32 rounding may differ in the last bit for odd nx, where kind 0 updates
+ * single nodes) except the diagnostics' summation order. Default for the
+ * shifted forms on lattices at least 32 columns wide.
  */
 int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows);
 int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows);
@@ -255,10 +257,20 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
                      int model, int prec, void* stream, lbm_batch** out);
 int lbm_batch_destroy(lbm_batch* b);
 
-/* Tile shape: blocks of bx x by threads (bx a multiple of 32, bx * by <= 512) updating
- * tiles of bx (node pairs: 2 bx) columns x by * rows rows. Rebuilds the tile list. */
+/* Tile shape, launch kind 0 (the column routine): blocks of bx x by threads (bx a
+ * multiple of 32, bx * by <= 512) updating tiles of bx (node pairs: 2 bx) columns x
+ * by * rows rows. Rebuilds the tile list (synchronous). */
 int lbm_batch_set_launch(lbm_batch* b, int bx, int by, int rows);
 int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* ntiles);
+
+/* Launch kind and tile shape. kind 0: as lbm_batch_set_launch. kind 1 (the shifted
+ * forms only; the default there): the bulk-copy pipeline of the single-lattice
+ * kind-1 kernel on tiles of W columns (256 FP32, 512 FP16) x rows rows (1..4096),
+ * any domain width; bx, by are ignored. A domain's results equal those of a single
+ * lattice stepped with the same launch kind. Errors: LBM_EINVAL (kind 1 on FP64
+ * storage, rows out of range). lbm_batch_get_launch_ex also reports the kind. */
+int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows);
+int lbm_batch_get_launch_ex(const lbm_batch* b, int* kind, int* bx, int* by, int* rows, int* ntiles);
 int lbm_batch_set_mode(lbm_batch* b, int mode);  /* enum lbm_batch_mode; default LBM_BATCH_GRAPH */
 /* Fused per-domain diagnostics every M steps in LBM_BATCH_GRAPH mode (0 = off). */
 int lbm_batch_set_diagnostics_interval(lbm_batch* b, int every);

@@ -59,12 +59,15 @@ class Batch:
         capi.lbm_batch_set_mode(self._b, {"graph": capi.LBM_BATCH_GRAPH,
                                           "persistent": capi.LBM_BATCH_PERSISTENT}[mode])
 
-    def set_launch(self, bx: int, by: int, rows: int) -> None:
+    def set_launch(self, *shape) -> None:
+        """(bx, by, rows) for launch kind 0, or (kind, bx, by, rows)."""
+        kind, bx, by, rows = (0, *shape) if len(shape) == 3 else shape
         with torch.cuda.device(self.device):
-            capi.lbm_batch_set_launch(self._b, bx, by, rows)
+            capi.lbm_batch_set_launch_ex(self._b, kind, bx, by, rows)
 
     def launch(self):
-        return capi.lbm_batch_get_launch(self._b)
+        """(kind, bx, by, rows, ntiles)."""
+        return capi.lbm_batch_get_launch_ex(self._b)
 
     def set_diagnostics_interval(self, every: int) -> None:
         capi.lbm_batch_set_diagnostics_interval(self._b, every)

@@ -62,6 +62,8 @@ _SIGNATURES = {
     "lbm_batch_destroy": ([_p], _i),
     "lbm_batch_set_launch": ([_p, _i, _i, _i], _i),
     "lbm_batch_get_launch": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "lbm_batch_set_launch_ex": ([_p, _i, _i, _i, _i], _i),
+    "lbm_batch_get_launch_ex": ([_p] + [ctypes.POINTER(_i)] * 5, _i),
     "lbm_batch_set_mode": ([_p, _i], _i),
     "lbm_batch_set_diagnostics_interval": ([_p, _i], _i),
     "lbm_batch_init": ([_p, _p, _p, _p], _i),
@@ -285,6 +287,17 @@ def lbm_batch_set_launch(b, bx: int, by: int, rows: int) -> None:
 def lbm_batch_get_launch(b):
     v = [_i() for _ in range(4)]
     bcheck(load().lbm_batch_get_launch(b, *[ctypes.byref(x) for x in v]), b)
+    return tuple(x.value for x in v)
+
+
+def lbm_batch_set_launch_ex(b, kind: int, bx: int, by: int, rows: int) -> None:
+    bcheck(load().lbm_batch_set_launch_ex(b, kind, bx, by, rows), b)
+
+
+def lbm_batch_get_launch_ex(b):
+    """(kind, bx, by, rows, ntiles)."""
+    v = [_i() for _ in range(5)]
+    bcheck(load().lbm_batch_get_launch_ex(b, *[ctypes.byref(x) for x in v]), b)
     return tuple(x.value for x in v)
 
 

@@ -5,10 +5,13 @@
 // Layout: one device arena holds every domain's two population buffers (each
 // in the single-lattice layout of lbm_layout). A descriptor table gives each
 // domain's geometry, buffers and collision coefficients in the compute type. A
-// tile work-list cuts every domain into tiles of (bx or 2 bx) columns x (by x rows)
-// rows; one thread block updates one tile with the same column routine as the
-// single-lattice kernel, so a tile's results equal those of a single lattice
-// run with the same launch shape.
+// tile work-list cuts every domain into tiles; one thread block updates one
+// tile with a single-lattice routine, so a tile's results equal those of a
+// single lattice run with the same launch kind. Launch kind 0: tiles of
+// (bx or 2 bx) columns x (by x rows) rows, the column routine. Launch kind 1
+// (shifted forms): tiles of W columns (256 FP32, 512 FP16) x `rows` rows, the
+// bulk-copy pipeline (producer warp, shared-memory ring, consumer warps), any
+// domain width.
 //
 // Two execution modes for lbm_batch_step(n):
 //   LBM_BATCH_GRAPH       n launches of the tile kernel (one per time step),
@@ -112,46 +115,124 @@ __global__ void __launch_bounds__(512) batch_persistent_kernel(const Desc<typena
   }
 }
 
-// Pull-only diagnostics of one tile (FP64), as diag_kernel for one lattice;
-// same block shape and tile as the step kernel.
+// Pull-only diagnostics of one tile (FP64), as diag_kernel for one lattice.
+// A tile spans cols1 columns (cols2 for node-pair domains) x trows rows; the
+// block's threads stride over its nodes.
 template <int PREC>
 __global__ void __launch_bounds__(512) batch_diag_kernel(const Desc<typename Form<PREC>::T>* __restrict__ desc,
-                                                         const int4* __restrict__ tiles, int parity, int rows,
-                                                         double rho_ref, double* __restrict__ partials) {
+                                                         const int4* __restrict__ tiles, int parity, int cols1,
+                                                         int cols2, int trows, double rho_ref,
+                                                         double* __restrict__ partials) {
   using S = typename Form<PREC>::S;
   const int4 tl = tiles[blockIdx.x];
   const Desc<typename Form<PREC>::T> d = desc[tl.x];
   const S* src = static_cast<const S*>(d.buf[parity]);
-  const int per = d.pairs ? 2 : 1;
+  const int w = min(d.pairs ? cols2 : cols1, d.g.nx - tl.y);
+  const int h = min(trows, d.g.ny - tl.z);
+  const int nthreads = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   int bad = 0;
-  for (int q = 0; q < per; ++q) {
-    const int x = tl.y + per * (int)threadIdx.x + q;
-    if (x >= d.g.nx) continue;
-    for (int r = 0; r < rows; ++r) {
-      const int y = tl.z + (int)threadIdx.y + r * (int)blockDim.y;
-      if (y >= d.g.ny) break;
-      long long o[9];
-      pull_offsets(x, y, d.g, o);
-      double m0 = 0.0, jx = 0.0, jy = 0.0;
+  for (int j = tid; j < w * h; j += nthreads) {
+    const int x = tl.y + j % w, y = tl.z + j / w;
+    long long o[9];
+    pull_offsets(x, y, d.g, o);
+    double m0 = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const double f = to_double(src[i * d.g.plane + o[i]]);
-        m0 += f;
-        jx += (double)cx_of(i) * f;
-        jy += (double)cy_of(i) * f;
-      }
-      if (finite_bits(m0)) {
-        v[0] += m0;
-        v[1] += jx;
-        v[2] += jy;
-        v[3] += 0.5 * (jx * jx + jy * jy) / (rho_ref + m0);
-      } else {
-        ++bad;
-      }
+    for (int i = 0; i < 9; ++i) {
+      const double f = to_double(src[i * d.g.plane + o[i]]);
+      m0 += f;
+      jx += (double)cx_of(i) * f;
+      jy += (double)cy_of(i) * f;
+    }
+    if (finite_bits(m0)) {
+      v[0] += m0;
+      v[1] += jx;
+      v[2] += jy;
+      v[3] += 0.5 * (jx * jx + jy * jy) / (rho_ref + m0);
+    } else {
+      ++bad;
     }
   }
   block_diag<double>(v, bad, partials + (long long)blockIdx.x * 5);
+}
+
+// Pipelined tile step (launch kind 1, shifted forms): one CTA per tile of W
+// columns x H rows of one domain, the single-lattice pipeline on that tile.
+template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
+__global__ void __launch_bounds__(NC + 32) batch_stream_kernel(const Desc<float>* __restrict__ desc,
+                                                              const int4* __restrict__ tiles, int parity,
+                                                              double* __restrict__ partials, int H,
+                                                              int* __restrict__ err) {
+  using P = Pipeline<PREC, NC, STAGES>;
+  using S = typename Form<PREC>::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  P pipe(smem);
+  pipe.init();
+  __syncthreads();
+  const int4 tl = tiles[blockIdx.x];
+  const Desc<float>* d = desc + tl.x;
+  const Geometry g = d->g;
+  const int rows = min(H, g.ny - tl.z);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DiagAcc<f32x2> acc;
+  if (warp == P::kConsumerWarps) {
+    pipe.produce(static_cast<const S*>(d->buf[parity]), g, tl.y, tl.z, rows, lane, err);
+    pipe.drain(err);
+  } else if (threadIdx.x < NC) {
+    pipe.template consume<MODEL, DIAG>(static_cast<S*>(d->buf[parity ^ 1]), g, broadcast(d->c), tl.y, tl.z, rows,
+                                       threadIdx.x, lane, acc, err);
+  }
+  if constexpr (DIAG) block_diag_acc(acc, partials + (long long)blockIdx.x * 5);
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// n steps of every domain in one cooperative launch of pipelined CTAs: tiles
+// strided over the grid, a bounded grid barrier between steps. The consumers'
+// stores (generic proxy) reach the next step's bulk copies (async proxy)
+// through a proxy fence on both sides of the barrier. A bounded wait that gives
+// up sets the barrier's error flag, so every CTA leaves at the next barrier.
+template <int MODEL, int PREC, int NC, int STAGES>
+__global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const Desc<float>* __restrict__ desc,
+                                                                         const int4* __restrict__ tiles, int ntiles,
+                                                                         int parity0, int nsteps, int H,
+                                                                         GridBarrier* bar) {
+  using P = Pipeline<PREC, NC, STAGES>;
+  using S = typename Form<PREC>::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  P pipe(smem);
+  pipe.init();
+  __syncthreads();
+  int* err = &bar->err;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool producer = warp == P::kConsumerWarps;
+  DiagAcc<f32x2> acc;  // no fused diagnostics in this mode
+  for (int s = 0; s < nsteps; ++s) {
+    const int parity = (parity0 + s) & 1;
+    if (producer) {
+      fence_proxy_async_global();
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const Desc<float>* d = desc + tl.x;
+        if (!pipe.produce(static_cast<const S*>(d->buf[parity]), d->g, tl.y, tl.z, min(H, d->g.ny - tl.z), lane,
+                          err))
+          break;
+      }
+    } else if (threadIdx.x < NC) {
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const Desc<float>* d = desc + tl.x;
+        if (!pipe.template consume<MODEL, false>(static_cast<S*>(d->buf[parity ^ 1]), d->g, broadcast(d->c), tl.y,
+                                                 tl.z, min(H, d->g.ny - tl.z), threadIdx.x, lane, acc, err))
+          break;
+      }
+      fence_proxy_async_global();
+    }
+    if (!grid_sync(bar, gridDim.x)) break;
+  }
+  if (producer) pipe.drain(err);
 }
 
 // Per-domain fixed-order sums of the tile partials: out[d * 5 + k].
@@ -206,6 +287,7 @@ struct lbm_batch {
   double* d_diag_now = nullptr;
   unsigned long long* d_sticky = nullptr;
   olbm::GridBarrier* d_bar = nullptr;
+  int* d_perr = nullptr;  // set by a bounded wait of the pipelined tile kernel that gave up
   olbm::LaunchCfg cfg{};
   int cur = 0;
   long long t = 0;
@@ -260,8 +342,14 @@ int build_tiles(lbm_batch* b) {
   std::vector<int2> ranges(b->n);
   for (int k = 0; k < b->n; ++k) {
     const olbm::Geometry& g = b->geo[k];
-    const int cols = olbm::uses_pairs(b->prec, g) ? 2 * b->cfg.bx : b->cfg.bx;
-    const int trows = b->cfg.by * b->cfg.rows;
+    int cols, trows;
+    if (b->cfg.kind == 1) {
+      cols = olbm::stream_width(b->prec);
+      trows = b->cfg.rows;
+    } else {
+      cols = olbm::uses_pairs(b->prec, g) ? 2 * b->cfg.bx : b->cfg.bx;
+      trows = b->cfg.by * b->cfg.rows;
+    }
     ranges[k].x = (int)tiles.size();
     for (int y0 = 0; y0 < g.ny; y0 += trows)
       for (int x0 = 0; x0 < g.nx; x0 += cols) tiles.push_back(make_int4(k, x0, y0, 0));
@@ -306,6 +394,7 @@ void free_batch(lbm_batch* b) {
   cudaFree(b->d_diag_now);
   cudaFree(b->d_sticky);
   cudaFree(b->d_bar);
+  cudaFree(b->d_perr);
   delete b;
 }
 
@@ -317,8 +406,74 @@ int check_batch(lbm_batch* b) {
   return LBM_OK;
 }
 
+// Pipeline shape of a shifted storage form (the single-lattice one).
+template <int PREC> struct StreamCfg {
+  static constexpr int NC = PREC == 1 ? olbm::kStreamNC32 : olbm::kStreamNC16;
+  static constexpr int STAGES = olbm::kStreamStages;
+  using Shape = olbm::StreamShape<PREC, NC, STAGES>;
+};
+
+// Opt a pipelined kernel in to its shared-memory ring, once per kernel. Called
+// before any launch or graph capture of the kernel (not during a capture).
+template <auto K> cudaError_t allow_ring(int bytes) {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int PREC, int MODEL> cudaError_t allow_rings() {
+  if constexpr (PREC == 0) {
+    return cudaSuccess;
+  } else {
+    using C = StreamCfg<PREC>;
+    constexpr int bytes = C::Shape::kSmemBytes;
+    cudaError_t e = allow_ring<olbm::batch_stream_kernel<MODEL, PREC, true, C::NC, C::STAGES>>(bytes);
+    if (e == cudaSuccess) e = allow_ring<olbm::batch_stream_kernel<MODEL, PREC, false, C::NC, C::STAGES>>(bytes);
+    if (e == cudaSuccess) e = allow_ring<olbm::batch_stream_persistent_kernel<MODEL, PREC, C::NC, C::STAGES>>(bytes);
+    return e;
+  }
+}
+
+template <int PREC> cudaError_t allow_rings_p(int model) {
+  switch (model) {
+    case 0: return allow_rings<PREC, 0>();
+    case 1: return allow_rings<PREC, 1>();
+    case 2: return allow_rings<PREC, 2>();
+    case 3: return allow_rings<PREC, 3>();
+    default: return allow_rings<PREC, 4>();
+  }
+}
+
+cudaError_t prepare_launch(const lbm_batch* b) {
+  if (b->cfg.kind != 1) return cudaSuccess;
+  switch (b->prec) {
+    case LBM_F32_SHIFT: return allow_rings_p<1>(b->model);
+    case LBM_F16_SHIFT: return allow_rings_p<2>(b->model);
+    default: return cudaSuccess;
+  }
+}
+
+template <int PREC, int MODEL>
+cudaError_t launch_batch_stream(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
+  if constexpr (PREC == 0) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using C = StreamCfg<PREC>;
+    const auto* desc = static_cast<const olbm::Desc<float>*>(b->d_desc);
+    auto k1 = olbm::batch_stream_kernel<MODEL, PREC, true, C::NC, C::STAGES>;
+    auto k0 = olbm::batch_stream_kernel<MODEL, PREC, false, C::NC, C::STAGES>;
+    auto kernel = diag ? k1 : k0;
+    kernel<<<b->ntiles, C::NC + 32, C::Shape::kSmemBytes, st>>>(desc, b->d_tiles, parity, b->d_partials, b->cfg.rows,
+                                                                 b->d_perr);
+    return cudaGetLastError();
+  }
+}
+
 template <int PREC, int MODEL>
 cudaError_t launch_batch_step(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
+  if (b->cfg.kind == 1) return launch_batch_stream<PREC, MODEL>(b, diag, parity, st);
   using T = typename olbm::Form<PREC>::T;
   const auto* desc = static_cast<const olbm::Desc<T>*>(b->d_desc);
   const dim3 block(b->cfg.bx, b->cfg.by);
@@ -356,7 +511,33 @@ cudaError_t launch_finalize(const lbm_batch* b, double* out, unsigned long long*
 }
 
 template <int PREC, int MODEL>
+cudaError_t launch_persistent_stream(lbm_batch* b, int n, int parity0, cudaStream_t st) {
+  if constexpr (PREC == 0) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using C = StreamCfg<PREC>;
+    auto kernel = olbm::batch_stream_persistent_kernel<MODEL, PREC, C::NC, C::STAGES>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, C::NC + 32, C::Shape::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(b->ntiles, per_sm * b->sms);
+    const auto* desc = static_cast<const olbm::Desc<float>*>(b->d_desc);
+    const int4* tiles = b->d_tiles;
+    int ntiles = b->ntiles, rows = b->cfg.rows;
+    olbm::GridBarrier* bar = b->d_bar;
+    void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows,
+                    (void*)&bar};
+    e = cudaMemsetAsync(b->d_bar, 0, sizeof(olbm::GridBarrier), st);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(C::NC + 32), args,
+                                       (size_t)C::Shape::kSmemBytes, st);
+  }
+}
+
+template <int PREC, int MODEL>
 cudaError_t launch_persistent(lbm_batch* b, int n, int parity0, cudaStream_t st) {
+  if (b->cfg.kind == 1) return launch_persistent_stream<PREC, MODEL>(b, n, parity0, st);
   using T = typename olbm::Form<PREC>::T;
   auto kernel = olbm::batch_persistent_kernel<MODEL, PREC>;
   const int threads = b->cfg.bx * b->cfg.by;
@@ -390,9 +571,14 @@ template <int PREC>
 cudaError_t launch_batch_diag(const lbm_batch* b, cudaStream_t st) {
   using T = typename olbm::Form<PREC>::T;
   const auto* desc = static_cast<const olbm::Desc<T>*>(b->d_desc);
-  olbm::batch_diag_kernel<PREC><<<b->ntiles, dim3(b->cfg.bx, b->cfg.by), 0, st>>>(desc, b->d_tiles, b->cur,
-                                                                                  b->cfg.rows, b->rho_ref,
-                                                                                  b->d_partials);
+  if (b->cfg.kind == 1) {
+    const int w = olbm::stream_width(b->prec);
+    olbm::batch_diag_kernel<PREC><<<b->ntiles, 256, 0, st>>>(desc, b->d_tiles, b->cur, w, w, b->cfg.rows, b->rho_ref,
+                                                             b->d_partials);
+  } else {
+    olbm::batch_diag_kernel<PREC><<<b->ntiles, dim3(b->cfg.bx, b->cfg.by), 0, st>>>(
+        desc, b->d_tiles, b->cur, b->cfg.bx, 2 * b->cfg.bx, b->cfg.by * b->cfg.rows, b->rho_ref, b->d_partials);
+  }
   return cudaGetLastError();
 }
 
@@ -447,7 +633,8 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
       (e = cudaMalloc(&b->d_diag, sizeof(double) * 5 * n)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_diag_now, sizeof(double) * 5 * n)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_sticky, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_bar, sizeof(olbm::GridBarrier))) != cudaSuccess) {
+      (e = cudaMalloc(&b->d_bar, sizeof(olbm::GridBarrier))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_perr, sizeof(int))) != cudaSuccess) {
     free_batch(b);
     cudaGetLastError();
     return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: %s", cudaGetErrorString(e));
@@ -464,17 +651,19 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
   if (e == cudaSuccess) e = cudaMemcpy(b->d_nodes, nodes.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->arena, 0, arena);
   if (e == cudaSuccess) e = cudaMemset(b->d_sticky, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b->d_perr, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_diag, 0, sizeof(double) * 5 * n);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_batch(b);
     return bfail(nullptr, LBM_ECUDA, "lbm_batch_create: %s", cudaGetErrorString(e));
   }
-  // Default tile shape: one of the single-lattice defaults, fewer rows for small domains.
+  // Default tiles: FP64 the column routine with 64 x 2 threads and 16 rows; the
+  // shifted forms the bulk-copy pipeline on tiles of 32 rows.
   if (prec == LBM_F64) {
     b->cfg.bx = 64, b->cfg.by = 2, b->cfg.rows = 16;
   } else {
-    b->cfg.bx = 64, b->cfg.by = 4, b->cfg.rows = 8;
+    b->cfg.kind = 1, b->cfg.bx = 0, b->cfg.by = 1, b->cfg.rows = 32;
   }
   int s = build_tiles(b);
   if (s != LBM_OK) {
@@ -506,6 +695,28 @@ int lbm_batch_set_launch(lbm_batch* b, int bx, int by, int rows) {
                  bx, by, rows);
   b->cfg = k;
   return build_tiles(b);
+}
+
+int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows) {
+  int s = check_batch(b);
+  if (s != LBM_OK) return s;
+  if (kind == 0) return lbm_batch_set_launch(b, bx, by, rows);
+  if (kind != 1 || b->prec == LBM_F64 || rows < 1 || rows > 4096)
+    return bfail(b, LBM_EINVAL,
+                 "launch kind %d with %d rows invalid (kind 1: shifted storage forms only, rows 1..4096)", kind, rows);
+  olbm::LaunchCfg k;
+  k.kind = 1;
+  k.bx = 0;
+  k.by = 1;
+  k.rows = rows;
+  b->cfg = k;
+  return build_tiles(b);
+}
+
+int lbm_batch_get_launch_ex(const lbm_batch* b, int* kind, int* bx, int* by, int* rows, int* ntiles) {
+  if (!b || !kind) return LBM_EINVAL;
+  *kind = b->cfg.kind;
+  return lbm_batch_get_launch(b, bx, by, rows, ntiles);
 }
 
 int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* ntiles) {
@@ -615,7 +826,8 @@ int lbm_batch_step(lbm_batch* b, int n) {
   if (n < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: n must be >= 0");
   if (!b->initialised) return bfail(b, LBM_ESTATE, "lbm_batch_step before lbm_batch_init");
   if (n == 0) return LBM_OK;
-  cudaError_t e;
+  cudaError_t e = prepare_launch(b);
+  if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step kernel attributes");
   if (b->mode == LBM_BATCH_PERSISTENT) {
     switch (b->prec) {
       case LBM_F64: e = launch_persistent_p<0>(b, n, b->cur, b->stream); break;
@@ -680,10 +892,13 @@ int lbm_batch_step_diagnostics(lbm_batch* b, double* h_out, long long* h_time) {
   if (s != LBM_OK) return s;
   if (!h_out) return bfail(b, LBM_EINVAL, "lbm_batch_step_diagnostics: NULL output");
   unsigned long long bad = 0;
+  int timed_out = 0;
   cudaError_t e = cudaMemcpyAsync(h_out, b->d_diag, sizeof(double) * 5 * b->n, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, b->d_sticky, sizeof(bad), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&timed_out, b->d_perr, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step_diagnostics");
+  if (timed_out) return bfail(b, LBM_ETIMEOUT, "a bounded device-side wait of the pipelined tile kernel gave up");
   if (h_time) *h_time = b->last_diag_t;
   if (bad > 0) return bfail(b, LBM_ENONFINITE, "%llu non-finite node(s) met by fused diagnostics", bad);
   return LBM_OK;
@@ -725,9 +940,12 @@ int lbm_batch_sync(lbm_batch* b) {
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_sync");
   unsigned long long bad = 0;
+  int timed_out = 0;
   e = cudaMemcpyAsync(&bad, b->d_sticky, sizeof(bad), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&timed_out, b->d_perr, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_sync");
+  if (timed_out) return bfail(b, LBM_ETIMEOUT, "a bounded device-side wait of the pipelined tile kernel gave up");
   if (bad > 0) return bfail(b, LBM_ENONFINITE, "%llu non-finite node(s) met by fused diagnostics", bad);
   return LBM_OK;
 }

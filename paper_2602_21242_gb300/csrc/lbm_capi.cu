@@ -56,15 +56,16 @@ long long nodes_of(const lbm_ctx* c) { return (long long)c->nx * c->ny; }
 // Default launch of the step kernel per storage form, chosen by timing on GB300
 // at the 4096^2 benchmark size: FP64 the column kernel with 64 x 2 threads and
 // 32 rows per thread; the shifted forms the bulk-copy pipeline with one CTA per
-// tile of 32 rows when nx is a multiple of 8 (FP32 90 % of HBM), else the
-// node-pair column kernel with 128 x 4 threads and 16 rows. On smaller lattices
-// the rows are halved until the grid has at least 4 CTAs per SM.
+// tile of 32 rows (FP32 90 % of HBM), except on lattices narrower than 32
+// columns, where the column kernel with 128 x 4 threads and 16 rows wastes fewer
+// threads. On smaller lattices the rows are halved until the grid has at least
+// 4 CTAs per SM.
 // lbm_set_launch[_ex] (and the autotuner built on it) overrides the choice.
 olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
   olbm::LaunchCfg k;
   if (prec == LBM_F64) {
     k.bx = 64, k.by = 2, k.rows = 32;
-  } else if (g.nx % 8 == 0) {
+  } else if (g.nx >= 32) {
     k.kind = 1, k.bx = 0, k.by = 1, k.rows = 32;
   } else {
     k.bx = 128, k.by = 4, k.rows = 16;

@@ -406,9 +406,10 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
 // The shifted forms update node pairs (x, x + 1) when nx is even.
 inline bool uses_pairs(int prec, const Geometry& g) { return prec != 0 && (g.nx % 2) == 0; }
-// The pipeline kernel applies to the shifted forms with nx a multiple of 8.
+// The pipeline kernel (launch kind 1) applies to the shifted forms, any nx.
 inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
-  return k.kind == 1 && prec != 0 && (g.nx % 8) == 0;
+  (void)g;
+  return k.kind == 1 && prec != 0;
 }
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   if (uses_stream(prec, g, k)) {

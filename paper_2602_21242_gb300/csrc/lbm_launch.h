@@ -10,7 +10,7 @@ namespace olbm {
 
 // Launch shape of the step kernel. kind 0: bx x by threads (bx a multiple of
 // 32, bx * by <= 512), each thread updating `rows` nodes of one column.
-// kind 1 (shifted forms, nx a multiple of 8): the bulk-copy pipeline over
+// kind 1 (shifted forms, any nx): the bulk-copy pipeline over
 // tiles of stream_width(prec) columns by `rows` rows; bx = 0 launches one CTA
 // per tile, bx > 0 a persistent grid of bx CTAs per SM (at most the resident
 // count) looping over the tiles; by unused.

@@ -9,10 +9,14 @@
 // shared-memory slots with cp.async.bulk (TMA bulk copies, tracked by mbarrier
 // transaction counts); NC consumer threads (node pairs, packed f32x2 collision)
 // read the slot, collide, store the pair to global memory and release the slot.
-// Each slot holds, per plane, the W-node row segment plus one 16-byte chunk on
-// each side that carries the x -+ 1 neighbours (periodic in x and y: the
-// producer computes the wrapped source row and the wrapped edge chunks). The
-// copies need 16-byte aligned starts and sizes: nx a multiple of 8.
+// Each slot holds, per plane, the row segment plus one 16-byte chunk on each
+// side that carries the x -+ 1 neighbours (periodic in x and y: the producer
+// computes the wrapped source row and the wrapped edge chunks). Bulk copies
+// need 16-byte aligned starts and sizes; any nx works: tiles start on multiples
+// of W, the main copy is rounded up to whole chunks (the layout's row padding
+// holds the overhang, which no node reads), the chunk left of column 0 is the
+// aligned chunk holding column nx - 1, and a pair whose second node lies past
+// the strip stores and reduces its first node only.
 //
 // Waits are bounded: an mbarrier wait that does not complete within ~1 s
 // records an error flag and the CTA stops issuing work; the producer first
@@ -127,125 +131,178 @@ template <int PREC, int NC, int STAGES> struct StreamShape {
   static constexpr int kSmemBytes = kRingBytes + kBarBytes;
 };
 
-template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const typename Form<PREC>::S* __restrict__ src,
-                                                             typename Form<PREC>::S* __restrict__ dst, Geometry g,
-                                                             Coef<f32x2> c, double* __restrict__ partials, int H,
-                                                             int* __restrict__ err) {
+// Copy plan of one tile: columns [x0, x0 + w) of a lattice of any width. The
+// main copy takes wr = w rounded up to whole 16-byte chunks into segment
+// elements [CH, CH + wr); the left chunk fills [0, CH) and the right chunk
+// [CH + wr, CH + wr + CH).
+template <int CH> struct TilePlan {
+  int w, wr;
+  int src_l, src_r;  // first source column of the left / right chunk
+  int lidx;          // segment element holding column x0 - 1 (periodic)
+  __device__ __forceinline__ TilePlan(const Geometry& g, int x0, int W) {
+    w = min(W, g.nx - x0);
+    wr = (w + CH - 1) / CH * CH;
+    if (x0 == 0) {
+      src_l = (g.nx - 1) / CH * CH;  // the aligned chunk holding column nx - 1
+      lidx = g.nx - 1 - src_l;
+    } else {
+      src_l = x0 - CH;
+      lidx = CH - 1;
+    }
+    src_r = (x0 + w >= g.nx) ? 0 : x0 + w;
+  }
+};
+
+// The ring of one CTA: STAGES slots, a full and an empty mbarrier per slot, and
+// the count of ring items this thread has issued (producer) or consumed.
+template <int PREC, int NC, int STAGES> struct Pipeline {
   using S = typename Form<PREC>::S;
   using Shape = StreamShape<PREC, NC, STAGES>;
-  constexpr int CH = Shape::kChunk, SEG = Shape::kSeg;
-  extern __shared__ __align__(128) unsigned char smem[];
-  S* ring = reinterpret_cast<S*>(smem);
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes);
-  unsigned long long* empty = full + STAGES;
+  static constexpr int CH = Shape::kChunk, SEG = Shape::kSeg, W = Shape::kW;
+  static constexpr int kConsumerWarps = NC / 32;
+  S* ring;
+  unsigned long long* full;
+  unsigned long long* empty;
+  int k = 0;
 
-  // Persistent form. Tiles: strips of W columns x blocks of H rows, numbered
-  // strip-fastest. CTA b takes tiles b, b + gridDim.x, ...; the ring's item
-  // counter runs on across tiles, so a CTA fills the pipeline once.
-  const int nstrips = (g.nx + Shape::kW - 1) / Shape::kW;
-  const int ntiles = nstrips * ((g.ny + H - 1) / H);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kConsumerWarps = NC / 32;
-  const bool producer = warp == kConsumerWarps;
+  __device__ __forceinline__ explicit Pipeline(unsigned char* smem)
+      : ring(reinterpret_cast<S*>(smem)),
+        full(reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes)),
+        empty(reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes) + STAGES) {}
 
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumerWarps);
+  // Thread 0 initialises the barriers; the caller synchronises the block after.
+  __device__ __forceinline__ void init() {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < STAGES; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], kConsumerWarps);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
 
-  DiagAcc<f32x2> acc;
-  if (producer) {
-    bool ok = true;
-    int k = 0;  // items (rows) issued by this CTA
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int x0 = (tile % nstrips) * Shape::kW, y0 = (tile / nstrips) * H;
-      const int w = min(Shape::kW, g.nx - x0);  // a multiple of 8
-      const int rows = min(H, g.ny - y0);
-      // Copy plan per plane: main segment [x0, x0 + w) always; the left chunk (ending
-      // at x0 - 1, periodic) for c_ix = +1, the right chunk (starting at x0 + w) for c_ix = -1.
-      const int xl = (x0 == 0) ? g.nx - CH : x0 - CH;
-      const int xr = (x0 + w >= g.nx) ? 0 : x0 + w;
-      const unsigned main_bytes = (unsigned)(w * sizeof(S));
-      const unsigned stage_bytes = 9u * main_bytes + 6u * 16u;
-      for (int r = 0; r < rows; ++r, ++k) {
-        const int s = k % STAGES;
-        if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
-        ok = __all_sync(0xffffffffu, ok);  // the whole warp leaves together
-        if (!ok) break;
-        const int y = y0 + r;
-        S* slot = ring + (size_t)s * 9 * SEG;
-        if (lane == 0) mbar_expect_tx_arrive(&full[s], stage_bytes);
-        __syncwarp();
-        // lanes 0..8: main segments; lanes 9..14: edge chunks of the planes with c_ix != 0
-        if (lane < 15) {
-          int i, part;  // part 0: main, 1: left chunk, 2: right chunk
-          if (lane < 9) {
-            i = lane;
-            part = 0;
-          } else {
-            const int e = lane - 9;  // planes 1, 5, 8 take the left chunk; 3, 6, 7 the right one
-            i = e == 0 ? 1 : e == 1 ? 5 : e == 2 ? 8 : e == 3 ? 3 : e == 4 ? 6 : 7;
-            part = e < 3 ? 1 : 2;
-          }
-          int ys = y - cy_of(i);
-          ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-          const S* row = src + i * g.plane + (long long)ys * g.pitch;
-          S* seg = slot + i * SEG;
-          if (part == 0)
-            bulk_g2s(seg + CH, row + x0, main_bytes, &full[s]);
-          else if (part == 1)
-            bulk_g2s(seg, row + xl, 16u, &full[s]);
-          else
-            bulk_g2s(seg + CH + w, row + xr, 16u, &full[s]);
-        }
+  // Producer warp: stream rows [y0, y0 + rows) of the tile at column x0.
+  // Returns false (in the whole warp) once a bounded wait gave up.
+  __device__ __forceinline__ bool produce(const S* __restrict__ src, const Geometry& g, int x0, int y0, int rows,
+                                          int lane, int* err) {
+    const TilePlan<CH> p(g, x0, W);
+    const unsigned main_bytes = (unsigned)(p.wr * (int)sizeof(S));
+    const unsigned stage_bytes = 9u * main_bytes + 6u * 16u;
+    for (int r = 0; r < rows; ++r, ++k) {
+      const int s = k % STAGES;
+      bool ok = true;
+      if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
+      if (!__all_sync(0xffffffffu, ok)) return false;  // the whole warp leaves together
+      const int y = y0 + r;
+      S* slot = ring + (size_t)s * 9 * SEG;
+      if (lane == 0) mbar_expect_tx_arrive(&full[s], stage_bytes);
+      __syncwarp();
+      // lanes 0..8: main segment of plane `lane`; lanes 9..14: edge chunks of the planes
+      // with c_ix != 0 (planes 1, 5, 8 the left chunk, 3, 6, 7 the right one). Operands
+      // are selected without branches, so the warp issues one copy instruction.
+      if (lane < 15) {
+        const int e = lane - 9;
+        const bool main = lane < 9, left = e < 3;
+        const int i = main ? lane : (int)((0x763851u >> (4 * e)) & 15u);
+        int ys = y - cy_of(i);
+        ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+        const int dst_off = main ? CH : (left ? 0 : CH + p.wr);
+        const int src_col = main ? x0 : (left ? p.src_l : p.src_r);
+        const unsigned bytes = main ? main_bytes : 16u;
+        bulk_g2s(slot + i * SEG + dst_off, src + i * g.plane + (long long)ys * g.pitch + src_col, bytes, &full[s]);
       }
     }
-    // Before leaving, every copy issued must have landed (bounded).
+    return true;
+  }
+
+  // Producer warp, before leaving: every copy issued must have landed (bounded).
+  __device__ __forceinline__ void drain(int* err) {
     for (int j = (k > STAGES ? k - STAGES : 0); j < k; ++j)
       if (!__all_sync(0xffffffffu, mbar_wait(&full[j % STAGES], (unsigned)((j / STAGES) & 1), err))) break;
-  } else if (threadIdx.x < NC) {
-    const int xl = 2 * (int)threadIdx.x;  // local node index of the pair's first node
-    bool ok = true;
-    int k = 0;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int x0 = (tile % nstrips) * Shape::kW, y0 = (tile / nstrips) * H;
-      const int w = min(Shape::kW, g.nx - x0);
-      const int rows = min(H, g.ny - y0);
-      const bool active = xl < w;
-      for (int r = 0; r < rows; ++r, ++k) {
-        const int s = k % STAGES;
-        ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err));
-        if (!ok) break;
-        const S* slot = ring + (size_t)s * 9 * SEG;
-        f32x2 f[9];
-        if (active) {
-          // plane i, node x0 + xl + q: element CH + xl + q - c_ix of the plane's segment
-          f[0] = lds_pair(slot + 0 * SEG + CH + xl);
-          f[1] = lds_two(slot + 1 * SEG + CH + xl - 1, slot + 1 * SEG + CH + xl);
-          f[2] = lds_pair(slot + 2 * SEG + CH + xl);
-          f[3] = lds_two(slot + 3 * SEG + CH + xl + 1, slot + 3 * SEG + CH + xl + 2);
-          f[4] = lds_pair(slot + 4 * SEG + CH + xl);
-          f[5] = lds_two(slot + 5 * SEG + CH + xl - 1, slot + 5 * SEG + CH + xl);
-          f[6] = lds_two(slot + 6 * SEG + CH + xl + 1, slot + 6 * SEG + CH + xl + 2);
-          f[7] = lds_two(slot + 7 * SEG + CH + xl + 1, slot + 7 * SEG + CH + xl + 2);
-          f[8] = lds_two(slot + 8 * SEG + CH + xl - 1, slot + 8 * SEG + CH + xl);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        if (active) {
-          NodeMoments<f32x2> m;
-          collide<MODEL, true, f32x2>(f, c, m);
-          S* q = dst + (long long)(y0 + r) * g.pitch + x0 + xl;
+  }
+
+  // Consumer thread t (pair of local nodes 2t, 2t + 1): collide the tile's rows.
+  template <int MODEL, bool DIAG>
+  __device__ __forceinline__ bool consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
+                                          int y0, int rows, int t, int lane, DiagAcc<f32x2>& acc, int* err) {
+    const TilePlan<CH> p(g, x0, W);
+    const int xl = 2 * t;
+    const bool active = xl < p.w;
+    const bool whole = xl + 1 < p.w;  // both nodes of the pair lie in the strip
+    // segment elements of the pair's nodes and of their x -+ 1 neighbours
+    const int iM = CH + xl;
+    const int iL = xl == 0 ? p.lidx : iM - 1;
+    const int iR0 = whole ? iM + 1 : CH + p.wr;
+    const int iR1 = xl + 2 < p.w ? iM + 2 : CH + p.wr;
+    for (int r = 0; r < rows; ++r, ++k) {
+      const int s = k % STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err))) return false;
+      const S* slot = ring + (size_t)s * 9 * SEG;
+      f32x2 f[9];
+      if (active) {
+        f[0] = lds_pair(slot + 0 * SEG + iM);
+        f[1] = lds_two(slot + 1 * SEG + iL, slot + 1 * SEG + iM);
+        f[2] = lds_pair(slot + 2 * SEG + iM);
+        f[3] = lds_two(slot + 3 * SEG + iR0, slot + 3 * SEG + iR1);
+        f[4] = lds_pair(slot + 4 * SEG + iM);
+        f[5] = lds_two(slot + 5 * SEG + iL, slot + 5 * SEG + iM);
+        f[6] = lds_two(slot + 6 * SEG + iR0, slot + 6 * SEG + iR1);
+        f[7] = lds_two(slot + 7 * SEG + iR0, slot + 7 * SEG + iR1);
+        f[8] = lds_two(slot + 8 * SEG + iL, slot + 8 * SEG + iM);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (active) {
+        NodeMoments<f32x2> m;
+        collide<MODEL, true, f32x2>(f, c, m);
+        S* q = dst + (long long)(y0 + r) * g.pitch + x0 + xl;
+        if (whole) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);
-          if constexpr (DIAG) acc.add(m);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i].v.x);
+          m.m0.v.y = 0.0f;
+          m.jx.v.y = 0.0f;
+          m.jy.v.y = 0.0f;
+          m.ke.v.y = 0.0f;
         }
+        if constexpr (DIAG) acc.add(m);
       }
+    }
+    return true;
+  }
+};
+
+// Persistent form over one lattice. Tiles: strips of W columns x blocks of H
+// rows, numbered strip-fastest. CTA b takes tiles b, b + gridDim.x, ...; the
+// ring's item counter runs on across tiles, so a CTA fills the pipeline once.
+template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
+__global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                                         typename Form<PREC>::S* __restrict__ dst,
+                                                                         Geometry g, Coef<f32x2> c,
+                                                                         double* __restrict__ partials, int H,
+                                                                         int* __restrict__ err) {
+  using P = Pipeline<PREC, NC, STAGES>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  P pipe(smem);
+  pipe.init();
+  __syncthreads();
+  const int nstrips = (g.nx + P::W - 1) / P::W;
+  const int ntiles = nstrips * ((g.ny + H - 1) / H);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DiagAcc<f32x2> acc;
+  if (warp == P::kConsumerWarps) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int x0 = (tile % nstrips) * P::W, y0 = (tile / nstrips) * H;
+      if (!pipe.produce(src, g, x0, y0, min(H, g.ny - y0), lane, err)) break;
+    }
+    pipe.drain(err);
+  } else if (threadIdx.x < NC) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int x0 = (tile % nstrips) * P::W, y0 = (tile / nstrips) * H;
+      if (!pipe.template consume<MODEL, DIAG>(dst, g, c, x0, y0, min(H, g.ny - y0), threadIdx.x, lane, acc, err))
+        break;
     }
   }
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)blockIdx.x * 5);
@@ -259,110 +316,20 @@ __global__ void __launch_bounds__(NC + 32) step_stream_kernel(const typename For
                                                              typename Form<PREC>::S* __restrict__ dst, Geometry g,
                                                              Coef<f32x2> c, double* __restrict__ partials, int H,
                                                              int* __restrict__ err) {
-  using S = typename Form<PREC>::S;
-  using Shape = StreamShape<PREC, NC, STAGES>;
-  constexpr int CH = Shape::kChunk, SEG = Shape::kSeg;
+  using P = Pipeline<PREC, NC, STAGES>;
   extern __shared__ __align__(128) unsigned char smem[];
-  S* ring = reinterpret_cast<S*>(smem);
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes);
-  unsigned long long* empty = full + STAGES;
-
-  const int x0 = blockIdx.x * Shape::kW;
-  const int y0 = blockIdx.y * H;
-  const int w = min(Shape::kW, g.nx - x0);       // nodes of this strip (a multiple of 8)
+  P pipe(smem);
+  pipe.init();
+  __syncthreads();
+  const int x0 = blockIdx.x * P::W, y0 = blockIdx.y * H;
   const int rows = min(H, g.ny - y0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kConsumerWarps = NC / 32;
-  const bool producer = warp == kConsumerWarps;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumerWarps);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
   DiagAcc<f32x2> acc;
-  if (producer) {
-    // Copy plan per plane: main segment [x0, x0 + w) always; the left chunk (ending
-    // at x0 - 1, periodic) for c_ix = +1, the right chunk (starting at x0 + w) for c_ix = -1.
-    const int xl = (x0 == 0) ? g.nx - CH : x0 - CH;
-    const int xr = (x0 + w >= g.nx) ? 0 : x0 + w;
-    const unsigned main_bytes = (unsigned)(w * sizeof(S));
-    const unsigned stage_bytes = 9u * main_bytes + 6u * 16u;
-    bool ok = true;
-    int issued = 0;
-    for (int k = 0; k < rows && ok; ++k) {
-      const int s = k % STAGES;
-      if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
-      ok = __all_sync(0xffffffffu, ok);  // the whole warp leaves together
-      if (!ok) break;
-      const int y = y0 + k;
-      S* slot = ring + (size_t)s * 9 * SEG;
-      if (lane == 0) mbar_expect_tx_arrive(&full[s], stage_bytes);
-      __syncwarp();
-      // lanes 0..8: main segments; lanes 9..14: edge chunks of the planes with c_ix != 0
-      if (lane < 15) {
-        int i, part;  // part 0: main, 1: left chunk, 2: right chunk
-        if (lane < 9) {
-          i = lane;
-          part = 0;
-        } else {
-          const int e = lane - 9;  // planes 1, 5, 8 take the left chunk; 3, 6, 7 the right one
-          const int planes[6] = {1, 5, 8, 3, 6, 7};
-          i = planes[e];
-          part = e < 3 ? 1 : 2;
-        }
-        int ys = y - cy_of(i);
-        ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-        const S* row = src + i * g.plane + (long long)ys * g.pitch;
-        S* seg = slot + i * SEG;
-        if (part == 0)
-          bulk_g2s(seg + CH, row + x0, main_bytes, &full[s]);
-        else if (part == 1)
-          bulk_g2s(seg, row + xl, 16u, &full[s]);
-        else
-          bulk_g2s(seg + CH + w, row + xr, 16u, &full[s]);
-      }
-      ++issued;
-    }
-    // Before leaving, every copy issued must have landed (bounded).
-    for (int k = (issued > STAGES ? issued - STAGES : 0); k < issued; ++k)
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[k % STAGES], (unsigned)((k / STAGES) & 1), err))) break;
+  if (warp == P::kConsumerWarps) {
+    pipe.produce(src, g, x0, y0, rows, lane, err);
+    pipe.drain(err);
   } else if (threadIdx.x < NC) {
-    const int t = threadIdx.x;
-    const int xl = 2 * t;  // local node index of the pair's first node
-    const bool active = xl < w;
-    for (int k = 0; k < rows; ++k) {
-      const int s = k % STAGES;
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err))) break;
-      const S* slot = ring + (size_t)s * 9 * SEG;
-      f32x2 f[9];
-      if (active) {
-        // plane i, node x0 + xl + q: element CH + xl + q - c_ix of the plane's segment
-        f[0] = lds_pair(slot + 0 * SEG + CH + xl);
-        f[1] = lds_two(slot + 1 * SEG + CH + xl - 1, slot + 1 * SEG + CH + xl);
-        f[2] = lds_pair(slot + 2 * SEG + CH + xl);
-        f[3] = lds_two(slot + 3 * SEG + CH + xl + 1, slot + 3 * SEG + CH + xl + 2);
-        f[4] = lds_pair(slot + 4 * SEG + CH + xl);
-        f[5] = lds_two(slot + 5 * SEG + CH + xl - 1, slot + 5 * SEG + CH + xl);
-        f[6] = lds_two(slot + 6 * SEG + CH + xl + 1, slot + 6 * SEG + CH + xl + 2);
-        f[7] = lds_two(slot + 7 * SEG + CH + xl + 1, slot + 7 * SEG + CH + xl + 2);
-        f[8] = lds_two(slot + 8 * SEG + CH + xl - 1, slot + 8 * SEG + CH + xl);
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-      if (active) {
-        NodeMoments<f32x2> m;
-        collide<MODEL, true, f32x2>(f, c, m);
-        S* q = dst + (long long)(y0 + k) * g.pitch + x0 + xl;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);
-        if constexpr (DIAG) acc.add(m);
-      }
-    }
+    pipe.template consume<MODEL, DIAG>(dst, g, c, x0, y0, rows, threadIdx.x, lane, acc, err);
   }
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
 }

@@ -21,13 +21,15 @@ from . import capi
 
 _lock = threading.Lock()
 
-# (kind, bx, by, rows): kind 0 = column kernel; kind 1 = bulk-copy pipeline (shifted forms,
-# nx a multiple of 8) with bx = CTAs per SM (0 = one CTA per tile)
+# (kind, bx, by, rows): kind 0 = column kernel; kind 1 = bulk-copy pipeline (shifted forms)
+# with bx = CTAs per SM (0 = one CTA per tile)
 LATTICE_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)], [4, 8, 16, 32])]
 PIPELINE_CANDIDATES = [(1, ctas, 1, rows) for ctas in (0, 1, 2) for rows in (4, 8, 16, 32, 64)]
-BATCH_CANDIDATES = [(bx, by, rows) for (bx, by), rows in itertools.product(
+BATCH_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)], [2, 4, 8, 16])]
+# kind 1: the pipeline on tiles of W columns x rows (shifted forms)
+BATCH_PIPELINE_CANDIDATES = [(1, 0, 1, rows) for rows in (8, 16, 32, 64, 128)]
 
 
 def cache_path() -> str:
@@ -78,7 +80,7 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
     from .lattice import Lattice
 
     path = path or cache_path()
-    key = _key("lattice", lat.nx * lat.ny, lat.prec, lat.model, f"|nx%8={lat.nx % 8}")
+    key = _key("lattice", lat.nx * lat.ny, lat.prec, lat.model, f"|nx={lat.nx}")
     if use_cache:
         hit = _load_cache(path).get(key)
         if hit:
@@ -86,7 +88,7 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
             return tuple(hit["shape"]), None
     if candidates is None:
         candidates = list(LATTICE_CANDIDATES)
-        if lat.prec != capi.LBM_F64 and lat.nx % 8 == 0:
+        if lat.prec != capi.LBM_F64:
             candidates += PIPELINE_CANDIDATES
     best = None
     with Lattice(lat.nx, lat.ny, lat.theta, lat.tau, lat.model, lat.prec, device=lat.device,
@@ -112,9 +114,11 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
 def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, path: str | None = None):
     """Pick and apply the fastest tile shape for `batch` (a Batch). The timing steps the
     batch itself from a rest state (rho = 1, u = 0): call it before Batch.init.
-    Returns ((bx, by, rows), ms_per_step or None if cached)."""
+    Candidates are (kind, bx, by, rows) or (bx, by, rows) for kind 0; the default set
+    adds the pipeline shapes for the shifted forms. Returns ((kind, bx, by, rows),
+    ms_per_step or None if cached)."""
     path = path or cache_path()
-    key = _key("batch", batch.total_nodes, batch.prec, batch.model, f"|n{batch.n}")
+    key = _key("batch", batch.total_nodes, batch.prec, batch.model, f"|n{batch.n}|k")
     if use_cache:
         hit = _load_cache(path).get(key)
         if hit:
@@ -123,7 +127,10 @@ def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, 
     rest = [torch.ones((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
     zero = [torch.zeros((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
     best = None
-    for shape in candidates or BATCH_CANDIDATES:
+    if candidates is None:
+        candidates = BATCH_CANDIDATES + (BATCH_PIPELINE_CANDIDATES if batch.prec != capi.LBM_F64 else [])
+    for shape in candidates:
+        shape = tuple(shape) if len(shape) == 4 else (0,) + tuple(shape)
         try:
             batch.set_launch(*shape)
         except capi.LBMError:

@@ -23,8 +23,12 @@ def states(seed, domains=DOMAINS):
     return [flows.random_populations(nx, ny, seed=seed + k, spread=0.15) for k, (nx, ny, _, _) in enumerate(domains)]
 
 
-def single_run(f0, nx, ny, theta, tau, model, prec, steps):
+def single_run(f0, nx, ny, theta, tau, model, prec, steps, kind=None):
     with Lattice(nx, ny, theta, tau, model, prec) as lat:
+        if kind == 1:
+            capi.lbm_set_launch_ex(lat.ctx, 1, 0, 1, 32)
+        elif kind == 0:
+            capi.lbm_set_launch_ex(lat.ctx, 0, 64, 4, 8)
         lat.set_state(torch.from_numpy(f0).cuda())
         lat.step(steps)
         return lat.state().cpu().numpy()
@@ -36,19 +40,26 @@ def make_batch(model, prec, mode, domains=DOMAINS):
 
 
 @pytest.mark.parametrize("mode", ["graph", "persistent"])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec,kind", [("f64", 0), ("f32", 0), ("f32", 1), ("f16", 0), ("f16", 1)])
 @pytest.mark.parametrize("model", [0, 3])
-def test_batch_bit_identical_to_single_lattices(model, prec, mode):
+def test_batch_bit_identical_to_single_lattices(model, prec, kind, mode):
+    """Kind 0 tiles run the column routine, kind 1 tiles the bulk-copy pipeline (any width, including
+    1 x 5 and odd widths); each matches a single lattice stepped with the same launch kind."""
     f0 = states(100 + model)
     steps = 13
     with make_batch(model, prec, mode) as b:
+        if kind == 0:
+            b.set_launch(0, 64, 4, 2)
+        else:
+            b.set_launch(1, 0, 1, 8)
+        assert b.launch()[0] == kind
         for k, f in enumerate(f0):
             b.set_state(k, f)
         b.step(steps)
         b.sync()
         got = [b.state(k).cpu().numpy() for k in range(b.n)]
     for k, (nx, ny, theta, tau) in enumerate(DOMAINS):
-        want = single_run(f0[k], nx, ny, theta, tau, model, prec, steps)
+        want = single_run(f0[k], nx, ny, theta, tau, model, prec, steps, kind=kind if prec != "f64" else None)
         np.testing.assert_array_equal(got[k], want, err_msg=f"domain {k} ({nx}x{ny})")
 
 
@@ -119,5 +130,6 @@ def test_tuners(tmp_path):
         again, cached = tune.tune_lattice(lat, path=path)
         assert again == shape and cached is None
     with make_batch(3, "f32", "graph") as b:
-        shape, ms = tune.tune_batch(b, candidates=[(32, 4, 4), (64, 2, 8)], steps=4, path=path)
-        assert b.launch()[:3] == shape
+        shape, ms = tune.tune_batch(b, candidates=[(32, 4, 4), (64, 2, 8), (1, 0, 1, 16)], steps=4, path=path)
+        assert shape in [(0, 32, 4, 4), (0, 64, 2, 8), (1, 0, 1, 16)]
+        assert b.launch()[:4] == shape

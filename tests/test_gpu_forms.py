@@ -140,3 +140,32 @@ def test_pipeline_kernel_matches_column_kernel(prec, nx, ny, rows, ctas, model):
             out[kind] = (lat.state().cpu().numpy(), np.array(d))
     np.testing.assert_array_equal(out[1][0], out[0][0])
     np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("nx,ny,rows,ctas", [(45, 19, 8, 0), (3, 7, 4, 0), (1, 4, 2, 0), (257, 9, 5, 0),
+                                             (513, 6, 4, 1), (100, 6, 3, 2), (250, 33, 16, 0)])
+def test_pipeline_kernel_any_width(oracle, prec, nx, ny, rows, ctas):
+    """The bulk-copy pipeline on widths that are not multiples of the 16-byte chunk: the main copy is
+    rounded up into the row padding, the chunk left of column 0 is the aligned chunk holding column
+    nx - 1, and a pair whose second node lies past the strip stores its first node only. Against the
+    oracle within the forms' bound, and fused diagnostics against the oracle's."""
+    theta, tau, steps = 0.33, 0.7, 40
+    f0 = flows.random_populations(nx, ny, seed=950 + nx + ny, spread=0.1)
+    d = np.abs(f0 - rest_state(theta)[:, None, None]).max()
+    from paper_2602_21242_gb300 import capi
+    with Lattice(nx, ny, theta, tau, 3, prec) as lat:
+        capi.lbm_set_launch_ex(lat.ctx, 1, ctas, 0, rows)
+        lat.set_state(torch.from_numpy(f0).cuda())
+        lat.step(steps - 1)
+        prev = lat.state().cpu().numpy()
+        lat.set_diagnostics_interval(1)
+        lat.step(1)
+        out, t, _ = lat.step_diagnostics()
+        got = lat.state().cpu().numpy()
+    ref = oracle.run(f0, theta, tau, 3, steps)
+    assert np.abs(got - ref).max() <= bound(prec, d, steps)
+    # the fused pass reduces f(steps - 1): FP32 sums of deviations inside a block, FP64 across blocks
+    assert t == steps - 1
+    np.testing.assert_allclose(out[:4], oracle.diagnostics(prev)[:4], rtol=1e-5, atol=1e-5)
+    assert out[4] == 0
