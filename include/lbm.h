@@ -265,10 +265,13 @@ int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* n
 
 /* Launch kind and tile shape. kind 0: as lbm_batch_set_launch. kind 1 (the shifted
  * forms only; the default there): the bulk-copy pipeline of the single-lattice
- * kind-1 kernel on tiles of W columns (256 FP32, 512 FP16) x rows rows (1..4096),
- * any domain width; bx, by are ignored. A domain's results equal those of a single
- * lattice stepped with the same launch kind. Errors: LBM_EINVAL (kind 1 on FP64
- * storage, rows out of range). lbm_batch_get_launch_ex also reports the kind. */
+ * kind-1 kernel, one CTA of bx consumer threads (+ one producer warp) per tile of
+ * 2 bx columns x rows rows (1..4096), any domain width; bx = 32, 64 or 128 (FP32),
+ * 64, 128 or 256 (FP16), 0 = 128 (FP32) / 256 (FP16); narrower tiles waste less
+ * of a strip on narrow domains. by is ignored. A domain's results equal those of
+ * a single lattice stepped with the same launch kind. Errors: LBM_EINVAL (kind 1
+ * on FP64 storage, bx or rows out of range). lbm_batch_get_launch_ex also reports
+ * the kind. */
 int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows);
 int lbm_batch_get_launch_ex(const lbm_batch* b, int* kind, int* bx, int* by, int* rows, int* ntiles);
 int lbm_batch_set_mode(lbm_batch* b, int mode);  /* enum lbm_batch_mode; default LBM_BATCH_GRAPH */

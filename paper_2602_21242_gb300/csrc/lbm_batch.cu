@@ -33,207 +33,9 @@
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_kernels.cuh"
+#include "lbm_batch.h"
 
 namespace olbm {
-
-// Per-domain descriptor; CT is the scalar compute type (double or float).
-template <typename CT> struct Desc {
-  Geometry g;
-  void* buf[2];
-  Coef<CT> c;
-  int pairs;  // 1: node pairs (shifted forms, even nx)
-  int pad;
-};
-
-__host__ __device__ inline Coef<f32x2> broadcast(const Coef<float>& a) {
-  Coef<f32x2> c;
-  c.theta = a.theta;
-  c.one_m_theta = a.one_m_theta;
-  c.half_theta = a.half_theta;
-  c.omega = a.omega;
-  c.one_m_omega = a.one_m_omega;
-  c.k1 = a.k1;
-  c.k2 = a.k2;
-  c.c3 = a.c3;
-  c.tt = a.tt;
-  c.inv2t2 = a.inv2t2;
-  c.mq_inv2t2 = a.mq_inv2t2;
-  c.rho_ref = a.rho_ref;
-  c.w[0] = a.w[0];
-  c.w[1] = a.w[1];
-  c.w[2] = a.w[2];
-  return c;
-}
-
-// Update one tile (d, x0, y0) from buffer `parity` into buffer parity ^ 1.
-template <int MODEL, int PREC, bool DIAG, bool CG>
-__device__ __forceinline__ void update_tile(const Desc<typename Form<PREC>::T>& d, int x0, int y0, int parity,
-                                            int rows, double* __restrict__ out5) {
-  using S = typename Form<PREC>::S;
-  const S* src = static_cast<const S*>(d.buf[parity]);
-  S* dst = static_cast<S*>(d.buf[parity ^ 1]);
-  const int y = y0 + threadIdx.y, dy = blockDim.y;
-  if constexpr (PREC != 0) {
-    if (d.pairs) {
-      using Col = Column<MODEL, PREC, DIAG, true, CG>;
-      DiagAcc<f32x2> acc;
-      Col::run(src, dst, d.g, broadcast(d.c), x0 + 2 * threadIdx.x, y, dy, rows, acc);
-      if constexpr (DIAG) block_diag_acc(acc, out5);
-      return;
-    }
-  }
-  using Col = Column<MODEL, PREC, DIAG, false, CG>;
-  DiagAcc<typename Col::CT> acc;
-  Col::run(src, dst, d.g, d.c, x0 + threadIdx.x, y, dy, rows, acc);
-  if constexpr (DIAG) block_diag_acc(acc, out5);
-}
-
-// One time step of every domain: block b updates tile b.
-template <int MODEL, int PREC, bool DIAG>
-__global__ void __launch_bounds__(512) batch_step_kernel(const Desc<typename Form<PREC>::T>* __restrict__ desc,
-                                                         const int4* __restrict__ tiles, int parity,
-                                                         double* __restrict__ partials, int rows) {
-  const int4 tl = tiles[blockIdx.x];
-  const Desc<typename Form<PREC>::T> d = desc[tl.x];
-  update_tile<MODEL, PREC, DIAG, false>(d, tl.y, tl.z, parity, rows, partials + (long long)blockIdx.x * 5);
-}
-
-// n steps of every domain in one launch; tiles strided over the grid.
-template <int MODEL, int PREC>
-__global__ void __launch_bounds__(512) batch_persistent_kernel(const Desc<typename Form<PREC>::T>* __restrict__ desc,
-                                                               const int4* __restrict__ tiles, int ntiles,
-                                                               int parity0, int nsteps, int rows, GridBarrier* bar) {
-  for (int s = 0; s < nsteps; ++s) {
-    const int parity = (parity0 + s) & 1;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int4 tl = tiles[t];
-      const Desc<typename Form<PREC>::T> d = desc[tl.x];
-      update_tile<MODEL, PREC, false, true>(d, tl.y, tl.z, parity, rows, nullptr);
-    }
-    if (!grid_sync(bar, gridDim.x)) return;
-  }
-}
-
-// Pull-only diagnostics of one tile (FP64), as diag_kernel for one lattice.
-// A tile spans cols1 columns (cols2 for node-pair domains) x trows rows; the
-// block's threads stride over its nodes.
-template <int PREC>
-__global__ void __launch_bounds__(512) batch_diag_kernel(const Desc<typename Form<PREC>::T>* __restrict__ desc,
-                                                         const int4* __restrict__ tiles, int parity, int cols1,
-                                                         int cols2, int trows, double rho_ref,
-                                                         double* __restrict__ partials) {
-  using S = typename Form<PREC>::S;
-  const int4 tl = tiles[blockIdx.x];
-  const Desc<typename Form<PREC>::T> d = desc[tl.x];
-  const S* src = static_cast<const S*>(d.buf[parity]);
-  const int w = min(d.pairs ? cols2 : cols1, d.g.nx - tl.y);
-  const int h = min(trows, d.g.ny - tl.z);
-  const int nthreads = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  int bad = 0;
-  for (int j = tid; j < w * h; j += nthreads) {
-    const int x = tl.y + j % w, y = tl.z + j / w;
-    long long o[9];
-    pull_offsets(x, y, d.g, o);
-    double m0 = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const double f = to_double(src[i * d.g.plane + o[i]]);
-      m0 += f;
-      jx += (double)cx_of(i) * f;
-      jy += (double)cy_of(i) * f;
-    }
-    if (finite_bits(m0)) {
-      v[0] += m0;
-      v[1] += jx;
-      v[2] += jy;
-      v[3] += 0.5 * (jx * jx + jy * jy) / (rho_ref + m0);
-    } else {
-      ++bad;
-    }
-  }
-  block_diag<double>(v, bad, partials + (long long)blockIdx.x * 5);
-}
-
-// Pipelined tile step (launch kind 1, shifted forms): one CTA per tile of W
-// columns x H rows of one domain, the single-lattice pipeline on that tile.
-template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32) batch_stream_kernel(const Desc<float>* __restrict__ desc,
-                                                              const int4* __restrict__ tiles, int parity,
-                                                              double* __restrict__ partials, int H,
-                                                              int* __restrict__ err) {
-  using P = Pipeline<PREC, NC, STAGES>;
-  using S = typename Form<PREC>::S;
-  extern __shared__ __align__(128) unsigned char smem[];
-  P pipe(smem);
-  pipe.init();
-  __syncthreads();
-  const int4 tl = tiles[blockIdx.x];
-  const Desc<float>* d = desc + tl.x;
-  const Geometry g = d->g;
-  const int rows = min(H, g.ny - tl.z);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  DiagAcc<f32x2> acc;
-  if (warp == P::kConsumerWarps) {
-    pipe.produce(static_cast<const S*>(d->buf[parity]), g, tl.y, tl.z, rows, lane, err);
-    pipe.drain(err);
-  } else if (threadIdx.x < NC) {
-    pipe.template consume<MODEL, DIAG>(static_cast<S*>(d->buf[parity ^ 1]), g, broadcast(d->c), tl.y, tl.z, rows,
-                                       threadIdx.x, lane, acc, err);
-  }
-  if constexpr (DIAG) block_diag_acc(acc, partials + (long long)blockIdx.x * 5);
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-// n steps of every domain in one cooperative launch of pipelined CTAs: tiles
-// strided over the grid, a bounded grid barrier between steps. The consumers'
-// stores (generic proxy) reach the next step's bulk copies (async proxy)
-// through a proxy fence on both sides of the barrier. A bounded wait that gives
-// up sets the barrier's error flag, so every CTA leaves at the next barrier.
-template <int MODEL, int PREC, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const Desc<float>* __restrict__ desc,
-                                                                         const int4* __restrict__ tiles, int ntiles,
-                                                                         int parity0, int nsteps, int H,
-                                                                         GridBarrier* bar) {
-  using P = Pipeline<PREC, NC, STAGES>;
-  using S = typename Form<PREC>::S;
-  extern __shared__ __align__(128) unsigned char smem[];
-  P pipe(smem);
-  pipe.init();
-  __syncthreads();
-  int* err = &bar->err;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool producer = warp == P::kConsumerWarps;
-  DiagAcc<f32x2> acc;  // no fused diagnostics in this mode
-  for (int s = 0; s < nsteps; ++s) {
-    const int parity = (parity0 + s) & 1;
-    if (producer) {
-      fence_proxy_async_global();
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[t];
-        const Desc<float>* d = desc + tl.x;
-        if (!pipe.produce(static_cast<const S*>(d->buf[parity]), d->g, tl.y, tl.z, min(H, d->g.ny - tl.z), lane,
-                          err))
-          break;
-      }
-    } else if (threadIdx.x < NC) {
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[t];
-        const Desc<float>* d = desc + tl.x;
-        if (!pipe.template consume<MODEL, false>(static_cast<S*>(d->buf[parity ^ 1]), d->g, broadcast(d->c), tl.y,
-                                                 tl.z, min(H, d->g.ny - tl.z), threadIdx.x, lane, acc, err))
-          break;
-      }
-      fence_proxy_async_global();
-    }
-    if (!grid_sync(bar, gridDim.x)) break;
-  }
-  if (producer) pipe.drain(err);
-}
 
 // Per-domain fixed-order sums of the tile partials: out[d * 5 + k].
 __global__ void __launch_bounds__(256) batch_finalize_kernel(const double* __restrict__ partials,
@@ -344,7 +146,7 @@ int build_tiles(lbm_batch* b) {
     const olbm::Geometry& g = b->geo[k];
     int cols, trows;
     if (b->cfg.kind == 1) {
-      cols = olbm::stream_width(b->prec);
+      cols = 2 * olbm::batch_stream_nc(b->prec, b->cfg.bx);
       trows = b->cfg.rows;
     } else {
       cols = olbm::uses_pairs(b->prec, g) ? 2 * b->cfg.bx : b->cfg.bx;
@@ -406,179 +208,55 @@ int check_batch(lbm_batch* b) {
   return LBM_OK;
 }
 
-// Pipeline shape of a shifted storage form (the single-lattice one).
-template <int PREC> struct StreamCfg {
-  static constexpr int NC = PREC == 1 ? olbm::kStreamNC32 : olbm::kStreamNC16;
-  static constexpr int STAGES = olbm::kStreamStages;
-  using Shape = olbm::StreamShape<PREC, NC, STAGES>;
-};
-
-// Opt a pipelined kernel in to its shared-memory ring, once per kernel. Called
-// before any launch or graph capture of the kernel (not during a capture).
-template <auto K> cudaError_t allow_ring(int bytes) {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done = true;
-  return e;
+olbm::BatchLaunch view(const lbm_batch* b) {
+  olbm::BatchLaunch v;
+  v.model = b->model;
+  v.cfg = b->cfg;
+  v.desc = b->d_desc;
+  v.tiles = b->d_tiles;
+  v.ntiles = b->ntiles;
+  v.partials = b->d_partials;
+  v.perr = b->d_perr;
+  v.bar = b->d_bar;
+  v.sms = b->sms;
+  return v;
 }
 
-template <int PREC, int MODEL> cudaError_t allow_rings() {
-  if constexpr (PREC == 0) {
-    return cudaSuccess;
-  } else {
-    using C = StreamCfg<PREC>;
-    constexpr int bytes = C::Shape::kSmemBytes;
-    cudaError_t e = allow_ring<olbm::batch_stream_kernel<MODEL, PREC, true, C::NC, C::STAGES>>(bytes);
-    if (e == cudaSuccess) e = allow_ring<olbm::batch_stream_kernel<MODEL, PREC, false, C::NC, C::STAGES>>(bytes);
-    if (e == cudaSuccess) e = allow_ring<olbm::batch_stream_persistent_kernel<MODEL, PREC, C::NC, C::STAGES>>(bytes);
-    return e;
-  }
-}
-
-template <int PREC> cudaError_t allow_rings_p(int model) {
-  switch (model) {
-    case 0: return allow_rings<PREC, 0>();
-    case 1: return allow_rings<PREC, 1>();
-    case 2: return allow_rings<PREC, 2>();
-    case 3: return allow_rings<PREC, 3>();
-    default: return allow_rings<PREC, 4>();
-  }
-}
-
+// Shared-memory opt-in of the pipelined kernels; before any launch or capture.
 cudaError_t prepare_launch(const lbm_batch* b) {
-  if (b->cfg.kind != 1) return cudaSuccess;
   switch (b->prec) {
-    case LBM_F32_SHIFT: return allow_rings_p<1>(b->model);
-    case LBM_F16_SHIFT: return allow_rings_p<2>(b->model);
-    default: return cudaSuccess;
-  }
-}
-
-template <int PREC, int MODEL>
-cudaError_t launch_batch_stream(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
-  if constexpr (PREC == 0) {
-    return cudaErrorInvalidConfiguration;
-  } else {
-    using C = StreamCfg<PREC>;
-    const auto* desc = static_cast<const olbm::Desc<float>*>(b->d_desc);
-    auto k1 = olbm::batch_stream_kernel<MODEL, PREC, true, C::NC, C::STAGES>;
-    auto k0 = olbm::batch_stream_kernel<MODEL, PREC, false, C::NC, C::STAGES>;
-    auto kernel = diag ? k1 : k0;
-    kernel<<<b->ntiles, C::NC + 32, C::Shape::kSmemBytes, st>>>(desc, b->d_tiles, parity, b->d_partials, b->cfg.rows,
-                                                                 b->d_perr);
-    return cudaGetLastError();
-  }
-}
-
-template <int PREC, int MODEL>
-cudaError_t launch_batch_step(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
-  if (b->cfg.kind == 1) return launch_batch_stream<PREC, MODEL>(b, diag, parity, st);
-  using T = typename olbm::Form<PREC>::T;
-  const auto* desc = static_cast<const olbm::Desc<T>*>(b->d_desc);
-  const dim3 block(b->cfg.bx, b->cfg.by);
-  if (diag)
-    olbm::batch_step_kernel<MODEL, PREC, true><<<b->ntiles, block, 0, st>>>(desc, b->d_tiles, parity, b->d_partials,
-                                                                            b->cfg.rows);
-  else
-    olbm::batch_step_kernel<MODEL, PREC, false><<<b->ntiles, block, 0, st>>>(desc, b->d_tiles, parity,
-                                                                             b->d_partials, b->cfg.rows);
-  return cudaGetLastError();
-}
-
-template <int PREC>
-cudaError_t launch_batch_step_p(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
-  switch (b->model) {
-    case 0: return launch_batch_step<PREC, 0>(b, diag, parity, st);
-    case 1: return launch_batch_step<PREC, 1>(b, diag, parity, st);
-    case 2: return launch_batch_step<PREC, 2>(b, diag, parity, st);
-    case 3: return launch_batch_step<PREC, 3>(b, diag, parity, st);
-    default: return launch_batch_step<PREC, 4>(b, diag, parity, st);
+    case LBM_F64: return olbm::batch_prepare_f64(view(b));
+    case LBM_F32_SHIFT: return olbm::batch_prepare_f32(view(b));
+    default: return olbm::batch_prepare_f16(view(b));
   }
 }
 
 cudaError_t launch_one_step(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
   switch (b->prec) {
-    case LBM_F64: return launch_batch_step_p<0>(b, diag, parity, st);
-    case LBM_F32_SHIFT: return launch_batch_step_p<1>(b, diag, parity, st);
-    default: return launch_batch_step_p<2>(b, diag, parity, st);
+    case LBM_F64: return olbm::batch_step_f64(view(b), diag, parity, st);
+    case LBM_F32_SHIFT: return olbm::batch_step_f32(view(b), diag, parity, st);
+    default: return olbm::batch_step_f16(view(b), diag, parity, st);
+  }
+}
+
+cudaError_t launch_persistent(const lbm_batch* b, int n, int parity0, cudaStream_t st) {
+  switch (b->prec) {
+    case LBM_F64: return olbm::batch_persistent_f64(view(b), n, parity0, st);
+    case LBM_F32_SHIFT: return olbm::batch_persistent_f32(view(b), n, parity0, st);
+    default: return olbm::batch_persistent_f16(view(b), n, parity0, st);
+  }
+}
+
+cudaError_t launch_diag(const lbm_batch* b, cudaStream_t st) {
+  switch (b->prec) {
+    case LBM_F64: return olbm::batch_diag_f64(view(b), b->cur, b->rho_ref, st);
+    case LBM_F32_SHIFT: return olbm::batch_diag_f32(view(b), b->cur, b->rho_ref, st);
+    default: return olbm::batch_diag_f16(view(b), b->cur, b->rho_ref, st);
   }
 }
 
 cudaError_t launch_finalize(const lbm_batch* b, double* out, unsigned long long* sticky, cudaStream_t st) {
   olbm::batch_finalize_kernel<<<b->n, 256, 0, st>>>(b->d_partials, b->d_ranges, b->d_nodes, b->rho_ref, out, sticky);
-  return cudaGetLastError();
-}
-
-template <int PREC, int MODEL>
-cudaError_t launch_persistent_stream(lbm_batch* b, int n, int parity0, cudaStream_t st) {
-  if constexpr (PREC == 0) {
-    return cudaErrorInvalidConfiguration;
-  } else {
-    using C = StreamCfg<PREC>;
-    auto kernel = olbm::batch_stream_persistent_kernel<MODEL, PREC, C::NC, C::STAGES>;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, C::NC + 32, C::Shape::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = std::min(b->ntiles, per_sm * b->sms);
-    const auto* desc = static_cast<const olbm::Desc<float>*>(b->d_desc);
-    const int4* tiles = b->d_tiles;
-    int ntiles = b->ntiles, rows = b->cfg.rows;
-    olbm::GridBarrier* bar = b->d_bar;
-    void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows,
-                    (void*)&bar};
-    e = cudaMemsetAsync(b->d_bar, 0, sizeof(olbm::GridBarrier), st);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(C::NC + 32), args,
-                                       (size_t)C::Shape::kSmemBytes, st);
-  }
-}
-
-template <int PREC, int MODEL>
-cudaError_t launch_persistent(lbm_batch* b, int n, int parity0, cudaStream_t st) {
-  if (b->cfg.kind == 1) return launch_persistent_stream<PREC, MODEL>(b, n, parity0, st);
-  using T = typename olbm::Form<PREC>::T;
-  auto kernel = olbm::batch_persistent_kernel<MODEL, PREC>;
-  const int threads = b->cfg.bx * b->cfg.by;
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int grid = std::min(b->ntiles, per_sm * b->sms);
-  const auto* desc = static_cast<const olbm::Desc<T>*>(b->d_desc);
-  const int4* tiles = b->d_tiles;
-  int ntiles = b->ntiles, rows = b->cfg.rows;
-  olbm::GridBarrier* bar = b->d_bar;
-  void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows, (void*)&bar};
-  e = cudaMemsetAsync(b->d_bar, 0, sizeof(olbm::GridBarrier), st);
-  if (e != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(b->cfg.bx, b->cfg.by), args, 0, st);
-}
-
-template <int PREC>
-cudaError_t launch_persistent_p(lbm_batch* b, int n, int parity0, cudaStream_t st) {
-  switch (b->model) {
-    case 0: return launch_persistent<PREC, 0>(b, n, parity0, st);
-    case 1: return launch_persistent<PREC, 1>(b, n, parity0, st);
-    case 2: return launch_persistent<PREC, 2>(b, n, parity0, st);
-    case 3: return launch_persistent<PREC, 3>(b, n, parity0, st);
-    default: return launch_persistent<PREC, 4>(b, n, parity0, st);
-  }
-}
-
-template <int PREC>
-cudaError_t launch_batch_diag(const lbm_batch* b, cudaStream_t st) {
-  using T = typename olbm::Form<PREC>::T;
-  const auto* desc = static_cast<const olbm::Desc<T>*>(b->d_desc);
-  if (b->cfg.kind == 1) {
-    const int w = olbm::stream_width(b->prec);
-    olbm::batch_diag_kernel<PREC><<<b->ntiles, 256, 0, st>>>(desc, b->d_tiles, b->cur, w, w, b->cfg.rows, b->rho_ref,
-                                                             b->d_partials);
-  } else {
-    olbm::batch_diag_kernel<PREC><<<b->ntiles, dim3(b->cfg.bx, b->cfg.by), 0, st>>>(
-        desc, b->d_tiles, b->cur, b->cfg.bx, 2 * b->cfg.bx, b->cfg.by * b->cfg.rows, b->rho_ref, b->d_partials);
-  }
   return cudaGetLastError();
 }
 
@@ -701,12 +379,14 @@ int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows) {
   int s = check_batch(b);
   if (s != LBM_OK) return s;
   if (kind == 0) return lbm_batch_set_launch(b, bx, by, rows);
-  if (kind != 1 || b->prec == LBM_F64 || rows < 1 || rows > 4096)
+  if (kind != 1 || b->prec == LBM_F64 || rows < 1 || rows > 4096 || !olbm::batch_stream_nc_valid(b->prec, bx))
     return bfail(b, LBM_EINVAL,
-                 "launch kind %d with %d rows invalid (kind 1: shifted storage forms only, rows 1..4096)", kind, rows);
+                 "launch kind %d, bx %d, %d rows invalid (kind 1: shifted storage forms only, bx = consumer threads "
+                 "0 (default), 32, 64 or 128 for FP32, 64, 128 or 256 for FP16, rows 1..4096)",
+                 kind, bx, rows);
   olbm::LaunchCfg k;
   k.kind = 1;
-  k.bx = 0;
+  k.bx = bx;
   k.by = 1;
   k.rows = rows;
   b->cfg = k;
@@ -829,11 +509,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
   cudaError_t e = prepare_launch(b);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step kernel attributes");
   if (b->mode == LBM_BATCH_PERSISTENT) {
-    switch (b->prec) {
-      case LBM_F64: e = launch_persistent_p<0>(b, n, b->cur, b->stream); break;
-      case LBM_F32_SHIFT: e = launch_persistent_p<1>(b, n, b->cur, b->stream); break;
-      default: e = launch_persistent_p<2>(b, n, b->cur, b->stream); break;
-    }
+    e = launch_persistent(b, n, b->cur, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step persistent launch");
     int timed_out = 0;
     e = cudaMemcpyAsync(&timed_out, &b->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
@@ -909,12 +585,7 @@ int lbm_batch_diagnostics(lbm_batch* b, double* h_out) {
   if (s != LBM_OK) return s;
   if (!h_out) return bfail(b, LBM_EINVAL, "lbm_batch_diagnostics: NULL output");
   if (!b->initialised) return bfail(b, LBM_ESTATE, "lbm_batch_diagnostics before lbm_batch_init");
-  cudaError_t e;
-  switch (b->prec) {
-    case LBM_F64: e = launch_batch_diag<0>(b, b->stream); break;
-    case LBM_F32_SHIFT: e = launch_batch_diag<1>(b, b->stream); break;
-    default: e = launch_batch_diag<2>(b, b->stream); break;
-  }
+  cudaError_t e = launch_diag(b, b->stream);
   if (e == cudaSuccess) e = launch_finalize(b, b->d_diag_now, nullptr, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_out, b->d_diag_now, sizeof(double) * 5 * b->n, cudaMemcpyDeviceToHost, b->stream);

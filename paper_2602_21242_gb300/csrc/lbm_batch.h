@@ -1,0 +1,75 @@
+// lbm_batch.h -- batched domains (internal to liblbm.so; the public entry
+// points are the lbm_batch_* calls of include/lbm.h): the per-domain
+// descriptor, the launch view the host side hands to the per-storage-form
+// kernel translation units, and their entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace olbm {
+
+// Per-domain descriptor; CT is the scalar compute type (double or float).
+template <typename CT> struct Desc {
+  Geometry g;
+  void* buf[2];
+  Coef<CT> c;
+  int pairs;  // 1: node pairs (shifted forms, even nx)
+  int pad;
+};
+
+__host__ __device__ inline Coef<f32x2> broadcast(const Coef<float>& a) {
+  Coef<f32x2> c;
+  c.theta = a.theta;
+  c.one_m_theta = a.one_m_theta;
+  c.half_theta = a.half_theta;
+  c.omega = a.omega;
+  c.one_m_omega = a.one_m_omega;
+  c.k1 = a.k1;
+  c.k2 = a.k2;
+  c.c3 = a.c3;
+  c.tt = a.tt;
+  c.inv2t2 = a.inv2t2;
+  c.mq_inv2t2 = a.mq_inv2t2;
+  c.rho_ref = a.rho_ref;
+  c.w[0] = a.w[0];
+  c.w[1] = a.w[1];
+  c.w[2] = a.w[2];
+  return c;
+}
+
+// Consumer threads of a pipelined batch tile (launch kind 1): bx, or the
+// single-lattice default when bx = 0. Tiles are 2 NC columns wide.
+inline int batch_stream_nc(int prec, int bx) { return bx != 0 ? bx : (prec == 1 ? kStreamNC32 : kStreamNC16); }
+inline bool batch_stream_nc_valid(int prec, int bx) {
+  const int nc = batch_stream_nc(prec, bx);
+  if (prec == 1) return nc == 32 || nc == 64 || nc == 128;
+  if (prec == 2) return nc == 64 || nc == 128 || nc == 256;
+  return false;
+}
+
+// What a kernel launch needs to know of a batch.
+struct BatchLaunch {
+  int model = 0;
+  LaunchCfg cfg{};           // kind 0: bx x by threads, rows; kind 1: bx = NC selector, rows = tile rows
+  const void* desc = nullptr;  // Desc<double> (FP64) or Desc<float> (shifted forms), one per domain
+  const int4* tiles = nullptr;  // (domain, x0, y0, 0)
+  int ntiles = 0;
+  double* partials = nullptr;  // 5 doubles per tile
+  int* perr = nullptr;         // bounded-wait flag of the pipelined tile kernel
+  GridBarrier* bar = nullptr;  // persistent mode
+  int sms = 1;
+};
+
+#define OLBM_DECLARE_BATCH(SUFFIX)                                                                          \
+  cudaError_t batch_prepare_##SUFFIX(const BatchLaunch& b);                                                 \
+  cudaError_t batch_step_##SUFFIX(const BatchLaunch& b, bool diag, int parity, cudaStream_t st);           \
+  cudaError_t batch_persistent_##SUFFIX(const BatchLaunch& b, int n, int parity0, cudaStream_t st);        \
+  cudaError_t batch_diag_##SUFFIX(const BatchLaunch& b, int parity, double rho_ref, cudaStream_t st);
+
+OLBM_DECLARE_BATCH(f64)
+OLBM_DECLARE_BATCH(f32)
+OLBM_DECLARE_BATCH(f16)
+
+}  // namespace olbm

@@ -28,8 +28,9 @@ LATTICE_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
 PIPELINE_CANDIDATES = [(1, ctas, 1, rows) for ctas in (0, 1, 2) for rows in (4, 8, 16, 32, 64)]
 BATCH_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)], [2, 4, 8, 16])]
-# kind 1: the pipeline on tiles of W columns x rows (shifted forms)
-BATCH_PIPELINE_CANDIDATES = [(1, 0, 1, rows) for rows in (8, 16, 32, 64, 128)]
+# kind 1: the pipeline with bx consumer threads (0 = default) on tiles of 2 bx columns x rows
+# (shifted forms; widths a form does not offer are skipped)
+BATCH_PIPELINE_CANDIDATES = [(1, nc, 1, rows) for nc in (0, 32, 64, 128) for rows in (16, 32, 64)]
 
 
 def cache_path() -> str:

@@ -40,18 +40,20 @@ def make_batch(model, prec, mode, domains=DOMAINS):
 
 
 @pytest.mark.parametrize("mode", ["graph", "persistent"])
-@pytest.mark.parametrize("prec,kind", [("f64", 0), ("f32", 0), ("f32", 1), ("f16", 0), ("f16", 1)])
+@pytest.mark.parametrize("prec,kind,nc", [("f64", 0, 0), ("f32", 0, 0), ("f32", 1, 0), ("f32", 1, 32),
+                                           ("f16", 0, 0), ("f16", 1, 0), ("f16", 1, 64)])
 @pytest.mark.parametrize("model", [0, 3])
-def test_batch_bit_identical_to_single_lattices(model, prec, kind, mode):
+def test_batch_bit_identical_to_single_lattices(model, prec, kind, nc, mode):
     """Kind 0 tiles run the column routine, kind 1 tiles the bulk-copy pipeline (any width, including
-    1 x 5 and odd widths); each matches a single lattice stepped with the same launch kind."""
+    1 x 5 and odd widths, tiles of 2 nc columns); each matches a single lattice stepped with the same
+    launch kind."""
     f0 = states(100 + model)
     steps = 13
     with make_batch(model, prec, mode) as b:
         if kind == 0:
             b.set_launch(0, 64, 4, 2)
         else:
-            b.set_launch(1, 0, 1, 8)
+            b.set_launch(1, nc, 1, 8)
         assert b.launch()[0] == kind
         for k, f in enumerate(f0):
             b.set_state(k, f)
@@ -110,6 +112,15 @@ def test_batch_init_moments_and_diagnostics(oracle):
             for got, want in zip(mom[k], oracle.moments(f9)):
                 np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-12, atol=1e-14)
     assert t == 8 and status == capi.LBM_OK
+
+
+def test_batch_launch_validation():
+    with make_batch(3, "f32", "graph") as b:
+        for bad in [(1, 256, 1, 8), (1, 48, 1, 8), (1, 0, 1, 0), (2, 0, 1, 8)]:
+            with pytest.raises(capi.LBMError):
+                b.set_launch(*bad)
+    with make_batch(3, "f64", "graph") as b, pytest.raises(capi.LBMError):
+        b.set_launch(1, 0, 1, 8)
 
 
 def test_batch_rejects_bad_domains():
