@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # the current kernels (profiles/step_kernel_f64_complete_2048.md and
 # profiles/step_stream_kernel_f32_complete_2048.md, 2048^2, scaled to the
 # lattice by node count since traffic grows with it). Keyed by (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.7, ("f32", "complete"): 60.3}
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.7, ("f32", "complete"): 60.0}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 
 

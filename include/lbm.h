@@ -311,7 +311,8 @@ int lbm_sync(lbm_ctx* ctx);
 /*
  * Measured arithmetic ceiling of the current device (no counterpart in the
  * paper; used as the roofline denominator of ALU-bound kernels): kind 0 = FP64,
- * kind 1 = FP32, as FLOP/s of fused multiply-adds (2 FLOP each) from independent
+ * kind 1 = FP32, kind 2 = packed FP32 (fma.rn.f32x2, two FMAs per instruction),
+ * as FLOP/s of fused multiply-adds (2 FLOP each) from independent
  * FMA chains on 8 blocks per SM, best of 3 timed launches. Synchronous, runs on
  * the legacy default stream and allocates a small scratch buffer.
  */

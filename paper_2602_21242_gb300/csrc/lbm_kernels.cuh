@@ -263,10 +263,10 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
 // kinetic energy and the number of nodes whose pulled populations do not sum to
 // a finite value go to partials[block * 5 + k].
 template <int MODEL, int PREC, bool DIAG, bool PAIRS>
-__global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S* __restrict__ src,
-                                                   typename Form<PREC>::S* __restrict__ dst, Geometry g,
-                                                   Coef<typename Column<MODEL, PREC, DIAG, PAIRS>::CT> c,
-                                                   double* __restrict__ partials, int rows) {
+__device__ __forceinline__ void step_body(const typename Form<PREC>::S* __restrict__ src,
+                                          typename Form<PREC>::S* __restrict__ dst, const Geometry& g,
+                                          const Coef<typename Column<MODEL, PREC, DIAG, PAIRS>::CT>& c,
+                                          double* __restrict__ partials, int rows) {
   using Col = Column<MODEL, PREC, DIAG, PAIRS>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int x = PAIRS ? 2 * t : t;
@@ -274,6 +274,23 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
   DiagAcc<typename Col::CT> acc;
   Col::run(src, dst, g, c, x, y0, (int)blockDim.y, rows, acc);
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
+}
+
+template <int MODEL, int PREC, bool DIAG, bool PAIRS>
+__global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                   typename Form<PREC>::S* __restrict__ dst, Geometry g,
+                                                   Coef<typename Column<MODEL, PREC, DIAG, PAIRS>::CT> c,
+                                                   double* __restrict__ partials, int rows) {
+  step_body<MODEL, PREC, DIAG, PAIRS>(src, dst, g, c, partials, rows);
+}
+
+// The FP64 form is bound by the FP64 pipe, whose latency is hidden by more
+// resident warps: capped at 96 registers a thread, five blocks of 128 threads
+// fit an SM (four at the uncapped count). Launched with at most 512 threads.
+template <int MODEL, bool DIAG>
+__global__ void __maxnreg__(96) step_kernel_f64(const double* __restrict__ src, double* __restrict__ dst, Geometry g,
+                                                Coef<double> c, double* __restrict__ partials, int rows) {
+  step_body<MODEL, 0, DIAG, false>(src, dst, g, c, partials, rows);
 }
 
 }  // namespace olbm
@@ -433,12 +450,21 @@ template <int PREC> struct Launch {
     const Coef<CT> c = make_coef<CT>(a.theta, a.tau, a.rho_ref);
     const dim3 block(a.cfg.bx, a.cfg.by);
     const dim3 grid = step_grid(a.g, a.cfg, PREC);
-    if (a.diag)
-      step_kernel<MODEL, PREC, true, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
-                                                                     a.cfg.rows);
-    else
-      step_kernel<MODEL, PREC, false, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
-                                                                      a.cfg.rows);
+    if constexpr (PREC == 0) {
+      if (a.diag)
+        step_kernel_f64<MODEL, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                              a.cfg.rows);
+      else
+        step_kernel_f64<MODEL, false><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                               a.cfg.rows);
+    } else {
+      if (a.diag)
+        step_kernel<MODEL, PREC, true, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                                       a.cfg.rows);
+      else
+        step_kernel<MODEL, PREC, false, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c,
+                                                                        a.partials, a.cfg.rows);
+    }
     return cudaGetLastError();
   }
 
