@@ -30,7 +30,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % of HBM roofline, D2Q9 OReg-GEq; FP32 vs FP64 at stated error"
-BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}
+BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "f64df": 144}
 # Algorithmic FP64 operations per node of one fused step (each add, mul or FMA is
 # one operation, i.e. one FP64 pipe issue), counted from the product-form
 # collision: 33 shared (moments 16, 1/rho 3, u 2, u^2 2, u/2 2, P 8), the
@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=4096, help="lattice side (nx = ny)")
     ap.add_argument("--model", default="complete", choices=MODEL_NAMES)
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "f64df"])
     ap.add_argument("--no-forms", action="store_true", help="skip the per-model / per-precision sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
@@ -256,7 +256,8 @@ def run_gpu(args):
 
     out = {"metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else "f32",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"f64": "f64", "f64df": "f32x2 double-float (FP64 storage)"}.get(args.prec, "f32"),
            "data": "synthetic",
            "config": {"workload": workload_name(w, args.model, args.prec), "nx": w["nx"], "ny": w["ny"],
                       "collision": args.model, "storage": args.prec, "theta": w["theta"], "nu": w["nu"],

@@ -58,11 +58,20 @@ enum lbm_model {
  *   LBM_F32_SHIFT  stored as deviations f_i - rho_ref w_i(theta) in FP32, where
  *                  w_i(theta) is the rest GEq (Eq. 10 at u = 0) and rho_ref = 1;
  *                  collision arithmetic in FP32, reductions in FP64.
- *   LBM_F16_SHIFT  as LBM_F32_SHIFT with the deviations stored in IEEE FP16. */
+ *   LBM_F16_SHIFT  as LBM_F32_SHIFT with the deviations stored in IEEE FP16.
+ *   LBM_F64_DF     populations stored in FP64 (the LBM_F64 layout), collision
+ *                  arithmetic in double-float: each value the unevaluated sum of
+ *                  two FP32 numbers (about 48 significant bits, FP32 exponent
+ *                  range; magnitudes below 1.2e-38 become zero), built from
+ *                  error-free transformations on the FP32 pipes. Same results
+ *                  as LBM_F64 to about 1e-13 relative per step. Step launches
+ *                  of at most 256 threads a block; not available to lbm_vjp or
+ *                  the batched form. */
 enum lbm_prec {
   LBM_F64 = 0,
   LBM_F32_SHIFT = 1,
-  LBM_F16_SHIFT = 2
+  LBM_F16_SHIFT = 2,
+  LBM_F64_DF = 3
 };
 
 enum lbm_status {
@@ -210,8 +219,9 @@ int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const 
 
 /*
  * Launch shape of the fused step kernel (no counterpart in the paper): blocks of
- * bx x by threads (bx a multiple of 32, bx * by <= 512), each thread updating
- * `rows` nodes of one column (1 <= rows <= 64). Results do not depend on the
+ * bx x by threads (bx a multiple of 32, bx * by <= 512; <= 256 for LBM_F64_DF),
+ * each thread updating `rows` nodes (node pairs for the shifted forms when nx
+ * is even) of one column (1 <= rows <= 64). Results do not depend on the
  * shape except for the order of the diagnostics sums. Each storage form starts
  * from a default measured on GB300; lbm_set_launch may reallocate the small
  * diagnostics buffer (it then synchronises the stream). Errors: LBM_EINVAL.

@@ -192,7 +192,8 @@ extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, 
     return vfail(c, LBM_EINVAL, "lbm_vjp: the current CUDA device is not the lattice's device");
   if (n < 0 || ckpt_every < 1) return vfail(c, LBM_EINVAL, "lbm_vjp: need n >= 0 and ckpt_every >= 1");
   if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp: NULL initial field");
-  if (c->prec == LBM_F16_SHIFT) return vfail(c, LBM_EINVAL, "lbm_vjp: FP64 and FP32 storage only");
+  if (c->prec != LBM_F64 && c->prec != LBM_F32_SHIFT)
+    return vfail(c, LBM_EINVAL, "lbm_vjp: storage forms LBM_F64 and LBM_F32_SHIFT only");
   const int K = std::min(ckpt_every, std::max(n, 1));
   const int nseg = (n + K - 1) / K;
   const size_t sb = (size_t)c->state_bytes;  // one state, and one adjoint field in the same layout

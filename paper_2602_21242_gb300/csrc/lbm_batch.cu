@@ -268,7 +268,9 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
                      int prec, void* stream, lbm_batch** out) {
   if (!out || n < 1 || !nx || !ny || !theta || !tau) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: bad arguments");
   if (model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ) return bfail(nullptr, LBM_EINVAL, "unknown model %d", model);
-  if (prec < LBM_F64 || prec > LBM_F16_SHIFT) return bfail(nullptr, LBM_EINVAL, "unknown storage form %d", prec);
+  if (prec < LBM_F64 || prec > LBM_F16_SHIFT)
+    return bfail(nullptr, LBM_EINVAL, "storage form %d not available for batches (LBM_F64, LBM_F32_SHIFT, LBM_F16_SHIFT)",
+                 prec);
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation failed");
   b->n = n;

@@ -34,12 +34,12 @@ int cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-long long elem_size(int prec) { return prec == LBM_F64 ? 8 : (prec == LBM_F32_SHIFT ? 4 : 2); }
+long long elem_size(int prec) { return (prec == LBM_F64 || prec == LBM_F64_DF) ? 8 : (prec == LBM_F32_SHIFT ? 4 : 2); }
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
 bool layout_of(int nx, int ny, int prec, long long* pitch, long long* plane, long long* bytes) {
-  if (nx < 1 || ny < 1 || prec < LBM_F64 || prec > LBM_F16_SHIFT) return false;
+  if (nx < 1 || ny < 1 || prec < LBM_F64 || prec > LBM_F64_DF) return false;
   const long long es = elem_size(prec);
   const long long p = round_up(nx, 128 / es);         // 128-byte rows
   const long long pl = round_up(p * (long long)ny, 256 / es);  // 256-byte planes
@@ -63,7 +63,7 @@ long long nodes_of(const lbm_ctx* c) { return (long long)c->nx * c->ny; }
 // lbm_set_launch[_ex] (and the autotuner built on it) overrides the choice.
 olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
   olbm::LaunchCfg k;
-  if (prec == LBM_F64) {
+  if (prec == LBM_F64 || prec == LBM_F64_DF) {
     k.bx = 64, k.by = 2, k.rows = 32;
   } else if (g.nx >= 32) {
     k.kind = 1, k.bx = 0, k.by = 1, k.rows = 32;
@@ -78,6 +78,7 @@ cudaError_t launch_step(const olbm::StepArgs& a, int prec, cudaStream_t st) {
   switch (prec) {
     case LBM_F64: return olbm::launch_step_f64(a, st);
     case LBM_F32_SHIFT: return olbm::launch_step_f32(a, st);
+    case LBM_F64_DF: return olbm::launch_step_f64df(a, st);
     default: return olbm::launch_step_f16(a, st);
   }
 }
@@ -85,7 +86,8 @@ cudaError_t launch_step(const olbm::StepArgs& a, int prec, cudaStream_t st) {
 cudaError_t launch_diag(const lbm_ctx* c, cudaStream_t st) {
   const void* src = c->buf[c->cur];
   switch (c->prec) {
-    case LBM_F64: return olbm::launch_diag_f64(src, c->g, c->rho_ref, c->d_partials, st);
+    case LBM_F64:
+    case LBM_F64_DF: return olbm::launch_diag_f64(src, c->g, c->rho_ref, c->d_partials, st);
     case LBM_F32_SHIFT: return olbm::launch_diag_f32(src, c->g, c->rho_ref, c->d_partials, st);
     default: return olbm::launch_diag_f16(src, c->g, c->rho_ref, c->d_partials, st);
   }
@@ -161,7 +163,7 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   c->prec = prec;
   c->theta = theta;
   c->tau = tau;
-  c->rho_ref = (prec == LBM_F64) ? 0.0 : 1.0;
+  c->rho_ref = (prec == LBM_F64 || prec == LBM_F64_DF) ? 0.0 : 1.0;
   c->g = olbm::Geometry{nx, ny, pitch, plane};
   c->state_bytes = bytes;
   c->stream = static_cast<cudaStream_t>(stream);
@@ -231,7 +233,8 @@ int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double
   cudaError_t e;
   void* dst = ctx->buf[ctx->cur];
   switch (ctx->prec) {
-    case LBM_F64: e = olbm::launch_init_f64(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+    case LBM_F64:
+    case LBM_F64_DF: e = olbm::launch_init_f64(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
     case LBM_F32_SHIFT: e = olbm::launch_init_f32(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
     default: e = olbm::launch_init_f16(d_rho, d_ux, d_uy, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
   }
@@ -362,7 +365,8 @@ int lbm_moments(lbm_ctx* ctx, double* d_rho, double* d_ux, double* d_uy) {
   const void* src = ctx->buf[ctx->cur];
   cudaError_t e;
   switch (ctx->prec) {
-    case LBM_F64: e = olbm::launch_moments_f64(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
+    case LBM_F64:
+    case LBM_F64_DF: e = olbm::launch_moments_f64(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
     case LBM_F32_SHIFT: e = olbm::launch_moments_f32(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
     default: e = olbm::launch_moments_f16(src, ctx->g, ctx->rho_ref, d_rho, d_ux, d_uy, ctx->stream); break;
   }
@@ -395,7 +399,8 @@ int lbm_get_state(lbm_ctx* ctx, double* d_f) {
   const void* src = ctx->buf[ctx->cur];
   cudaError_t e;
   switch (ctx->prec) {
-    case LBM_F64: e = olbm::launch_get_state_f64(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
+    case LBM_F64:
+    case LBM_F64_DF: e = olbm::launch_get_state_f64(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
     case LBM_F32_SHIFT: e = olbm::launch_get_state_f32(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
     default: e = olbm::launch_get_state_f16(src, ctx->g, ctx->theta, ctx->rho_ref, d_f, ctx->stream); break;
   }
@@ -409,7 +414,8 @@ int lbm_set_state(lbm_ctx* ctx, const double* d_f) {
   void* dst = ctx->buf[ctx->cur];
   cudaError_t e;
   switch (ctx->prec) {
-    case LBM_F64: e = olbm::launch_set_state_f64(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
+    case LBM_F64:
+    case LBM_F64_DF: e = olbm::launch_set_state_f64(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
     case LBM_F32_SHIFT: e = olbm::launch_set_state_f32(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
     default: e = olbm::launch_set_state_f16(d_f, ctx->g, ctx->theta, ctx->rho_ref, dst, ctx->stream); break;
   }
@@ -482,6 +488,8 @@ int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows) {
                 "launch kind %d shape %dx%d x %d rows invalid (kind 0: bx a multiple of 32, bx*by <= 512, rows 1..64; "
                 "kind 1: rows 1..4096)",
                 kind, bx, by, rows);
+  if (ctx->prec == LBM_F64_DF && (k.kind != 0 || bx * by > 256))
+    return fail(ctx, LBM_EINVAL, "storage form LBM_F64_DF takes launch kind 0 with at most 256 threads a block");
   const long long need = olbm::step_blocks(ctx->g, k, ctx->prec);
   if (need > ctx->parts_cap) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);

@@ -178,6 +178,12 @@ __device__ __forceinline__ double recip(double x) {
 __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 __device__ __forceinline__ f32x2 recip(f32x2 x) { return f32x2(make_float2(1.0f / x.v.x, 1.0f / x.v.y)); }
 
+// k x and k x + c for a power of two k (exact scaling); the double-float type
+// overloads them with a scaling of both parts, two instructions instead of a
+// full product.
+template <typename T> __device__ __forceinline__ T scaled(T x, float k) { return T(k) * x; }
+template <typename T> __device__ __forceinline__ T fma_scaled(T x, float k, T c) { return fma(T(k), x, c); }
+
 // ---------------------------------------------------------------- collision
 // In-place collision of one node (Eq. 1a). f holds the stored values of the
 // pulled pre-collision populations (absolute, or deviations from the rest
@@ -208,12 +214,12 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
   mom.m0 = m0;
   mom.jx = jx;
   mom.jy = jy;
-  mom.ke = T(0.5) * fma(jx, ux, jy * uy);
+  mom.ke = scaled(fma(jx, ux, jy * uy), 0.5f);
 
   const T ux2 = ux * ux, uy2 = uy * uy;
   // Per-axis GEq factors P(a) (Eq. 10), a = -1, 0, +1, and their deviations
   // dP = P - W from the rest values (dP(0) = -u^2, dP(+-1) = (u^2 +- u)/2).
-  const T hux = T(0.5) * ux, huy = T(0.5) * uy;
+  const T hux = scaled(ux, 0.5f), huy = scaled(uy, 0.5f);
   // Shifted forms need dP exactly (no cancellation against W); the absolute form
   // only needs P, one operation cheaper per axis.
   T dx[3], dy[3], px[3], py[3];
@@ -223,7 +229,7 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
     px[0] = c.half_theta + dx[0], px[1] = c.one_m_theta - ux2, px[2] = c.half_theta + dx[2];
     py[0] = c.half_theta + dy[0], py[1] = c.one_m_theta - uy2, py[2] = c.half_theta + dy[2];
   } else {
-    const T hx = fma(T(0.5), ux2, c.half_theta), hy = fma(T(0.5), uy2, c.half_theta);
+    const T hx = fma_scaled(ux2, 0.5f, c.half_theta), hy = fma_scaled(uy2, 0.5f, c.half_theta);
     px[0] = hx - hux, px[1] = c.one_m_theta - ux2, px[2] = hx + hux;
     py[0] = hy - huy, py[1] = c.one_m_theta - uy2, py[2] = hy + huy;
   }
@@ -272,10 +278,10 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
       const T wpsy = -A1 * uy * (c.c3 - uy2);  // omega' psi_y
       if constexpr (MODEL == 2) {
         // Psi^P: -1/2 c_ia psi_a on the axis populations.
-        cor[1] = T(-0.5) * wpsx;
-        cor[3] = T(0.5) * wpsx;
-        cor[2] = T(-0.5) * wpsy;
-        cor[4] = T(0.5) * wpsy;
+        cor[1] = scaled(wpsx, -0.5f);
+        cor[3] = scaled(wpsx, 0.5f);
+        cor[2] = scaled(wpsy, -0.5f);
+        cor[4] = scaled(wpsy, 0.5f);
       } else {
         // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12, evaluated on f^OReg (model 3):
         // pref = -(K1/2)(mu_xx + mu_yy); or on f^neq (model 4): pref = -K1.
@@ -285,17 +291,17 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
           const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
           hwpref = c.mq_inv2t2 * A1 * (muxx + muyy);
         } else {
-          hwpref = T(-0.5) * A1;
+          hwpref = scaled(A1, -0.5f);
         }
         const T hPxx = -hwpref * fma(ux2, ux2 - T(1.0), c.tt);       // omega' Pi~_xx / 2
         const T hPyy = hwpref * fma(uy2, uy2 - T(1.0), c.tt);        // omega' Pi~_yy / 2
-        const T qPxy = T(0.5) * hwpref * (ux * uy) * (ux2 - uy2);  // omega' Pi~_xy / 4
-        const T hpsx = T(0.5) * wpsx, hpsy = T(0.5) * wpsy;
+        const T qPxy = scaled(hwpref, 0.5f) * (ux * uy) * (ux2 - uy2);  // omega' Pi~_xy / 4
+        const T hpsx = scaled(wpsx, 0.5f), hpsy = scaled(wpsy, 0.5f);
         cor[1] = hPyy - hpsx;
         cor[3] = hPyy + hpsx;
         cor[2] = hPxx - hpsy;
         cor[4] = hPxx + hpsy;
-        const T dsum = T(-0.5) * (hPxx + hPyy);
+        const T dsum = scaled(hPxx + hPyy, -0.5f);
         cor[5] = dsum - qPxy;  // c_x c_y = +1
         cor[7] = dsum - qPxy;
         cor[6] = dsum + qPxy;  // c_x c_y = -1

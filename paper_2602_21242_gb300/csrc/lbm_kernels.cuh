@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "lbm_device.cuh"
+#include "lbm_df64.cuh"
 #include "lbm_launch.h"
 
 namespace olbm {
@@ -148,6 +149,13 @@ template <> __device__ __forceinline__ void DiagAcc<float>::add(const NodeMoment
     ++bad;
   }
 }
+template <> __device__ __forceinline__ void DiagAcc<df64>::add(const NodeMoments<df64>& m) {
+  if (finite_bits(m.m0.hi)) {
+    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
+  } else {
+    ++bad;
+  }
+}
 template <> __device__ __forceinline__ void DiagAcc<f32x2>::add(const NodeMoments<f32x2>& m) {
   const bool ok0 = finite_bits(m.m0.v.x), ok1 = finite_bits(m.m0.v.y);
   if (ok0 && ok1) {
@@ -169,6 +177,12 @@ template <typename CT> __device__ __forceinline__ void block_diag_acc(DiagAcc<CT
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[k] = a.v[k].v.x + a.v[k].v.y;
     block_diag<float>(v, a.bad, out5);
+  } else if constexpr (std::is_same<CT, df64>::value) {
+    double v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = join_f64(a.v[k]);
+    block_diag<double>(v, a.bad, out5);
+
   } else {
     block_diag<CT>(a.v, a.bad, out5);
   }
@@ -232,6 +246,33 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
     } else {
       xp = (x == g.nx - 1) ? 0 : x + 1;
     }
+    if constexpr (PREC == 3) {
+      // Double-float form: the loads stay raw FP64 until their row is computed,
+      // so the next row's loads are in flight during the current row's arithmetic
+      // (splitting them at load time would wait for each load at once).
+      using Raw = Column<MODEL, 0, DIAG, false, CG>;
+      double r[9], rn[9];
+      int y = y0;
+      if (y < g.ny) Raw::pull(src, g, x, xm, xp, y, r);
+      for (int k = 0; k < rows && y < g.ny; ++k, y += dy) {
+        const bool more = (k + 1 < rows) && (y + dy < g.ny);
+        if (more) Raw::pull(src, g, x, xm, xp, y + dy, rn);
+        CT f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = split_f64(r[i]);
+        NodeMoments<CT> m;
+        collide<MODEL, false, CT>(f, c, m);
+        S* q = dst + (long long)y * g.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
+        if constexpr (DIAG) acc.add(m);
+        if (more) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) r[i] = rn[i];
+        }
+      }
+      return;
+    }
     CT f[9], fn[9];
     int y = y0;
     if (y < g.ny) pull(src, g, x, xm, xp, y, f);
@@ -282,6 +323,16 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
                                                    Coef<typename Column<MODEL, PREC, DIAG, PAIRS>::CT> c,
                                                    double* __restrict__ partials, int rows) {
   step_body<MODEL, PREC, DIAG, PAIRS>(src, dst, g, c, partials, rows);
+}
+
+// Double-float form (3): its state per node is as large as the FP64 form's
+// but its dependent chains are longer; at most 256 threads a block, so that
+// the compiler may keep it all in registers.
+template <int MODEL, bool DIAG, bool PAIRS>
+__global__ void __launch_bounds__(256) step_kernel_df(const double* __restrict__ src, double* __restrict__ dst,
+                                                      Geometry g, Coef<typename Column<MODEL, 3, DIAG, PAIRS>::CT> c,
+                                                      double* __restrict__ partials, int rows) {
+  step_body<MODEL, 3, DIAG, PAIRS>(src, dst, g, c, partials, rows);
 }
 
 // The FP64 form is bound by the FP64 pipe, whose latency is hidden by more
@@ -421,12 +472,12 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 
 // ------------------------------------------------------------------ launchers
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
-// The shifted forms update node pairs (x, x + 1) when nx is even.
-inline bool uses_pairs(int prec, const Geometry& g) { return prec != 0 && (g.nx % 2) == 0; }
+// The shifted forms (1, 2) update node pairs (x, x + 1) when nx is even.
+inline bool uses_pairs(int prec, const Geometry& g) { return (prec == 1 || prec == 2) && (g.nx % 2) == 0; }
 // The pipeline kernel (launch kind 1) applies to the shifted forms, any nx.
 inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
   (void)g;
-  return k.kind == 1 && prec != 0;
+  return k.kind == 1 && (prec == 1 || prec == 2);
 }
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   if (uses_stream(prec, g, k)) {
@@ -450,7 +501,15 @@ template <int PREC> struct Launch {
     const Coef<CT> c = make_coef<CT>(a.theta, a.tau, a.rho_ref);
     const dim3 block(a.cfg.bx, a.cfg.by);
     const dim3 grid = step_grid(a.g, a.cfg, PREC);
-    if constexpr (PREC == 0) {
+    if constexpr (PREC == 3) {
+      if (block.x * block.y > 256) return cudaErrorInvalidConfiguration;
+      if (a.diag)
+        step_kernel_df<MODEL, true, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                                    a.cfg.rows);
+      else
+        step_kernel_df<MODEL, false, PAIRS><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
+                                                                     a.cfg.rows);
+    } else if constexpr (PREC == 0) {
       if (a.diag)
         step_kernel_f64<MODEL, true><<<grid, block, 0, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials,
                                                               a.cfg.rows);
@@ -508,8 +567,10 @@ template <int PREC> struct Launch {
 
   template <int MODEL>
   static cudaError_t step_m(const StepArgs& a, cudaStream_t st) {
-    if constexpr (PREC != 0) {
+    if constexpr (PREC == 1 || PREC == 2) {
       if (uses_stream(PREC, a.g, a.cfg)) return a.diag ? stream_d<MODEL, true>(a, st) : stream_d<MODEL, false>(a, st);
+    }
+    if constexpr (PREC == 1 || PREC == 2) {
       if (uses_pairs(PREC, a.g)) return step_p<MODEL, true>(a, st);
     }
     return step_p<MODEL, false>(a, st);

@@ -60,6 +60,9 @@ long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec);
 OLBM_DECLARE_LAUNCHERS(f64)
 OLBM_DECLARE_LAUNCHERS(f32)
 OLBM_DECLARE_LAUNCHERS(f16)
+// storage form 3 (FP64 storage, double-float arithmetic): its own step kernel; the
+// other kernels are the FP64 form's (same storage)
+cudaError_t launch_step_f64df(const StepArgs& a, cudaStream_t st);
 
 // Record a message for lbm_last_error(NULL) on this thread; returns status.
 int set_thread_error(int status, const char* fmt, ...);
