@@ -332,8 +332,9 @@ def lat_bytes(prec, n):
 
 
 def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=200):
-    """MLUPS of every model in FP64 and of the complete model in the shifted FP32 / FP16 forms,
-    with the velocity error of the shifted forms against FP64 after err_steps steps."""
+    """MLUPS of every model in FP64 and in the double-float form (FP64 storage, FP32-pair
+    arithmetic), and of the complete model in the shifted FP32 / FP16 forms, with the velocity
+    error of the non-FP64 forms against FP64 after err_steps steps."""
     import torch
 
     from paper_2602_21242_gb300.lattice import Lattice
@@ -361,18 +362,20 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
 
     for model in MODEL_NAMES:
         res[f"{model}/f64"] = timed(model, "f64")
+    for model in MODEL_NAMES:
+        res[f"{model}/f64df"] = timed(model, "f64df")
     for prec in ("f32", "f16"):
         res[f"complete/{prec}"] = timed("complete", prec)
 
-    # velocity error of the shifted forms against FP64 on the same flow
+    # velocity error of the double-float and shifted forms against FP64 on the same flow
     finals = {}
-    for prec in ("f64", "f32", "f16"):
+    for prec in ("f64", "f64df", "f32", "f16"):
         lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], "complete", prec, device=dev, stream=stream)
         lat.init(*fields)
         lat.step(err_steps)
         finals[prec] = [t.clone() for t in lat.moments()]
         lat.close()
-    for prec in ("f32", "f16"):
+    for prec in ("f64df", "f32", "f16"):
         du = max(float((finals[prec][k] - finals["f64"][k]).abs().max()) for k in (1, 2))
         dr = float((finals[prec][0] - finals["f64"][0]).abs().max())
         res[f"complete/{prec}"]["error_vs_f64"] = {
