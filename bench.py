@@ -68,6 +68,9 @@ def parse_args():
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 256-domain batched workload")
     ap.add_argument("--batch-tile", default="", help="kind,bx,by,rows (or bx,by,rows for kind 0) of the batched tiles (default: autotuned)")
+    ap.add_argument("--config-sweep", action="store_true",
+                    help="time every model, U and theta of the 4096^2 shear-wave benchmark (FP64 and double-float)")
+    ap.add_argument("--sweep-steps", type=int, default=200)
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the 256-domain batched workload (graph and persistent modes) and print its JSON")
     return ap.parse_args()
@@ -521,11 +524,46 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def config_sweep(args):
+    """The bandwidth benchmark's full matrix: 4096^2 advected shear wave with u_x = U in {0, 0.1, 0.2},
+    theta in {0.25, 1/3, 0.4}, nu = 0.005, every model, FP64 and the double-float form; MLUPS over
+    `--sweep-steps` steps with fused diagnostics every step, and whether the state stayed finite."""
+    import torch
+
+    from paper_2602_21242_gb300 import flows
+    from paper_2602_21242_gb300.lattice import Lattice
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, nu, steps = 4096, 0.005, args.sweep_steps
+    table = {}
+    for U in (0.0, 0.1, 0.2):
+        fields = [torch.from_numpy(a).to(dev) for a in flows.shear_wave(n, n, U=U, amp=0.01)]
+        for theta in (0.25, 1.0 / 3.0, 0.4):
+            for prec in ("f64", "f64df"):
+                for model in MODEL_NAMES:
+                    with Lattice(n, n, theta, nu / theta + 0.5, model, prec, device=dev, stream=stream) as lat:
+                        lat.init(*fields)
+                        lat.set_diagnostics_interval(1)
+                        lat.step(5)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        lat.step(steps)
+                        e1.record(stream)
+                        torch.cuda.synchronize(dev)
+                        ms = e0.elapsed_time(e1) / steps
+                        d, t, status = lat.step_diagnostics(raise_nonfinite=False)
+                    table[f"U={U}/theta={theta:.3f}/{prec}/{model}"] = {
+                        "mlups": round(n * n / (ms * 1e-3) / 1e6, 1), "finite": status == 0 and d[4] == 0}
+    print(json.dumps({"sweep": "4096^2 advected shear wave, nu=0.005", "steps": steps, "results": table}),
+          flush=True)
+
+
 def precision_study(args):
     """8192^2 doubly periodic shear layer (u_x = 0.1 tanh((y - ny/4)/80), mirrored; u_y = 0.005
     sin(2 pi x / nx)), theta = 0.3, nu = 1e-3, completely corrected model, `--study-steps` steps in
-    FP64, FP32-shifted and FP16-shifted storage; prints the velocity and density error of the
-    shifted forms against FP64 and each form's throughput. LBGK is run in FP64 alongside to record
+    FP64, FP64 storage with double-float arithmetic, FP32-shifted and FP16-shifted storage; prints
+    the velocity and density error of the other forms against FP64 and each form's throughput. LBGK is run in FP64 alongside to record
     whether it stays finite at this Reynolds number (U N / nu = 8.2e5)."""
     import torch
 
@@ -538,7 +576,8 @@ def precision_study(args):
     tau = nu / theta + 0.5
     fields = [torch.from_numpy(a).to(dev) for a in flows.shear_layer(n, n, U=U, width=80.0, delta_amp=0.005)]
     res, final = {}, {}
-    for model, prec in (("complete", "f64"), ("complete", "f32"), ("complete", "f16"), ("lbgk", "f64")):
+    for model, prec in (("complete", "f64"), ("complete", "f64df"), ("complete", "f32"), ("complete", "f16"),
+                        ("lbgk", "f64")):
         with Lattice(n, n, theta, tau, model, prec, device=dev, stream=stream) as lat:
             lat.init(*fields)
             lat.set_diagnostics_interval(100)
@@ -553,7 +592,7 @@ def precision_study(args):
                 final[prec] = [x.clone() for x in lat.moments()]
             res[f"{model}/{prec}"] = {"mlups": round(n * n * args.study_steps / (ms * 1e-3) / 1e6, 1),
                                       "finite": status == 0 and d[4] == 0, "mass": d[0], "t_diag": t}
-    for prec in ("f32", "f16"):
+    for prec in ("f64df", "f32", "f16"):
         du = max(float((final[prec][k] - final["f64"][k]).abs().max()) for k in (1, 2))
         du_rms = max(float(((final[prec][k] - final["f64"][k]) ** 2).mean().sqrt()) for k in (1, 2))
         dr = float((final[prec][0] - final["f64"][0]).abs().max())
@@ -610,6 +649,9 @@ def main():
         return
     if args.precision_study:
         precision_study(args)
+        return
+    if args.config_sweep:
+        config_sweep(args)
         return
     if args.batch_only:
         import torch
