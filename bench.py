@@ -345,10 +345,10 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
     n = w["nx"] * w["ny"]
     res = {}
 
-    def timed(model, prec):
+    def timed(model, prec, diag_every=1):
         lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], model, prec, device=dev, stream=stream)
         lat.init(*fields)
-        lat.set_diagnostics_interval(1)
+        lat.set_diagnostics_interval(diag_every)
         lat.step(warm)
         lat.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -369,6 +369,7 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
         res[f"{model}/f64df"] = timed(model, "f64df")
     for prec in ("f32", "f16"):
         res[f"complete/{prec}"] = timed("complete", prec)
+        res[f"complete/{prec}/diagnostics_every_100"] = timed("complete", prec, 100)
 
     # velocity error of the double-float and shifted forms against FP64 on the same flow
     finals = {}

@@ -17,10 +17,11 @@
 // for this collision on GB300: the packed pair state needs about 220 registers
 // a thread, too few warps remain to cover the long dependent chains.
 //
-// Conversions from and to FP64 storage work on the bit patterns with integer
-// instructions, so a step issues no FP64 instruction except the one addition
-// that joins hi and lo on the way out: on GB300 the FP64 pipe runs at 1/64 of
-// the FP32 rate. Magnitudes below 2^-126 (about 1.2e-38) convert to zero.
+// Conversions from FP64 storage work on the bit patterns with integer
+// instructions; on the way out hi is widened the same way and lo converted and
+// added on the FP64 pipe, two FP64-pipe instructions per stored value (on GB300
+// the FP64 pipe runs at 1/64 of the FP32 rate). Magnitudes below 2^-126 (about
+// 1.2e-38) convert to zero.
 #pragma once
 
 #include <cstdint>
@@ -111,26 +112,24 @@ template <class F> __device__ __forceinline__ dfloat<F> recip(dfloat<F> x) {
 // ---------------------------------------------------------------- FP64 <-> double-float
 // Split a double into hi + lo with integer instructions: hi takes the sign,
 // the exponent and the leading 23 stored mantissa bits (a truncation), lo the
-// remaining 29 bits rounded to FP32, then Fast2Sum renormalises. NaN and
-// infinity keep their class in hi; magnitudes below 2^-126 become zero.
+// remaining 29 bits rounded to FP32 (so |lo| < ulp(hi): the pair is left
+// unnormalised, which the operations above accept). NaN and infinity keep their
+// class in hi; magnitudes below 2^-126 become zero, above FP32's range infinity.
+// Cases are selected without branches.
 __device__ __forceinline__ df64 split_f64(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
   const unsigned sign = h32 & 0x80000000u;
   const int E = (int)((h32 >> 20) & 0x7FFu);
   const unsigned m23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
   const unsigned rest = l32 & 0x1FFFFFFFu;
   const int fe = E - 896;  // FP32 biased exponent of the same power of two
-  if (E == 0x7FF) return df64(__uint_as_float(sign | 0x7F800000u | m23 | (rest != 0u ? 1u : 0u)), 0.0f);
-  if (fe <= 0) return df64(__uint_as_float(sign), 0.0f);
-  if (fe >= 255) return df64(__uint_as_float(sign | 0x7F800000u), 0.0f);
-  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | m23);
-  // rest * 2^(E - 1075); the scale is an FP32 normal number while E >= 949
-  float lo = 0.0f;
-  if (E >= 949) lo = __fmul_rn(__uint2float_rn(rest), __uint_as_float((unsigned)(E - 948) << 23));
-  lo = __uint_as_float(__float_as_uint(lo) | sign);
-  const float s = __fadd_rn(hi, lo);
-  return df64(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+  unsigned hib = sign | ((unsigned)min(max(fe, 0), 255) << 23) | m23;
+  hib = fe <= 0 ? sign : (fe >= 255 ? (sign | 0x7F800000u | (E == 0x7FF ? (m23 | (rest != 0u)) : 0u)) : hib);
+  // rest * 2^(E - 1075): the scale's FP32 exponent E - 948 is clamped at 0 (scale 0)
+  // below FP32's normal range, where lo would underflow anyway
+  const float scale = __uint_as_float((unsigned)min(max(E - 948, 0), 254) << 23);
+  const float lo = (fe > 0 && fe < 255) ? __fmul_rn(__uint2float_rn(rest), scale) : 0.0f;
+  return df64(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) | sign));
 }
 
 // FP32 -> FP64 by exponent rebias (exact; FP32 subnormals become zero).
@@ -144,8 +143,9 @@ __device__ __forceinline__ double widen_f32(float f) {
   return __longlong_as_double((long long)(sign | (E << 52) | m));
 }
 
-// hi + lo rounded to FP64: the one FP64 instruction of the conversion.
-__device__ __forceinline__ double join_f64(df64 v) { return widen_f32(v.hi) + widen_f32(v.lo); }
+// hi + lo rounded to FP64: hi widened with integer instructions, lo converted
+// and added on the FP64 pipe (two FP64-pipe instructions a value).
+__device__ __forceinline__ double join_f64(df64 v) { return widen_f32(v.hi) + (double)v.lo; }
 
 // Storage form 3: FP64 populations, double-float arithmetic.
 template <> struct Form<3> {

@@ -251,3 +251,55 @@ def test_vjp_and_batch_argument_errors():
             capi.lbm_set_launch_ex(lat.ctx, 0, 48, 4, 4)  # bx not a multiple of 32
         with pytest.raises(capi.LBMError):
             capi.lbm_set_launch_ex(lat.ctx, 2, 32, 4, 4)  # unknown kind
+
+
+@pytest.mark.parametrize("model", [0, 3])
+def test_full_size_sampled_parity_f64df(oracle, model):
+    """The benchmark workload in the double-float form (FP64 storage): 20 fused steps with diagnostics
+    every step, then 512 sampled nodes over one step against the oracle's collision, 2e-13 relative
+    (one step of double-float rounding, about 2^-47 per operation)."""
+    n, theta = 4096, 1.0 / 3.0
+    tau = oracle.tau_from_nu(0.005, theta)
+    rho, ux, uy = flows.shear_wave(n, n, U=0.1, amp=0.01)
+    with Lattice(n, n, theta, tau, model, "f64df") as lat:
+        lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+        lat.set_diagnostics_interval(1)
+        lat.step(20)
+        d, t, status = lat.step_diagnostics()
+        assert t == 19 and status == capi.LBM_OK
+        assert d[0] == pytest.approx(n * n, rel=1e-13)
+        assert d[1] == pytest.approx(0.1 * n * n, rel=1e-12)
+        _one_step_sample_check(oracle, lat, theta, tau, model, 512, 91 + model, 2e-13)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_full_size_sampled_shifted_forms(oracle, prec):
+    """The benchmark workload in the shifted forms (bulk-copy pipeline, diagnostics every step): 512
+    sampled nodes over one step against the oracle's FP64 collision of the same pre-collision values.
+    Bound per population: storage rounding of the stored deviation (2^-24 FP32, 2^-11 FP16) plus a few
+    FP32 ulps of the O(deviation) arithmetic, as k 2^-p max|f - rest| with k = 16 (FP32), 1.5 (FP16)."""
+    n, theta = 4096, 1.0 / 3.0
+    tau = oracle.tau_from_nu(0.005, theta)
+    rho, ux, uy = flows.shear_wave(n, n, U=0.1, amp=0.01)
+    w0, w1 = 1 - theta, theta / 2
+    rest = np.array([w0, w1, w0, w1, w0, w1, w1, w1, w1]) * np.array([w0, w0, w1, w0, w1, w1, w1, w1, w1])
+    with Lattice(n, n, theta, tau, "complete", prec) as lat:
+        assert capi.lbm_get_launch_ex(lat.ctx)[0] == 1  # the pipeline, as benchmarked
+        lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+        lat.set_diagnostics_interval(1)
+        lat.step(20)
+        nx, ny = lat.nx, lat.ny
+        g = flows.rng(55)
+        xs = torch.from_numpy(g.integers(0, nx, 512)).cuda()
+        ys = torch.from_numpy(g.integers(0, ny, 512)).cuda()
+        pre = lat.state()[:, ys, xs].cpu().numpy().T
+        lat.step(1)
+        f1 = lat.state()
+        cx, cy = torch.tensor(CX).cuda(), torch.tensor(CY).cuda()
+        post = f1[torch.arange(9).cuda()[None, :], (ys[:, None] + cy[None, :]) % ny,
+                  (xs[:, None] + cx[None, :]) % nx].cpu().numpy()
+    k, p = (16, 24) if prec == "f32" else (1.5, 11)
+    for j in range(512):
+        want = oracle.collide_node(pre[j], theta, tau, 3)
+        d = max(np.abs(pre[j] - rest).max(), np.abs(want - rest).max())
+        assert np.abs(post[j] - want).max() <= k * 2.0 ** -p * d, f"node {j}"
