@@ -65,8 +65,8 @@ enum lbm_model {
  *                  range; magnitudes below 1.2e-38 become zero), built from
  *                  error-free transformations on the FP32 pipes. Same results
  *                  as LBM_F64 to about 1e-13 relative per step. Step launches
- *                  of at most 256 threads a block; not available to lbm_vjp or
- *                  the batched form. */
+ *                  of at most 256 threads a block; lbm_vjp runs its adjoint in
+ *                  double-float too; not available to the batched form. */
 enum lbm_prec {
   LBM_F64 = 0,
   LBM_F32_SHIFT = 1,
@@ -195,8 +195,9 @@ int lbm_set_state(lbm_ctx* ctx, const double* d_f);
  * every ckpt_every steps, then per segment, last first, a recomputation of its
  * states and the adjoint steps lambda(t) = J_C(f(t))^T S^T lambda(t + 1), where S^T
  * reads lambda_i(t + 1) at x + c_i and J_C^T is the hand-derived transposed
- * Jacobian of the model's collision. FP64 and FP32 storage (the FP32 form's
- * adjoint runs in FP32); LBM_EINVAL for FP16. Device work memory of
+ * Jacobian of the model's collision. FP64, double-float and FP32 storage (the
+ * adjoint runs in the form's arithmetic: FP64, double-float pairs, FP32);
+ * LBM_EINVAL for FP16. Device work memory of
  * (ceil(n / ckpt_every) + ckpt_every + 2) population buffers is kept by the
  * lattice. Asynchronous; on return the lattice holds f(x, n) of this run.
  */

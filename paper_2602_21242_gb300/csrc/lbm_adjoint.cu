@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kABX* kABY) adj_final_kernel(const typename Fo
   for (int a = -1; a <= 1; ++a)
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
-      const double l = (double)lam[pop_index(a, b) * g.plane + here];
+      const double l = to_double(lam[pop_index(a, b) * g.plane + here]);
       gr += l * px[a + 1] * py[b + 1];
       gx += l * dpx[a + 1] * py[b + 1];
       gy += l * px[a + 1] * dpy[b + 1];
@@ -163,6 +163,33 @@ int vfail(lbm_ctx* c, int status, const char* msg, cudaError_t e = cudaSuccess) 
   return status;
 }
 
+int elem_bytes(const lbm_ctx* c) { return c->prec == LBM_F32_SHIFT ? 4 : 8; }
+
+cudaError_t adj_seed(lbm_ctx* c, const double* gr, const double* gx, const double* gy, void* lam) {
+  switch (c->prec) {
+    case LBM_F64: return olbm::Adjoint<0>::seed(c->buf[c->cur], c->g, c->rho_ref, gr, gx, gy, lam, c->stream);
+    case LBM_F64_DF: return olbm::Adjoint<3>::seed(c->buf[c->cur], c->g, c->rho_ref, gr, gx, gy, lam, c->stream);
+    default: return olbm::Adjoint<1>::seed(c->buf[c->cur], c->g, c->rho_ref, gr, gx, gy, lam, c->stream);
+  }
+}
+
+cudaError_t adj_step(lbm_ctx* c, const void* fbuf, const void* lam_next, void* lam) {
+  switch (c->prec) {
+    case LBM_F64: return olbm::Adjoint<0>::step(c->model, fbuf, lam_next, lam, c->g, c->theta, c->tau, c->rho_ref, c->stream);
+    case LBM_F64_DF: return olbm::Adjoint<3>::step(c->model, fbuf, lam_next, lam, c->g, c->theta, c->tau, c->rho_ref, c->stream);
+    default: return olbm::Adjoint<1>::step(c->model, fbuf, lam_next, lam, c->g, c->theta, c->tau, c->rho_ref, c->stream);
+  }
+}
+
+cudaError_t adj_final(lbm_ctx* c, const void* lam, const double* r0, const double* u0, const double* v0, double* gr,
+                      double* gx, double* gy) {
+  switch (c->prec) {
+    case LBM_F64: return olbm::Adjoint<0>::final_(lam, c->g, c->theta, r0, u0, v0, gr, gx, gy, c->stream);
+    case LBM_F64_DF: return olbm::Adjoint<3>::final_(lam, c->g, c->theta, r0, u0, v0, gr, gx, gy, c->stream);
+    default: return olbm::Adjoint<1>::final_(lam, c->g, c->theta, r0, u0, v0, gr, gx, gy, c->stream);
+  }
+}
+
 cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
   olbm::StepArgs a;
   a.model = c->model;
@@ -175,9 +202,11 @@ cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
   a.rho_ref = c->rho_ref;
   a.partials = c->d_partials;
   a.cfg = c->cfg;
-  cudaError_t e = c->prec == LBM_F64 ? olbm::launch_step_f64(a, c->stream) : olbm::launch_step_f32(a, c->stream);
+  cudaError_t e = c->prec == LBM_F64      ? olbm::launch_step_f64(a, c->stream)
+                  : c->prec == LBM_F64_DF ? olbm::launch_step_f64df(a, c->stream)
+                                          : olbm::launch_step_f32(a, c->stream);
   if (e == cudaSuccess && c->n_walls > 0)
-    e = olbm::launch_walls(c->prec == LBM_F64 ? 8 : 4, src, dst, c->g, c->d_walls, c->n_walls, c->stream);
+    e = olbm::launch_walls(elem_bytes(c), src, dst, c->g, c->d_walls, c->n_walls, c->stream);
   return e;
 }
 
@@ -192,8 +221,8 @@ extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, 
     return vfail(c, LBM_EINVAL, "lbm_vjp: the current CUDA device is not the lattice's device");
   if (n < 0 || ckpt_every < 1) return vfail(c, LBM_EINVAL, "lbm_vjp: need n >= 0 and ckpt_every >= 1");
   if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp: NULL initial field");
-  if (c->prec != LBM_F64 && c->prec != LBM_F32_SHIFT)
-    return vfail(c, LBM_EINVAL, "lbm_vjp: storage forms LBM_F64 and LBM_F32_SHIFT only");
+  if (c->prec == LBM_F16_SHIFT)
+    return vfail(c, LBM_EINVAL, "lbm_vjp: storage forms LBM_F64, LBM_F64_DF and LBM_F32_SHIFT only");
   const int K = std::min(ckpt_every, std::max(n, 1));
   const int nseg = (n + K - 1) / K;
   const size_t sb = (size_t)c->state_bytes;  // one state, and one adjoint field in the same layout
@@ -231,8 +260,7 @@ extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, 
   }
   // seed lambda(n)
   int li = 0;
-  e = c->prec == LBM_F64 ? olbm::Adjoint<0>::seed(c->buf[c->cur], c->g, c->rho_ref, g_rho, g_ux, g_uy, lam[li], c->stream)
-                         : olbm::Adjoint<1>::seed(c->buf[c->cur], c->g, c->rho_ref, g_rho, g_ux, g_uy, lam[li], c->stream);
+  e = adj_seed(c, g_rho, g_ux, g_uy, lam[li]);
   if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp seed", e);
   // backward over segments: recompute the segment's states, then reverse them
   for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -244,20 +272,15 @@ extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, 
     }
     for (int j = len - 1; j >= 0; --j) {
       const void* fbuf = j == 0 ? ckpt(seg) : ring(j);
-      e = c->prec == LBM_F64
-              ? olbm::Adjoint<0>::step(c->model, fbuf, lam[li], lam[li ^ 1], c->g, c->theta, c->tau, c->rho_ref, c->stream)
-              : olbm::Adjoint<1>::step(c->model, fbuf, lam[li], lam[li ^ 1], c->g, c->theta, c->tau, c->rho_ref, c->stream);
+      e = adj_step(c, fbuf, lam[li], lam[li ^ 1]);
       if (e == cudaSuccess && c->n_walls > 0)
-        e = olbm::launch_walls_adjoint(c->prec == LBM_F64 ? 8 : 4, lam[li], lam[li ^ 1], c->g, c->d_walls,
-                                       c->n_walls, c->stream);
+        e = olbm::launch_walls_adjoint(elem_bytes(c), lam[li], lam[li ^ 1], c->g, c->d_walls, c->n_walls, c->stream);
       if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp adjoint step", e);
       li ^= 1;
     }
   }
   // through the equilibrium initialisation
-  e = c->prec == LBM_F64
-          ? olbm::Adjoint<0>::final_(lam[li], c->g, c->theta, d_rho0, d_ux0, d_uy0, g_rho0, g_ux0, g_uy0, c->stream)
-          : olbm::Adjoint<1>::final_(lam[li], c->g, c->theta, d_rho0, d_ux0, d_uy0, g_rho0, g_ux0, g_uy0, c->stream);
+  e = adj_final(c, lam[li], d_rho0, d_ux0, d_uy0, g_rho0, g_ux0, g_uy0);
   if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp final", e);
   return LBM_OK;
 }

@@ -156,6 +156,7 @@ template <> struct Form<3> {
 __device__ __forceinline__ df64 ld_t(const double* p, df64) { return split_f64(__ldg(p)); }
 __device__ __forceinline__ void st_t(double* p, df64 v) { *p = join_f64(v); }
 __device__ __forceinline__ df64 ld_cg(const double* p, df64) { return split_f64(__ldcg(p)); }
+__device__ __forceinline__ double to_double(df64 v) { return join_f64(v); }
 
 
 }  // namespace olbm

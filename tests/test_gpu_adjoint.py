@@ -49,13 +49,15 @@ def dot(grads, v):
     return sum(float((gk * vk).sum()) for gk, vk in zip(grads, v))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f64df"])
 @pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("theta", [1.0 / 3.0, 0.4])
-def test_vjp_matches_oracle_complex_step(oracle, model, theta):
+def test_vjp_matches_oracle_complex_step(oracle, model, theta, prec):
+    """FP64 and the double-float form (FP64 storage and adjoint fields in double-float pairs)."""
     n, steps, k = 20, 30, 7  # segments of 7, 7, 7, 7, 2 steps
     tau = oracle.tau_from_nu(0.02, theta)
     fields, v, w = problem(n, 11 + model, theta)
-    grads = gpu_vjp(fields, w, theta, tau, model, steps, k)
+    grads = gpu_vjp(fields, w, theta, tau, model, steps, k, prec)
     want = oracle_dd(oracle, fields, v, w, theta, tau, model, steps)
     assert dot(grads, v) == pytest.approx(want, rel=1e-10)
 
