@@ -43,8 +43,11 @@ FALLBACK_HBM_GBS = 6800.0
 # the current kernels (profiles/step_kernel_f64_complete_2048.md and
 # profiles/step_stream_kernel_f32_complete_2048.md, 2048^2, scaled to the
 # lattice by node count since traffic grows with it). Keyed by (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.7, ("f32", "complete"): 60.0}
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.6, ("f32", "complete"): 60.0}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
+# the step kernel each storage form launches under its default launch shape
+STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_kernel",
+               "f16": "step_stream_kernel"}
 
 
 def parse_args():
@@ -242,7 +245,7 @@ def run_gpu(args):
             "frac": round(hbm_gbs / peak_hbm, 4), "traffic": traffic,
             "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
             else "profiling-recipe fallback 6.8 TB/s",
-            "kernel": f"step_kernel<{args.model},{args.prec},diag>", "ms_per_launch": round(step_ms, 4)}
+            "kernel": f"{STEP_KERNEL[args.prec]}<{args.model},diag>", "ms_per_launch": round(step_ms, 4)}
     alu = None
     if args.prec == "f64":
         peak_ops = capi.lbm_measure_peak(0) / 2.0  # FMA instructions per second (2 FLOP each)

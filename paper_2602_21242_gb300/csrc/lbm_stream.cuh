@@ -131,17 +131,22 @@ template <int PREC, int NC, int STAGES> struct StreamShape {
   static constexpr int kSmemBytes = kRingBytes + kBarBytes;
 };
 
-// Copy plan of one tile: columns [x0, x0 + w) of a lattice of any width. The
-// main copy takes wr = w rounded up to whole 16-byte chunks into segment
-// elements [CH, CH + wr); the left chunk fills [0, CH) and the right chunk
-// [CH + wr, CH + wr + CH).
+// Copy plan of one tile: columns [x0, x0 + w) of a lattice of any width. A
+// row's plane segment holds the main copy (wr = w rounded up to whole 16-byte
+// chunks) at elements [CH, CH + wr), the left chunk at [0, CH) and the right
+// chunk at [CH + wr, CH + wr + CH): sub = wr + 2 CH elements. A slot's plane
+// segment (SEG elements) holds R = SEG / sub consecutive rows side by side, so
+// narrow strips (the last strip of a lattice, small domains of a batch) still
+// fill the ring's slots.
 template <int CH> struct TilePlan {
-  int w, wr;
+  int w, wr, sub, R;
   int src_l, src_r;  // first source column of the left / right chunk
-  int lidx;          // segment element holding column x0 - 1 (periodic)
-  __device__ __forceinline__ TilePlan(const Geometry& g, int x0, int W) {
+  int lidx;          // element of a row's segment holding column x0 - 1 (periodic)
+  __device__ __forceinline__ TilePlan(const Geometry& g, int x0, int W, int SEG) {
     w = min(W, g.nx - x0);
     wr = (w + CH - 1) / CH * CH;
+    sub = wr + 2 * CH;
+    R = max(1, SEG / sub);
     if (x0 == 0) {
       src_l = (g.nx - 1) / CH * CH;  // the aligned chunk holding column nx - 1
       lidx = g.nx - 1 - src_l;
@@ -181,35 +186,41 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
     }
   }
 
-  // Producer warp: stream rows [y0, y0 + rows) of the tile at column x0.
-  // Returns false (in the whole warp) once a bounded wait gave up.
+  // Producer warp: stream rows [y0, y0 + rows) of the tile at column x0, R rows
+  // a slot. Returns false (in the whole warp) once a bounded wait gave up.
   __device__ __forceinline__ bool produce(const S* __restrict__ src, const Geometry& g, int x0, int y0, int rows,
                                           int lane, int* err) {
-    const TilePlan<CH> p(g, x0, W);
+    const TilePlan<CH> p(g, x0, W, SEG);
     const unsigned main_bytes = (unsigned)(p.wr * (int)sizeof(S));
-    const unsigned stage_bytes = 9u * main_bytes + 6u * 16u;
-    for (int r = 0; r < rows; ++r, ++k) {
+    const unsigned row_bytes = 9u * main_bytes + 6u * 16u;
+    for (int r0 = 0; r0 < rows; r0 += p.R, ++k) {
+      const int nr = min(p.R, rows - r0);
       const int s = k % STAGES;
       bool ok = true;
       if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
       if (!__all_sync(0xffffffffu, ok)) return false;  // the whole warp leaves together
-      const int y = y0 + r;
       S* slot = ring + (size_t)s * 9 * SEG;
-      if (lane == 0) mbar_expect_tx_arrive(&full[s], stage_bytes);
+      if (lane == 0) mbar_expect_tx_arrive(&full[s], (unsigned)nr * row_bytes);
       __syncwarp();
-      // lanes 0..8: main segment of plane `lane`; lanes 9..14: edge chunks of the planes
-      // with c_ix != 0 (planes 1, 5, 8 the left chunk, 3, 6, 7 the right one). Operands
-      // are selected without branches, so the warp issues one copy instruction.
-      if (lane < 15) {
-        const int e = lane - 9;
-        const bool main = lane < 9, left = e < 3;
-        const int i = main ? lane : (int)((0x763851u >> (4 * e)) & 15u);
-        int ys = y - cy_of(i);
+      // 15 copies per row: the main segments of the nine planes, then the edge chunks of
+      // the planes with c_ix != 0 (planes 1, 5, 8 the left chunk, 3, 6, 7 the right one).
+      // Operands are selected without branches; a slot of one row (full strips) takes
+      // one copy per lane without a loop, so the ring fills as fast as it can.
+      auto copy = [&](int j, int c) {
+        const int e = c - 9;
+        const bool main = c < 9, left = e < 3;
+        const int i = main ? c : (int)((0x763851u >> (4 * e)) & 15u);
+        int ys = y0 + r0 + j - cy_of(i);
         ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-        const int dst_off = main ? CH : (left ? 0 : CH + p.wr);
+        const int dst_off = j * p.sub + (main ? CH : (left ? 0 : CH + p.wr));
         const int src_col = main ? x0 : (left ? p.src_l : p.src_r);
         const unsigned bytes = main ? main_bytes : 16u;
         bulk_g2s(slot + i * SEG + dst_off, src + i * g.plane + (long long)ys * g.pitch + src_col, bytes, &full[s]);
+      };
+      if (nr == 1) {
+        if (lane < 15) copy(0, lane);
+      } else {
+        for (int q = lane; q < 15 * nr; q += 32) copy(q / 15, q % 15);
       }
     }
     return true;
@@ -221,20 +232,24 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
       if (!__all_sync(0xffffffffu, mbar_wait(&full[j % STAGES], (unsigned)((j / STAGES) & 1), err))) break;
   }
 
-  // Consumer thread t (pair of local nodes 2t, 2t + 1): collide the tile's rows.
+  // Consumer thread t: the pair of local nodes xl, xl + 1 of row j of each slot
+  // (t = j * ceil(w / 2) + xl / 2); collide the tile's rows.
   template <int MODEL, bool DIAG>
   __device__ __forceinline__ bool consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
                                           int y0, int rows, int t, int lane, DiagAcc<f32x2>& acc, int* err) {
-    const TilePlan<CH> p(g, x0, W);
-    const int xl = 2 * t;
-    const bool active = xl < p.w;
+    const TilePlan<CH> p(g, x0, W, SEG);
+    const int ppr = (p.w + 1) / 2;  // pairs per row
+    const int j = t / ppr;
+    const int xl = 2 * (t - j * ppr);
     const bool whole = xl + 1 < p.w;  // both nodes of the pair lie in the strip
     // segment elements of the pair's nodes and of their x -+ 1 neighbours
-    const int iM = CH + xl;
-    const int iL = xl == 0 ? p.lidx : iM - 1;
-    const int iR0 = whole ? iM + 1 : CH + p.wr;
-    const int iR1 = xl + 2 < p.w ? iM + 2 : CH + p.wr;
-    for (int r = 0; r < rows; ++r, ++k) {
+    const int base = j * p.sub;
+    const int iM = base + CH + xl;
+    const int iL = xl == 0 ? base + p.lidx : iM - 1;
+    const int iR0 = whole ? iM + 1 : base + CH + p.wr;
+    const int iR1 = xl + 2 < p.w ? iM + 2 : base + CH + p.wr;
+    for (int r0 = 0; r0 < rows; r0 += p.R, ++k) {
+      const bool active = j < min(p.R, rows - r0);
       const int s = k % STAGES;
       if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err))) return false;
       const S* slot = ring + (size_t)s * 9 * SEG;
@@ -255,7 +270,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
       if (active) {
         NodeMoments<f32x2> m;
         collide<MODEL, true, f32x2>(f, c, m);
-        S* q = dst + (long long)(y0 + r) * g.pitch + x0 + xl;
+        S* q = dst + (long long)(y0 + r0 + j) * g.pitch + x0 + xl;
         if (whole) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) st_pair(q + i * g.plane, f[i]);

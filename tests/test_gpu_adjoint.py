@@ -100,13 +100,16 @@ def test_vjp_matches_gpu_central_difference(model):
     assert dot(grads, v) == pytest.approx(fd, rel=1e-6)
 
 
-def test_vjp_f32_against_f64(oracle):
-    """The FP32 form's adjoint (FP32 arithmetic) against the FP64 adjoint on the same problem."""
-    n, theta, steps = 32, 1.0 / 3.0, 40
+@pytest.mark.parametrize("n", [32, 31])
+@pytest.mark.parametrize("model", [0, 3])
+def test_vjp_f32_against_f64(oracle, n, model):
+    """The FP32 form's adjoint (FP32 arithmetic) against the FP64 adjoint on the same problem, even and
+    odd widths."""
+    theta, steps = 1.0 / 3.0, 40
     tau = 0.56
     fields, v, w = problem(n, 29, theta)
-    g64 = gpu_vjp(fields, w, theta, tau, 3, steps, 10, "f64")
-    g32 = gpu_vjp(fields, w, theta, tau, 3, steps, 10, "f32")
+    g64 = gpu_vjp(fields, w, theta, tau, model, steps, 10, "f64")
+    g32 = gpu_vjp(fields, w, theta, tau, model, steps, 10, "f32")
     for a, b in zip(g32, g64):
         assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b)
 
