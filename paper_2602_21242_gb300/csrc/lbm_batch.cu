@@ -81,7 +81,6 @@ struct lbm_batch {
   size_t arena_bytes = 0;
   void* d_desc = nullptr;
   int4* d_tiles = nullptr;
-  int* d_sched = nullptr;  // tile order for the persistent pipelined kernel
   int2* d_ranges = nullptr;
   long long* d_nodes = nullptr;
   int ntiles = 0;
@@ -161,40 +160,18 @@ int build_tiles(lbm_batch* b) {
   if (tiles.size() > (size_t)0x7fffffff) return bfail(b, LBM_EINVAL, "too many tiles");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch tiles sync");
-  // Persistent order (launch kind 1): tiles sorted by their ring traffic, costliest
-  // first, so that the round-robin over the grid gives every CTA a similar share
-  // (a strip of w columns moves its rows R = (W + 2 CH) / (wr + 2 CH) at a time).
-  std::vector<int> sched(tiles.size());
-  for (size_t t = 0; t < tiles.size(); ++t) sched[t] = (int)t;
-  if (b->cfg.kind == 1) {
-    const int W = 2 * olbm::batch_stream_nc(b->prec, b->cfg.bx);
-    const int CH = b->prec == LBM_F32_SHIFT ? 4 : 8;
-    std::vector<long long> cost(tiles.size());
-    for (size_t t = 0; t < tiles.size(); ++t) {
-      const olbm::Geometry& g = b->geo[tiles[t].x];
-      const int w = std::min(W, g.nx - tiles[t].y), h = std::min(b->cfg.rows, g.ny - tiles[t].z);
-      const int wr = (w + CH - 1) / CH * CH;
-      const int R = std::max(1, (W + 2 * CH) / (wr + 2 * CH));
-      cost[t] = (long long)((h + R - 1) / R) * std::min(W, R * wr);
-    }
-    std::stable_sort(sched.begin(), sched.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-  }
   cudaFree(b->d_tiles);
-  cudaFree(b->d_sched);
   cudaFree(b->d_ranges);
   cudaFree(b->d_partials);
   b->d_tiles = nullptr;
-  b->d_sched = nullptr;
   b->d_ranges = nullptr;
   b->d_partials = nullptr;
   b->ntiles = (int)tiles.size();
   if ((e = cudaMalloc(&b->d_tiles, sizeof(int4) * tiles.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_sched, sizeof(int) * sched.size())) != cudaSuccess ||
       (e = cudaMalloc(&b->d_ranges, sizeof(int2) * ranges.size())) != cudaSuccess ||
       (e = cudaMalloc(&b->d_partials, sizeof(double) * 5 * tiles.size())) != cudaSuccess)
     return bcuda(b, e, "lbm_batch tile allocation");
   if ((e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_sched, sched.data(), sizeof(int) * sched.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(b->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
     return bcuda(b, e, "lbm_batch tile upload");
@@ -212,7 +189,6 @@ void free_batch(lbm_batch* b) {
   cudaFree(b->arena);
   cudaFree(b->d_desc);
   cudaFree(b->d_tiles);
-  cudaFree(b->d_sched);
   cudaFree(b->d_ranges);
   cudaFree(b->d_nodes);
   cudaFree(b->d_partials);
@@ -238,7 +214,6 @@ olbm::BatchLaunch view(const lbm_batch* b) {
   v.cfg = b->cfg;
   v.desc = b->d_desc;
   v.tiles = b->d_tiles;
-  v.sched = b->d_sched;
   v.ntiles = b->ntiles;
   v.partials = b->d_partials;
   v.perr = b->d_perr;

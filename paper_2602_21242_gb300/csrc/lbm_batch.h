@@ -55,7 +55,6 @@ struct BatchLaunch {
   LaunchCfg cfg{};           // kind 0: bx x by threads, rows; kind 1: bx = NC selector, rows = tile rows
   const void* desc = nullptr;  // Desc<double> (FP64) or Desc<float> (shifted forms), one per domain
   const int4* tiles = nullptr;  // (domain, x0, y0, 0)
-  const int* sched = nullptr;   // tile order of the persistent pipelined kernel (costliest first)
   int ntiles = 0;
   double* partials = nullptr;  // 5 doubles per tile
   int* perr = nullptr;         // bounded-wait flag of the pipelined tile kernel

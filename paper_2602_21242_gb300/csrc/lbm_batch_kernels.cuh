@@ -148,8 +148,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 // up sets the barrier's error flag, so every CTA leaves at the next barrier.
 template <int MODEL, int PREC, int NC, int STAGES>
 __global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const Desc<float>* __restrict__ desc,
-                                                                         const int4* __restrict__ tiles,
-                                                                         const int* __restrict__ sched, int ntiles,
+                                                                         const int4* __restrict__ tiles, int ntiles,
                                                                          int parity0, int nsteps, int H,
                                                                          GridBarrier* bar) {
   using P = Pipeline<PREC, NC, STAGES>;
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const 
     if (producer) {
       fence_proxy_async_global();
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[sched[t]];
+        const int4 tl = tiles[t];
         const Desc<float>* d = desc + tl.x;
         if (!pipe.produce(static_cast<const S*>(d->buf[parity]), d->g, tl.y, tl.z, min(H, d->g.ny - tl.z), lane,
                           err))
@@ -175,7 +174,7 @@ __global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const 
       }
     } else if (threadIdx.x < NC) {
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tl = tiles[sched[t]];
+        const int4 tl = tiles[t];
         const Desc<float>* d = desc + tl.x;
         if (!pipe.template consume<MODEL, false>(static_cast<S*>(d->buf[parity ^ 1]), d->g, broadcast(d->c), tl.y,
                                                  tl.z, min(H, d->g.ny - tl.z), threadIdx.x, lane, acc, err))
@@ -235,11 +234,10 @@ template <int PREC> struct BatchOps {
     const int grid = std::min(b.ntiles, per_sm * b.sms);
     const auto* desc = static_cast<const Desc<float>*>(b.desc);
     const int4* tiles = b.tiles;
-    const int* sched = b.sched;
     int ntiles = b.ntiles, rows = b.cfg.rows;
     GridBarrier* bar = b.bar;
-    void* args[] = {(void*)&desc, (void*)&tiles, (void*)&sched, (void*)&ntiles, (void*)&parity0, (void*)&n,
-                    (void*)&rows, (void*)&bar};
+    void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows,
+                    (void*)&bar};
     e = cudaMemsetAsync(b.bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(NC + 32), args, (size_t)bytes, st);
