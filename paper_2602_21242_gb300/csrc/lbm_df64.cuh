@@ -68,14 +68,15 @@ template <class F> struct dfloat {
   friend __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
   friend __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
   friend __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
-  // TwoProd of the high parts, the cross terms folded into its error, Fast2Sum.
+  // TwoProd of the high parts, the cross terms folded into its error. The pair
+  // (p, e) is returned without renormalising: |e| stays within about an ulp of p
+  // (the product of the high parts dominates), which every operation here accepts.
   friend __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
     const F p = ef_mul(a.hi, b.hi);
     F e = ef_fms(a.hi, b.hi, p);
     e = ef_fma(a.hi, b.lo, e);
     e = ef_fma(a.lo, b.hi, e);
-    const F h = ef_add(p, e);
-    return dfloat(h, ef_sub(e, ef_sub(h, p)));
+    return dfloat(p, e);
   }
   // a b + c: the product as above, then TwoSum with c.
   friend __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
