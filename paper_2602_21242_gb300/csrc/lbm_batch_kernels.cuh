@@ -13,6 +13,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 
 #include "lbm_batch.h"
 
@@ -194,11 +195,17 @@ template <int PREC> struct BatchOps {
   static constexpr int kNcA = PREC == 1 ? 32 : 64, kNcB = PREC == 1 ? 64 : 128, kNcC = PREC == 1 ? 128 : 256;
   static constexpr int kStages = kStreamStages;
 
+  // The shared-memory opt-in is a per-device attribute: set once per kernel and device.
   template <auto K> static cudaError_t allow_ring(int bytes) {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done = true;
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const unsigned long long bit = 1ull << dev;
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
     return e;
   }
 

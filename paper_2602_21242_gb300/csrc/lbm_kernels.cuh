@@ -533,26 +533,31 @@ template <int PREC> struct Launch {
     using Shape = StreamShape<PREC, NC, kStreamStages>;
     auto kernel = step_stream_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
     auto pkernel = step_stream_persistent_kernel<MODEL, PREC, DIAG, NC, kStreamStages>;
-    // Per instantiation, once: opt in to the large shared-memory carve-out and
-    // size the persistent grid (resident CTAs per SM x SMs).
-    static int resident = 0, sms_seen = 1;
-    if (resident == 0) {
-      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
+    // Per instantiation and device, once: opt in to the large shared-memory
+    // carve-out (a per-device attribute) and size the persistent grid (resident
+    // CTAs per SM x SMs). Concurrent first calls store the same values.
+    constexpr int kMaxDev = 64;
+    static int resident[kMaxDev] = {0}, sms_of[kMaxDev] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (resident[dev] == 0) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pkernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
-      int dev = 0, sms = 0, per_sm = 0;
-      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      int sms = 0, per_sm = 0;
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pkernel, NC + 32, Shape::kSmemBytes);
       if (e != cudaSuccess) return e;
       if (per_sm < 1) return cudaErrorInvalidConfiguration;
-      resident = per_sm * sms;
-      sms_seen = sms;
+      sms_of[dev] = sms;
+      resident[dev] = per_sm * sms;
     }
     // bx > 0: a persistent grid of bx CTAs per SM (at most the resident count);
     // bx == 0: one CTA per tile.
     LaunchCfg k = a.cfg;
-    k.cap = a.cfg.bx > 0 ? std::min(resident, a.cfg.bx * sms_seen) : 0;
+    k.cap = a.cfg.bx > 0 ? std::min(resident[dev], a.cfg.bx * sms_of[dev]) : 0;
     const dim3 grid = step_grid(a.g, k, PREC);
     if (a.parts_used) *a.parts_used = (long long)grid.x * grid.y;
     const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
