@@ -332,9 +332,9 @@ int lbm_measure_peak(int kind, double* h_flops);
 /*
  * One fused FP64 step with diagnostics that allocates no device memory (no
  * counterpart in the paper). For callers that cannot call cudaMalloc: code
- * whose device memory must all come from its own pool or arena, loops where an
- * allocation's implicit synchronisation would stall the GPU, or work recorded
- * into a CUDA graph. It needs no lattice object: the caller passes every input
+ * whose device memory must all come from its own pool or arena, or loops where
+ * an allocation's implicit synchronisation would stall the GPU. It needs no
+ * lattice object: the caller passes every input
  * and output, and the only scratch, the per-block diagnostics sums, lives in a
  * fixed static device array of 320 KiB (8192 blocks x 5 doubles) that every
  * GPU which loads the library holds until the process exits.

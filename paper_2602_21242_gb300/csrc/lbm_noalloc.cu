@@ -3,10 +3,9 @@
 //
 // Who needs it: code that must not call cudaMalloc/cudaFree -- a caller whose
 // device memory all comes from its own pool or arena (so the library may not
-// take more behind its back), a caller in a latency-critical loop where an
-// allocation's implicit synchronisation would stall the GPU, or a caller that
-// records its work into a CUDA graph and cannot allocate while doing so. The
-// regular entry points allocate per-lattice buffers in lbm_create; this one
+// take more behind its back), or a caller in a latency-critical loop where an
+// allocation's implicit synchronisation would stall the GPU. The regular entry
+// points allocate per-lattice buffers in lbm_create; this one
 // takes every input and output from the caller and keeps its only scratch (the
 // per-block diagnostics partial sums) in a fixed array in the library's device
 // image.
@@ -15,8 +14,8 @@
 // library holds it until the process exits, and all calls on a device share
 // it. Each call overwrites the partials it reads (every block writes its own
 // five sums before the final reduction reads them), so nothing needs clearing
-// between calls, but two calls that run at the same time on one device (on
-// different streams, or overlapping graph nodes) race on it.
+// between calls, but two calls whose work overlaps on one device (for example
+// on different streams) race on it.
 #include <mutex>
 
 #include "lbm.h"

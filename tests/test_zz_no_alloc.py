@@ -1,8 +1,8 @@
 """lbm_step_noalloc, the entry point for callers that cannot allocate device memory.
 
 Some callers may not call cudaMalloc: their device memory all comes from their
-own pool, or an allocation's implicit synchronisation would stall their loop,
-or they record work into a CUDA graph. lbm_step_noalloc takes every buffer
+own pool, or an allocation's implicit synchronisation would stall their loop.
+lbm_step_noalloc takes every buffer
 from the caller and keeps its only scratch in a fixed device array. These tests
 check it against the regular path (a lattice from lbm_create_ex advanced by
 lbm_step with fused diagnostics) on the same state, for two calls in a row, and
