@@ -89,7 +89,8 @@ struct lbm_batch {
   double* d_diag_now = nullptr;
   unsigned long long* d_sticky = nullptr;
   olbm::GridBarrier* d_bar = nullptr;
-  int* d_perr = nullptr;  // set by a bounded wait of the pipelined tile kernel that gave up
+  int* d_perr = nullptr;
+  int* d_ctr = nullptr;  // tile counters of the persistent pipelined kernel  // set by a bounded wait of the pipelined tile kernel that gave up
   olbm::LaunchCfg cfg{};
   int cur = 0;
   long long t = 0;
@@ -197,6 +198,7 @@ void free_batch(lbm_batch* b) {
   cudaFree(b->d_sticky);
   cudaFree(b->d_bar);
   cudaFree(b->d_perr);
+  cudaFree(b->d_ctr);
   delete b;
 }
 
@@ -218,6 +220,7 @@ olbm::BatchLaunch view(const lbm_batch* b) {
   v.partials = b->d_partials;
   v.perr = b->d_perr;
   v.bar = b->d_bar;
+  v.ctr = b->d_ctr;
   v.sms = b->sms;
   return v;
 }
@@ -314,7 +317,8 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
       (e = cudaMalloc(&b->d_diag_now, sizeof(double) * 5 * n)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_sticky, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_bar, sizeof(olbm::GridBarrier))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_perr, sizeof(int))) != cudaSuccess) {
+      (e = cudaMalloc(&b->d_perr, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_ctr, 2 * sizeof(int))) != cudaSuccess) {
     free_batch(b);
     cudaGetLastError();
     return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: %s", cudaGetErrorString(e));

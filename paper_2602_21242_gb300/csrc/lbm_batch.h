@@ -59,6 +59,7 @@ struct BatchLaunch {
   double* partials = nullptr;  // 5 doubles per tile
   int* perr = nullptr;         // bounded-wait flag of the pipelined tile kernel
   GridBarrier* bar = nullptr;  // persistent mode
+  int* ctr = nullptr;          // persistent pipelined mode: two tile counters
   int sms = 1;
 };
 

@@ -142,19 +142,27 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// n steps of every domain in one cooperative launch of pipelined CTAs: tiles
-// strided over the grid, a bounded grid barrier between steps. The consumers'
-// stores (generic proxy) reach the next step's bulk copies (async proxy)
-// through a proxy fence on both sides of the barrier. A bounded wait that gives
-// up sets the barrier's error flag, so every CTA leaves at the next barrier.
+// n steps of every domain in one cooperative launch of pipelined CTAs, a
+// bounded grid barrier between steps. Tiles are handed out in list (domain)
+// order by an atomic counter per step, ctr[s & 1]: a CTA's producer takes the
+// next tile when it has issued the previous one, so CTAs that finish early take
+// more, and tiles that run together stay neighbours (their halo rows meet in
+// L2). The producer tags every ring slot with its tile and closes the step with
+// a slot tagged -1; the consumers follow the tags. The counter of the step
+// after next is reset at the start of a step (it was last used two barriers
+// ago). The consumers' stores (generic proxy) reach the next step's bulk copies
+// (async proxy) through a proxy fence on both sides of the barrier. A bounded
+// wait that gives up sets the barrier's error flag, so every CTA leaves at the
+// next barrier.
 template <int MODEL, int PREC, int NC, int STAGES>
 __global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const Desc<float>* __restrict__ desc,
                                                                          const int4* __restrict__ tiles, int ntiles,
                                                                          int parity0, int nsteps, int H,
-                                                                         GridBarrier* bar) {
+                                                                         GridBarrier* bar, int* ctr) {
   using P = Pipeline<PREC, NC, STAGES>;
   using S = typename Form<PREC>::S;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int tags[STAGES];
   P pipe(smem);
   pipe.init();
   __syncthreads();
@@ -165,16 +173,44 @@ __global__ void __launch_bounds__(NC + 32) batch_stream_persistent_kernel(const 
   for (int s = 0; s < nsteps; ++s) {
     const int parity = (parity0 + s) & 1;
     if (producer) {
+      if (blockIdx.x == 0 && lane == 0) atomicExch(&ctr[(s + 1) & 1], 0);
       fence_proxy_async_global();
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      bool ok = true;
+      for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&ctr[s & 1], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) {  // close the step: a slot without data, tagged -1
+          const int q = pipe.k % STAGES;
+          if (pipe.k >= STAGES) ok = mbar_wait(&pipe.empty[q], (unsigned)((pipe.k / STAGES - 1) & 1), err);
+          ok = __all_sync(0xffffffffu, ok);
+          if (ok && lane == 0) {
+            tags[q] = -1;
+            mbar_arrive(&pipe.full[q]);
+          }
+          ++pipe.k;
+          break;
+        }
         const int4 tl = tiles[t];
         const Desc<float>* d = desc + tl.x;
         if (!pipe.produce(static_cast<const S*>(d->buf[parity]), d->g, tl.y, tl.z, min(H, d->g.ny - tl.z), lane,
-                          err))
+                          err, tags, t)) {
+          ok = false;
           break;
+        }
       }
+      (void)ok;
     } else if (threadIdx.x < NC) {
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (;;) {
+        const int q = pipe.k % STAGES;
+        if (!__all_sync(0xffffffffu, mbar_wait(&pipe.full[q], (unsigned)((pipe.k / STAGES) & 1), err))) break;
+        const int t = *(volatile int*)&tags[q];
+        if (t < 0) {  // end of the step
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&pipe.empty[q]);
+          ++pipe.k;
+          break;
+        }
         const int4 tl = tiles[t];
         const Desc<float>* d = desc + tl.x;
         if (!pipe.template consume<MODEL, false>(static_cast<S*>(d->buf[parity ^ 1]), d->g, broadcast(d->c), tl.y,
@@ -243,9 +279,11 @@ template <int PREC> struct BatchOps {
     const int4* tiles = b.tiles;
     int ntiles = b.ntiles, rows = b.cfg.rows;
     GridBarrier* bar = b.bar;
+    int* ctr = b.ctr;
     void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows,
-                    (void*)&bar};
+                    (void*)&bar, (void*)&ctr};
     e = cudaMemsetAsync(b.bar, 0, sizeof(GridBarrier), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.ctr, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(NC + 32), args, (size_t)bytes, st);
   }

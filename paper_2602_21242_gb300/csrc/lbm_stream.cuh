@@ -187,9 +187,11 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
   }
 
   // Producer warp: stream rows [y0, y0 + rows) of the tile at column x0, R rows
-  // a slot. Returns false (in the whole warp) once a bounded wait gave up.
+  // a slot. With tags, each slot's entry tags[s] is set to `tag` before the slot
+  // is armed (the consumers read it once the slot is full). Returns false (in the
+  // whole warp) once a bounded wait gave up.
   __device__ __forceinline__ bool produce(const S* __restrict__ src, const Geometry& g, int x0, int y0, int rows,
-                                          int lane, int* err) {
+                                          int lane, int* err, volatile int* tags = nullptr, int tag = 0) {
     const TilePlan<CH> p(g, x0, W, SEG);
     const unsigned main_bytes = (unsigned)(p.wr * (int)sizeof(S));
     const unsigned row_bytes = 9u * main_bytes + 6u * 16u;
@@ -200,7 +202,10 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
       if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
       if (!__all_sync(0xffffffffu, ok)) return false;  // the whole warp leaves together
       S* slot = ring + (size_t)s * 9 * SEG;
-      if (lane == 0) mbar_expect_tx_arrive(&full[s], (unsigned)nr * row_bytes);
+      if (lane == 0) {
+        if (tags != nullptr) tags[s] = tag;
+        mbar_expect_tx_arrive(&full[s], (unsigned)nr * row_bytes);
+      }
       __syncwarp();
       // 15 copies per row: the main segments of the nine planes, then the edge chunks of
       // the planes with c_ix != 0 (planes 1, 5, 8 the left chunk, 3, 6, 7 the right one).
