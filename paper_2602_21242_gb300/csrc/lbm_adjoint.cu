@@ -202,6 +202,8 @@ cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
   a.rho_ref = c->rho_ref;
   a.partials = c->d_partials;
   a.cfg = c->cfg;
+  a.err = c->d_err;
+  a.sched = c->d_sched;
   cudaError_t e = c->prec == LBM_F64      ? olbm::launch_step_f64(a, c->stream)
                   : c->prec == LBM_F64_DF ? olbm::launch_step_f64df(a, c->stream)
                                           : olbm::launch_step_f32(a, c->stream);

@@ -112,6 +112,7 @@ void free_ctx(lbm_ctx* c) {
   cudaFree(c->d_diag_now);
   cudaFree(c->d_sticky);
   cudaFree(c->d_err);
+  cudaFree(c->d_sched);
   cudaFree(c->d_stage);
   cudaFree(c->d_vjp);
   cudaFree(c->d_walls);
@@ -191,7 +192,8 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
       (e = cudaMalloc(&c->d_diag, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag_now, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) {
+      (e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_sched, 2 * sizeof(int))) != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
     return fail(nullptr, LBM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
@@ -201,7 +203,8 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
       (e = cudaMemsetAsync(c->buf[1], 0, (size_t)bytes, c->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->d_diag, 0, sizeof(double) * 6, c->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->d_sticky, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess) {
+      (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_sched, 0, 2 * sizeof(int), c->stream)) != cudaSuccess) {
     free_ctx(c);
     return fail(nullptr, LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
@@ -312,6 +315,7 @@ int lbm_step(lbm_ctx* ctx, int n) {
   a.partials = ctx->d_partials;
   a.cfg = ctx->cfg;
   a.err = ctx->d_err;
+  a.sched = ctx->d_sched;
   long long used = ctx->nparts;
   a.parts_used = &used;
   for (int k = 0; k < n; ++k) {

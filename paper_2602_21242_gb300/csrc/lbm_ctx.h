@@ -25,6 +25,7 @@ struct lbm_ctx {
   double* d_diag_now = nullptr;  // [6] scratch of lbm_diagnostics
   unsigned long long* d_sticky = nullptr;
   int* d_err = nullptr;  // set by a bounded device-side wait that gave up
+  int* d_sched = nullptr;  // [next tile, CTAs done] of the persistent pipeline kernel; zero between launches
   int diag_every = 0;
   long long t = 0;
   long long last_diag_t = -1;

@@ -564,9 +564,11 @@ template <int PREC> struct Launch {
     if (a.cfg.bx == 0)
       kernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
                                                        a.err);
+    else if (a.err == nullptr || a.sched == nullptr)
+      return cudaErrorInvalidValue;
     else
       pkernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
-                                                        a.err);
+                                                        a.err, a.sched);
     return cudaGetLastError();
   }
 

@@ -36,6 +36,7 @@ struct StepArgs {
   double* partials;  // grid blocks * 5 doubles when diag
   LaunchCfg cfg;
   int* err = nullptr;  // device flag set by a bounded wait that gave up (pipeline kernel)
+  int* sched = nullptr;  // two ints, zero between launches: tile counter of the persistent pipeline kernel
   long long* parts_used = nullptr;  // out: diagnostics partials the launch wrote (its grid size)
 };
 

@@ -295,16 +295,21 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
 };
 
 // Persistent form over one lattice. Tiles: strips of W columns x blocks of H
-// rows, numbered strip-fastest. CTA b takes tiles b, b + gridDim.x, ...; the
-// ring's item counter runs on across tiles, so a CTA fills the pipeline once.
+// rows, numbered strip-fastest. A CTA's producer takes the next tile from the
+// counter sched[0] when it has issued the last one, tags the ring slots with it
+// and closes with a slot tagged -1; the consumers follow the tags. The ring's
+// item counter runs on across tiles, so a CTA fills the pipeline once. The
+// last CTA to finish (counted in sched[1]) zeroes both counters for the next
+// launch.
 template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
 __global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const typename Form<PREC>::S* __restrict__ src,
                                                                          typename Form<PREC>::S* __restrict__ dst,
                                                                          Geometry g, Coef<f32x2> c,
                                                                          double* __restrict__ partials, int H,
-                                                                         int* __restrict__ err) {
+                                                                         int* __restrict__ err, int* sched) {
   using P = Pipeline<PREC, NC, STAGES>;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int tags[STAGES];
   P pipe(smem);
   pipe.init();
   __syncthreads();
@@ -313,19 +318,50 @@ __global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const t
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DiagAcc<f32x2> acc;
   if (warp == P::kConsumerWarps) {
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (;;) {
+      int tile = 0;
+      if (lane == 0) tile = atomicAdd(&sched[0], 1);
+      tile = __shfl_sync(0xffffffffu, tile, 0);
+      if (tile >= ntiles) {  // close: a slot without data, tagged -1
+        const int q = pipe.k % STAGES;
+        bool ok = true;
+        if (pipe.k >= STAGES) ok = mbar_wait(&pipe.empty[q], (unsigned)((pipe.k / STAGES - 1) & 1), err);
+        if (__all_sync(0xffffffffu, ok) && lane == 0) {
+          tags[q] = -1;
+          mbar_arrive(&pipe.full[q]);
+        }
+        ++pipe.k;
+        break;
+      }
       const int x0 = (tile % nstrips) * P::W, y0 = (tile / nstrips) * H;
-      if (!pipe.produce(src, g, x0, y0, min(H, g.ny - y0), lane, err)) break;
+      if (!pipe.produce(src, g, x0, y0, min(H, g.ny - y0), lane, err, tags, tile)) break;
     }
     pipe.drain(err);
   } else if (threadIdx.x < NC) {
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (;;) {
+      const int q = pipe.k % STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(&pipe.full[q], (unsigned)((pipe.k / STAGES) & 1), err))) break;
+      const int tile = *(volatile int*)&tags[q];
+      if (tile < 0) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pipe.empty[q]);
+        ++pipe.k;
+        break;
+      }
       const int x0 = (tile % nstrips) * P::W, y0 = (tile / nstrips) * H;
       if (!pipe.template consume<MODEL, DIAG>(dst, g, c, x0, y0, min(H, g.ny - y0), threadIdx.x, lane, acc, err))
         break;
     }
   }
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)blockIdx.x * 5);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1) == (int)gridDim.x - 1) {
+      atomicExch(&sched[0], 0);
+      atomicExch(&sched[1], 0);
+    }
+  }
 }
 
 // One CTA per tile: strip blockIdx.x of W columns, rows [blockIdx.y H, + H).

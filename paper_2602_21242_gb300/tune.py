@@ -25,7 +25,7 @@ _lock = threading.Lock()
 # with bx = CTAs per SM (0 = one CTA per tile)
 LATTICE_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)], [4, 8, 16, 32])]
-PIPELINE_CANDIDATES = [(1, ctas, 1, rows) for ctas in (0, 1, 2) for rows in (4, 8, 16, 32, 64)]
+PIPELINE_CANDIDATES = [(1, ctas, 1, rows) for ctas in (0, 2, 64) for rows in (4, 8, 16, 32, 64)]
 BATCH_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)], [2, 4, 8, 16])]
 # kind 1: the pipeline with bx consumer threads (0 = default) on tiles of 2 bx columns x rows
