@@ -159,19 +159,46 @@ template <typename T> struct NodeMoments {
   T ke;  // rho |u|^2 / 2
 };
 
-// 1 / x. FP64: a single-precision seed (rcp.approx, relative error < 2^-22 after
-// rounding x to FP32) refined by one cubic Newton step r = r0 (1 + e + e^2),
-// e = 1 - x r0, which leaves a relative error O(e^3) < 2^-64 before the final
-// rounding: 3 FP64 operations instead of a full IEEE division. Valid for
-// |x| in the FP32 normal range; other x (rho <= 0 or non-finite) give a
-// non-finite or meaningless result, which the diagnostics report.
+// ---------------------------------------------------------------- FP64 helpers off the FP64 pipe
+// On GB300 the FP64 pipe runs at 1/64 of the FP32 rate and bounds the FP64
+// kernels; these helpers do exact work on the integer pipe instead.
+
+// FP32 -> FP64 by exponent rebias (exact; FP32 subnormals become zero).
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned fe = (u >> 23) & 0xFFu;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  if (fe == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long E = fe == 0xFFu ? 0x7FFull : (unsigned long long)(fe + 896u);
+  return __longlong_as_double((long long)(sign | (E << 52) | m));
+}
+
+// FP64 -> FP32 by truncating the mantissa to 23 bits: magnitudes below FP32's
+// normal range give a signed zero, above it (and infinities, NaNs) infinity.
+__device__ __forceinline__ float narrow_trunc(double d) {
+  const unsigned h = (unsigned)__double2hiint(d), l = (unsigned)__double2loint(d);
+  const unsigned sign = h & 0x80000000u;
+  const int fe = (int)((h >> 20) & 0x7FFu) - 896;  // FP32 biased exponent of the same power of two
+  const unsigned r = sign | ((unsigned)fe << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
+  return __uint_as_float(fe <= 0 ? sign : (fe >= 255 ? (sign | 0x7F800000u) : r));
+}
+
+// 1 / x. FP64: a single-precision seed (rcp.approx of x truncated to FP32,
+// relative error below 2^-21) refined by one cubic Newton step
+// r = r0 (1 + e + e^2), e = 1 - x r0, which leaves a relative error
+// O(e^3) < 2^-62 before the final rounding: 3 FP64 operations instead of a full
+// IEEE division, the conversions on the integer pipe. Valid for |x| in the
+// FP32 normal range; x = 0, non-finite or tiny x give a non-finite result
+// (rcp.approx returns infinity for a zero seed, the Newton step then forms
+// 0 * inf or inf - inf), which the diagnostics report.
 __device__ __forceinline__ float rcp_seed(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ double recip(double x) {
-  const double r0 = (double)rcp_seed((float)x);
+  const double r0 = widen_f32(rcp_seed(narrow_trunc(x)));
   const double e = fma(-x, r0, 1.0);
   return fma(r0, fma(e, e, e), r0);
 }
@@ -183,6 +210,19 @@ __device__ __forceinline__ f32x2 recip(f32x2 x) { return f32x2(make_float2(1.0f 
 // full product.
 template <typename T> __device__ __forceinline__ T scaled(T x, float k) { return T(k) * x; }
 template <typename T> __device__ __forceinline__ T fma_scaled(T x, float k, T c) { return fma(T(k), x, c); }
+// FP64: the exponent field moves by log2 |k| and the sign flips for k < 0, on
+// the integer pipe. Zeros, infinities and NaNs keep their exponent field, so
+// they come out as k x does. Normal results only: x and k x must lie in
+// FP64's normal range (the callers scale moments of O(1) populations by 1/2
+// or 1/4; a normal x below 2^-1020 would not come out as k x).
+__device__ __forceinline__ double scaled(double x, float k) {
+  const unsigned kb = __float_as_uint(k);
+  const int e = (int)((kb >> 23) & 0xFFu) - 127;
+  const unsigned h = (unsigned)__double2hiint(x);
+  const bool normal = (h & 0x7FF00000u) - 0x00100000u < 0x7FE00000u;
+  const unsigned nh = (normal ? h + ((unsigned)e << 20) : h) ^ (kb & 0x80000000u);
+  return __hiloint2double((int)nh, __double2loint(x));
+}
 
 // ---------------------------------------------------------------- collision
 // In-place collision of one node (Eq. 1a). f holds the stored values of the
@@ -312,7 +352,7 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const T base = SHIFT ? rho * dx[k] : rho * px[k];  // f^eq part carried by P_y(b)
-      E[k] = fma(A1 * px[k], cxm[k] * cxm[k], base);
+      E[k] = fma(A1 * px[k], k == 1 ? ux2 : cxm[k] * cxm[k], base);  // C_x(0)^2 = u_x^2
       B[k] = A1 * px[k];
       G[k] = A2 * (px[k] * cxm[k]);
     }

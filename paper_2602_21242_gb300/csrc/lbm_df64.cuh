@@ -133,17 +133,6 @@ __device__ __forceinline__ df64 split_f64(double d) {
   return df64(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) | sign));
 }
 
-// FP32 -> FP64 by exponent rebias (exact; FP32 subnormals become zero).
-__device__ __forceinline__ double widen_f32(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned fe = (u >> 23) & 0xFFu;
-  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
-  if (fe == 0) return __longlong_as_double((long long)sign);
-  const unsigned long long E = fe == 0xFFu ? 0x7FFull : (unsigned long long)(fe + 896u);
-  return __longlong_as_double((long long)(sign | (E << 52) | m));
-}
-
 // hi + lo rounded to FP64: hi widened with integer instructions, lo converted
 // and added on the FP64 pipe (two FP64-pipe instructions a value).
 __device__ __forceinline__ double join_f64(df64 v) { return widen_f32(v.hi) + (double)v.lo; }
