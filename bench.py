@@ -31,22 +31,24 @@ if ROOT not in sys.path:
 
 METRIC = "MLUPS and % of HBM roofline, D2Q9 OReg-GEq; FP32 vs FP64 at stated error"
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "f64df": 144}
-# Algorithmic FP64 operations per node of one fused step (each add, mul or FMA is
-# one operation, i.e. one FP64 pipe issue), counted from the product-form
-# collision: 33 shared (moments 16, 1/rho 3, u 2, u^2 2, u/2 2, P 8), the
-# model part (LBGK 22, OReg 56, partial 66, complete 89; complete with the Eq. 12
-# prefactor from f^neq 83) and the fused diagnostics (7). The FP64 form is bound by
-# the FP64 pipe on GB300.
+# Algorithmic FP64 operations per node of one fused step (each add, mul or FMA of
+# the product-form collision is one operation): 33 shared (moments 16, 1/rho 3,
+# u 2, u^2 2, u/2 2, P 8), the model part (LBGK 22, OReg 56, partial 66,
+# complete 89; complete with the Eq. 12 prefactor from f^neq 83) and the fused
+# diagnostics (7). The FP64 form is bound by the FP64 pipe on GB300; the kernel
+# issues fewer of them to it (exact power-of-two scalings run on the integer
+# pipe: 121 of the complete model's 129), and the count stays the method's.
 FP64_OPS_PER_NODE = {"lbgk": 62, "oreg": 96, "partial": 106, "complete": 129, "complete_neq": 123}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch from the ncu capture of
-# the current kernels (profiles/step_kernel_f64_complete_2048.md and
-# profiles/step_stream_kernel_f32_complete_2048.md, 2048^2, scaled to the
-# lattice by node count since traffic grows with it). Keyed by (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.6, ("f32", "complete"): 60.0}
+# the current kernels (profiles/step_kernel_f64_complete_2048.md at 2048^2, scaled to
+# the lattice by node count since traffic grows with it, and
+# profiles/step_stream_persistent_kernel_f32_complete_4096.md at 4096^2). Keyed by
+# (storage, model).
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.5, ("f32", "complete"): 68.9}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
-STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_kernel",
+STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_persistent_kernel",
                "f16": "step_stream_kernel"}
 
 

@@ -19,25 +19,7 @@ template <typename CT> struct Desc {
   int pad;
 };
 
-__host__ __device__ inline Coef<f32x2> broadcast(const Coef<float>& a) {
-  Coef<f32x2> c;
-  c.theta = a.theta;
-  c.one_m_theta = a.one_m_theta;
-  c.half_theta = a.half_theta;
-  c.omega = a.omega;
-  c.one_m_omega = a.one_m_omega;
-  c.k1 = a.k1;
-  c.k2 = a.k2;
-  c.c3 = a.c3;
-  c.tt = a.tt;
-  c.inv2t2 = a.inv2t2;
-  c.mq_inv2t2 = a.mq_inv2t2;
-  c.rho_ref = a.rho_ref;
-  c.w[0] = a.w[0];
-  c.w[1] = a.w[1];
-  c.w[2] = a.w[2];
-  return c;
-}
+__host__ __device__ inline Coef<f32x2> broadcast(const Coef<float>& a) { return coef_cast<f32x2>(a); }
 
 // Consumer threads of a pipelined batch tile (launch kind 1): bx, or the
 // single-lattice default when bx = 0. Tiles are 2 NC columns wide.

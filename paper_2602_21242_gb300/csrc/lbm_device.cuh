@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace olbm {
 
 // ---------------------------------------------------------------- storage forms
@@ -127,6 +129,8 @@ template <typename T> struct Coef {
   T tt;           // theta (1 - 3 theta)
   T inv2t2;       // 1 / (2 theta^2)
   T mq_inv2t2;    // -1 / (8 theta^2)
+  T q_inv2t2;     // 1 / (8 theta^2)
+  T ntt;          // -theta (1 - 3 theta)
   T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
   T w[3];         // rho_ref * rest weights per axis pair are W(a) W(b); W(-1) = W(1) = theta/2, W(0) = 1 - theta
 };
@@ -145,10 +149,37 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
   c.tt = (T)(theta * (1.0 - 3.0 * theta));
   c.inv2t2 = (T)(1.0 / (2.0 * theta * theta));
   c.mq_inv2t2 = (T)(-0.25 / (2.0 * theta * theta));
+  c.q_inv2t2 = (T)(0.25 / (2.0 * theta * theta));
+  c.ntt = (T)(-theta * (1.0 - 3.0 * theta));
   c.rho_ref = (T)rho_ref;
   c.w[0] = (T)(0.5 * theta);
   c.w[1] = (T)(1.0 - theta);
   c.w[2] = (T)(0.5 * theta);
+  return c;
+}
+
+// The same coefficients in another arithmetic type (a batch stores FP32
+// coefficients per domain and broadcasts them to packed pairs).
+template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Coef<T>& a) {
+  static_assert(sizeof(Coef<float>) == 17 * sizeof(float), "coef_cast lists every field of Coef");
+  Coef<U> c;
+  c.theta = U(a.theta);
+  c.one_m_theta = U(a.one_m_theta);
+  c.half_theta = U(a.half_theta);
+  c.omega = U(a.omega);
+  c.one_m_omega = U(a.one_m_omega);
+  c.k1 = U(a.k1);
+  c.k2 = U(a.k2);
+  c.c3 = U(a.c3);
+  c.tt = U(a.tt);
+  c.inv2t2 = U(a.inv2t2);
+  c.mq_inv2t2 = U(a.mq_inv2t2);
+  c.q_inv2t2 = U(a.q_inv2t2);
+  c.ntt = U(a.ntt);
+  c.rho_ref = U(a.rho_ref);
+  c.w[0] = U(a.w[0]);
+  c.w[1] = U(a.w[1]);
+  c.w[2] = U(a.w[2]);
   return c;
 }
 
@@ -202,8 +233,16 @@ __device__ __forceinline__ double recip(double x) {
   const double e = fma(-x, r0, 1.0);
   return fma(r0, fma(e, e, e), r0);
 }
-__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
-__device__ __forceinline__ f32x2 recip(f32x2 x) { return f32x2(make_float2(1.0f / x.v.x, 1.0f / x.v.y)); }
+// FP32: the same seed and one Newton step r0 + r0 (1 - x r0) (within an ulp or
+// two of 1/x; the shifted forms round their stored deviations far more coarsely).
+__device__ __forceinline__ float recip(float x) {
+  const float r0 = rcp_seed(x);
+  return __fmaf_rn(r0, __fmaf_rn(-x, r0, 1.0f), r0);
+}
+__device__ __forceinline__ f32x2 recip(f32x2 x) {
+  const f32x2 r0(make_float2(rcp_seed(x.v.x), rcp_seed(x.v.y)));
+  return fma(r0, fma(-x, r0, f32x2(1.0f)), r0);
+}
 
 // k x and k x + c for a power of two k (exact scaling); the double-float type
 // overloads them with a scaling of both parts, two instructions instead of a
@@ -228,7 +267,9 @@ __device__ __forceinline__ double scaled(double x, float k) {
 // In-place collision of one node (Eq. 1a). f holds the stored values of the
 // pulled pre-collision populations (absolute, or deviations from the rest
 // state in the shifted forms); on return it holds the post-collision values
-// in the same representation.
+// in the same representation. sink(NodeMoments) receives the node's moments as
+// soon as they are known (the diagnostics accumulate them there, so they need
+// not stay live through the rest of the collision).
 //
 // With P(b), C(b) = b - u the per-axis factors, every post-collision
 // population of the Onsager-regularised models is written as
@@ -236,8 +277,8 @@ __device__ __forceinline__ double scaled(double x, float k) {
 // where E(a) = P_x(a) (rho + A1 C_x(a)^2), B(a) = A1 P_x(a), G(a) = A2 P_x(a) C_x(a),
 // A1 = omega' K1, A2 = omega' K2: the expansion of
 // f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] at three FMAs per population.
-template <int MODEL, bool SHIFT, typename T>
-__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments<T>& mom) {
+template <int MODEL, bool SHIFT, typename T, typename Sink>
+__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink) {
   // Moments (Sec. 1). The rest state has zero momentum, zero
   // sum (c_x^2 - c_y^2) W and zero sum c_x c_y W, so these sums are the same for
   // absolute and shifted values.
@@ -251,10 +292,14 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
   const T rho = SHIFT ? c.rho_ref + m0 : m0;
   const T inv_rho = recip(rho);
   const T ux = jx * inv_rho, uy = jy * inv_rho;
-  mom.m0 = m0;
-  mom.jx = jx;
-  mom.jy = jy;
-  mom.ke = scaled(fma(jx, ux, jy * uy), 0.5f);
+  {
+    NodeMoments<T> mom;
+    mom.m0 = m0;
+    mom.jx = jx;
+    mom.jy = jy;
+    mom.ke = scaled(fma(jx, ux, jy * uy), 0.5f);
+    sink(mom);
+  }
 
   const T ux2 = ux * ux, uy2 = uy * uy;
   // Per-axis GEq factors P(a) (Eq. 10), a = -1, 0, +1, and their deviations
@@ -264,8 +309,8 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
   // only needs P, one operation cheaper per axis.
   T dx[3], dy[3], px[3], py[3];
   if constexpr (SHIFT) {
-    dx[0] = fma(T(0.5), ux2, -hux), dx[1] = -ux2, dx[2] = fma(T(0.5), ux2, hux);
-    dy[0] = fma(T(0.5), uy2, -huy), dy[1] = -uy2, dy[2] = fma(T(0.5), uy2, huy);
+    dx[2] = fma(T(0.5), ux2, hux), dx[1] = -ux2, dx[0] = dx[2] - ux;
+    dy[2] = fma(T(0.5), uy2, huy), dy[1] = -uy2, dy[0] = dy[2] - uy;
     px[0] = c.half_theta + dx[0], px[1] = c.one_m_theta - ux2, px[2] = c.half_theta + dx[2];
     py[0] = c.half_theta + dy[0], py[1] = c.one_m_theta - uy2, py[2] = c.half_theta + dy[2];
   } else {
@@ -303,19 +348,24 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
     // Onsager-regularised models (Eq. 2) with corrections (Eqs. 14, 15).
     // Non-equilibrium stress (Eq. 4 gives Pi^eq = rho (u u + theta I) exactly):
     //   2 N_d = sum (c_x^2 - c_y^2) f - rho (u_x^2 - u_y^2),  N_xy = sum c_x c_y f - rho u_x u_y.
+    // (rho u_x u_y = j_x u_y. FP64 instructions negate operands for free; the
+    // packed FP32 forms have no negated operands and take C(0) = -u, which they
+    // form anyway.)
     const T Dxy = s13 - s24;
     const T Pxy = s57 - s68;
-    const T A1 = c.k1 * fma(-rho, ux2 - uy2, Dxy);  // omega' K1
-    const T A2 = c.k2 * fma(-jx, uy, Pxy);          // omega' K2
     const T cxm[3] = {T(-1.0) - ux, -ux, T(1.0) - ux};  // C_x(a) = a - u_x
     const T cym[3] = {T(-1.0) - uy, -uy, T(1.0) - uy};
+    constexpr bool kNegFree = std::is_same<T, double>::value;
+    const T dyx2 = uy2 - ux2;
+    const T A1 = c.k1 * fma(rho, dyx2, Dxy);                                    // omega' K1
+    const T A2 = c.k2 * (kNegFree ? fma(-jx, uy, Pxy) : fma(jx, cym[1], Pxy));  // omega' K2
     // omega' Psi per population (Eqs. 14, 15), from closed-form psi and Pi~.
     T cor[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) cor[i] = T(0.0);
     if constexpr (MODEL >= 2) {
       const T wpsx = A1 * ux * (c.c3 - ux2);   // omega' psi_x
-      const T wpsy = -A1 * uy * (c.c3 - uy2);  // omega' psi_y
+      const T wpsy = (kNegFree ? -A1 * uy : A1 * cym[1]) * (c.c3 - uy2);  // omega' psi_y
       if constexpr (MODEL == 2) {
         // Psi^P: -1/2 c_ia psi_a on the axis populations.
         cor[1] = scaled(wpsx, -0.5f);
@@ -325,17 +375,17 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, NodeMoments
       } else {
         // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12, evaluated on f^OReg (model 3):
         // pref = -(K1/2)(mu_xx + mu_yy); or on f^neq (model 4): pref = -K1.
-        T hwpref;  // omega' pref / 2
+        T nhw;  // -omega' pref / 2
         if constexpr (MODEL == 3) {
           const T muxx = (c.theta - ux2) * px[1];  // 2 theta^2 mu_xx
           const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
-          hwpref = c.mq_inv2t2 * A1 * (muxx + muyy);
+          nhw = c.q_inv2t2 * A1 * (muxx + muyy);
         } else {
-          hwpref = scaled(A1, -0.5f);
+          nhw = scaled(A1, 0.5f);
         }
-        const T hPxx = -hwpref * fma(ux2, ux2 - T(1.0), c.tt);       // omega' Pi~_xx / 2
-        const T hPyy = hwpref * fma(uy2, uy2 - T(1.0), c.tt);        // omega' Pi~_yy / 2
-        const T qPxy = scaled(hwpref, 0.5f) * (ux * uy) * (ux2 - uy2);  // omega' Pi~_xy / 4
+        const T hPxx = nhw * fma(ux2, ux2 - T(1.0), c.tt);               // omega' Pi~_xx / 2
+        const T hPyy = nhw * fma(uy2, T(1.0) - uy2, c.ntt);              // omega' Pi~_yy / 2
+        const T qPxy = scaled(nhw, 0.5f) * (ux * uy) * dyx2;             // omega' Pi~_xy / 4
         const T hpsx = scaled(wpsx, 0.5f), hpsy = scaled(wpsy, 0.5f);
         cor[1] = hPyy - hpsx;
         cor[3] = hPyy + hpsx;

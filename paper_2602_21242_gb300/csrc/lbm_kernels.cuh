@@ -260,12 +260,12 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
         CT f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = split_f64(r[i]);
-        NodeMoments<CT> m;
-        collide<MODEL, false, CT>(f, c, m);
+        collide<MODEL, false, CT>(f, c, [&](const NodeMoments<CT>& m) {
+          if constexpr (DIAG) acc.add(m);
+        });
         S* q = dst + (long long)y * g.pitch + x;
 #pragma unroll
         for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
-        if constexpr (DIAG) acc.add(m);
         if (more) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) r[i] = rn[i];
@@ -279,8 +279,9 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
     for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
       const bool more = (r + 1 < rows) && (y + dy < g.ny);
       if (more) pull(src, g, x, xm, xp, y + dy, fn);
-      NodeMoments<CT> m;
-      collide<MODEL, Form<PREC>::kShift, CT>(f, c, m);
+      collide<MODEL, Form<PREC>::kShift, CT>(f, c, [&](const NodeMoments<CT>& m) {
+        if constexpr (DIAG) acc.add(m);
+      });
       S* q = dst + (long long)y * g.pitch + x;
       if constexpr (PAIRS) {
 #pragma unroll
@@ -289,7 +290,6 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
 #pragma unroll
         for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
       }
-      if constexpr (DIAG) acc.add(m);
       if (more) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];

@@ -120,6 +120,13 @@ __device__ __forceinline__ f32x2 lds_two(const __half* p0, const __half* p1) {
 }
 
 // Shared-memory footprint of the ring (bytes).
+// Resident CTAs per SM the pipeline kernels ask the compiler to allow for:
+// three when a CTA of NC + 32 threads at 72 registers a thread fits three
+// times in the register file (NC = 256: the ring then also fits three times).
+// Without the bound the FP16 form's diagnostics variant takes 78 registers and
+// two CTAs a SM (measured: 2 x 9 warps, 113 against 136 GLUPS without it).
+template <int NC> constexpr int stream_min_blocks() { return (NC + 32) * 3 * 72 <= 65536 && NC >= 256 ? 3 : 1; }
+
 template <int PREC, int NC, int STAGES> struct StreamShape {
   using S = typename Form<PREC>::S;
   static constexpr int kChunk = 16 / (int)sizeof(S);   // elements in one 16-byte chunk
@@ -273,8 +280,17 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       if (active) {
-        NodeMoments<f32x2> m;
-        collide<MODEL, true, f32x2>(f, c, m);
+        collide<MODEL, true, f32x2>(f, c, [&](NodeMoments<f32x2> m) {
+          if constexpr (DIAG) {
+            if (!whole) {  // the pair's second node lies past the strip
+              m.m0.v.y = 0.0f;
+              m.jx.v.y = 0.0f;
+              m.jy.v.y = 0.0f;
+              m.ke.v.y = 0.0f;
+            }
+            acc.add(m);
+          }
+        });
         S* q = dst + (long long)(y0 + r0 + j) * g.pitch + x0 + xl;
         if (whole) {
 #pragma unroll
@@ -282,12 +298,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
         } else {
 #pragma unroll
           for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i].v.x);
-          m.m0.v.y = 0.0f;
-          m.jx.v.y = 0.0f;
-          m.jy.v.y = 0.0f;
-          m.ke.v.y = 0.0f;
         }
-        if constexpr (DIAG) acc.add(m);
       }
     }
     return true;
@@ -302,7 +313,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
 // last CTA to finish (counted in sched[1]) zeroes both counters for the next
 // launch.
 template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const typename Form<PREC>::S* __restrict__ src,
+__global__ void __launch_bounds__(NC + 32, stream_min_blocks<NC>()) step_stream_persistent_kernel(const typename Form<PREC>::S* __restrict__ src,
                                                                          typename Form<PREC>::S* __restrict__ dst,
                                                                          Geometry g, Coef<f32x2> c,
                                                                          double* __restrict__ partials, int H,
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(NC + 32) step_stream_persistent_kernel(const t
 // (Measured faster than the persistent form when registers allow only two
 // resident CTAs per SM: overlapping CTA lifetimes hide the ring's fill.)
 template <int MODEL, int PREC, bool DIAG, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32) step_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
+__global__ void __launch_bounds__(NC + 32, stream_min_blocks<NC>()) step_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
                                                              typename Form<PREC>::S* __restrict__ dst, Geometry g,
                                                              Coef<f32x2> c, double* __restrict__ partials, int H,
                                                              int* __restrict__ err) {
