@@ -369,6 +369,22 @@ int lbm_step_noalloc(int nx, int ny, double theta, double tau, int model, const 
  */
 int lbm_selftest_timeout(int which, double* h_seconds);
 
+/*
+ * Self-test of the FP64 arithmetic helpers the FP64 step kernel runs on the
+ * integer pipe (no counterpart in the paper): applies helper `op` on the GPU to
+ * the n host values h_x and writes the results to h_out (host, n doubles,
+ * caller-owned). op = 0, 1, 2: the exact scaling x * k for k = 1/2, -1/2, 1/4
+ * (exponent-field arithmetic; exact for x and x k in FP64's normal range, zeros,
+ * infinities and NaNs as x k); op = 3: the reciprocal used for 1/rho (FP32 seed
+ * of x truncated to FP32, one cubic Newton step; within an ulp or two of 1/x for
+ * 2^-126 <= |x| < 2^126, non-finite for x = 0, for non-finite x and below that
+ * range, zero above it); op = 4: x truncated to FP32 and widened back
+ * (integer conversions; zero below FP32's normal range, infinity above it and
+ * for infinities and NaNs). Synchronous.
+ * Returns LBM_EINVAL for another op, n < 0 or null pointers with n > 0.
+ */
+int lbm_selftest_fp64(int op, const double* h_x, long long n, double* h_out);
+
 /* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

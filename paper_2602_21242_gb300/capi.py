@@ -51,6 +51,7 @@ _SIGNATURES = {
     "lbm_sync": ([_p], _i),
     "lbm_measure_peak": ([_i, _pd], _i),
     "lbm_selftest_timeout": ([_i, _pd], _i),
+    "lbm_selftest_fp64": ([_i, _pd, _ll, _pd], _i),
     "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "lbm_set_launch": ([_p, _i, _i, _i], _i),
     "lbm_set_launch_ex": ([_p, _i, _i, _i, _i], _i),
@@ -371,6 +372,15 @@ def lbm_get_launch_ex(ctx):
     v = [_i() for _ in range(4)]
     check(load().lbm_get_launch_ex(ctx, *[ctypes.byref(x) for x in v]), ctx)
     return tuple(x.value for x in v)
+
+
+def lbm_selftest_fp64(op: int, x):
+    """Apply FP64 helper `op` (0-2: x/2, -x/2, x/4; 3: 1/x; 4: FP32 truncation) on the GPU."""
+    import numpy as np
+    xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    out = np.empty_like(xs)
+    check(load().lbm_selftest_fp64(op, xs.ctypes.data_as(_pd), xs.size, out.ctypes.data_as(_pd)), None)
+    return out
 
 
 def lbm_selftest_timeout(which: int):

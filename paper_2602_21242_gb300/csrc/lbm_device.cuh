@@ -219,10 +219,11 @@ __device__ __forceinline__ float narrow_trunc(double d) {
 // relative error below 2^-21) refined by one cubic Newton step
 // r = r0 (1 + e + e^2), e = 1 - x r0, which leaves a relative error
 // O(e^3) < 2^-62 before the final rounding: 3 FP64 operations instead of a full
-// IEEE division, the conversions on the integer pipe. Valid for |x| in the
-// FP32 normal range; x = 0, non-finite or tiny x give a non-finite result
-// (rcp.approx returns infinity for a zero seed, the Newton step then forms
-// 0 * inf or inf - inf), which the diagnostics report.
+// IEEE division, the conversions on the integer pipe. Valid for
+// 2^-126 <= |x| < 2^126 (the seed and its reciprocal FP32 normal numbers);
+// x = 0, non-finite or smaller x give a non-finite result (rcp.approx returns
+// infinity for a zero seed, the Newton step then forms 0 * inf or inf - inf),
+// which the diagnostics report; larger x give 0.
 __device__ __forceinline__ float rcp_seed(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -28,7 +28,41 @@ __global__ void stuck_grid_barrier_kernel(olbm::GridBarrier* b) {
   olbm::grid_sync(b, gridDim.x);
 }
 
+__global__ void fp64_helpers_kernel(int op, const double* __restrict__ x, long long n, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double r;
+  switch (op) {
+    case 0: r = olbm::scaled(v, 0.5f); break;
+    case 1: r = olbm::scaled(v, -0.5f); break;
+    case 2: r = olbm::scaled(v, 0.25f); break;
+    case 3: r = olbm::recip(v); break;
+    default: r = olbm::widen_f32(olbm::narrow_trunc(v)); break;
+  }
+  out[i] = r;
+}
+
 }  // namespace
+
+extern "C" int lbm_selftest_fp64(int op, const double* h_x, long long n, double* h_out) {
+  if (op < 0 || op > 4 || n < 0 || (n > 0 && (h_x == nullptr || h_out == nullptr))) return LBM_EINVAL;
+  if (n == 0) return LBM_OK;
+  double* d = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  if (cudaMalloc(&d, 2 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d, h_x, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    fp64_helpers_kernel<<<(unsigned)((n + 255) / 256), 256>>>(op, d, n, d + n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h_out, d + n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
 
 extern "C" int lbm_selftest_timeout(int which, double* h_seconds) {
   if (which != 0 && which != 1) return LBM_EINVAL;
