@@ -187,7 +187,7 @@ template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Co
 template <typename T> struct NodeMoments {
   T m0;  // sum of stored values: rho (absolute) or rho - rho_ref (shifted)
   T jx, jy;
-  T ke;  // rho |u|^2 / 2
+  T ux, uy;  // the kinetic energy is (j_x u_x + j_y u_y) / 2
 };
 
 // ---------------------------------------------------------------- FP64 helpers off the FP64 pipe
@@ -298,7 +298,8 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
     mom.m0 = m0;
     mom.jx = jx;
     mom.jy = jy;
-    mom.ke = scaled(fma(jx, ux, jy * uy), 0.5f);
+    mom.ux = ux;
+    mom.uy = uy;
     sink(mom);
   }
 

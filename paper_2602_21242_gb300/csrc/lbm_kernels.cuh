@@ -125,7 +125,13 @@ __device__ __forceinline__ f32x2 ld_two_cg(const __half* p0, const __half* p1) {
 __device__ __forceinline__ void st_pair(float* p, f32x2 v) { *reinterpret_cast<float2*>(p) = v.v; }
 __device__ __forceinline__ void st_pair(__half* p, f32x2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
 
-// Per-thread diagnostics accumulator in the compute type CT.
+// Per-thread diagnostics accumulator in the compute type CT: sums of m0, j_x,
+// j_y and of j_x u_x + j_y u_y (twice the kinetic energy: two FMAs a node, the
+// factor 1/2 applied once per block) over the nodes whose m0 is finite, and the
+// count of the others.
+__device__ __forceinline__ bool finite_lead(double x) { return finite_bits(x); }
+__device__ __forceinline__ bool finite_lead(float x) { return finite_bits(x); }
+__device__ __forceinline__ bool finite_lead(df64 x) { return finite_bits(x.hi); }
 template <typename CT> struct DiagAcc {
   CT v[4];
   int bad;
@@ -133,45 +139,38 @@ template <typename CT> struct DiagAcc {
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[k] = CT(0.0);
   }
-  __device__ __forceinline__ void add(const NodeMoments<CT>& m);
+  __device__ __forceinline__ void add(const NodeMoments<CT>& m) {
+    if (finite_lead(m.m0)) {
+      v[0] += m.m0;
+      v[1] += m.jx;
+      v[2] += m.jy;
+      v[3] = fma(m.jx, m.ux, fma(m.jy, m.uy, v[3]));
+    } else {
+      ++bad;
+    }
+  }
 };
-template <> __device__ __forceinline__ void DiagAcc<double>::add(const NodeMoments<double>& m) {
-  if (finite_bits(m.m0)) {
-    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
-  } else {
-    ++bad;
-  }
-}
-template <> __device__ __forceinline__ void DiagAcc<float>::add(const NodeMoments<float>& m) {
-  if (finite_bits(m.m0)) {
-    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
-  } else {
-    ++bad;
-  }
-}
-template <> __device__ __forceinline__ void DiagAcc<df64>::add(const NodeMoments<df64>& m) {
-  if (finite_bits(m.m0.hi)) {
-    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
-  } else {
-    ++bad;
-  }
-}
 template <> __device__ __forceinline__ void DiagAcc<f32x2>::add(const NodeMoments<f32x2>& m) {
   const bool ok0 = finite_bits(m.m0.v.x), ok1 = finite_bits(m.m0.v.y);
   if (ok0 && ok1) {
-    v[0] += m.m0; v[1] += m.jx; v[2] += m.jy; v[3] += m.ke;
-  } else {  // keep the finite node of the pair, count the other
-    const float2 k = make_float2(ok0 ? 1.0f : 0.0f, ok1 ? 1.0f : 0.0f);
-    v[0] += f32x2(make_float2(ok0 ? m.m0.v.x : 0.0f, ok1 ? m.m0.v.y : 0.0f));
-    v[1] += f32x2(make_float2(k.x * m.jx.v.x, k.y * m.jx.v.y));
-    v[2] += f32x2(make_float2(k.x * m.jy.v.x, k.y * m.jy.v.y));
-    v[3] += f32x2(make_float2(k.x * m.ke.v.x, k.y * m.ke.v.y));
+    v[0] += m.m0;
+    v[1] += m.jx;
+    v[2] += m.jy;
+    v[3] = fma(m.jx, m.ux, fma(m.jy, m.uy, v[3]));
+  } else {  // keep the finite node of the pair (selects, so that no NaN enters), count the other
+    auto keep = [&](const f32x2& a) { return f32x2(make_float2(ok0 ? a.v.x : 0.0f, ok1 ? a.v.y : 0.0f)); };
+    const f32x2 jx = keep(m.jx), jy = keep(m.jy);
+    v[0] += keep(m.m0);
+    v[1] += jx;
+    v[2] += jy;
+    v[3] = fma(jx, keep(m.ux), fma(jy, keep(m.uy), v[3]));
     bad += (ok0 ? 0 : 1) + (ok1 ? 0 : 1);
   }
 }
 
 // Reduce a thread's accumulator over the block into out5 (thread 0 writes).
 template <typename CT> __device__ __forceinline__ void block_diag_acc(DiagAcc<CT>& a, double* out5) {
+  a.v[3] = scaled(a.v[3], 0.5f);  // kinetic energy
   if constexpr (std::is_same<CT, f32x2>::value) {
     float v[4];
 #pragma unroll

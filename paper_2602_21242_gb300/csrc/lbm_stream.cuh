@@ -286,7 +286,8 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
               m.m0.v.y = 0.0f;
               m.jx.v.y = 0.0f;
               m.jy.v.y = 0.0f;
-              m.ke.v.y = 0.0f;
+              m.ux.v.y = 0.0f;
+              m.uy.v.y = 0.0f;
             }
             acc.add(m);
           }
