@@ -334,15 +334,16 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
           f[i] = fma(e[a + 1], py[b + 1], c.one_m_omega * f[i]);
         }
     } else {
-      // Shifted: f^eq - rho_ref W W = m0 W_a W_b + rho (dP_x(a) P_y(b) + W_a dP_y(b)),
-      // so no O(1) terms cancel.
+      // Shifted: f^eq - rho_ref W W = rho dP_x(a) P_y(b) + W_a Q(b) with
+      // Q(b) = m0 W_b + rho dP_y(b), so no O(1) terms cancel.
+      const T rdx[3] = {rho * dx[0], rho * dx[1], rho * dx[2]};
+      const T Q[3] = {fma(m0, c.w[0], rho * dy[0]), fma(m0, c.w[1], rho * dy[1]), fma(m0, c.w[2], rho * dy[2])};
 #pragma unroll
       for (int a = -1; a <= 1; ++a)
 #pragma unroll
         for (int b = -1; b <= 1; ++b) {
           const int i = pop_index(a, b);
-          const T feq = fma(m0 * c.w[a + 1], c.w[b + 1],
-                            rho * fma(dx[a + 1], py[b + 1], c.w[a + 1] * dy[b + 1]));
+          const T feq = fma(c.w[a + 1], Q[b + 1], rdx[a + 1] * py[b + 1]);
           f[i] = fma(c.omega, feq - f[i], f[i]);
         }
     }
@@ -400,6 +401,13 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
         cor[8] = dsum + qPxy;
       }
     }
+    // Shifted forms: the f^eq deviation not carried by P_y(b) E(a) is W_a Q(b),
+    // Q(b) = m0 W_b + rho dP_y(b).
+    T Q[3];
+    if constexpr (SHIFT) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Q[k] = fma(m0, c.w[k], rho * dy[k]);
+    }
     T E[3], B[3], G[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -414,10 +422,7 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
       for (int b = -1; b <= 1; ++b) {
         const int i = pop_index(a, b);
         T rest = cor[i];
-        if constexpr (SHIFT) {
-          // remaining f^eq deviation: m0 W_a W_b + rho W_a dP_y(b)
-          rest = fma(m0 * c.w[a + 1], c.w[b + 1], fma(rho * c.w[a + 1], dy[b + 1], rest));
-        }
+        if constexpr (SHIFT) rest = fma(c.w[a + 1], Q[b + 1], rest);
         f[i] = fma(py[b + 1], fma(cym[b + 1], fma(-B[a + 1], cym[b + 1], G[a + 1]), E[a + 1]), rest);
       }
   }
