@@ -169,3 +169,28 @@ def test_pipeline_kernel_any_width(oracle, prec, nx, ny, rows, ctas):
     assert t == steps - 1
     np.testing.assert_allclose(out[:4], oracle.diagnostics(prev)[:4], rtol=1e-5, atol=1e-5)
     assert out[4] == 0
+
+
+@pytest.mark.parametrize("prec,launch", [("f64", None), ("f64df", None), ("f32", (0, 128, 4, 16)),
+                                         ("f32", (1, 0, 1, 8)), ("f32", (1, 64, 1, 8)), ("f16", (0, 128, 4, 16)),
+                                         ("f16", (1, 0, 1, 8)), ("f16", (1, 64, 1, 8))])
+def test_fused_diagnostics_skip_a_nonfinite_node(oracle, prec, launch):
+    """One NaN population (at an odd column, so the second node of a pair in the shifted forms):
+    the fused pass counts exactly that node and sums the others, in every storage form and
+    launch kind, against the oracle's sums over the finite nodes of the same stored state."""
+    from paper_2602_21242_gb300 import capi
+    f0 = flows.random_populations(40, 17, seed=31, spread=0.1)
+    f0[4, 6, 11] = np.nan
+    with Lattice(40, 17, 1 / 3, 0.8, "complete", prec) as lat:
+        if launch is not None:
+            capi.lbm_set_launch_ex(lat.ctx, *launch)
+        lat.set_state(torch.from_numpy(f0).cuda())
+        stored = lat.state().cpu().numpy()
+        lat.set_diagnostics_interval(1)
+        lat.step(1)
+        d, t, status = lat.step_diagnostics(raise_nonfinite=False)
+    assert status == capi.LBM_ENONFINITE and t == 0
+    want = oracle.diagnostics(stored)
+    assert want[4] == 1 and d[4] == 1
+    tol = {"f64": 1e-12, "f64df": 1e-11}.get(prec, 1e-5)
+    np.testing.assert_allclose(d[:4], want[:4], rtol=tol, atol=tol)
