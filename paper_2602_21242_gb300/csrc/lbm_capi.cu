@@ -70,11 +70,25 @@ olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
   } else {
     k.bx = 128, k.by = 4, k.rows = 16;
   }
+  if (k.kind == 1 && prec == LBM_F16_SHIFT) {
+    // One CTA per tile: the tile height whose last wave of CTAs is fullest,
+    // preferring taller tiles unless a shorter one wastes 2 % less of a wave
+    // (4096^2: 24 rows, 3.0 waves, +2-4 % over 32 rows; 8192^2: 48 rows).
+    const long long strips = (g.nx + olbm::stream_tile_width(prec) - 1) / olbm::stream_tile_width(prec);
+    const double resident = (double)olbm::stream_ctas_per_sm(prec) * sms;
+    double best_waste = 2.0;
+    for (int rows : {48, 40, 32, 24, 16}) {
+      const double waves = (double)(strips * ((g.ny + rows - 1) / rows)) / resident;
+      const double full = std::ceil(waves);
+      const double waste = (full - waves) / full;
+      if (waste < best_waste - 0.02) best_waste = waste, k.rows = rows;
+    }
+  }
   while (k.rows > 1 && olbm::step_blocks(g, k, prec) < 4LL * sms) k.rows /= 2;
-  // FP32: the persistent pipeline over all resident CTAs on 16-row tiles
-  // (measured 2-3 % above one CTA per tile at 4096^2 and 8192^2; for FP16 it
+  // FP32: the persistent pipeline over all resident CTAs on 4-row tiles
+  // (measured 3-5 % above one CTA per tile at 4096^2 and 8192^2; for FP16 it
   // is slower, so FP16 keeps one CTA per tile).
-  if (k.kind == 1 && prec == LBM_F32_SHIFT) k.bx = 64, k.rows = k.rows < 16 ? k.rows : 16;
+  if (k.kind == 1 && prec == LBM_F32_SHIFT) k.bx = 64, k.rows = k.rows < 4 ? k.rows : 4;
   return k;
 }
 

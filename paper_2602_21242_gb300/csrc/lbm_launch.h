@@ -44,6 +44,10 @@ struct StepArgs {
 // step kernel under a launch shape (= diagnostics partials they write).
 long long node_blocks(const Geometry& g);
 long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec);
+// Columns of one bulk-copy pipeline tile and the CTAs of that kernel resident
+// on one SM (launch kind 1) for a shifted storage form.
+int stream_tile_width(int prec);
+int stream_ctas_per_sm(int prec);
 
 #define OLBM_DECLARE_LAUNCHERS(SUFFIX)                                                                        \
   cudaError_t launch_step_##SUFFIX(const StepArgs& a, cudaStream_t st);                                       \

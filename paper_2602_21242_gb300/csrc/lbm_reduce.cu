@@ -15,6 +15,12 @@ long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec) {
   return (long long)gr.x * gr.y;
 }
 
+int stream_tile_width(int prec) { return stream_width(prec); }
+
+// The ring fits three times in an SM's shared memory for both shifted forms;
+// FP16 is compiled for three CTAs (registers), FP32 (160 threads) fits them.
+int stream_ctas_per_sm(int) { return 3; }
+
 // Fixed-order final sum of the block partials: out[0..4] as in lbm_diagnostics
 // (mass gets rho_ref for every finite node), out[5] = t; non-finite nodes are
 // added to *sticky.
