@@ -238,12 +238,15 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * mbarrier transaction counts while consumer warps collide node pairs; the
  * lattice is cut into tiles of 256 (FP32) or 512 (FP16) columns by `rows` rows
  * (1..4096); bx = 0 launches one CTA per tile, bx = k > 0 a persistent grid of k
- * CTAs per SM (capped at the resident count) that takes the tiles round robin
- * (by ignored). Its waits are bounded: a wait that gives up makes lbm_sync and
- * lbm_step_diagnostics return LBM_ETIMEOUT. Same results as kind 0 for even nx
- * (FP32 rounding may differ in the last bit for odd nx, where kind 0 updates
- * single nodes) except the diagnostics' summation order. Default for the
- * shifted forms on lattices at least 32 columns wide.
+ * CTAs per SM (capped at the resident count) whose CTAs take the next tile from
+ * a counter in device memory that the context owns (by ignored). Its waits are
+ * bounded: a wait that gives up makes lbm_sync and lbm_step_diagnostics return
+ * LBM_ETIMEOUT. Same results as kind 0 for even nx (FP32 rounding may differ in
+ * the last bit for odd nx, where kind 0 updates single nodes) except the
+ * diagnostics' summation order. Default for the shifted forms on lattices at
+ * least 32 columns wide: FP32 the persistent grid on 4-row tiles, FP16 one CTA
+ * per tile with the height in {48, 40, 32, 24, 16} that best fills the last
+ * wave of CTAs (halved further on small lattices).
  */
 int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows);
 int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows);
