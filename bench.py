@@ -77,6 +77,9 @@ def parse_args():
     ap.add_argument("--config-sweep", action="store_true",
                     help="time every model, U and theta of the 4096^2 shear-wave benchmark (FP64 and double-float)")
     ap.add_argument("--sweep-steps", type=int, default=200)
+    ap.add_argument("--vjp-only", action="store_true",
+                    help="run only the differentiation workload (gradient through lbm_vjp) and print its JSON")
+    ap.add_argument("--vjp-steps", type=int, default=500, help="steps of the differentiation workload")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the 256-domain batched workload (graph and persistent modes) and print its JSON")
     return ap.parse_args()
@@ -305,7 +308,7 @@ def run_gpu(args):
     if not args.no_forms:
         out["forms"] = forms_sweep(w, fields, dev, stream, peak_hbm)
         out["forms"].update(batch_sweep(dev, stream, peak_hbm, steps=args.batch_steps))
-        out["forms"].update(vjp_sweep(dev, stream))
+        out["forms"].update(vjp_sweep(dev, stream, steps=args.vjp_steps))
 
     # ---- CPU baseline (oracle) on rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -661,6 +664,13 @@ def main():
         return
     if args.config_sweep:
         config_sweep(args)
+        return
+    if args.vjp_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        print(json.dumps(vjp_sweep(torch.device("cuda", 0), stream, steps=args.vjp_steps)), flush=True)
         return
     if args.batch_only:
         import torch
