@@ -263,8 +263,13 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
           if constexpr (DIAG) acc.add(m);
         });
         S* q = dst + (long long)y * g.pitch + x;
+        if constexpr (MODEL == 0) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
+          for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) q[i * g.plane] = join_f64_fp64pipe(f[i]);
+        }
         if (more) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) r[i] = rn[i];
