@@ -232,12 +232,13 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
 
 /*
  * Step-kernel selection (no counterpart in the paper). kind 0: the column kernel
- * of lbm_set_launch. kind 1 (shifted FP32/FP16 forms, any nx; FP64 lattices
- * keep kind 0's kernel): a producer warp streams each output
- * row's nine plane segments into a shared-memory ring with TMA bulk copies and
- * mbarrier transaction counts while consumer warps collide node pairs; the
- * lattice is cut into tiles of 256 (FP32) or 512 (FP16) columns by `rows` rows
- * (1..4096); bx = 0 launches one CTA per tile, bx = k > 0 a persistent grid of k
+ * of lbm_set_launch. kind 1 (shifted FP32/FP16 forms and FP64, any nx; not
+ * LBM_F64_DF): a producer warp streams each output row's nine plane segments
+ * into a shared-memory ring with TMA bulk copies and mbarrier transaction
+ * counts while consumer warps collide node pairs (FP64: single nodes); the
+ * lattice is cut into tiles of 256 (FP32), 512 (FP16) or 128 (FP64) columns by
+ * `rows` rows (1..4096); bx = 0 launches one CTA per tile, bx = k > 0 (shifted
+ * forms only; LBM_EINVAL for FP64) a persistent grid of k
  * CTAs per SM (capped at the resident count) whose CTAs take the next tile from
  * a counter in device memory that the context owns (by ignored). Its waits are
  * bounded: a wait that gives up makes lbm_sync and lbm_step_diagnostics return

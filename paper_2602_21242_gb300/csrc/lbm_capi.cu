@@ -512,6 +512,8 @@ int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows) {
                 kind, bx, by, rows);
   if (ctx->prec == LBM_F64_DF && (k.kind != 0 || bx * by > 256))
     return fail(ctx, LBM_EINVAL, "storage form LBM_F64_DF takes launch kind 0 with at most 256 threads a block");
+  if (ctx->prec == LBM_F64 && k.kind == 1 && bx != 0)
+    return fail(ctx, LBM_EINVAL, "storage form LBM_F64 takes launch kind 1 with one CTA per tile (bx = 0)");
   const long long need = olbm::step_blocks(ctx->g, k, ctx->prec);
   if (need > ctx->parts_cap) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);

@@ -354,9 +354,13 @@ __global__ void __maxnreg__(96) step_kernel_f64(const double* __restrict__ src, 
 
 namespace olbm {
 
-// Pipeline shapes per storage form: consumer threads (node pairs) and ring slots.
+// Pipeline shapes per storage form: consumer threads (node pairs; FP64: single
+// nodes) and ring slots.
 constexpr int kStreamNC32 = 128, kStreamNC16 = 256, kStreamStages = 8;
-inline int stream_width(int prec) { return 2 * (prec == 1 ? kStreamNC32 : kStreamNC16); }
+constexpr int kStreamNC64 = 128, kStreamStages64 = 4;
+inline int stream_width(int prec) {
+  return prec == 0 ? kStreamNC64 : 2 * (prec == 1 ? kStreamNC32 : kStreamNC16);
+}
 
 // ------------------------------------------------------------------ diagnostics of the state
 // Pull only (no collision): FP64 moments of f(x, t), block partials as above.
@@ -478,10 +482,10 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
 // The shifted forms (1, 2) update node pairs (x, x + 1) when nx is even.
 inline bool uses_pairs(int prec, const Geometry& g) { return (prec == 1 || prec == 2) && (g.nx % 2) == 0; }
-// The pipeline kernel (launch kind 1) applies to the shifted forms, any nx.
+// The pipeline kernel (launch kind 1) applies to the shifted forms and FP64, any nx.
 inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
   (void)g;
-  return k.kind == 1 && (prec == 1 || prec == 2);
+  return k.kind == 1 && (prec == 0 || prec == 1 || prec == 2);
 }
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   if (uses_stream(prec, g, k)) {
@@ -576,10 +580,28 @@ template <int PREC> struct Launch {
     return cudaGetLastError();
   }
 
+  // FP64 pipeline (launch kind 1, one CTA per tile).
+  template <int MODEL, bool DIAG>
+  static cudaError_t stream_f64(const StepArgs& a, cudaStream_t st) {
+    using Shape = StreamShape<0, kStreamNC64, kStreamStages64>;
+    static_assert(Shape::kSmemBytes <= 48 * 1024, "the FP64 ring fits the default shared-memory window");
+    if (a.err == nullptr || a.cfg.bx != 0) return cudaErrorInvalidValue;
+    const dim3 grid = step_grid(a.g, a.cfg, 0);
+    if (a.parts_used) *a.parts_used = (long long)grid.x * grid.y;
+    const Coef<double> c = make_coef<double>(a.theta, a.tau, a.rho_ref);
+    step_stream_f64_kernel<MODEL, DIAG, kStreamNC64, kStreamStages64><<<grid, kStreamNC64 + 32, Shape::kSmemBytes, st>>>(
+        (const double*)a.src, (double*)a.dst, a.g, c, a.partials, a.cfg.rows, a.err);
+    return cudaGetLastError();
+  }
+
   template <int MODEL>
   static cudaError_t step_m(const StepArgs& a, cudaStream_t st) {
     if constexpr (PREC == 1 || PREC == 2) {
       if (uses_stream(PREC, a.g, a.cfg)) return a.diag ? stream_d<MODEL, true>(a, st) : stream_d<MODEL, false>(a, st);
+    }
+    if constexpr (PREC == 0) {
+      if (uses_stream(PREC, a.g, a.cfg))
+        return a.diag ? stream_f64<MODEL, true>(a, st) : stream_f64<MODEL, false>(a, st);
     }
     if constexpr (PREC == 1 || PREC == 2) {
       if (uses_pairs(PREC, a.g)) return step_p<MODEL, true>(a, st);

@@ -10,10 +10,10 @@ namespace olbm {
 
 // Launch shape of the step kernel. kind 0: bx x by threads (bx a multiple of
 // 32, bx * by <= 512), each thread updating `rows` nodes of one column.
-// kind 1 (shifted forms, any nx): the bulk-copy pipeline over
+// kind 1 (shifted forms and FP64, any nx): the bulk-copy pipeline over
 // tiles of stream_width(prec) columns by `rows` rows; bx = 0 launches one CTA
-// per tile, bx > 0 a persistent grid of bx CTAs per SM (at most the resident
-// count) looping over the tiles; by unused.
+// per tile, bx > 0 (shifted forms) a persistent grid of bx CTAs per SM (at
+// most the resident count) looping over the tiles; by unused.
 struct LaunchCfg {
   int bx = 32, by = 8, rows = 1, kind = 0;
   int cap = 0;  // kind 1: most CTAs launched (a multiple of the SM count); 0 = one CTA per tile

@@ -130,7 +130,7 @@ template <int NC> constexpr int stream_min_blocks() { return (NC + 32) * 3 * 72 
 template <int PREC, int NC, int STAGES> struct StreamShape {
   using S = typename Form<PREC>::S;
   static constexpr int kChunk = 16 / (int)sizeof(S);   // elements in one 16-byte chunk
-  static constexpr int kW = 2 * NC;                     // nodes per row segment
+  static constexpr int kW = PREC == 0 ? NC : 2 * NC;    // nodes per row segment (FP64: one per consumer)
   static constexpr int kSeg = kW + 2 * kChunk;          // elements per plane per slot
   static constexpr int kSlotBytes = 9 * kSeg * (int)sizeof(S);
   static constexpr int kRingBytes = STAGES * kSlotBytes;
@@ -304,6 +304,51 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
     }
     return true;
   }
+
+  // FP64 storage (PREC 0): consumer thread t updates local node xl of row j of
+  // each slot (t = j w + xl) in FP64, one node a thread.
+  template <int MODEL, bool DIAG>
+  __device__ __forceinline__ bool consume_f64(double* __restrict__ dst, const Geometry& g, const Coef<double>& c,
+                                              int x0, int y0, int rows, int t, int lane, DiagAcc<double>& acc,
+                                              int* err) {
+    static_assert(PREC == 0, "one node a consumer thread is the FP64 layout");
+    const TilePlan<CH> p(g, x0, W, SEG);
+    const int j = t / p.w;
+    const int xl = t - j * p.w;
+    const int base = j * p.sub;
+    const int iM = base + CH + xl;
+    const int iL = xl == 0 ? base + p.lidx : iM - 1;
+    const int iR = xl + 1 < p.w ? iM + 1 : base + CH + p.wr;
+    for (int r0 = 0; r0 < rows; r0 += p.R, ++k) {
+      const bool active = j < min(p.R, rows - r0);
+      const int s = k % STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err))) return false;
+      const double* slot = ring + (size_t)s * 9 * SEG;
+      double f[9];
+      if (active) {
+        f[0] = slot[0 * SEG + iM];
+        f[1] = slot[1 * SEG + iL];
+        f[2] = slot[2 * SEG + iM];
+        f[3] = slot[3 * SEG + iR];
+        f[4] = slot[4 * SEG + iM];
+        f[5] = slot[5 * SEG + iL];
+        f[6] = slot[6 * SEG + iR];
+        f[7] = slot[7 * SEG + iR];
+        f[8] = slot[8 * SEG + iL];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (active) {
+        collide<MODEL, false, double>(f, c, [&](const NodeMoments<double>& m) {
+          if constexpr (DIAG) acc.add(m);
+        });
+        double* q = dst + (long long)(y0 + r0 + j) * g.pitch + x0 + xl;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[i * g.plane] = f[i];
+      }
+    }
+    return true;
+  }
 };
 
 // Persistent form over one lattice. Tiles: strips of W columns x blocks of H
@@ -398,6 +443,31 @@ __global__ void __launch_bounds__(NC + 32, stream_min_blocks<NC>()) step_stream_
     pipe.drain(err);
   } else if (threadIdx.x < NC) {
     pipe.template consume<MODEL, DIAG>(dst, g, c, x0, y0, rows, threadIdx.x, lane, acc, err);
+  }
+  if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
+}
+
+// FP64 storage, one CTA per tile of W = NC columns: the same producer, one
+// node a consumer thread (compiled for four resident CTAs: 96 registers).
+template <int MODEL, bool DIAG, int NC, int STAGES>
+__global__ void __launch_bounds__(NC + 32, 4) step_stream_f64_kernel(const double* __restrict__ src,
+                                                                      double* __restrict__ dst, Geometry g,
+                                                                      Coef<double> c, double* __restrict__ partials,
+                                                                      int H, int* __restrict__ err) {
+  using P = Pipeline<0, NC, STAGES>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  P pipe(smem);
+  pipe.init();
+  __syncthreads();
+  const int x0 = blockIdx.x * P::W, y0 = blockIdx.y * H;
+  const int rows = min(H, g.ny - y0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DiagAcc<double> acc;
+  if (warp == P::kConsumerWarps) {
+    pipe.produce(src, g, x0, y0, rows, lane, err);
+    pipe.drain(err);
+  } else if (threadIdx.x < NC) {
+    pipe.template consume_f64<MODEL, DIAG>(dst, g, c, x0, y0, rows, threadIdx.x, lane, acc, err);
   }
   if constexpr (DIAG) block_diag_acc(acc, partials + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5);
 }

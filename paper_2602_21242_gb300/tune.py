@@ -89,7 +89,7 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
             return tuple(hit["shape"]), None
     if candidates is None:
         candidates = list(LATTICE_CANDIDATES)
-        if lat.prec != capi.LBM_F64:
+        if lat.prec != capi.LBM_F64_DF:  # shapes a form does not take are skipped below
             candidates += PIPELINE_CANDIDATES
     best = None
     with Lattice(lat.nx, lat.ny, lat.theta, lat.tau, lat.model, lat.prec, device=lat.device,

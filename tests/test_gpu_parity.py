@@ -303,3 +303,36 @@ def test_full_size_sampled_shifted_forms(oracle, prec):
         want = oracle.collide_node(pre[j], theta, tau, 3)
         d = max(np.abs(pre[j] - rest).max(), np.abs(want - rest).max())
         assert np.abs(post[j] - want).max() <= k * 2.0 ** -p * d, f"node {j}"
+
+
+@pytest.mark.parametrize("nx,ny,rows", [(37, 23, 5), (128, 16, 4), (130, 9, 3), (257, 12, 7), (1, 5, 2), (3, 4, 4),
+                                        (45, 19, 8), (600, 33, 16)])
+@pytest.mark.parametrize("model", [0, 3, 4])
+def test_fp64_pipeline_parity(oracle, nx, ny, rows, model):
+    """FP64 through the bulk-copy pipeline (launch kind 1: 128-column tiles, one node a consumer
+    thread): full and partial strips, narrow lattices whose rows share a ring slot, odd widths
+    whose last main copy runs into the row padding, ragged row blocks; 100 steps against the
+    oracle at the FP64 bar, and one fused diagnostics pass against the oracle's sums."""
+    theta, tau = 0.35, 0.8
+    f0 = flows.random_populations(nx, ny, seed=4100 + nx + 3 * ny + model, spread=0.2)
+    with Lattice(nx, ny, theta, tau, model, "f64") as lat:
+        capi.lbm_set_launch_ex(lat.ctx, 1, 0, 0, rows)
+        assert capi.lbm_get_launch_ex(lat.ctx)[0] == 1
+        lat.set_state(torch.from_numpy(f0).cuda())
+        lat.step(99)
+        prev = lat.state().cpu().numpy()
+        lat.set_diagnostics_interval(1)
+        lat.step(1)
+        d, t, status = lat.step_diagnostics()
+        got = lat.state().cpu().numpy()
+    ref = oracle.run(f0, theta, tau, model, 100)
+    assert_rel(got, ref, REL_F64, f"pipeline {nx}x{ny} rows {rows} model {model}")
+    assert t == 99 and status == 0
+    np.testing.assert_allclose(d, oracle.diagnostics(prev), rtol=1e-12, atol=1e-13)
+
+
+def test_fp64_pipeline_rejects_persistent_grid():
+    with Lattice(64, 8, 1 / 3, 0.8, "complete", "f64") as lat:
+        with pytest.raises(capi.LBMError) as e:
+            capi.lbm_set_launch_ex(lat.ctx, 1, 2, 0, 8)
+        assert e.value.status == capi.LBM_EINVAL
