@@ -2,13 +2,15 @@
 // forms (arXiv 2602.21242, Eq. 1; same per-node arithmetic as the column
 // kernels).
 //
-// Work is cut into tiles: strips of W = 2 * NC node columns [x0, x0 + W) by
-// blocks of H rows; a persistent grid of CTAs takes tiles round robin. A
+// Work is cut into tiles: strips of W = 2 * NC node columns [x0, x0 + W) (FP64:
+// W = NC) by blocks of H rows, one CTA per tile or a persistent grid whose CTAs
+// take the next tile from a counter. A
 // producer warp streams, row by row, the nine plane segments each output row
 // pulls (plane i: row y - c_iy, columns x0 - c_ix ..) into a ring of STAGES
 // shared-memory slots with cp.async.bulk (TMA bulk copies, tracked by mbarrier
-// transaction counts); NC consumer threads (node pairs, packed f32x2 collision)
-// read the slot, collide, store the pair to global memory and release the slot.
+// transaction counts); NC consumer threads (node pairs, packed f32x2 collision;
+// FP64: single nodes) read the slot, collide, store to global memory and
+// release the slot.
 // Each slot holds, per plane, the row segment plus one 16-byte chunk on each
 // side that carries the x -+ 1 neighbours (periodic in x and y: the producer
 // computes the wrapped source row and the wrapped edge chunks). Bulk copies
