@@ -138,8 +138,8 @@ __device__ __forceinline__ df64 split_f64(double d) {
 __device__ __forceinline__ double join_f64(df64 v) { return widen_f32(v.hi) + (double)v.lo; }
 // The same sum with both conversions on the FP64 pipe: three FP64-pipe
 // instructions and no integer work. Faster where the FP64 pipe has room beside
-// a long double-float collision (the Onsager-regularised models: +4 %), slower
-// where it does not (LBGK: -18 %).
+// a long double-float collision (the corrected models: +3 to +4 %), slower
+// where it does not (LBGK: -18 %, the uncorrected model: -1 %).
 __device__ __forceinline__ double join_f64_fp64pipe(df64 v) { return (double)v.hi + (double)v.lo; }
 
 // Storage form 3: FP64 populations, double-float arithmetic.

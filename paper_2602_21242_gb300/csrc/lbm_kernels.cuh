@@ -263,7 +263,7 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
           if constexpr (DIAG) acc.add(m);
         });
         S* q = dst + (long long)y * g.pitch + x;
-        if constexpr (MODEL == 0) {
+        if constexpr (MODEL <= 1) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
         } else {
