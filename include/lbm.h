@@ -381,8 +381,7 @@ int lbm_selftest_timeout(int which, double* h_seconds);
  * (exponent-field arithmetic; exact for x and x k in FP64's normal range, zeros,
  * infinities and NaNs as x k); op = 3: the reciprocal used for 1/rho (FP32 seed
  * of x truncated to FP32, one cubic Newton step; within an ulp or two of 1/x for
- * 2^-126 <= |x| < 2^126, non-finite for x = 0, for non-finite x and below that
- * range, zero above it); op = 4: x truncated to FP32 and widened back
+ * 2^-126 <= |x| < 2^126, non-finite for every other x); op = 4: x truncated to FP32 and widened back
  * (integer conversions; zero below FP32's normal range, infinity above it and
  * for infinities and NaNs). Synchronous.
  * Returns LBM_EINVAL for another op, n < 0 or null pointers with n > 0.

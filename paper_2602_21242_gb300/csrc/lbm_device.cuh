@@ -221,16 +221,19 @@ __device__ __forceinline__ float narrow_trunc(double d) {
 // O(e^3) < 2^-62 before the final rounding: 3 FP64 operations instead of a full
 // IEEE division, the conversions on the integer pipe. Valid for
 // 2^-126 <= |x| < 2^126 (the seed and its reciprocal FP32 normal numbers);
-// x = 0, non-finite or smaller x give a non-finite result (rcp.approx returns
-// infinity for a zero seed, the Newton step then forms 0 * inf or inf - inf),
-// which the diagnostics report; larger x give 0.
+// every other x gives a non-finite result, which the diagnostics report: x = 0,
+// non-finite or smaller x through the Newton step (rcp.approx returns infinity
+// for a zero seed, the step then forms 0 * inf or inf - inf), larger x through a
+// NaN seed in place of the zero that rcp.approx returns for them (a density
+// that large only arises in a simulation that has blown up).
 __device__ __forceinline__ float rcp_seed(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ double recip(double x) {
-  const double r0 = widen_f32(rcp_seed(narrow_trunc(x)));
+  const float s = rcp_seed(narrow_trunc(x));
+  const double r0 = widen_f32(__float_as_uint(s) << 1 == 0u ? __uint_as_float(0x7FC00000u) : s);
   const double e = fma(-x, r0, 1.0);
   return fma(r0, fma(e, e, e), r0);
 }
@@ -428,14 +431,13 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
   }
 }
 
-// Guided equilibrium (Eq. 10) in FP64, product form; used by lbm_init.
-__device__ __forceinline__ void geq_f64(double rho, double ux, double uy, double theta, double (&feq)[9]) {
-  const double px[3] = {0.5 * (theta + ux * ux - ux), 1.0 - theta - ux * ux, 0.5 * (theta + ux * ux + ux)};
-  const double py[3] = {0.5 * (theta + uy * uy - uy), 1.0 - theta - uy * uy, 0.5 * (theta + uy * uy + uy)};
-#pragma unroll
-  for (int a = -1; a <= 1; ++a)
-#pragma unroll
-    for (int b = -1; b <= 1; ++b) feq[pop_index(a, b)] = rho * px[a + 1] * py[b + 1];
+// Population i of the guided equilibrium (Eq. 10) in FP64, product form:
+// rho P_x(c_ix) P_y(c_iy); used by lbm_init.
+__device__ __forceinline__ double geq_one_f64(int i, double rho, double ux, double uy, double theta) {
+  const int a = cx_of(i), b = cy_of(i);
+  const double px = a == 0 ? 1.0 - theta - ux * ux : 0.5 * (theta + ux * ux + (a > 0 ? ux : -ux));
+  const double py = b == 0 ? 1.0 - theta - uy * uy : 0.5 * (theta + uy * uy + (b > 0 ? uy : -uy));
+  return rho * px * py;
 }
 
 // Rest-state value of population i for the shifted forms: rho_ref W(c_ix) W(c_iy).

@@ -416,9 +416,7 @@ __global__ void __launch_bounds__(kNT) init_kernel(const double* __restrict__ rh
     xs = (xs < 0) ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
     ys = (ys < 0) ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
     const long long n = (long long)ys * g.nx + xs;
-    double feq[9];
-    geq_f64(rho[n], ux[n], uy[n], theta, feq);
-    dst[i * g.plane + here] = from_double<S>(feq[i] - rest_value(i, theta, rho_ref));
+    dst[i * g.plane + here] = from_double<S>(geq_one_f64(i, rho[n], ux[n], uy[n], theta) - rest_value(i, theta, rho_ref));
   }
 }
 

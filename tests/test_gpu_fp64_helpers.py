@@ -42,9 +42,9 @@ def test_reciprocal_within_two_ulps():
 
 
 def test_reciprocal_of_bad_densities_is_not_finite():
-    """rho = 0, non-finite rho and rho below FP32's range give a non-finite 1/rho, so the
-    node is counted by the diagnostics."""
-    x = np.array([0.0, -0.0, np.nan, np.inf, -np.inf, 1e-40, -1e-300])
+    """rho = 0, non-finite rho and rho outside [2^-126, 2^126) (a blown-up state) give a
+    non-finite 1/rho, so the node is counted by the diagnostics."""
+    x = np.array([0.0, -0.0, np.nan, np.inf, -np.inf, 1e-40, -1e-300, 2.0 ** 127, -1e38, 1e40, 1e300])
     got = capi.lbm_selftest_fp64(3, x)
     assert not np.any(np.isfinite(got))
 
