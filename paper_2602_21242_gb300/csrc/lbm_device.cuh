@@ -431,13 +431,11 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
   }
 }
 
-// Population i of the guided equilibrium (Eq. 10) in FP64, product form:
-// rho P_x(c_ix) P_y(c_iy); used by lbm_init.
-__device__ __forceinline__ double geq_one_f64(int i, double rho, double ux, double uy, double theta) {
-  const int a = cx_of(i), b = cy_of(i);
-  const double px = a == 0 ? 1.0 - theta - ux * ux : 0.5 * (theta + ux * ux + (a > 0 ? ux : -ux));
-  const double py = b == 0 ? 1.0 - theta - uy * uy : 0.5 * (theta + uy * uy + (b > 0 ? uy : -uy));
-  return rho * px * py;
+// Per-axis factor of the guided equilibrium (Eq. 10) in FP64, for velocity
+// component a in {-1, 0, 1}: 1 - theta - u^2, or (theta + u^2 + a u) / 2; the
+// equilibrium is rho P(c_ix; u_x) P(c_iy; u_y). Used by lbm_init.
+__device__ __forceinline__ double geq_factor(int a, double u, double theta) {
+  return a == 0 ? 1.0 - theta - u * u : 0.5 * (theta + u * u + (a > 0 ? u : -u));
 }
 
 // Rest-state value of population i for the shifted forms: rho_ref W(c_ix) W(c_iy).

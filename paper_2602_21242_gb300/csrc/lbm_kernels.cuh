@@ -401,6 +401,8 @@ __global__ void __launch_bounds__(kNT) diag_kernel(const typename Form<PREC>::S*
 
 // ------------------------------------------------------------------ init, moments, state copies
 // B_i(x) = f^eq_i(rho0(x + c_i), u0(x + c_i)) - rest_i: the buffer whose pull is f^eq(rho0, u0).
+// Written as a push (each element once): node x forms its nine f^eq_i from one
+// set of per-axis factors and stores them at x - c_i.
 template <int PREC>
 __global__ void __launch_bounds__(kNT) init_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
                                                    const double* __restrict__ uy, Geometry g, double theta,
@@ -409,15 +411,15 @@ __global__ void __launch_bounds__(kNT) init_kernel(const double* __restrict__ rh
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  const long long here = (long long)y * g.pitch + x;
+  long long o[9];
+  pull_offsets(x, y, g, o);
+  const long long n = (long long)y * g.nx + x;
+  const double r = rho[n], u = ux[n], v = uy[n];
+  const double px[3] = {geq_factor(-1, u, theta), geq_factor(0, u, theta), geq_factor(1, u, theta)};
+  const double py[3] = {geq_factor(-1, v, theta), geq_factor(0, v, theta), geq_factor(1, v, theta)};
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    int xs = x + cx_of(i), ys = y + cy_of(i);  // node x + c_i, periodic
-    xs = (xs < 0) ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
-    ys = (ys < 0) ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-    const long long n = (long long)ys * g.nx + xs;
-    dst[i * g.plane + here] = from_double<S>(geq_one_f64(i, rho[n], ux[n], uy[n], theta) - rest_value(i, theta, rho_ref));
-  }
+  for (int i = 0; i < 9; ++i)
+    dst[i * g.plane + o[i]] = from_double<S>(r * px[cx_of(i) + 1] * py[cy_of(i) + 1] - rest_value(i, theta, rho_ref));
 }
 
 // (rho, u) of f(x, t) in FP64, unpadded [y][x] output.
