@@ -194,3 +194,17 @@ def test_fused_diagnostics_skip_a_nonfinite_node(oracle, prec, launch):
     assert want[4] == 1 and d[4] == 1
     tol = {"f64": 1e-12, "f64df": 1e-11}.get(prec, 1e-5)
     np.testing.assert_allclose(d[:4], want[:4], rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("prec,n,want", [("f64", 4096, (0, 64, 2, 32)), ("f64df", 4096, (0, 64, 2, 32)),
+                                         ("f32", 4096, (1, 64, 1, 4)), ("f32", 8192, (1, 64, 1, 4)),
+                                         ("f16", 4096, (1, 0, 1, 24)), ("f16", 8192, (1, 0, 1, 48))])
+def test_default_launch_shapes(prec, n, want):
+    """The documented defaults: FP64 and double-float on the column kernel; FP32 on the persistent
+    pipeline with 4-row tiles; FP16 one CTA per tile with the height that fills the last wave of
+    three CTAs per SM on GB300's 152 SMs (24 rows at 4096^2: 3.0 waves; 48 rows at 8192^2: 6.0)."""
+    from paper_2602_21242_gb300 import capi
+    if prec == "f16" and torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("the FP16 tile height depends on the SM count")
+    with Lattice(n, n, 1 / 3, 0.6, "complete", prec) as lat:
+        assert capi.lbm_get_launch_ex(lat.ctx) == want
