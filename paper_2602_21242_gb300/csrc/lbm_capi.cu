@@ -126,6 +126,12 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->buf[1]);
   }
   cudaFree(c->d_partials);
+  cudaFree(c->d_partials2);
+  for (int b = 0; b < 2; ++b) {
+    if (c->ev_step[b]) cudaEventDestroy(c->ev_step[b]);
+    if (c->ev_fin[b]) cudaEventDestroy(c->ev_fin[b]);
+  }
+  if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->d_diag);
   cudaFree(c->d_diag_now);
   cudaFree(c->d_sticky);
@@ -207,6 +213,7 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
     }
   }
   if ((e = cudaMalloc(&c->d_partials, sizeof(double) * 5 * (size_t)c->parts_cap)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_partials2, sizeof(double) * 5 * (size_t)c->parts_cap)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag_now, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess ||
@@ -215,6 +222,15 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
     free_ctx(c);
     cudaGetLastError();
     return fail(nullptr, LBM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+  }
+  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_step[0], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_step[1], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fin[0], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fin[1], cudaEventDisableTiming)) != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, LBM_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
   }
   // Defined contents everywhere, including row and plane padding.
   if ((e = cudaMemsetAsync(c->buf[0], 0, (size_t)bytes, c->stream)) != cudaSuccess ||
@@ -237,6 +253,7 @@ int lbm_create(int nx, int ny, double theta, double tau, int model, lbm_ctx** ou
 int lbm_destroy(lbm_ctx* ctx) {
   if (!ctx) return LBM_OK;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   free_ctx(ctx);
   return LBM_OK;
 }
@@ -336,12 +353,18 @@ int lbm_step(lbm_ctx* ctx, int n) {
   a.sched = ctx->d_sched;
   long long used = ctx->nparts;
   a.parts_used = &used;
+  int joined = -1;  // partials buffer whose final sum was launched last (-1: none in this call)
   for (int k = 0; k < n; ++k) {
     a.diag = ctx->diag_every > 0 && (ctx->t % ctx->diag_every) == 0;
     a.src = ctx->buf[ctx->cur];
     a.dst = ctx->buf[ctx->cur ^ 1];
     used = ctx->nparts;
-    cudaError_t e = launch_step(a, ctx->prec, ctx->stream);
+    const int b = ctx->pbuf;
+    cudaError_t e = cudaSuccess;
+    if (a.diag && ctx->fin_pending[b]) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_fin[b], 0);  // buffer b free
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step event wait");
+    a.partials = b ? ctx->d_partials2 : ctx->d_partials;
+    e = launch_step(a, ctx->prec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step launch");
     if (ctx->n_walls > 0) {
       e = olbm::launch_walls((int)elem_size(ctx->prec), a.src, a.dst, ctx->g, ctx->d_walls, ctx->n_walls,
@@ -349,13 +372,24 @@ int lbm_step(lbm_ctx* ctx, int n) {
       if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step walls launch");
     }
     if (a.diag) {
-      e = olbm::launch_finalize(ctx->d_partials, (int)used, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
-                                ctx->d_sticky, ctx->stream);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step diagnostics launch");
+      // the final sum of this step's partials runs on the side stream, beside the next step
+      if ((e = cudaEventRecord(ctx->ev_step[b], ctx->stream)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(ctx->side, ctx->ev_step[b], 0)) != cudaSuccess ||
+          (e = olbm::launch_finalize(a.partials, (int)used, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
+                                     ctx->d_sticky, ctx->side)) != cudaSuccess ||
+          (e = cudaEventRecord(ctx->ev_fin[b], ctx->side)) != cudaSuccess)
+        return cuda_fail(ctx, e, "lbm_step diagnostics launch");
+      ctx->fin_pending[b] = true;
+      ctx->pbuf ^= 1;
+      joined = b;
       ctx->last_diag_t = ctx->t;
     }
     ctx->cur ^= 1;
     ctx->t += 1;
+  }
+  if (joined >= 0) {  // everything queued on `stream` after this call follows the final sums
+    cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_fin[joined], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step join");
   }
   return LBM_OK;
 }
@@ -517,15 +551,20 @@ int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows) {
   const long long need = olbm::step_blocks(ctx->g, k, ctx->prec);
   if (need > ctx->parts_cap) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->side);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_launch sync");
-    double* p = nullptr;
-    e = cudaMalloc(&p, sizeof(double) * 5 * (size_t)need);
+    double* p[2] = {nullptr, nullptr};
+    e = cudaMalloc(&p[0], sizeof(double) * 5 * (size_t)need);
+    if (e == cudaSuccess) e = cudaMalloc(&p[1], sizeof(double) * 5 * (size_t)need);
     if (e != cudaSuccess) {
+      cudaFree(p[0]);
       cudaGetLastError();
       return fail(ctx, LBM_ENOMEM, "lbm_set_launch: %s", cudaGetErrorString(e));
     }
     cudaFree(ctx->d_partials);
-    ctx->d_partials = p;
+    cudaFree(ctx->d_partials2);
+    ctx->d_partials = p[0];
+    ctx->d_partials2 = p[1];
     ctx->parts_cap = need;
   }
   ctx->cfg = k;

@@ -20,7 +20,16 @@ struct lbm_ctx {
   olbm::LaunchCfg cfg{};
   double* d_partials = nullptr;
   long long nparts = 0;      // partials the step kernel writes under cfg
-  long long parts_cap = 0;   // partials allocated
+  long long parts_cap = 0;   // partials allocated (each of the two buffers)
+  // Fused diagnostics: consecutive diagnosed steps alternate between two partials
+  // buffers, and the final sum of step t runs on a second stream while step t + 1
+  // runs; lbm_step joins that stream back into `stream` before it returns.
+  double* d_partials2 = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_step[2] = {nullptr, nullptr};  // partials of buffer b written (on `stream`)
+  cudaEvent_t ev_fin[2] = {nullptr, nullptr};   // partials of buffer b summed (on `side`)
+  bool fin_pending[2] = {false, false};
+  int pbuf = 0;  // partials buffer of the next diagnosed step
   double* d_diag = nullptr;      // [6] latest fused diagnostics (out5 + time)
   double* d_diag_now = nullptr;  // [6] scratch of lbm_diagnostics
   unsigned long long* d_sticky = nullptr;
