@@ -136,6 +136,10 @@ int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double
  * Asynchronous. If a diagnostics interval M > 0 is set, every step whose start
  * time t is a multiple of M also reduces the diagnostics of f(x, t) (see
  * lbm_diagnostics) on the device; lbm_sync / lbm_step_diagnostics report them.
+ * The final sums of those reductions run on a second stream that the context
+ * owns, beside the following steps; before returning, the call makes the
+ * context's stream wait for them, so work queued on that stream afterwards sees
+ * every result of the call.
  * Errors: LBM_ESTATE before lbm_init or lbm_set_state; LBM_EINVAL for n < 0.
  */
 int lbm_step(lbm_ctx* ctx, int n);
