@@ -72,6 +72,12 @@ struct lbm_batch {
   double rho_ref = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;  // private non-blocking stream used only for graph capture
+  // Fused diagnostics in graph mode: diagnosed steps alternate between two partials
+  // buffers and each step's final sum is a branch of the graph (captured from a
+  // second stream) beside the following step.
+  cudaStream_t capture_side = nullptr;
+  cudaEvent_t ev_step[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fin[2] = {nullptr, nullptr};
   std::vector<olbm::Geometry> geo;
   std::vector<double> theta, tau;
   std::vector<long long> node0;  // offset of each domain in packed field arrays
@@ -85,6 +91,7 @@ struct lbm_batch {
   long long* d_nodes = nullptr;
   int ntiles = 0;
   double* d_partials = nullptr;
+  double* d_partials2 = nullptr;  // second buffer of the graph mode's fused diagnostics
   double* d_diag = nullptr;  // n * 5, latest fused diagnostics
   double* d_diag_now = nullptr;
   unsigned long long* d_sticky = nullptr;
@@ -164,13 +171,16 @@ int build_tiles(lbm_batch* b) {
   cudaFree(b->d_tiles);
   cudaFree(b->d_ranges);
   cudaFree(b->d_partials);
+  cudaFree(b->d_partials2);
   b->d_tiles = nullptr;
   b->d_ranges = nullptr;
   b->d_partials = nullptr;
+  b->d_partials2 = nullptr;
   b->ntiles = (int)tiles.size();
   if ((e = cudaMalloc(&b->d_tiles, sizeof(int4) * tiles.size())) != cudaSuccess ||
       (e = cudaMalloc(&b->d_ranges, sizeof(int2) * ranges.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_partials, sizeof(double) * 5 * tiles.size())) != cudaSuccess)
+      (e = cudaMalloc(&b->d_partials, sizeof(double) * 5 * tiles.size())) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_partials2, sizeof(double) * 5 * tiles.size())) != cudaSuccess)
     return bcuda(b, e, "lbm_batch tile allocation");
   if ((e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(b->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice)) !=
@@ -187,12 +197,18 @@ void free_batch(lbm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->capture_side) cudaStreamDestroy(b->capture_side);
+  for (int k = 0; k < 2; ++k) {
+    if (b->ev_step[k]) cudaEventDestroy(b->ev_step[k]);
+    if (b->ev_fin[k]) cudaEventDestroy(b->ev_fin[k]);
+  }
   cudaFree(b->arena);
   cudaFree(b->d_desc);
   cudaFree(b->d_tiles);
   cudaFree(b->d_ranges);
   cudaFree(b->d_nodes);
   cudaFree(b->d_partials);
+  cudaFree(b->d_partials2);
   cudaFree(b->d_diag);
   cudaFree(b->d_diag_now);
   cudaFree(b->d_sticky);
@@ -234,11 +250,13 @@ cudaError_t prepare_launch(const lbm_batch* b) {
   }
 }
 
-cudaError_t launch_one_step(const lbm_batch* b, bool diag, int parity, cudaStream_t st) {
+cudaError_t launch_one_step(const lbm_batch* b, bool diag, int parity, cudaStream_t st, double* partials) {
+  olbm::BatchLaunch v = view(b);
+  v.partials = partials;
   switch (b->prec) {
-    case LBM_F64: return olbm::batch_step_f64(view(b), diag, parity, st);
-    case LBM_F32_SHIFT: return olbm::batch_step_f32(view(b), diag, parity, st);
-    default: return olbm::batch_step_f16(view(b), diag, parity, st);
+    case LBM_F64: return olbm::batch_step_f64(v, diag, parity, st);
+    case LBM_F32_SHIFT: return olbm::batch_step_f32(v, diag, parity, st);
+    default: return olbm::batch_step_f16(v, diag, parity, st);
   }
 }
 
@@ -258,8 +276,9 @@ cudaError_t launch_diag(const lbm_batch* b, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_finalize(const lbm_batch* b, double* out, unsigned long long* sticky, cudaStream_t st) {
-  olbm::batch_finalize_kernel<<<b->n, 256, 0, st>>>(b->d_partials, b->d_ranges, b->d_nodes, b->rho_ref, out, sticky);
+cudaError_t launch_finalize(const lbm_batch* b, const double* partials, double* out, unsigned long long* sticky,
+                            cudaStream_t st) {
+  olbm::batch_finalize_kernel<<<b->n, 256, 0, st>>>(partials, b->d_ranges, b->d_nodes, b->rho_ref, out, sticky);
   return cudaGetLastError();
 }
 
@@ -338,6 +357,11 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
   if (e == cudaSuccess) e = cudaMemset(b->d_perr, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_diag, 0, sizeof(double) * 5 * n);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_side, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&b->ev_step[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fin[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     free_batch(b);
     return bfail(nullptr, LBM_ECUDA, "lbm_batch_create: %s", cudaGetErrorString(e));
@@ -538,12 +562,25 @@ int lbm_batch_step(lbm_batch* b, int n) {
     e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step capture");
     cudaError_t le = cudaSuccess;
+    bool pending[2] = {false, false};
+    int pb = 0, last = -1;
     for (int k = 0; k < n && le == cudaSuccess; ++k) {
       const long long tk = b->t + k;
       const bool diag = b->diag_every > 0 && (tk % b->diag_every) == 0;
-      le = launch_one_step(b, diag, (int)((b->cur + k) & 1), b->capture);
-      if (le == cudaSuccess && diag) le = launch_finalize(b, b->d_diag, b->d_sticky, b->capture);
+      double* parts = pb ? b->d_partials2 : b->d_partials;
+      if (diag && pending[pb]) le = cudaStreamWaitEvent(b->capture, b->ev_fin[pb], 0);  // buffer free again
+      if (le == cudaSuccess) le = launch_one_step(b, diag, (int)((b->cur + k) & 1), b->capture, parts);
+      if (le == cudaSuccess && diag) {
+        le = cudaEventRecord(b->ev_step[pb], b->capture);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(b->capture_side, b->ev_step[pb], 0);
+        if (le == cudaSuccess) le = launch_finalize(b, parts, b->d_diag, b->d_sticky, b->capture_side);
+        if (le == cudaSuccess) le = cudaEventRecord(b->ev_fin[pb], b->capture_side);
+        pending[pb] = true;
+        last = pb;
+        pb ^= 1;
+      }
     }
+    if (le == cudaSuccess && last >= 0) le = cudaStreamWaitEvent(b->capture, b->ev_fin[last], 0);  // join
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -592,7 +629,7 @@ int lbm_batch_diagnostics(lbm_batch* b, double* h_out) {
   if (!h_out) return bfail(b, LBM_EINVAL, "lbm_batch_diagnostics: NULL output");
   if (!b->initialised) return bfail(b, LBM_ESTATE, "lbm_batch_diagnostics before lbm_batch_init");
   cudaError_t e = launch_diag(b, b->stream);
-  if (e == cudaSuccess) e = launch_finalize(b, b->d_diag_now, nullptr, b->stream);
+  if (e == cudaSuccess) e = launch_finalize(b, b->d_partials, b->d_diag_now, nullptr, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_out, b->d_diag_now, sizeof(double) * 5 * b->n, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
