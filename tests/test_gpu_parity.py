@@ -336,3 +336,40 @@ def test_fp64_pipeline_rejects_persistent_grid():
         with pytest.raises(capi.LBMError) as e:
             capi.lbm_set_launch_ex(lat.ctx, 1, 2, 0, 8)
         assert e.value.status == capi.LBM_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_largest_lattice_sampled_parity(oracle, prec):
+    """A 16384^2 lattice: each population buffer holds 2.4e9 elements (plane offsets beyond 2^31),
+    stepped with the default launch of the form; 512 sampled nodes over one step against the
+    oracle's collision (FP64 at 1e-13 relative; FP16 within its storage rounding as above)."""
+    n, theta = 16384, 1.0 / 3.0
+    tau = oracle.tau_from_nu(0.005, theta)
+    rho, ux, uy = flows.shear_wave(n, n, U=0.1, amp=0.01)
+    with Lattice(n, n, theta, tau, "complete", prec) as lat:
+        assert 9 * lat.nx * lat.ny > 2 ** 31
+        lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+        del rho, ux, uy
+        lat.set_diagnostics_interval(1)
+        lat.step(2)
+        d, t, status = lat.step_diagnostics()
+        assert t == 1 and status == capi.LBM_OK and d[4] == 0
+        assert d[0] == pytest.approx(n * n, rel=1e-12 if prec == "f64" else 1e-5)
+        if prec == "f64":
+            _one_step_sample_check(oracle, lat, theta, tau, 3, 512, 99, 1e-13)
+            return
+        theta_w = (1 - theta, theta / 2)
+        rest = np.array([theta_w[0], theta_w[1], theta_w[0], theta_w[1], theta_w[0]] + [theta_w[1]] * 4) * \
+            np.array([theta_w[0], theta_w[0], theta_w[1], theta_w[0], theta_w[1]] + [theta_w[1]] * 4)
+        g = flows.rng(98)
+        xs = torch.from_numpy(g.integers(0, n, 512)).cuda()
+        ys = torch.from_numpy(g.integers(0, n, 512)).cuda()
+        pre = lat.state()[:, ys, xs].cpu().numpy().T
+        lat.step(1)
+        cx, cy = torch.tensor(CX).cuda(), torch.tensor(CY).cuda()
+        post = lat.state()[torch.arange(9).cuda()[None, :], (ys[:, None] + cy[None, :]) % n,
+                           (xs[:, None] + cx[None, :]) % n].cpu().numpy()
+    for j in range(512):
+        want = oracle.collide_node(pre[j], theta, tau, 3)
+        dev = max(np.abs(pre[j] - rest).max(), np.abs(want - rest).max())
+        assert np.abs(post[j] - want).max() <= 1.5 * 2.0 ** -11 * dev, f"node {j}"
