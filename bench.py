@@ -482,7 +482,7 @@ def vjp_sweep(dev, stream, n=1024, steps=500, ckpt=50):
                 "forward_ms": round(fwd_ms, 2), "backward_ms": round(bwd_ms, 2), "loss": float(loss.detach()),
                 "gradient_mlups": round(n * n * steps / ((fwd_ms + bwd_ms) * 1e-3) / 1e6, 1),
                 "steps": steps, "ckpt_every": ckpt,
-                "note": "backward = forward recompute with checkpoints + segment recomputes + adjoint steps"}
+                "note": "forward = lbm_vjp_forward (checkpoints kept); backward = segment recomputes + adjoint steps"}
     den = sum(float((b ** 2).sum()) for b in grads["f64"])
     for prec in ("f64df", "f32"):
         num = sum(float(((a - b) ** 2).sum()) for a, b in zip(grads[prec], grads["f64"]))

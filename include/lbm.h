@@ -209,6 +209,32 @@ int lbm_vjp(lbm_ctx* ctx, int n, int ckpt_every, const double* d_rho0, const dou
             const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
             double* g_rho0, double* g_ux0, double* g_uy0);
 
+/*
+ * The forward pass of lbm_vjp on its own (no counterpart in the paper): lbm_init
+ * from d_rho0, d_ux0, d_uy0 (device, nx * ny doubles), then n steps, keeping the
+ * checkpoints (every ckpt_every steps) and the states of the last segment in the
+ * lattice's work memory; the lattice then holds f(x, n), as after lbm_init +
+ * lbm_step(n) without fused diagnostics. A following lbm_vjp_ex with flag
+ * LBM_VJP_REUSE_FORWARD and the same n and ckpt_every skips its own forward pass,
+ * as long as no call changed the lattice in between (lbm_init, lbm_set_state,
+ * lbm_step, lbm_set_walls, lbm_vjp*). Errors and forms as lbm_vjp. Asynchronous.
+ */
+int lbm_vjp_forward(lbm_ctx* ctx, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+                    const double* d_uy0);
+
+#define LBM_VJP_REUSE_FORWARD 1
+
+/*
+ * lbm_vjp with flags: 0 is lbm_vjp; LBM_VJP_REUSE_FORWARD uses the checkpoints of
+ * the preceding lbm_vjp_forward (d_rho0, d_ux0, d_uy0 must be the fields it ran
+ * from: the derivative through Eq. 10 is taken at them) and returns LBM_ESTATE,
+ * with nothing done, when they no longer describe the lattice. LBM_EINVAL for
+ * other flags.
+ */
+int lbm_vjp_ex(lbm_ctx* ctx, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+               const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
+               double* g_rho0, double* g_ux0, double* g_uy0, int flags);
+
 /* Current time t (steps since lbm_init / lbm_set_state). */
 int lbm_time(const lbm_ctx* ctx, long long* h_t);
 

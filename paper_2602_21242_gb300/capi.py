@@ -53,6 +53,8 @@ _SIGNATURES = {
     "lbm_selftest_timeout": ([_i, _pd], _i),
     "lbm_selftest_fp64": ([_i, _pd, _ll, _pd], _i),
     "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
+    "lbm_vjp_forward": ([_p, _i, _i, _p, _p, _p], _i),
+    "lbm_vjp_ex": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i], _i),
     "lbm_set_launch": ([_p, _i, _i, _i], _i),
     "lbm_set_launch_ex": ([_p, _i, _i, _i, _i], _i),
     "lbm_get_launch_ex": ([_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
@@ -362,6 +364,21 @@ def lbm_vjp(ctx, n: int, ckpt_every: int, d_rho0: int, d_ux0: int, d_uy0: int, g
     """Cotangents of (rho0, u0) for cotangents of the moments after n steps (device pointers, 0 = NULL)."""
     check(load().lbm_vjp(ctx, n, ckpt_every, d_rho0, d_ux0, d_uy0, g_rho or None, g_ux or None, g_uy or None,
                          g_rho0 or None, g_ux0 or None, g_uy0 or None), ctx)
+
+
+LBM_VJP_REUSE_FORWARD = 1
+
+
+def lbm_vjp_forward(ctx, n: int, ckpt_every: int, d_rho0: int, d_ux0: int, d_uy0: int) -> None:
+    """Forward pass of lbm_vjp on its own: init from (rho0, u0) and n checkpointed steps."""
+    check(load().lbm_vjp_forward(ctx, n, ckpt_every, d_rho0, d_ux0, d_uy0), ctx)
+
+
+def lbm_vjp_ex(ctx, n: int, ckpt_every: int, d_rho0: int, d_ux0: int, d_uy0: int, g_rho: int = 0, g_ux: int = 0,
+               g_uy: int = 0, g_rho0: int = 0, g_ux0: int = 0, g_uy0: int = 0, flags: int = 0) -> None:
+    """lbm_vjp with flags (LBM_VJP_REUSE_FORWARD: reuse the checkpoints of lbm_vjp_forward)."""
+    check(load().lbm_vjp_ex(ctx, n, ckpt_every, d_rho0, d_ux0, d_uy0, g_rho or None, g_ux or None, g_uy or None,
+                            g_rho0 or None, g_ux0 or None, g_uy0 or None, flags), ctx)
 
 
 def lbm_set_launch_ex(ctx, kind: int, bx: int, by: int, rows: int) -> None:

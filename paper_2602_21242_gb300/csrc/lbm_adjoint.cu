@@ -214,66 +214,133 @@ cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
 
 }  // namespace
 
-extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
-                       const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
-                       double* g_rho0, double* g_ux0, double* g_uy0) {
-  if (!c) return LBM_EINVAL;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
-    return vfail(c, LBM_EINVAL, "lbm_vjp: the current CUDA device is not the lattice's device");
-  if (n < 0 || ckpt_every < 1) return vfail(c, LBM_EINVAL, "lbm_vjp: need n >= 0 and ckpt_every >= 1");
-  if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp: NULL initial field");
-  if (c->prec == LBM_F16_SHIFT)
-    return vfail(c, LBM_EINVAL, "lbm_vjp: storage forms LBM_F64, LBM_F64_DF and LBM_F32_SHIFT only");
-  const int K = std::min(ckpt_every, std::max(n, 1));
-  const int nseg = (n + K - 1) / K;
-  const size_t sb = (size_t)c->state_bytes;  // one state, and one adjoint field in the same layout
-  const size_t need = sb * ((size_t)nseg + (size_t)K + 2);
+namespace {
+
+// Work memory of lbm_vjp for n steps in segments of K: ceil(n / K) checkpoints,
+// a ring of K recomputed states, two adjoint fields.
+struct VjpLayout {
+  int K = 1, nseg = 0;
+  size_t sb = 0;
+  char* base = nullptr;
+  void* ckpt(int s) const { return base + sb * (size_t)s; }
+  void* ring(int j) const { return base + sb * ((size_t)nseg + (size_t)j); }
+  void* lam(int k) const { return base + sb * ((size_t)nseg + (size_t)K + (size_t)k); }
+};
+
+int vjp_layout(lbm_ctx* c, int n, int ckpt_every, VjpLayout& L) {
+  L.K = std::min(ckpt_every, std::max(n, 1));
+  L.nseg = (n + L.K - 1) / L.K;
+  L.sb = (size_t)c->state_bytes;  // one state, and one adjoint field in the same layout
+  const size_t need = L.sb * ((size_t)L.nseg + (size_t)L.K + 2);
   cudaError_t e;
   if (need > c->vjp_bytes) {
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp sync", e);
     cudaFree(c->d_vjp);
     c->d_vjp = nullptr;
     c->vjp_bytes = 0;
+    c->vjp_gen = -1;
     if ((e = cudaMalloc(&c->d_vjp, need)) != cudaSuccess) {
       cudaGetLastError();
       return vfail(c, LBM_ENOMEM, "lbm_vjp work memory", e);
     }
     c->vjp_bytes = need;
   }
-  char* base = static_cast<char*>(c->d_vjp);
-  auto ckpt = [&](int s) { return base + sb * (size_t)s; };
-  auto ring = [&](int j) { return base + sb * ((size_t)nseg + (size_t)j); };
-  void* lam[2] = {base + sb * ((size_t)nseg + K), base + sb * ((size_t)nseg + K + 1)};
+  L.base = static_cast<char*>(c->d_vjp);
+  return LBM_OK;
+}
 
-  // forward: init, then n steps with a checkpoint at the start of every segment
+// Forward pass: init, then n steps with a checkpoint at the start of every
+// segment; the last segment's states go straight to the ring (the backward pass
+// does not recompute them). The lattice ends holding f(x, n).
+int vjp_forward(lbm_ctx* c, int n, const VjpLayout& L, const double* d_rho0, const double* d_ux0,
+                const double* d_uy0) {
   int s = lbm_init(c, d_rho0, d_ux0, d_uy0);
   if (s != LBM_OK) return s;
-  for (int seg = 0; seg < nseg; ++seg) {
-    if ((e = cudaMemcpyAsync(ckpt(seg), c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+  cudaError_t e;
+  for (int seg = 0; seg < L.nseg; ++seg) {
+    if ((e = cudaMemcpyAsync(L.ckpt(seg), c->buf[c->cur], L.sb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
       return vfail(c, LBM_ECUDA, "lbm_vjp checkpoint", e);
-    const int len = std::min(K, n - seg * K);
+    const int len = std::min(L.K, n - seg * L.K);
+    const bool last = seg == L.nseg - 1;
     for (int k = 0; k < len; ++k) {
-      if ((e = fwd_step(c, c->buf[c->cur], c->buf[c->cur ^ 1])) != cudaSuccess)
-        return vfail(c, LBM_ECUDA, "lbm_vjp forward", e);
-      c->cur ^= 1;
+      const void* src = (last && k > 0) ? L.ring(k) : c->buf[c->cur];
+      void* dst = (last && k + 1 < len) ? L.ring(k + 1) : c->buf[c->cur ^ 1];
+      if ((e = fwd_step(c, src, dst)) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp forward", e);
+      if (!last || k + 1 == len) c->cur ^= 1;
       c->t += 1;
     }
   }
+  c->vjp_gen = c->state_gen;
+  c->vjp_n = n;
+  c->vjp_k = L.K;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_vjp_forward(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+                               const double* d_uy0) {
+  if (!c) return LBM_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return vfail(c, LBM_EINVAL, "lbm_vjp_forward: the current CUDA device is not the lattice's device");
+  if (n < 0 || ckpt_every < 1) return vfail(c, LBM_EINVAL, "lbm_vjp_forward: need n >= 0 and ckpt_every >= 1");
+  if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp_forward: NULL initial field");
+  if (c->prec == LBM_F16_SHIFT)
+    return vfail(c, LBM_EINVAL, "lbm_vjp_forward: storage forms LBM_F64, LBM_F64_DF and LBM_F32_SHIFT only");
+  VjpLayout L;
+  int s = vjp_layout(c, n, ckpt_every, L);
+  if (s != LBM_OK) return s;
+  return vjp_forward(c, n, L, d_rho0, d_ux0, d_uy0);
+}
+
+extern "C" int lbm_vjp_ex(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+                          const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
+                          double* g_rho0, double* g_ux0, double* g_uy0, int flags) {
+  if (!c) return LBM_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return vfail(c, LBM_EINVAL, "lbm_vjp: the current CUDA device is not the lattice's device");
+  if (n < 0 || ckpt_every < 1) return vfail(c, LBM_EINVAL, "lbm_vjp: need n >= 0 and ckpt_every >= 1");
+  if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp: NULL initial field");
+  if (flags & ~LBM_VJP_REUSE_FORWARD) return vfail(c, LBM_EINVAL, "lbm_vjp_ex: unknown flags");
+  if (c->prec == LBM_F16_SHIFT)
+    return vfail(c, LBM_EINVAL, "lbm_vjp: storage forms LBM_F64, LBM_F64_DF and LBM_F32_SHIFT only");
+  VjpLayout L;
+  int s;
+  if (flags & LBM_VJP_REUSE_FORWARD) {
+    const int K = std::min(ckpt_every, std::max(n, 1));
+    if (c->vjp_gen != c->state_gen || c->vjp_n != n || c->vjp_k != K)
+      return vfail(c, LBM_ESTATE, "lbm_vjp_ex: no forward pass of lbm_vjp_forward with these n and ckpt_every "
+                                  "describes the lattice (it changed since, or none was run)");
+    L.K = K;
+    L.nseg = (n + K - 1) / K;
+    L.sb = (size_t)c->state_bytes;
+    L.base = static_cast<char*>(c->d_vjp);
+  } else {
+    if ((s = vjp_layout(c, n, ckpt_every, L)) != LBM_OK) return s;
+    if ((s = vjp_forward(c, n, L, d_rho0, d_ux0, d_uy0)) != LBM_OK) return s;
+  }
+  cudaError_t e;
+  c->vjp_gen = -1;  // the backward pass overwrites the ring of the last segment
   // seed lambda(n)
+  void* lam[2] = {L.lam(0), L.lam(1)};
   int li = 0;
   e = adj_seed(c, g_rho, g_ux, g_uy, lam[li]);
   if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp seed", e);
-  // backward over segments: recompute the segment's states, then reverse them
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int len = std::min(K, n - seg * K);
-    const void* prev = ckpt(seg);
-    for (int j = 1; j < len; ++j) {
-      if ((e = fwd_step(c, prev, ring(j))) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp recompute", e);
-      prev = ring(j);
+  // backward over segments: recompute the segment's states (the last one is still in
+  // the ring from the forward pass), then reverse them
+  for (int seg = L.nseg - 1; seg >= 0; --seg) {
+    const int len = std::min(L.K, n - seg * L.K);
+    if (seg < L.nseg - 1) {
+      const void* prev = L.ckpt(seg);
+      for (int j = 1; j < len; ++j) {
+        if ((e = fwd_step(c, prev, L.ring(j))) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp recompute", e);
+        prev = L.ring(j);
+      }
     }
     for (int j = len - 1; j >= 0; --j) {
-      const void* fbuf = j == 0 ? ckpt(seg) : ring(j);
+      const void* fbuf = j == 0 ? L.ckpt(seg) : L.ring(j);
       e = adj_step(c, fbuf, lam[li], lam[li ^ 1]);
       if (e == cudaSuccess && c->n_walls > 0)
         e = olbm::launch_walls_adjoint(elem_bytes(c), lam[li], lam[li ^ 1], c->g, c->d_walls, c->n_walls, c->stream);
@@ -285,4 +352,10 @@ extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, 
   e = adj_final(c, lam[li], d_rho0, d_ux0, d_uy0, g_rho0, g_ux0, g_uy0);
   if (e != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp final", e);
   return LBM_OK;
+}
+
+extern "C" int lbm_vjp(lbm_ctx* c, int n, int ckpt_every, const double* d_rho0, const double* d_ux0,
+                       const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
+                       double* g_rho0, double* g_ux0, double* g_uy0) {
+  return lbm_vjp_ex(c, n, ckpt_every, d_rho0, d_ux0, d_uy0, g_rho, g_ux, g_uy, g_rho0, g_ux0, g_uy0, 0);
 }

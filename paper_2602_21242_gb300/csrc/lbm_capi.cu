@@ -282,12 +282,14 @@ int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double
   ctx->initialised = true;
   ctx->t = 0;
   ctx->last_diag_t = -1;
+  ++ctx->state_gen;
   return LBM_OK;
 }
 
 int lbm_set_walls(lbm_ctx* ctx, const unsigned char* h_mask, long long* h_count) {
   int s = check_ctx(ctx);
   if (s != LBM_OK) return s;
+  ++ctx->state_gen;
   const long long nodes = nodes_of(ctx);
   long long n = 0;
   int2* list = nullptr;
@@ -341,6 +343,7 @@ int lbm_step(lbm_ctx* ctx, int n) {
   if (s != LBM_OK) return s;
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n must be >= 0");
   if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_step before lbm_init / lbm_set_state");
+  if (n > 0) ++ctx->state_gen;
   olbm::StepArgs a;
   a.model = ctx->model;
   a.g = ctx->g;
@@ -481,6 +484,7 @@ int lbm_set_state(lbm_ctx* ctx, const double* d_f) {
   ctx->initialised = true;
   ctx->t = 0;
   ctx->last_diag_t = -1;
+  ++ctx->state_gen;
   return LBM_OK;
 }
 

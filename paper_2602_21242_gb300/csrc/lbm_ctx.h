@@ -42,6 +42,12 @@ struct lbm_ctx {
   // lbm_vjp work memory: checkpoints, recompute ring, adjoint fields (grown on demand)
   void* d_vjp = nullptr;
   size_t vjp_bytes = 0;
+  // Count of calls that changed the state or the dynamics (init, set_state, step,
+  // walls); the forward pass of lbm_vjp_forward records it with its (n, ckpt_every)
+  // so that lbm_vjp_ex can tell whether its checkpoints still describe the lattice.
+  long long state_gen = 0;
+  long long vjp_gen = -1;
+  int vjp_n = -1, vjp_k = -1;
   // fullway bounce-back wall nodes (x, y), applied after every step (lbm_set_walls)
   int2* d_walls = nullptr;
   long long n_walls = 0;

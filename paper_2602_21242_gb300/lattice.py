@@ -151,8 +151,12 @@ class _Run(torch.autograd.Function):
     def forward(fctx, rho0, ux0, uy0, lattice, n, ckpt_every):
         shape = (lattice.ny, lattice.nx)
         r0, u0, v0 = (_dev_f64(t.detach(), shape, nm) for t, nm in ((rho0, "rho0"), (ux0, "ux0"), (uy0, "uy0")))
-        lattice.init(r0, u0, v0)
-        lattice.step(n)
+        if lattice.prec == capi.LBM_F16_SHIFT:  # no adjoint for this form: a plain run
+            lattice.init(r0, u0, v0)
+            lattice.step(n)
+        else:  # the adjoint's forward pass, whose checkpoints the backward pass reuses
+            with torch.cuda.device(lattice.device):
+                capi.lbm_vjp_forward(lattice.ctx, n, ckpt_every, r0.data_ptr(), u0.data_ptr(), v0.data_ptr())
         rho, ux, uy = lattice.moments()
         fctx.save_for_backward(r0, u0, v0)
         fctx.lattice, fctx.n, fctx.k = lattice, n, ckpt_every
@@ -164,10 +168,15 @@ class _Run(torch.autograd.Function):
         lat = fctx.lattice
         grads = [torch.empty_like(r0) for _ in range(3)]
         gs = [g.contiguous().to(torch.float64) if g is not None else None for g in (g_rho, g_ux, g_uy)]
+        args = (lat.ctx, fctx.n, fctx.k, r0.data_ptr(), u0.data_ptr(), v0.data_ptr(),
+                *[g.data_ptr() if g is not None else 0 for g in gs], *[g.data_ptr() for g in grads])
         with torch.cuda.device(lat.device):
-            capi.lbm_vjp(lat.ctx, fctx.n, fctx.k, r0.data_ptr(), u0.data_ptr(), v0.data_ptr(),
-                         *[g.data_ptr() if g is not None else 0 for g in gs],
-                         *[g.data_ptr() for g in grads])
+            try:  # the forward pass's checkpoints, unless the lattice changed since
+                capi.lbm_vjp_ex(*args, flags=capi.LBM_VJP_REUSE_FORWARD)
+            except capi.LBMError as e:
+                if e.status != capi.LBM_ESTATE:
+                    raise
+                capi.lbm_vjp(*args)
             lat.stream.synchronize()
         return grads[0], grads[1], grads[2], None, None, None
 

@@ -134,3 +134,44 @@ def test_autograd_function_uses_the_adjoint(oracle):
     r = oracle.moments_cplx(f)[0]
     want = (0.5 * (r - ref_rho) ** 2).sum().imag / h
     assert dot(grads, v) == pytest.approx(want, rel=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64df", "f32"])
+@pytest.mark.parametrize("n_steps,k", [(23, 5), (20, 5), (7, 50)])
+def test_vjp_reusing_the_forward_pass(prec, n_steps, k):
+    """lbm_vjp_forward + lbm_vjp_ex(LBM_VJP_REUSE_FORWARD) gives the same cotangents as lbm_vjp
+    (bit for bit: the same states, the same adjoint steps), leaves the same final state, and is
+    refused (LBM_ESTATE, nothing done) once the lattice changed after the forward pass."""
+    n, theta, tau, model = 24, 1 / 3, 0.6, 3
+    fields, _, w = problem(n, 7, theta)
+    dev = [torch.from_numpy(a).cuda() for a in fields]
+    gw = [torch.from_numpy(a).cuda() for a in w]
+    ptrs = [t.data_ptr() for t in dev] + [t.data_ptr() for t in gw]
+    ref = [torch.empty_like(dev[0]) for _ in range(3)]
+    got = [torch.empty_like(dev[0]) for _ in range(3)]
+    with Lattice(n, n, theta, tau, model, prec) as lat:
+        capi.lbm_vjp(lat.ctx, n_steps, k, *ptrs, *[t.data_ptr() for t in ref])
+        state_ref = lat.state().cpu().numpy()
+        capi.lbm_vjp_forward(lat.ctx, n_steps, k, *ptrs[:3])
+        np.testing.assert_array_equal(lat.state().cpu().numpy(), state_ref)
+        capi.lbm_vjp_ex(lat.ctx, n_steps, k, *ptrs, *[t.data_ptr() for t in got], flags=capi.LBM_VJP_REUSE_FORWARD)
+        lat.sync()
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+        # the backward pass consumed the forward pass; another call, or a changed lattice, is refused
+        for change in (None, "step"):
+            if change == "step":
+                capi.lbm_vjp_forward(lat.ctx, n_steps, k, *ptrs[:3])
+                lat.step(1)
+            with pytest.raises(capi.LBMError) as e:
+                capi.lbm_vjp_ex(lat.ctx, n_steps, k, *ptrs, *[t.data_ptr() for t in got],
+                                flags=capi.LBM_VJP_REUSE_FORWARD)
+            assert e.value.status == capi.LBM_ESTATE
+        capi.lbm_vjp_forward(lat.ctx, n_steps, k, *ptrs[:3])
+        with pytest.raises(capi.LBMError) as e:  # other n
+            capi.lbm_vjp_ex(lat.ctx, n_steps + 1, k, *ptrs, *[t.data_ptr() for t in got],
+                            flags=capi.LBM_VJP_REUSE_FORWARD)
+        assert e.value.status == capi.LBM_ESTATE
+        with pytest.raises(capi.LBMError) as e:
+            capi.lbm_vjp_ex(lat.ctx, n_steps, k, *ptrs, *[t.data_ptr() for t in got], flags=2)
+        assert e.value.status == capi.LBM_EINVAL
