@@ -334,9 +334,11 @@ int lbm_batch_moments(lbm_batch* b, double* d_rho, double* d_ux, double* d_uy);
 /*
  * Advance every domain by n steps. LBM_BATCH_GRAPH: asynchronous; the n launches
  * are captured once into a graph (re-captured when n, the buffer parity or the
- * diagnostics phase changes) and replayed. LBM_BATCH_PERSISTENT: one cooperative
- * launch; synchronises and returns LBM_ETIMEOUT if a grid barrier waited longer
- * than about a second (the state is then undefined).
+ * diagnostics phase changes) and replayed; each diagnosed step's final sum is a
+ * parallel branch of the graph. LBM_BATCH_PERSISTENT: one cooperative launch,
+ * without fused diagnostics (lbm_batch_diagnostics reduces the state after it);
+ * synchronises and returns LBM_ETIMEOUT if a grid barrier waited longer than
+ * about a second (the state is then undefined).
  */
 int lbm_batch_step(lbm_batch* b, int n);
 /* Latest fused diagnostics, h_out[5 * k + j] as lbm_diagnostics for domain k; *h_time
