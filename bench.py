@@ -34,12 +34,12 @@ BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "f64df": 144}
 # Algorithmic FP64 operations per node of one fused step (each add, mul or FMA of
 # the product-form collision is one operation): 33 shared (moments 16, 1/rho 3,
 # u 2, u^2 2, u/2 2, P 8), the model part (LBGK 22, OReg 56, partial 66,
-# complete 89; complete with the Eq. 12 prefactor from f^neq 83) and the fused
-# diagnostics (5: three sums and j.u by two FMAs). The FP64 form is bound by the
-# FP64 pipe on GB300; the kernel issues fewer of them to it (exact power-of-two
-# scalings run on the integer pipe: 120 of the complete model's 127), and the
-# count stays the method's.
-FP64_OPS_PER_NODE = {"lbgk": 60, "oreg": 94, "partial": 104, "complete": 127, "complete_neq": 121}
+# complete 86, the mu sum and Pi~ sharing u^2 - 1; complete with the Eq. 12
+# prefactor from f^neq 83) and the fused diagnostics (5: three sums and j.u by
+# two FMAs). The FP64 form is bound by the FP64 pipe on GB300; the kernel issues
+# fewer of them to it (exact power-of-two scalings run on the integer pipe: 117
+# of the complete model's 124), and the count stays the method's.
+FP64_OPS_PER_NODE = {"lbgk": 60, "oreg": 94, "partial": 104, "complete": 124, "complete_neq": 121}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch from the ncu capture of
 # the current kernels (profiles/step_kernel_f64_complete_2048.md at 2048^2, scaled to

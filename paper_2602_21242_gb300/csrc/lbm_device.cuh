@@ -131,6 +131,7 @@ template <typename T> struct Coef {
   T mq_inv2t2;    // -1 / (8 theta^2)
   T q_inv2t2;     // 1 / (8 theta^2)
   T ntt;          // -theta (1 - 3 theta)
+  T tt2;          // 2 theta (1 - theta)
   T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
   T w[3];         // rho_ref * rest weights per axis pair are W(a) W(b); W(-1) = W(1) = theta/2, W(0) = 1 - theta
 };
@@ -151,6 +152,7 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
   c.mq_inv2t2 = (T)(-0.25 / (2.0 * theta * theta));
   c.q_inv2t2 = (T)(0.25 / (2.0 * theta * theta));
   c.ntt = (T)(-theta * (1.0 - 3.0 * theta));
+  c.tt2 = (T)(2.0 * theta * (1.0 - theta));
   c.rho_ref = (T)rho_ref;
   c.w[0] = (T)(0.5 * theta);
   c.w[1] = (T)(1.0 - theta);
@@ -161,7 +163,7 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
 // The same coefficients in another arithmetic type (a batch stores FP32
 // coefficients per domain and broadcasts them to packed pairs).
 template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Coef<T>& a) {
-  static_assert(sizeof(Coef<float>) == 17 * sizeof(float), "coef_cast lists every field of Coef");
+  static_assert(sizeof(Coef<float>) == 18 * sizeof(float), "coef_cast lists every field of Coef");
   Coef<U> c;
   c.theta = U(a.theta);
   c.one_m_theta = U(a.one_m_theta);
@@ -176,6 +178,7 @@ template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Co
   c.mq_inv2t2 = U(a.mq_inv2t2);
   c.q_inv2t2 = U(a.q_inv2t2);
   c.ntt = U(a.ntt);
+  c.tt2 = U(a.tt2);
   c.rho_ref = U(a.rho_ref);
   c.w[0] = U(a.w[0]);
   c.w[1] = U(a.w[1]);
@@ -381,16 +384,17 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
       } else {
         // Psi^C with Pi~ of Eq. 11b and pref of Eq. 12, evaluated on f^OReg (model 3):
         // pref = -(K1/2)(mu_xx + mu_yy); or on f^neq (model 4): pref = -K1.
+        const T e1x = ux2 - T(1.0), e1y = uy2 - T(1.0);
         T nhw;  // -omega' pref / 2
         if constexpr (MODEL == 3) {
-          const T muxx = (c.theta - ux2) * px[1];  // 2 theta^2 mu_xx
-          const T muyy = (c.theta - uy2) * py[1];  // 2 theta^2 mu_yy
-          nhw = c.q_inv2t2 * A1 * (muxx + muyy);
+          // 2 theta^2 (mu_xx + mu_yy) = (theta - u_x^2) P_x(0) + (theta - u_y^2) P_y(0)
+          //   = 2 theta (1 - theta) + u_x^2 (u_x^2 - 1) + u_y^2 (u_y^2 - 1)
+          nhw = c.q_inv2t2 * A1 * fma(ux2, e1x, fma(uy2, e1y, c.tt2));
         } else {
           nhw = scaled(A1, 0.5f);
         }
-        const T hPxx = nhw * fma(ux2, ux2 - T(1.0), c.tt);               // omega' Pi~_xx / 2
-        const T hPyy = nhw * fma(uy2, T(1.0) - uy2, c.ntt);              // omega' Pi~_yy / 2
+        const T hPxx = nhw * fma(ux2, e1x, c.tt);  // omega' Pi~_xx / 2
+        const T hPyy = nhw * (kNegFree ? fma(-uy2, e1y, c.ntt) : fma(uy2, T(1.0) - uy2, c.ntt));  // omega' Pi~_yy / 2
         const T qPxy = scaled(nhw, 0.5f) * (ux * uy) * dyx2;             // omega' Pi~_xy / 4
         const T hpsx = scaled(wpsx, 0.5f), hpsy = scaled(wpsy, 0.5f);
         cor[1] = hPyy - hpsx;
