@@ -121,14 +121,14 @@ __device__ __forceinline__ f32x2 lds_two(const __half* p0, const __half* p1) {
   return f32x2(make_float2(__half2float(*p0), __half2float(*p1)));
 }
 
-// Shared-memory footprint of the ring (bytes).
 // Resident CTAs per SM the pipeline kernels ask the compiler to allow for:
 // three when a CTA of NC + 32 threads at 72 registers a thread fits three
 // times in the register file (NC = 256: the ring then also fits three times).
-// Without the bound the FP16 form's diagnostics variant takes 78 registers and
-// two CTAs a SM (measured: 2 x 9 warps, 113 against 136 GLUPS without it).
+// Without the bound the FP16 form's diagnostics variant took 78 registers and
+// ran two CTAs a SM (measured at 4096^2: 113.7 GLUPS, against 118.8 with it).
 template <int NC> constexpr int stream_min_blocks() { return (NC + 32) * 3 * 72 <= 65536 && NC >= 256 ? 3 : 1; }
 
+// Shared-memory footprint of the ring (bytes).
 template <int PREC, int NC, int STAGES> struct StreamShape {
   using S = typename Form<PREC>::S;
   static constexpr int kChunk = 16 / (int)sizeof(S);   // elements in one 16-byte chunk
