@@ -121,10 +121,11 @@ __device__ __forceinline__ void collide_vjp(const T (&f)[9], const T (&mu)[9], c
     } else if constexpr (MODEL >= 3) {
       // Psi^C through h = omega' pref / 2 (model 3: mq A1 (mu_xx' + mu_yy'); model 4:
       // -A1 / 2), the halved Pi~ terms hPxx = -h Fx, hPyy = h Fy, qPxy = h G / 2 and hps = psi' / 2.
-      const T muxx = (c.theta - ux2) * px[1];
-      const T muyy = (c.theta - uy2) * py[1];
-      const T h = MODEL == 3 ? c.mq_inv2t2 * A1 * (muxx + muyy) : scaled(A1, -0.5f);
-      const T Fx = fma(ux2, ux2 - T(1.0), c.tt), Fy = fma(uy2, uy2 - T(1.0), c.tt);
+      // 2 theta^2 (mu_xx' + mu_yy') = 2 theta (1 - theta) + u_x^2 (u_x^2 - 1) + u_y^2 (u_y^2 - 1)
+      const T e1x = ux2 - T(1.0), e1y = uy2 - T(1.0);
+      const T musum = fma(ux2, e1x, fma(uy2, e1y, c.tt2));
+      const T h = MODEL == 3 ? c.mq_inv2t2 * A1 * musum : scaled(A1, -0.5f);
+      const T Fx = fma(ux2, e1x, c.tt), Fy = fma(uy2, e1y, c.tt);
       const T G = ux * uy * (ux2 - uy2);
       const T Sd = (mu[5] + mu[7]) + (mu[6] + mu[8]);
       const T hPyyb = mu[1] + mu[3] - T(0.5) * Sd;
@@ -148,7 +149,7 @@ __device__ __forceinline__ void collide_vjp(const T (&f)[9], const T (&mu)[9], c
       // model 4, h = -A1 / 2
       const T hb = fma(hqb, G, fma(hPyyb, Fy, -(hPxxb * Fx)));
       if constexpr (MODEL == 3) {
-        A1b = fma(hb * c.mq_inv2t2, muxx + muyy, A1b);
+        A1b = fma(hb * c.mq_inv2t2, musum, A1b);
         const T m2hA = scaled(hb * c.mq_inv2t2 * A1, -2.0f);
         uxb = fma(m2hA * ux, fma(T(-2.0), ux2, T(1.0)), uxb);
         uyb = fma(m2hA * uy, fma(T(-2.0), uy2, T(1.0)), uyb);
