@@ -133,7 +133,7 @@ template <typename T> struct Coef {
   T ntt;          // -theta (1 - 3 theta)
   T tt2;          // 2 theta (1 - theta)
   T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
-  T w[3];         // rho_ref * rest weights per axis pair are W(a) W(b); W(-1) = W(1) = theta/2, W(0) = 1 - theta
+  T rw0, rwp;     // rho_ref W(0) and rho_ref W(+-1): the rest state is rho_ref W(a) W(b), W(0) = 1 - theta, W(+-1) = theta/2
 };
 
 template <typename T> __host__ Coef<T> make_coef(double theta, double tau, double rho_ref) {
@@ -154,16 +154,15 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
   c.ntt = (T)(-theta * (1.0 - 3.0 * theta));
   c.tt2 = (T)(2.0 * theta * (1.0 - theta));
   c.rho_ref = (T)rho_ref;
-  c.w[0] = (T)(0.5 * theta);
-  c.w[1] = (T)(1.0 - theta);
-  c.w[2] = (T)(0.5 * theta);
+  c.rw0 = (T)(rho_ref * (1.0 - theta));
+  c.rwp = (T)(rho_ref * 0.5 * theta);
   return c;
 }
 
 // The same coefficients in another arithmetic type (a batch stores FP32
 // coefficients per domain and broadcasts them to packed pairs).
 template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Coef<T>& a) {
-  static_assert(sizeof(Coef<float>) == 18 * sizeof(float), "coef_cast lists every field of Coef");
+  static_assert(sizeof(Coef<float>) == 17 * sizeof(float), "coef_cast lists every field of Coef");
   Coef<U> c;
   c.theta = U(a.theta);
   c.one_m_theta = U(a.one_m_theta);
@@ -180,9 +179,8 @@ template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Co
   c.ntt = U(a.ntt);
   c.tt2 = U(a.tt2);
   c.rho_ref = U(a.rho_ref);
-  c.w[0] = U(a.w[0]);
-  c.w[1] = U(a.w[1]);
-  c.w[2] = U(a.w[2]);
+  c.rw0 = U(a.rw0);
+  c.rwp = U(a.rwp);
   return c;
 }
 
@@ -340,16 +338,19 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
           f[i] = fma(e[a + 1], py[b + 1], c.one_m_omega * f[i]);
         }
     } else {
-      // Shifted: f^eq - rho_ref W W = rho dP_x(a) P_y(b) + W_a Q(b) with
-      // Q(b) = m0 W_b + rho dP_y(b), so no O(1) terms cancel.
-      const T rdx[3] = {rho * dx[0], rho * dx[1], rho * dx[2]};
-      const T Q[3] = {fma(m0, c.w[0], rho * dy[0]), fma(m0, c.w[1], rho * dy[1]), fma(m0, c.w[2], rho * dy[2])};
+      // Shifted: with P = W + dP and rho = rho_ref + m0,
+      //   f^eq - rho_ref W_a W_b = P_y(b) (rho dP_x(a) + m0 W_a) + rho_ref W_a dP_y(b),
+      // every term small, so no O(1) terms cancel.
+      const T m0w0 = m0 * c.one_m_theta, m0wp = m0 * c.half_theta;
+      const T ex[3] = {fma(rho, dx[0], m0wp), fma(rho, dx[1], m0w0), fma(rho, dx[2], m0wp)};
+      const T rdy0[3] = {c.rw0 * dy[0], c.rw0 * dy[1], c.rw0 * dy[2]};
+      const T rdyp[3] = {c.rwp * dy[0], c.rwp * dy[1], c.rwp * dy[2]};
 #pragma unroll
       for (int a = -1; a <= 1; ++a)
 #pragma unroll
         for (int b = -1; b <= 1; ++b) {
           const int i = pop_index(a, b);
-          const T feq = fma(c.w[a + 1], Q[b + 1], rdx[a + 1] * py[b + 1]);
+          const T feq = fma(ex[a + 1], py[b + 1], a == 0 ? rdy0[b + 1] : rdyp[b + 1]);
           f[i] = fma(c.omega, feq - f[i], f[i]);
         }
     }
@@ -408,17 +409,15 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
         cor[8] = dsum + qPxy;
       }
     }
-    // Shifted forms: the f^eq deviation not carried by P_y(b) E(a) is W_a Q(b),
-    // Q(b) = m0 W_b + rho dP_y(b).
-    T Q[3];
-    if constexpr (SHIFT) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) Q[k] = fma(m0, c.w[k], rho * dy[k]);
-    }
+    // Shifted forms: f^eq - rho_ref W_a W_b = P_y(b) (rho dP_x(a) + m0 W_a) + rho_ref W_a dP_y(b)
+    // (P = W + dP, rho = rho_ref + m0); the first part joins E(a), the second is added per population.
     T E[3], B[3], G[3];
+    T m0w0, m0wp;
+    if constexpr (SHIFT) m0w0 = m0 * c.one_m_theta, m0wp = m0 * c.half_theta;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const T base = SHIFT ? rho * dx[k] : rho * px[k];  // f^eq part carried by P_y(b)
+      // f^eq part carried by P_y(b)
+      const T base = SHIFT ? fma(rho, dx[k], k == 1 ? m0w0 : m0wp) : rho * px[k];
       E[k] = fma(A1 * px[k], k == 1 ? ux2 : cxm[k] * cxm[k], base);  // C_x(0)^2 = u_x^2
       B[k] = A1 * px[k];
       G[k] = A2 * (px[k] * cxm[k]);
@@ -429,7 +428,7 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
       for (int b = -1; b <= 1; ++b) {
         const int i = pop_index(a, b);
         T rest = cor[i];
-        if constexpr (SHIFT) rest = fma(c.w[a + 1], Q[b + 1], rest);
+        if constexpr (SHIFT) rest = fma(a == 0 ? c.rw0 : c.rwp, dy[b + 1], rest);
         f[i] = fma(py[b + 1], fma(cym[b + 1], fma(-B[a + 1], cym[b + 1], G[a + 1]), E[a + 1]), rest);
       }
   }
