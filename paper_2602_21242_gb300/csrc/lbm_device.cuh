@@ -134,6 +134,7 @@ template <typename T> struct Coef {
   T tt2;          // 2 theta (1 - theta)
   T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
   T rw0, rwp;     // rho_ref W(0) and rho_ref W(+-1): the rest state is rho_ref W(a) W(b), W(0) = 1 - theta, W(+-1) = theta/2
+  T nrw0, nrwp;   // -rw0, -rwp
 };
 
 template <typename T> __host__ Coef<T> make_coef(double theta, double tau, double rho_ref) {
@@ -156,13 +157,15 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
   c.rho_ref = (T)rho_ref;
   c.rw0 = (T)(rho_ref * (1.0 - theta));
   c.rwp = (T)(rho_ref * 0.5 * theta);
+  c.nrw0 = (T)(-rho_ref * (1.0 - theta));
+  c.nrwp = (T)(-rho_ref * 0.5 * theta);
   return c;
 }
 
 // The same coefficients in another arithmetic type (a batch stores FP32
 // coefficients per domain and broadcasts them to packed pairs).
 template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Coef<T>& a) {
-  static_assert(sizeof(Coef<float>) == 17 * sizeof(float), "coef_cast lists every field of Coef");
+  static_assert(sizeof(Coef<float>) == 19 * sizeof(float), "coef_cast lists every field of Coef");
   Coef<U> c;
   c.theta = U(a.theta);
   c.one_m_theta = U(a.one_m_theta);
@@ -181,6 +184,8 @@ template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Co
   c.rho_ref = U(a.rho_ref);
   c.rw0 = U(a.rw0);
   c.rwp = U(a.rwp);
+  c.nrw0 = U(a.nrw0);
+  c.nrwp = U(a.nrwp);
   return c;
 }
 
@@ -358,24 +363,24 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
     // Onsager-regularised models (Eq. 2) with corrections (Eqs. 14, 15).
     // Non-equilibrium stress (Eq. 4 gives Pi^eq = rho (u u + theta I) exactly):
     //   2 N_d = sum (c_x^2 - c_y^2) f - rho (u_x^2 - u_y^2),  N_xy = sum c_x c_y f - rho u_x u_y.
-    // (rho u_x u_y = j_x u_y. FP64 instructions negate operands for free; the
-    // packed FP32 forms have no negated operands and take C(0) = -u, which they
-    // form anyway.)
+    // (rho u_x u_y = j_x u_y.) FP64 instructions negate operands for free; the
+    // packed FP32 instructions have no negated operands, so the products below
+    // are arranged with -C_x(a) = u_x - a and -K2, whose signs cancel exactly.
     const T Dxy = s13 - s24;
-    const T Pxy = s57 - s68;
-    const T cxm[3] = {T(-1.0) - ux, -ux, T(1.0) - ux};  // C_x(a) = a - u_x
-    const T cym[3] = {T(-1.0) - uy, -uy, T(1.0) - uy};
-    constexpr bool kNegFree = std::is_same<T, double>::value;
+    const T nPxy = s68 - s57;                                // -sum c_x c_y f
+    const T ncx[3] = {ux + T(1.0), ux, ux - T(1.0)};         // -C_x(a)
+    const T cym[3] = {T(-1.0) - uy, -uy, T(1.0) - uy};       // C_y(b) = b - u_y
+    constexpr bool kNegFree = !std::is_same<T, f32x2>::value;  // scalar and double-float negations are free
     const T dyx2 = uy2 - ux2;
-    const T A1 = c.k1 * fma(rho, dyx2, Dxy);                                    // omega' K1
-    const T A2 = c.k2 * (kNegFree ? fma(-jx, uy, Pxy) : fma(jx, cym[1], Pxy));  // omega' K2
+    const T A1 = c.k1 * fma(rho, dyx2, Dxy);    // omega' K1
+    const T nA2 = c.k2 * fma(jx, uy, nPxy);     // -omega' K2
     // omega' Psi per population (Eqs. 14, 15), from closed-form psi and Pi~.
     T cor[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) cor[i] = T(0.0);
     if constexpr (MODEL >= 2) {
       const T wpsx = A1 * ux * (c.c3 - ux2);   // omega' psi_x
-      const T wpsy = (kNegFree ? -A1 * uy : A1 * cym[1]) * (c.c3 - uy2);  // omega' psi_y
+      const T wpsy = A1 * uy * (uy2 - c.c3);   // omega' psi_y
       if constexpr (MODEL == 2) {
         // Psi^P: -1/2 c_ia psi_a on the axis populations.
         cor[1] = scaled(wpsx, -0.5f);
@@ -416,20 +421,29 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
     if constexpr (SHIFT) m0w0 = m0 * c.one_m_theta, m0wp = m0 * c.half_theta;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      // f^eq part carried by P_y(b)
-      const T base = SHIFT ? fma(rho, dx[k], k == 1 ? m0w0 : m0wp) : rho * px[k];
-      E[k] = fma(A1 * px[k], k == 1 ? ux2 : cxm[k] * cxm[k], base);  // C_x(0)^2 = u_x^2
       B[k] = A1 * px[k];
-      G[k] = A2 * (px[k] * cxm[k]);
+      G[k] = nA2 * (px[k] * ncx[k]);
+      if (SHIFT && k == 1) {
+        E[k] = fma(ux2, B[k] - rho, m0w0);  // m0 W(0) - rho u_x^2 + B(0) C_x(0)^2
+      } else {
+        // f^eq part carried by P_y(b)
+        const T base = SHIFT ? fma(rho, dx[k], m0wp) : rho * px[k];
+        E[k] = fma(B[k], k == 1 ? ux2 : ncx[k] * ncx[k], base);  // C_x(0)^2 = u_x^2
+      }
     }
+    // G(a) - B(a) C_y(b): the packed forms take B(a) (-C_y(b)) instead of a negated B(a).
+    const T ncy[3] = {uy + T(1.0), uy, uy - T(1.0)};  // -C_y(b)
 #pragma unroll
     for (int a = -1; a <= 1; ++a)
 #pragma unroll
       for (int b = -1; b <= 1; ++b) {
         const int i = pop_index(a, b);
         T rest = cor[i];
-        if constexpr (SHIFT) rest = fma(a == 0 ? c.rw0 : c.rwp, dy[b + 1], rest);
-        f[i] = fma(py[b + 1], fma(cym[b + 1], fma(-B[a + 1], cym[b + 1], G[a + 1]), E[a + 1]), rest);
+        // rho_ref W_a dP_y(b), dP_y(0) = -u_y^2
+        if constexpr (SHIFT)
+          rest = b == 0 ? fma(a == 0 ? c.nrw0 : c.nrwp, uy2, rest) : fma(a == 0 ? c.rw0 : c.rwp, dy[b + 1], rest);
+        const T inner = kNegFree ? fma(-B[a + 1], cym[b + 1], G[a + 1]) : fma(B[a + 1], ncy[b + 1], G[a + 1]);
+        f[i] = fma(py[b + 1], fma(cym[b + 1], inner, E[a + 1]), rest);
       }
   }
 }
