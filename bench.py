@@ -37,8 +37,8 @@ BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "f64df": 144}
 # complete 86, the mu sum and Pi~ sharing u^2 - 1; complete with the Eq. 12
 # prefactor from f^neq 83) and the fused diagnostics (5: three sums and j.u by
 # two FMAs). The FP64 form is bound by the FP64 pipe on GB300; the kernel issues
-# fewer of them to it (exact power-of-two scalings run on the integer pipe: 117
-# of the complete model's 124), and the count stays the method's.
+# fewer of them to it (exact power-of-two scalings run on the integer pipe: about
+# 116 of the complete model's 124 by the ncu counters), and the count stays the method's.
 FP64_OPS_PER_NODE = {"lbgk": 60, "oreg": 94, "partial": 104, "complete": 124, "complete_neq": 121}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch from the ncu capture of
@@ -46,7 +46,7 @@ FALLBACK_HBM_GBS = 6800.0
 # the lattice by node count since traffic grows with it, and
 # profiles/step_stream_persistent_kernel_f32_complete_4096.md at 4096^2). Keyed by
 # (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.4, ("f32", "complete"): 68.8}
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.5, ("f32", "complete"): 68.8}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
 STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_persistent_kernel",
