@@ -347,9 +347,11 @@ __global__ void __launch_bounds__(256) step_kernel_df(const double* __restrict__
   step_body<MODEL, 3, DIAG, PAIRS>(src, dst, g, c, partials, rows);
 }
 
-// The FP64 form is bound by the FP64 pipe, whose latency is hidden by more
-// resident warps: capped at 96 registers a thread, five blocks of 128 threads
-// fit an SM (four at the uncapped count). Launched with at most 512 threads.
+// The FP64 form is bound by the FP64 pipe. Capped at 96 registers a thread,
+// five blocks of 128 threads fit an SM (four at the uncapped count); the rate
+// measures the same with caps from 72 (seven blocks, spilling) to 128 registers
+// (4751-4762 MLUPS at 4096^2), so the cap is not critical. Launched with at
+// most 512 threads.
 template <int MODEL, bool DIAG>
 __global__ void __maxnreg__(96) step_kernel_f64(const double* __restrict__ src, double* __restrict__ dst, Geometry g,
                                                 Coef<double> c, double* __restrict__ partials, int rows) {
