@@ -171,7 +171,9 @@ int lbm_step_diagnostics(lbm_ctx* ctx, double* h_out5, long long* h_time);
 
 /*
  * Moments of the current state (Sec. 1): rho = sum_i f_i and u = sum_i c_i f_i / rho,
- * written to device arrays of nx * ny doubles.
+ * written to device arrays of nx * ny doubles. 1 / rho is formed as in the step
+ * (within an ulp or two of the quotient); a node whose density lies outside
+ * [2^-126, 2^126) gets non-finite velocities.
  */
 int lbm_moments(lbm_ctx* ctx, double* d_rho, double* d_ux, double* d_uy);
 

@@ -439,7 +439,7 @@ int lbm_diagnostics(lbm_ctx* ctx, double* h_out5) {
   if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_diagnostics before lbm_init / lbm_set_state");
   cudaError_t e = launch_diag(ctx, ctx->stream);
   if (e == cudaSuccess)
-    e = olbm::launch_finalize(ctx->d_partials, (int)olbm::node_blocks(ctx->g), ctx->rho_ref, nodes_of(ctx), ctx->t,
+    e = olbm::launch_finalize(ctx->d_partials, (int)olbm::diag_blocks(ctx->g), ctx->rho_ref, nodes_of(ctx), ctx->t,
                               ctx->d_diag_now, nullptr, ctx->stream);
   double d[6];
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, ctx->d_diag_now, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);

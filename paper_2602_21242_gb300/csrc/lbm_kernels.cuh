@@ -26,6 +26,7 @@ constexpr int kBX = 32;  // threads along x of the auxiliary kernels (init, mome
 constexpr int kBY = 8;   // rows per block of the auxiliary kernels
 constexpr int kNT = kBX * kBY;
 constexpr int kNDiag = 5;  // partial sums per block: m0, jx, jy, ke, non-finite nodes
+constexpr int kDiagRows = 8;  // rows per thread of the diagnostics kernel (one block reduction per 8 nodes)
 
 // Source offsets of the pull f_i(x) = B_i(x - c_i) inside one plane.
 __device__ __forceinline__ void pull_offsets(int x, int y, const Geometry& g, long long (&o)[9]) {
@@ -373,31 +374,50 @@ inline int stream_width(int prec) {
 }
 
 // ------------------------------------------------------------------ diagnostics of the state
-// Pull only (no collision): FP64 moments of f(x, t), block partials as above.
+// FP64 moments of the pulled populations of node (x, y) of f(x, t): m0 (the sum of
+// the stored values), j_x, j_y, with the lattice's 0 and +-1 coefficients taken
+// as adds and subtracts (16 operations, as in the collision).
+template <int PREC>
+__device__ __forceinline__ void pulled_moments(const typename Form<PREC>::S* __restrict__ src, const Geometry& g,
+                                               int x, int y, double& m0, double& jx, double& jy) {
+  long long o[9];
+  pull_offsets(x, y, g, o);
+  double f[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = to_double(src[i * g.plane + o[i]]);
+  const double s13 = f[1] + f[3], d13 = f[1] - f[3];
+  const double s24 = f[2] + f[4], d24 = f[2] - f[4];
+  const double s57 = f[5] + f[7], d57 = f[5] - f[7];
+  const double s68 = f[6] + f[8], d68 = f[6] - f[8];
+  m0 = f[0] + (s13 + s24) + (s57 + s68);
+  jx = d13 + (d57 - d68);
+  jy = d24 + (d57 + d68);
+}
+
+// Pull only (no collision): FP64 moments of f(x, t), block partials as above;
+// each thread takes kDiagRows rows of its column, so the block reduction is paid
+// once per kDiagRows nodes. The kinetic energy uses the reciprocal of the
+// collision (a density outside [2^-126, 2^126) makes it non-finite).
 template <int PREC>
 __global__ void __launch_bounds__(kNT) diag_kernel(const typename Form<PREC>::S* __restrict__ src, Geometry g,
                                                    double rho_ref, double* __restrict__ partials) {
   const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
+  const int y0 = blockIdx.y * kBY * kDiagRows + threadIdx.y;
   double acc[kNDiag] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (x < g.nx && y < g.ny) {
-    long long o[9];
-    pull_offsets(x, y, g, o);
-    double m0 = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const double v = to_double(src[i * g.plane + o[i]]);
-      m0 += v;
-      jx += (double)cx_of(i) * v;
-      jy += (double)cy_of(i) * v;
-    }
-    if (finite_bits(m0)) {
-      acc[0] = m0;
-      acc[1] = jx;
-      acc[2] = jy;
-      acc[3] = 0.5 * (jx * jx + jy * jy) / (rho_ref + m0);
-    } else {
-      acc[4] = 1.0;
+  if (x < g.nx) {
+    for (int r = 0; r < kDiagRows; ++r) {
+      const int y = y0 + r * kBY;
+      if (y >= g.ny) break;
+      double m0, jx, jy;
+      pulled_moments<PREC>(src, g, x, y, m0, jx, jy);
+      if (finite_bits(m0)) {
+        acc[0] += m0;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] = fma(0.5 * fma(jx, jx, jy * jy), recip(rho_ref + m0), acc[3]);
+      } else {
+        acc[4] += 1.0;
+      }
     }
   }
   double tot[kNDiag];
@@ -427,9 +447,15 @@ __global__ void __launch_bounds__(kNT) init_kernel(const double* __restrict__ rh
   const double r = rho[n], u = ux[n], v = uy[n];
   const double px[3] = {geq_factor(-1, u, theta), geq_factor(0, u, theta), geq_factor(1, u, theta)};
   const double py[3] = {geq_factor(-1, v, theta), geq_factor(0, v, theta), geq_factor(1, v, theta)};
+  const double rpx[3] = {r * px[0], r * px[1], r * px[2]};
+  // rest values rho_ref W(a) W(b): three distinct products
+  const double w0 = 1.0 - theta, wp = 0.5 * theta;
+  const double rest[3] = {rho_ref * (w0 * w0), rho_ref * (w0 * wp), rho_ref * (wp * wp)};
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    dst[i * g.plane + o[i]] = from_double<S>(r * px[cx_of(i) + 1] * py[cy_of(i) + 1] - rest_value(i, theta, rho_ref));
+  for (int i = 0; i < 9; ++i) {
+    const int nz = (cx_of(i) != 0) + (cy_of(i) != 0);  // axes with a nonzero velocity component
+    dst[i * g.plane + o[i]] = from_double<S>(fma(rpx[cx_of(i) + 1], py[cy_of(i) + 1], -rest[nz]));
+  }
 }
 
 // (rho, u) of f(x, t) in FP64, unpadded [y][x] output.
@@ -440,21 +466,14 @@ __global__ void __launch_bounds__(kNT) moments_kernel(const typename Form<PREC>:
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  long long o[9];
-  pull_offsets(x, y, g, o);
-  double m0 = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const double v = to_double(src[i * g.plane + o[i]]);
-    m0 += v;
-    jx += (double)cx_of(i) * v;
-    jy += (double)cy_of(i) * v;
-  }
+  double m0, jx, jy;
+  pulled_moments<PREC>(src, g, x, y, m0, jx, jy);
   const double r = rho_ref + m0;
+  const double ir = recip(r);  // a density outside [2^-126, 2^126) gives non-finite velocities
   const long long n = (long long)y * g.nx + x;
   rho[n] = r;
-  ux[n] = jx / r;
-  uy[n] = jy / r;
+  ux[n] = jx * ir;
+  uy[n] = jy * ir;
 }
 
 // out_i(x) = B_i(x - c_i) + rest_i  (pre-collision f(x, t), FP64, unpadded [i][y][x]).
@@ -490,6 +509,9 @@ __global__ void __launch_bounds__(kNT) set_state_kernel(const double* __restrict
 
 // ------------------------------------------------------------------ launchers
 inline dim3 grid_of(const Geometry& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY); }
+inline dim3 diag_grid(const Geometry& g) {
+  return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY * kDiagRows - 1) / (kBY * kDiagRows));
+}
 // The shifted forms (1, 2) update node pairs (x, x + 1) when nx is even.
 inline bool uses_pairs(int prec, const Geometry& g) { return (prec == 1 || prec == 2) && (g.nx % 2) == 0; }
 // The pipeline kernel (launch kind 1) applies to the shifted forms and FP64, any nx.
@@ -632,7 +654,7 @@ template <int PREC> struct Launch {
   }
 
   static cudaError_t diag(const void* src, const Geometry& g, double rho_ref, double* partials, cudaStream_t st) {
-    diag_kernel<PREC><<<grid_of(g), dim3(kBX, kBY), 0, st>>>((const S*)src, g, rho_ref, partials);
+    diag_kernel<PREC><<<diag_grid(g), dim3(kBX, kBY), 0, st>>>((const S*)src, g, rho_ref, partials);
     return cudaGetLastError();
   }
 

@@ -43,6 +43,8 @@ struct StepArgs {
 // Number of thread blocks of the auxiliary node-parallel kernels and of the
 // step kernel under a launch shape (= diagnostics partials they write).
 long long node_blocks(const Geometry& g);
+// Blocks (= diagnostics partials) of the diagnostics kernel, at most node_blocks.
+long long diag_blocks(const Geometry& g);
 long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec);
 // Columns of one bulk-copy pipeline tile and the CTAs of that kernel resident
 // on one SM (launch kind 1) for a shifted storage form.

@@ -10,6 +10,11 @@ long long node_blocks(const Geometry& g) {
   return (long long)gr.x * gr.y;
 }
 
+long long diag_blocks(const Geometry& g) {
+  const dim3 gr = diag_grid(g);
+  return (long long)gr.x * gr.y;
+}
+
 long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec) {
   const dim3 gr = step_grid(g, k, prec);
   return (long long)gr.x * gr.y;
