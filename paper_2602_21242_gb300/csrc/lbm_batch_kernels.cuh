@@ -87,21 +87,13 @@ __global__ void __launch_bounds__(512) batch_diag_kernel(const Desc<typename For
   int bad = 0;
   for (int j = tid; j < w * h; j += nthreads) {
     const int x = tl.y + j % w, y = tl.z + j / w;
-    long long o[9];
-    pull_offsets(x, y, d.g, o);
-    double m0 = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const double f = to_double(src[i * d.g.plane + o[i]]);
-      m0 += f;
-      jx += (double)cx_of(i) * f;
-      jy += (double)cy_of(i) * f;
-    }
+    double m0, jx, jy;
+    pulled_moments<PREC>(src, d.g, x, y, m0, jx, jy);
     if (finite_bits(m0)) {
       v[0] += m0;
       v[1] += jx;
       v[2] += jy;
-      v[3] += 0.5 * (jx * jx + jy * jy) / (rho_ref + m0);
+      v[3] = fma(0.5 * fma(jx, jx, jy * jy), recip(rho_ref + m0), v[3]);
     } else {
       ++bad;
     }
