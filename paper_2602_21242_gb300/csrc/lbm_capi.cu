@@ -131,6 +131,7 @@ void free_ctx(lbm_ctx* c) {
     if (c->ev_step[b]) cudaEventDestroy(c->ev_step[b]);
     if (c->ev_fin[b]) cudaEventDestroy(c->ev_fin[b]);
   }
+  if (c->ev_io) cudaEventDestroy(c->ev_io);
   if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->d_diag);
   cudaFree(c->d_diag_now);
@@ -227,7 +228,8 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
       (e = cudaEventCreateWithFlags(&c->ev_step[0], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_step[1], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_fin[0], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_fin[1], cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&c->ev_fin[1], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming)) != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
     return fail(nullptr, LBM_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
@@ -520,15 +522,21 @@ int lbm_run_host(lbm_ctx* ctx, const double* h_rho0, const double* h_ux0, const 
   if ((s = lbm_init(ctx, in, in + N, in + 2 * N)) != LBM_OK) return s;
   if ((s = lbm_step(ctx, n)) != LBM_OK) return s;
   if (h_rho || h_ux || h_uy) {
+    // The downloads run on the side stream, beside the diagnostics pass on the main one.
     if ((s = lbm_moments(ctx, outp, outp + N, outp + 2 * N)) != LBM_OK) return s;
-    if (h_rho && (e = cudaMemcpyAsync(h_rho, outp, fb, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    if ((e = cudaEventRecord(ctx->ev_io, ctx->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->side, ctx->ev_io, 0)) != cudaSuccess)
       return cuda_fail(ctx, e, "lbm_run_host download");
-    if (h_ux && (e = cudaMemcpyAsync(h_ux, outp + N, fb, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    if (h_rho && (e = cudaMemcpyAsync(h_rho, outp, fb, cudaMemcpyDeviceToHost, ctx->side)) != cudaSuccess)
       return cuda_fail(ctx, e, "lbm_run_host download");
-    if (h_uy && (e = cudaMemcpyAsync(h_uy, outp + 2 * N, fb, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    if (h_ux && (e = cudaMemcpyAsync(h_ux, outp + N, fb, cudaMemcpyDeviceToHost, ctx->side)) != cudaSuccess)
+      return cuda_fail(ctx, e, "lbm_run_host download");
+    if (h_uy && (e = cudaMemcpyAsync(h_uy, outp + 2 * N, fb, cudaMemcpyDeviceToHost, ctx->side)) != cudaSuccess)
       return cuda_fail(ctx, e, "lbm_run_host download");
   }
-  if (h_diag5) return lbm_diagnostics(ctx, h_diag5);  // synchronises
+  s = h_diag5 ? lbm_diagnostics(ctx, h_diag5) : LBM_OK;  // synchronises the main stream
+  if ((e = cudaStreamSynchronize(ctx->side)) != cudaSuccess) return cuda_fail(ctx, e, "lbm_run_host download");
+  if (s != LBM_OK) return s;
   e = cudaStreamSynchronize(ctx->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(ctx, e, "lbm_run_host sync");
 }
