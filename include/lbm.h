@@ -120,7 +120,13 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
 /* Release the lattice and the device memory it owns. NULL is accepted. Synchronises its stream. */
 int lbm_destroy(lbm_ctx* ctx);
 
-/* Rebind the lattice to another stream (cudaStream_t as void*, NULL = legacy default). */
+/*
+ * Rebind the lattice to another stream (cudaStream_t as void*, NULL = legacy
+ * default). Work already enqueued for the lattice (steps on the old stream and
+ * the fused diagnostics' final sums joined into it) is ordered before anything
+ * later enqueued on the new stream: the new stream waits for an event recorded
+ * on the old one. Does not synchronise the host.
+ */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
 /*
@@ -293,6 +299,19 @@ int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows
  * ------------------------------------------------------------------------ */
 typedef struct lbm_batch lbm_batch;
 
+/*
+ * The batched form advances many domains "in one persistent launch captured in a
+ * CUDA graph". The two modes take the two halves of that phrase:
+ *   LBM_BATCH_GRAPH      the graph: every step is one launch of the tile kernel
+ *                        over all domains, and the n launches of a call are
+ *                        captured once into a CUDA graph and replayed as one
+ *                        graph launch (fused diagnostics as a parallel branch).
+ *   LBM_BATCH_PERSISTENT the persistent launch: one cooperative launch runs all
+ *                        n steps, a grid barrier with a bounded wait between
+ *                        steps; issued directly, because the call reads the
+ *                        barrier's status back and synchronises.
+ * Both measure the same on GB300 (88 % of HBM on 256 Taylor-Green domains).
+ */
 enum lbm_batch_mode {
   LBM_BATCH_GRAPH = 0,      /* one tile-kernel launch per step, n steps captured into one CUDA graph */
   LBM_BATCH_PERSISTENT = 1  /* one cooperative launch for all n steps, bounded-wait grid barrier per step */
@@ -381,14 +400,20 @@ int lbm_measure_peak(int kind, double* h_flops);
  *           holding the state at time t as the library keeps it: plane i, node y
  *           holds f_i(y + c_i, t) (periodic), the population that node y + c_i
  *           pulls from y; read only.
- *   d_dst   a second such buffer (not aliasing d_src); receives the state at t + 1
- *           in the same convention.
- *   d_diag5 device array of 5 doubles: diagnostics of f(x, t) as in lbm_diagnostics.
+ *   d_dst   a second such buffer; receives the state at t + 1 in the same
+ *           convention.
+ *   d_diag5 device array of 5 doubles: mass, momentum x, y and kinetic energy of
+ *           f(x, t) as in lbm_diagnostics, and in element 4 the number of nodes
+ *           whose populations do not sum to a finite value (left out of the
+ *           sums). The call never returns LBM_ENONFINITE: callers check
+ *           element 4 themselves.
  *   stream  cudaStream_t as void* (NULL = legacy default stream).
  *
- * Asynchronous. The first call on a device resolves the scratch array's device
- * address (a cudaGetSymbolAddress on that device, which must be current); make
- * that first call before any stream capture. All calls on a device share the
+ * d_src, d_dst and d_diag5 must not share a byte (LBM_EINVAL otherwise).
+ * Asynchronous. The first call on a device, and the first after that device's
+ * context was reset or re-created, resolves the scratch array's device address
+ * (a cudaGetSymbolAddress on that device, which must be current); make that
+ * first call before any stream capture. All calls on a device share the
  * scratch: calls whose work overlaps on the GPU race on it. Lattices that need
  * more than 8192 blocks of 32 x 8 threads with up to 64 rows per thread (for
  * example a 16384 x 16384 grid; 8192 x 8192 fits) are rejected with LBM_EINVAL.

@@ -132,6 +132,7 @@ void free_ctx(lbm_ctx* c) {
     if (c->ev_fin[b]) cudaEventDestroy(c->ev_fin[b]);
   }
   if (c->ev_io) cudaEventDestroy(c->ev_io);
+  if (c->ev_rebind) cudaEventDestroy(c->ev_rebind);
   if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->d_diag);
   cudaFree(c->d_diag_now);
@@ -229,7 +230,8 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
       (e = cudaEventCreateWithFlags(&c->ev_step[1], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_fin[0], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_fin[1], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_rebind, cudaEventDisableTiming)) != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
     return fail(nullptr, LBM_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
@@ -261,8 +263,16 @@ int lbm_destroy(lbm_ctx* ctx) {
 }
 
 int lbm_set_stream(lbm_ctx* ctx, void* stream) {
-  if (!ctx) return LBM_EINVAL;
-  ctx->stream = static_cast<cudaStream_t>(stream);
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  cudaStream_t next = static_cast<cudaStream_t>(stream);
+  if (next == ctx->stream) return LBM_OK;
+  // Everything enqueued so far (lbm_step joins the side stream's final sums into
+  // the old stream before it returns) precedes the next call's work.
+  cudaError_t e = cudaEventRecord(ctx->ev_rebind, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(next, ctx->ev_rebind, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_stream");
+  ctx->stream = next;
   return LBM_OK;
 }
 

@@ -29,6 +29,7 @@ struct lbm_ctx {
   cudaEvent_t ev_step[2] = {nullptr, nullptr};  // partials of buffer b written (on `stream`)
   cudaEvent_t ev_fin[2] = {nullptr, nullptr};   // partials of buffer b summed (on `side`)
   cudaEvent_t ev_io = nullptr;                  // lbm_run_host: moments written (on `stream`)
+  cudaEvent_t ev_rebind = nullptr;              // lbm_set_stream: end of the old stream's work
   bool fin_pending[2] = {false, false};
   int pbuf = 0;  // partials buffer of the next diagnosed step
   double* d_diag = nullptr;      // [6] latest fused diagnostics (out5 + time)

@@ -16,6 +16,7 @@
 // five sums before the final reduction reads them), so nothing needs clearing
 // between calls, but two calls whose work overlaps on one device (for example
 // on different streams) race on it.
+#include <cstdint>
 #include <mutex>
 
 #include "lbm.h"
@@ -27,24 +28,78 @@ namespace {
 constexpr int kNoAllocMaxBlocks = 8192;
 __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * 5];
 
-// Device address of g_noalloc_partials, resolved once per device. In host code
-// the symbol's name is only a host-side stand-in, so kernels get this address.
+// Device address of g_noalloc_partials, resolved once per device and CUDA
+// context. In host code the symbol's name is only a host-side stand-in, so
+// kernels get this address. A cudaDeviceReset (or the release and re-creation
+// of the primary context) reloads the library's device image, and the array may
+// then lie elsewhere: each entry remembers the unique id of the context it was
+// resolved in (cuCtxGetId, reached through the runtime's driver entry points so
+// that the library needs no link-time dependency on the driver library) and is
+// resolved again when the current context's id differs. Where those entry
+// points are missing the address is resolved on every call
+// (cudaGetSymbolAddress allocates nothing).
 constexpr int kMaxDevices = 128;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchEntry {
+  double* addr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+ScratchEntry g_scratch[kMaxDevices];
 std::mutex g_scratch_lock;
+
+using CtxGetCurrentFn = int (*)(void** ctx);                       // CUresult cuCtxGetCurrent(CUcontext*)
+using CtxGetIdFn = int (*)(void* ctx, unsigned long long* ctx_id);  // CUresult cuCtxGetId(CUcontext, ...)
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::once_flag g_driver_once;
+
+void load_driver_entry_points() {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess && p)
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+  p = nullptr;
+  q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess && p)
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(p);
+  cudaGetLastError();  // a failed lookup leaves no sticky error behind
+}
+
+// Unique id of the current CUDA context, 0 if it cannot be read.
+unsigned long long current_context_id() {
+  std::call_once(g_driver_once, load_driver_entry_points);
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != 0 || ctx == nullptr || g_ctx_get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 int scratch_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
+  // cudaGetDevice does not create the context; the symbol lookup below does,
+  // so the id is read again after it when the first read found no context.
+  unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> guard(g_scratch_lock);
-  if (g_scratch_addr[dev] == nullptr) {
+  ScratchEntry& e = g_scratch[dev];
+  if (e.addr == nullptr || id == 0 || e.ctx_id != id) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess || p == nullptr) return LBM_ECUDA;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (err != cudaSuccess || p == nullptr) return LBM_ECUDA;
+    if (id == 0) id = current_context_id();
+    e.addr = static_cast<double*>(p);
+    e.ctx_id = id;
   }
-  *out = g_scratch_addr[dev];
+  *out = e.addr;
   return LBM_OK;
+}
+
+// [a, a + na) and [b, b + nb) share a byte.
+bool overlaps(const void* a, long long na, const void* b, long long nb) {
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+  return pa < pb + (uintptr_t)nb && pb < pa + (uintptr_t)na;
 }
 
 // Final fixed-order sum of the partials into the caller's 5 doubles.
@@ -80,8 +135,13 @@ extern "C" int lbm_step_noalloc(int nx, int ny, double theta, double tau, int mo
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: invalid size %d x %d", nx, ny);
   if (!(theta > 0.0 && theta < 1.0) || !(tau > 0.5) || model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ)
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: theta, tau or model out of range");
-  if (!d_src || !d_dst || !d_diag5 || d_src == d_dst)
-    return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: NULL or aliased buffers");
+  if (!d_src || !d_dst || !d_diag5)
+    return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: NULL buffer");
+  // The kernels take the buffers as __restrict__: no byte may be shared.
+  const long long diag_bytes = 5 * (long long)sizeof(double);
+  if (overlaps(d_src, bytes, d_dst, bytes) || overlaps(d_diag5, diag_bytes, d_src, bytes) ||
+      overlaps(d_diag5, diag_bytes, d_dst, bytes))
+    return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: d_src, d_dst and d_diag5 overlap");
   const olbm::Geometry g{nx, ny, pitch, plane};
   // 32 x 8 threads per block; rows per thread grows until the grid fits the scratch array.
   olbm::LaunchCfg k;

@@ -105,6 +105,12 @@ class Lattice:
         with torch.cuda.device(self.device):
             capi.lbm_step(self._ctx, int(n))
 
+    def set_stream(self, stream: torch.cuda.Stream) -> None:
+        """Run later calls on `stream`; the library orders them after the work already queued."""
+        with torch.cuda.device(self.device):
+            capi.lbm_set_stream(self._ctx, stream.cuda_stream)
+        self.stream = stream
+
     def set_diagnostics_interval(self, every: int) -> None:
         capi.lbm_set_diagnostics_interval(self._ctx, int(every))
 

@@ -8,6 +8,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import riemann
 from paper_2602_21242_gb300 import experiments
 from paper_2602_21242_gb300.lattice import tau_from_nu
 
@@ -73,7 +74,8 @@ def test_shocktube_matches_the_paper_statements():
     free of them but its middle-state density is low while its velocity is right; the partially and
     completely corrected models recover the exact middle state. (0.55, 1e-9): LBGK is unphysical; the
     uncorrected model keeps its deficiency; the corrected ones stay accurate, oscillations small."""
-    r = {m: experiments.shocktube_run(m, 0.4, 1e-12) for m in ("lbgk", "oreg", "partial", "complete")}
+    r = {m: riemann.shocktube_measures(experiments.shocktube_run(m, 0.4, 1e-12))
+         for m in ("lbgk", "oreg", "partial", "complete")}
     rs, us = r["oreg"]["rho_star"], r["oreg"]["u_star"]
     assert r["lbgk"]["tv_excess"] > 1.0
     assert r["oreg"]["tv_excess"] < 0.02
@@ -81,7 +83,8 @@ def test_shocktube_matches_the_paper_statements():
     for m in ("partial", "complete"):
         assert abs(r[m]["plateau_rho"] - rs) < 2e-4 and abs(r[m]["plateau_ux"] - us) < 2e-4
         assert r[m]["tv_excess"] < 0.02 and r[m]["l1_rho"] < 0.5 * r["oreg"]["l1_rho"]
-    r = {m: experiments.shocktube_run(m, 0.55, 1e-9) for m in ("lbgk", "oreg", "partial", "complete")}
+    r = {m: riemann.shocktube_measures(experiments.shocktube_run(m, 0.55, 1e-9))
+         for m in ("lbgk", "oreg", "partial", "complete")}
     assert (not r["lbgk"]["finite"]) or r["lbgk"]["l1_rho"] > 1.0
     assert rs - r["oreg"]["plateau_rho"] > 2e-3
     for m in ("partial", "complete"):

@@ -163,6 +163,31 @@ def test_library_owned_buffers_match_torch_buffers(oracle):
         np.testing.assert_array_equal(lat.state().cpu().numpy(), ref)
 
 
+def test_set_stream_orders_new_work_after_old():
+    """Steps queued on one stream, then the lattice rebound to a second stream: work on the
+    second stream (reading the state back) sees every earlier step and diagnostics sum."""
+    n, steps = 1024, 60
+    rho, ux, uy = flows.shear_wave(n, n, U=0.1, amp=0.01)
+    ref_state = None
+    for rebind in (False, True):
+        first, second = torch.cuda.Stream(), torch.cuda.Stream()
+        with Lattice(n, n, 1 / 3, 0.52, "complete", stream=first) as lat:
+            lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+            lat.set_diagnostics_interval(1)
+            lat.step(steps)  # asynchronous on `first`
+            if rebind:
+                lat.set_stream(second)
+            got = lat.state()  # runs on the lattice's current stream
+            diag, t, status = lat.step_diagnostics()
+        torch.cuda.synchronize()
+        if ref_state is None:
+            ref_state, ref_diag = got.cpu().numpy(), diag
+        else:
+            np.testing.assert_array_equal(got.cpu().numpy(), ref_state)
+            np.testing.assert_array_equal(diag, ref_diag)
+            assert t == steps - 1 and status == capi.LBM_OK
+
+
 def test_run_host_matches_device_path(oracle):
     """lbm_run_host (host buffers in and out) equals init + step + moments on the device."""
     n, theta, tau = 48, 1 / 3, 0.56

@@ -7,9 +7,7 @@ import math
 import numpy as np
 import pytest
 
-pytest.importorskip("torch")
-
-from paper_2602_21242_gb300 import experiments as ex
+from oracle import riemann as ex
 
 
 @pytest.mark.parametrize("theta", [0.4, 0.55, 1.0 / 3.0])
@@ -67,8 +65,28 @@ def test_integrals_of_mass_and_momentum(theta):
     assert trapezoid(rho * u, dx=h) == pytest.approx(theta * (rho_l - rho_r) * t, rel=2e-5)
 
 
+def test_measures_of_the_exact_profile():
+    """shocktube_measures on a run that equals the exact solution at its nodes: no l1 error, no
+    total-variation excess, and the plateau at the middle state."""
+    theta, steps, n = 0.4, 400, 800
+    x = np.arange(1, n - 1)
+    x0 = n // 2 - 0.5
+    rho, u = ex.isothermal_riemann_sample(1.5, 0.75, theta, (x - x0) / steps)
+    m = ex.shocktube_measures({"x": x, "rho": rho, "ux": u, "finite": True, "x0": x0, "theta": theta,
+                               "steps": steps, "rho_l": 1.5, "rho_r": 0.75})
+    assert m["l1_rho"] == 0.0 and m["l1_ux"] == 0.0 and abs(m["tv_excess"]) < 1e-12
+    assert m["plateau_rho"] == pytest.approx(m["rho_star"], rel=1e-14)
+    assert m["plateau_ux"] == pytest.approx(m["u_star"], rel=1e-14)
+    bad = ex.shocktube_measures({"x": x, "rho": rho, "ux": u, "finite": False, "x0": x0, "theta": theta,
+                                 "steps": steps, "rho_l": 1.5, "rho_r": 0.75})
+    assert not bad["finite"] and "l1_rho" not in bad
+
+
 def test_shocktube_fields_layout():
-    rho, ux, uy, walls = ex.shocktube_fields(800)
+    pytest.importorskip("torch")
+    from paper_2602_21242_gb300 import experiments
+
+    rho, ux, uy, walls = experiments.shocktube_fields(800)
     assert rho.shape == ux.shape == uy.shape == walls.shape == (1, 800)
     assert walls[0, 0] == 1 and walls[0, 799] == 1 and walls.sum() == 2
     assert (rho[0, :400] == 1.5).all() and (rho[0, 400:] == 0.75).all()

@@ -58,6 +58,57 @@ def test_noalloc_matches_regular_step_twice(model, nx, ny):
             src, dst = dst, src
 
 
+def test_noalloc_large_lattice_grows_rows_per_thread():
+    """A 4096 x 4096 lattice needs 16384 blocks at 4 rows per thread, more than the
+    scratch holds, so the entry point doubles the rows per thread (to 8): the path
+    of the large benchmark lattices. Two calls in a row against the regular path,
+    compared on the device element by element at the same tolerance."""
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    nx = ny = 4096
+    model, theta, tau = 3, 1.0 / 3.0, 0.52
+    pitch, plane, nbytes = capi.lbm_layout(nx, ny, capi.LBM_F64)
+    rho, ux, uy = flows.shear_wave(nx, ny, 0.1, 0.01)
+    stream = torch.cuda.current_stream()
+    with Lattice(nx, ny, theta, tau, model, "f64", stream=stream) as lat:
+        lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+        lat.step(4)  # a state off equilibrium; an even count leaves it in buffer 0
+        raw = lat._buffers.view(torch.float64).view(2, 9 * plane)
+        src = raw[0].clone()
+        dst = torch.full_like(src, float("nan"))
+        diag = torch.full((5,), float("nan"), dtype=torch.float64, device=src.device)
+        lat.set_diagnostics_interval(1)
+        for call in range(2):
+            lat.step(1)
+            ref_diag, _, status = lat.step_diagnostics()
+            assert status == capi.LBM_OK
+            capi.lbm_step_noalloc(nx, ny, theta, tau, model, src.data_ptr(), dst.data_ptr(), diag.data_ptr(),
+                                  stream.cuda_stream)
+            torch.cuda.synchronize()
+            want = _interior(raw[(call + 1) % 2], nx, ny, pitch, plane)
+            got = _interior(dst, nx, ny, pitch, plane)
+            err = ((got - want).abs() / want.abs()).max().item()
+            assert err <= REL, f"call {call}: max rel err {err:.3e}"
+            np.testing.assert_allclose(diag.cpu().numpy(), ref_diag, rtol=REL, atol=1e-9)
+            src, dst = dst, src
+
+
+def test_noalloc_rejects_overlapping_buffers():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    nx, ny = 32, 16
+    _, _, nbytes = capi.lbm_layout(nx, ny, capi.LBM_F64)
+    buf = torch.zeros(2 * nbytes // 8 + 16, dtype=torch.float64, device="cuda")
+    base = buf.data_ptr()
+    # rejected on the host before any launch: the buffers are never touched
+    for src, dst, diag in [(base, base + 8 * 64, base + 2 * nbytes),       # d_dst starts inside d_src
+                           (base, base + nbytes, base + 8 * 10),           # d_diag5 inside d_src
+                           (base, base + nbytes, base + nbytes + 8 * 3)]:  # d_diag5 inside d_dst
+        with pytest.raises(capi.LBMError) as e:
+            capi.lbm_step_noalloc(nx, ny, 1 / 3, 0.6, 3, src, dst, diag)
+        assert e.value.status == capi.LBM_EINVAL and "overlap" in str(e.value)
+
+
 def test_noalloc_rejects_lattices_beyond_its_scratch():
     if not torch.cuda.is_available():
         pytest.fail("GPU test needs a CUDA device")
