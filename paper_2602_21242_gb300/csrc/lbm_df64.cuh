@@ -1,27 +1,32 @@
-// lbm_df64.cuh -- double-float arithmetic for the FP64-storage form that
-// computes on the FP32 pipes (storage form 3, LBM_F64_DF).
+// lbm_df64.cuh -- double-word arithmetic for the FP64-storage form that
+// computes on the FP32 pipes (storage form 3, LBM_F64_DF), and the collision
+// of Eq. 1a written for it.
 //
-// A value is the unevaluated sum hi + lo of two FP32 numbers with |lo| at most
-// about an ulp of hi: 48 significant bits, relative rounding error near 2^-47
-// per operation, FP32's exponent range. The operations are built from
-// error-free transformations: Knuth's TwoSum (s + e = a + b exactly), Dekker's
-// Fast2Sum (the same when |a| >= |b|) and the FMA form of TwoProd
-// (p + e = a * b exactly, e = fma(a, b, -p)). Addition is the variant that
-// bounds the error relative to |a| + |b|; multiplication drops the lo * lo
-// term. Every FP32 step goes through an intrinsic that is rounded on its own,
-// so the compiler never contracts a multiply and an add into an FMA, which
-// would break the transformations.
+// A value is the unevaluated sum hi + lo of two FP32 numbers: about 48
+// significant bits and FP32's exponent range. The operations are built from
+// error-free transformations: Knuth's TwoSum (s + e = a + b exactly, any a, b)
+// and the FMA form of TwoProd (p + e = a * b exactly, e = fma(a, b, -p)).
+// Every FP32 step goes through an intrinsic that is rounded on its own, so the
+// compiler never contracts a multiply and an add into an FMA, which would break
+// the transformations.
 //
-// F is float; the operations are also written for f32x2 (two values per
-// register pair, Blackwell's packed add/mul/fma.f32x2), which measured slower
-// for this collision on GB300: the packed pair state needs about 220 registers
-// a thread, too few warps remain to cover the long dependent chains.
+// Results are left unnormalised: a sum is TwoSum of the high parts with the
+// low parts added to its error term (8 FP32 operations, where renormalising
+// with Fast2Sum would take 3 more), a product is TwoProd of the high parts with
+// the two cross terms added to its error (4 operations; lo * lo dropped).
+// Without the renormalisation |lo| is no longer bounded by half an ulp of hi,
+// but it stays within a few ulps of the operands' magnitude (the error term of
+// a TwoSum or TwoProd plus low parts of earlier results), so every operation
+// keeps an absolute error of about 2^-47 of its operands' magnitude -- the
+// bound of the renormalised "sloppy" double-word sum, which is also relative
+// to |a| + |b| rather than to |a + b|. The one place that needs a normalised
+// operand is the FP32 seed of a reciprocal: recip() renormalises first.
+// Operations with an FP32 operand (add_f, mul_f) skip the terms that operand's
+// zero low part would contribute.
 //
 // Conversions from FP64 storage work on the bit patterns with integer
-// instructions; on the way out hi is widened the same way and lo converted and
-// added on the FP64 pipe, two FP64-pipe instructions per stored value (on GB300
-// the FP64 pipe runs at 1/64 of the FP32 rate). Magnitudes below 2^-126 (about
-// 1.2e-38) convert to zero.
+// instructions; on the way out the two parts are added on the FP64 pipe (on
+// GB300 the FP64 pipe runs at 1/64 of the FP32 rate).
 #pragma once
 
 #include <cstdint>
@@ -35,88 +40,96 @@ __device__ __forceinline__ float ef_add(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ float ef_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float ef_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float ef_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float ef_fms(float a, float b, float c) { return __fmaf_rn(a, b, -c); }  // a b - c
-__device__ __forceinline__ float ef_rcp(float a) { return __frcp_rn(a); }
-// f32x2: its operators are the packed intrinsics, each lane rounded once.
-__device__ __forceinline__ f32x2 ef_add(f32x2 a, f32x2 b) { return a + b; }
-__device__ __forceinline__ f32x2 ef_sub(f32x2 a, f32x2 b) { return a - b; }
-__device__ __forceinline__ f32x2 ef_mul(f32x2 a, f32x2 b) { return a * b; }
-__device__ __forceinline__ f32x2 ef_fma(f32x2 a, f32x2 b, f32x2 c) { return fma(a, b, c); }
-__device__ __forceinline__ f32x2 ef_fms(f32x2 a, f32x2 b, f32x2 c) {
-  return f32x2(__ffma2_rn(a.v, b.v, make_float2(-c.v.x, -c.v.y)));
-}
-__device__ __forceinline__ f32x2 ef_rcp(f32x2 a) { return f32x2(make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))); }
 
-template <class F> struct dfloat {
-  F hi, lo;
-  dfloat() = default;
-  __host__ __device__ dfloat(F h, F l) : hi(h), lo(l) {}
+// Knuth's TwoSum: s + e = a + b exactly, for any order of magnitude of a and b.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = ef_add(a, b);
+  const float v = ef_sub(s, a);
+  e = ef_add(ef_sub(a, ef_sub(s, v)), ef_sub(b, v));
+}
+
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
   // From a double (constants and host-built coefficients): hi the nearest
   // FP32 value, lo the nearest FP32 value of the remainder.
-  __host__ __device__ dfloat(double d) : hi(F((float)d)), lo(F((float)(d - (double)(float)d))) {}
-  __host__ __device__ dfloat(int i) : dfloat((double)i) {}
+  __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ df64(int i) : df64((double)i) {}
 
-  // TwoSum of the high parts, the low parts added to the error, Fast2Sum to renormalise.
-  friend __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
-    const F s = ef_add(a.hi, b.hi);
-    const F v = ef_sub(s, a.hi);
-    F e = ef_add(ef_sub(a.hi, ef_sub(s, v)), ef_sub(b.hi, v));
-    e = ef_add(e, ef_add(a.lo, b.lo));
-    const F h = ef_add(s, e);
-    return dfloat(h, ef_sub(e, ef_sub(h, s)));
+  friend __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return df64(s, ef_add(e, ef_add(a.lo, b.lo)));
   }
-  friend __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
-  friend __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
-  friend __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
-  // TwoProd of the high parts, the cross terms folded into its error. The pair
-  // (p, e) is returned without renormalising: |e| stays within about an ulp of p
-  // (the product of the high parts dominates), which every operation here accepts.
-  friend __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
-    const F p = ef_mul(a.hi, b.hi);
-    F e = ef_fms(a.hi, b.hi, p);
+  friend __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+  friend __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+  friend __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+  // TwoProd of the high parts, the cross terms folded into its error.
+  friend __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+    const float p = ef_mul(a.hi, b.hi);
+    float e = ef_fma(a.hi, b.hi, -p);
     e = ef_fma(a.hi, b.lo, e);
     e = ef_fma(a.lo, b.hi, e);
-    return dfloat(p, e);
+    return df64(p, e);
   }
-  // a b + c: the product as above, then TwoSum with c.
-  friend __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
-    const F p = ef_mul(a.hi, b.hi);
-    F e = ef_fms(a.hi, b.hi, p);
+  // a b + c: the product as above, then TwoSum with c's high part; the
+  // product's error and c's low part join TwoSum's error term.
+  friend __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) {
+    const float p = ef_mul(a.hi, b.hi);
+    float e = ef_fma(a.hi, b.hi, -p);
     e = ef_fma(a.hi, b.lo, e);
     e = ef_fma(a.lo, b.hi, e);
-    const F s = ef_add(p, c.hi);
-    const F v = ef_sub(s, p);
-    F t = ef_add(ef_sub(p, ef_sub(s, v)), ef_sub(c.hi, v));
-    t = ef_add(t, ef_add(e, c.lo));
-    const F h = ef_add(s, t);
-    return dfloat(h, ef_sub(t, ef_sub(h, s)));
+    float s, w;
+    two_sum(p, c.hi, s, w);
+    return df64(s, ef_add(w, ef_add(e, c.lo)));
   }
 };
 
-template <class F> __device__ __forceinline__ dfloat<F> scaled(dfloat<F> x, float k) {
-  return dfloat<F>(ef_mul(x.hi, F(k)), ef_mul(x.lo, F(k)));
+// a + b for an FP32 b (7 operations).
+__device__ __forceinline__ df64 add_f(df64 a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  return df64(s, ef_add(e, a.lo));
 }
-template <class F> __device__ __forceinline__ dfloat<F> fma_scaled(dfloat<F> x, float k, dfloat<F> c) {
-  return scaled(x, k) + c;
+// a b for an FP32 b (3 operations).
+__device__ __forceinline__ df64 mul_f(df64 a, float b) {
+  const float p = ef_mul(a.hi, b);
+  return df64(p, ef_fma(a.lo, b, ef_fma(a.hi, b, -p)));
+}
+// k x for a power of two k: both parts scaled exactly.
+__device__ __forceinline__ df64 scaled(df64 x, float k) { return df64(ef_mul(x.hi, k), ef_mul(x.lo, k)); }
+__device__ __forceinline__ df64 fma_scaled(df64 x, float k, df64 c) { return scaled(x, k) + c; }
+// hi + lo renormalised (Dekker's Fast2Sum; |hi| >= |lo|): |lo| at most half an ulp of hi.
+__device__ __forceinline__ df64 normalised(df64 x) {
+  const float h = ef_add(x.hi, x.lo);
+  return df64(h, ef_sub(x.lo, ef_sub(h, x.hi)));
 }
 
-using df64 = dfloat<float>;
-
-// 1 / x: the FP32 reciprocal of hi, one Newton step r + r (1 - x r) in
-// double-float (relative error about 2^-47).
-template <class F> __device__ __forceinline__ dfloat<F> recip(dfloat<F> x) {
-  const dfloat<F> r(ef_rcp(x.hi), F(0.0f));
-  const dfloat<F> e = dfloat<F>(1.0) - x * r;
-  return fma(r, e, r);
+// 1 / x. The operand is renormalised and its high part's FP32 reciprocal r
+// (rcp.approx, relative error below 2^-22) gives the residual e = 1 - x r,
+// computed from the exact product of x's high part and r (1 - p is exact for
+// p near 1); one cubic Newton step r (1 + e + e^2) in double-word arithmetic
+// leaves a relative error of about 2^-47 (the rounding of e) plus e^3. A zero,
+// infinite or NaN x gives NaN, and so does |x| >= 2^126, where the seed would
+// underflow to zero (a density that large only arises in a simulation that has
+// blown up).
+__device__ __forceinline__ df64 recip(df64 x) {
+  x = normalised(x);
+  float r = rcp_seed(x.hi);
+  r = (__float_as_uint(r) << 1) == 0u ? __uint_as_float(0x7FC00000u) : r;
+  const float p = ef_mul(x.hi, r);
+  const float pe = ef_fma(x.hi, r, -p);
+  const float e = ef_fma(-x.lo, r, ef_sub(ef_sub(1.0f, p), pe));
+  return df64(r, ef_mul(r, ef_fma(e, e, e)));
 }
 
-// ---------------------------------------------------------------- FP64 <-> double-float
+// ---------------------------------------------------------------- FP64 <-> double-word
 // Split a double into hi + lo with integer instructions: hi takes the sign,
 // the exponent and the leading 23 stored mantissa bits (a truncation), lo the
-// remaining 29 bits rounded to FP32 (so |lo| < ulp(hi): the pair is left
-// unnormalised, which the operations above accept). NaN and infinity keep their
-// class in hi; magnitudes below 2^-126 become zero, above FP32's range infinity.
-// Cases are selected without branches.
+// remaining 29 bits rounded to FP32 (so |lo| < ulp(hi)). NaN and infinity keep
+// their class in hi; magnitudes below 2^-126 become zero, above FP32's range
+// infinity. Cases are selected without branches.
 __device__ __forceinline__ df64 split_f64(double d) {
   const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
   const unsigned sign = h32 & 0x80000000u;
@@ -133,16 +146,47 @@ __device__ __forceinline__ df64 split_f64(double d) {
   return df64(__uint_as_float(hib), __uint_as_float(__float_as_uint(lo) | sign));
 }
 
+// The same split for 2^-74 <= |d| < 2^128, in seven instructions. The high
+// word shifted left by 3 (with the low word's top three bits shifted in) holds
+// the FP32 exponent's low seven bits and the 23 mantissa bits in place; bit 30
+// of the FP32 exponent equals bit 10 of the FP64 exponent (E - 896 >= 128 iff
+// E >= 1024) and bit 31 is the sign, both taken from the high word. lo is the
+// remaining 29 bits converted to FP32 and scaled by 2^(E - 1075), a power of two
+// whose bit pattern is hi's sign and exponent field less 52 (a normal FP32
+// number from E >= 949 on).
+__device__ __forceinline__ bool in_fast_split_range(double d) {
+  const unsigned h2 = (unsigned)__double2hiint(d) << 1;  // exponent in bits 31..21, sign dropped
+  return h2 - (0x3B5u << 21) < ((0x47Fu - 0x3B5u) << 21);
+}
+__device__ __forceinline__ df64 split_f64_fast(double d) {
+  const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
+  const unsigned hib = (__funnelshift_l(l32, h32, 3) & 0x3FFFFFFFu) | (h32 & 0xC0000000u);
+  const float scale = __uint_as_float((hib & 0xFF800000u) - (52u << 23));
+  return df64(__uint_as_float(hib), __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale));
+}
+
 // hi + lo rounded to FP64: hi widened with integer instructions, lo converted
-// and added on the FP64 pipe (two FP64-pipe instructions a value).
-__device__ __forceinline__ double join_f64(df64 v) { return widen_f32(v.hi) + (double)v.lo; }
+// and added on the FP64 pipe (two FP64-pipe instructions a value). The widening
+// rebiases the exponent of a normal FP32 value in place: the high word is
+// (u >> 3) + 896 * 2^20 with the sign moved from bit 28 to bit 31 (adding
+// 7 * 2^28 for a negative u), the low word u << 29; a zero hi keeps its sign
+// and nothing else. An FP32 subnormal hi (below 2^-126, only in the final
+// digits of an underflowing value) widens to a number below 2^-126 as well.
+// A non-finite hi always comes with a non-finite lo (TwoSum and TwoProd turn
+// an overflow or a NaN into NaN or infinity in the error term), so the sum is
+// non-finite too, whatever the widened hi.
+__device__ __forceinline__ double widen_hi(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned neg = (unsigned)((int)u >> 31) & 0x70000000u;
+  const unsigned hw = (u << 1) == 0u ? (u & 0x80000000u) : (u >> 3) + 0x38000000u + neg;
+  return __hiloint2double((int)hw, (int)(u << 29));
+}
+__device__ __forceinline__ double join_f64(df64 v) { return widen_hi(v.hi) + (double)v.lo; }
 // The same sum with both conversions on the FP64 pipe: three FP64-pipe
-// instructions and no integer work. Faster where the FP64 pipe has room beside
-// a long double-float collision (the corrected models: +3 to +4 %), slower
-// where it does not (LBGK: -18 %, the uncorrected model: -1 %).
+// instructions and no integer work.
 __device__ __forceinline__ double join_f64_fp64pipe(df64 v) { return (double)v.hi + (double)v.lo; }
 
-// Storage form 3: FP64 populations, double-float arithmetic.
+// Storage form 3: FP64 populations, double-word arithmetic.
 template <> struct Form<3> {
   using S = double;
   using T = df64;
@@ -153,5 +197,132 @@ __device__ __forceinline__ void st_t(double* p, df64 v) { *p = join_f64(v); }
 __device__ __forceinline__ df64 ld_cg(const double* p, df64) { return split_f64(__ldcg(p)); }
 __device__ __forceinline__ double to_double(df64 v) { return join_f64(v); }
 
+// Split a row's nine pulled FP64 populations: the seven-instruction split when
+// every value lies in its range (all populations of a live simulation), the
+// general split otherwise (zeros, tiny or huge magnitudes, infinities, NaNs).
+__device__ __forceinline__ void split_node(const double (&r)[9], df64 (&f)[9]) {
+  bool fast = true;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fast = fast & in_fast_split_range(r[i]);
+  if (fast) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = split_f64_fast(r[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = split_f64(r[i]);
+  }
+}
+
+// ---------------------------------------------------------------- collision
+// The collision of Eq. 1a on double-word values: the product form of
+// collide() (lbm_device.cuh) with the same per-axis factors and the same
+// closed forms of psi (Eq. 6a), the Eq. 12 prefactor and Pi~ (Eq. 11b), with
+// the constants 1 and -1 as FP32 operands and P(a) of Eq. 10 built from
+// w = theta + u^2: P(0) = 1 - w, P(+-1) = (w +- u)/2. In place: f holds the
+// pulled pre-collision populations and receives the post-collision ones.
+template <int MODEL> __host__ __device__ constexpr bool has_correction(int i) {
+  return MODEL == 2 ? (i >= 1 && i <= 4) : (MODEL >= 3 ? i != 0 : false);
+}
+
+template <int MODEL, typename Sink>
+__device__ __forceinline__ void collide_df(df64 (&f)[9], const Coef<df64>& c, Sink&& sink) {
+  // moments (Sec. 1)
+  const df64 s13 = f[1] + f[3], d13 = f[1] - f[3];
+  const df64 s24 = f[2] + f[4], d24 = f[2] - f[4];
+  const df64 s57 = f[5] + f[7], d57 = f[5] - f[7];
+  const df64 s68 = f[6] + f[8], d68 = f[6] - f[8];
+  const df64 m0 = f[0] + ((s13 + s24) + (s57 + s68));
+  const df64 jx = d13 + (d57 - d68);
+  const df64 jy = d24 + (d57 + d68);
+  const df64 rho = m0;
+  const df64 inv_rho = recip(rho);
+  const df64 ux = jx * inv_rho, uy = jy * inv_rho;
+  {
+    NodeMoments<df64> mom;
+    mom.m0 = m0;
+    mom.jx = jx;
+    mom.jy = jy;
+    mom.ux = ux;
+    mom.uy = uy;
+    sink(mom);
+  }
+  const df64 ux2 = ux * ux, uy2 = uy * uy;
+  // per-axis GEq factors (Eq. 10)
+  const df64 wx = ux2 + c.theta, wy = uy2 + c.theta;
+  const df64 px[3] = {scaled(wx - ux, 0.5f), add_f(-wx, 1.0f), scaled(wx + ux, 0.5f)};
+  const df64 py[3] = {scaled(wy - uy, 0.5f), add_f(-wy, 1.0f), scaled(wy + uy, 0.5f)};
+
+  if constexpr (MODEL == 0) {
+    // LBGK: f* = (1 - 1/tau) f + (1/tau) f^eq
+    const df64 orho = c.omega * rho;
+    const df64 e[3] = {orho * px[0], orho * px[1], orho * px[2]};
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const int i = pop_index(a, b);
+        f[i] = fma(e[a + 1], py[b + 1], c.one_m_omega * f[i]);
+      }
+  } else {
+    // Onsager-regularised models (Eq. 2) with corrections (Eqs. 14, 15)
+    const df64 Dxy = s13 - s24;    // sum (c_x^2 - c_y^2) f
+    const df64 nPxy = s68 - s57;   // -sum c_x c_y f
+    const df64 ncx[3] = {add_f(ux, 1.0f), ux, add_f(ux, -1.0f)};  // -C_x(a) = u_x - a
+    const df64 ncy[3] = {add_f(uy, 1.0f), uy, add_f(uy, -1.0f)};  // -C_y(b)
+    const df64 dyx2 = uy2 - ux2;
+    const df64 A1 = c.k1 * fma(rho, dyx2, Dxy);   // omega' K1
+    const df64 nA2 = c.k2 * fma(jx, uy, nPxy);    // -omega' K2
+    df64 cor[9];
+    if constexpr (MODEL >= 2) {
+      const df64 wpsx = (A1 * ux) * (c.c3 - ux2);  // omega' psi_x
+      const df64 wpsy = (A1 * uy) * (uy2 - c.c3);  // omega' psi_y
+      if constexpr (MODEL == 2) {
+        cor[1] = scaled(wpsx, -0.5f);
+        cor[3] = scaled(wpsx, 0.5f);
+        cor[2] = scaled(wpsy, -0.5f);
+        cor[4] = scaled(wpsy, 0.5f);
+      } else {
+        // u_a^2 (u_a^2 - 1), shared by Eq. 12's mu sum and Eq. 11b's Pi~
+        const df64 X = ux2 * add_f(ux2, -1.0f), Y = uy2 * add_f(uy2, -1.0f);
+        df64 nhw;  // -omega' pref / 2
+        if constexpr (MODEL == 3) {
+          nhw = (c.q_inv2t2 * A1) * ((X + Y) + c.tt2);
+        } else {
+          nhw = scaled(A1, 0.5f);
+        }
+        const df64 hPxx = nhw * (X + c.tt);        // omega' Pi~_xx / 2
+        const df64 hPyy = -(nhw * (Y + c.tt));     // omega' Pi~_yy / 2
+        const df64 qPxy = (scaled(nhw, 0.5f) * (ux * uy)) * dyx2;  // omega' Pi~_xy / 4
+        const df64 hpsx = scaled(wpsx, 0.5f), hpsy = scaled(wpsy, 0.5f);
+        cor[1] = hPyy - hpsx;
+        cor[3] = hPyy + hpsx;
+        cor[2] = hPxx - hpsy;
+        cor[4] = hPxx + hpsy;
+        const df64 dsum = scaled(hPxx + hPyy, -0.5f);
+        cor[5] = dsum - qPxy;  // c_x c_y = +1
+        cor[7] = cor[5];
+        cor[6] = dsum + qPxy;  // c_x c_y = -1
+        cor[8] = cor[6];
+      }
+    }
+    // f*_(a,b) = P_y(b) [E(a) + C_y(b) (G(a) - B(a) C_y(b))] + omega' Psi_(a,b)
+    df64 E[3], B[3], G[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      B[k] = A1 * px[k];
+      G[k] = nA2 * (px[k] * ncx[k]);
+      E[k] = fma(B[k], k == 1 ? ux2 : ncx[k] * ncx[k], rho * px[k]);
+    }
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const int i = pop_index(a, b);
+        const df64 inner = fma(B[a + 1], ncy[b + 1], G[a + 1]);  // G(a) - B(a) C_y(b)
+        const df64 t = fma(-ncy[b + 1], inner, E[a + 1]);
+        f[i] = has_correction<MODEL>(i) ? fma(py[b + 1], t, cor[i]) : py[b + 1] * t;
+      }
+  }
+}
 
 }  // namespace olbm

@@ -27,6 +27,10 @@ constexpr int kBY = 8;   // rows per block of the auxiliary kernels
 constexpr int kNT = kBX * kBY;
 constexpr int kNDiag = 5;  // partial sums per block: m0, jx, jy, ke, non-finite nodes
 constexpr int kDiagRows = 8;  // rows per thread of the diagnostics kernel (one block reduction per 8 nodes)
+#ifndef OLBM_DF_JOIN_FP64
+#define OLBM_DF_JOIN_FP64 0
+#endif
+constexpr int kDfJoinFp64 = OLBM_DF_JOIN_FP64;  // double-word form: populations joined on the FP64 pipe alone
 
 // Source offsets of the pull f_i(x) = B_i(x - c_i) inside one plane.
 __device__ __forceinline__ void pull_offsets(int x, int y, const Geometry& g, long long (&o)[9]) {
@@ -255,34 +259,28 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
       xp = (x == g.nx - 1) ? 0 : x + 1;
     }
     if constexpr (PREC == 3) {
-      // Double-float form: the loads stay raw FP64 until their row is computed,
+      // Double-word form: the loads stay raw FP64 until their row is computed,
       // so the next row's loads are in flight during the current row's arithmetic
       // (splitting them at load time would wait for each load at once).
       using Raw = Column<MODEL, 0, DIAG, false, CG>;
-      double r[9], rn[9];
+      double r[9];
       int y = y0;
       if (y < g.ny) Raw::pull(src, g, x, xm, xp, y, r);
       for (int k = 0; k < rows && y < g.ny; ++k, y += dy) {
-        const bool more = (k + 1 < rows) && (y + dy < g.ny);
-        if (more) Raw::pull(src, g, x, xm, xp, y + dy, rn);
-        CT f[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = split_f64(r[i]);
-        collide<MODEL, false, CT>(f, c, [&](const NodeMoments<CT>& m) {
+        df64 f[9];
+        split_node(r, f);
+        // r is free once split: the next row's loads go into it and are in
+        // flight during this row's collision (no second set of registers).
+        if ((k + 1 < rows) && (y + dy < g.ny)) Raw::pull(src, g, x, xm, xp, y + dy, r);
+        collide_df<MODEL>(f, c, [&](const NodeMoments<df64>& m) {
           if constexpr (DIAG) acc.add(m);
         });
         S* q = dst + (long long)y * g.pitch + x;
-        if constexpr (MODEL <= 1) {
+        // The first kDfJoinFp64 populations are joined entirely on the FP64
+        // pipe (three FP64 instructions), the others with hi widened by integer
+        // instructions (two FP64 instructions and five integer ones).
 #pragma unroll
-          for (int i = 0; i < 9; ++i) st_t(q + i * g.plane, f[i]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) q[i * g.plane] = join_f64_fp64pipe(f[i]);
-        }
-        if (more) {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) r[i] = rn[i];
-        }
+        for (int i = 0; i < 9; ++i) q[i * g.plane] = i < kDfJoinFp64 ? join_f64_fp64pipe(f[i]) : join_f64(f[i]);
       }
       return;
     }
@@ -338,11 +336,16 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
   step_body<MODEL, PREC, DIAG, PAIRS>(src, dst, g, c, partials, rows);
 }
 
-// Double-float form (3): its state per node is as large as the FP64 form's
-// but its dependent chains are longer; at most 256 threads a block, so that
-// the compiler may keep it all in registers.
+// Double-word form (3): launched with at most 256 threads a block and capped
+// at 80 registers a thread, six blocks of 128 threads per SM. The complete
+// model with fused diagnostics compiles to 100 registers uncapped (four blocks
+// per SM: 22.5 GLUPS at 4096^2) and to 80, 88 and 96 without spills (23.5,
+// 23.2 and 21.2 GLUPS; 96 registers still allow only five blocks).
+#ifndef OLBM_DF_MAXNREG
+#define OLBM_DF_MAXNREG 80
+#endif
 template <int MODEL, bool DIAG, bool PAIRS>
-__global__ void __launch_bounds__(256) step_kernel_df(const double* __restrict__ src, double* __restrict__ dst,
+__global__ void __maxnreg__(OLBM_DF_MAXNREG) step_kernel_df(const double* __restrict__ src, double* __restrict__ dst,
                                                       Geometry g, Coef<typename Column<MODEL, 3, DIAG, PAIRS>::CT> c,
                                                       double* __restrict__ partials, int rows) {
   step_body<MODEL, 3, DIAG, PAIRS>(src, dst, g, c, partials, rows);

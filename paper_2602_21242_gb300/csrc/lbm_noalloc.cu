@@ -137,11 +137,6 @@ extern "C" int lbm_step_noalloc(int nx, int ny, double theta, double tau, int mo
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: theta, tau or model out of range");
   if (!d_src || !d_dst || !d_diag5)
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: NULL buffer");
-  // The kernels take the buffers as __restrict__: no byte may be shared.
-  const long long diag_bytes = 5 * (long long)sizeof(double);
-  if (overlaps(d_src, bytes, d_dst, bytes) || overlaps(d_diag5, diag_bytes, d_src, bytes) ||
-      overlaps(d_diag5, diag_bytes, d_dst, bytes))
-    return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: d_src, d_dst and d_diag5 overlap");
   const olbm::Geometry g{nx, ny, pitch, plane};
   // 32 x 8 threads per block; rows per thread grows until the grid fits the scratch array.
   olbm::LaunchCfg k;
@@ -155,6 +150,11 @@ extern "C" int lbm_step_noalloc(int nx, int ny, double theta, double tau, int mo
                                   "lbm_step_noalloc: a %d x %d lattice needs %lld thread blocks, more than the %d "
                                   "the fixed scratch holds (32 x 8 threads, up to 64 rows per thread)",
                                   nx, ny, nparts, kNoAllocMaxBlocks);
+  // The kernels take the buffers as __restrict__: no byte may be shared.
+  const long long diag_bytes = 5 * (long long)sizeof(double);
+  if (overlaps(d_src, bytes, d_dst, bytes) || overlaps(d_diag5, diag_bytes, d_src, bytes) ||
+      overlaps(d_diag5, diag_bytes, d_dst, bytes))
+    return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: d_src, d_dst and d_diag5 overlap");
   double* scratch = nullptr;
   if (scratch_for_current_device(&scratch) != LBM_OK)
     return olbm::set_thread_error(LBM_ECUDA, "lbm_step_noalloc: cannot resolve the scratch array on this device");
