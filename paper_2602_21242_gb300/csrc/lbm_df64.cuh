@@ -124,6 +124,76 @@ __device__ __forceinline__ df64 recip(df64 x) {
   return df64(r, ef_mul(r, ef_fma(e, e, e)));
 }
 
+// ---------------------------------------------------------------- paired double-word values
+// Two double-word values, one per lane of Blackwell's packed FP32 instructions
+// (add/mul/fma .f32x2, each lane rounded as the scalar instruction): one
+// instruction serves both. The packed instructions take no negated operands,
+// so a subtraction is fma(b, -1, a) (exact: one rounding of a - b) and the
+// error of a product is formed against the negated product (one more
+// instruction than the scalar TwoProd).
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// TwoSum on both lanes.
+__device__ __forceinline__ void two_sum(float2 a, float2 b, float2& s, float2& e) {
+  s = p_add(a, b);
+  const float2 v = p_sub(s, a);
+  e = p_add(p_sub(a, p_sub(s, v)), p_sub(b, v));
+}
+// The product's high part p and its error e (p + e = a b to double-word accuracy).
+__device__ __forceinline__ void two_prod(float2 ahi, float2 alo, float2 bhi, float2 blo, float2& p, float2& e) {
+  p = p_mul(ahi, bhi);
+  e = p_fma(ahi, bhi, p_mul(p, make_float2(-1.0f, -1.0f)));
+  e = p_fma(ahi, blo, e);
+  e = p_fma(alo, bhi, e);
+}
+
+// Operators are hidden friends: found only by argument-dependent lookup on dw2,
+// so they never capture the scalar fma(double, ...) of the enclosing namespace.
+struct dw2 {
+  float2 hi, lo;
+  friend __device__ __forceinline__ dw2 operator+(const dw2& a, const dw2& b) {
+    float2 s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return dw2{s, p_add(e, p_add(a.lo, b.lo))};
+  }
+  friend __device__ __forceinline__ dw2 operator*(const dw2& a, const dw2& b) {
+    float2 p, e;
+    two_prod(a.hi, a.lo, b.hi, b.lo, p, e);
+    return dw2{p, e};
+  }
+  // a b + c
+  friend __device__ __forceinline__ dw2 fma(const dw2& a, const dw2& b, const dw2& c) {
+    float2 p, e, s, w;
+    two_prod(a.hi, a.lo, b.hi, b.lo, p, e);
+    two_sum(p, c.hi, s, w);
+    return dw2{s, p_add(w, p_add(e, c.lo))};
+  }
+  // c - a b: TwoSum of c and -p written as a difference, no negation needed.
+  friend __device__ __forceinline__ dw2 fnma(const dw2& a, const dw2& b, const dw2& c) {
+    float2 p, e;
+    two_prod(a.hi, a.lo, b.hi, b.lo, p, e);
+    const float2 s = p_sub(c.hi, p);
+    const float2 v = p_sub(s, c.hi);
+    const float2 w = p_sub(p_sub(c.hi, p_sub(s, v)), p_add(p, v));
+    return dw2{s, p_add(w, p_sub(c.lo, e))};
+  }
+  // a + k for an FP32 pair k.
+  friend __device__ __forceinline__ dw2 add_c(const dw2& a, float2 k) {
+    float2 s, e;
+    two_sum(a.hi, k, s, e);
+    return dw2{s, p_add(e, a.lo)};
+  }
+  // a k for a pair k of powers of two (or -1, 1): both parts scaled exactly.
+  friend __device__ __forceinline__ dw2 scaled_c(const dw2& a, float2 k) { return dw2{p_mul(a.hi, k), p_mul(a.lo, k)}; }
+};
+__device__ __forceinline__ dw2 pair(df64 x, df64 y) { return dw2{make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+__device__ __forceinline__ dw2 bcast(df64 x) { return pair(x, x); }
+__device__ __forceinline__ df64 lane0(const dw2& v) { return df64(v.hi.x, v.lo.x); }
+__device__ __forceinline__ df64 lane1(const dw2& v) { return df64(v.hi.y, v.lo.y); }
+
 // ---------------------------------------------------------------- FP64 <-> double-word
 // Split a double into hi + lo with integer instructions: hi takes the sign,
 // the exponent and the leading 23 stored mantissa bits (a truncation), lo the
@@ -181,7 +251,17 @@ __device__ __forceinline__ double widen_hi(float f) {
   const unsigned hw = (u << 1) == 0u ? (u & 0x80000000u) : (u >> 3) + 0x38000000u + neg;
   return __hiloint2double((int)hw, (int)(u << 29));
 }
+// The same widening with FP32 subnormals flushed to a signed zero (for the low
+// part, whose subnormal values must not widen to 2^-127).
+__device__ __forceinline__ double widen_lo(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned neg = (unsigned)((int)u >> 31) & 0x70000000u;
+  const unsigned hw = (u & 0x7F800000u) == 0u ? (u & 0x80000000u) : (u >> 3) + 0x38000000u + neg;
+  return __hiloint2double((int)hw, (u & 0x7F800000u) == 0u ? 0 : (int)(u << 29));
+}
 __device__ __forceinline__ double join_f64(df64 v) { return widen_hi(v.hi) + (double)v.lo; }
+// Both parts widened with integer instructions: one FP64-pipe instruction a value.
+__device__ __forceinline__ double join_f64_int(df64 v) { return widen_hi(v.hi) + widen_lo(v.lo); }
 // The same sum with both conversions on the FP64 pipe: three FP64-pipe
 // instructions and no integer work.
 __device__ __forceinline__ double join_f64_fp64pipe(df64 v) { return (double)v.hi + (double)v.lo; }
@@ -218,14 +298,16 @@ __device__ __forceinline__ void split_node(const double (&r)[9], df64 (&f)[9]) {
 // collide() (lbm_device.cuh) with the same per-axis factors and the same
 // closed forms of psi (Eq. 6a), the Eq. 12 prefactor and Pi~ (Eq. 11b), with
 // the constants 1 and -1 as FP32 operands and P(a) of Eq. 10 built from
-// w = theta + u^2: P(0) = 1 - w, P(+-1) = (w +- u)/2. In place: f holds the
-// pulled pre-collision populations and receives the post-collision ones.
+// w = theta + u^2: P(0) = 1 - w, P(+-1) = (w +- u)/2. f holds the pulled
+// pre-collision populations; out(i, value) receives each post-collision
+// population as soon as it is known (so that its conversion and store overlap
+// the rest of the node's arithmetic).
 template <int MODEL> __host__ __device__ constexpr bool has_correction(int i) {
   return MODEL == 2 ? (i >= 1 && i <= 4) : (MODEL >= 3 ? i != 0 : false);
 }
 
-template <int MODEL, typename Sink>
-__device__ __forceinline__ void collide_df(df64 (&f)[9], const Coef<df64>& c, Sink&& sink) {
+template <int MODEL, typename Sink, typename Out>
+__device__ __forceinline__ void collide_df(const df64 (&f)[9], const Coef<df64>& c, Sink&& sink, Out&& out) {
   // moments (Sec. 1)
   const df64 s13 = f[1] + f[3], d13 = f[1] - f[3];
   const df64 s24 = f[2] + f[4], d24 = f[2] - f[4];
@@ -261,13 +343,12 @@ __device__ __forceinline__ void collide_df(df64 (&f)[9], const Coef<df64>& c, Si
 #pragma unroll
       for (int b = -1; b <= 1; ++b) {
         const int i = pop_index(a, b);
-        f[i] = fma(e[a + 1], py[b + 1], c.one_m_omega * f[i]);
+        out(i, fma(e[a + 1], py[b + 1], c.one_m_omega * f[i]));
       }
   } else {
     // Onsager-regularised models (Eq. 2) with corrections (Eqs. 14, 15)
     const df64 Dxy = s13 - s24;    // sum (c_x^2 - c_y^2) f
     const df64 nPxy = s68 - s57;   // -sum c_x c_y f
-    const df64 ncx[3] = {add_f(ux, 1.0f), ux, add_f(ux, -1.0f)};  // -C_x(a) = u_x - a
     const df64 ncy[3] = {add_f(uy, 1.0f), uy, add_f(uy, -1.0f)};  // -C_y(b)
     const df64 dyx2 = uy2 - ux2;
     const df64 A1 = c.k1 * fma(rho, dyx2, Dxy);   // omega' K1
@@ -305,23 +386,33 @@ __device__ __forceinline__ void collide_df(df64 (&f)[9], const Coef<df64>& c, Si
         cor[8] = cor[6];
       }
     }
-    // f*_(a,b) = P_y(b) [E(a) + C_y(b) (G(a) - B(a) C_y(b))] + omega' Psi_(a,b)
-    df64 E[3], B[3], G[3];
+    // f*_(a,b) = P_y(b) [E(a) + C_y(b) (G(a) - B(a) C_y(b))] + omega' Psi_(a,b),
+    // E(a) = P_x(a) (rho + A1 C_x(a)^2), B(a) = A1 P_x(a), G(a) = -nA2 P_x(a) C_x(a).
+    // Column a = 0 in scalar arithmetic; the columns a = -1 and a = +1 as pairs
+    // (lane 0: a = -1, lane 1: a = +1) that share each row's P_y(b), C_y(b).
+    const df64 B0 = A1 * px[1];
+    const df64 G0 = nA2 * (px[1] * ux);
+    const df64 E0 = fma(B0, ux2, rho * px[1]);  // C_x(0)^2 = u_x^2
+    const dw2 NCX = add_c(bcast(ux), make_float2(1.0f, -1.0f));                                   // u_x - a
+    const dw2 PX = scaled_c(bcast(wx) + scaled_c(bcast(ux), make_float2(-1.0f, 1.0f)), make_float2(0.5f, 0.5f));
+    const dw2 B2 = bcast(A1) * PX;
+    const dw2 G2 = bcast(nA2) * (PX * NCX);
+    const dw2 E2 = fma(B2, NCX * NCX, bcast(rho) * PX);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      B[k] = A1 * px[k];
-      G[k] = nA2 * (px[k] * ncx[k]);
-      E[k] = fma(B[k], k == 1 ? ux2 : ncx[k] * ncx[k], rho * px[k]);
-    }
-#pragma unroll
-    for (int a = -1; a <= 1; ++a)
-#pragma unroll
-      for (int b = -1; b <= 1; ++b) {
-        const int i = pop_index(a, b);
-        const df64 inner = fma(B[a + 1], ncy[b + 1], G[a + 1]);  // G(a) - B(a) C_y(b)
-        const df64 t = fma(-ncy[b + 1], inner, E[a + 1]);
-        f[i] = has_correction<MODEL>(i) ? fma(py[b + 1], t, cor[i]) : py[b + 1] * t;
+    for (int b = -1; b <= 1; ++b) {
+      const int i0 = pop_index(0, b), im = pop_index(-1, b), ip = pop_index(1, b);
+      {
+        const df64 inner = fma(B0, ncy[b + 1], G0);  // G(0) - B(0) C_y(b)
+        const df64 t = fma(-ncy[b + 1], inner, E0);
+        out(i0, has_correction<MODEL>(i0) ? fma(py[b + 1], t, cor[i0]) : py[b + 1] * t);
       }
+      const dw2 NCY = bcast(ncy[b + 1]);
+      const dw2 inner = fma(B2, NCY, G2);
+      const dw2 t = fnma(NCY, inner, E2);
+      const dw2 F = has_correction<MODEL>(im) ? fma(bcast(py[b + 1]), t, pair(cor[im], cor[ip])) : bcast(py[b + 1]) * t;
+      out(im, lane0(F));
+      out(ip, lane1(F));
+    }
   }
 }
 

@@ -27,10 +27,18 @@ constexpr int kBY = 8;   // rows per block of the auxiliary kernels
 constexpr int kNT = kBX * kBY;
 constexpr int kNDiag = 5;  // partial sums per block: m0, jx, jy, ke, non-finite nodes
 constexpr int kDiagRows = 8;  // rows per thread of the diagnostics kernel (one block reduction per 8 nodes)
-#ifndef OLBM_DF_JOIN_FP64
-#define OLBM_DF_JOIN_FP64 0
+#ifndef OLBM_DF_JOIN
+#define OLBM_DF_JOIN 2
 #endif
-constexpr int kDfJoinFp64 = OLBM_DF_JOIN_FP64;  // double-word form: populations joined on the FP64 pipe alone
+// Double-word form: how a post-collision population is joined into FP64.
+// 0: hi widened with integer instructions, lo converted on the FP64 pipe, both
+// added there (two FP64-pipe instructions); 1: both converted on the FP64 pipe
+// (three); 2: both widened with integer instructions and added on the FP64 pipe
+// (one). With the collision's populations paired on the FP32 pipe, the FP64
+// pipe is the first to fill: complete model at 4096^2, diagnostics every step,
+// 96 registers: 24.2 GLUPS with 0 (FP64 pipe 68 % busy, warps waiting on it),
+// 25.2 with 2.
+constexpr int kDfJoin = OLBM_DF_JOIN;
 
 // Source offsets of the pull f_i(x) = B_i(x - c_i) inside one plane.
 __device__ __forceinline__ void pull_offsets(int x, int y, const Geometry& g, long long (&o)[9]) {
@@ -272,15 +280,15 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
         // r is free once split: the next row's loads go into it and are in
         // flight during this row's collision (no second set of registers).
         if ((k + 1 < rows) && (y + dy < g.ny)) Raw::pull(src, g, x, xm, xp, y + dy, r);
-        collide_df<MODEL>(f, c, [&](const NodeMoments<df64>& m) {
-          if constexpr (DIAG) acc.add(m);
-        });
         S* q = dst + (long long)y * g.pitch + x;
-        // The first kDfJoinFp64 populations are joined entirely on the FP64
-        // pipe (three FP64 instructions), the others with hi widened by integer
-        // instructions (two FP64 instructions and five integer ones).
-#pragma unroll
-        for (int i = 0; i < 9; ++i) q[i * g.plane] = i < kDfJoinFp64 ? join_f64_fp64pipe(f[i]) : join_f64(f[i]);
+        collide_df<MODEL>(
+            f, c,
+            [&](const NodeMoments<df64>& m) {
+              if constexpr (DIAG) acc.add(m);
+            },
+            [&](int i, df64 v) {
+              q[i * g.plane] = kDfJoin == 2 ? join_f64_int(v) : (kDfJoin == 1 ? join_f64_fp64pipe(v) : join_f64(v));
+            });
       }
       return;
     }
@@ -337,12 +345,12 @@ __global__ void __launch_bounds__(512) step_kernel(const typename Form<PREC>::S*
 }
 
 // Double-word form (3): launched with at most 256 threads a block and capped
-// at 80 registers a thread, six blocks of 128 threads per SM. The complete
-// model with fused diagnostics compiles to 100 registers uncapped (four blocks
-// per SM: 22.5 GLUPS at 4096^2) and to 80, 88 and 96 without spills (23.5,
-// 23.2 and 21.2 GLUPS; 96 registers still allow only five blocks).
+// at 96 registers a thread, five blocks of 128 threads per SM. The complete
+// model with fused diagnostics at 4096^2 (integer join): 80, 88 and 96
+// registers give 24.7, 25.0 and 25.2 GLUPS (80 spills 48 bytes); uncapped it
+// takes more than 100 registers and four blocks per SM.
 #ifndef OLBM_DF_MAXNREG
-#define OLBM_DF_MAXNREG 80
+#define OLBM_DF_MAXNREG 96
 #endif
 template <int MODEL, bool DIAG, bool PAIRS>
 __global__ void __maxnreg__(OLBM_DF_MAXNREG) step_kernel_df(const double* __restrict__ src, double* __restrict__ dst,
