@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "lbm_device.cuh"
 #include "lbm_df64.cuh"
@@ -378,7 +379,13 @@ namespace olbm {
 
 // Pipeline shapes per storage form: consumer threads (node pairs; FP64: single
 // nodes) and ring slots.
-constexpr int kStreamNC32 = 128, kStreamNC16 = 256, kStreamStages = 8;
+#ifndef OLBM_STREAM_NC16
+#define OLBM_STREAM_NC16 256
+#endif
+#ifndef OLBM_STREAM_STAGES
+#define OLBM_STREAM_STAGES 8
+#endif
+constexpr int kStreamNC32 = 128, kStreamNC16 = OLBM_STREAM_NC16, kStreamStages = OLBM_STREAM_STAGES;
 constexpr int kStreamNC64 = 128, kStreamStages64 = 4;
 inline int stream_width(int prec) {
   return prec == 0 ? kStreamNC64 : 2 * (prec == 1 ? kStreamNC32 : kStreamNC16);
@@ -542,6 +549,28 @@ inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   return dim3((g.nx + cols - 1) / cols, (g.ny + k.by * k.rows - 1) / (k.by * k.rows));
 }
 
+// Launch of a pipeline step kernel with programmatic stream serialisation (see
+// pdl_wait): the grid may be scheduled while the previous kernel of the stream
+// finishes. OLBM_PDL=0 launches it as an ordinary stream-ordered kernel.
+#ifndef OLBM_PDL
+#define OLBM_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_step_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = OLBM_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <int PREC> struct Launch {
   using S = typename Form<PREC>::S;
   using T = typename Form<PREC>::T;
@@ -613,14 +642,11 @@ template <int PREC> struct Launch {
     if (a.parts_used) *a.parts_used = (long long)grid.x * grid.y;
     const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
     if (a.cfg.bx == 0)
-      kernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
-                                                       a.err);
-    else if (a.err == nullptr || a.sched == nullptr)
-      return cudaErrorInvalidValue;
-    else
-      pkernel<<<grid, NC + 32, Shape::kSmemBytes, st>>>((const S*)a.src, (S*)a.dst, a.g, c, a.partials, a.cfg.rows,
-                                                        a.err, a.sched);
-    return cudaGetLastError();
+      return launch_step_kernel(kernel, grid, dim3(NC + 32), Shape::kSmemBytes, st, (const S*)a.src, (S*)a.dst, a.g,
+                                c, a.partials, a.cfg.rows, a.err);
+    if (a.err == nullptr || a.sched == nullptr) return cudaErrorInvalidValue;
+    return launch_step_kernel(pkernel, grid, dim3(NC + 32), Shape::kSmemBytes, st, (const S*)a.src, (S*)a.dst, a.g, c,
+                              a.partials, a.cfg.rows, a.err, a.sched);
   }
 
   // FP64 pipeline (launch kind 1, one CTA per tile).
@@ -632,9 +658,9 @@ template <int PREC> struct Launch {
     const dim3 grid = step_grid(a.g, a.cfg, 0);
     if (a.parts_used) *a.parts_used = (long long)grid.x * grid.y;
     const Coef<double> c = make_coef<double>(a.theta, a.tau, a.rho_ref);
-    step_stream_f64_kernel<MODEL, DIAG, kStreamNC64, kStreamStages64><<<grid, kStreamNC64 + 32, Shape::kSmemBytes, st>>>(
-        (const double*)a.src, (double*)a.dst, a.g, c, a.partials, a.cfg.rows, a.err);
-    return cudaGetLastError();
+    return launch_step_kernel(step_stream_f64_kernel<MODEL, DIAG, kStreamNC64, kStreamStages64>, grid,
+                              dim3(kStreamNC64 + 32), Shape::kSmemBytes, st, (const double*)a.src, (double*)a.dst,
+                              a.g, c, a.partials, a.cfg.rows, a.err);
   }
 
   template <int MODEL>

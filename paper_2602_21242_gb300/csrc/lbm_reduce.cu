@@ -24,7 +24,10 @@ int stream_tile_width(int prec) { return stream_width(prec); }
 
 // The ring fits three times in an SM's shared memory for both shifted forms;
 // FP16 is compiled for three CTAs (registers), FP32 (160 threads) fits them.
-int stream_ctas_per_sm(int) { return 3; }
+#ifndef OLBM_STREAM_CTAS
+#define OLBM_STREAM_CTAS 3
+#endif
+int stream_ctas_per_sm(int) { return OLBM_STREAM_CTAS; }
 
 // Fixed-order final sum of the block partials: out[0..4] as in lbm_diagnostics
 // (mass gets rho_ref for every finite node), out[5] = t; non-finite nodes are

@@ -69,6 +69,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Programmatic dependent launch (sm_90 and later). A step kernel launched with
+// the programmatic-serialization attribute may be scheduled while the previous
+// kernel of its stream is finishing; every CTA of a step kernel signals at its
+// start that the next grid may launch (launch_dependents), and the next grid's
+// producer waits for the previous grid to complete, its writes visible, before
+// it reads anything that grid wrote (griddepcontrol.wait, a no-op for a kernel
+// launched without the attribute). The consumers touch global memory only
+// after the producer's copies, so they follow the wait. What overlaps is the
+// next grid's launch and set-up (CTA placement, mbarrier initialisation) with
+// the previous grid's last CTAs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Grid barrier with bounded waits. count/gen/err live in device memory zeroed
 // before the launch. Returns false (in every thread of the block) once any
 // block has given up.
@@ -126,7 +139,12 @@ __device__ __forceinline__ f32x2 lds_two(const __half* p0, const __half* p1) {
 // times in the register file (NC = 256: the ring then also fits three times).
 // Without the bound the FP16 form's diagnostics variant took 78 registers and
 // ran two CTAs a SM (measured at 4096^2: 113.7 GLUPS, against 118.8 with it).
-template <int NC> constexpr int stream_min_blocks() { return (NC + 32) * 3 * 72 <= 65536 && NC >= 256 ? 3 : 1; }
+#ifndef OLBM_STREAM_MINB256
+#define OLBM_STREAM_MINB256 3
+#endif
+template <int NC> constexpr int stream_min_blocks() {
+  return (NC + 32) * 3 * 72 <= 65536 && NC >= 256 ? OLBM_STREAM_MINB256 : 1;
+}
 
 // Shared-memory footprint of the ring (bytes).
 template <int PREC, int NC, int STAGES> struct StreamShape {
@@ -251,19 +269,29 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
   template <int MODEL, bool DIAG>
   __device__ __forceinline__ bool consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
                                           int y0, int rows, int t, int lane, DiagAcc<f32x2>& acc, int* err) {
+    // A full strip (one row a slot, every consumer thread a whole pair) takes a
+    // path without the per-pair tests of partial strips.
     const TilePlan<CH> p(g, x0, W, SEG);
-    const int ppr = (p.w + 1) / 2;  // pairs per row
-    const int j = t / ppr;
+    if (p.w == W && p.R == 1) return consume_tile<MODEL, DIAG, true>(dst, g, c, p, x0, y0, rows, t, lane, acc, err);
+    return consume_tile<MODEL, DIAG, false>(dst, g, c, p, x0, y0, rows, t, lane, acc, err);
+  }
+
+  template <int MODEL, bool DIAG, bool FULL>
+  __device__ __forceinline__ bool consume_tile(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c,
+                                               const TilePlan<CH>& p, int x0, int y0, int rows, int t, int lane,
+                                               DiagAcc<f32x2>& acc, int* err) {
+    const int ppr = FULL ? NC : (p.w + 1) / 2;  // pairs per row
+    const int j = FULL ? 0 : t / ppr;
     const int xl = 2 * (t - j * ppr);
-    const bool whole = xl + 1 < p.w;  // both nodes of the pair lie in the strip
+    const bool whole = FULL || xl + 1 < p.w;  // both nodes of the pair lie in the strip
     // segment elements of the pair's nodes and of their x -+ 1 neighbours
     const int base = j * p.sub;
     const int iM = base + CH + xl;
     const int iL = xl == 0 ? base + p.lidx : iM - 1;
     const int iR0 = whole ? iM + 1 : base + CH + p.wr;
     const int iR1 = xl + 2 < p.w ? iM + 2 : base + CH + p.wr;
-    for (int r0 = 0; r0 < rows; r0 += p.R, ++k) {
-      const bool active = j < min(p.R, rows - r0);
+    for (int r0 = 0; r0 < rows; r0 += (FULL ? 1 : p.R), ++k) {
+      const bool active = FULL || j < min(p.R, rows - r0);
       const int s = k % STAGES;
       if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err))) return false;
       const S* slot = ring + (size_t)s * 9 * SEG;
@@ -372,11 +400,13 @@ __global__ void __launch_bounds__(NC + 32, stream_min_blocks<NC>()) step_stream_
   P pipe(smem);
   pipe.init();
   __syncthreads();
+  pdl_launch_dependents();
   const int nstrips = (g.nx + P::W - 1) / P::W;
   const int ntiles = nstrips * ((g.ny + H - 1) / H);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DiagAcc<f32x2> acc;
   if (warp == P::kConsumerWarps) {
+    pdl_wait();  // the tile counter and src belong to the previous step until it completes
     for (;;) {
       int tile = 0;
       if (lane == 0) tile = atomicAdd(&sched[0], 1);
@@ -436,11 +466,13 @@ __global__ void __launch_bounds__(NC + 32, stream_min_blocks<NC>()) step_stream_
   P pipe(smem);
   pipe.init();
   __syncthreads();
+  pdl_launch_dependents();
   const int x0 = blockIdx.x * P::W, y0 = blockIdx.y * H;
   const int rows = min(H, g.ny - y0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DiagAcc<f32x2> acc;
   if (warp == P::kConsumerWarps) {
+    pdl_wait();
     pipe.produce(src, g, x0, y0, rows, lane, err);
     pipe.drain(err);
   } else if (threadIdx.x < NC) {
@@ -461,11 +493,13 @@ __global__ void __launch_bounds__(NC + 32, 4) step_stream_f64_kernel(const doubl
   P pipe(smem);
   pipe.init();
   __syncthreads();
+  pdl_launch_dependents();
   const int x0 = blockIdx.x * P::W, y0 = blockIdx.y * H;
   const int rows = min(H, g.ny - y0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DiagAcc<double> acc;
   if (warp == P::kConsumerWarps) {
+    pdl_wait();
     pipe.produce(src, g, x0, y0, rows, lane, err);
     pipe.drain(err);
   } else if (threadIdx.x < NC) {
