@@ -33,6 +33,43 @@ def bound(prec, d, steps=STEPS):
     return steps * (2.0 ** -24 * 16 * d if prec == "f32" else 2.0 ** -11 * d)
 
 
+U32 = 2.0 ** -24
+
+
+def rows_per_thread(lat, prec):
+    """Most nodes (or node pairs) one thread of the step kernel accumulates into its FP32 diagnostics
+    sums under the lattice's launch: `rows` for the column kernel and one CTA per tile; for a
+    persistent grid a CTA may take every tile, so rows x tiles."""
+    from paper_2602_21242_gb300 import capi
+    kind, bx, _, rows = capi.lbm_get_launch_ex(lat.ctx)
+    if kind == 1 and bx > 0:
+        width = 256 if prec == "f32" else 512
+        return rows * (-(-lat.nx // width)) * (-(-lat.ny // rows))
+    return rows
+
+
+def diag_sum_bound(state, theta, h_rows):
+    """Derived bound on the error of the shifted forms' fused diagnostics of the pre-collision state
+    `state` (9, ny, nx): FP32 sums inside a thread block, FP64 across blocks.
+
+    For a floating-point sum whose longest chain of additions has h roundings, |fl(S) - S| is at
+    most h u sum_i |x_i| to first order (u = 2^-24 for FP32). The chains here: a node's moment
+    (m0: 4 additions; j: 3; twice the kinetic energy j.u: j, the FP32 reciprocal of rho and the
+    products, 8), the thread's accumulation over its h_rows rows (two roundings a row for m0 and j,
+    the pair's sum and the running sum; four for the energy's chained FMAs), the warp's xor
+    butterfly (5) and thread 0's sum of up to 16 warp totals (15). The FP64 sum across blocks adds
+    at most 2^-53 of the total. Returns the bounds for (mass, momentum x, momentum y, energy)."""
+    dev = state - rest_state(theta)[:, None, None]
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])[:, None, None]
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])[:, None, None]
+    m0, jx, jy = dev.sum(0), (cx * dev).sum(0), (cy * dev).sum(0)
+    ke = 0.5 * (jx * jx + jy * jy) / state.sum(0)
+    h = np.array([4 + 2 * h_rows + 20, 3 + 2 * h_rows + 20, 3 + 2 * h_rows + 20, 8 + 4 * h_rows + 20])
+    sums = np.array([np.abs(m0).sum(), np.abs(jx).sum(), np.abs(jy).sum(), np.abs(ke).sum()])
+    totals = np.abs(np.array([state.sum(), jx.sum(), jy.sum(), ke.sum()]))
+    return h * U32 * sums + 2.0 ** -53 * totals
+
+
 def run_form(f0, theta, tau, model, prec, steps=STEPS):
     _, ny, nx = f0.shape
     with Lattice(nx, ny, theta, tau, model, prec) as lat:
@@ -103,13 +140,47 @@ def test_forms_diagnostics(oracle, prec):
         st = lat.state().cpu().numpy()
         lat.step(1)  # fused pass at t = STEPS
         fused, t, status = lat.step_diagnostics()
+        h_rows = rows_per_thread(lat, prec)
     assert t == STEPS and status == 0
     ref = oracle.diagnostics(st)
-    # fused sums (FP32 within a block for the shifted forms, FP64 across blocks)
-    np.testing.assert_allclose(fused[0], ref[0], rtol=1e-9)
-    np.testing.assert_allclose(fused[1:4], ref[1:4], rtol=1e-5, atol=1e-5)
+    # fused sums (FP32 within a block for the shifted forms, FP64 across blocks): the derived bound
+    err = np.abs(np.asarray(fused[:4]) - ref[:4])
+    assert (err <= diag_sum_bound(st, theta, h_rows)).all(), (err, diag_sum_bound(st, theta, h_rows))
     drift = abs(ref[0] - oracle.diagnostics(f0)[0]) / ref[0]
     assert drift <= (1e-8 if prec == "f32" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("launch", [None, (1, 0, 1, 24), (0, 128, 4, 16)])
+def test_fused_sums_against_fp64_sums_of_the_same_state(prec, launch):
+    """Separates the two errors in the shifted forms' mass drift. The fused pass sums in FP32
+    inside a block; lbm_diagnostics sums the same stored state in FP64 per node. Their
+    difference is the reduction error alone and stays within the derived bound; the FP64 sums'
+    change over the run is the storage rounding's drift (rounding a stored deviation does not
+    conserve mass), reported by the FP64 path, not the reduction."""
+    from paper_2602_21242_gb300 import capi
+    n, theta, steps = 256, 0.3, 200
+    rho, ux, uy = flows.shear_layer(n, n, U=0.1, width=n / 16)
+    with Lattice(n, n, theta, 0.50333, "complete", prec) as lat:
+        if launch is not None:
+            capi.lbm_set_launch_ex(lat.ctx, *launch)
+        lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+        m_init = lat.diagnostics()[0]
+        lat.step(steps - 1)
+        st = lat.state().cpu().numpy()
+        exact = lat.diagnostics()  # FP64 per-node sums of the stored state at t = steps - 1
+        lat.set_diagnostics_interval(1)
+        lat.step(1)  # fused pass over the same state
+        fused, t, status = lat.step_diagnostics()
+        h_rows = rows_per_thread(lat, prec)
+    assert t == steps - 1 and status == 0
+    err = np.abs(np.asarray(fused[:4]) - np.asarray(exact[:4]))
+    assert (err <= diag_sum_bound(st, theta, h_rows)).all(), (err, diag_sum_bound(st, theta, h_rows))
+    # the storage drift is what the FP64 sums see: each step rounds the nine stored deviations of
+    # every node once, at most half an ulp each (2^-24 or 2^-11 of a deviation of at most d)
+    d = np.abs(st - rest_state(theta)[:, None, None]).max()
+    drift = abs(exact[0] - m_init) / (n * n)
+    assert drift <= steps * 9 * (U32 if prec == "f32" else 2.0 ** -11) * d
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
@@ -123,7 +194,7 @@ def test_pipeline_kernel_matches_column_kernel(prec, nx, ny, rows, ctas, model):
     both one CTA per tile (ctas = 0) and persistent grids (ctas CTAs per SM)."""
     theta, tau = 0.33, 0.7
     f0 = flows.random_populations(nx, ny, seed=900 + nx + ny, spread=0.1)
-    out = {}
+    out, h_rows = {}, {}
     for kind in (0, 1):
         with Lattice(nx, ny, theta, tau, model, prec) as lat:
             from paper_2602_21242_gb300 import capi
@@ -133,13 +204,18 @@ def test_pipeline_kernel_matches_column_kernel(prec, nx, ny, rows, ctas, model):
             else:
                 capi.lbm_set_launch_ex(lat.ctx, 0, 128, 4, 16)
             lat.set_state(torch.from_numpy(f0).cuda())
+            lat.step(5)
+            prev = lat.state().cpu().numpy()
             lat.set_diagnostics_interval(1)
-            lat.step(6)
+            lat.step(1)
             lat.sync()
             d, t, _ = lat.step_diagnostics()
             out[kind] = (lat.state().cpu().numpy(), np.array(d))
+            h_rows[kind] = rows_per_thread(lat, prec)
     np.testing.assert_array_equal(out[1][0], out[0][0])
-    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-6, atol=1e-6)
+    # two FP32 summation orders of the same state: each within its derived bound of the exact sums
+    both = diag_sum_bound(prev, theta, h_rows[0]) + diag_sum_bound(prev, theta, h_rows[1])
+    assert (np.abs(out[1][1][:4] - out[0][1][:4]) <= both).all()
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
@@ -163,11 +239,13 @@ def test_pipeline_kernel_any_width(oracle, prec, nx, ny, rows, ctas):
         lat.step(1)
         out, t, _ = lat.step_diagnostics()
         got = lat.state().cpu().numpy()
+        h_rows = rows_per_thread(lat, prec)
     ref = oracle.run(f0, theta, tau, 3, steps)
     assert np.abs(got - ref).max() <= bound(prec, d, steps)
     # the fused pass reduces f(steps - 1): FP32 sums of deviations inside a block, FP64 across blocks
     assert t == steps - 1
-    np.testing.assert_allclose(out[:4], oracle.diagnostics(prev)[:4], rtol=1e-5, atol=1e-5)
+    err = np.abs(np.asarray(out[:4]) - oracle.diagnostics(prev)[:4])
+    assert (err <= diag_sum_bound(prev, theta, h_rows)).all(), (err, diag_sum_bound(prev, theta, h_rows))
     assert out[4] == 0
 
 
