@@ -28,7 +28,7 @@ _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LBGK, OREG, OREG_PARTIAL, OREG_COMPLETE, OREG_COMPLETE_NEQ = 0, 1, 2, 3, 4
+LBGK, OREG, OREG_PARTIAL, OREG_COMPLETE, OREG_COMPLETE_NEQ, LBGK_POLY = 0, 1, 2, 3, 4, 5
 NO_COLLISION = -1  # test hook: streaming only
 
 # D2Q9 velocities, Fig. 1a numbering (the oracle's own copy).

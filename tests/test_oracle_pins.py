@@ -188,7 +188,7 @@ def test_pref_and_pitilde_closed_forms(oracle, theta):
 
 # --------------------------------------------------------------------------- collision (Eq. 1a)
 
-@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("theta", THETAS)
 def test_collision_conservation(oracle, model, theta):
     """Mass is conserved by every model; momentum by LBGK, partial and complete; the uncorrected
@@ -243,6 +243,67 @@ def test_lbgk_is_bgk_relaxation(oracle):
         rho, ux, uy, *_ = moments_np(f)
         feq = oracle.geq(rho, ux, uy, 0.35)
         np.testing.assert_allclose(oracle.collide_node(f, 0.35, 0.9, 0), f + (feq - f) / 0.9, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------- LBGK, second reading (model 5)
+
+def _poly_equilibrium(oracle, f, theta):
+    """The equilibrium model 5 relaxes to, read off the collision itself: with tau = 1 the
+    collision returns f^eq of f's moments (Eq. 1a with 1 - 1/tau = 0)."""
+    return oracle.collide_node(f, theta, 1.0, 5)
+
+
+def test_poly_lbgk_is_the_textbook_d2q9_equilibrium_at_one_third(oracle):
+    """At theta = 1/3 the second reading's equilibrium is the textbook D2Q9 one,
+    w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2) with w = 4/9, 1/9, 1/36."""
+    w = np.array([16, 4, 4, 4, 4, 1, 1, 1, 1]) / 36.0
+    g = flows.rng(23)
+    for _ in range(10):
+        f = random_node(g, 1.0 / 3.0)
+        rho, ux, uy, *_ = moments_np(f)
+        cu = CX * ux + CY * uy
+        textbook = w * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
+        np.testing.assert_allclose(_poly_equilibrium(oracle, f, 1.0 / 3.0), textbook, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("theta", THETAS + [0.6])
+def test_poly_lbgk_equilibrium_moments(oracle, theta):
+    """Moments of the polynomial equilibrium with the rest weights W(0) = 1 - theta, W(+-1) = theta/2:
+    sum f^eq = rho, sum c f^eq = rho u, sum c_x c_y f^eq = rho u_x u_y exactly, but, since c^4 = c^2
+    on D2Q9 (sum_a W(a) a^4 = theta, not the continuum's 3 theta^2), sum c_x^2 f^eq =
+    rho (theta + u_x^2 (1 - theta) / (2 theta)): the GEq's rho (theta + u_x^2) only at theta = 1/3."""
+    g = flows.rng(29)
+    for _ in range(10):
+        f = random_node(g, theta, spread=0.2)
+        rho, ux, uy, *_ = moments_np(f)
+        feq = _poly_equilibrium(oracle, f, theta)
+        r, vx, vy, pxx, pyy, pxy = moments_np(feq)
+        np.testing.assert_allclose([r, vx, vy], [rho, ux, uy], rtol=1e-14, atol=1e-16)
+        np.testing.assert_allclose(pxy, rho * ux * uy, rtol=1e-13, atol=1e-16)
+        np.testing.assert_allclose(pxx, rho * (theta + ux * ux * (1 - theta) / (2 * theta)), rtol=1e-14)
+        np.testing.assert_allclose(pyy, rho * (theta + uy * uy * (1 - theta) / (2 * theta)), rtol=1e-14)
+
+
+def test_poly_and_guided_equilibria_differ_at_third_order(oracle):
+    """At theta = 1/3 the two readings of the LBGK equilibrium agree to second order in u: their
+    difference scales as u^3 (halving u divides it by 8 up to the next order)."""
+    prev = None
+    for u in (0.08, 0.04, 0.02):
+        f = oracle.geq(1.0, u, -0.7 * u, 1.0 / 3.0)
+        d = np.abs(_poly_equilibrium(oracle, f, 1.0 / 3.0) - f).max()
+        if prev is not None:
+            assert 7.0 < prev / d < 9.0
+        prev = d
+
+
+def test_poly_lbgk_fixed_point_and_relaxation(oracle):
+    """Model 5 is f* = f + (f^eq - f)/tau with its own f^eq, so that f^eq is a fixed point."""
+    g = flows.rng(31)
+    for theta in THETAS:
+        f = random_node(g, theta)
+        feq = _poly_equilibrium(oracle, f, theta)
+        np.testing.assert_allclose(oracle.collide_node(f, theta, 0.9, 5), f + (feq - f) / 0.9, rtol=1e-14)
+        np.testing.assert_allclose(oracle.collide_node(feq, theta, 0.57, 5), feq, rtol=0, atol=1e-15)
 
 
 # --------------------------------------------------------------------------- streaming (Eq. 1b)
