@@ -614,8 +614,10 @@ def precision_study(args):
 
 
 def paper_experiments(args):
-    """Sec. 5.1: nu~/nu of the rotated decaying shear wave (N = 200, nu = 1e-3, 1200 steps) for the four
-    models, theta in {0.25, 1/3, 0.4, 0.5}, Ma = 0.1 .. 1.0 (0 = the run became non-finite).
+    """Sec. 5.1: nu~/nu of the rotated decaying shear wave (N = 200, nu = 1e-3, 1200 steps) for every
+    model (with both readings of the LBGK equilibrium), theta in {0.25, 1/3, 0.4, 0.5}, Ma = 0.1 .. 1.0
+    (0 = the run became non-finite), for the wave along y on a column and along the lattice diagonal,
+    and for two fitting windows.
     Sec. 5.3: the doubly periodic shear layer (kappa = 80, delta = 0.05, u0 = 0.04, Re = 3e4) to one
     turnover time for N in {128, 256, 512}, theta in {0.4, 0.6}: whether each model stays finite.
     Sec. 5.2: the isothermal shocktube (800 x 1, bounce-back walls, 400 steps) at (theta, nu) =
@@ -628,22 +630,29 @@ def paper_experiments(args):
     torch.cuda.set_device(0)
     models = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
     mas = [round(0.1 * k, 1) for k in range(1, 11)]
+    # two orientations of the wave, both readings of the LBGK equilibrium (GEq and the polynomial one),
+    # and two fitting windows of nu~ (the default t = 200 .. 1200 and a later one, t = 600 .. 1200)
     table = {}
-    for theta in (0.25, 1.0 / 3.0, 0.4, 0.5):
-        for model in models:
-            table[f"{model}/theta={theta:.3f}"] = [
-                round(experiments.rotated_shear_wave_viscosity(model, theta, ma), 4) for ma in mas]
+    for orientation in ("axis", "diagonal"):
+        for t_fit in (200, 600):
+            for theta in (0.25, 1.0 / 3.0, 0.4, 0.5):
+                for model in models + ["lbgk_poly"]:
+                    if t_fit != 200 and model not in ("lbgk", "lbgk_poly", "oreg"):
+                        continue
+                    table[f"{orientation}/t_fit={t_fit}/{model}/theta={theta:.3f}"] = [
+                        round(experiments.rotated_shear_wave_viscosity(model, theta, ma, t_fit=t_fit,
+                                                                       orientation=orientation), 4) for ma in mas]
     layer = {}
     for theta in (0.4, 0.6):
         for n in (128, 256, 512):
-            for model in models:
+            for model in models + ["lbgk_poly"]:
                 finite, steps, w = experiments.shear_layer_run(model, theta, n)
                 layer[f"{model}/theta={theta}/N={n}"] = {
                     "finite": finite, "steps": steps,
                     "max_abs_vorticity": None if w is None else float(abs(w).max())}
     tube = {}
     for theta, nu in ((0.4, 1e-12), (0.55, 1e-9)):
-        for model in models:
+        for model in models + ["lbgk_poly"]:
             r = experiments.shocktube_run(model, theta, nu)
             entry = {"finite": r["finite"]}
             if r["finite"]:

@@ -16,6 +16,12 @@
  *   LBM_OREG_COMPLETE_NEQ  as LBM_OREG_COMPLETE with Eq. 12's strain estimate taken
  *                      from f^neq instead of f^OReg (pref = -N_d / (2 theta^2)), with
  *                      which the corrected stress equals Pi^NS exactly (Eq. 7)
+ *   LBM_LBGK_POLY      g = f - f^eq with f^eq the second-order polynomial equilibrium
+ *                      rho w_i [1 + c.u/theta + ((c.u)^2 - theta u^2)/(2 theta^2)],
+ *                      w_i = W(c_ix) W(c_iy), W(0) = 1 - theta, W(+-1) = theta/2: a second
+ *                      reading of Sec. 5.1's "standard Lattice-BGK" (the paper does not
+ *                      print its equilibrium); at theta = 1/3 the textbook D2Q9 BGK. Not
+ *                      differentiable through lbm_vjp (LBM_EINVAL).
  *
  * Conventions shared by every call:
  *   - Fields are row-major [y][x] (x fastest), nx * ny doubles, unpadded.
@@ -44,13 +50,15 @@ extern "C" {
 
 typedef struct lbm_ctx lbm_ctx;
 
-/* Collision models (Sec. 4; model 4 is the f^neq variant of Eq. 12's prefactor). */
+/* Collision models (Sec. 4; model 4 is the f^neq variant of Eq. 12's prefactor,
+ * model 5 the polynomial-equilibrium reading of Sec. 5.1's LBGK). */
 enum lbm_model {
   LBM_LBGK = 0,
   LBM_OREG = 1,
   LBM_OREG_PARTIAL = 2,
   LBM_OREG_COMPLETE = 3,
-  LBM_OREG_COMPLETE_NEQ = 4
+  LBM_OREG_COMPLETE_NEQ = 4,
+  LBM_LBGK_POLY = 5
 };
 
 /* Storage / arithmetic forms.

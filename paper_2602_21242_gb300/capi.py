@@ -14,14 +14,14 @@ import numpy as np
 
 from . import build as _build
 
-LBM_LBGK, LBM_OREG, LBM_OREG_PARTIAL, LBM_OREG_COMPLETE, LBM_OREG_COMPLETE_NEQ = 0, 1, 2, 3, 4
+LBM_LBGK, LBM_OREG, LBM_OREG_PARTIAL, LBM_OREG_COMPLETE, LBM_OREG_COMPLETE_NEQ, LBM_LBGK_POLY = 0, 1, 2, 3, 4, 5
 LBM_F64, LBM_F32_SHIFT, LBM_F16_SHIFT, LBM_F64_DF = 0, 1, 2, 3
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_ENONFINITE",
                 -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 MODELS = {"lbgk": LBM_LBGK, "oreg": LBM_OREG, "partial": LBM_OREG_PARTIAL, "complete": LBM_OREG_COMPLETE,
-          "complete_neq": LBM_OREG_COMPLETE_NEQ}
+          "complete_neq": LBM_OREG_COMPLETE_NEQ, "lbgk_poly": LBM_LBGK_POLY}
 PRECS = {"f64": LBM_F64, "f32": LBM_F32_SHIFT, "f16": LBM_F16_SHIFT, "f64df": LBM_F64_DF}
 
 _lock = threading.Lock()

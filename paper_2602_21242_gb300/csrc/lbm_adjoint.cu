@@ -288,6 +288,8 @@ extern "C" int lbm_vjp_forward(lbm_ctx* c, int n, int ckpt_every, const double* 
   if (!d_rho0 || !d_ux0 || !d_uy0) return vfail(c, LBM_EINVAL, "lbm_vjp_forward: NULL initial field");
   if (c->prec == LBM_F16_SHIFT)
     return vfail(c, LBM_EINVAL, "lbm_vjp_forward: storage forms LBM_F64, LBM_F64_DF and LBM_F32_SHIFT only");
+  if (c->model > LBM_OREG_COMPLETE_NEQ)
+    return vfail(c, LBM_EINVAL, "lbm_vjp_forward: no adjoint for LBM_LBGK_POLY");
   VjpLayout L;
   int s = vjp_layout(c, n, ckpt_every, L);
   if (s != LBM_OK) return s;
@@ -306,6 +308,7 @@ extern "C" int lbm_vjp_ex(lbm_ctx* c, int n, int ckpt_every, const double* d_rho
   if (flags & ~LBM_VJP_REUSE_FORWARD) return vfail(c, LBM_EINVAL, "lbm_vjp_ex: unknown flags");
   if (c->prec == LBM_F16_SHIFT)
     return vfail(c, LBM_EINVAL, "lbm_vjp: storage forms LBM_F64, LBM_F64_DF and LBM_F32_SHIFT only");
+  if (c->model > LBM_OREG_COMPLETE_NEQ) return vfail(c, LBM_EINVAL, "lbm_vjp: no adjoint for LBM_LBGK_POLY");
   VjpLayout L;
   int s;
   if (flags & LBM_VJP_REUSE_FORWARD) {

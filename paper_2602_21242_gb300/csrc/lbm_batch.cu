@@ -289,7 +289,7 @@ extern "C" {
 int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, const double* tau, int model,
                      int prec, void* stream, lbm_batch** out) {
   if (!out || n < 1 || !nx || !ny || !theta || !tau) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: bad arguments");
-  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ) return bfail(nullptr, LBM_EINVAL, "unknown model %d", model);
+  if (model < LBM_LBGK || model > LBM_LBGK_POLY) return bfail(nullptr, LBM_EINVAL, "unknown model %d", model);
   if (prec < LBM_F64 || prec > LBM_F16_SHIFT)
     return bfail(nullptr, LBM_EINVAL, "storage form %d not available for batches (LBM_F64, LBM_F32_SHIFT, LBM_F16_SHIFT)",
                  prec);

@@ -350,6 +350,7 @@ template <int PREC> struct BatchOps {
       case 2: return prepare_m<2>(b);
       case 3: return prepare_m<3>(b);
       case 4: return prepare_m<4>(b);
+      case 5: return prepare_m<5>(b);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -361,6 +362,7 @@ template <int PREC> struct BatchOps {
       case 2: return step_m<2>(b, diag, parity, st);
       case 3: return step_m<3>(b, diag, parity, st);
       case 4: return step_m<4>(b, diag, parity, st);
+      case 5: return step_m<5>(b, diag, parity, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -372,6 +374,7 @@ template <int PREC> struct BatchOps {
       case 2: return persistent_m<2>(b, n, parity0, st);
       case 3: return persistent_m<3>(b, n, parity0, st);
       case 4: return persistent_m<4>(b, n, parity0, st);
+      case 5: return persistent_m<5>(b, n, parity0, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -172,7 +172,7 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
   if (!(theta > 0.0 && theta < 1.0)) return fail(nullptr, LBM_EINVAL, "theta must lie in (0, 1), got %g", theta);
   if (!(tau > 0.5) || !std::isfinite(tau))
     return fail(nullptr, LBM_EINVAL, "tau must exceed 1/2 (positive viscosity), got %g", tau);
-  if (model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ)
+  if (model < LBM_LBGK || model > LBM_LBGK_POLY)
     return fail(nullptr, LBM_EINVAL, "unknown collision model %d", model);
   if (d_pop_buffers && (reinterpret_cast<uintptr_t>(d_pop_buffers) % 256) != 0)
     return fail(nullptr, LBM_EINVAL, "population buffers must be 256-byte aligned");

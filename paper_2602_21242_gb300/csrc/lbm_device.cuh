@@ -132,6 +132,7 @@ template <typename T> struct Coef {
   T q_inv2t2;     // 1 / (8 theta^2)
   T ntt;          // -theta (1 - 3 theta)
   T tt2;          // 2 theta (1 - theta)
+  T inv_theta;    // 1 / theta                (polynomial equilibrium of model 5)
   T rho_ref;      // reference density of the shifted forms (0 for absolute storage)
   T rw0, rwp;     // rho_ref W(0) and rho_ref W(+-1): the rest state is rho_ref W(a) W(b), W(0) = 1 - theta, W(+-1) = theta/2
   T nrw0, nrwp;   // -rw0, -rwp
@@ -154,6 +155,7 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
   c.q_inv2t2 = (T)(0.25 / (2.0 * theta * theta));
   c.ntt = (T)(-theta * (1.0 - 3.0 * theta));
   c.tt2 = (T)(2.0 * theta * (1.0 - theta));
+  c.inv_theta = (T)(1.0 / theta);
   c.rho_ref = (T)rho_ref;
   c.rw0 = (T)(rho_ref * (1.0 - theta));
   c.rwp = (T)(rho_ref * 0.5 * theta);
@@ -165,7 +167,7 @@ template <typename T> __host__ Coef<T> make_coef(double theta, double tau, doubl
 // The same coefficients in another arithmetic type (a batch stores FP32
 // coefficients per domain and broadcasts them to packed pairs).
 template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Coef<T>& a) {
-  static_assert(sizeof(Coef<float>) == 19 * sizeof(float), "coef_cast lists every field of Coef");
+  static_assert(sizeof(Coef<float>) == 20 * sizeof(float), "coef_cast lists every field of Coef");
   Coef<U> c;
   c.theta = U(a.theta);
   c.one_m_theta = U(a.one_m_theta);
@@ -181,6 +183,7 @@ template <typename U, typename T> __host__ __device__ Coef<U> coef_cast(const Co
   c.q_inv2t2 = U(a.q_inv2t2);
   c.ntt = U(a.ntt);
   c.tt2 = U(a.tt2);
+  c.inv_theta = U(a.inv_theta);
   c.rho_ref = U(a.rho_ref);
   c.rw0 = U(a.rw0);
   c.rwp = U(a.rwp);
@@ -330,7 +333,34 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
     py[0] = hy - huy, py[1] = c.one_m_theta - uy2, py[2] = hy + huy;
   }
 
-  if constexpr (MODEL == 0) {
+  if constexpr (MODEL == 5) {
+    // LBGK on the polynomial equilibrium (second reading of Sec. 5.1's standard
+    // LBGK): f^eq_(a,b) = rho W_a W_b [1 + s + s^2/2 - |u|^2/(2 theta)],
+    // s = (a u_x + b u_y)/theta. Shifted forms: f^eq - rho_ref W_a W_b =
+    // W_a W_b [m0 + rho (t - 1)], t - 1 = s (1 + s/2) - |u|^2/(2 theta), every
+    // term small.
+    const T vx = ux * c.inv_theta, vy = uy * c.inv_theta;
+    const T q1 = -(ux2 + uy2) * scaled(c.inv_theta, 0.5f);  // -|u|^2/(2 theta)
+    const T w[3] = {c.half_theta, c.one_m_theta, c.half_theta};
+    const T rw[3] = {rho * w[0], rho * w[1], rho * w[2]};
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const int i = pop_index(a, b);
+        const T sx = a == 0 ? T(0.0) : (a > 0 ? vx : -vx);
+        const T s = b == 0 ? sx : (a == 0 ? (b > 0 ? vy : -vy) : (b > 0 ? sx + vy : sx - vy));
+        const T t1 = fma(s, fma(T(0.5), s, T(1.0)), q1);  // t - 1
+        if constexpr (SHIFT) {
+          // f^eq - rest = W_a W_b (m0 + rho t1)
+          const T feq = w[b + 1] * fma(rw[a + 1], t1, m0 * w[a + 1]);
+          f[i] = fma(c.omega, feq - f[i], f[i]);
+        } else {
+          const T feq = w[b + 1] * fma(rw[a + 1], t1, rw[a + 1]);
+          f[i] = fma(c.omega, feq - f[i], f[i]);
+        }
+      }
+  } else if constexpr (MODEL == 0) {
     // LBGK: f* = f + (f^eq - f)/tau = (1 - 1/tau) f + (1/tau) f^eq.
     if constexpr (!SHIFT) {
       const T orho = c.omega * rho;

@@ -303,7 +303,7 @@ __device__ __forceinline__ void split_node(const double (&r)[9], df64 (&f)[9]) {
 // population as soon as it is known (so that its conversion and store overlap
 // the rest of the node's arithmetic).
 template <int MODEL> __host__ __device__ constexpr bool has_correction(int i) {
-  return MODEL == 2 ? (i >= 1 && i <= 4) : (MODEL >= 3 ? i != 0 : false);
+  return MODEL == 2 ? (i >= 1 && i <= 4) : ((MODEL == 3 || MODEL == 4) ? i != 0 : false);
 }
 
 template <int MODEL, typename Sink, typename Out>
@@ -334,7 +334,28 @@ __device__ __forceinline__ void collide_df(const df64 (&f)[9], const Coef<df64>&
   const df64 px[3] = {scaled(wx - ux, 0.5f), add_f(-wx, 1.0f), scaled(wx + ux, 0.5f)};
   const df64 py[3] = {scaled(wy - uy, 0.5f), add_f(-wy, 1.0f), scaled(wy + uy, 0.5f)};
 
-  if constexpr (MODEL == 0) {
+  if constexpr (MODEL == 5) {
+    // LBGK on the polynomial equilibrium: f^eq_(a,b) = rho W_a W_b [1 + s (1 + s/2) - |u|^2/(2 theta)],
+    // s = (a u_x + b u_y)/theta (the collide() of lbm_device.cuh, model 5)
+    const df64 vx = ux * c.inv_theta, vy = uy * c.inv_theta;
+    const df64 t0 = add_f(-((ux2 + uy2) * scaled(c.inv_theta, 0.5f)), 1.0f);  // 1 - |u|^2/(2 theta)
+    const df64 orho = c.omega * rho;
+    const df64 ow[3] = {orho * c.half_theta, orho * c.one_m_theta, orho * c.half_theta};
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const int i = pop_index(a, b);
+        const df64 sx = a > 0 ? vx : -vx;
+        const df64 sy = b > 0 ? vy : -vy;
+        const df64 t = a == 0 && b == 0 ? t0
+                       : (a == 0 ? fma(sy, add_f(scaled(sy, 0.5f), 1.0f), t0)
+                                 : (b == 0 ? fma(sx, add_f(scaled(sx, 0.5f), 1.0f), t0)
+                                           : fma(sx + sy, add_f(scaled(sx + sy, 0.5f), 1.0f), t0)));
+        const df64 wb = b == 0 ? c.one_m_theta : c.half_theta;
+        out(i, fma(ow[a + 1] * wb, t, c.one_m_omega * f[i]));
+      }
+  } else if constexpr (MODEL == 0) {
     // LBGK: f* = (1 - 1/tau) f + (1/tau) f^eq
     const df64 orho = c.omega * rho;
     const df64 e[3] = {orho * px[0], orho * px[1], orho * px[2]};

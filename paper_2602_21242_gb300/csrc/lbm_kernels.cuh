@@ -686,6 +686,7 @@ template <int PREC> struct Launch {
       case 2: return step_m<2>(a, st);
       case 3: return step_m<3>(a, st);
       case 4: return step_m<4>(a, st);
+      case 5: return step_m<5>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -133,7 +133,7 @@ extern "C" int lbm_step_noalloc(int nx, int ny, double theta, double tau, int mo
   long long pitch = 0, plane = 0, bytes = 0;
   if (lbm_layout(nx, ny, LBM_F64, &pitch, &plane, &bytes) != LBM_OK)
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: invalid size %d x %d", nx, ny);
-  if (!(theta > 0.0 && theta < 1.0) || !(tau > 0.5) || model < LBM_LBGK || model > LBM_OREG_COMPLETE_NEQ)
+  if (!(theta > 0.0 && theta < 1.0) || !(tau > 0.5) || model < LBM_LBGK || model > LBM_LBGK_POLY)
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: theta, tau or model out of range");
   if (!d_src || !d_dst || !d_diag5)
     return olbm::set_thread_error(LBM_EINVAL, "lbm_step_noalloc: NULL buffer");
@@ -166,7 +166,8 @@ extern "C" int lbm_step_noalloc(int nx, int ny, double theta, double tau, int mo
     case 1: e = launch<1>(g, c, d_src, d_dst, scratch, k, st); break;
     case 2: e = launch<2>(g, c, d_src, d_dst, scratch, k, st); break;
     case 3: e = launch<3>(g, c, d_src, d_dst, scratch, k, st); break;
-    default: e = launch<4>(g, c, d_src, d_dst, scratch, k, st); break;
+    case 4: e = launch<4>(g, c, d_src, d_dst, scratch, k, st); break;
+    default: e = launch<5>(g, c, d_src, d_dst, scratch, k, st); break;
   }
   if (e == cudaSuccess) {
     noalloc_sum_kernel<<<1, kSumThreads, 0, st>>>(scratch, (int)nparts, d_diag5);

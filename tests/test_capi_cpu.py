@@ -62,7 +62,7 @@ def test_layout():
     ((8, 8, 0.0, 0.6, 3), "theta"),
     ((8, 8, 1 / 3, 0.5, 3), "tau"),
     ((8, 8, 1 / 3, float("nan"), 3), "tau"),
-    ((8, 8, 1 / 3, 0.6, 5), "model"),
+    ((8, 8, 1 / 3, 0.6, 6), "model"),
     ((8, 8, 1 / 3, 0.6, -1), "model"),
 ])
 def test_create_rejects_bad_arguments(args, fragment):

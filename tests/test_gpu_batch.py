@@ -65,7 +65,7 @@ def test_batch_bit_identical_to_single_lattices(model, prec, kind, nc, mode):
         np.testing.assert_array_equal(got[k], want, err_msg=f"domain {k} ({nx}x{ny})")
 
 
-@pytest.mark.parametrize("model", [1, 2, 3, 4])
+@pytest.mark.parametrize("model", [1, 2, 3, 4, 5])
 def test_batch_f64_oracle_parity(oracle, model):
     f0 = states(200 + model)
     with make_batch(model, "f64", "graph") as b:

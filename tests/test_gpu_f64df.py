@@ -49,7 +49,7 @@ def assert_rel(got, ref, rel, what=""):
 
 
 @pytest.mark.parametrize("nx,ny", [(37, 23), (64, 64), (1, 5), (130, 3)])
-@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("theta", [0.25, 1.0 / 3.0, 0.4])
 def test_random_state_parity(oracle, nx, ny, model, theta):
     f0 = flows.random_populations(nx, ny, seed=1000 + nx * 7 + ny + model, spread=0.2)

@@ -80,7 +80,7 @@ def run_form(f0, theta, tau, model, prec, steps=STEPS):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4, 5])
 def test_taylor_green_forms(oracle, prec, model):
     n, theta, nu, u0 = 64, 1.0 / 3.0, 0.01, 0.05
     tau = oracle.tau_from_nu(nu, theta)

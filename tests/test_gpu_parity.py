@@ -52,7 +52,7 @@ SIZES = [(37, 23), (64, 64), (100, 3), (1, 5), (5, 1), (1, 1), (33, 9)]
 
 
 @pytest.mark.parametrize("nx,ny", SIZES)
-@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("theta", [0.25, 1.0 / 3.0, 0.4])
 def test_random_state_parity_f64(oracle, nx, ny, model, theta):
     """Generic non-equilibrium populations, 100 steps, tau = 0.8."""
@@ -62,7 +62,7 @@ def test_random_state_parity_f64(oracle, nx, ny, model, theta):
     assert_rel(got, ref, REL_F64, f"{nx}x{ny} model {model} theta {theta:.3f}")
 
 
-@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4, 5])
 def test_taylor_green_parity_f64(oracle, model):
     """Taylor-Green at 64^2, theta = 1/3, nu = 0.01, u0 = 0.05, through lbm_init and lbm_moments."""
     n, theta, nu, u0 = 64, 1.0 / 3.0, 0.01, 0.05
@@ -269,6 +269,10 @@ def test_vjp_and_batch_argument_errors():
         with pytest.raises(capi.LBMError) as e:
             capi.lbm_vjp(lat.ctx, 4, 2, z.data_ptr(), z.data_ptr(), z.data_ptr())
         assert e.value.status == capi.LBM_EINVAL
+    with Lattice(16, 16, 1 / 3, 0.6, "lbgk_poly", "f64") as lat:
+        with pytest.raises(capi.LBMError) as e:  # the polynomial-equilibrium LBGK has no adjoint
+            capi.lbm_vjp(lat.ctx, 4, 2, z.data_ptr(), z.data_ptr(), z.data_ptr())
+        assert e.value.status == capi.LBM_EINVAL and "LBGK_POLY" in str(e.value)
     with Lattice(16, 16, 1 / 3, 0.6, "complete", "f64") as lat:
         with pytest.raises(capi.LBMError):
             capi.lbm_vjp(lat.ctx, 4, 0, z.data_ptr(), z.data_ptr(), z.data_ptr())
@@ -332,7 +336,7 @@ def test_full_size_sampled_shifted_forms(oracle, prec):
 
 @pytest.mark.parametrize("nx,ny,rows", [(37, 23, 5), (128, 16, 4), (130, 9, 3), (257, 12, 7), (1, 5, 2), (3, 4, 4),
                                         (45, 19, 8), (600, 33, 16)])
-@pytest.mark.parametrize("model", [0, 3, 4])
+@pytest.mark.parametrize("model", [0, 3, 4, 5])
 def test_fp64_pipeline_parity(oracle, nx, ny, rows, model):
     """FP64 through the bulk-copy pipeline (launch kind 1: 128-column tiles, one node a consumer
     thread): full and partial strips, narrow lattices whose rows share a ring slot, odd widths
