@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # the current kernels: the FP64 kernel captured at 2048^2 and scaled to the lattice by
 # node count (its traffic grows in proportion), the FP32 pipeline captured at 4096^2.
 # Keyed by (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.5, ("f32", "complete"): 68.8}
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.4, ("f32", "complete"): 68.8}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
 STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_persistent_kernel",
