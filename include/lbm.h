@@ -314,10 +314,12 @@ typedef struct lbm_batch lbm_batch;
  *                        over all domains, and the n launches of a call are
  *                        captured once into a CUDA graph and replayed as one
  *                        graph launch (fused diagnostics as a parallel branch).
- *   LBM_BATCH_PERSISTENT the persistent launch: one cooperative launch runs all
- *                        n steps, a grid barrier with a bounded wait between
- *                        steps; issued directly, because the call reads the
- *                        barrier's status back and synchronises.
+ *   LBM_BATCH_PERSISTENT the persistent launch in a graph: one cooperative
+ *                        launch runs all n steps, a grid barrier with a bounded
+ *                        wait between steps; it is captured with the barrier's
+ *                        reset into a CUDA graph once per n and buffer parity
+ *                        and replayed; the call then reads the barrier's status
+ *                        back and synchronises.
  * Both measure the same on GB300 (88 % of HBM on 256 Taylor-Green domains).
  */
 enum lbm_batch_mode {
@@ -364,8 +366,9 @@ int lbm_batch_moments(lbm_batch* b, double* d_rho, double* d_ux, double* d_uy);
  * Advance every domain by n steps. LBM_BATCH_GRAPH: asynchronous; the n launches
  * are captured once into a graph (re-captured when n, the buffer parity or the
  * diagnostics phase changes) and replayed; each diagnosed step's final sum is a
- * parallel branch of the graph. LBM_BATCH_PERSISTENT: one cooperative launch,
- * without fused diagnostics (lbm_batch_diagnostics reduces the state after it);
+ * parallel branch of the graph. LBM_BATCH_PERSISTENT: one cooperative launch
+ * replayed from a CUDA graph (captured once per n and buffer parity), without
+ * fused diagnostics (lbm_batch_diagnostics reduces the state after it);
  * synchronises and returns LBM_ETIMEOUT if a grid barrier waited longer than
  * about a second (the state is then undefined).
  */

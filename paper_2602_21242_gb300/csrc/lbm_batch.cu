@@ -18,7 +18,9 @@
 //                         captured once into a CUDA graph and replayed as one
 //                         graph launch; fused diagnostics as for one lattice.
 //   LBM_BATCH_PERSISTENT  one cooperative launch of a persistent kernel that
-//                         loops over the n steps, tiles strided over the grid,
+//                         loops over the n steps (captured with its barrier
+//                         reset into a CUDA graph once per n and buffer parity,
+//                         and replayed), tiles strided over the grid,
 //                         separated by a grid barrier whose waits are bounded:
 //                         a barrier that does not complete within ~1 s sets an
 //                         error flag, every block leaves, and the call reports
@@ -106,6 +108,10 @@ struct lbm_batch {
   long long last_diag_t = -1;
   cudaGraphExec_t graph = nullptr;
   long long graph_key[4] = {-1, -1, -1, -1};
+  // Persistent mode: the barrier reset and the cooperative launch of n steps,
+  // captured once per (n, buffer parity) and replayed.
+  cudaGraphExec_t pgraph = nullptr;
+  long long pgraph_key[2] = {-1, -1};
   char err[320] = {0};
 };
 
@@ -190,12 +196,17 @@ int build_tiles(lbm_batch* b) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+  if (b->pgraph) {
+    cudaGraphExecDestroy(b->pgraph);
+    b->pgraph = nullptr;
+  }
   return LBM_OK;
 }
 
 void free_batch(lbm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
   if (b->capture) cudaStreamDestroy(b->capture);
   if (b->capture_side) cudaStreamDestroy(b->capture_side);
   for (int k = 0; k < 2; ++k) {
@@ -539,7 +550,33 @@ int lbm_batch_step(lbm_batch* b, int n) {
   cudaError_t e = prepare_launch(b);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step kernel attributes");
   if (b->mode == LBM_BATCH_PERSISTENT) {
-    e = launch_persistent(b, n, b->cur, b->stream);
+    // One persistent cooperative launch for the n steps, captured with its barrier
+    // reset into a CUDA graph once per (n, buffer parity) and replayed.
+    const long long pkey[2] = {n, b->cur};
+    if (!b->pgraph || !std::equal(pkey, pkey + 2, b->pgraph_key)) {
+      if (b->pgraph) {
+        cudaGraphExecDestroy(b->pgraph);
+        b->pgraph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step persistent capture");
+      const cudaError_t le = launch_persistent(b, n, b->cur, b->capture);
+      e = cudaStreamEndCapture(b->capture, &g);
+      if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return bcuda(b, le != cudaSuccess ? le : e, "lbm_batch_step persistent capture");
+      }
+      e = cudaGraphInstantiate(&b->pgraph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->pgraph = nullptr;
+        return bcuda(b, e, "lbm_batch_step persistent graph instantiate");
+      }
+      std::copy(pkey, pkey + 2, b->pgraph_key);
+    }
+    e = cudaGraphLaunch(b->pgraph, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step persistent launch");
     int timed_out = 0;
     e = cudaMemcpyAsync(&timed_out, &b->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
