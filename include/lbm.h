@@ -205,6 +205,44 @@ int lbm_get_state(lbm_ctx* ctx, double* d_f);
 int lbm_set_state(lbm_ctx* ctx, const double* d_f);
 
 /*
+ * Slab split of one periodic lattice along y (Eq. 1's streaming across the faces
+ * between slabs; no counterpart in the paper, which runs one lattice). A context
+ * of nx x ny nodes created for rows [y0, y0 + ny) of an nx x NY lattice is
+ * initialised from those rows (lbm_init, lbm_set_state; they need no exchange)
+ * and advanced one step at a time: after every step (lbm_step(ctx, 1)) each
+ * slab calls lbm_halo_pack, sends the two face buffers to its neighbours (`up`
+ * to the slab above, y0 + ny, `down` to the slab below, y0 - 1, both taken
+ * periodically) and calls lbm_halo_unpack with the buffers it received from
+ * the slab below and the slab above. The context then describes its rows of
+ * the whole lattice: the next step pulls across the faces, and lbm_moments,
+ * lbm_get_state, lbm_diagnostics and the fused diagnostics of the next step
+ * cover exactly its rows (summed over the slabs they give the whole
+ * lattice's). With one slab the exchange returns each buffer to its sender and
+ * changes nothing. Between a step and its exchange the context's state is not
+ * that of the whole lattice. Walls, lbm_run_host and lbm_vjp act on the
+ * context alone.
+ *
+ * lbm_halo_bytes: *h_bytes = bytes of each face buffer, 3 * nx storage elements
+ * (8 bytes each for LBM_F64 and LBM_F64_DF, 4 for LBM_F32_SHIFT, 2 for
+ * LBM_F16_SHIFT; values move bit for bit in the storage form, so every slab must
+ * use the same form, theta and tau).
+ * lbm_halo_pack: d_up receives the populations with c_y = +1 (i = 2, 5, 6, in
+ * that order, each nx values, x fastest) that leave through the top face, d_down
+ * those with c_y = -1 (i = 4, 7, 8) that leave through the bottom face.
+ * lbm_halo_unpack: the slab below's d_up (d_from_below) and the slab above's
+ * d_down (d_from_above) take their places.
+ * Buffers: device memory of lbm_halo_bytes each, aligned to the storage element,
+ * owned by the caller, not overlapping the context's buffers or each other.
+ * Asynchronous on the context's stream. Errors: LBM_EINVAL for NULL or
+ * misaligned pointers; LBM_ESTATE before lbm_init / lbm_set_state, for a pack
+ * unless exactly one step has run since the last unpack, lbm_init or
+ * lbm_set_state, and for an unpack without a pack since the last step.
+ */
+int lbm_halo_bytes(const lbm_ctx* ctx, long long* h_bytes);
+int lbm_halo_pack(lbm_ctx* ctx, void* d_up, void* d_down);
+int lbm_halo_unpack(lbm_ctx* ctx, const void* d_from_below, const void* d_from_above);
+
+/*
  * Reverse-mode derivative (vector-Jacobian product) of n steps of Eq. 1 started
  * from the guided equilibrium f(x, 0) = f^eq(rho0(x), u0(x)) (Eq. 10), with
  * respect to the initial fields. Given the cotangents g_rho, g_ux, g_uy of the

@@ -46,6 +46,9 @@ _SIGNATURES = {
     "lbm_diagnostics": ([_p, _pd], _i),
     "lbm_get_state": ([_p, _p], _i),
     "lbm_set_state": ([_p, _p], _i),
+    "lbm_halo_bytes": ([_p, _pll], _i),
+    "lbm_halo_pack": ([_p, _p, _p], _i),
+    "lbm_halo_unpack": ([_p, _p, _p], _i),
     "lbm_time": ([_p, _pll], _i),
     "lbm_run_host": ([_p, _p, _p, _p, _i, _p, _p, _p, _pd], _i),
     "lbm_sync": ([_p], _i),
@@ -213,6 +216,20 @@ def lbm_get_state(ctx, d_f: int) -> None:
 
 def lbm_set_state(ctx, d_f: int) -> None:
     check(load().lbm_set_state(ctx, d_f), ctx)
+
+
+def lbm_halo_bytes(ctx) -> int:
+    n = _ll()
+    check(load().lbm_halo_bytes(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def lbm_halo_pack(ctx, d_up: int, d_down: int) -> None:
+    check(load().lbm_halo_pack(ctx, d_up, d_down), ctx)
+
+
+def lbm_halo_unpack(ctx, d_from_below: int, d_from_above: int) -> None:
+    check(load().lbm_halo_unpack(ctx, d_from_below, d_from_above), ctx)
 
 
 def lbm_time(ctx) -> int:

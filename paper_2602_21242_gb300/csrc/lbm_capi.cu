@@ -15,6 +15,7 @@
 #include "lbm.h"
 #include "lbm_ctx.h"
 #include "lbm_launch.h"
+#include "lbm_halo.h"
 #include "lbm_walls.h"
 
 namespace {
@@ -293,6 +294,8 @@ int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_init reset");
   ctx->initialised = true;
   ctx->t = 0;
+  ctx->halo_t = 0;
+  ctx->packed_t = -1;
   ctx->last_diag_t = -1;
   ++ctx->state_gen;
   return LBM_OK;
@@ -340,6 +343,55 @@ int lbm_set_walls(lbm_ctx* ctx, const unsigned char* h_mask, long long* h_count)
     ctx->n_walls = n;
   }
   if (h_count) *h_count = n;
+  return LBM_OK;
+}
+
+int lbm_halo_bytes(const lbm_ctx* ctx, long long* h_bytes) {
+  if (!ctx || !h_bytes) return LBM_EINVAL;
+  *h_bytes = 3LL * ctx->nx * elem_size(ctx->prec);
+  return LBM_OK;
+}
+
+namespace {
+
+int halo_check(lbm_ctx* ctx, const void* a, const void* b, const char* what) {
+  int s = check_ctx(ctx);
+  if (s != LBM_OK) return s;
+  if (!a || !b) return fail(ctx, LBM_EINVAL, "%s: NULL pointer", what);
+  const uintptr_t es = (uintptr_t)elem_size(ctx->prec);
+  if ((uintptr_t)a % es || (uintptr_t)b % es)
+    return fail(ctx, LBM_EINVAL, "%s: face buffers must be aligned to %d bytes", what, (int)es);
+  if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "%s before lbm_init / lbm_set_state", what);
+  return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_halo_pack(lbm_ctx* ctx, void* d_up, void* d_down) {
+  int s = halo_check(ctx, d_up, d_down, "lbm_halo_pack");
+  if (s != LBM_OK) return s;
+  if (ctx->t != ctx->halo_t + 1)
+    return fail(ctx, LBM_ESTATE,
+                "lbm_halo_pack: %lld step(s) since the last lbm_halo_unpack / lbm_init / lbm_set_state (needs 1)",
+                ctx->t - ctx->halo_t);
+  cudaError_t e = olbm::launch_halo_pack((int)elem_size(ctx->prec), ctx->buf[ctx->cur], ctx->g, d_up, d_down,
+                                         ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_halo_pack launch");
+  ctx->packed_t = ctx->t;
+  return LBM_OK;
+}
+
+int lbm_halo_unpack(lbm_ctx* ctx, const void* d_from_below, const void* d_from_above) {
+  int s = halo_check(ctx, d_from_below, d_from_above, "lbm_halo_unpack");
+  if (s != LBM_OK) return s;
+  if (ctx->packed_t != ctx->t)
+    return fail(ctx, LBM_ESTATE, "lbm_halo_unpack: no lbm_halo_pack since the last step");
+  cudaError_t e = olbm::launch_halo_unpack((int)elem_size(ctx->prec), ctx->buf[ctx->cur], ctx->g, d_from_below,
+                                           d_from_above, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_halo_unpack launch");
+  ctx->halo_t = ctx->t;
+  ctx->packed_t = -1;
+  ++ctx->state_gen;
   return LBM_OK;
 }
 
@@ -495,6 +547,8 @@ int lbm_set_state(lbm_ctx* ctx, const double* d_f) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_state reset");
   ctx->initialised = true;
   ctx->t = 0;
+  ctx->halo_t = 0;
+  ctx->packed_t = -1;
   ctx->last_diag_t = -1;
   ++ctx->state_gen;
   return LBM_OK;

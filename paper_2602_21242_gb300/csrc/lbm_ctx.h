@@ -53,6 +53,11 @@ struct lbm_ctx {
   // fullway bounce-back wall nodes (x, y), applied after every step (lbm_set_walls)
   int2* d_walls = nullptr;
   long long n_walls = 0;
+  // Slab halo trade (lbm_halo_pack / lbm_halo_unpack): the time of the last
+  // unpack, or of lbm_init / lbm_set_state (a pack needs exactly one step
+  // since), and the time of the last pack (an unpack needs one at this time).
+  long long halo_t = 0;
+  long long packed_t = -1;
   char err[320] = {0};
 };
 
