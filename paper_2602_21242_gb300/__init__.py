@@ -2,7 +2,7 @@
 
 The compute path is the CUDA C-ABI library ``liblbm.so`` (sources in ``csrc/``,
 declarations in ``include/lbm.h``); ``capi`` binds it through ctypes and
-``lattice`` wraps it for torch tensors. Nothing here computes lattice
+``lattice`` wraps it for torch tensors, ``slab`` splits one lattice over ranks. Nothing here computes lattice
 Boltzmann arithmetic in Python.
 """
-__all__ = ["capi", "lattice", "flows"]
+__all__ = ["capi", "lattice", "flows", "slab"]
