@@ -43,9 +43,11 @@ FP64_OPS_PER_NODE = {"lbgk": 60, "oreg": 94, "partial": 104, "complete": 124, "c
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch, from ncu captures of
 # the current kernels: the FP64 kernel captured at 2048^2 and scaled to the lattice by
-# node count (its traffic grows in proportion), the FP32 pipeline captured at 4096^2.
-# Keyed by (storage, model).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete"): 133.4, ("f32", "complete"): 68.8}
+# node count (its traffic grows in proportion), the FP32 kernels (single steps, and two
+# steps a launch) captured at 4096^2.
+# Keyed by (storage, model, steps per launch).
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete", 1): 133.4, ("f32", "complete", 1): 68.8,
+                               ("f32", "complete", 2): 71.4}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
 STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_persistent_kernel",
@@ -218,39 +220,49 @@ def run_gpu(args):
     lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], args.model, args.prec, device=dev, stream=stream)
     lat.init(*fields)
     lat.set_diagnostics_interval(1)
+    # steps per launch: 2 under launch kind 2 (the FP32 default where it applies), timed per launch
+    # (kind 2 applies where nx is a multiple of the 16-byte chunk)
+    chunk = {"f32": 4, "f16": 8}.get(args.prec, 0)
+    spl = 2 if capi.lbm_get_launch_ex(lat.ctx)[0] == 2 and chunk and w["nx"] % chunk == 0 else 1
     for _ in range(args.warmup):
-        lat.step(1)
+        lat.step(spl)
     lat.sync()
     props = torch.cuda.get_device_properties(dev)
     gpu_id = str(getattr(props, "uuid", local))
     if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
         gpu_id = "GPU-" + gpu_id
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches = -(-args.steps // spl)
+    args.steps = launches * spl
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(launches + 1)]
     barrier()
     with ClockSampler(gpu_id) as clocks:
         events[0].record(stream)
-        for k in range(args.steps):
-            lat.step(1)
+        for k in range(launches):
+            lat.step(spl)
             events[k + 1].record(stream)
         barrier()
     total_ms = events[0].elapsed_time(events[-1])
-    per_step = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
+    per_launch = [events[k].elapsed_time(events[k + 1]) for k in range(launches)]
     diag, t_diag, status = lat.step_diagnostics()
     total_ms = max_over_ranks(total_ms, world, dev)
     mlups = aggregate_mlups(n, args.steps, total_ms, world)
-    step_ms = statistics.mean(per_step)
+    launch_ms = statistics.mean(per_launch)
+    step_ms = launch_ms / spl
 
-    # ---- roofline of the step kernel (fused step + its tiny diagnostics finalisation)
+    # ---- roofline of the step kernel (fused step + its tiny diagnostics finalisation); a
+    # two-step launch reads and writes the state once, so its algorithmic bytes per launch
+    # are one step's
     peak_hbm, hbm_src = hbm_peak()
-    bytes_step = BYTES_PER_NODE[args.prec] * n
-    hbm_gbs = bytes_step / (step_ms * 1e-3) / 1e9
-    tpn = PROFILED_TRAFFIC_B_PER_NODE.get((args.prec, args.model))
+    bytes_launch = BYTES_PER_NODE[args.prec] * n
+    hbm_gbs = bytes_launch / (launch_ms * 1e-3) / 1e9
+    tpn = PROFILED_TRAFFIC_B_PER_NODE.get((args.prec, args.model, spl))
     traffic = round(tpn * n) if tpn is not None else None
     roof = {"bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
             "frac": round(hbm_gbs / peak_hbm, 4), "traffic": traffic,
             "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
             else "profiling-recipe fallback 6.8 TB/s",
-            "kernel": f"{STEP_KERNEL[args.prec]}<{args.model},diag>", "ms_per_launch": round(step_ms, 4)}
+            "kernel": f"{'step2_stream_kernel' if spl == 2 else STEP_KERNEL[args.prec]}<{args.model},diag>",
+            "ms_per_launch": round(launch_ms, 4), "steps_per_launch": spl}
     alu = None
     if args.prec == "f64":
         peak_ops = capi.lbm_measure_peak(0) / 2.0  # FMA instructions per second (2 FLOP each)
@@ -276,8 +288,9 @@ def run_gpu(args):
                       "l2": f"inputs larger than L2: two {lat_bytes(args.prec, n)/1e9:.2f} GB population buffers",
                       "parallelism": f"one independent lattice per GPU (replicas), {world} GPU(s)"},
            "roofline": roof, "roofline_other": alu,
-           "gpu_launches": 2 * args.steps,
-           "gpu_launches_note": "per step: 1 fused step kernel + 1 diagnostics finalisation kernel",
+           "gpu_launches": launches * (1 + spl),
+           "gpu_launches_note": f"per launch: 1 fused step kernel ({spl} step(s)) + {spl} diagnostics finalisation "
+                                f"kernel(s)",
            "clocks": clocks.summary(),
            "final_diagnostics": {"t": t_diag, "mass": diag[0], "mom_x": diag[1], "mom_y": diag[2],
                                  "kinetic": diag[3], "nonfinite": diag[4]}}
@@ -353,8 +366,13 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
     n = w["nx"] * w["ny"]
     res = {}
 
-    def timed(model, prec, diag_every=1):
+    from paper_2602_21242_gb300 import capi
+
+    def timed(model, prec, diag_every=1, launch=None):
         lat = Lattice(w["nx"], w["ny"], w["theta"], w["tau"], model, prec, device=dev, stream=stream)
+        if launch is not None:
+            capi.lbm_set_launch_ex(lat.ctx, *launch)
+        kind = capi.lbm_get_launch_ex(lat.ctx)[0]
         lat.init(*fields)
         lat.set_diagnostics_interval(diag_every)
         lat.step(warm)
@@ -367,6 +385,15 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
         ms = e0.elapsed_time(e1) / steps
         lat.close()
         mlups = n / (ms * 1e-3) / 1e6
+        if kind == 2:
+            # two steps a launch: the state is read and written once per two steps, so the
+            # algorithmic traffic of a step is half the single step's; the rate is also
+            # given against the single-step HBM roof
+            bpn = BYTES_PER_NODE[prec] / 2
+            gbs = bpn * n / (ms * 1e-3) / 1e9
+            return {"mlups": round(mlups, 1), "ms_per_step": round(ms, 4), "launch": "two steps a launch (kind 2)",
+                    "bytes_per_node_step": bpn, "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_hbm, 4),
+                    "vs_single_step_hbm_roof": round(2 * gbs / peak_hbm, 4)}
         gbs = BYTES_PER_NODE[prec] * n / (ms * 1e-3) / 1e9
         return {"mlups": round(mlups, 1), "ms_per_step": round(ms, 4), "hbm_gbs": round(gbs, 1),
                 "hbm_frac": round(gbs / peak_hbm, 4)}
@@ -378,6 +405,8 @@ def forms_sweep(w, fields, dev, stream, peak_hbm, steps=100, warm=5, err_steps=2
     for prec in ("f32", "f16"):
         res[f"complete/{prec}"] = timed("complete", prec)
         res[f"complete/{prec}/diagnostics_every_100"] = timed("complete", prec, 100)
+    # FP32 single steps (the persistent pipeline on 4-row tiles) beside the default two-step launch
+    res["complete/f32/single_step"] = timed("complete", "f32", 1, (1, 64, 1, 4))
 
     # velocity error of the double-float and shifted forms against FP64 on the same flow
     finals = {}

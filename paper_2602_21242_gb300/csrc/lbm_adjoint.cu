@@ -200,7 +200,7 @@ cudaError_t fwd_step(lbm_ctx* c, const void* src, void* dst) {
   a.theta = c->theta;
   a.tau = c->tau;
   a.rho_ref = c->rho_ref;
-  a.partials = c->d_partials;
+  a.partials = c->d_parts[0];
   a.cfg = c->cfg;
   a.err = c->d_err;
   a.sched = c->d_sched;

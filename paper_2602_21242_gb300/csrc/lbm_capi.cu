@@ -86,10 +86,22 @@ olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
     }
   }
   while (k.rows > 1 && olbm::step_blocks(g, k, prec) < 4LL * sms) k.rows /= 2;
-  // FP32: the persistent pipeline over all resident CTAs on 4-row tiles
-  // (measured 3-5 % above one CTA per tile at 4096^2 and 8192^2; for FP16 it
-  // is slower, so FP16 keeps one CTA per tile).
-  if (k.kind == 1 && prec == LBM_F32_SHIFT) k.bx = 64, k.rows = k.rows < 4 ? k.rows : 4;
+  // FP32: two steps a launch (kind 2) on 32-row tiles where nx is a multiple of
+  // 4 (4096^2, diagnostics every step: 142 GLUPS against 92.6 for single steps;
+  // 8192^2 with 64-row tiles: 162 against 96.7); otherwise the persistent
+  // pipeline over all resident CTAs on 4-row tiles (measured 3-5 % above one CTA
+  // per tile at 4096^2 and 8192^2). FP16 is bound by its arithmetic, not by
+  // memory, and keeps single steps on one CTA per tile (two steps: 136.7 against
+  // 152 GLUPS at 4096^2).
+  if (k.kind == 1 && prec == LBM_F32_SHIFT) {
+    olbm::LaunchCfg k2 = k;
+    k2.kind = 2, k2.bx = 0, k2.rows = g.nx >= 8192 && g.ny >= 8192 ? 64 : 32;
+    if (olbm::uses_step2(prec, g, k2)) {
+      while (k2.rows > 1 && olbm::step2_blocks(g, k2, prec) < 4LL * sms) k2.rows /= 2;
+      return k2;
+    }
+    k.bx = 64, k.rows = k.rows < 4 ? k.rows : 4;
+  }
   return k;
 }
 
@@ -102,13 +114,21 @@ cudaError_t launch_step(const olbm::StepArgs& a, int prec, cudaStream_t st) {
   }
 }
 
+cudaError_t launch_step2(const olbm::StepArgs& a, int prec, cudaStream_t st) {
+  switch (prec) {
+    case LBM_F32_SHIFT: return olbm::launch_step2_f32(a, st);
+    case LBM_F16_SHIFT: return olbm::launch_step2_f16(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_diag(const lbm_ctx* c, cudaStream_t st) {
   const void* src = c->buf[c->cur];
   switch (c->prec) {
     case LBM_F64:
-    case LBM_F64_DF: return olbm::launch_diag_f64(src, c->g, c->rho_ref, c->d_partials, st);
-    case LBM_F32_SHIFT: return olbm::launch_diag_f32(src, c->g, c->rho_ref, c->d_partials, st);
-    default: return olbm::launch_diag_f16(src, c->g, c->rho_ref, c->d_partials, st);
+    case LBM_F64_DF: return olbm::launch_diag_f64(src, c->g, c->rho_ref, c->d_parts[0], st);
+    case LBM_F32_SHIFT: return olbm::launch_diag_f32(src, c->g, c->rho_ref, c->d_parts[0], st);
+    default: return olbm::launch_diag_f16(src, c->g, c->rho_ref, c->d_parts[0], st);
   }
 }
 
@@ -126,9 +146,8 @@ void free_ctx(lbm_ctx* c) {
     cudaFree(c->buf[0]);
     cudaFree(c->buf[1]);
   }
-  cudaFree(c->d_partials);
-  cudaFree(c->d_partials2);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < lbm_ctx::kParts; ++b) {
+    cudaFree(c->d_parts[b]);
     if (c->ev_step[b]) cudaEventDestroy(c->ev_step[b]);
     if (c->ev_fin[b]) cudaEventDestroy(c->ev_fin[b]);
   }
@@ -215,8 +234,9 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
       }
     }
   }
-  if ((e = cudaMalloc(&c->d_partials, sizeof(double) * 5 * (size_t)c->parts_cap)) != cudaSuccess ||
-      (e = cudaMalloc(&c->d_partials2, sizeof(double) * 5 * (size_t)c->parts_cap)) != cudaSuccess ||
+  for (int b = 0; b < lbm_ctx::kParts && e == cudaSuccess; ++b)
+    e = cudaMalloc(&c->d_parts[b], sizeof(double) * 5 * (size_t)c->parts_cap);
+  if (e != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag_now, sizeof(double) * 6)) != cudaSuccess ||
       (e = cudaMalloc(&c->d_sticky, sizeof(unsigned long long))) != cudaSuccess ||
@@ -226,12 +246,12 @@ int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
     cudaGetLastError();
     return fail(nullptr, LBM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
   }
-  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_step[0], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_step[1], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_fin[0], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_fin[1], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming)) != cudaSuccess ||
+  e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  for (int b = 0; b < lbm_ctx::kParts && e == cudaSuccess; ++b) {
+    e = cudaEventCreateWithFlags(&c->ev_step[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fin[b], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess || (e = cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_rebind, cudaEventDisableTiming)) != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
@@ -414,45 +434,64 @@ int lbm_step(lbm_ctx* ctx, int n) {
   a.theta = ctx->theta;
   a.tau = ctx->tau;
   a.rho_ref = ctx->rho_ref;
-  a.partials = ctx->d_partials;
+  a.partials = ctx->d_parts[0];
   a.cfg = ctx->cfg;
   a.err = ctx->d_err;
   a.sched = ctx->d_sched;
   long long used = ctx->nparts;
   a.parts_used = &used;
   int joined = -1;  // partials buffer whose final sum was launched last (-1: none in this call)
-  for (int k = 0; k < n; ++k) {
-    a.diag = ctx->diag_every > 0 && (ctx->t % ctx->diag_every) == 0;
+  // The next free partials buffer (waiting for its previous final sum), or null.
+  auto take = [&](bool diag, int& b) -> cudaError_t {
+    b = -1;
+    if (!diag) return cudaSuccess;
+    b = ctx->pbuf;
+    ctx->pbuf = (ctx->pbuf + 1) % lbm_ctx::kParts;
+    return ctx->fin_pending[b] ? cudaStreamWaitEvent(ctx->stream, ctx->ev_fin[b], 0) : cudaSuccess;
+  };
+  // The final sum of buffer b's partials (step time t) on the side stream, beside the next step.
+  auto finish = [&](int b, long long t) -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaEventRecord(ctx->ev_step[b], ctx->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->side, ctx->ev_step[b], 0)) != cudaSuccess ||
+        (e = olbm::launch_finalize(ctx->d_parts[b], (int)used, ctx->rho_ref, nodes_of(ctx), t, ctx->d_diag,
+                                   ctx->d_sticky, ctx->side)) != cudaSuccess ||
+        (e = cudaEventRecord(ctx->ev_fin[b], ctx->side)) != cudaSuccess)
+      return e;
+    ctx->fin_pending[b] = true;
+    joined = b;
+    ctx->last_diag_t = t;
+    return cudaSuccess;
+  };
+  auto due = [&](long long t) { return ctx->diag_every > 0 && (t % ctx->diag_every) == 0; };
+  for (int k = 0; k < n;) {
+    // launch kind 2: two steps in one launch where two remain (no walls: they act after every step)
+    const bool two = k + 1 < n && ctx->n_walls == 0 && olbm::uses_step2(ctx->prec, ctx->g, ctx->cfg);
+    a.diag = due(ctx->t);
+    a.diag2 = two && due(ctx->t + 1);
     a.src = ctx->buf[ctx->cur];
     a.dst = ctx->buf[ctx->cur ^ 1];
     used = ctx->nparts;
-    const int b = ctx->pbuf;
-    cudaError_t e = cudaSuccess;
-    if (a.diag && ctx->fin_pending[b]) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_fin[b], 0);  // buffer b free
+    int b1 = -1, b2 = -1;
+    cudaError_t e = take(a.diag, b1);
+    if (e == cudaSuccess) e = take(a.diag2, b2);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step event wait");
-    a.partials = b ? ctx->d_partials2 : ctx->d_partials;
-    e = launch_step(a, ctx->prec, ctx->stream);
+    a.partials = ctx->d_parts[b1 < 0 ? 0 : b1];
+    a.partials2 = ctx->d_parts[b2 < 0 ? 0 : b2];
+    e = two ? launch_step2(a, ctx->prec, ctx->stream) : launch_step(a, ctx->prec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step launch");
     if (ctx->n_walls > 0) {
       e = olbm::launch_walls((int)elem_size(ctx->prec), a.src, a.dst, ctx->g, ctx->d_walls, ctx->n_walls,
                              ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_step walls launch");
     }
-    if (a.diag) {
-      // the final sum of this step's partials runs on the side stream, beside the next step
-      if ((e = cudaEventRecord(ctx->ev_step[b], ctx->stream)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(ctx->side, ctx->ev_step[b], 0)) != cudaSuccess ||
-          (e = olbm::launch_finalize(a.partials, (int)used, ctx->rho_ref, nodes_of(ctx), ctx->t, ctx->d_diag,
-                                     ctx->d_sticky, ctx->side)) != cudaSuccess ||
-          (e = cudaEventRecord(ctx->ev_fin[b], ctx->side)) != cudaSuccess)
-        return cuda_fail(ctx, e, "lbm_step diagnostics launch");
-      ctx->fin_pending[b] = true;
-      ctx->pbuf ^= 1;
-      joined = b;
-      ctx->last_diag_t = ctx->t;
-    }
+    if (b1 >= 0 && (e = finish(b1, ctx->t)) != cudaSuccess) return cuda_fail(ctx, e, "lbm_step diagnostics launch");
+    if (b2 >= 0 && (e = finish(b2, ctx->t + 1)) != cudaSuccess)
+      return cuda_fail(ctx, e, "lbm_step diagnostics launch");
     ctx->cur ^= 1;
-    ctx->t += 1;
+    const int done = two ? 2 : 1;
+    ctx->t += done;
+    k += done;
   }
   if (joined >= 0) {  // everything queued on `stream` after this call follows the final sums
     cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_fin[joined], 0);
@@ -503,7 +542,7 @@ int lbm_diagnostics(lbm_ctx* ctx, double* h_out5) {
   if (!ctx->initialised) return fail(ctx, LBM_ESTATE, "lbm_diagnostics before lbm_init / lbm_set_state");
   cudaError_t e = launch_diag(ctx, ctx->stream);
   if (e == cudaSuccess)
-    e = olbm::launch_finalize(ctx->d_partials, (int)olbm::diag_blocks(ctx->g), ctx->rho_ref, nodes_of(ctx), ctx->t,
+    e = olbm::launch_finalize(ctx->d_parts[0], (int)olbm::diag_blocks(ctx->g), ctx->rho_ref, nodes_of(ctx), ctx->t,
                               ctx->d_diag_now, nullptr, ctx->stream);
   double d[6];
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, ctx->d_diag_now, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
@@ -618,10 +657,12 @@ int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows) {
   if (!olbm::valid_cfg(k))
     return fail(ctx, LBM_EINVAL,
                 "launch kind %d shape %dx%d x %d rows invalid (kind 0: bx a multiple of 32, bx*by <= 512, rows 1..64; "
-                "kind 1: rows 1..4096)",
+                "kind 1: rows 1..4096; kind 2: rows 1..4096, bx = 0)",
                 kind, bx, by, rows);
   if (ctx->prec == LBM_F64_DF && (k.kind != 0 || bx * by > 256))
     return fail(ctx, LBM_EINVAL, "storage form LBM_F64_DF takes launch kind 0 with at most 256 threads a block");
+  if (k.kind == 2 && ctx->prec != LBM_F32_SHIFT && ctx->prec != LBM_F16_SHIFT)
+    return fail(ctx, LBM_EINVAL, "launch kind 2 (two steps a launch) applies to the shifted storage forms");
   if (ctx->prec == LBM_F64 && k.kind == 1 && bx != 0)
     return fail(ctx, LBM_EINVAL, "storage form LBM_F64 takes launch kind 1 with one CTA per tile (bx = 0)");
   const long long need = olbm::step_blocks(ctx->g, k, ctx->prec);
@@ -629,18 +670,18 @@ int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->side);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_launch sync");
-    double* p[2] = {nullptr, nullptr};
-    e = cudaMalloc(&p[0], sizeof(double) * 5 * (size_t)need);
-    if (e == cudaSuccess) e = cudaMalloc(&p[1], sizeof(double) * 5 * (size_t)need);
+    double* p[lbm_ctx::kParts] = {};
+    for (int b = 0; b < lbm_ctx::kParts && e == cudaSuccess; ++b)
+      e = cudaMalloc(&p[b], sizeof(double) * 5 * (size_t)need);
     if (e != cudaSuccess) {
-      cudaFree(p[0]);
+      for (int b = 0; b < lbm_ctx::kParts; ++b) cudaFree(p[b]);
       cudaGetLastError();
       return fail(ctx, LBM_ENOMEM, "lbm_set_launch: %s", cudaGetErrorString(e));
     }
-    cudaFree(ctx->d_partials);
-    cudaFree(ctx->d_partials2);
-    ctx->d_partials = p[0];
-    ctx->d_partials2 = p[1];
+    for (int b = 0; b < lbm_ctx::kParts; ++b) {
+      cudaFree(ctx->d_parts[b]);
+      ctx->d_parts[b] = p[b];
+    }
     ctx->parts_cap = need;
   }
   ctx->cfg = k;

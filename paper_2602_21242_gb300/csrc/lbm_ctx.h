@@ -18,20 +18,22 @@ struct lbm_ctx {
   bool initialised = false;
   cudaStream_t stream = nullptr;
   olbm::LaunchCfg cfg{};
-  double* d_partials = nullptr;
+  // Per-block diagnostics partials, kParts buffers of parts_cap blocks each (d_parts[0]
+  // also serves lbm_diagnostics). Consecutive diagnosed steps take the buffers in turn,
+  // and the final sum of step t runs on a second stream while later steps run; lbm_step
+  // joins that stream back into `stream` before it returns. A two-step launch takes two
+  // buffers at once, so the next launch's buffers are never the ones still being summed.
+  static constexpr int kParts = 4;
+  double* d_parts[kParts] = {nullptr, nullptr, nullptr, nullptr};
   long long nparts = 0;      // partials the step kernel writes under cfg
-  long long parts_cap = 0;   // partials allocated (each of the two buffers)
-  // Fused diagnostics: consecutive diagnosed steps alternate between two partials
-  // buffers, and the final sum of step t runs on a second stream while step t + 1
-  // runs; lbm_step joins that stream back into `stream` before it returns.
-  double* d_partials2 = nullptr;
+  long long parts_cap = 0;   // partials allocated (each buffer)
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_step[2] = {nullptr, nullptr};  // partials of buffer b written (on `stream`)
-  cudaEvent_t ev_fin[2] = {nullptr, nullptr};   // partials of buffer b summed (on `side`)
+  cudaEvent_t ev_step[kParts] = {};  // partials of buffer b written (on `stream`)
+  cudaEvent_t ev_fin[kParts] = {};   // partials of buffer b summed (on `side`)
   cudaEvent_t ev_io = nullptr;                  // lbm_run_host: moments written (on `stream`)
   cudaEvent_t ev_rebind = nullptr;              // lbm_set_stream: end of the old stream's work
-  bool fin_pending[2] = {false, false};
-  int pbuf = 0;  // partials buffer of the next diagnosed step
+  bool fin_pending[kParts] = {};
+  int pbuf = 0;  // partials buffer of the next diagnosed step (0 .. kParts - 1)
   double* d_diag = nullptr;      // [6] latest fused diagnostics (out5 + time)
   double* d_diag_now = nullptr;  // [6] scratch of lbm_diagnostics
   unsigned long long* d_sticky = nullptr;

@@ -535,7 +535,17 @@ inline bool uses_pairs(int prec, const Geometry& g) { return (prec == 1 || prec 
 // The pipeline kernel (launch kind 1) applies to the shifted forms and FP64, any nx.
 inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
   (void)g;
-  return k.kind == 1 && (prec == 0 || prec == 1 || prec == 2);
+  return (k.kind == 1 && (prec == 0 || prec == 1 || prec == 2)) || (k.kind == 2 && (prec == 1 || prec == 2));
+}
+// Two-step tiles (kind 2): 2 NC - 2 output columns; nx a multiple of the chunk.
+inline int stream2_width(int prec) { return 2 * (prec == 1 ? kStreamNC32 : kStreamNC16) - 2; }
+inline bool step2_applies(int prec, const Geometry& g, const LaunchCfg& k) {
+  const int ch = prec == 1 ? 4 : 8;
+  return k.kind == 2 && (prec == 1 || prec == 2) && g.nx >= ch && g.nx % ch == 0;
+}
+inline dim3 step2_grid(const Geometry& g, const LaunchCfg& k, int prec) {
+  const int w = stream2_width(prec);
+  return dim3((g.nx + w - 1) / w, (g.ny + k.rows - 1) / k.rows);
 }
 inline dim3 step_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   if (uses_stream(prec, g, k)) {

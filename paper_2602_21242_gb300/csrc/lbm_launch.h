@@ -13,7 +13,11 @@ namespace olbm {
 // kind 1 (shifted forms and FP64, any nx): the bulk-copy pipeline over
 // tiles of stream_width(prec) columns by `rows` rows; bx = 0 launches one CTA
 // per tile, bx > 0 (shifted forms) a persistent grid of bx CTAs per SM (at
-// most the resident count) looping over the tiles; by unused.
+// most the resident count) looping over the tiles; by unused. kind 2 (shifted
+// forms): two steps per launch (step2_stream_kernel, one CTA per tile of
+// 2 NC - 2 columns by `rows` rows) wherever two steps follow each other, nx is a
+// multiple of the 16-byte chunk and no walls are set; a single step (the last
+// of an odd count) takes the kind 1 pipeline with the same rows; bx = 0.
 struct LaunchCfg {
   int bx = 32, by = 8, rows = 1, kind = 0;
   int cap = 0;  // kind 1: most CTAs launched (a multiple of the SM count); 0 = one CTA per tile
@@ -21,6 +25,7 @@ struct LaunchCfg {
 
 inline bool valid_cfg(const LaunchCfg& k) {
   if (k.kind == 1) return k.rows >= 1 && k.rows <= 4096 && k.bx >= 0 && k.bx <= 64;
+  if (k.kind == 2) return k.rows >= 1 && k.rows <= 4096 && k.bx == 0;
   return k.kind == 0 && k.bx >= 32 && k.bx % 32 == 0 && k.by >= 1 && k.bx * k.by <= 512 && k.rows >= 1 &&
          k.rows <= 64;
 }
@@ -38,6 +43,9 @@ struct StepArgs {
   int* err = nullptr;  // device flag set by a bounded wait that gave up (pipeline kernel)
   int* sched = nullptr;  // two ints, zero between launches: tile counter of the persistent pipeline kernel
   long long* parts_used = nullptr;  // out: diagnostics partials the launch wrote (its grid size)
+  // two-step launches (kind 2): diagnostics of the second step into partials2
+  bool diag2 = false;
+  double* partials2 = nullptr;
 };
 
 // Number of thread blocks of the auxiliary node-parallel kernels and of the
@@ -50,6 +58,11 @@ long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec);
 // on one SM (launch kind 1) for a shifted storage form.
 int stream_tile_width(int prec);
 int stream_ctas_per_sm(int prec);
+// Whether a launch of kind 2 runs two steps (the shifted forms on a width that
+// is a multiple of the 16-byte chunk), and the blocks (= diagnostics partials)
+// of that two-step launch.
+bool uses_step2(int prec, const Geometry& g, const LaunchCfg& k);
+long long step2_blocks(const Geometry& g, const LaunchCfg& k, int prec);
 
 #define OLBM_DECLARE_LAUNCHERS(SUFFIX)                                                                        \
   cudaError_t launch_step_##SUFFIX(const StepArgs& a, cudaStream_t st);                                       \
@@ -70,6 +83,9 @@ OLBM_DECLARE_LAUNCHERS(f16)
 // storage form 3 (FP64 storage, double-float arithmetic): its own step kernel; the
 // other kernels are the FP64 form's (same storage)
 cudaError_t launch_step_f64df(const StepArgs& a, cudaStream_t st);
+// two steps per launch (kind 2) for the shifted forms
+cudaError_t launch_step2_f32(const StepArgs& a, cudaStream_t st);
+cudaError_t launch_step2_f16(const StepArgs& a, cudaStream_t st);
 
 // Record a message for lbm_last_error(NULL) on this thread; returns status.
 int set_thread_error(int status, const char* fmt, ...);

@@ -17,10 +17,20 @@ long long diag_blocks(const Geometry& g) {
 
 long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec) {
   const dim3 gr = step_grid(g, k, prec);
-  return (long long)gr.x * gr.y;
+  const long long one = (long long)gr.x * gr.y;
+  if (!step2_applies(prec, g, k)) return one;
+  const dim3 g2 = step2_grid(g, k, prec);
+  return std::max(one, (long long)g2.x * g2.y);  // kind 2 also launches single steps
 }
 
 int stream_tile_width(int prec) { return stream_width(prec); }
+
+bool uses_step2(int prec, const Geometry& g, const LaunchCfg& k) { return step2_applies(prec, g, k); }
+
+long long step2_blocks(const Geometry& g, const LaunchCfg& k, int prec) {
+  const dim3 gr = step2_grid(g, k, prec);
+  return (long long)gr.x * gr.y;
+}
 
 // The ring fits three times in an SM's shared memory for both shifted forms;
 // FP16 is compiled for three CTAs (registers), FP32 (160 threads) fits them.

@@ -1,0 +1,286 @@
+// lbm_stream2.cuh -- two steps of Eq. 1 per launch for the shifted storage
+// forms (temporal blocking of the bulk-copy pipeline; same per-node arithmetic
+// and the same rounding to the storage type between the steps, so the result is
+// bit-identical to two single steps).
+//
+// A CTA owns output columns [x0, x0 + w) and rows [y0, y0 + H) of step t + 1.
+// They pull step t's post-collision values s1 at rows y0 - 1 .. y0 + H and
+// columns x0 - 1 .. x0 + w, which pull the stored state at rows y0 - 2 ..
+// y0 + H + 1 and columns x0 - 2 .. x0 + w + 1. The producer warp streams, for
+// each s1 row, the nine pulled plane rows of columns x0 - 2 .. x0 + w + 1 (from
+// the 16-byte aligned chunk at or left of x0 - 2, in up to three bulk copies
+// per plane where the range wraps around the lattice) into a ring of STAGES
+// slots. Consumer thread t computes the s1 node pair (x0 - 1 + 2t, x0 + 2t),
+// rounds it to the storage type into a four-row window in shared memory and,
+// once every consumer warp has written s1 row r, the output pair
+// (x0 + 2t, x0 + 2t + 1) of row r - 1 from the window. The window's four rows
+// need one wait a row: s1 row r + 1 overwrites row r - 3, which the last read
+// (output row r - 2) finished before its warp wrote s1 row r.
+//
+// With NC consumers a full strip is w = 2 NC - 2 columns (the s1 range is two
+// columns wider). The range's wrap-around copies are aligned when nx is a
+// multiple of the chunk (4 FP32 or 8 FP16 elements); other widths take the
+// single-step kernels. s1 rows and columns outside the tile are computed in
+// every tile that needs them (2 rows and 2 columns of each tile, about 1/H +
+// 1/w more collisions) and counted in the diagnostics of step t once, by the
+// tile that owns them.
+//
+// Every wait is bounded (ring mbarriers and the window's mbarriers). A warp
+// whose wait gave up records the error and stops waiting and computing; the
+// other warps then give up at their next wait. No named barrier is used, so no
+// warp can be left waiting for one that has left.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace olbm {
+
+template <int PREC, int NC, int STAGES> struct Stream2Shape {
+  using S = typename Form<PREC>::S;
+  static constexpr int CH = 16 / (int)sizeof(S);                // elements in one 16-byte chunk
+  static constexpr int W = 2 * NC - 2;                          // output columns of a full strip
+  static constexpr int kSeg = (W + 4 + CH - 1) / CH * CH + CH;  // ring elements per plane (aligned start)
+  static constexpr int kWin = 2 * NC;                           // window elements per plane (s1 columns)
+  static constexpr int kSlotBytes = 9 * kSeg * (int)sizeof(S);
+  static constexpr int kRingBytes = STAGES * kSlotBytes;
+  static constexpr int kWinBytes = 4 * 9 * kWin * (int)sizeof(S);
+  static constexpr int kBarBytes = (2 * STAGES + 4) * 8;
+  static constexpr int kSmemBytes = kRingBytes + kWinBytes + kBarBytes;
+  static_assert(kSlotBytes % 16 == 0 && kWinBytes % 16 == 0, "16-byte aligned ring and window");
+};
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <int PREC, int NC, int STAGES> struct Pipeline2 {
+  using S = typename Form<PREC>::S;
+  using Shape = Stream2Shape<PREC, NC, STAGES>;
+  static constexpr int CH = Shape::CH, SEG = Shape::kSeg, WIN = Shape::kWin, W = Shape::W;
+  static constexpr int kConsumerWarps = NC / 32;
+  S* ring;
+  S* win;
+  unsigned long long* full;
+  unsigned long long* empty;
+  unsigned long long* wbar;  // [4]: s1 row of window slot q written by every consumer warp
+  int k = 0;                 // ring items issued (producer) or consumed
+
+  __device__ __forceinline__ explicit Pipeline2(unsigned char* smem)
+      : ring(reinterpret_cast<S*>(smem)),
+        win(reinterpret_cast<S*>(smem + Shape::kRingBytes)),
+        full(reinterpret_cast<unsigned long long*>(smem + Shape::kRingBytes + Shape::kWinBytes)),
+        empty(full + STAGES),
+        wbar(full + 2 * STAGES) {}
+
+  __device__ __forceinline__ void init() {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < STAGES; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], kConsumerWarps);
+      }
+      for (int q = 0; q < 4; ++q) mbar_init(&wbar[q], kConsumerWarps);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+
+  // Producer warp: the pulled rows of s1 rows y0 - 1 .. y0 + rows, one slot each.
+  __device__ __forceinline__ bool produce(const S* __restrict__ src, const Geometry& g, int x0, int w, int y0,
+                                          int rows, int lane, int* err) {
+    const int xa = floor_div(x0 - 2, CH) * CH;                // aligned start (may be negative: wraps)
+    const int xe = (x0 + w + 2 + CH - 1) / CH * CH;           // aligned end (may pass nx: wraps)
+    // up to three pieces per plane row: (global column, slot element, elements)
+    const bool left = xa < 0, right = xe > g.nx;
+    const int np = 1 + (left ? 1 : 0) + (right ? 1 : 0);
+    const int mid_a = left ? 0 : xa, mid_b = right ? g.nx : xe;
+    const unsigned row_bytes = 9u * (unsigned)(xe - xa) * (unsigned)sizeof(S);
+    for (int it = 0; it < rows + 2; ++it, ++k) {
+      const int s = k % STAGES;
+      bool ok = true;
+      if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      S* slot = ring + (size_t)s * 9 * SEG;
+      if (lane == 0) mbar_expect_tx_arrive(&full[s], row_bytes);
+      __syncwarp();
+      if (lane < 9 * np) {
+        const int i = lane / np;
+        int p = lane - i * np;
+        if (!left) ++p;  // piece 0 is the left wrap, 1 the middle, 2 the right wrap
+        const int gcol = p == 0 ? xa + g.nx : (p == 1 ? mid_a : 0);
+        const int scol = p == 0 ? 0 : (p == 1 ? mid_a - xa : g.nx - xa);
+        const int len = p == 0 ? -xa : (p == 1 ? mid_b - mid_a : xe - g.nx);
+        int ys = (y0 - 1 + it - cy_of(i)) % g.ny;
+        if (ys < 0) ys += g.ny;
+        bulk_g2s(slot + i * SEG + scol, src + i * g.plane + (long long)ys * g.pitch + gcol,
+                 (unsigned)len * (unsigned)sizeof(S), &full[s]);
+      }
+    }
+    return true;
+  }
+
+  __device__ __forceinline__ void drain(int* err) {
+    for (int j = (k > STAGES ? k - STAGES : 0); j < k; ++j)
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[j % STAGES], (unsigned)((j / STAGES) & 1), err))) break;
+  }
+
+  // The nine pulled values of a node pair whose first node's c_ix = 0 value sits
+  // at the odd element e0 of each plane (stride `plane` elements): planes with
+  // c_ix = 0 at e0, e0 + 1 (they straddle a pair boundary and are read element by
+  // element), c_ix = +1 at e0 - 1, e0 and c_ix = -1 at e0 + 1, e0 + 2 (aligned
+  // pairs). From the window (WINDOW), plane i comes from the slot of s1 row
+  // it - 1 - c_iy; from the ring, all planes from the one slot at base.
+  template <bool WINDOW>
+  __device__ static __forceinline__ void pull9(const S* base, int plane, int it, int e0, f32x2 (&f)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int slot = WINDOW ? ((it - 1 - cy_of(i)) & 3) * 9 * WIN : 0;
+      const S* p = base + slot + i * plane + e0 - cx_of(i);
+      if (cx_of(i) == 0)
+        f[i] = lds_two(p, p + 1);
+      else
+        f[i] = lds_pair(p);
+    }
+  }
+
+  template <int MODEL, int DIAGS>
+  __device__ __forceinline__ void consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
+                                          int w, int y0, int rows, int t, int lane, DiagAcc<f32x2>& acc1,
+                                          DiagAcc<f32x2>& acc2, int* err) {
+    const int xa = floor_div(x0 - 2, CH) * CH;
+    const int e1 = 2 * t + 1 + (x0 - 2 - xa);  // ring element of s1 node x0 - 1 + 2t (c_ix = 0; odd)
+    const bool act1 = 2 * t < w + 2, act2 = 2 * t < w;
+    const bool mask_lo = t == 0, mask_hi = 2 * t == w;  // s1 nodes x0 - 1 and x0 + w: not this tile's
+    bool failed = false;
+    for (int it = 0; it < rows + 2; ++it, ++k) {
+      // ---- s1 row y0 - 1 + it
+      const int s = k % STAGES;
+      if (!failed) failed = !__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err));
+      f32x2 f[9];
+      if (!failed && act1) pull9<false>(ring + (size_t)s * 9 * SEG, SEG, it, e1, f);
+      __syncwarp();
+      if (!failed && lane == 0) mbar_arrive(&empty[s]);
+      const int q = it & 3;
+      if (!failed && act1) {
+        collide<MODEL, true, f32x2>(f, c, [&](NodeMoments<f32x2> m) {
+          if constexpr ((DIAGS & 1) != 0) {
+            if (it >= 1 && it <= rows) {
+              if (mask_lo) m.m0.v.x = m.jx.v.x = m.jy.v.x = m.ux.v.x = m.uy.v.x = 0.0f;
+              if (mask_hi) m.m0.v.y = m.jx.v.y = m.jy.v.y = m.ux.v.y = m.uy.v.y = 0.0f;
+              acc1.add(m);
+            }
+          }
+        });
+        S* wq = win + (size_t)q * 9 * WIN + 2 * t;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_pair(wq + i * WIN, f[i]);
+      }
+      __syncwarp();
+      if (!failed && lane == 0) mbar_arrive(&wbar[q]);
+      if (it < 2) continue;
+      // ---- output row y0 + it - 2 from s1 rows it - 2, it - 1, it of the window
+      if (!failed) failed = !__all_sync(0xffffffffu, mbar_wait(&wbar[q], (unsigned)((it >> 2) & 1), err));
+      if (failed || !act2) continue;
+      pull9<true>(win, WIN, it, 2 * t + 1, f);
+      collide<MODEL, true, f32x2>(f, c, [&](NodeMoments<f32x2> m) {
+        if constexpr ((DIAGS & 2) != 0) acc2.add(m);
+      });
+      S* o = dst + (long long)(y0 + it - 2) * g.pitch + x0 + 2 * t;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) st_pair(o + i * g.plane, f[i]);
+    }
+  }
+};
+
+// One CTA per tile: strip blockIdx.x (w = W columns, the last strip the rest),
+// output rows [blockIdx.y H, + H). DIAGS bit 0: diagnostics of step t into
+// partials1; bit 1: of step t + 1 into partials2.
+template <int MODEL, int PREC, int DIAGS, int NC, int STAGES>
+__global__ void __launch_bounds__(NC + 32, NC <= 128 ? 4 : 3) step2_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
+                                                                   typename Form<PREC>::S* __restrict__ dst,
+                                                                   Geometry g, Coef<f32x2> c,
+                                                                   double* __restrict__ partials1,
+                                                                   double* __restrict__ partials2, int H,
+                                                                   int* __restrict__ err) {
+  using P = Pipeline2<PREC, NC, STAGES>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  P pipe(smem);
+  pipe.init();
+  __syncthreads();
+  pdl_launch_dependents();
+  const int x0 = blockIdx.x * P::W, y0 = blockIdx.y * H;
+  const int w = min(P::W, g.nx - x0), rows = min(H, g.ny - y0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DiagAcc<f32x2> acc1, acc2;
+  if (warp == P::kConsumerWarps) {
+    pdl_wait();
+    pipe.produce(src, g, x0, w, y0, rows, lane, err);
+    pipe.drain(err);
+  } else if (threadIdx.x < NC) {
+    pipe.template consume<MODEL, DIAGS>(dst, g, c, x0, w, y0, rows, threadIdx.x, lane, acc1, acc2, err);
+  }
+  const long long b = (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5;
+  if constexpr ((DIAGS & 1) != 0) block_diag_acc(acc1, partials1 + b);
+  if constexpr (DIAGS == 3) __syncthreads();  // block_diag's shared scratch is reused
+  if constexpr ((DIAGS & 2) != 0) block_diag_acc(acc2, partials2 + b);
+}
+
+// ------------------------------------------------------------------ launcher
+// Two ring slots: the ring (2 x 9.5 KB) and the window (36 KB) let four FP32 CTAs
+// share an SM (measured at 4096^2, complete model, diagnostics every step: 2 slots
+// 142.0 GLUPS, 3 slots 133.6, 4 slots 134.3, 6 slots 113.3).
+#ifndef OLBM_STREAM2_STAGES
+#define OLBM_STREAM2_STAGES 2
+#endif
+constexpr int kStream2Stages = OLBM_STREAM2_STAGES;
+
+template <int PREC> struct Launch2 {
+  using S = typename Form<PREC>::S;
+  static constexpr int NC = PREC == 1 ? kStreamNC32 : kStreamNC16;
+  using Shape = Stream2Shape<PREC, NC, kStream2Stages>;
+  static_assert(Shape::W == 2 * NC - 2, "tile width of the launcher");
+
+  template <int MODEL, int DIAGS>
+  static cudaError_t run(const StepArgs& a, cudaStream_t st) {
+    auto kernel = step2_stream_kernel<MODEL, PREC, DIAGS, NC, kStream2Stages>;
+    // once per device: opt in to the large shared-memory carve-out
+    constexpr int kMaxDev = 64;
+    static bool ready[kMaxDev] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (!ready[dev]) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape::kSmemBytes);
+      if (e != cudaSuccess) return e;
+      ready[dev] = true;
+    }
+    const dim3 grid = step2_grid(a.g, a.cfg, PREC);
+    if (a.parts_used) *a.parts_used = (long long)grid.x * grid.y;
+    const Coef<f32x2> c = make_coef<f32x2>(a.theta, a.tau, a.rho_ref);
+    return launch_step_kernel(kernel, grid, dim3(NC + 32), Shape::kSmemBytes, st, (const S*)a.src, (S*)a.dst, a.g,
+                              c, a.partials, a.partials2, a.cfg.rows, a.err);
+  }
+
+  template <int MODEL>
+  static cudaError_t run_m(const StepArgs& a, cudaStream_t st) {
+    switch ((a.diag ? 1 : 0) | (a.diag2 ? 2 : 0)) {
+      case 0: return run<MODEL, 0>(a, st);
+      case 1: return run<MODEL, 1>(a, st);
+      case 2: return run<MODEL, 2>(a, st);
+      default: return run<MODEL, 3>(a, st);
+    }
+  }
+
+  static cudaError_t step2(const StepArgs& a, cudaStream_t st) {
+    if (!step2_applies(PREC, a.g, a.cfg) || a.err == nullptr) return cudaErrorInvalidConfiguration;
+    if ((a.diag && a.partials == nullptr) || (a.diag2 && a.partials2 == nullptr)) return cudaErrorInvalidValue;
+    switch (a.model) {
+      case 0: return run_m<0>(a, st);
+      case 1: return run_m<1>(a, st);
+      case 2: return run_m<2>(a, st);
+      case 3: return run_m<3>(a, st);
+      case 4: return run_m<4>(a, st);
+      case 5: return run_m<5>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+};
+
+}  // namespace olbm

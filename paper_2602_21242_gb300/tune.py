@@ -22,10 +22,12 @@ from . import capi
 _lock = threading.Lock()
 
 # (kind, bx, by, rows): kind 0 = column kernel; kind 1 = bulk-copy pipeline (shifted forms)
-# with bx = CTAs per SM (0 = one CTA per tile)
+# with bx = CTAs per SM (0 = one CTA per tile); kind 2 = two steps a launch
 LATTICE_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)], [4, 8, 16, 32])]
 PIPELINE_CANDIDATES = [(1, ctas, 1, rows) for ctas in (0, 2, 64) for rows in (4, 8, 16, 32, 64)]
+# kind 2: two steps a launch (shifted forms), one CTA per tile of `rows` rows
+TWO_STEP_CANDIDATES = [(2, 0, 1, rows) for rows in (8, 16, 32, 64)]
 BATCH_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
     [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)], [2, 4, 8, 16])]
 # kind 1: the pipeline with bx consumer threads (0 = default) on tiles of 2 bx columns x rows
@@ -90,7 +92,7 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
     if candidates is None:
         candidates = list(LATTICE_CANDIDATES)
         if lat.prec != capi.LBM_F64_DF:  # shapes a form does not take are skipped below
-            candidates += PIPELINE_CANDIDATES
+            candidates += PIPELINE_CANDIDATES + TWO_STEP_CANDIDATES
     best = None
     with Lattice(lat.nx, lat.ny, lat.theta, lat.tau, lat.model, lat.prec, device=lat.device,
                  stream=lat.stream) as tmp:

@@ -303,17 +303,20 @@ def test_full_size_sampled_parity_f64df(oracle, model):
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
 def test_full_size_sampled_shifted_forms(oracle, prec):
-    """The benchmark workload in the shifted forms (bulk-copy pipeline, diagnostics every step): 512
+    """The benchmark workload in the shifted forms (default launch, diagnostics every step): 512
     sampled nodes over one step against the oracle's FP64 collision of the same pre-collision values.
     Bound per population: storage rounding of the stored deviation (2^-24 FP32, 2^-11 FP16) plus a few
-    FP32 ulps of the O(deviation) arithmetic, as k 2^-p max|f - rest| with k = 16 (FP32), 1.5 (FP16)."""
+    FP32 ulps of the O(deviation) arithmetic, as k 2^-p max|f - rest| with k = 16 (FP32), 1.5 (FP16).
+    FP32 runs two steps a launch by default: its first 20 steps are 10 such launches, the sampled
+    step a single one, and the whole state after the 21 steps equals, bit for bit, 21 single steps
+    of the persistent pipeline."""
     n, theta = 4096, 1.0 / 3.0
     tau = oracle.tau_from_nu(0.005, theta)
     rho, ux, uy = flows.shear_wave(n, n, U=0.1, amp=0.01)
     w0, w1 = 1 - theta, theta / 2
     rest = np.array([w0, w1, w0, w1, w0, w1, w1, w1, w1]) * np.array([w0, w0, w1, w0, w1, w1, w1, w1, w1])
     with Lattice(n, n, theta, tau, "complete", prec) as lat:
-        assert capi.lbm_get_launch_ex(lat.ctx)[0] == 1  # the pipeline, as benchmarked
+        assert capi.lbm_get_launch_ex(lat.ctx)[0] == (2 if prec == "f32" else 1)  # as benchmarked
         lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
         lat.set_diagnostics_interval(1)
         lat.step(20)
@@ -327,6 +330,14 @@ def test_full_size_sampled_shifted_forms(oracle, prec):
         cx, cy = torch.tensor(CX).cuda(), torch.tensor(CY).cuda()
         post = f1[torch.arange(9).cuda()[None, :], (ys[:, None] + cy[None, :]) % ny,
                   (xs[:, None] + cx[None, :]) % nx].cpu().numpy()
+    if prec == "f32":
+        with Lattice(n, n, theta, tau, "complete", prec) as one:
+            capi.lbm_set_launch_ex(one.ctx, 1, 64, 1, 4)
+            one.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+            one.set_diagnostics_interval(1)
+            one.step(21)
+            assert torch.equal(one.state(), f1)
+    del f1
     k, p = (16, 24) if prec == "f32" else (1.5, 11)
     for j in range(512):
         want = oracle.collide_node(pre[j], theta, tau, 3)
