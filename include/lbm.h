@@ -329,8 +329,7 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * LBM_ETIMEOUT. Same results as kind 0 for even nx (FP32 rounding may differ in
  * the last bit for odd nx, where kind 0 updates single nodes) except the
  * diagnostics' summation order. Default for the shifted forms on lattices at
- * least 32 columns wide: FP32 kind 2 below on 32-row tiles (64 from 8192^2) where
- * nx is a multiple of 4, else the persistent grid on 4-row tiles; FP16 one CTA
+ * least 32 columns wide: FP32 kind 2 below on 32-row tiles (64 from 8192^2); FP16 one CTA
  * per tile with the height in {48, 40, 32, 24, 16} that best fills the last
  * wave of CTAs (halved further on small lattices).
  * kind 2 (shifted FP32/FP16 forms; bx = 0, by ignored): two steps per launch
@@ -340,9 +339,8 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * and computes step t + 1 from there, so the state is read and written once per
  * two steps. Results are bit-identical to two single steps (the diagnostics'
  * summation order aside). It applies where two steps of a call follow each
- * other, nx is a multiple of 4 (FP32) or 8 (FP16) and no walls are set; other
- * steps (the last of an odd count) take kind 1 with one CTA per tile of the
- * same height.
+ * other and no walls are set (any nx >= 2); other steps (the last of an odd
+ * count) take kind 1 with one CTA per tile of the same height.
  */
 int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows);
 int lbm_get_launch_ex(const lbm_ctx* ctx, int* kind, int* bx, int* by, int* rows);

@@ -86,13 +86,12 @@ olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
     }
   }
   while (k.rows > 1 && olbm::step_blocks(g, k, prec) < 4LL * sms) k.rows /= 2;
-  // FP32: two steps a launch (kind 2) on 32-row tiles where nx is a multiple of
-  // 4 (4096^2, diagnostics every step: 142 GLUPS against 92.6 for single steps;
-  // 8192^2 with 64-row tiles: 162 against 96.7); otherwise the persistent
-  // pipeline over all resident CTAs on 4-row tiles (measured 3-5 % above one CTA
-  // per tile at 4096^2 and 8192^2). FP16 is bound by its arithmetic, not by
-  // memory, and keeps single steps on one CTA per tile (two steps: 136.7 against
-  // 152 GLUPS at 4096^2).
+  // FP32: two steps a launch (kind 2) on 32-row tiles (4096^2, diagnostics every
+  // step: 142 GLUPS against 92.6 for single steps; 8192^2 with 64-row tiles: 162
+  // against 96.7); where it does not apply, the persistent pipeline over all
+  // resident CTAs on 4-row tiles (measured 3-5 % above one CTA per tile at 4096^2
+  // and 8192^2). FP16 is bound by its arithmetic, not by memory, and keeps single
+  // steps on one CTA per tile (two steps: 136.7 against 152 GLUPS at 4096^2).
   if (k.kind == 1 && prec == LBM_F32_SHIFT) {
     olbm::LaunchCfg k2 = k;
     k2.kind = 2, k2.bx = 0, k2.rows = g.nx >= 8192 && g.ny >= 8192 ? 64 : 32;

@@ -537,11 +537,10 @@ inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
   (void)g;
   return (k.kind == 1 && (prec == 0 || prec == 1 || prec == 2)) || (k.kind == 2 && (prec == 1 || prec == 2));
 }
-// Two-step tiles (kind 2): 2 NC - 2 output columns; nx a multiple of the chunk.
+// Two-step tiles (kind 2): 2 NC - 2 output columns; any nx >= 2.
 inline int stream2_width(int prec) { return 2 * (prec == 1 ? kStreamNC32 : kStreamNC16) - 2; }
 inline bool step2_applies(int prec, const Geometry& g, const LaunchCfg& k) {
-  const int ch = prec == 1 ? 4 : 8;
-  return k.kind == 2 && (prec == 1 || prec == 2) && g.nx >= ch && g.nx % ch == 0;
+  return k.kind == 2 && (prec == 1 || prec == 2) && g.nx >= 2;
 }
 inline dim3 step2_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   const int w = stream2_width(prec);

@@ -7,10 +7,12 @@
 // They pull step t's post-collision values s1 at rows y0 - 1 .. y0 + H and
 // columns x0 - 1 .. x0 + w, which pull the stored state at rows y0 - 2 ..
 // y0 + H + 1 and columns x0 - 2 .. x0 + w + 1. The producer warp streams, for
-// each s1 row, the nine pulled plane rows of columns x0 - 2 .. x0 + w + 1 (from
-// the 16-byte aligned chunk at or left of x0 - 2, in up to three bulk copies
-// per plane where the range wraps around the lattice) into a ring of STAGES
-// slots. Consumer thread t computes the s1 node pair (x0 - 1 + 2t, x0 + 2t),
+// each s1 row, the nine pulled plane rows of those columns into a ring of STAGES
+// slots: per plane the columns inside the lattice from the 16-byte aligned chunk
+// at or left of x0 - 2 (rounded up into the row padding at the right end), and,
+// where the range wraps around the lattice, the aligned chunk(s) holding columns
+// nx - 2 and nx - 1 (left of column 0) and the chunk of columns 0 .. into two
+// halo areas after the main part, so any width works. Consumer thread t computes the s1 node pair (x0 - 1 + 2t, x0 + 2t),
 // rounds it to the storage type into a four-row window in shared memory and,
 // once every consumer warp has written s1 row r, the output pair
 // (x0 + 2t, x0 + 2t + 1) of row r - 1 from the window. The window's four rows
@@ -18,9 +20,11 @@
 // (output row r - 2) finished before its warp wrote s1 row r.
 //
 // With NC consumers a full strip is w = 2 NC - 2 columns (the s1 range is two
-// columns wider). The range's wrap-around copies are aligned when nx is a
-// multiple of the chunk (4 FP32 or 8 FP16 elements); other widths take the
-// single-step kernels. s1 rows and columns outside the tile are computed in
+// columns wider). The consumer pairs whose columns wrap (the first pair of the
+// first strip, the last ones of the strip that reaches nx) read element by
+// element through the halo areas; the others read aligned pairs from the main
+// part. On odd widths the last s1 and output pairs carry a node past the range
+// in their second lane, which is neither stored nor counted. s1 rows and columns outside the tile are computed in
 // every tile that needs them (2 rows and 2 columns of each tile, about 1/H +
 // 1/w more collisions) and counted in the diagnostics of step t once, by the
 // tile that owns them.
@@ -39,7 +43,8 @@ template <int PREC, int NC, int STAGES> struct Stream2Shape {
   using S = typename Form<PREC>::S;
   static constexpr int CH = 16 / (int)sizeof(S);                // elements in one 16-byte chunk
   static constexpr int W = 2 * NC - 2;                          // output columns of a full strip
-  static constexpr int kSeg = (W + 4 + CH - 1) / CH * CH + CH;  // ring elements per plane (aligned start)
+  static constexpr int kMain = (W + 4 + CH - 1) / CH * CH + CH;  // main part: columns from an aligned start
+  static constexpr int kSeg = kMain + 3 * CH;                    // + left halo (two chunks) + right halo (one)
   static constexpr int kWin = 2 * NC;                           // window elements per plane (s1 columns)
   static constexpr int kSlotBytes = 9 * kSeg * (int)sizeof(S);
   static constexpr int kRingBytes = STAGES * kSlotBytes;
@@ -54,7 +59,7 @@ __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b :
 template <int PREC, int NC, int STAGES> struct Pipeline2 {
   using S = typename Form<PREC>::S;
   using Shape = Stream2Shape<PREC, NC, STAGES>;
-  static constexpr int CH = Shape::CH, SEG = Shape::kSeg, WIN = Shape::kWin, W = Shape::W;
+  static constexpr int CH = Shape::CH, SEG = Shape::kSeg, MAIN = Shape::kMain, WIN = Shape::kWin, W = Shape::W;
   static constexpr int kConsumerWarps = NC / 32;
   S* ring;
   S* win;
@@ -82,15 +87,28 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
   }
 
   // Producer warp: the pulled rows of s1 rows y0 - 1 .. y0 + rows, one slot each.
+  // CONTIG (nx a multiple of the chunk): per plane the columns [xa, xe) from the
+  // aligned chunk at or left of x0 - 2 to past x0 + w + 1, contiguous, the parts
+  // left of 0 and right of nx copied from the other end of the row (aligned there
+  // too). Otherwise: the main part [m0, m1) of the columns inside the lattice
+  // (clipped at 0 and at the padded row end), then, if x0 == 0, the chunks
+  // [a0, a1 + CH) holding columns nx - 2 and nx - 1 at element MAIN, and, if the
+  // range passes nx, the chunk of columns 0 .. CH - 1 at element MAIN + 2 CH.
+  template <bool CONTIG>
   __device__ __forceinline__ bool produce(const S* __restrict__ src, const Geometry& g, int x0, int w, int y0,
                                           int rows, int lane, int* err) {
-    const int xa = floor_div(x0 - 2, CH) * CH;                // aligned start (may be negative: wraps)
-    const int xe = (x0 + w + 2 + CH - 1) / CH * CH;           // aligned end (may pass nx: wraps)
-    // up to three pieces per plane row: (global column, slot element, elements)
-    const bool left = xa < 0, right = xe > g.nx;
+    const int xa = floor_div(x0 - 2, CH) * CH;
+    const int xe = (x0 + w + 2 + CH - 1) / CH * CH;
+    const int nxr = (g.nx + CH - 1) / CH * CH;  // row padding holds the overhang
+    const int m0 = xa < 0 ? 0 : xa, m1 = min(xe, CONTIG ? g.nx : nxr);
+    const bool left = xa < 0, right = CONTIG ? xe > g.nx : x0 + w + 2 > g.nx;
+    const int a0 = CONTIG ? xa + g.nx : floor_div(g.nx - 2, CH) * CH;
+    const int a1 = CONTIG ? g.nx - CH : (g.nx - 1) / CH * CH;
+    const int llen = a1 + CH - a0, rlen = CONTIG ? xe - g.nx : CH;
+    const int lcol = CONTIG ? 0 : MAIN, rcol = CONTIG ? g.nx - xa : MAIN + 2 * CH;
     const int np = 1 + (left ? 1 : 0) + (right ? 1 : 0);
-    const int mid_a = left ? 0 : xa, mid_b = right ? g.nx : xe;
-    const unsigned row_bytes = 9u * (unsigned)(xe - xa) * (unsigned)sizeof(S);
+    const unsigned plane_elems = (unsigned)(m1 - m0) + (left ? (unsigned)llen : 0u) + (right ? (unsigned)rlen : 0u);
+    const unsigned row_bytes = 9u * plane_elems * (unsigned)sizeof(S);
     for (int it = 0; it < rows + 2; ++it, ++k) {
       const int s = k % STAGES;
       bool ok = true;
@@ -101,11 +119,11 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
       __syncwarp();
       if (lane < 9 * np) {
         const int i = lane / np;
-        int p = lane - i * np;
-        if (!left) ++p;  // piece 0 is the left wrap, 1 the middle, 2 the right wrap
-        const int gcol = p == 0 ? xa + g.nx : (p == 1 ? mid_a : 0);
-        const int scol = p == 0 ? 0 : (p == 1 ? mid_a - xa : g.nx - xa);
-        const int len = p == 0 ? -xa : (p == 1 ? mid_b - mid_a : xe - g.nx);
+        int p = lane - i * np;  // piece 0 the main part, 1 the left part (if any), 2 the right part
+        if (p == 1 && !left) p = 2;
+        const int gcol = p == 0 ? m0 : (p == 1 ? a0 : 0);
+        const int scol = p == 0 ? m0 - xa : (p == 1 ? lcol : rcol);
+        const int len = p == 0 ? m1 - m0 : (p == 1 ? llen : rlen);
         int ys = (y0 - 1 + it - cy_of(i)) % g.ny;
         if (ys < 0) ys += g.ny;
         bulk_g2s(slot + i * SEG + scol, src + i * g.plane + (long long)ys * g.pitch + gcol,
@@ -139,21 +157,46 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
     }
   }
 
-  template <int MODEL, int DIAGS>
+  // The same for a pair whose columns wrap around the lattice, element by element:
+  // column c of the main part at c - xa, columns -2, -1 in the left halo, columns
+  // nx, nx + 1, .. in the right halo.
+  __device__ static __forceinline__ void pull9_edge(const S* base, const Geometry& g, int xs, int xa,
+                                                    f32x2 (&f)[9]) {
+    const int a0 = floor_div(g.nx - 2, CH) * CH;
+    auto at = [&](int c) { return c < 0 ? MAIN + (c + g.nx - a0) : (c >= g.nx ? MAIN + 2 * CH + (c - g.nx) : c - xa); };
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const S* p = base + i * SEG;
+      f[i] = lds_two(p + at(xs - cx_of(i)), p + at(xs + 1 - cx_of(i)));
+    }
+  }
+
+  // CONTIG: the ring holds every column contiguously (produce<true>); otherwise the
+  // pairs whose columns wrap read through the halo areas.
+  template <int MODEL, int DIAGS, bool CONTIG>
   __device__ __forceinline__ void consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
                                           int w, int y0, int rows, int t, int lane, DiagAcc<f32x2>& acc1,
                                           DiagAcc<f32x2>& acc2, int* err) {
     const int xa = floor_div(x0 - 2, CH) * CH;
     const int e1 = 2 * t + 1 + (x0 - 2 - xa);  // ring element of s1 node x0 - 1 + 2t (c_ix = 0; odd)
-    const bool act1 = 2 * t < w + 2, act2 = 2 * t < w;
-    const bool mask_lo = t == 0, mask_hi = 2 * t == w;  // s1 nodes x0 - 1 and x0 + w: not this tile's
+    // (with nx a multiple of the chunk every strip's width is even: whole output pairs)
+    const bool act1 = 2 * t < w + 2, act2 = 2 * t < w, pair2 = CONTIG || 2 * t + 1 < w;
+    // the pair's columns wrap around the lattice
+    const bool edge = !CONTIG && ((x0 == 0 && t == 0) || x0 + 2 * t + 1 >= g.nx);
+    // s1 nodes outside [x0, x0 + w) (the border, and a node past the range on odd widths)
+    const bool mask_lo = !(t >= 1 && 2 * t <= w), mask_hi = !(2 * t < w);
     bool failed = false;
     for (int it = 0; it < rows + 2; ++it, ++k) {
       // ---- s1 row y0 - 1 + it
       const int s = k % STAGES;
       if (!failed) failed = !__all_sync(0xffffffffu, mbar_wait(&full[s], (unsigned)((k / STAGES) & 1), err));
       f32x2 f[9];
-      if (!failed && act1) pull9<false>(ring + (size_t)s * 9 * SEG, SEG, it, e1, f);
+      if (!failed && act1) {
+        if (edge)
+          pull9_edge(ring + (size_t)s * 9 * SEG, g, x0 - 1 + 2 * t, xa, f);
+        else
+          pull9<false>(ring + (size_t)s * 9 * SEG, SEG, it, e1, f);
+      }
       __syncwarp();
       if (!failed && lane == 0) mbar_arrive(&empty[s]);
       const int q = it & 3;
@@ -179,11 +222,19 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
       if (failed || !act2) continue;
       pull9<true>(win, WIN, it, 2 * t + 1, f);
       collide<MODEL, true, f32x2>(f, c, [&](NodeMoments<f32x2> m) {
-        if constexpr ((DIAGS & 2) != 0) acc2.add(m);
+        if constexpr ((DIAGS & 2) != 0) {
+          if (!pair2) m.m0.v.y = m.jx.v.y = m.jy.v.y = m.ux.v.y = m.uy.v.y = 0.0f;  // past the strip
+          acc2.add(m);
+        }
       });
       S* o = dst + (long long)(y0 + it - 2) * g.pitch + x0 + 2 * t;
+      if (pair2) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) st_pair(o + i * g.plane, f[i]);
+        for (int i = 0; i < 9; ++i) st_pair(o + i * g.plane, f[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_t(o + i * g.plane, f[i].v.x);
+      }
     }
   }
 };
@@ -210,10 +261,16 @@ __global__ void __launch_bounds__(NC + 32, NC <= 128 ? 4 : 3) step2_stream_kerne
   DiagAcc<f32x2> acc1, acc2;
   if (warp == P::kConsumerWarps) {
     pdl_wait();
-    pipe.produce(src, g, x0, w, y0, rows, lane, err);
+    if (g.nx % P::CH == 0)
+      pipe.template produce<true>(src, g, x0, w, y0, rows, lane, err);
+    else
+      pipe.template produce<false>(src, g, x0, w, y0, rows, lane, err);
     pipe.drain(err);
   } else if (threadIdx.x < NC) {
-    pipe.template consume<MODEL, DIAGS>(dst, g, c, x0, w, y0, rows, threadIdx.x, lane, acc1, acc2, err);
+    if (g.nx % P::CH == 0)
+      pipe.template consume<MODEL, DIAGS, true>(dst, g, c, x0, w, y0, rows, threadIdx.x, lane, acc1, acc2, err);
+    else
+      pipe.template consume<MODEL, DIAGS, false>(dst, g, c, x0, w, y0, rows, threadIdx.x, lane, acc1, acc2, err);
   }
   const long long b = (long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5;
   if constexpr ((DIAGS & 1) != 0) block_diag_acc(acc1, partials1 + b);
