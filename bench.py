@@ -462,10 +462,16 @@ def batch_sweep(dev, stream, peak_hbm, steps=1000, tile=None):
             ms = e0.elapsed_time(e1) / steps
             d = b.diagnostics()
             mass = sum(x[0] for x in d)
+            # a kind 2 batch runs two steps a launch in graph mode (36 B a node-step), single
+            # steps in persistent mode
+            two = shape[0] == 2 and mode == "graph"
+            bpn = 36 if two else 72
             res[f"batch256/complete/f32/{mode}"] = {
                 "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
-                "hbm_gbs": round(72 * nodes / (ms * 1e-3) / 1e9, 1),
-                "hbm_frac": round(72 * nodes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
+                "bytes_per_node_step": bpn, "hbm_gbs": round(bpn * nodes / (ms * 1e-3) / 1e9, 1),
+                "hbm_frac": round(bpn * nodes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
+                "vs_single_step_hbm_roof": round(72 * nodes / (ms * 1e-3) / 1e9 / peak_hbm, 4),
+                "steps_per_launch": 2 if two else 1,
                 "domains": 256, "nodes": nodes, "steps": steps, "tile": list(shape),
                 "fused_diagnostics": mode == "graph", "mass_rel_drift": abs(mass - sum(rho_k.sum() for rho_k in rho)) / mass}
     return res

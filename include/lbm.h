@@ -339,7 +339,7 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * and computes step t + 1 from there, so the state is read and written once per
  * two steps. Results are bit-identical to two single steps (the diagnostics'
  * summation order aside). It applies where two steps of a call follow each
- * other and no walls are set (any nx >= 2); other steps (the last of an odd
+ * other and no walls are set (any nx); other steps (the last of an odd
  * count) take kind 1 with one CTA per tile of the same height.
  */
 int lbm_set_launch_ex(lbm_ctx* ctx, int kind, int bx, int by, int rows);
@@ -387,14 +387,19 @@ int lbm_batch_set_launch(lbm_batch* b, int bx, int by, int rows);
 int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* ntiles);
 
 /* Launch kind and tile shape. kind 0: as lbm_batch_set_launch. kind 1 (the shifted
- * forms only; the default there): the bulk-copy pipeline of the single-lattice
+ * forms only; the FP16 default): the bulk-copy pipeline of the single-lattice
  * kind-1 kernel, one CTA of bx consumer threads (+ one producer warp) per tile of
  * 2 bx columns x rows rows (1..4096), any domain width; bx = 32, 64 or 128 (FP32),
  * 64, 128 or 256 (FP16), 0 = 128 (FP32) / 256 (FP16); narrower tiles waste less
  * of a strip on narrow domains. by is ignored. A domain's results equal those of
- * a single lattice stepped with the same launch kind. Errors: LBM_EINVAL (kind 1
- * on FP64 storage, bx or rows out of range). lbm_batch_get_launch_ex also reports
- * the kind. */
+ * a single lattice stepped with the same launch kind. kind 2 (shifted forms, bx =
+ * 0; the FP32 default, 32 rows): two steps a launch in graph mode (the two-step tile routine of the
+ * single-lattice kind 2 on tiles of 254 (FP32) or 510 (FP16) columns x rows
+ * rows of every domain, any width); an odd step and the persistent mode use
+ * the kind 1 tiles of the same height; results equal kind 1 bit for bit.
+ * Errors: LBM_EINVAL (kinds 1 and 2 on FP64 storage, bx or rows out of range).
+ * lbm_batch_get_launch_ex also reports the kind (and, for kind 2, the two-step
+ * tile count). */
 int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows);
 int lbm_batch_get_launch_ex(const lbm_batch* b, int* kind, int* bx, int* by, int* rows, int* ntiles);
 int lbm_batch_set_mode(lbm_batch* b, int mode);  /* enum lbm_batch_mode; default LBM_BATCH_GRAPH */

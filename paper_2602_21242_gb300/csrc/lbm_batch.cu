@@ -74,12 +74,13 @@ struct lbm_batch {
   double rho_ref = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;  // private non-blocking stream used only for graph capture
-  // Fused diagnostics in graph mode: diagnosed steps alternate between two partials
-  // buffers and each step's final sum is a branch of the graph (captured from a
-  // second stream) beside the following step.
+  // Fused diagnostics in graph mode: diagnosed steps take four partials buffers in
+  // turn (a two-step launch takes two) and each step's final sum is a branch of the
+  // graph (captured from a second stream) beside the following steps.
+  static constexpr int kParts = 4;
   cudaStream_t capture_side = nullptr;
-  cudaEvent_t ev_step[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fin[2] = {nullptr, nullptr};
+  cudaEvent_t ev_step[kParts] = {};
+  cudaEvent_t ev_fin[kParts] = {};
   std::vector<olbm::Geometry> geo;
   std::vector<double> theta, tau;
   std::vector<long long> node0;  // offset of each domain in packed field arrays
@@ -92,8 +93,12 @@ struct lbm_batch {
   int2* d_ranges = nullptr;
   long long* d_nodes = nullptr;
   int ntiles = 0;
-  double* d_partials = nullptr;
-  double* d_partials2 = nullptr;  // second buffer of the graph mode's fused diagnostics
+  // launch kind 2: the two-step tiles (2 NC - 2 columns) and their per-domain ranges;
+  // the single steps of an odd count take the kind 1 tiles above
+  int4* d_tiles2 = nullptr;
+  int2* d_ranges2 = nullptr;
+  int ntiles2 = 0;
+  double* d_parts[kParts] = {};  // per-tile partials, max(ntiles, ntiles2) each
   double* d_diag = nullptr;  // n * 5, latest fused diagnostics
   double* d_diag_now = nullptr;
   unsigned long long* d_sticky = nullptr;
@@ -108,6 +113,7 @@ struct lbm_batch {
   long long last_diag_t = -1;
   cudaGraphExec_t graph = nullptr;
   long long graph_key[4] = {-1, -1, -1, -1};
+  int graph_parity_end = 0;  // buffer holding the state after a replay of `graph`
   // Persistent mode: the barrier reset and the cooperative launch of n steps,
   // captured once per (n, buffer parity) and replayed.
   cudaGraphExec_t pgraph = nullptr;
@@ -152,46 +158,72 @@ template <typename CT> void fill_desc(lbm_batch* b, std::vector<olbm::Desc<CT>>&
   }
 }
 
-// Rebuild the tile list for the current launch shape.
-int build_tiles(lbm_batch* b) {
-  std::vector<int4> tiles;
-  std::vector<int2> ranges(b->n);
+// Tiles of cols x trows of every domain, domain after domain, and each domain's range.
+void cut_tiles(const lbm_batch* b, int cols, int trows, std::vector<int4>& tiles, std::vector<int2>& ranges) {
+  tiles.clear();
+  ranges.assign(b->n, make_int2(0, 0));
   for (int k = 0; k < b->n; ++k) {
     const olbm::Geometry& g = b->geo[k];
-    int cols, trows;
-    if (b->cfg.kind == 1) {
-      cols = 2 * olbm::batch_stream_nc(b->prec, b->cfg.bx);
-      trows = b->cfg.rows;
-    } else {
-      cols = olbm::uses_pairs(b->prec, g) ? 2 * b->cfg.bx : b->cfg.bx;
-      trows = b->cfg.by * b->cfg.rows;
-    }
     ranges[k].x = (int)tiles.size();
     for (int y0 = 0; y0 < g.ny; y0 += trows)
       for (int x0 = 0; x0 < g.nx; x0 += cols) tiles.push_back(make_int4(k, x0, y0, 0));
     ranges[k].y = (int)tiles.size() - ranges[k].x;
   }
-  if (tiles.size() > (size_t)0x7fffffff) return bfail(b, LBM_EINVAL, "too many tiles");
+}
+
+// Rebuild the tile lists for the current launch shape.
+int build_tiles(lbm_batch* b) {
+  std::vector<int4> tiles, tiles2;
+  std::vector<int2> ranges, ranges2;
+  if (b->cfg.kind == 1 || b->cfg.kind == 2) {
+    const int nc = olbm::batch_stream_nc(b->prec, b->cfg.kind == 2 ? 0 : b->cfg.bx);
+    cut_tiles(b, 2 * nc, b->cfg.rows, tiles, ranges);
+    if (b->cfg.kind == 2) cut_tiles(b, 2 * nc - 2, b->cfg.rows, tiles2, ranges2);
+  } else {
+    // kind 0: (bx or 2 bx) columns per domain, by x rows rows
+    tiles.clear();
+    ranges.assign(b->n, make_int2(0, 0));
+    for (int k = 0; k < b->n; ++k) {
+      const olbm::Geometry& g = b->geo[k];
+      const int cols = olbm::uses_pairs(b->prec, g) ? 2 * b->cfg.bx : b->cfg.bx, trows = b->cfg.by * b->cfg.rows;
+      ranges[k].x = (int)tiles.size();
+      for (int y0 = 0; y0 < g.ny; y0 += trows)
+        for (int x0 = 0; x0 < g.nx; x0 += cols) tiles.push_back(make_int4(k, x0, y0, 0));
+      ranges[k].y = (int)tiles.size() - ranges[k].x;
+    }
+  }
+  if (tiles.size() > (size_t)0x7fffffff || tiles2.size() > (size_t)0x7fffffff) return bfail(b, LBM_EINVAL, "too many tiles");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch tiles sync");
   cudaFree(b->d_tiles);
   cudaFree(b->d_ranges);
-  cudaFree(b->d_partials);
-  cudaFree(b->d_partials2);
+  cudaFree(b->d_tiles2);
+  cudaFree(b->d_ranges2);
   b->d_tiles = nullptr;
   b->d_ranges = nullptr;
-  b->d_partials = nullptr;
-  b->d_partials2 = nullptr;
+  b->d_tiles2 = nullptr;
+  b->d_ranges2 = nullptr;
+  for (int q = 0; q < lbm_batch::kParts; ++q) {
+    cudaFree(b->d_parts[q]);
+    b->d_parts[q] = nullptr;
+  }
   b->ntiles = (int)tiles.size();
-  if ((e = cudaMalloc(&b->d_tiles, sizeof(int4) * tiles.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_ranges, sizeof(int2) * ranges.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_partials, sizeof(double) * 5 * tiles.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_partials2, sizeof(double) * 5 * tiles.size())) != cudaSuccess)
-    return bcuda(b, e, "lbm_batch tile allocation");
-  if ((e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice)) !=
-          cudaSuccess)
-    return bcuda(b, e, "lbm_batch tile upload");
+  b->ntiles2 = (int)tiles2.size();
+  const size_t nparts = std::max(tiles.size(), tiles2.size());
+  e = cudaMalloc(&b->d_tiles, sizeof(int4) * tiles.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ranges, sizeof(int2) * ranges.size());
+  if (e == cudaSuccess && !tiles2.empty()) e = cudaMalloc(&b->d_tiles2, sizeof(int4) * tiles2.size());
+  if (e == cudaSuccess && !tiles2.empty()) e = cudaMalloc(&b->d_ranges2, sizeof(int2) * ranges2.size());
+  for (int q = 0; q < lbm_batch::kParts && e == cudaSuccess; ++q)
+    e = cudaMalloc(&b->d_parts[q], sizeof(double) * 5 * nparts);
+  if (e != cudaSuccess) return bcuda(b, e, "lbm_batch tile allocation");
+  e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tiles2.empty())
+    e = cudaMemcpy(b->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tiles2.empty())
+    e = cudaMemcpy(b->d_ranges2, ranges2.data(), sizeof(int2) * ranges2.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bcuda(b, e, "lbm_batch tile upload");
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -209,17 +241,18 @@ void free_batch(lbm_batch* b) {
   if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
   if (b->capture) cudaStreamDestroy(b->capture);
   if (b->capture_side) cudaStreamDestroy(b->capture_side);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < lbm_batch::kParts; ++k) {
     if (b->ev_step[k]) cudaEventDestroy(b->ev_step[k]);
     if (b->ev_fin[k]) cudaEventDestroy(b->ev_fin[k]);
+    cudaFree(b->d_parts[k]);
   }
   cudaFree(b->arena);
   cudaFree(b->d_desc);
   cudaFree(b->d_tiles);
   cudaFree(b->d_ranges);
+  cudaFree(b->d_tiles2);
+  cudaFree(b->d_ranges2);
   cudaFree(b->d_nodes);
-  cudaFree(b->d_partials);
-  cudaFree(b->d_partials2);
   cudaFree(b->d_diag);
   cudaFree(b->d_diag_now);
   cudaFree(b->d_sticky);
@@ -241,10 +274,13 @@ olbm::BatchLaunch view(const lbm_batch* b) {
   olbm::BatchLaunch v;
   v.model = b->model;
   v.cfg = b->cfg;
+  if (b->cfg.kind == 2) v.cfg.kind = 1, v.cfg.bx = 0;  // single steps: the kind 1 tiles
   v.desc = b->d_desc;
   v.tiles = b->d_tiles;
   v.ntiles = b->ntiles;
-  v.partials = b->d_partials;
+  v.tiles2 = b->d_tiles2;
+  v.ntiles2 = b->ntiles2;
+  v.partials = b->d_parts[0];
   v.perr = b->d_perr;
   v.bar = b->d_bar;
   v.ctr = b->d_ctr;
@@ -254,11 +290,24 @@ olbm::BatchLaunch view(const lbm_batch* b) {
 
 // Shared-memory opt-in of the pipelined kernels; before any launch or capture.
 cudaError_t prepare_launch(const lbm_batch* b) {
+  cudaError_t e;
   switch (b->prec) {
     case LBM_F64: return olbm::batch_prepare_f64(view(b));
-    case LBM_F32_SHIFT: return olbm::batch_prepare_f32(view(b));
-    default: return olbm::batch_prepare_f16(view(b));
+    case LBM_F32_SHIFT: e = olbm::batch_prepare_f32(view(b)); break;
+    default: e = olbm::batch_prepare_f16(view(b)); break;
   }
+  if (e != cudaSuccess || b->cfg.kind != 2) return e;
+  return b->prec == LBM_F32_SHIFT ? olbm::batch_prepare2_f32(view(b)) : olbm::batch_prepare2_f16(view(b));
+}
+
+// Two steps of every domain in one launch (kind 2) from buffer `parity`.
+cudaError_t launch_two_steps(const lbm_batch* b, bool diag1, bool diag2, int parity, cudaStream_t st,
+                             double* partials1, double* partials2) {
+  olbm::BatchLaunch v = view(b);
+  v.partials = partials1;
+  v.partials2 = partials2;
+  return b->prec == LBM_F32_SHIFT ? olbm::batch_step2_f32(v, diag1, diag2, parity, st)
+                                  : olbm::batch_step2_f16(v, diag1, diag2, parity, st);
 }
 
 cudaError_t launch_one_step(const lbm_batch* b, bool diag, int parity, cudaStream_t st, double* partials) {
@@ -287,9 +336,11 @@ cudaError_t launch_diag(const lbm_batch* b, cudaStream_t st) {
   }
 }
 
+// Per-domain sums of one launch's partials; ranges: the tile ranges of that launch's list.
 cudaError_t launch_finalize(const lbm_batch* b, const double* partials, double* out, unsigned long long* sticky,
-                            cudaStream_t st) {
-  olbm::batch_finalize_kernel<<<b->n, 256, 0, st>>>(partials, b->d_ranges, b->d_nodes, b->rho_ref, out, sticky);
+                            cudaStream_t st, const int2* ranges = nullptr) {
+  olbm::batch_finalize_kernel<<<b->n, 256, 0, st>>>(partials, ranges ? ranges : b->d_ranges, b->d_nodes,
+                                                    b->rho_ref, out, sticky);
   return cudaGetLastError();
 }
 
@@ -369,7 +420,7 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
   if (e == cudaSuccess) e = cudaMemset(b->d_diag, 0, sizeof(double) * 5 * n);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_side, cudaStreamNonBlocking);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < lbm_batch::kParts && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&b->ev_step[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fin[k], cudaEventDisableTiming);
   }
@@ -377,12 +428,15 @@ int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, c
     free_batch(b);
     return bfail(nullptr, LBM_ECUDA, "lbm_batch_create: %s", cudaGetErrorString(e));
   }
-  // Default tiles: FP64 the column routine with 64 x 2 threads and 16 rows; the
-  // shifted forms the bulk-copy pipeline on tiles of 32 rows.
+  // Default tiles: FP64 the column routine with 64 x 2 threads and 16 rows; FP16
+  // the bulk-copy pipeline on tiles of 32 rows; FP32 two steps a launch on tiles of
+  // 32 rows (256 Taylor-Green domains N ~ U{64..512}, diagnostics every step: 113.3
+  // GLUPS in graph mode against 83.3 for the single-step pipeline; the persistent
+  // mode takes single steps either way).
   if (prec == LBM_F64) {
     b->cfg.bx = 64, b->cfg.by = 2, b->cfg.rows = 16;
   } else {
-    b->cfg.kind = 1, b->cfg.bx = 0, b->cfg.by = 1, b->cfg.rows = 32;
+    b->cfg.kind = prec == LBM_F32_SHIFT ? 2 : 1, b->cfg.bx = 0, b->cfg.by = 1, b->cfg.rows = 32;
   }
   int s = build_tiles(b);
   if (s != LBM_OK) {
@@ -420,13 +474,14 @@ int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows) {
   int s = check_batch(b);
   if (s != LBM_OK) return s;
   if (kind == 0) return lbm_batch_set_launch(b, bx, by, rows);
-  if (kind != 1 || b->prec == LBM_F64 || rows < 1 || rows > 4096 || !olbm::batch_stream_nc_valid(b->prec, bx))
+  if ((kind != 1 && kind != 2) || b->prec == LBM_F64 || rows < 1 || rows > 4096 ||
+      !olbm::batch_stream_nc_valid(b->prec, bx) || (kind == 2 && bx != 0))
     return bfail(b, LBM_EINVAL,
-                 "launch kind %d, bx %d, %d rows invalid (kind 1: shifted storage forms only, bx = consumer threads "
-                 "0 (default), 32, 64 or 128 for FP32, 64, 128 or 256 for FP16, rows 1..4096)",
+                 "launch kind %d, bx %d, %d rows invalid (kinds 1 and 2: shifted storage forms only, bx = consumer "
+                 "threads 0 (default), 32, 64 or 128 for FP32, 64, 128 or 256 for FP16 (kind 2: 0), rows 1..4096)",
                  kind, bx, rows);
   olbm::LaunchCfg k;
-  k.kind = 1;
+  k.kind = kind;
   k.bx = bx;
   k.by = 1;
   k.rows = rows;
@@ -445,7 +500,7 @@ int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* n
   if (bx) *bx = b->cfg.bx;
   if (by) *by = b->cfg.by;
   if (rows) *rows = b->cfg.rows;
-  if (ntiles) *ntiles = b->ntiles;
+  if (ntiles) *ntiles = b->cfg.kind == 2 ? b->ntiles2 : b->ntiles;
   return LBM_OK;
 }
 
@@ -599,24 +654,50 @@ int lbm_batch_step(lbm_batch* b, int n) {
     e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step capture");
     cudaError_t le = cudaSuccess;
-    bool pending[2] = {false, false};
+    bool pending[lbm_batch::kParts] = {};
     int pb = 0, last = -1;
-    for (int k = 0; k < n && le == cudaSuccess; ++k) {
+    // the next free partials buffer (after its previous final sum) for a diagnosed step
+    auto take = [&](bool diag, int& q) {
+      q = -1;
+      if (!diag || le != cudaSuccess) return;
+      q = pb;
+      pb = (pb + 1) % lbm_batch::kParts;
+      if (pending[q]) le = cudaStreamWaitEvent(b->capture, b->ev_fin[q], 0);
+    };
+    // the final sum of buffer q (tile ranges of the launch that wrote it) beside the next steps
+    auto finish = [&](int q, const int2* ranges) {
+      if (q < 0 || le != cudaSuccess) return;
+      le = cudaEventRecord(b->ev_step[q], b->capture);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(b->capture_side, b->ev_step[q], 0);
+      if (le == cudaSuccess) le = launch_finalize(b, b->d_parts[q], b->d_diag, b->d_sticky, b->capture_side, ranges);
+      if (le == cudaSuccess) le = cudaEventRecord(b->ev_fin[q], b->capture_side);
+      pending[q] = true;
+      last = q;
+    };
+    auto due = [&](long long tk) { return b->diag_every > 0 && (tk % b->diag_every) == 0; };
+    int parity = b->cur;
+    for (int k = 0; k < n && le == cudaSuccess;) {
       const long long tk = b->t + k;
-      const bool diag = b->diag_every > 0 && (tk % b->diag_every) == 0;
-      double* parts = pb ? b->d_partials2 : b->d_partials;
-      if (diag && pending[pb]) le = cudaStreamWaitEvent(b->capture, b->ev_fin[pb], 0);  // buffer free again
-      if (le == cudaSuccess) le = launch_one_step(b, diag, (int)((b->cur + k) & 1), b->capture, parts);
-      if (le == cudaSuccess && diag) {
-        le = cudaEventRecord(b->ev_step[pb], b->capture);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(b->capture_side, b->ev_step[pb], 0);
-        if (le == cudaSuccess) le = launch_finalize(b, parts, b->d_diag, b->d_sticky, b->capture_side);
-        if (le == cudaSuccess) le = cudaEventRecord(b->ev_fin[pb], b->capture_side);
-        pending[pb] = true;
-        last = pb;
-        pb ^= 1;
+      int q1 = -1, q2 = -1;
+      if (b->cfg.kind == 2 && k + 1 < n) {  // two steps in one launch
+        take(due(tk), q1);
+        take(due(tk + 1), q2);
+        if (le == cudaSuccess)
+          le = launch_two_steps(b, q1 >= 0, q2 >= 0, parity, b->capture, b->d_parts[q1 < 0 ? 0 : q1],
+                                b->d_parts[q2 < 0 ? 0 : q2]);
+        finish(q1, b->d_ranges2);
+        finish(q2, b->d_ranges2);
+        k += 2;
+      } else {
+        take(due(tk), q1);
+        if (le == cudaSuccess)
+          le = launch_one_step(b, q1 >= 0, parity, b->capture, b->d_parts[q1 < 0 ? 0 : q1]);
+        finish(q1, b->d_ranges);
+        k += 1;
       }
+      parity ^= 1;
     }
+    b->graph_parity_end = parity;
     if (le == cudaSuccess && last >= 0) le = cudaStreamWaitEvent(b->capture, b->ev_fin[last], 0);  // join
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -638,7 +719,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     const long long ld = last - (last % b->diag_every);  // latest fused pass in [t, t + n), if any
     if (ld >= b->t) b->last_diag_t = ld;
   }
-  b->cur = (int)((b->cur + n) & 1);
+  b->cur = b->graph_parity_end;
   b->t += n;
   return LBM_OK;
 }
@@ -666,7 +747,7 @@ int lbm_batch_diagnostics(lbm_batch* b, double* h_out) {
   if (!h_out) return bfail(b, LBM_EINVAL, "lbm_batch_diagnostics: NULL output");
   if (!b->initialised) return bfail(b, LBM_ESTATE, "lbm_batch_diagnostics before lbm_batch_init");
   cudaError_t e = launch_diag(b, b->stream);
-  if (e == cudaSuccess) e = launch_finalize(b, b->d_partials, b->d_diag_now, nullptr, b->stream);
+  if (e == cudaSuccess) e = launch_finalize(b, b->d_parts[0], b->d_diag_now, nullptr, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_out, b->d_diag_now, sizeof(double) * 5 * b->n, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

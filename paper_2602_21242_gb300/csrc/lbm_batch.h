@@ -35,6 +35,7 @@ inline bool batch_stream_nc_valid(int prec, int bx) {
 struct BatchLaunch {
   int model = 0;
   LaunchCfg cfg{};           // kind 0: bx x by threads, rows; kind 1: bx = NC selector, rows = tile rows
+                             // (a batch of kind 2 hands its single steps to kind 1 with bx = 0)
   const void* desc = nullptr;  // Desc<double> (FP64) or Desc<float> (shifted forms), one per domain
   const int4* tiles = nullptr;  // (domain, x0, y0, 0)
   int ntiles = 0;
@@ -43,6 +44,10 @@ struct BatchLaunch {
   GridBarrier* bar = nullptr;  // persistent mode
   int* ctr = nullptr;          // persistent pipelined mode: two tile counters
   int sms = 1;
+  // two steps a launch (kind 2): tiles of 2 NC - 2 columns and the second step's partials
+  const int4* tiles2 = nullptr;
+  int ntiles2 = 0;
+  double* partials2 = nullptr;
 };
 
 #define OLBM_DECLARE_BATCH(SUFFIX)                                                                          \
@@ -54,5 +59,12 @@ struct BatchLaunch {
 OLBM_DECLARE_BATCH(f64)
 OLBM_DECLARE_BATCH(f32)
 OLBM_DECLARE_BATCH(f16)
+
+// Two steps a launch (kind 2, shifted forms): the tiles2 list, step t's diagnostics
+// into partials (diag1), step t + 1's into partials2 (diag2).
+cudaError_t batch_prepare2_f32(const BatchLaunch& b);
+cudaError_t batch_prepare2_f16(const BatchLaunch& b);
+cudaError_t batch_step2_f32(const BatchLaunch& b, bool diag1, bool diag2, int parity, cudaStream_t st);
+cudaError_t batch_step2_f16(const BatchLaunch& b, bool diag1, bool diag2, int parity, cudaStream_t st);
 
 }  // namespace olbm

@@ -1,0 +1,12 @@
+// lbm_batch_f16_step2.cu -- two-step batch kernels (launch kind 2) for storage
+// form 2 (FP16 deviations; see lbm_batch_stream2.cuh).
+#include <atomic>
+
+#include "lbm_batch_stream2.cuh"
+
+namespace olbm {
+cudaError_t batch_prepare2_f16(const BatchLaunch& b) { return BatchOps2<2>::prepare(b); }
+cudaError_t batch_step2_f16(const BatchLaunch& b, bool diag1, bool diag2, int parity, cudaStream_t st) {
+  return BatchOps2<2>::step(b, diag1, diag2, parity, st);
+}
+}  // namespace olbm

@@ -537,10 +537,10 @@ inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
   (void)g;
   return (k.kind == 1 && (prec == 0 || prec == 1 || prec == 2)) || (k.kind == 2 && (prec == 1 || prec == 2));
 }
-// Two-step tiles (kind 2): 2 NC - 2 output columns; any nx >= 2.
+// Two-step tiles (kind 2): 2 NC - 2 output columns; any nx.
 inline int stream2_width(int prec) { return 2 * (prec == 1 ? kStreamNC32 : kStreamNC16) - 2; }
 inline bool step2_applies(int prec, const Geometry& g, const LaunchCfg& k) {
-  return k.kind == 2 && (prec == 1 || prec == 2) && g.nx >= 2;
+  return k.kind == 2 && (prec == 1 || prec == 2) && g.nx >= 1;
 }
 inline dim3 step2_grid(const Geometry& g, const LaunchCfg& k, int prec) {
   const int w = stream2_width(prec);

@@ -16,7 +16,7 @@ namespace olbm {
 // most the resident count) looping over the tiles; by unused. kind 2 (shifted
 // forms): two steps per launch (step2_stream_kernel, one CTA per tile of
 // 2 NC - 2 columns by `rows` rows) wherever two steps follow each other and no
-// walls are set (nx >= 2); a single step (the last of an odd count) takes the
+// walls are set (any nx); a single step (the last of an odd count) takes the
 // kind 1 pipeline with the same rows; bx = 0.
 struct LaunchCfg {
   int bx = 32, by = 8, rows = 1, kind = 0;
@@ -58,7 +58,7 @@ long long step_blocks(const Geometry& g, const LaunchCfg& k, int prec);
 // on one SM (launch kind 1) for a shifted storage form.
 int stream_tile_width(int prec);
 int stream_ctas_per_sm(int prec);
-// Whether a launch of kind 2 runs two steps (the shifted forms, nx >= 2), and
+// Whether a launch of kind 2 runs two steps (the shifted forms), and
 // the blocks (= diagnostics partials) of that two-step launch.
 bool uses_step2(int prec, const Geometry& g, const LaunchCfg& k);
 long long step2_blocks(const Geometry& g, const LaunchCfg& k, int prec);

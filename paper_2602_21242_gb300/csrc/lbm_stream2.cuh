@@ -101,7 +101,8 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
     const int xe = (x0 + w + 2 + CH - 1) / CH * CH;
     const int nxr = (g.nx + CH - 1) / CH * CH;  // row padding holds the overhang
     const int m0 = xa < 0 ? 0 : xa, m1 = min(xe, CONTIG ? g.nx : nxr);
-    const bool left = xa < 0, right = CONTIG ? xe > g.nx : x0 + w + 2 > g.nx;
+    // (a lattice one column wide has no other columns: its main part holds column 0)
+    const bool left = xa < 0 && g.nx > 1, right = (CONTIG ? xe > g.nx : x0 + w + 2 > g.nx) && g.nx > 1;
     const int a0 = CONTIG ? xa + g.nx : floor_div(g.nx - 2, CH) * CH;
     const int a1 = CONTIG ? g.nx - CH : (g.nx - 1) / CH * CH;
     const int llen = a1 + CH - a0, rlen = CONTIG ? xe - g.nx : CH;
@@ -159,11 +160,15 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
 
   // The same for a pair whose columns wrap around the lattice, element by element:
   // column c of the main part at c - xa, columns -2, -1 in the left halo, columns
-  // nx, nx + 1, .. in the right halo.
+  // nx, nx + 1, .. in the right halo (for nx >= 2 the pairs read no column below
+  // -2 or from 2 nx on).
   __device__ static __forceinline__ void pull9_edge(const S* base, const Geometry& g, int xs, int xa,
                                                     f32x2 (&f)[9]) {
     const int a0 = floor_div(g.nx - 2, CH) * CH;
-    auto at = [&](int c) { return c < 0 ? MAIN + (c + g.nx - a0) : (c >= g.nx ? MAIN + 2 * CH + (c - g.nx) : c - xa); };
+    auto at = [&](int c) {
+      if (g.nx == 1) return -xa;  // every column is column 0
+      return c < 0 ? MAIN + (c + g.nx - a0) : (c >= g.nx ? MAIN + 2 * CH + (c - g.nx) : c - xa);
+    };
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const S* p = base + i * SEG;

@@ -33,6 +33,8 @@ BATCH_CANDIDATES = [(0, bx, by, rows) for (bx, by), rows in itertools.product(
 # kind 1: the pipeline with bx consumer threads (0 = default) on tiles of 2 bx columns x rows
 # (shifted forms; widths a form does not offer are skipped)
 BATCH_PIPELINE_CANDIDATES = [(1, nc, 1, rows) for nc in (0, 32, 64, 128) for rows in (16, 32, 64)]
+# kind 2: two steps a launch (graph mode) on tiles of the default width
+BATCH_TWO_STEP_CANDIDATES = [(2, 0, 1, rows) for rows in (8, 16, 32, 64)]
 
 
 def cache_path() -> str:
@@ -131,7 +133,8 @@ def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, 
     zero = [torch.zeros((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
     best = None
     if candidates is None:
-        candidates = BATCH_CANDIDATES + (BATCH_PIPELINE_CANDIDATES if batch.prec != capi.LBM_F64 else [])
+        candidates = BATCH_CANDIDATES + (BATCH_PIPELINE_CANDIDATES + BATCH_TWO_STEP_CANDIDATES
+                                         if batch.prec != capi.LBM_F64 else [])
     for shape in candidates:
         shape = tuple(shape) if len(shape) == 4 else (0,) + tuple(shape)
         try:

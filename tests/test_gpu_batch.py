@@ -41,19 +41,21 @@ def make_batch(model, prec, mode, domains=DOMAINS):
 
 @pytest.mark.parametrize("mode", ["graph", "persistent"])
 @pytest.mark.parametrize("prec,kind,nc", [("f64", 0, 0), ("f32", 0, 0), ("f32", 1, 0), ("f32", 1, 32),
-                                           ("f16", 0, 0), ("f16", 1, 0), ("f16", 1, 64)])
+                                           ("f16", 0, 0), ("f16", 1, 0), ("f16", 1, 64), ("f32", 2, 0),
+                                           ("f16", 2, 0)])
 @pytest.mark.parametrize("model", [0, 3])
 def test_batch_bit_identical_to_single_lattices(model, prec, kind, nc, mode):
     """Kind 0 tiles run the column routine, kind 1 tiles the bulk-copy pipeline (any width, including
-    1 x 5 and odd widths, tiles of 2 nc columns); each matches a single lattice stepped with the same
-    launch kind."""
+    1 x 5 and odd widths, tiles of 2 nc columns), kind 2 two steps a launch (graph mode; the odd 13th
+    step and the persistent mode take single steps); each matches a single lattice stepped with the
+    same launch kind (kind 2 with kind 1, which it equals bit for bit)."""
     f0 = states(100 + model)
     steps = 13
     with make_batch(model, prec, mode) as b:
         if kind == 0:
             b.set_launch(0, 64, 4, 2)
         else:
-            b.set_launch(1, nc, 1, 8)
+            b.set_launch(kind, nc, 1, 8)
         assert b.launch()[0] == kind
         for k, f in enumerate(f0):
             b.set_state(k, f)
@@ -61,7 +63,8 @@ def test_batch_bit_identical_to_single_lattices(model, prec, kind, nc, mode):
         b.sync()
         got = [b.state(k).cpu().numpy() for k in range(b.n)]
     for k, (nx, ny, theta, tau) in enumerate(DOMAINS):
-        want = single_run(f0[k], nx, ny, theta, tau, model, prec, steps, kind=kind if prec != "f64" else None)
+        want = single_run(f0[k], nx, ny, theta, tau, model, prec, steps,
+                          kind=min(kind, 1) if prec != "f64" else None)
         np.testing.assert_array_equal(got[k], want, err_msg=f"domain {k} ({nx}x{ny})")
 
 
@@ -115,8 +118,12 @@ def test_batch_init_moments_and_diagnostics(oracle):
 
 
 def test_batch_launch_validation():
+    # defaults: FP32 two steps a launch, FP16 the single-step pipeline, on 32-row tiles
+    for prec, kind in (("f32", 2), ("f16", 1)):
+        with make_batch(3, prec, "graph") as b:
+            assert b.launch()[:4] == (kind, 0, 1, 32)
     with make_batch(3, "f32", "graph") as b:
-        for bad in [(1, 256, 1, 8), (1, 48, 1, 8), (1, 0, 1, 0), (2, 0, 1, 8)]:
+        for bad in [(1, 256, 1, 8), (1, 48, 1, 8), (1, 0, 1, 0), (2, 32, 1, 8), (3, 0, 1, 8)]:
             with pytest.raises(capi.LBMError):
                 b.set_launch(*bad)
     with make_batch(3, "f64", "graph") as b, pytest.raises(capi.LBMError):
@@ -144,3 +151,30 @@ def test_tuners(tmp_path):
         shape, ms = tune.tune_batch(b, candidates=[(32, 4, 4), (64, 2, 8), (1, 0, 1, 16)], steps=4, path=path)
         assert shape in [(0, 32, 4, 4), (0, 64, 2, 8), (1, 0, 1, 16)]
         assert b.launch()[:4] == shape
+
+
+@pytest.mark.parametrize("every", [1, 3])
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_batch_two_step_launch_diagnostics(prec, every):
+    """Two steps a launch in graph mode: every domain's state equals the kind 1 batch's bit for bit
+    after even and odd step counts, and the fused diagnostics of each domain agree within the FP32
+    block-sum bound (about 1e-7 of the mass here) at the same time stamp."""
+    doms = [(136, 40, 0.3, 0.7), (257, 33, 1 / 3, 0.6), (64, 64, 0.38, 0.8), (1, 7, 0.3, 0.9)]
+    f0 = states(400, doms)
+    out = {}
+    for kind in (1, 2):
+        with make_batch(3, prec, "graph", doms) as b:
+            b.set_launch(kind, 0, 1, 16)
+            b.set_diagnostics_interval(every)
+            for k, f in enumerate(f0):
+                b.set_state(k, f)
+            for n in (4, 3, 6):
+                b.step(n)
+            fused, t, status = b.step_diagnostics()
+            out[kind] = ([b.state(k).cpu().numpy() for k in range(b.n)], fused, t)
+    for k in range(len(doms)):
+        np.testing.assert_array_equal(out[2][0][k], out[1][0][k], err_msg=f"domain {k}")
+        scale = doms[k][0] * doms[k][1]
+        np.testing.assert_allclose(out[2][1][k][:4], out[1][1][k][:4], rtol=1e-6, atol=1e-6 * scale)
+        assert out[2][1][k][4] == out[1][1][k][4] == 0
+    assert out[1][2] == out[2][2] == (13 - 1) // every * every

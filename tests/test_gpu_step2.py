@@ -47,7 +47,7 @@ def _run(nx, ny, model, prec, f0, steps, launch, diag_every=0, chunks=(), walls=
 
 
 SIZES = [(4, 3), (8, 1), (12, 5), (64, 64), (254, 9), (256, 40), (260, 33), (508, 17), (516, 8), (1024, 70),
-         (2, 3), (3, 2), (37, 5), (255, 3), (257, 9), (509, 11), (511, 4), (66, 10), (130, 7)]
+         (1, 5), (2, 3), (3, 2), (37, 5), (255, 3), (257, 9), (509, 11), (511, 4), (66, 10), (130, 7)]
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
