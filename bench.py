@@ -462,9 +462,9 @@ def batch_sweep(dev, stream, peak_hbm, steps=1000, tile=None):
             ms = e0.elapsed_time(e1) / steps
             d = b.diagnostics()
             mass = sum(x[0] for x in d)
-            # a kind 2 batch runs two steps a launch in graph mode (36 B a node-step), single
-            # steps in persistent mode
-            two = shape[0] == 2 and mode == "graph"
+            # a kind 2 batch runs two steps a launch (graph mode) or a pair of steps between grid
+            # barriers (persistent mode): 36 B a node-step
+            two = shape[0] == 2
             bpn = 36 if two else 72
             res[f"batch256/complete/f32/{mode}"] = {
                 "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),

@@ -393,10 +393,13 @@ int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* n
  * 64, 128 or 256 (FP16), 0 = 128 (FP32) / 256 (FP16); narrower tiles waste less
  * of a strip on narrow domains. by is ignored. A domain's results equal those of
  * a single lattice stepped with the same launch kind. kind 2 (shifted forms, bx =
- * 0; the FP32 default, 32 rows): two steps a launch in graph mode (the two-step tile routine of the
- * single-lattice kind 2 on tiles of 254 (FP32) or 510 (FP16) columns x rows
- * rows of every domain, any width); an odd step and the persistent mode use
- * the kind 1 tiles of the same height; results equal kind 1 bit for bit.
+ * 0; the FP32 default, 32 rows): two steps a launch (the two-step tile routine
+ * of the single-lattice kind 2 on tiles of 254 (FP32) or 510 (FP16) columns x
+ * rows rows of every domain, any width): in graph mode n / 2 two-step launches,
+ * in persistent mode one cooperative launch looping over n / 2 pairs of steps;
+ * an odd last step uses the kind 1 tiles of the same height (in persistent mode
+ * a second cooperative launch captured in the same graph); results equal kind 1
+ * bit for bit.
  * Errors: LBM_EINVAL (kinds 1 and 2 on FP64 storage, bx or rows out of range).
  * lbm_batch_get_launch_ex also reports the kind (and, for kind 2, the two-step
  * tile count). */

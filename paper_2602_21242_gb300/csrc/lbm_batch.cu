@@ -27,6 +27,11 @@
 //                         LBM_ETIMEOUT. Loads bypass L1 (data written by other
 //                         blocks earlier in the same launch). No fused
 //                         diagnostics; lbm_batch_diagnostics computes them.
+// With launch kind 2 (shifted forms) both modes take two steps a launch: the
+// graph holds n / 2 two-step launches, the persistent kernel loops over n / 2
+// pairs of steps (barrier between pairs); an odd last step is a single-step
+// launch of the kind 1 tiles (in persistent mode a second cooperative launch in
+// the same graph, which keeps the first one's error flag).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -118,6 +123,7 @@ struct lbm_batch {
   // captured once per (n, buffer parity) and replayed.
   cudaGraphExec_t pgraph = nullptr;
   long long pgraph_key[2] = {-1, -1};
+  int pgraph_parity_end = 0;  // buffer holding the state after a replay of `pgraph`
   char err[320] = {0};
 };
 
@@ -320,12 +326,30 @@ cudaError_t launch_one_step(const lbm_batch* b, bool diag, int parity, cudaStrea
   }
 }
 
-cudaError_t launch_persistent(const lbm_batch* b, int n, int parity0, cudaStream_t st) {
+cudaError_t launch_persistent(const lbm_batch* b, int n, int parity0, cudaStream_t st, bool keep_err = false) {
+  olbm::BatchLaunch v = view(b);
+  v.keep_err = keep_err;
   switch (b->prec) {
-    case LBM_F64: return olbm::batch_persistent_f64(view(b), n, parity0, st);
-    case LBM_F32_SHIFT: return olbm::batch_persistent_f32(view(b), n, parity0, st);
-    default: return olbm::batch_persistent_f16(view(b), n, parity0, st);
+    case LBM_F64: return olbm::batch_persistent_f64(v, n, parity0, st);
+    case LBM_F32_SHIFT: return olbm::batch_persistent_f32(v, n, parity0, st);
+    default: return olbm::batch_persistent_f16(v, n, parity0, st);
   }
+}
+
+// Persistent mode with launch kind 2: n / 2 pairs of steps in one cooperative launch,
+// then, for odd n, the last step in a single-step one. Returns the parity after them.
+cudaError_t launch_persistent_pairs(const lbm_batch* b, int n, int parity0, cudaStream_t st, int& parity_end) {
+  const int pairs = n / 2;
+  olbm::BatchLaunch v = view(b);
+  cudaError_t e = b->prec == LBM_F32_SHIFT ? olbm::batch_persistent2_f32(v, pairs, parity0, st)
+                                           : olbm::batch_persistent2_f16(v, pairs, parity0, st);
+  int parity = parity0 ^ (pairs & 1);
+  if (e == cudaSuccess && (n & 1)) {
+    e = launch_persistent(b, 1, parity, st, true);
+    parity ^= 1;
+  }
+  parity_end = parity;
+  return e;
 }
 
 cudaError_t launch_diag(const lbm_batch* b, cudaStream_t st) {
@@ -616,7 +640,11 @@ int lbm_batch_step(lbm_batch* b, int n) {
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step persistent capture");
-      const cudaError_t le = launch_persistent(b, n, b->cur, b->capture);
+      int parity_end = (b->cur + n) & 1;
+      const cudaError_t le = b->cfg.kind == 2 && n >= 2
+                                 ? launch_persistent_pairs(b, n, b->cur, b->capture, parity_end)
+                                 : launch_persistent(b, n, b->cur, b->capture);
+      b->pgraph_parity_end = parity_end;
       e = cudaStreamEndCapture(b->capture, &g);
       if (le != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -637,7 +665,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     e = cudaMemcpyAsync(&timed_out, &b->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step persistent");
-    b->cur = (int)((b->cur + n) & 1);
+    b->cur = b->pgraph_parity_end;
     b->t += n;
     if (timed_out) return bfail(b, LBM_ETIMEOUT, "a grid barrier of the persistent batch kernel timed out");
     return LBM_OK;

@@ -48,6 +48,9 @@ struct BatchLaunch {
   const int4* tiles2 = nullptr;
   int ntiles2 = 0;
   double* partials2 = nullptr;
+  // persistent launches: reset only the barrier's count and generation, keeping an
+  // error flag that an earlier launch of the same call set
+  bool keep_err = false;
 };
 
 #define OLBM_DECLARE_BATCH(SUFFIX)                                                                          \
@@ -66,5 +69,8 @@ cudaError_t batch_prepare2_f32(const BatchLaunch& b);
 cudaError_t batch_prepare2_f16(const BatchLaunch& b);
 cudaError_t batch_step2_f32(const BatchLaunch& b, bool diag1, bool diag2, int parity, cudaStream_t st);
 cudaError_t batch_step2_f16(const BatchLaunch& b, bool diag1, bool diag2, int parity, cudaStream_t st);
+// npairs two-step pairs of every domain in one cooperative launch (persistent mode, kind 2)
+cudaError_t batch_persistent2_f32(const BatchLaunch& b, int npairs, int parity0, cudaStream_t st);
+cudaError_t batch_persistent2_f16(const BatchLaunch& b, int npairs, int parity0, cudaStream_t st);
 
 }  // namespace olbm

@@ -9,4 +9,7 @@ cudaError_t batch_prepare2_f16(const BatchLaunch& b) { return BatchOps2<2>::prep
 cudaError_t batch_step2_f16(const BatchLaunch& b, bool diag1, bool diag2, int parity, cudaStream_t st) {
   return BatchOps2<2>::step(b, diag1, diag2, parity, st);
 }
+cudaError_t batch_persistent2_f16(const BatchLaunch& b, int npairs, int parity0, cudaStream_t st) {
+  return BatchOps2<2>::persistent(b, npairs, parity0, st);
+}
 }  // namespace olbm

@@ -274,7 +274,7 @@ template <int PREC> struct BatchOps {
     int* ctr = b.ctr;
     void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows,
                     (void*)&bar, (void*)&ctr};
-    e = cudaMemsetAsync(b.bar, 0, sizeof(GridBarrier), st);
+    e = cudaMemsetAsync(b.bar, 0, b.keep_err ? 2 * sizeof(unsigned) : sizeof(GridBarrier), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.ctr, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(NC + 32), args, (size_t)bytes, st);
@@ -338,7 +338,7 @@ template <int PREC> struct BatchOps {
     GridBarrier* bar = b.bar;
     void* args[] = {(void*)&desc, (void*)&tiles, (void*)&ntiles, (void*)&parity0, (void*)&n, (void*)&rows,
                     (void*)&bar};
-    e = cudaMemsetAsync(b.bar, 0, sizeof(GridBarrier), st);
+    e = cudaMemsetAsync(b.bar, 0, b.keep_err ? 2 * sizeof(unsigned) : sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(b.cfg.bx, b.cfg.by), args, 0, st);
   }

@@ -67,6 +67,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
   unsigned long long* empty;
   unsigned long long* wbar;  // [4]: s1 row of window slot q written by every consumer warp
   int k = 0;                 // ring items issued (producer) or consumed
+  int kw = 0;                // window rows written by this CTA's consumers before the current tile
 
   __device__ __forceinline__ explicit Pipeline2(unsigned char* smem)
       : ring(reinterpret_cast<S*>(smem)),
@@ -94,9 +95,12 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
   // (clipped at 0 and at the padded row end), then, if x0 == 0, the chunks
   // [a0, a1 + CH) holding columns nx - 2 and nx - 1 at element MAIN, and, if the
   // range passes nx, the chunk of columns 0 .. CH - 1 at element MAIN + 2 CH.
+  // With tags (a CTA taking several tiles), each slot's tags entry is set to `tag`
+  // before the slot is armed.
   template <bool CONTIG>
   __device__ __forceinline__ bool produce(const S* __restrict__ src, const Geometry& g, int x0, int w, int y0,
-                                          int rows, int lane, int* err) {
+                                          int rows, int lane, int* err, volatile int* tags = nullptr,
+                                          int tag = 0) {
     const int xa = floor_div(x0 - 2, CH) * CH;
     const int xe = (x0 + w + 2 + CH - 1) / CH * CH;
     const int nxr = (g.nx + CH - 1) / CH * CH;  // row padding holds the overhang
@@ -116,7 +120,10 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
       if (k >= STAGES) ok = mbar_wait(&empty[s], (unsigned)((k / STAGES - 1) & 1), err);
       if (!__all_sync(0xffffffffu, ok)) return false;
       S* slot = ring + (size_t)s * 9 * SEG;
-      if (lane == 0) mbar_expect_tx_arrive(&full[s], row_bytes);
+      if (lane == 0) {
+        if (tags != nullptr) tags[s] = tag;
+        mbar_expect_tx_arrive(&full[s], row_bytes);
+      }
       __syncwarp();
       if (lane < 9 * np) {
         const int i = lane / np;
@@ -177,9 +184,13 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
   }
 
   // CONTIG: the ring holds every column contiguously (produce<true>); otherwise the
-  // pairs whose columns wrap read through the halo areas.
+  // pairs whose columns wrap read through the halo areas. The window rows of a CTA's
+  // tiles are numbered on (kw): a tile's first row takes the slot after the previous
+  // tile's last, and before its second row overwrites a slot that the previous tile's
+  // last output row may still be reading, every warp must have written the first.
+  // Returns false once a bounded wait gave up.
   template <int MODEL, int DIAGS, bool CONTIG>
-  __device__ __forceinline__ void consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
+  __device__ __forceinline__ bool consume(S* __restrict__ dst, const Geometry& g, const Coef<f32x2>& c, int x0,
                                           int w, int y0, int rows, int t, int lane, DiagAcc<f32x2>& acc1,
                                           DiagAcc<f32x2>& acc2, int* err) {
     const int xa = floor_div(x0 - 2, CH) * CH;
@@ -204,7 +215,10 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
       }
       __syncwarp();
       if (!failed && lane == 0) mbar_arrive(&empty[s]);
-      const int q = it & 3;
+      const int a = kw + it;  // this s1 row's number in the window
+      const int q = a & 3;
+      if (it == 1 && kw > 0 && !failed)  // the previous tile's last reads are done once every warp wrote row kw
+        failed = !__all_sync(0xffffffffu, mbar_wait(&wbar[kw & 3], (unsigned)((kw >> 2) & 1), err));
       if (!failed && act1) {
         collide<MODEL, true, f32x2>(f, c, [&](NodeMoments<f32x2> m) {
           if constexpr ((DIAGS & 1) != 0) {
@@ -223,9 +237,9 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
       if (!failed && lane == 0) mbar_arrive(&wbar[q]);
       if (it < 2) continue;
       // ---- output row y0 + it - 2 from s1 rows it - 2, it - 1, it of the window
-      if (!failed) failed = !__all_sync(0xffffffffu, mbar_wait(&wbar[q], (unsigned)((it >> 2) & 1), err));
+      if (!failed) failed = !__all_sync(0xffffffffu, mbar_wait(&wbar[q], (unsigned)((a >> 2) & 1), err));
       if (failed || !act2) continue;
-      pull9<true>(win, WIN, it, 2 * t + 1, f);
+      pull9<true>(win, WIN, a, 2 * t + 1, f);
       collide<MODEL, true, f32x2>(f, c, [&](NodeMoments<f32x2> m) {
         if constexpr ((DIAGS & 2) != 0) {
           if (!pair2) m.m0.v.y = m.jx.v.y = m.jy.v.y = m.ux.v.y = m.uy.v.y = 0.0f;  // past the strip
@@ -241,6 +255,8 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
         for (int i = 0; i < 9; ++i) st_t(o + i * g.plane, f[i].v.x);
       }
     }
+    kw += rows + 2;
+    return !failed;
   }
 };
 
