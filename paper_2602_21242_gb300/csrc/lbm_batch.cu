@@ -198,7 +198,8 @@ int build_tiles(lbm_batch* b) {
       ranges[k].y = (int)tiles.size() - ranges[k].x;
     }
   }
-  if (tiles.size() > (size_t)0x7fffffff || tiles2.size() > (size_t)0x7fffffff) return bfail(b, LBM_EINVAL, "too many tiles");
+  if (tiles.size() > (size_t)0x7fffffff || tiles2.size() > (size_t)0x7fffffff)
+    return bfail(b, LBM_EINVAL, "too many tiles");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch tiles sync");
   cudaFree(b->d_tiles);
@@ -224,7 +225,8 @@ int build_tiles(lbm_batch* b) {
     e = cudaMalloc(&b->d_parts[q], sizeof(double) * 5 * nparts);
   if (e != cudaSuccess) return bcuda(b, e, "lbm_batch tile allocation");
   e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !tiles2.empty())
     e = cudaMemcpy(b->d_tiles2, tiles2.data(), sizeof(int4) * tiles2.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !tiles2.empty())

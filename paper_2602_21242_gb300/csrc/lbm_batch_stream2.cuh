@@ -108,8 +108,9 @@ __global__ void __launch_bounds__(NC + 32, NC <= 128 ? OLBM_BATCH2_PERSISTENT_MI
         const Geometry g = d->g;
         const S* src = static_cast<const S*>(d->buf[parity]);
         const int w = min(P::W, g.nx - tl.y), rows = min(H, g.ny - tl.z);
-        const bool ok = g.nx % P::CH == 0 ? pipe.template produce<true>(src, g, tl.y, w, tl.z, rows, lane, err, tags, t)
-                                          : pipe.template produce<false>(src, g, tl.y, w, tl.z, rows, lane, err, tags, t);
+        const bool ok = g.nx % P::CH == 0
+                            ? pipe.template produce<true>(src, g, tl.y, w, tl.z, rows, lane, err, tags, t)
+                            : pipe.template produce<false>(src, g, tl.y, w, tl.z, rows, lane, err, tags, t);
         if (!ok) break;
       }
     } else if (threadIdx.x < NC) {

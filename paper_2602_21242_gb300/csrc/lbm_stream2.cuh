@@ -7,27 +7,28 @@
 // They pull step t's post-collision values s1 at rows y0 - 1 .. y0 + H and
 // columns x0 - 1 .. x0 + w, which pull the stored state at rows y0 - 2 ..
 // y0 + H + 1 and columns x0 - 2 .. x0 + w + 1. The producer warp streams, for
-// each s1 row, the nine pulled plane rows of those columns into a ring of STAGES
-// slots: per plane the columns inside the lattice from the 16-byte aligned chunk
-// at or left of x0 - 2 (rounded up into the row padding at the right end), and,
-// where the range wraps around the lattice, the aligned chunk(s) holding columns
-// nx - 2 and nx - 1 (left of column 0) and the chunk of columns 0 .. into two
-// halo areas after the main part, so any width works. Consumer thread t computes the s1 node pair (x0 - 1 + 2t, x0 + 2t),
-// rounds it to the storage type into a four-row window in shared memory and,
-// once every consumer warp has written s1 row r, the output pair
-// (x0 + 2t, x0 + 2t + 1) of row r - 1 from the window. The window's four rows
-// need one wait a row: s1 row r + 1 overwrites row r - 3, which the last read
-// (output row r - 2) finished before its warp wrote s1 row r.
+// each s1 row, the nine pulled plane rows of those columns into a ring of
+// STAGES slots: per plane the columns inside the lattice from the 16-byte
+// aligned chunk at or left of x0 - 2 (rounded up into the row padding at the
+// right end), and, where the range wraps around the lattice, the aligned
+// chunk(s) holding columns nx - 2 and nx - 1 (left of column 0) and the chunk
+// of columns 0 .. into two halo areas after the main part, so any width works.
+// Consumer thread t computes the s1 node pair (x0 - 1 + 2t, x0 + 2t), rounds it
+// to the storage type into a four-row window in shared memory and, once every
+// consumer warp has written s1 row r, the output pair (x0 + 2t, x0 + 2t + 1) of
+// row r - 1 from the window. The window's four rows need one wait a row: s1 row
+// r + 1 overwrites row r - 3, which the last read (output row r - 2) finished
+// before its warp wrote s1 row r.
 //
 // With NC consumers a full strip is w = 2 NC - 2 columns (the s1 range is two
 // columns wider). The consumer pairs whose columns wrap (the first pair of the
 // first strip, the last ones of the strip that reaches nx) read element by
 // element through the halo areas; the others read aligned pairs from the main
 // part. On odd widths the last s1 and output pairs carry a node past the range
-// in their second lane, which is neither stored nor counted. s1 rows and columns outside the tile are computed in
-// every tile that needs them (2 rows and 2 columns of each tile, about 1/H +
-// 1/w more collisions) and counted in the diagnostics of step t once, by the
-// tile that owns them.
+// in their second lane, which is neither stored nor counted. s1 rows and
+// columns outside the tile are computed in every tile that needs them (2 rows
+// and 2 columns of each tile, about 1/H + 1/w more collisions) and counted in
+// the diagnostics of step t once, by the tile that owns them.
 //
 // Every wait is bounded (ring mbarriers and the window's mbarriers). A warp
 // whose wait gave up records the error and stops waiting and computing; the
@@ -264,7 +265,8 @@ template <int PREC, int NC, int STAGES> struct Pipeline2 {
 // output rows [blockIdx.y H, + H). DIAGS bit 0: diagnostics of step t into
 // partials1; bit 1: of step t + 1 into partials2.
 template <int MODEL, int PREC, int DIAGS, int NC, int STAGES>
-__global__ void __launch_bounds__(NC + 32, NC <= 128 ? 4 : 3) step2_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
+__global__ void __launch_bounds__(NC + 32, NC <= 128 ? 4 : 3)
+    step2_stream_kernel(const typename Form<PREC>::S* __restrict__ src,
                                                                    typename Form<PREC>::S* __restrict__ dst,
                                                                    Geometry g, Coef<f32x2> c,
                                                                    double* __restrict__ partials1,
