@@ -184,7 +184,7 @@ int build_tiles(lbm_batch* b) {
   if (b->cfg.kind == 1 || b->cfg.kind == 2) {
     const int nc = olbm::batch_stream_nc(b->prec, b->cfg.kind == 2 ? 0 : b->cfg.bx);
     cut_tiles(b, 2 * nc, b->cfg.rows, tiles, ranges);
-    if (b->cfg.kind == 2) cut_tiles(b, 2 * nc - 2, b->cfg.rows, tiles2, ranges2);
+    if (b->cfg.kind == 2) cut_tiles(b, olbm::stream2_width(b->prec), b->cfg.rows, tiles2, ranges2);
   } else {
     // kind 0: (bx or 2 bx) columns per domain, by x rows rows
     tiles.clear();

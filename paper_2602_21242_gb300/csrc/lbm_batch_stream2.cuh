@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NC + 32, NC <= 128 ? OLBM_BATCH2_PERSISTENT_MI
 }
 
 template <int PREC> struct BatchOps2 {
-  static constexpr int NC = PREC == 1 ? kStreamNC32 : kStreamNC16;
+  static constexpr int NC = PREC == 1 ? kStream2NC32 : kStream2NC16;
   using Shape = Stream2Shape<PREC, NC, kStream2Stages>;
 
   template <auto K> static cudaError_t allow() {

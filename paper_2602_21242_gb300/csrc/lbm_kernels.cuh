@@ -386,6 +386,11 @@ namespace olbm {
 #define OLBM_STREAM_STAGES 8
 #endif
 constexpr int kStreamNC32 = 128, kStreamNC16 = OLBM_STREAM_NC16, kStreamStages = OLBM_STREAM_STAGES;
+// consumer threads of the two-step tiles (launch kind 2)
+#ifndef OLBM_STREAM2_NC16
+#define OLBM_STREAM2_NC16 256
+#endif
+constexpr int kStream2NC32 = 128, kStream2NC16 = OLBM_STREAM2_NC16;
 constexpr int kStreamNC64 = 128, kStreamStages64 = 4;
 inline int stream_width(int prec) {
   return prec == 0 ? kStreamNC64 : 2 * (prec == 1 ? kStreamNC32 : kStreamNC16);
@@ -538,7 +543,7 @@ inline bool uses_stream(int prec, const Geometry& g, const LaunchCfg& k) {
   return (k.kind == 1 && (prec == 0 || prec == 1 || prec == 2)) || (k.kind == 2 && (prec == 1 || prec == 2));
 }
 // Two-step tiles (kind 2): 2 NC - 2 output columns; any nx.
-inline int stream2_width(int prec) { return 2 * (prec == 1 ? kStreamNC32 : kStreamNC16) - 2; }
+inline int stream2_width(int prec) { return 2 * (prec == 1 ? kStream2NC32 : kStream2NC16) - 2; }
 inline bool step2_applies(int prec, const Geometry& g, const LaunchCfg& k) {
   return k.kind == 2 && (prec == 1 || prec == 2) && g.nx >= 1;
 }

@@ -312,7 +312,7 @@ constexpr int kStream2Stages = OLBM_STREAM2_STAGES;
 
 template <int PREC> struct Launch2 {
   using S = typename Form<PREC>::S;
-  static constexpr int NC = PREC == 1 ? kStreamNC32 : kStreamNC16;
+  static constexpr int NC = PREC == 1 ? kStream2NC32 : kStream2NC16;
   using Shape = Stream2Shape<PREC, NC, kStream2Stages>;
   static_assert(Shape::W == 2 * NC - 2, "tile width of the launcher");
 
