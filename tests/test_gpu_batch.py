@@ -178,3 +178,24 @@ def test_batch_two_step_launch_diagnostics(prec, every):
         np.testing.assert_allclose(out[2][1][k][:4], out[1][1][k][:4], rtol=1e-6, atol=1e-6 * scale)
         assert out[2][1][k][4] == out[1][1][k][4] == 0
     assert out[1][2] == out[2][2] == (13 - 1) // every * every
+
+
+@pytest.mark.parametrize("mode", ["graph", "persistent"])
+def test_batch_two_step_long_run(mode):
+    """Two steps a launch over 200 steps in calls of uneven length (odd calls end in a single step,
+    which flips the buffer parity the next call starts from): every domain equals the kind 1 batch bit
+    for bit."""
+    doms = [(136, 40, 0.3, 0.7), (257, 33, 1 / 3, 0.6), (64, 64, 0.38, 0.8), (3, 7, 0.3, 0.9), (511, 19, 0.26, 0.55)]
+    f0 = states(500, doms)
+    got = {}
+    for kind in (1, 2):
+        with make_batch(3, "f32", mode, doms) as b:
+            b.set_launch(kind, 0, 1, 16)
+            for k, f in enumerate(f0):
+                b.set_state(k, f)
+            for n in (7, 100, 1, 92):
+                b.step(n)
+            b.sync()
+            got[kind] = [b.state(k).cpu().numpy() for k in range(b.n)]
+    for k in range(len(doms)):
+        np.testing.assert_array_equal(got[2][k], got[1][k], err_msg=f"domain {k}")

@@ -122,3 +122,22 @@ def test_kind_two_is_refused_for_fp64_forms():
     with Lattice(16, 8, THETA, TAU, "complete", "f32") as lat:
         with pytest.raises(capi.LBMError, match="LBM_EINVAL"):
             capi.lbm_set_launch_ex(lat.ctx, 2, 64, 1, 16)  # one CTA per tile only
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_two_step_launch_long_run(prec):
+    """600 steps of a Taylor-Green flow in calls of uneven length, diagnostics every 7 steps: the
+    two-step launches stay equal to single steps bit for bit over a long run."""
+    nx, ny = 260, 130
+    fields = [torch.from_numpy(a).cuda() for a in flows.taylor_green(nx, ny, 0.08, THETA)]
+    out = []
+    for launch in ((1, 0, 1, 16), (2, 0, 1, 16)):
+        with Lattice(nx, ny, THETA, 0.53, "complete", prec) as lat:
+            capi.lbm_set_launch_ex(lat.ctx, *launch)
+            lat.set_diagnostics_interval(7)
+            lat.init(*fields)
+            for n in (1, 2, 3, 97, 200, 297):
+                lat.step(n)
+            out.append((lat.state(), lat.step_diagnostics()[1]))
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] == 595
