@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6800.0
 # steps a launch) captured at 4096^2.
 # Keyed by (storage, model, steps per launch).
 PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete", 1): 133.4, ("f32", "complete", 1): 68.8,
-                               ("f32", "complete", 2): 71.4}
+                               ("f32", "complete", 2): 72.1}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
 STEP_KERNEL = {"f64": "step_kernel_f64", "f64df": "step_kernel_df", "f32": "step_stream_persistent_kernel",

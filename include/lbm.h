@@ -329,7 +329,7 @@ int lbm_get_launch(const lbm_ctx* ctx, int* bx, int* by, int* rows);
  * LBM_ETIMEOUT. Same results as kind 0 for even nx (FP32 rounding may differ in
  * the last bit for odd nx, where kind 0 updates single nodes) except the
  * diagnostics' summation order. Default for the shifted forms on lattices at
- * least 32 columns wide: FP32 kind 2 below on 32-row tiles (64 from 8192^2); FP16 one CTA
+ * least 32 columns wide: FP32 kind 2 below on 24-row tiles (48 from 8192^2); FP16 one CTA
  * per tile with the height in {48, 40, 32, 24, 16} that best fills the last
  * wave of CTAs (halved further on small lattices).
  * kind 2 (shifted FP32/FP16 forms; bx = 0, by ignored): two steps per launch

@@ -86,15 +86,15 @@ olbm::LaunchCfg default_cfg(int prec, const olbm::Geometry& g, int sms) {
     }
   }
   while (k.rows > 1 && olbm::step_blocks(g, k, prec) < 4LL * sms) k.rows /= 2;
-  // FP32: two steps a launch (kind 2) on 32-row tiles (4096^2, diagnostics every
-  // step: 142 GLUPS against 92.6 for single steps; 8192^2 with 64-row tiles: 162
-  // against 96.7); where it does not apply, the persistent pipeline over all
+  // FP32: two steps a launch (kind 2) on 24-row tiles, 48 from 8192^2 (diagnostics
+  // every step: 143.6 GLUPS at 4096^2 against 92.6 for single steps, heights 16 to
+  // 58 within 3 %; 161.6 at 8192^2 against 96.7); where it does not apply, the persistent pipeline over all
   // resident CTAs on 4-row tiles (measured 3-5 % above one CTA per tile at 4096^2
   // and 8192^2). FP16 is bound by its arithmetic, not by memory, and keeps single
   // steps on one CTA per tile (two steps: 136.7 against 152 GLUPS at 4096^2).
   if (k.kind == 1 && prec == LBM_F32_SHIFT) {
     olbm::LaunchCfg k2 = k;
-    k2.kind = 2, k2.bx = 0, k2.rows = g.nx >= 8192 && g.ny >= 8192 ? 64 : 32;
+    k2.kind = 2, k2.bx = 0, k2.rows = g.nx >= 8192 && g.ny >= 8192 ? 48 : 24;
     if (olbm::uses_step2(prec, g, k2)) {
       while (k2.rows > 1 && olbm::step2_blocks(g, k2, prec) < 4LL * sms) k2.rows /= 2;
       return k2;

@@ -275,12 +275,12 @@ def test_fused_diagnostics_skip_a_nonfinite_node(oracle, prec, launch):
 
 
 @pytest.mark.parametrize("prec,n,want", [("f64", 4096, (0, 64, 2, 32)), ("f64df", 4096, (0, 64, 2, 32)),
-                                         ("f32", 4096, (2, 0, 1, 32)), ("f32", 8192, (2, 0, 1, 64)),
-                                         ("f32", 4097, (2, 0, 1, 32)),
+                                         ("f32", 4096, (2, 0, 1, 24)), ("f32", 8192, (2, 0, 1, 48)),
+                                         ("f32", 4097, (2, 0, 1, 24)),
                                          ("f16", 4096, (1, 0, 1, 24)), ("f16", 8192, (1, 0, 1, 48))])
 def test_default_launch_shapes(prec, n, want):
     """The documented defaults: FP64 and double-float on the column kernel; FP32 two steps a launch
-    on 32-row tiles (64 from 8192^2; any width); FP16 one CTA per tile with the height that fills the
+    on 24-row tiles (48 from 8192^2; any width); FP16 one CTA per tile with the height that fills the
     last wave of three CTAs per SM on GB300's 152 SMs (24 rows at 4096^2: 3.0 waves; 48 rows at
     8192^2: 6.0)."""
     from paper_2602_21242_gb300 import capi
