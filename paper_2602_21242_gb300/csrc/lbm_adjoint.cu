@@ -268,6 +268,31 @@ struct VjpLayout {
   void* lam(int k) const { return base + sb * ((size_t)nseg + (size_t)K + (size_t)k); }
 };
 
+// Two forward steps src -> dst in one launch (launch kind 2 of the shifted forms;
+// bit-identical to two single steps), where the lattice's launch allows it.
+bool two_steps_apply(const lbm_ctx* c) {
+  return c->n_walls == 0 && c->prec == LBM_F32_SHIFT && olbm::uses_step2(c->prec, c->g, c->cfg);
+}
+
+cudaError_t fwd_step2(lbm_ctx* c, const void* src, void* dst) {
+  olbm::StepArgs a;
+  a.model = c->model;
+  a.diag = false;
+  a.diag2 = false;
+  a.src = src;
+  a.dst = dst;
+  a.g = c->g;
+  a.theta = c->theta;
+  a.tau = c->tau;
+  a.rho_ref = c->rho_ref;
+  a.partials = c->d_parts[0];
+  a.partials2 = c->d_parts[0];
+  a.cfg = c->cfg;
+  a.err = c->d_err;
+  a.sched = c->d_sched;
+  return olbm::launch_step2_f32(a, c->stream);
+}
+
 int vjp_layout(lbm_ctx* c, int n, int ckpt_every, VjpLayout& L) {
   L.K = std::min(ckpt_every, std::max(n, 1));
   L.nseg = (n + L.K - 1) / L.K;
@@ -292,7 +317,8 @@ int vjp_layout(lbm_ctx* c, int n, int ckpt_every, VjpLayout& L) {
 
 // Forward pass: init, then n steps with a checkpoint at the start of every
 // segment; the last segment's states go straight to the ring (the backward pass
-// does not recompute them). The lattice ends holding f(x, n).
+// does not recompute them). The lattice ends holding f(x, n). Segments whose
+// states are not kept take two steps a launch where the lattice's launch does.
 int vjp_forward(lbm_ctx* c, int n, const VjpLayout& L, const double* d_rho0, const double* d_ux0,
                 const double* d_uy0) {
   int s = lbm_init(c, d_rho0, d_ux0, d_uy0);
@@ -303,12 +329,21 @@ int vjp_forward(lbm_ctx* c, int n, const VjpLayout& L, const double* d_rho0, con
       return vfail(c, LBM_ECUDA, "lbm_vjp checkpoint", e);
     const int len = std::min(L.K, n - seg * L.K);
     const bool last = seg == L.nseg - 1;
-    for (int k = 0; k < len; ++k) {
+    for (int k = 0; k < len;) {
+      if (!last && k + 1 < len && two_steps_apply(c)) {  // no state of this segment is kept: two a launch
+        if ((e = fwd_step2(c, c->buf[c->cur], c->buf[c->cur ^ 1])) != cudaSuccess)
+          return vfail(c, LBM_ECUDA, "lbm_vjp forward", e);
+        c->cur ^= 1;
+        c->t += 2;
+        k += 2;
+        continue;
+      }
       const void* src = (last && k > 0) ? L.ring(k) : c->buf[c->cur];
       void* dst = (last && k + 1 < len) ? L.ring(k + 1) : c->buf[c->cur ^ 1];
       if ((e = fwd_step(c, src, dst)) != cudaSuccess) return vfail(c, LBM_ECUDA, "lbm_vjp forward", e);
       if (!last || k + 1 == len) c->cur ^= 1;
       c->t += 1;
+      k += 1;
     }
   }
   c->vjp_gen = c->state_gen;
