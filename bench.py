@@ -32,21 +32,25 @@ if ROOT not in sys.path:
 METRIC = "MLUPS and % of HBM roofline, D2Q9 OReg-GEq; FP32 vs FP64 at stated error"
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "f64df": 144}
 # Algorithmic FP64 operations per node of one fused step (each add, mul or FMA of
-# the product-form collision is one operation): 33 shared (moments 16, 1/rho 3,
-# u 2, u^2 2, u/2 2, P 8), the model part (LBGK 22, OReg 56, partial 66,
-# complete 86, the mu sum and Pi~ sharing u^2 - 1; complete with the Eq. 12
-# prefactor from f^neq 83) and the fused diagnostics (5: three sums and j.u by
-# two FMAs). The FP64 form is bound by the FP64 pipe on GB300; the kernel issues
-# fewer of them to it (exact power-of-two scalings run on the integer pipe: about
-# 116 of the complete model's 124 by the ncu counters), and the count stays the method's.
-FP64_OPS_PER_NODE = {"lbgk": 60, "oreg": 94, "partial": 104, "complete": 124, "complete_neq": 121}
+# the product-form collision is one operation, the exact power-of-two scalings
+# too): 33 shared (moments 16, 1/rho 3, u 2, u^2 2, u/2 2, P 8), the model part
+# (LBGK 22, OReg 55, partial 65, complete 85, the mu sum and Pi~ sharing u^2 - 1;
+# complete with the Eq. 12 prefactor from f^neq 82) and the fused diagnostics (5:
+# three sums and j.u by two FMAs).
+FP64_OPS_PER_NODE = {"lbgk": 60, "oreg": 93, "partial": 103, "complete": 123, "complete_neq": 120}
+# The FP64 form on GB300 is bound by the FP64 pipe, which carries only the sums and
+# FMAs of that count: the products run on the integer pipes (correctly rounded
+# binary64 products from the operands' bit fields, bit-identical to the FP64
+# instruction) and the power-of-two scalings move exponent bits there too.
+FP64_PIPE_OPS_PER_NODE = {"lbgk": 41, "oreg": 71, "partial": 73, "complete": 86, "complete_neq": 84}
+INT_PIPE_PRODUCTS_PER_NODE = {"lbgk": 17, "oreg": 20, "partial": 24, "complete": 31, "complete_neq": 29}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per node of one step-kernel launch, from ncu captures of
 # the current kernels: the FP64 kernel captured at 2048^2 and scaled to the lattice by
 # node count (its traffic grows in proportion), the FP32 kernels (single steps, and two
 # steps a launch) captured at 4096^2.
 # Keyed by (storage, model, steps per launch).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete", 1): 133.4, ("f32", "complete", 1): 68.8,
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete", 1): 133.0, ("f32", "complete", 1): 68.8,
                                ("f32", "complete", 2): 72.1}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
@@ -266,11 +270,14 @@ def run_gpu(args):
     alu = None
     if args.prec == "f64":
         peak_ops = capi.lbm_measure_peak(0) / 2.0  # FMA instructions per second (2 FLOP each)
-        ops = FP64_OPS_PER_NODE[args.model] * n / (step_ms * 1e-3)
+        ops = FP64_PIPE_OPS_PER_NODE[args.model] * n / (step_ms * 1e-3)
         alu = {"bound": "alu", "achieved": round(ops / 1e12, 4), "peak": round(peak_ops / 1e12, 4),
-               "unit": "Top/s (FP64 add/mul/fma)", "frac": round(ops / peak_ops, 4), "traffic": traffic,
+               "unit": "Top/s (FP64-pipe add/fma)", "frac": round(ops / peak_ops, 4), "traffic": traffic,
                "peak_source": "FP64 FMA issue rate measured live on this GPU (lbm_measure_peak / 2)",
-               "ops_per_node": FP64_OPS_PER_NODE[args.model],
+               "ops_per_node": FP64_PIPE_OPS_PER_NODE[args.model],
+               "method_ops_per_node": FP64_OPS_PER_NODE[args.model],
+               "integer_pipe_products_per_node": INT_PIPE_PRODUCTS_PER_NODE[args.model],
+               "method_ops_rate": round(FP64_OPS_PER_NODE[args.model] * n / (step_ms * 1e-3) / 1e12, 4),
                "kernel": roof["kernel"], "ms_per_launch": round(step_ms, 4)}
         if alu["frac"] > roof["frac"]:
             roof, alu = alu, roof

@@ -513,6 +513,33 @@ int lbm_selftest_timeout(int which, double* h_seconds);
  */
 int lbm_selftest_fp64(int op, const double* h_x, long long n, double* h_out);
 
+/*
+ * Self-test of the integer-pipe binary64 arithmetic of the FP64 form (no
+ * counterpart in the paper; IEEE 754 round to nearest, ties to even): for the n
+ * host operand pairs (h_a[k], h_b[k]) writes the integer-pipe result to h_emu[k]
+ * and the FP64 instruction's result to h_fp64[k] (host, n doubles each,
+ * caller-owned); op = 0 the sum, op = 1 the product. The two agree bit for bit
+ * for every input (NaNs as NaNs). Synchronous. Returns LBM_EINVAL for another
+ * op, n < 0 or null pointers with n > 0.
+ */
+int lbm_selftest_fp64_emu(int op, const double* h_a, const double* h_b, long long n, double* h_emu,
+                          double* h_fp64);
+
+/*
+ * Self-test of the FP64 collision (Eq. 1a with the model's f^OReg and
+ * corrections; no counterpart in the paper beyond that): collides the n nodes
+ * of h_f (host, n x 9 doubles, populations in the order of Fig. 1a) on the GPU
+ * twice, with the FP64 kernels' arithmetic (products on the integer pipes) and
+ * with every product on the FP64 pipe (never contracted into an FMA), and
+ * writes per node the nine post-collision populations and m0, j_x, j_y, u_x,
+ * u_y (14 doubles) to h_emu and h_ref (host, n x 14 doubles each,
+ * caller-owned). The two agree bit for bit. Coefficients from theta and tau
+ * (rho_ref = 1). Synchronous. Returns LBM_EINVAL for an unknown model, n < 0,
+ * theta outside (0, 1), tau <= 1/2 or null pointers with n > 0.
+ */
+int lbm_selftest_collide_f64(int model, double theta, double tau, const double* h_f, long long n, double* h_emu,
+                             double* h_ref);
+
 /* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

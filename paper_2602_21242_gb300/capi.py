@@ -55,6 +55,8 @@ _SIGNATURES = {
     "lbm_measure_peak": ([_i, _pd], _i),
     "lbm_selftest_timeout": ([_i, _pd], _i),
     "lbm_selftest_fp64": ([_i, _pd, _ll, _pd], _i),
+    "lbm_selftest_fp64_emu": ([_i, _pd, _pd, _ll, _pd, _pd], _i),
+    "lbm_selftest_collide_f64": ([_i, _d, _d, _pd, _ll, _pd, _pd], _i),
     "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "lbm_vjp_forward": ([_p, _i, _i, _p, _p, _p], _i),
     "lbm_vjp_ex": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i], _i),
@@ -415,6 +417,32 @@ def lbm_selftest_fp64(op: int, x):
     out = np.empty_like(xs)
     check(load().lbm_selftest_fp64(op, xs.ctypes.data_as(_pd), xs.size, out.ctypes.data_as(_pd)), None)
     return out
+
+
+def lbm_selftest_fp64_emu(op: int, a, b):
+    """Integer-pipe sum (op 0) or product (op 1) of the pairs (a, b) on the GPU, and the FP64
+    instruction's; returns (emu, fp64)."""
+    import numpy as np
+    av = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    bv = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    if av.shape != bv.shape:
+        raise ValueError("a and b must have the same shape")
+    emu, ref = np.empty_like(av), np.empty_like(av)
+    check(load().lbm_selftest_fp64_emu(op, av.ctypes.data_as(_pd), bv.ctypes.data_as(_pd), av.size,
+                                       emu.ctypes.data_as(_pd), ref.ctypes.data_as(_pd)), None)
+    return emu, ref
+
+
+def lbm_selftest_collide_f64(model: int, theta: float, tau: float, f):
+    """FP64 collision of the nodes f (n x 9) with the kernels' integer-pipe products and with every
+    product on the FP64 pipe; returns (emu, ref), each n x 14 (populations, m0, jx, jy, ux, uy)."""
+    import numpy as np
+    fv = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1, 9))
+    n = fv.shape[0]
+    emu, ref = np.empty((n, 14)), np.empty((n, 14))
+    check(load().lbm_selftest_collide_f64(model, theta, tau, fv.ctypes.data_as(_pd), n, emu.ctypes.data_as(_pd),
+                                          ref.ctypes.data_as(_pd)), None)
+    return emu, ref
 
 
 def lbm_selftest_timeout(which: int):

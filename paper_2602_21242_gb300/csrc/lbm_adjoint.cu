@@ -52,8 +52,13 @@ __global__ void __launch_bounds__(kABX* kABY) adj_seed_kernel(const typename For
 }
 
 // lambda(t)(x) = J_C(f(x, t))^T mu(x), mu_i(x) = lambda_i(t + 1)(x + c_i).
+// Two blocks a SM (the FP64 form: OLBM_ADJ_F64_MINB; with one it takes 174 registers
+// and the 1024^2 FP64 gradient's backward pass took 320 ms instead of 292).
+#ifndef OLBM_ADJ_F64_MINB
+#define OLBM_ADJ_F64_MINB 2
+#endif
 template <int MODEL, int PREC>
-__global__ void __launch_bounds__(kABX* kABY) adj_step_kernel(const typename Form<PREC>::S* __restrict__ fbuf,
+__global__ void __launch_bounds__(kABX* kABY, PREC == 0 ? OLBM_ADJ_F64_MINB : 2) adj_step_kernel(const typename Form<PREC>::S* __restrict__ fbuf,
                                                               const typename Form<PREC>::T* __restrict__ lam_next,
                                                               typename Form<PREC>::T* __restrict__ lam, Geometry g,
                                                               Coef<typename Form<PREC>::T> c) {
@@ -72,7 +77,17 @@ __global__ void __launch_bounds__(kABX* kABY) adj_step_kernel(const typename For
     yd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
     mu[i] = lam_next[i * g.plane + (long long)yd * g.pitch + xd];
   }
-  collide_vjp<MODEL, Form<PREC>::kShift, T>(f, mu, c, out);
+  if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
+    // FP64: the products on the integer pipes, as in the forward collision
+    d64m fe[9], me[9], oe[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fe[i] = d64m(f[i]), me[i] = d64m(mu[i]);
+    collide_vjp<MODEL, Form<PREC>::kShift, d64m>(fe, me, coef_cast<d64m>(c), oe);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = oe[i].v;
+  } else {
+    collide_vjp<MODEL, Form<PREC>::kShift, T>(f, mu, c, out);
+  }
   const long long here = (long long)y * g.pitch + x;
 #pragma unroll
   for (int i = 0; i < 9; ++i) lam[i * g.plane + here] = out[i];

@@ -26,6 +26,8 @@
 
 #include <type_traits>
 
+#include "lbm_fp64emu.cuh"
+
 namespace olbm {
 
 // ---------------------------------------------------------------- storage forms
@@ -290,18 +292,23 @@ __device__ __forceinline__ double scaled(double x, float k) {
 // where E(a) = P_x(a) (rho + A1 C_x(a)^2), B(a) = A1 P_x(a), G(a) = A2 P_x(a) C_x(a),
 // A1 = omega' K1, A2 = omega' K2: the expansion of
 // f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] at three FMAs per population.
+// The sums and differences of the moments (the FP64 form may take them on the
+// integer pipes, see d64m).
+template <typename T> __device__ __forceinline__ T sum_m(T a, T b) { return a + b; }
+template <typename T> __device__ __forceinline__ T dif_m(T a, T b) { return a - b; }
+
 template <int MODEL, bool SHIFT, typename T, typename Sink>
-__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink) {
+__device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&& sink) {
   // Moments (Sec. 1). The rest state has zero momentum, zero
   // sum (c_x^2 - c_y^2) W and zero sum c_x c_y W, so these sums are the same for
   // absolute and shifted values.
-  const T s13 = f[1] + f[3], d13 = f[1] - f[3];
-  const T s24 = f[2] + f[4], d24 = f[2] - f[4];
-  const T s57 = f[5] + f[7], d57 = f[5] - f[7];
-  const T s68 = f[6] + f[8], d68 = f[6] - f[8];
-  const T m0 = f[0] + (s13 + s24) + (s57 + s68);
-  const T jx = d13 + (d57 - d68);
-  const T jy = d24 + (d57 + d68);
+  const T s13 = sum_m(f[1], f[3]), d13 = dif_m(f[1], f[3]);
+  const T s24 = sum_m(f[2], f[4]), d24 = dif_m(f[2], f[4]);
+  const T s57 = sum_m(f[5], f[7]), d57 = dif_m(f[5], f[7]);
+  const T s68 = sum_m(f[6], f[8]), d68 = dif_m(f[6], f[8]);
+  const T m0 = sum_m(sum_m(f[0], sum_m(s13, s24)), sum_m(s57, s68));
+  const T jx = sum_m(d13, dif_m(d57, d68));
+  const T jy = sum_m(d24, sum_m(d57, d68));
   const T rho = SHIFT ? c.rho_ref + m0 : m0;
   const T inv_rho = recip(rho);
   const T ux = jx * inv_rho, uy = jy * inv_rho;
@@ -475,6 +482,60 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
         const T inner = kNegFree ? fma(-B[a + 1], cym[b + 1], G[a + 1]) : fma(B[a + 1], ncy[b + 1], G[a + 1]);
         f[i] = fma(py[b + 1], fma(cym[b + 1], inner, E[a + 1]), rest);
       }
+  }
+}
+
+// FP64 values whose products run on the integer pipes (emu::mul64, bit-identical
+// to the FP64 instruction); sums and FMAs stay on the FP64 pipe. The FP64
+// collision runs on this type, so the FP64 pipe, which bounds the FP64 form on
+// GB300, carries only the sums and FMAs, while the products overlap with them on
+// the otherwise idle integer pipes.
+#ifndef OLBM_F64_EMU_MUL
+#define OLBM_F64_EMU_MUL 1
+#endif
+#ifndef OLBM_F64_EMU_ADD
+#define OLBM_F64_EMU_ADD 0
+#endif
+struct d64m {
+  double v;
+  d64m() = default;
+  __host__ __device__ constexpr d64m(double x) : v(x) {}
+  // Hidden friends: found only by argument-dependent lookup on d64m, so they
+  // never capture a call on plain doubles.
+  friend __device__ __forceinline__ d64m operator+(d64m a, d64m b) { return d64m(a.v + b.v); }
+  friend __device__ __forceinline__ d64m operator-(d64m a, d64m b) { return d64m(a.v - b.v); }
+  friend __device__ __forceinline__ d64m operator-(d64m a) { return d64m(-a.v); }
+  friend __device__ __forceinline__ d64m operator*(d64m a, d64m b) { return d64m(emu::mul64(a.v, b.v)); }
+  friend __device__ __forceinline__ d64m fma(d64m a, d64m b, d64m c) { return d64m(::fma(a.v, b.v, c.v)); }
+  friend __device__ __forceinline__ d64m recip(d64m x) { return d64m(recip(x.v)); }
+  friend __device__ __forceinline__ d64m scaled(d64m x, float k) { return d64m(scaled(x.v, k)); }
+#if OLBM_F64_EMU_ADD >= 1
+  friend __device__ __forceinline__ d64m sum_m(d64m a, d64m b) { return d64m(emu::add64(a.v, b.v)); }
+#endif
+#if OLBM_F64_EMU_ADD >= 2
+  friend __device__ __forceinline__ d64m dif_m(d64m a, d64m b) { return d64m(emu::add64(a.v, -b.v)); }
+#endif
+};
+
+
+// In-place collision of one node (see collide_form); the FP64 form takes its
+// products on the integer pipes.
+template <int MODEL, bool SHIFT, typename T, typename Sink>
+__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink) {
+  if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
+    d64m g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = d64m(f[i]);
+    const Coef<d64m> ce = coef_cast<d64m>(c);
+    collide_form<MODEL, SHIFT, d64m>(g, ce, [&](const NodeMoments<d64m>& m) {
+      NodeMoments<double> md;
+      md.m0 = m.m0.v, md.jx = m.jx.v, md.jy = m.jy.v, md.ux = m.ux.v, md.uy = m.uy.v;
+      sink(md);
+    });
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = g[i].v;
+  } else {
+    collide_form<MODEL, SHIFT, T>(f, c, sink);
   }
 }
 

@@ -365,8 +365,11 @@ __global__ void __maxnreg__(OLBM_DF_MAXNREG) step_kernel_df(const double* __rest
 // measures the same with caps from 72 (seven blocks, spilling) to 128 registers
 // (4751-4762 MLUPS at 4096^2), so the cap is not critical. Launched with at
 // most 512 threads.
+#ifndef OLBM_F64_MAXNREG
+#define OLBM_F64_MAXNREG 128
+#endif
 template <int MODEL, bool DIAG>
-__global__ void __maxnreg__(96) step_kernel_f64(const double* __restrict__ src, double* __restrict__ dst, Geometry g,
+__global__ void __maxnreg__(OLBM_F64_MAXNREG) step_kernel_f64(const double* __restrict__ src, double* __restrict__ dst, Geometry g,
                                                 Coef<double> c, double* __restrict__ partials, int rows) {
   step_body<MODEL, 0, DIAG, false>(src, dst, g, c, partials, rows);
 }

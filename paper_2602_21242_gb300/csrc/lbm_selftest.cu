@@ -87,3 +87,118 @@ extern "C" int lbm_selftest_timeout(int which, double* h_seconds) {
   if (e != cudaSuccess) return LBM_ECUDA;
   return flag ? LBM_ETIMEOUT : LBM_OK;
 }
+
+namespace {
+
+// The integer-pipe binary64 sum and product next to the FP64 instructions.
+__global__ void fp64_emu_kernel(int op, const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                double* __restrict__ emu, double* __restrict__ fp64) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (op == 0) {
+    emu[i] = olbm::emu::add64(a[i], b[i]);
+    fp64[i] = __dadd_rn(a[i], b[i]);
+  } else {
+    emu[i] = olbm::emu::mul64(a[i], b[i]);
+    fp64[i] = __dmul_rn(a[i], b[i]);
+  }
+}
+
+// FP64 values with the same operations as d64m, every product on the FP64 pipe
+// (__dmul_rn, never contracted into an FMA): the collision on this type is the
+// reference for the integer-pipe products.
+struct d64r {
+  double v;
+  d64r() = default;
+  __host__ __device__ constexpr d64r(double x) : v(x) {}
+  friend __device__ __forceinline__ d64r operator+(d64r a, d64r b) { return d64r(a.v + b.v); }
+  friend __device__ __forceinline__ d64r operator-(d64r a, d64r b) { return d64r(a.v - b.v); }
+  friend __device__ __forceinline__ d64r operator-(d64r a) { return d64r(-a.v); }
+  friend __device__ __forceinline__ d64r operator*(d64r a, d64r b) { return d64r(__dmul_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ d64r fma(d64r a, d64r b, d64r c) { return d64r(::fma(a.v, b.v, c.v)); }
+  friend __device__ __forceinline__ d64r recip(d64r x) { return d64r(olbm::recip(x.v)); }
+  friend __device__ __forceinline__ d64r scaled(d64r x, float k) { return d64r(olbm::scaled(x.v, k)); }
+};
+
+template <int MODEL>
+__global__ void collide_f64_kernel(const double* __restrict__ fin, long long n, olbm::Coef<double> c,
+                                   double* __restrict__ out_emu, double* __restrict__ out_ref) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f[9];
+  d64r g[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) f[k] = fin[i * 9 + k], g[k] = d64r(f[k]);
+  double mom[5], momr[5];
+  olbm::collide<MODEL, false, double>(f, c, [&](const olbm::NodeMoments<double>& m) {
+    mom[0] = m.m0, mom[1] = m.jx, mom[2] = m.jy, mom[3] = m.ux, mom[4] = m.uy;
+  });
+  const olbm::Coef<d64r> cr = olbm::coef_cast<d64r>(c);
+  olbm::collide_form<MODEL, false, d64r>(g, cr, [&](const olbm::NodeMoments<d64r>& m) {
+    momr[0] = m.m0.v, momr[1] = m.jx.v, momr[2] = m.jy.v, momr[3] = m.ux.v, momr[4] = m.uy.v;
+  });
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out_emu[i * 14 + k] = f[k], out_ref[i * 14 + k] = g[k].v;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out_emu[i * 14 + 9 + k] = mom[k], out_ref[i * 14 + 9 + k] = momr[k];
+}
+
+}  // namespace
+
+extern "C" int lbm_selftest_fp64_emu(int op, const double* h_a, const double* h_b, long long n, double* h_emu,
+                                     double* h_fp64) {
+  if ((op != 0 && op != 1) || n < 0 ||
+      (n > 0 && (h_a == nullptr || h_b == nullptr || h_emu == nullptr || h_fp64 == nullptr)))
+    return LBM_EINVAL;
+  if (n == 0) return LBM_OK;
+  double* d = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  if (cudaMalloc(&d, 4 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d, h_a, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + n, h_b, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    fp64_emu_kernel<<<(unsigned)((n + 255) / 256), 256>>>(op, d, d + n, n, d + 2 * n, d + 3 * n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h_emu, d + 2 * n, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(h_fp64, d + 3 * n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_selftest_collide_f64(int model, double theta, double tau, const double* h_f, long long n,
+                                        double* h_emu, double* h_ref) {
+  if (model < LBM_LBGK || model > LBM_LBGK_POLY || n < 0 || !(theta > 0.0 && theta < 1.0) || !(tau > 0.5) ||
+      (n > 0 && (h_f == nullptr || h_emu == nullptr || h_ref == nullptr)))
+    return LBM_EINVAL;
+  if (n == 0) return LBM_OK;
+  double* d = nullptr;
+  const size_t in_bytes = sizeof(double) * 9 * (size_t)n, out_bytes = sizeof(double) * 14 * (size_t)n;
+  if (cudaMalloc(&d, in_bytes + 2 * out_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  double* d_emu = d + 9 * n;
+  double* d_ref = d_emu + 14 * n;
+  const olbm::Coef<double> c = olbm::make_coef<double>(theta, tau, 1.0);
+  cudaError_t e = cudaMemcpy(d, h_f, in_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    switch (model) {
+      case 0: collide_f64_kernel<0><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+      case 1: collide_f64_kernel<1><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+      case 2: collide_f64_kernel<2><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+      case 3: collide_f64_kernel<3><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+      case 4: collide_f64_kernel<4><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+      default: collide_f64_kernel<5><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h_emu, d_emu, out_bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(h_ref, d_ref, out_bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
