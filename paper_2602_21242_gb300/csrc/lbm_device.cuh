@@ -292,23 +292,18 @@ __device__ __forceinline__ double scaled(double x, float k) {
 // where E(a) = P_x(a) (rho + A1 C_x(a)^2), B(a) = A1 P_x(a), G(a) = A2 P_x(a) C_x(a),
 // A1 = omega' K1, A2 = omega' K2: the expansion of
 // f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] at three FMAs per population.
-// The sums and differences of the moments (the FP64 form may take them on the
-// integer pipes, see d64m).
-template <typename T> __device__ __forceinline__ T sum_m(T a, T b) { return a + b; }
-template <typename T> __device__ __forceinline__ T dif_m(T a, T b) { return a - b; }
-
 template <int MODEL, bool SHIFT, typename T, typename Sink>
 __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&& sink) {
   // Moments (Sec. 1). The rest state has zero momentum, zero
   // sum (c_x^2 - c_y^2) W and zero sum c_x c_y W, so these sums are the same for
   // absolute and shifted values.
-  const T s13 = sum_m(f[1], f[3]), d13 = dif_m(f[1], f[3]);
-  const T s24 = sum_m(f[2], f[4]), d24 = dif_m(f[2], f[4]);
-  const T s57 = sum_m(f[5], f[7]), d57 = dif_m(f[5], f[7]);
-  const T s68 = sum_m(f[6], f[8]), d68 = dif_m(f[6], f[8]);
-  const T m0 = sum_m(sum_m(f[0], sum_m(s13, s24)), sum_m(s57, s68));
-  const T jx = sum_m(d13, dif_m(d57, d68));
-  const T jy = sum_m(d24, sum_m(d57, d68));
+  const T s13 = f[1] + f[3], d13 = f[1] - f[3];
+  const T s24 = f[2] + f[4], d24 = f[2] - f[4];
+  const T s57 = f[5] + f[7], d57 = f[5] - f[7];
+  const T s68 = f[6] + f[8], d68 = f[6] - f[8];
+  const T m0 = f[0] + (s13 + s24) + (s57 + s68);
+  const T jx = d13 + (d57 - d68);
+  const T jy = d24 + (d57 + d68);
   const T rho = SHIFT ? c.rho_ref + m0 : m0;
   const T inv_rho = recip(rho);
   const T ux = jx * inv_rho, uy = jy * inv_rho;
@@ -489,12 +484,13 @@ __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&&
 // to the FP64 instruction); sums and FMAs stay on the FP64 pipe. The FP64
 // collision runs on this type, so the FP64 pipe, which bounds the FP64 form on
 // GB300, carries only the sums and FMAs, while the products overlap with them on
-// the otherwise idle integer pipes.
+// the otherwise idle integer pipes (complete model at 4096^2, diagnostics every
+// step: 4.78 -> 5.76 GLUPS). Sums on the integer pipes as well (emu::add64)
+// measured slower wherever they were put: the moments, which head the
+// collision's dependency chain, 4.9; the corrections, the factors P or C, or the
+// diagnostics sums, 5.2 to 5.6.
 #ifndef OLBM_F64_EMU_MUL
 #define OLBM_F64_EMU_MUL 1
-#endif
-#ifndef OLBM_F64_EMU_ADD
-#define OLBM_F64_EMU_ADD 0
 #endif
 struct d64m {
   double v;
@@ -509,12 +505,6 @@ struct d64m {
   friend __device__ __forceinline__ d64m fma(d64m a, d64m b, d64m c) { return d64m(::fma(a.v, b.v, c.v)); }
   friend __device__ __forceinline__ d64m recip(d64m x) { return d64m(recip(x.v)); }
   friend __device__ __forceinline__ d64m scaled(d64m x, float k) { return d64m(scaled(x.v, k)); }
-#if OLBM_F64_EMU_ADD >= 1
-  friend __device__ __forceinline__ d64m sum_m(d64m a, d64m b) { return d64m(emu::add64(a.v, b.v)); }
-#endif
-#if OLBM_F64_EMU_ADD >= 2
-  friend __device__ __forceinline__ d64m dif_m(d64m a, d64m b) { return d64m(emu::add64(a.v, -b.v)); }
-#endif
 };
 
 
