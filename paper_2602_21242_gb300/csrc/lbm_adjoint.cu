@@ -52,16 +52,11 @@ __global__ void __launch_bounds__(kABX* kABY) adj_seed_kernel(const typename For
 }
 
 // lambda(t)(x) = J_C(f(x, t))^T mu(x), mu_i(x) = lambda_i(t + 1)(x + c_i).
-// Two blocks a SM (the FP64 form: OLBM_ADJ_F64_MINB; with one it takes 174 registers
-// and the 1024^2 FP64 gradient's backward pass took 320 ms instead of 292).
-#ifndef OLBM_ADJ_F64_MINB
-#define OLBM_ADJ_F64_MINB 2
-#endif
 template <int MODEL, int PREC>
-__global__ void __launch_bounds__(kABX* kABY, PREC == 0 ? OLBM_ADJ_F64_MINB : 2) adj_step_kernel(const typename Form<PREC>::S* __restrict__ fbuf,
-                                                              const typename Form<PREC>::T* __restrict__ lam_next,
-                                                              typename Form<PREC>::T* __restrict__ lam, Geometry g,
-                                                              Coef<typename Form<PREC>::T> c) {
+__device__ __forceinline__ void adj_step_body(const typename Form<PREC>::S* __restrict__ fbuf,
+                                              const typename Form<PREC>::T* __restrict__ lam_next,
+                                              typename Form<PREC>::T* __restrict__ lam, const Geometry& g,
+                                              const Coef<typename Form<PREC>::T>& c) {
   using T = typename Form<PREC>::T;
   const int x = blockIdx.x * kABX + threadIdx.x, y = blockIdx.y * kABY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
@@ -91,6 +86,27 @@ __global__ void __launch_bounds__(kABX* kABY, PREC == 0 ? OLBM_ADJ_F64_MINB : 2)
   const long long here = (long long)y * g.pitch + x;
 #pragma unroll
   for (int i = 0; i < 9; ++i) lam[i * g.plane + here] = out[i];
+}
+
+template <int MODEL, int PREC>
+__global__ void __launch_bounds__(kABX* kABY) adj_step_kernel(const typename Form<PREC>::S* __restrict__ fbuf,
+                                                              const typename Form<PREC>::T* __restrict__ lam_next,
+                                                              typename Form<PREC>::T* __restrict__ lam, Geometry g,
+                                                              Coef<typename Form<PREC>::T> c) {
+  adj_step_body<MODEL, PREC>(fbuf, lam_next, lam, g, c);
+}
+
+// The FP64 form, compiled for two blocks a SM (118 registers; with one it takes
+// 174 and the 1024^2 FP64 gradient's backward pass took 320 ms instead of 292).
+#ifndef OLBM_ADJ_F64_MINB
+#define OLBM_ADJ_F64_MINB 2
+#endif
+template <int MODEL>
+__global__ void __launch_bounds__(kABX* kABY, OLBM_ADJ_F64_MINB) adj_step_f64_kernel(const double* __restrict__ fbuf,
+                                                                                     const double* __restrict__ lam_next,
+                                                                                     double* __restrict__ lam, Geometry g,
+                                                                                     Coef<double> c) {
+  adj_step_body<MODEL, 0>(fbuf, lam_next, lam, g, c);
 }
 
 // The FP32 form on node pairs (x, x + 1), x even, with packed f32x2 arithmetic
@@ -182,8 +198,13 @@ template <int PREC> struct Adjoint {
         return cudaGetLastError();
       }
     }
-    adj_step_kernel<MODEL, PREC><<<adj_grid(g), dim3(kABX, kABY), 0, st>>>((const S*)fbuf, (const T*)lam_next,
-                                                                          (T*)lam, g, c);
+    if constexpr (PREC == 0) {
+      adj_step_f64_kernel<MODEL><<<adj_grid(g), dim3(kABX, kABY), 0, st>>>((const double*)fbuf,
+                                                                          (const double*)lam_next, (double*)lam, g, c);
+    } else {
+      adj_step_kernel<MODEL, PREC><<<adj_grid(g), dim3(kABX, kABY), 0, st>>>((const S*)fbuf, (const T*)lam_next,
+                                                                            (T*)lam, g, c);
+    }
     return cudaGetLastError();
   }
 
