@@ -186,27 +186,37 @@ OLBM_EMU_HD double add64(double a, double b) {
   return take_fallback(fast) ? (fast ? r : add_fallback(a, b)) : r;
 }
 
-// a * b, correctly rounded (round to nearest, ties to even).
+// a * b, correctly rounded (round to nearest, ties to even), in 32-bit words:
+// the significands with the hidden bit at 63 (the shift drops sign and exponent
+// bits; the lowest exponent bit lands on 63 and is set to one), their 128-bit
+// product from four 32 x 32 -> 64-bit multiply-adds, a normalisation by at most
+// one bit, and the rounding increment (rem + lsb > half) carried into the packed
+// exponent field.
 OLBM_EMU_HD double mul64(double a, double b) {
   const uint64_t ua = bits_of(a), ub = bits_of(b);
-  const int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
-  // significands with the hidden bit at 63 (the shift drops sign and exponent
-  // bits; the lowest exponent bit lands on 63 and is set to one)
-  const uint64_t A = (ua << 11) | kSign, B = (ub << 11) | kSign;
-  // 128-bit product from four 32 x 32 -> 64-bit products
-  const uint32_t a0 = (uint32_t)A, a1 = (uint32_t)(A >> 32), b0 = (uint32_t)B, b1 = (uint32_t)(B >> 32);
-  const uint64_t p00 = (uint64_t)a0 * b0, p01 = (uint64_t)a0 * b1, p10 = (uint64_t)a1 * b0,
-                 p11 = (uint64_t)a1 * b1;
-  const uint64_t mid = (p00 >> 32) + (uint32_t)p01 + (uint32_t)p10;
-  const uint64_t hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
-  const uint32_t lo1 = (uint32_t)mid, lo0 = (uint32_t)p00;  // low 64 bits: lo1 * 2^32 + lo0
-  // A B lies in [2^126, 2^128): hi in [2^62, 2^64)
-  const bool top = (hi >> 63) != 0;
-  const uint64_t N = top ? hi : (hi << 1) | (lo1 >> 31);
-  const bool sticky = (top ? (lo1 | lo0) : ((lo1 & 0x7FFFFFFFu) | lo0)) != 0;
+  const uint32_t ah = (uint32_t)(ua >> 32), al = (uint32_t)ua, bh = (uint32_t)(ub >> 32), bl = (uint32_t)ub;
+  const int ea = (int)((ah >> 20) & 0x7FF), eb = (int)((bh >> 20) & 0x7FF);
+  const uint32_t a1 = shl_hi(al, ah, 11) | 0x80000000u, a0 = al << 11;
+  const uint32_t b1 = shl_hi(bl, bh, 11) | 0x80000000u, b0 = bl << 11;
+  // 128-bit product (w3 w2 w1 w0)
+  const uint64_t p00 = (uint64_t)a0 * b0;
+  const uint64_t t = (uint64_t)a0 * b1 + (p00 >> 32);
+  const uint64_t u = (uint64_t)a1 * b0 + (uint32_t)t;
+  const uint64_t hi = (uint64_t)a1 * b1 + (t >> 32) + (u >> 32);
+  const uint32_t w1 = (uint32_t)u, w0 = (uint32_t)p00;
+  // A B lies in [2^126, 2^128): hi in [2^62, 2^64); normalise its leading bit to 63
+  const uint32_t h1 = (uint32_t)(hi >> 32), h0 = (uint32_t)hi;
+  const bool top = (h1 >> 31) != 0;
+  const uint32_t n1 = top ? h1 : shl_hi(h0, h1, 1), n0 = top ? h0 : shl_hi(w1, h0, 1);
+  const uint32_t low = top ? (w1 | w0) : ((w1 << 1) | w0);  // the bits below the 64 kept
   const int e = ea + eb - 1023 + (top ? 1 : 0);
-  const bool fast = ea != 0 && eb != 0 && ea != 0x7FF && eb != 0x7FF && e >= 1 && e <= 2046;
-  const double r = double_of(round_pack((ua ^ ub) & kSign, e, N >> 11, (uint32_t)(N & 0x7FFu) | (sticky ? 1u : 0u)));
+  // m = n >> 11 (53 bits), rem its 11 guard bits with the sticky bit ORed in
+  const uint32_t m1 = n1 >> 11, m0 = shr_lo(n0, n1, 11);
+  const uint32_t rem = (n0 & 0x7FFu) | (low != 0 ? 1u : 0u);
+  const uint32_t inc = rem + (m0 & 1u) > 0x400u ? 1u : 0u;
+  const uint64_t m = ((uint64_t)m1 << 32) | m0;
+  const bool fast = (unsigned)(ea - 1) < 2046u && (unsigned)(eb - 1) < 2046u && (unsigned)(e - 1) < 2046u;
+  const double r = double_of((((uint64_t)((ah ^ bh) & 0x80000000u)) << 32) | ((((uint64_t)(e - 1)) << 52) + m + inc));
   return take_fallback(fast) ? (fast ? r : mul_fallback(a, b)) : r;
 }
 
