@@ -73,11 +73,12 @@ __device__ __forceinline__ void adj_step_body(const typename Form<PREC>::S* __re
     mu[i] = lam_next[i * g.plane + (long long)yd * g.pitch + xd];
   }
   if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
-    // FP64: the products on the integer pipes, as in the forward collision
-    d64m fe[9], me[9], oe[9];
+    // FP64: the products on the integer pipes, each with its own fallback (a
+    // single check of the results would keep f and mu live for a redo: spills)
+    d64c fe[9], me[9], oe[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fe[i] = d64m(f[i]), me[i] = d64m(mu[i]);
-    collide_vjp<MODEL, Form<PREC>::kShift, d64m>(fe, me, coef_cast<d64m>(c), oe);
+    for (int i = 0; i < 9; ++i) fe[i] = d64c(f[i]), me[i] = d64c(mu[i]);
+    collide_vjp<MODEL, Form<PREC>::kShift, d64c>(fe, me, coef_cast<d64c>(c), oe);
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i] = oe[i].v;
   } else {

@@ -292,6 +292,10 @@ __device__ __forceinline__ double scaled(double x, float k) {
 // where E(a) = P_x(a) (rho + A1 C_x(a)^2), B(a) = A1 P_x(a), G(a) = A2 P_x(a) C_x(a),
 // A1 = omega' K1, A2 = omega' K2: the expansion of
 // f^eq + omega' [K1 (Q_x P_y - P_x Q_y) + K2 R_x R_y] at three FMAs per population.
+// u = j / rho as j * (1 / rho): the velocities go to the diagnostics before the
+// collision ends, so the FP64 form takes these two products with their fallback.
+template <typename T> __device__ __forceinline__ T mul_u(T a, T b) { return a * b; }
+
 template <int MODEL, bool SHIFT, typename T, typename Sink>
 __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&& sink) {
   // Moments (Sec. 1). The rest state has zero momentum, zero
@@ -306,7 +310,7 @@ __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&&
   const T jy = d24 + (d57 + d68);
   const T rho = SHIFT ? c.rho_ref + m0 : m0;
   const T inv_rho = recip(rho);
-  const T ux = jx * inv_rho, uy = jy * inv_rho;
+  const T ux = mul_u(jx, inv_rho), uy = mul_u(jy, inv_rho);
   {
     NodeMoments<T> mom;
     mom.m0 = m0;
@@ -485,10 +489,12 @@ __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&&
 // collision runs on this type, so the FP64 pipe, which bounds the FP64 form on
 // GB300, carries only the sums and FMAs, while the products overlap with them on
 // the otherwise idle integer pipes (complete model at 4096^2, diagnostics every
-// step: 4.78 -> 5.76 GLUPS). Sums on the integer pipes as well (emu::add64)
-// measured slower wherever they were put: the moments, which head the
-// collision's dependency chain, 4.9; the corrections, the factors P or C, or the
-// diagnostics sums, 5.2 to 5.6.
+// step: 4.78 -> 5.93 GLUPS). The products leave out their fallback (a product
+// outside the fast path is a quiet NaN), and collide() checks the node's nine
+// results once instead: a branch per product measured 8 % slower. Sums on the
+// integer pipes as well (emu::add64) measured slower wherever they were put: the
+// moments, which head the collision's dependency chain, 4.9; the corrections,
+// the factors P or C, or the diagnostics sums, 5.2 to 5.6 (against 5.76).
 #ifndef OLBM_F64_EMU_MUL
 #define OLBM_F64_EMU_MUL 1
 #endif
@@ -501,27 +507,81 @@ struct d64m {
   friend __device__ __forceinline__ d64m operator+(d64m a, d64m b) { return d64m(a.v + b.v); }
   friend __device__ __forceinline__ d64m operator-(d64m a, d64m b) { return d64m(a.v - b.v); }
   friend __device__ __forceinline__ d64m operator-(d64m a) { return d64m(-a.v); }
-  friend __device__ __forceinline__ d64m operator*(d64m a, d64m b) { return d64m(emu::mul64(a.v, b.v)); }
+  friend __device__ __forceinline__ d64m operator*(d64m a, d64m b) { return d64m(emu::mul64<false>(a.v, b.v)); }
+  friend __device__ __forceinline__ d64m mul_u(d64m a, d64m b) { return d64m(emu::mul64<true>(a.v, b.v)); }
   friend __device__ __forceinline__ d64m fma(d64m a, d64m b, d64m c) { return d64m(::fma(a.v, b.v, c.v)); }
   friend __device__ __forceinline__ d64m recip(d64m x) { return d64m(recip(x.v)); }
   friend __device__ __forceinline__ d64m scaled(d64m x, float k) { return d64m(scaled(x.v, k)); }
 };
 
+// The same with every product checked on its own (emu::mul64<true>: the FP64
+// instruction behind a warp-uniform branch where the fast path does not apply),
+// for callers that cannot redo a node (the adjoint step).
+struct d64c {
+  double v;
+  d64c() = default;
+  __host__ __device__ constexpr d64c(double x) : v(x) {}
+  friend __device__ __forceinline__ d64c operator+(d64c a, d64c b) { return d64c(a.v + b.v); }
+  friend __device__ __forceinline__ d64c operator-(d64c a, d64c b) { return d64c(a.v - b.v); }
+  friend __device__ __forceinline__ d64c operator-(d64c a) { return d64c(-a.v); }
+  friend __device__ __forceinline__ d64c operator*(d64c a, d64c b) { return d64c(emu::mul64<true>(a.v, b.v)); }
+  friend __device__ __forceinline__ d64c fma(d64c a, d64c b, d64c c) { return d64c(::fma(a.v, b.v, c.v)); }
+  friend __device__ __forceinline__ d64c recip(d64c x) { return d64c(recip(x.v)); }
+  friend __device__ __forceinline__ d64c scaled(d64c x, float k) { return d64c(scaled(x.v, k)); }
+};
+
+// The same operations with every product on the FP64 pipe (__dmul_rn, never
+// contracted into an FMA): the FP64 collision of a node whose integer-pipe
+// products left the fast path is redone on this type, with the same result
+// bits as the integer-pipe products would have given.
+struct d64f {
+  double v;
+  d64f() = default;
+  __host__ __device__ constexpr d64f(double x) : v(x) {}
+  friend __device__ __forceinline__ d64f operator+(d64f a, d64f b) { return d64f(a.v + b.v); }
+  friend __device__ __forceinline__ d64f operator-(d64f a, d64f b) { return d64f(a.v - b.v); }
+  friend __device__ __forceinline__ d64f operator-(d64f a) { return d64f(-a.v); }
+  friend __device__ __forceinline__ d64f operator*(d64f a, d64f b) { return d64f(__dmul_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ d64f fma(d64f a, d64f b, d64f c) { return d64f(::fma(a.v, b.v, c.v)); }
+  friend __device__ __forceinline__ d64f recip(d64f x) { return d64f(recip(x.v)); }
+  friend __device__ __forceinline__ d64f scaled(d64f x, float k) { return d64f(scaled(x.v, k)); }
+};
+
+// Bit 31 set iff x is infinite or NaN (its exponent field all ones).
+__device__ __forceinline__ unsigned nonfinite_bit(double x) {
+  return (((unsigned)__double2hiint(x)) & 0x7FF00000u) + 0x00100000u;
+}
 
 // In-place collision of one node (see collide_form); the FP64 form takes its
-// products on the integer pipes.
+// products on the integer pipes. Its results are checked once: a node with a
+// non-finite result (a product outside the integer fast path, or non-finite
+// data) is collided again with its products on the FP64 pipe, which gives the
+// integer-pipe products' bits where they applied and the FP64 instruction's
+// elsewhere; the redo is a warp-uniform branch that normal data never takes.
 template <int MODEL, bool SHIFT, typename T, typename Sink>
 __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink) {
   if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
     d64m g[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = d64m(f[i]);
-    const Coef<d64m> ce = coef_cast<d64m>(c);
-    collide_form<MODEL, SHIFT, d64m>(g, ce, [&](const NodeMoments<d64m>& m) {
+    collide_form<MODEL, SHIFT, d64m>(g, coef_cast<d64m>(c), [&](const NodeMoments<d64m>& m) {
       NodeMoments<double> md;
       md.m0 = m.m0.v, md.jx = m.jx.v, md.jy = m.jy.v, md.ux = m.ux.v, md.uy = m.uy.v;
       sink(md);
     });
+    unsigned bad = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) bad |= nonfinite_bit(g[i].v);
+    if (__any_sync(__activemask(), (int)bad < 0)) {
+      if ((int)bad < 0) {
+        d64f h[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i] = d64f(f[i]);
+        collide_form<MODEL, SHIFT, d64f>(h, coef_cast<d64f>(c), [](const NodeMoments<d64f>&) {});
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = d64m(h[i].v);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = g[i].v;
   } else {

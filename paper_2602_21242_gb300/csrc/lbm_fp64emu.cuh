@@ -192,6 +192,11 @@ OLBM_EMU_HD double add64(double a, double b) {
 // product from four 32 x 32 -> 64-bit multiply-adds, a normalisation by at most
 // one bit, and the rounding increment (rem + lsb > half) carried into the packed
 // exponent field.
+// CHECKED = false leaves out the fallback: a product outside the fast path
+// comes out as a quiet NaN, which every later sum, product or FMA propagates,
+// so a caller that checks its results for non-finite values once (and redoes
+// those with the FP64 instruction) needs no branch per product.
+template <bool CHECKED = true>
 OLBM_EMU_HD double mul64(double a, double b) {
   const uint64_t ua = bits_of(a), ub = bits_of(b);
   const uint32_t ah = (uint32_t)(ua >> 32), al = (uint32_t)ua, bh = (uint32_t)(ub >> 32), bl = (uint32_t)ub;
@@ -217,7 +222,11 @@ OLBM_EMU_HD double mul64(double a, double b) {
   const uint64_t m = ((uint64_t)m1 << 32) | m0;
   const bool fast = (unsigned)(ea - 1) < 2046u && (unsigned)(eb - 1) < 2046u && (unsigned)(e - 1) < 2046u;
   const double r = double_of((((uint64_t)((ah ^ bh) & 0x80000000u)) << 32) | ((((uint64_t)(e - 1)) << 52) + m + inc));
-  return take_fallback(fast) ? (fast ? r : mul_fallback(a, b)) : r;
+  if constexpr (CHECKED) {
+    return take_fallback(fast) ? (fast ? r : mul_fallback(a, b)) : r;
+  } else {
+    return fast ? r : double_of(0x7FF8000000000000ull);  // a quiet NaN where the fast path does not apply
+  }
 }
 
 }  // namespace emu

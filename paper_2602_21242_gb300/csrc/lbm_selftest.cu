@@ -104,37 +104,21 @@ __global__ void fp64_emu_kernel(int op, const double* __restrict__ a, const doub
   }
 }
 
-// FP64 values with the same operations as d64m, every product on the FP64 pipe
-// (__dmul_rn, never contracted into an FMA): the collision on this type is the
-// reference for the integer-pipe products.
-struct d64r {
-  double v;
-  d64r() = default;
-  __host__ __device__ constexpr d64r(double x) : v(x) {}
-  friend __device__ __forceinline__ d64r operator+(d64r a, d64r b) { return d64r(a.v + b.v); }
-  friend __device__ __forceinline__ d64r operator-(d64r a, d64r b) { return d64r(a.v - b.v); }
-  friend __device__ __forceinline__ d64r operator-(d64r a) { return d64r(-a.v); }
-  friend __device__ __forceinline__ d64r operator*(d64r a, d64r b) { return d64r(__dmul_rn(a.v, b.v)); }
-  friend __device__ __forceinline__ d64r fma(d64r a, d64r b, d64r c) { return d64r(::fma(a.v, b.v, c.v)); }
-  friend __device__ __forceinline__ d64r recip(d64r x) { return d64r(olbm::recip(x.v)); }
-  friend __device__ __forceinline__ d64r scaled(d64r x, float k) { return d64r(olbm::scaled(x.v, k)); }
-};
-
 template <int MODEL>
 __global__ void collide_f64_kernel(const double* __restrict__ fin, long long n, olbm::Coef<double> c,
                                    double* __restrict__ out_emu, double* __restrict__ out_ref) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double f[9];
-  d64r g[9];
+  olbm::d64f g[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) f[k] = fin[i * 9 + k], g[k] = d64r(f[k]);
+  for (int k = 0; k < 9; ++k) f[k] = fin[i * 9 + k], g[k] = olbm::d64f(f[k]);
   double mom[5], momr[5];
   olbm::collide<MODEL, false, double>(f, c, [&](const olbm::NodeMoments<double>& m) {
     mom[0] = m.m0, mom[1] = m.jx, mom[2] = m.jy, mom[3] = m.ux, mom[4] = m.uy;
   });
-  const olbm::Coef<d64r> cr = olbm::coef_cast<d64r>(c);
-  olbm::collide_form<MODEL, false, d64r>(g, cr, [&](const olbm::NodeMoments<d64r>& m) {
+  const olbm::Coef<olbm::d64f> cr = olbm::coef_cast<olbm::d64f>(c);
+  olbm::collide_form<MODEL, false, olbm::d64f>(g, cr, [&](const olbm::NodeMoments<olbm::d64f>& m) {
     momr[0] = m.m0.v, momr[1] = m.jx.v, momr[2] = m.jy.v, momr[3] = m.ux.v, momr[4] = m.uy.v;
   });
 #pragma unroll

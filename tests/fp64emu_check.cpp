@@ -47,6 +47,14 @@ int check(const char* what, double a, double b) {
     std::printf("MISMATCH %s mul a=%a b=%a host=%a emu=%a\n", what, a, b, p, ep);
     return 1;
   }
+  // the product without its fallback: the same bits, or a NaN outside the fast path
+  // (never for normal operands whose product lies well inside the normal range)
+  const double eu = olbm::emu::mul64<false>(a, b);
+  const bool inside = std::isnormal(a) && std::isnormal(b) && std::fabs(p) > 0x1p-1020 && std::fabs(p) < 0x1p+1022;
+  if (!(same(p, eu) || (std::isnan(eu) && !inside))) {
+    std::printf("MISMATCH %s unchecked mul a=%a b=%a host=%a emu=%a\n", what, a, b, p, eu);
+    return 1;
+  }
   return 0;
 }
 
