@@ -60,25 +60,44 @@ __device__ __forceinline__ void adj_step_body(const typename Form<PREC>::S* __re
   using T = typename Form<PREC>::T;
   const int x = blockIdx.x * kABX + threadIdx.x, y = blockIdx.y * kABY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  long long o[9];
-  pull_offsets(x, y, g, o);
+  // f pulled at (x, y); mu_i = lambda_i(t + 1) at x + c_i, periodic
+  auto load = [&](T (&f)[9], T (&mu)[9]) {
+    long long o[9];
+    pull_offsets(x, y, g, o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ld_t(fbuf + i * g.plane + o[i], T());
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      int xd = x + cx_of(i), yd = y + cy_of(i);
+      xd = xd < 0 ? xd + g.nx : (xd >= g.nx ? xd - g.nx : xd);
+      yd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
+      mu[i] = lam_next[i * g.plane + (long long)yd * g.pitch + xd];
+    }
+  };
   T f[9], mu[9], out[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = ld_t(fbuf + i * g.plane + o[i], T());
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    int xd = x + cx_of(i), yd = y + cy_of(i);  // x + c_i, periodic
-    xd = xd < 0 ? xd + g.nx : (xd >= g.nx ? xd - g.nx : xd);
-    yd = yd < 0 ? yd + g.ny : (yd >= g.ny ? yd - g.ny : yd);
-    mu[i] = lam_next[i * g.plane + (long long)yd * g.pitch + xd];
-  }
+  load(f, mu);
   if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
-    // FP64: the products on the integer pipes, each with its own fallback (a
-    // single check of the results would keep f and mu live for a redo: spills)
-    d64c fe[9], me[9], oe[9];
+    // FP64: the products on the integer pipes, as in the forward collision, and
+    // the same single check of the results: a node with a non-finite result is
+    // loaded again and redone with its products on the FP64 pipe (same bits)
+    d64m fe[9], me[9], oe[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fe[i] = d64c(f[i]), me[i] = d64c(mu[i]);
-    collide_vjp<MODEL, Form<PREC>::kShift, d64c>(fe, me, coef_cast<d64c>(c), oe);
+    for (int i = 0; i < 9; ++i) fe[i] = d64m(f[i]), me[i] = d64m(mu[i]);
+    collide_vjp<MODEL, Form<PREC>::kShift, d64m>(fe, me, coef_cast<d64m>(c), oe);
+    unsigned bad = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) bad |= nonfinite_bit(oe[i].v);
+    if (__any_sync(__activemask(), (int)bad < 0)) {
+      if ((int)bad < 0) {
+        load(f, mu);
+        d64f fr[9], mr[9], orr[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fr[i] = d64f(f[i]), mr[i] = d64f(mu[i]);
+        collide_vjp<MODEL, Form<PREC>::kShift, d64f>(fr, mr, coef_cast<d64f>(c), orr);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) oe[i] = d64m(orr[i].v);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i] = oe[i].v;
   } else {

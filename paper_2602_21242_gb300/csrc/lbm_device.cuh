@@ -552,15 +552,24 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x) {
   return (((unsigned)__double2hiint(x)) & 0x7FF00000u) + 0x00100000u;
 }
 
+// No way to fetch a node's populations again: collide() keeps its own copy.
+struct KeepInputs {
+  __device__ void operator()(double (&)[9]) const {}
+};
+
 // In-place collision of one node (see collide_form); the FP64 form takes its
 // products on the integer pipes. Its results are checked once: a node with a
 // non-finite result (a product outside the integer fast path, or non-finite
 // data) is collided again with its products on the FP64 pipe, which gives the
 // integer-pipe products' bits where they applied and the FP64 instruction's
 // elsewhere; the redo is a warp-uniform branch that normal data never takes.
-template <int MODEL, bool SHIFT, typename T, typename Sink>
-__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink) {
+// refetch(f) loads the node's pulled populations again for the redo (callers
+// that can: no copy of them stays live through the collision); with KeepInputs
+// collide() keeps a copy.
+template <int MODEL, bool SHIFT, typename T, typename Sink, typename Refetch = KeepInputs>
+__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink, Refetch&& refetch = Refetch()) {
   if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
+    constexpr bool kKeep = std::is_same<std::decay_t<Refetch>, KeepInputs>::value;
     d64m g[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = d64m(f[i]);
@@ -574,6 +583,7 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
     for (int i = 0; i < 9; ++i) bad |= nonfinite_bit(g[i].v);
     if (__any_sync(__activemask(), (int)bad < 0)) {
       if ((int)bad < 0) {
+        if constexpr (!kKeep) refetch(f);
         d64f h[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) h[i] = d64f(f[i]);

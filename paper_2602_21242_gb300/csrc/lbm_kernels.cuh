@@ -299,9 +299,12 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
     for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
       const bool more = (r + 1 < rows) && (y + dy < g.ny);
       if (more) pull(src, g, x, xm, xp, y + dy, fn);
-      collide<MODEL, Form<PREC>::kShift, CT>(f, c, [&](const NodeMoments<CT>& m) {
-        if constexpr (DIAG) acc.add(m);
-      });
+      collide<MODEL, Form<PREC>::kShift, CT>(
+          f, c,
+          [&](const NodeMoments<CT>& m) {
+            if constexpr (DIAG) acc.add(m);
+          },
+          [&](CT (&r)[9]) { pull(src, g, x, xm, xp, y, r); });
       S* q = dst + (long long)y * g.pitch + x;
       if constexpr (PAIRS) {
 #pragma unroll
