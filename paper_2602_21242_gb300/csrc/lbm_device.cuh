@@ -559,29 +559,45 @@ struct KeepInputs {
 
 // In-place collision of one node (see collide_form); the FP64 form takes its
 // products on the integer pipes. Its results are checked once: a node with a
-// non-finite result (a product outside the integer fast path, or non-finite
-// data) is collided again with its products on the FP64 pipe, which gives the
-// integer-pipe products' bits where they applied and the FP64 instruction's
-// elsewhere; the redo is a warp-uniform branch that normal data never takes.
-// refetch(f) loads the node's pulled populations again for the redo (callers
-// that can: no copy of them stays live through the collision); with KeepInputs
-// collide() keeps a copy.
+// non-finite result (a product outside the integer fast path, such as a zero
+// velocity, or non-finite data) is collided again with its products on the FP64
+// pipe, which gives the integer-pipe products' bits where they applied and the
+// FP64 instruction's elsewhere; the redo is a warp-uniform branch. refetch(f)
+// loads the node's pulled populations again for the redo (callers that can: no
+// copy of them stays live through the collision); with KeepInputs collide()
+// keeps a copy. native (optional, per thread, the same in every thread of a
+// warp): set once a warp has needed a redo, after which its nodes take the FP64
+// products directly (zeros come in regions: a flow at rest, a velocity component
+// that vanishes everywhere).
 template <int MODEL, bool SHIFT, typename T, typename Sink, typename Refetch = KeepInputs>
-__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink, Refetch&& refetch = Refetch()) {
+__device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink, Refetch&& refetch = Refetch(),
+                                        bool* native = nullptr) {
   if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
     constexpr bool kKeep = std::is_same<std::decay_t<Refetch>, KeepInputs>::value;
+    auto to_double = [&](const auto& m) {
+      NodeMoments<double> md;
+      md.m0 = m.m0.v, md.jx = m.jx.v, md.jy = m.jy.v, md.ux = m.ux.v, md.uy = m.uy.v;
+      return md;
+    };
+    if (native != nullptr && *native) {
+      d64f h[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = d64f(f[i]);
+      collide_form<MODEL, SHIFT, d64f>(h, coef_cast<d64f>(c),
+                                       [&](const NodeMoments<d64f>& m) { sink(to_double(m)); });
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = h[i].v;
+      return;
+    }
     d64m g[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = d64m(f[i]);
-    collide_form<MODEL, SHIFT, d64m>(g, coef_cast<d64m>(c), [&](const NodeMoments<d64m>& m) {
-      NodeMoments<double> md;
-      md.m0 = m.m0.v, md.jx = m.jx.v, md.jy = m.jy.v, md.ux = m.ux.v, md.uy = m.uy.v;
-      sink(md);
-    });
+    collide_form<MODEL, SHIFT, d64m>(g, coef_cast<d64m>(c), [&](const NodeMoments<d64m>& m) { sink(to_double(m)); });
     unsigned bad = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) bad |= nonfinite_bit(g[i].v);
     if (__any_sync(__activemask(), (int)bad < 0)) {
+      if (native != nullptr) *native = true;
       if ((int)bad < 0) {
         if constexpr (!kKeep) refetch(f);
         d64f h[9];

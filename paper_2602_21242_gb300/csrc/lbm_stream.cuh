@@ -349,6 +349,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
     const int iM = base + CH + xl;
     const int iL = xl == 0 ? base + p.lidx : iM - 1;
     const int iR = xl + 1 < p.w ? iM + 1 : base + CH + p.wr;
+    bool native = false;  // this warp's nodes take FP64-pipe products (see collide)
     for (int r0 = 0; r0 < rows; r0 += p.R, ++k) {
       const bool active = j < min(p.R, rows - r0);
       const int s = k % STAGES;
@@ -369,9 +370,12 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       if (active) {
-        collide<MODEL, false, double>(f, c, [&](const NodeMoments<double>& m) {
-          if constexpr (DIAG) acc.add(m);
-        });
+        collide<MODEL, false, double>(
+            f, c,
+            [&](const NodeMoments<double>& m) {
+              if constexpr (DIAG) acc.add(m);
+            },
+            KeepInputs(), &native);
         double* q = dst + (long long)(y0 + r0 + j) * g.pitch + x0 + xl;
 #pragma unroll
         for (int i = 0; i < 9; ++i) q[i * g.plane] = f[i];

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 
 #include "lbm_fp64emu.cuh"
 
@@ -63,9 +64,14 @@ int check(const char* what, double a, double b) {
 int main(int argc, char** argv) {
   const long n = argc > 1 ? std::atol(argv[1]) : 1000000;
   uint64_t st = argc > 2 ? std::strtoull(argv[2], nullptr, 10) : 1;
-  const int kFamilies = 8;
+  const int kFamilies = 10;
   const char* names[kFamilies] = {"random bits", "normal, any distance", "cancelling", "add ties",
-                                  "mul ties and exact", "range edges", "lattice magnitudes", "near one"};
+                                  "mul ties and exact", "range edges", "lattice magnitudes", "near one",
+                                  "zeros and specials", "special pairs"};
+  const double special[] = {0.0, -0.0, 1.0, -1.0, 0.5, 3.0, -0.1, 1e-300, -1e300, 0x1p-1022, -0x1p-1022,
+                            0x1p-1074, -0x1p-1074, 0x1.8p-1060, 0x1.fffffffffffffp+1023, -0x1.fffffffffffffp+1023,
+                            HUGE_VAL, -HUGE_VAL, NAN, -NAN};
+  const int nspecial = (int)(sizeof special / sizeof special[0]);
   for (int fam = 0; fam < kFamilies; ++fam) {
     for (long i = 0; i < n; ++i) {
       const uint64_t r0 = splitmix(st), r1 = splitmix(st), r2 = splitmix(st);
@@ -129,6 +135,18 @@ int main(int argc, char** argv) {
           const double u0 = (double)(r0 >> 11) * 0x1p-53;
           a = 1.0 + (u0 - 0.5) * 1e-6;
           b = (r2 & 1) ? -1.0 : 1.0 / 3.0;
+          break;
+        }
+        case 8: {
+          // a special value against a random normal one
+          a = special[r2 % nspecial];
+          b = make(r1 >> 63, 1 + (int)((r1 >> 20) % 2046), r0);
+          break;
+        }
+        case 9: {
+          // every pair of special values
+          a = special[i % nspecial];
+          b = special[(i / nspecial) % nspecial];
           break;
         }
       }

@@ -3,7 +3,8 @@ compiled for the host, against the host's own IEEE 754 binary64 arithmetic bit f
 bit: tests/fp64emu_check.cpp draws operand families that reach every path of the
 routines (random bit patterns with zeros, subnormals, infinities and NaNs; every
 exponent distance; cancelling sums; exact ties of the sum and of the product;
-products at the edges of the normal range; the lattice's magnitudes)."""
+products at the edges of the normal range; the lattice's magnitudes; zeros of both
+signs, subnormals, infinities and NaNs against normal values and against each other)."""
 import os
 import shutil
 import subprocess
@@ -32,4 +33,4 @@ def test_integer_pipe_arithmetic_matches_ieee(checker, seed):
     res = subprocess.run([checker, "400000", str(seed)], capture_output=True, text=True, timeout=300)
     assert res.returncode == 0, res.stdout + res.stderr
     lines = [l for l in res.stdout.splitlines() if l.strip()]
-    assert len(lines) == 8 and all(l.endswith("all equal") for l in lines), res.stdout
+    assert len(lines) == 10 and all(l.endswith("all equal") for l in lines), res.stdout
