@@ -489,63 +489,50 @@ __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&&
 // collision runs on this type, so the FP64 pipe, which bounds the FP64 form on
 // GB300, carries only the sums and FMAs, while the products overlap with them on
 // the otherwise idle integer pipes (complete model at 4096^2, diagnostics every
-// step: 4.78 -> 5.93 GLUPS). The products leave out their fallback (a product
+// step: 4.78 -> 6.33 GLUPS). The products leave out their fallback (a product
 // outside the fast path is a quiet NaN), and collide() checks the node's nine
-// results once instead: a branch per product measured 8 % slower. Sums on the
+// results once instead: a branch per product measured 6 % slower. Sums on the
 // integer pipes as well (emu::add64) measured slower wherever they were put: the
 // moments, which head the collision's dependency chain, 4.9; the corrections,
 // the factors P or C, or the diagnostics sums, 5.2 to 5.6 (against 5.76).
 #ifndef OLBM_F64_EMU_MUL
 #define OLBM_F64_EMU_MUL 1
 #endif
-struct d64m {
+// How an FP64 wrapper type below forms its products.
+enum class Mul64 {
+  kIntUnchecked,  // integer pipes, a quiet NaN outside the fast path (the caller checks its results)
+  kIntChecked,    // integer pipes, the FP64 instruction behind a warp-uniform branch outside the fast path
+  kFp64           // the FP64 instruction (__dmul_rn, never contracted into an FMA)
+};
+template <Mul64 M> struct d64 {
   double v;
-  d64m() = default;
-  __host__ __device__ constexpr d64m(double x) : v(x) {}
-  // Hidden friends: found only by argument-dependent lookup on d64m, so they
+  d64() = default;
+  __host__ __device__ constexpr d64(double x) : v(x) {}
+  // Hidden friends: found only by argument-dependent lookup on d64, so they
   // never capture a call on plain doubles.
-  friend __device__ __forceinline__ d64m operator+(d64m a, d64m b) { return d64m(a.v + b.v); }
-  friend __device__ __forceinline__ d64m operator-(d64m a, d64m b) { return d64m(a.v - b.v); }
-  friend __device__ __forceinline__ d64m operator-(d64m a) { return d64m(-a.v); }
-  friend __device__ __forceinline__ d64m operator*(d64m a, d64m b) { return d64m(emu::mul64<false>(a.v, b.v)); }
-  friend __device__ __forceinline__ d64m mul_u(d64m a, d64m b) { return d64m(emu::mul64<true>(a.v, b.v)); }
-  friend __device__ __forceinline__ d64m fma(d64m a, d64m b, d64m c) { return d64m(::fma(a.v, b.v, c.v)); }
-  friend __device__ __forceinline__ d64m recip(d64m x) { return d64m(recip(x.v)); }
-  friend __device__ __forceinline__ d64m scaled(d64m x, float k) { return d64m(scaled(x.v, k)); }
+  friend __device__ __forceinline__ d64 operator+(d64 a, d64 b) { return d64(a.v + b.v); }
+  friend __device__ __forceinline__ d64 operator-(d64 a, d64 b) { return d64(a.v - b.v); }
+  friend __device__ __forceinline__ d64 operator-(d64 a) { return d64(-a.v); }
+  friend __device__ __forceinline__ d64 operator*(d64 a, d64 b) {
+    if constexpr (M == Mul64::kFp64) return d64(__dmul_rn(a.v, b.v));
+    else return d64(emu::mul64<M == Mul64::kIntChecked>(a.v, b.v));
+  }
+  // u = j / rho: checked in every integer form (the velocities reach the diagnostics early)
+  friend __device__ __forceinline__ d64 mul_u(d64 a, d64 b) {
+    if constexpr (M == Mul64::kFp64) return d64(__dmul_rn(a.v, b.v));
+    else return d64(emu::mul64<true>(a.v, b.v));
+  }
+  friend __device__ __forceinline__ d64 fma(d64 a, d64 b, d64 c) { return d64(::fma(a.v, b.v, c.v)); }
+  friend __device__ __forceinline__ d64 recip(d64 x) { return d64(recip(x.v)); }
+  friend __device__ __forceinline__ d64 scaled(d64 x, float k) { return d64(scaled(x.v, k)); }
 };
-
-// The same with every product checked on its own (emu::mul64<true>: the FP64
-// instruction behind a warp-uniform branch where the fast path does not apply),
-// for callers that cannot redo a node (the adjoint step).
-struct d64c {
-  double v;
-  d64c() = default;
-  __host__ __device__ constexpr d64c(double x) : v(x) {}
-  friend __device__ __forceinline__ d64c operator+(d64c a, d64c b) { return d64c(a.v + b.v); }
-  friend __device__ __forceinline__ d64c operator-(d64c a, d64c b) { return d64c(a.v - b.v); }
-  friend __device__ __forceinline__ d64c operator-(d64c a) { return d64c(-a.v); }
-  friend __device__ __forceinline__ d64c operator*(d64c a, d64c b) { return d64c(emu::mul64<true>(a.v, b.v)); }
-  friend __device__ __forceinline__ d64c fma(d64c a, d64c b, d64c c) { return d64c(::fma(a.v, b.v, c.v)); }
-  friend __device__ __forceinline__ d64c recip(d64c x) { return d64c(recip(x.v)); }
-  friend __device__ __forceinline__ d64c scaled(d64c x, float k) { return d64c(scaled(x.v, k)); }
-};
-
-// The same operations with every product on the FP64 pipe (__dmul_rn, never
-// contracted into an FMA): the FP64 collision of a node whose integer-pipe
-// products left the fast path is redone on this type, with the same result
-// bits as the integer-pipe products would have given.
-struct d64f {
-  double v;
-  d64f() = default;
-  __host__ __device__ constexpr d64f(double x) : v(x) {}
-  friend __device__ __forceinline__ d64f operator+(d64f a, d64f b) { return d64f(a.v + b.v); }
-  friend __device__ __forceinline__ d64f operator-(d64f a, d64f b) { return d64f(a.v - b.v); }
-  friend __device__ __forceinline__ d64f operator-(d64f a) { return d64f(-a.v); }
-  friend __device__ __forceinline__ d64f operator*(d64f a, d64f b) { return d64f(__dmul_rn(a.v, b.v)); }
-  friend __device__ __forceinline__ d64f fma(d64f a, d64f b, d64f c) { return d64f(::fma(a.v, b.v, c.v)); }
-  friend __device__ __forceinline__ d64f recip(d64f x) { return d64f(recip(x.v)); }
-  friend __device__ __forceinline__ d64f scaled(d64f x, float k) { return d64f(scaled(x.v, k)); }
-};
+// The FP64 collision's type; the adjoint step's (every product checked on its
+// own: it cannot switch a warp to FP64 products, see adj_step_body); and the type
+// a node whose integer products left the fast path is redone on, which gives the
+// integer products' bits where they applied and the FP64 instruction's elsewhere.
+using d64m = d64<Mul64::kIntUnchecked>;
+using d64c = d64<Mul64::kIntChecked>;
+using d64f = d64<Mul64::kFp64>;
 
 // Bit 31 set iff x is infinite or NaN (its exponent field all ones).
 __device__ __forceinline__ unsigned nonfinite_bit(double x) {
