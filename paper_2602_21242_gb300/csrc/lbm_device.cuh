@@ -501,6 +501,7 @@ __device__ __forceinline__ void collide_form(T (&f)[9], const Coef<T>& c, Sink&&
 // How an FP64 wrapper type below forms its products.
 enum class Mul64 {
   kIntUnchecked,  // integer pipes, a quiet NaN outside the fast path (the caller checks its results)
+  kIntZeros,      // the same with zero operands on the fast path
   kIntChecked,    // integer pipes, the FP64 instruction behind a warp-uniform branch outside the fast path
   kFp64           // the FP64 instruction (__dmul_rn, never contracted into an FMA)
 };
@@ -515,7 +516,7 @@ template <Mul64 M> struct d64 {
   friend __device__ __forceinline__ d64 operator-(d64 a) { return d64(-a.v); }
   friend __device__ __forceinline__ d64 operator*(d64 a, d64 b) {
     if constexpr (M == Mul64::kFp64) return d64(__dmul_rn(a.v, b.v));
-    else return d64(emu::mul64<M == Mul64::kIntChecked>(a.v, b.v));
+    else return d64(emu::mul64<M == Mul64::kIntChecked, M == Mul64::kIntZeros>(a.v, b.v));
   }
   // u = j / rho: checked in every integer form (the velocities reach the diagnostics early)
   friend __device__ __forceinline__ d64 mul_u(d64 a, d64 b) {
@@ -526,11 +527,13 @@ template <Mul64 M> struct d64 {
   friend __device__ __forceinline__ d64 recip(d64 x) { return d64(recip(x.v)); }
   friend __device__ __forceinline__ d64 scaled(d64 x, float k) { return d64(scaled(x.v, k)); }
 };
-// The FP64 collision's type; the adjoint step's (every product checked on its
-// own: it cannot switch a warp to FP64 products, see adj_step_body); and the type
-// a node whose integer products left the fast path is redone on, which gives the
-// integer products' bits where they applied and the FP64 instruction's elsewhere.
+// The FP64 collision's type; the one its warps switch to after zero operands sent
+// a node to a redo; the adjoint step's (every product checked on its own: it
+// cannot switch a warp, see adj_step_body); and the type a node whose integer
+// products left the fast path is redone on, which gives the integer products'
+// bits where they applied and the FP64 instruction's elsewhere.
 using d64m = d64<Mul64::kIntUnchecked>;
+using d64z = d64<Mul64::kIntZeros>;
 using d64c = d64<Mul64::kIntChecked>;
 using d64f = d64<Mul64::kFp64>;
 
@@ -548,17 +551,17 @@ struct KeepInputs {
 // products on the integer pipes. Its results are checked once: a node with a
 // non-finite result (a product outside the integer fast path, such as a zero
 // velocity, or non-finite data) is collided again with its products on the FP64
-// pipe, which gives the integer-pipe products' bits where they applied and the
-// FP64 instruction's elsewhere; the redo is a warp-uniform branch. refetch(f)
-// loads the node's pulled populations again for the redo (callers that can: no
-// copy of them stays live through the collision); with KeepInputs collide()
-// keeps a copy. native (optional, per thread, the same in every thread of a
-// warp): set once a warp has needed a redo, after which its nodes take the FP64
-// products directly (zeros come in regions: a flow at rest, a velocity component
-// that vanishes everywhere).
+// pipe, which gives the integer products' bits where they applied and the FP64
+// instruction's elsewhere; the redo is a warp-uniform branch. refetch(f) loads
+// the node's pulled populations again for the redo (callers that can: no copy of
+// them stays live through the collision); with KeepInputs collide() keeps a copy.
+// mode (optional, per thread, the same in every thread of a warp) steps up each
+// time the warp needs a redo: 0 the integer products, 1 the integer products
+// with zero operands on the fast path (zeros come in regions: a flow at rest, a
+// velocity component that vanishes everywhere), 2 the FP64 products.
 template <int MODEL, bool SHIFT, typename T, typename Sink, typename Refetch = KeepInputs>
 __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink, Refetch&& refetch = Refetch(),
-                                        bool* native = nullptr) {
+                                        int* mode = nullptr) {
   if constexpr (std::is_same<T, double>::value && OLBM_F64_EMU_MUL) {
     constexpr bool kKeep = std::is_same<std::decay_t<Refetch>, KeepInputs>::value;
     auto to_double = [&](const auto& m) {
@@ -566,7 +569,8 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
       md.m0 = m.m0.v, md.jx = m.jx.v, md.jy = m.jy.v, md.ux = m.ux.v, md.uy = m.uy.v;
       return md;
     };
-    if (native != nullptr && *native) {
+    const int md = mode != nullptr ? *mode : 0;
+    if (md >= 2) {
       d64f h[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) h[i] = d64f(f[i]);
@@ -576,15 +580,29 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
       for (int i = 0; i < 9; ++i) f[i] = h[i].v;
       return;
     }
-    d64m g[9];
+    double g[9];
+    if (md == 0) {
+      d64m e[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = d64m(f[i]);
-    collide_form<MODEL, SHIFT, d64m>(g, coef_cast<d64m>(c), [&](const NodeMoments<d64m>& m) { sink(to_double(m)); });
+      for (int i = 0; i < 9; ++i) e[i] = d64m(f[i]);
+      collide_form<MODEL, SHIFT, d64m>(e, coef_cast<d64m>(c),
+                                       [&](const NodeMoments<d64m>& m) { sink(to_double(m)); });
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = e[i].v;
+    } else {
+      d64z e[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) e[i] = d64z(f[i]);
+      collide_form<MODEL, SHIFT, d64z>(e, coef_cast<d64z>(c),
+                                       [&](const NodeMoments<d64z>& m) { sink(to_double(m)); });
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = e[i].v;
+    }
     unsigned bad = 0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) bad |= nonfinite_bit(g[i].v);
+    for (int i = 0; i < 9; ++i) bad |= nonfinite_bit(g[i]);
     if (__any_sync(__activemask(), (int)bad < 0)) {
-      if (native != nullptr) *native = true;
+      if (mode != nullptr) *mode = md + 1;
       if ((int)bad < 0) {
         if constexpr (!kKeep) refetch(f);
         d64f h[9];
@@ -592,11 +610,11 @@ __device__ __forceinline__ void collide(T (&f)[9], const Coef<T>& c, Sink&& sink
         for (int i = 0; i < 9; ++i) h[i] = d64f(f[i]);
         collide_form<MODEL, SHIFT, d64f>(h, coef_cast<d64f>(c), [](const NodeMoments<d64f>&) {});
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = d64m(h[i].v);
+        for (int i = 0; i < 9; ++i) g[i] = h[i].v;
       }
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = g[i].v;
+    for (int i = 0; i < 9; ++i) f[i] = g[i];
   } else {
     collide_form<MODEL, SHIFT, T>(f, c, sink);
   }

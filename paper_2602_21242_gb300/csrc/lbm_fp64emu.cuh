@@ -195,8 +195,9 @@ OLBM_EMU_HD double add64(double a, double b) {
 // CHECKED = false leaves out the fallback: a product outside the fast path
 // comes out as a quiet NaN, which every later sum, product or FMA propagates,
 // so a caller that checks its results for non-finite values once (and redoes
-// those with the FP64 instruction) needs no branch per product.
-template <bool CHECKED = true>
+// those with the FP64 instruction) needs no branch per product. ZEROS = true
+// takes zero operands on the fast path too (a few more instructions).
+template <bool CHECKED = true, bool ZEROS = false>
 OLBM_EMU_HD double mul64(double a, double b) {
   const uint64_t ua = bits_of(a), ub = bits_of(b);
   const uint32_t ah = (uint32_t)(ua >> 32), al = (uint32_t)ua, bh = (uint32_t)(ub >> 32), bl = (uint32_t)ub;
@@ -220,8 +221,17 @@ OLBM_EMU_HD double mul64(double a, double b) {
   const uint32_t rem = (n0 & 0x7FFu) | (low != 0 ? 1u : 0u);
   const uint32_t inc = rem + (m0 & 1u) > 0x400u ? 1u : 0u;
   const uint64_t m = ((uint64_t)m1 << 32) | m0;
-  const bool fast = (unsigned)(ea - 1) < 2046u && (unsigned)(eb - 1) < 2046u && (unsigned)(e - 1) < 2046u;
-  const double r = double_of((((uint64_t)((ah ^ bh) & 0x80000000u)) << 32) | ((((uint64_t)(e - 1)) << 52) + m + inc));
+  const bool na = (unsigned)(ea - 1) < 2046u, nb = (unsigned)(eb - 1) < 2046u;
+  const uint64_t sign = ((uint64_t)((ah ^ bh) & 0x80000000u)) << 32;
+  bool fast = na && nb && (unsigned)(e - 1) < 2046u;
+  double r = double_of(sign | ((((uint64_t)(e - 1)) << 52) + m + inc));
+  if constexpr (ZEROS) {
+    // a zero operand times a normal one (or zero) gives a zero of the product's sign
+    const bool za = ((ah << 1) | al) == 0, zb = ((bh << 1) | bl) == 0;
+    const bool zero = (za && (nb || zb)) || (zb && na);
+    fast = fast || zero;
+    r = zero ? double_of(sign) : r;
+  }
   if constexpr (CHECKED) {
     return take_fallback(fast) ? (fast ? r : mul_fallback(a, b)) : r;
   } else {

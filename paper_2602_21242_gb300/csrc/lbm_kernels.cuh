@@ -295,7 +295,7 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
     }
     CT f[9], fn[9];
     int y = y0;
-    bool native = false;  // FP64: this warp's nodes take FP64-pipe products (see collide)
+    int mode = 0;  // FP64: which products this warp's nodes take (see collide)
     if (y < g.ny) pull(src, g, x, xm, xp, y, f);
     for (int r = 0; r < rows && y < g.ny; ++r, y += dy) {
       const bool more = (r + 1 < rows) && (y + dy < g.ny);
@@ -305,7 +305,7 @@ template <int MODEL, int PREC, bool DIAG, bool PAIRS, bool CG = false> struct Co
           [&](const NodeMoments<CT>& m) {
             if constexpr (DIAG) acc.add(m);
           },
-          [&](CT (&r)[9]) { pull(src, g, x, xm, xp, y, r); }, &native);
+          [&](CT (&r)[9]) { pull(src, g, x, xm, xp, y, r); }, &mode);
       S* q = dst + (long long)y * g.pitch + x;
       if constexpr (PAIRS) {
 #pragma unroll

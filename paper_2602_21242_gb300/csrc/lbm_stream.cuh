@@ -349,7 +349,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
     const int iM = base + CH + xl;
     const int iL = xl == 0 ? base + p.lidx : iM - 1;
     const int iR = xl + 1 < p.w ? iM + 1 : base + CH + p.wr;
-    bool native = false;  // this warp's nodes take FP64-pipe products (see collide)
+    int mode = 0;  // which products this warp's nodes take (see collide)
     for (int r0 = 0; r0 < rows; r0 += p.R, ++k) {
       const bool active = j < min(p.R, rows - r0);
       const int s = k % STAGES;
@@ -375,7 +375,7 @@ template <int PREC, int NC, int STAGES> struct Pipeline {
             [&](const NodeMoments<double>& m) {
               if constexpr (DIAG) acc.add(m);
             },
-            KeepInputs(), &native);
+            KeepInputs(), &mode);
         double* q = dst + (long long)(y0 + r0 + j) * g.pitch + x0 + xl;
 #pragma unroll
         for (int i = 0; i < 9; ++i) q[i * g.plane] = f[i];

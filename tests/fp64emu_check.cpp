@@ -50,10 +50,15 @@ int check(const char* what, double a, double b) {
   }
   // the product without its fallback: the same bits, or a NaN outside the fast path
   // (never for normal operands whose product lies well inside the normal range)
-  const double eu = olbm::emu::mul64<false>(a, b);
+  const double eu = olbm::emu::mul64<false>(a, b), ez = olbm::emu::mul64<false, true>(a, b);
   const bool inside = std::isnormal(a) && std::isnormal(b) && std::fabs(p) > 0x1p-1020 && std::fabs(p) < 0x1p+1022;
+  const bool zero_in = (a == 0 && (std::isnormal(b) || b == 0)) || (b == 0 && std::isnormal(a));
   if (!(same(p, eu) || (std::isnan(eu) && !inside))) {
     std::printf("MISMATCH %s unchecked mul a=%a b=%a host=%a emu=%a\n", what, a, b, p, eu);
+    return 1;
+  }
+  if (!(same(p, ez) || (std::isnan(ez) && !inside && !zero_in))) {
+    std::printf("MISMATCH %s unchecked mul with zeros a=%a b=%a host=%a emu=%a\n", what, a, b, p, ez);
     return 1;
   }
   return 0;
