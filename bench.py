@@ -50,7 +50,7 @@ FALLBACK_HBM_GBS = 6800.0
 # node count (its traffic grows in proportion), the FP32 kernels (single steps, and two
 # steps a launch) captured at 4096^2.
 # Keyed by (storage, model, steps per launch).
-PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete", 1): 133.0, ("f32", "complete", 1): 68.8,
+PROFILED_TRAFFIC_B_PER_NODE = {("f64", "complete", 1): 133.7, ("f32", "complete", 1): 68.8,
                                ("f32", "complete", 2): 72.1}
 MODEL_NAMES = ["lbgk", "oreg", "partial", "complete", "complete_neq"]
 # the step kernel each storage form launches under its default launch shape
