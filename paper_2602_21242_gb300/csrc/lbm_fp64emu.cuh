@@ -11,13 +11,14 @@
 // the guard bits with a sticky bit (a textbook soft-float scheme, e.g. Muller
 // et al., Handbook of Floating-Point Arithmetic, ch. 8).
 //
-// Fast paths cover normal operands with a normal result (and, for sums,
-// exponents at most 31 apart and no cancellation of more than 31 bits).
-// Everything else (a zero, subnormal, infinite or NaN operand, a result below
-// the normal range or past the largest finite value before rounding) goes to
-// the FP64 instruction itself, which gives the same correctly rounded result; a
-// rounding that carries past the largest finite value comes out as infinity, as
-// it must.
+// Fast paths cover normal operands with a normal result (for sums, exponents
+// at most 31 apart and no cancellation of more than 31 bits; for products, on
+// request, zero operands too). Everything else (a zero, subnormal, infinite or
+// NaN operand, a result below the normal range or past the largest finite value
+// before rounding) goes to the FP64 instruction itself, which gives the same
+// correctly rounded result, or, in the product's unchecked form, comes out as a
+// quiet NaN for the caller to find and redo; a rounding that carries past the
+// largest finite value comes out as infinity, as it must.
 //
 // The routines compile for the host as well (plain C++ with 128-bit integer
 // products), where tests compare them bit for bit with the host's binary64
@@ -84,21 +85,8 @@ OLBM_EMU_HD uint32_t shr_lo(uint32_t lo, uint32_t hi, int s) {
 // they sit out of line, so the rare branch that takes them is a real branch and
 // not an FP64 instruction issued under a predicate by every thread.
 #if defined(__CUDACC__)
-#if defined(OLBM_EMU_ASM)
-__device__ __forceinline__ double add_fp64(double a, double b) {
-  double r;
-  asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
-  return r;
-}
-__device__ __forceinline__ double mul_fp64(double a, double b) {
-  double r;
-  asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
-  return r;
-}
-#else
 __device__ __noinline__ inline double add_fp64(double a, double b) { return __dadd_rn(a, b); }
 __device__ __noinline__ inline double mul_fp64(double a, double b) { return __dmul_rn(a, b); }
-#endif
 #endif
 OLBM_EMU_HD double add_fallback(double a, double b) {
 #if defined(__CUDA_ARCH__)
@@ -122,19 +110,13 @@ OLBM_EMU_HD double mul_fallback(double a, double b) {
 // instruction that every thread issues under a predicate.
 OLBM_EMU_HD bool take_fallback(bool fast) {
 #if defined(__CUDA_ARCH__)
-#if defined(OLBM_EMU_EXPECT)
-  return __builtin_expect(!fast, 0);
-#else
   return __any_sync(__activemask(), !fast);
-#endif
 #else
   return !fast;
 #endif
 }
 
 constexpr uint64_t kSign = 0x8000000000000000ull;
-constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull;
-constexpr uint64_t kHidden = 0x0010000000000000ull;
 
 // m (53 bits, leading bit at 52, before rounding) with the 11 bits below it in
 // rem (half = 0x400, any lower non-zero bits already ORed into bit 0), rounded
