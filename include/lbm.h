@@ -529,16 +529,19 @@ int lbm_selftest_fp64_emu(int op, const double* h_a, const double* h_b, long lon
  * Self-test of the FP64 collision (Eq. 1a with the model's f^OReg and
  * corrections; no counterpart in the paper beyond that): collides the n nodes
  * of h_f (host, n x 9 doubles, populations in the order of Fig. 1a) on the GPU
- * twice, with the FP64 kernels' arithmetic (products on the integer pipes) and
- * with every product on the FP64 pipe (never contracted into an FMA), and
- * writes per node the nine post-collision populations and m0, j_x, j_y, u_x,
- * u_y (14 doubles) to h_emu and h_ref (host, n x 14 doubles each,
- * caller-owned). The two agree bit for bit. Coefficients from theta and tau
- * (rho_ref = 1). Synchronous. Returns LBM_EINVAL for an unknown model, n < 0,
- * theta outside (0, 1), tau <= 1/2 or null pointers with n > 0.
+ * twice, with the FP64 kernels' arithmetic and with every product on the FP64
+ * pipe (never contracted into an FMA), and writes per node the nine
+ * post-collision populations and m0, j_x, j_y, u_x, u_y (14 doubles) to h_emu
+ * and h_ref (host, n x 14 doubles each, caller-owned). mode selects the
+ * products the kernels' arithmetic starts with: 0 the integer pipes, 1 the
+ * integer pipes with zero operands on their fast path, 2 the FP64 pipe (the
+ * kernels step a warp from 0 to 1 to 2 each time one of its nodes needs a redo
+ * on FP64 products). The two agree bit for bit. Coefficients from theta and tau
+ * (rho_ref = 1). Synchronous. Returns LBM_EINVAL for an unknown model or mode,
+ * n < 0, theta outside (0, 1), tau <= 1/2 or null pointers with n > 0.
  */
-int lbm_selftest_collide_f64(int model, double theta, double tau, const double* h_f, long long n, double* h_emu,
-                             double* h_ref);
+int lbm_selftest_collide_f64(int model, int mode, double theta, double tau, const double* h_f, long long n,
+                             double* h_emu, double* h_ref);
 
 /* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);

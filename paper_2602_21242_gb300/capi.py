@@ -56,7 +56,7 @@ _SIGNATURES = {
     "lbm_selftest_timeout": ([_i, _pd], _i),
     "lbm_selftest_fp64": ([_i, _pd, _ll, _pd], _i),
     "lbm_selftest_fp64_emu": ([_i, _pd, _pd, _ll, _pd, _pd], _i),
-    "lbm_selftest_collide_f64": ([_i, _d, _d, _pd, _ll, _pd, _pd], _i),
+    "lbm_selftest_collide_f64": ([_i, _i, _d, _d, _pd, _ll, _pd, _pd], _i),
     "lbm_vjp": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "lbm_vjp_forward": ([_p, _i, _i, _p, _p, _p], _i),
     "lbm_vjp_ex": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i], _i),
@@ -433,15 +433,16 @@ def lbm_selftest_fp64_emu(op: int, a, b):
     return emu, ref
 
 
-def lbm_selftest_collide_f64(model: int, theta: float, tau: float, f):
-    """FP64 collision of the nodes f (n x 9) with the kernels' integer-pipe products and with every
-    product on the FP64 pipe; returns (emu, ref), each n x 14 (populations, m0, jx, jy, ux, uy)."""
+def lbm_selftest_collide_f64(model: int, theta: float, tau: float, f, mode: int = 0):
+    """FP64 collision of the nodes f (n x 9) with the kernels' arithmetic (starting in product mode
+    `mode`: 0 integer, 1 integer with zeros, 2 FP64 pipe) and with every product on the FP64 pipe;
+    returns (emu, ref), each n x 14 (populations, m0, jx, jy, ux, uy)."""
     import numpy as np
     fv = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1, 9))
     n = fv.shape[0]
     emu, ref = np.empty((n, 14)), np.empty((n, 14))
-    check(load().lbm_selftest_collide_f64(model, theta, tau, fv.ctypes.data_as(_pd), n, emu.ctypes.data_as(_pd),
-                                          ref.ctypes.data_as(_pd)), None)
+    check(load().lbm_selftest_collide_f64(model, mode, theta, tau, fv.ctypes.data_as(_pd), n,
+                                          emu.ctypes.data_as(_pd), ref.ctypes.data_as(_pd)), None)
     return emu, ref
 
 

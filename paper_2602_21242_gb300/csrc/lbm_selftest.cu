@@ -105,7 +105,7 @@ __global__ void fp64_emu_kernel(int op, const double* __restrict__ a, const doub
 }
 
 template <int MODEL>
-__global__ void collide_f64_kernel(const double* __restrict__ fin, long long n, olbm::Coef<double> c,
+__global__ void collide_f64_kernel(const double* __restrict__ fin, long long n, olbm::Coef<double> c, int mode,
                                    double* __restrict__ out_emu, double* __restrict__ out_ref) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -114,9 +114,13 @@ __global__ void collide_f64_kernel(const double* __restrict__ fin, long long n, 
 #pragma unroll
   for (int k = 0; k < 9; ++k) f[k] = fin[i * 9 + k], g[k] = olbm::d64f(f[k]);
   double mom[5], momr[5];
-  olbm::collide<MODEL, false, double>(f, c, [&](const olbm::NodeMoments<double>& m) {
-    mom[0] = m.m0, mom[1] = m.jx, mom[2] = m.jy, mom[3] = m.ux, mom[4] = m.uy;
-  });
+  int md = mode;  // the products the collision starts with (see olbm::collide)
+  olbm::collide<MODEL, false, double>(
+      f, c,
+      [&](const olbm::NodeMoments<double>& m) {
+        mom[0] = m.m0, mom[1] = m.jx, mom[2] = m.jy, mom[3] = m.ux, mom[4] = m.uy;
+      },
+      olbm::KeepInputs(), &md);
   const olbm::Coef<olbm::d64f> cr = olbm::coef_cast<olbm::d64f>(c);
   olbm::collide_form<MODEL, false, olbm::d64f>(g, cr, [&](const olbm::NodeMoments<olbm::d64f>& m) {
     momr[0] = m.m0.v, momr[1] = m.jx.v, momr[2] = m.jy.v, momr[3] = m.ux.v, momr[4] = m.uy.v;
@@ -153,9 +157,10 @@ extern "C" int lbm_selftest_fp64_emu(int op, const double* h_a, const double* h_
   return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
-extern "C" int lbm_selftest_collide_f64(int model, double theta, double tau, const double* h_f, long long n,
-                                        double* h_emu, double* h_ref) {
-  if (model < LBM_LBGK || model > LBM_LBGK_POLY || n < 0 || !(theta > 0.0 && theta < 1.0) || !(tau > 0.5) ||
+extern "C" int lbm_selftest_collide_f64(int model, int mode, double theta, double tau, const double* h_f,
+                                        long long n, double* h_emu, double* h_ref) {
+  if (model < LBM_LBGK || model > LBM_LBGK_POLY || mode < 0 || mode > 2 || n < 0 || !(theta > 0.0 && theta < 1.0) ||
+      !(tau > 0.5) ||
       (n > 0 && (h_f == nullptr || h_emu == nullptr || h_ref == nullptr)))
     return LBM_EINVAL;
   if (n == 0) return LBM_OK;
@@ -172,12 +177,12 @@ extern "C" int lbm_selftest_collide_f64(int model, double theta, double tau, con
   if (e == cudaSuccess) {
     const unsigned grid = (unsigned)((n + 127) / 128);
     switch (model) {
-      case 0: collide_f64_kernel<0><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
-      case 1: collide_f64_kernel<1><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
-      case 2: collide_f64_kernel<2><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
-      case 3: collide_f64_kernel<3><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
-      case 4: collide_f64_kernel<4><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
-      default: collide_f64_kernel<5><<<grid, 128>>>(d, n, c, d_emu, d_ref); break;
+      case 0: collide_f64_kernel<0><<<grid, 128>>>(d, n, c, mode, d_emu, d_ref); break;
+      case 1: collide_f64_kernel<1><<<grid, 128>>>(d, n, c, mode, d_emu, d_ref); break;
+      case 2: collide_f64_kernel<2><<<grid, 128>>>(d, n, c, mode, d_emu, d_ref); break;
+      case 3: collide_f64_kernel<3><<<grid, 128>>>(d, n, c, mode, d_emu, d_ref); break;
+      case 4: collide_f64_kernel<4><<<grid, 128>>>(d, n, c, mode, d_emu, d_ref); break;
+      default: collide_f64_kernel<5><<<grid, 128>>>(d, n, c, mode, d_emu, d_ref); break;
     }
     e = cudaGetLastError();
   }

@@ -97,11 +97,12 @@ def _nodes(seed, n):
     return np.concatenate([near, far, rest, zeros, sym])
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("model", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("theta,tau", [(1.0 / 3.0, 0.8), (0.25, 0.51), (0.4, 1.7)])
-def test_collision_with_integer_pipe_products_is_bit_identical(model, theta, tau):
+def test_collision_with_integer_pipe_products_is_bit_identical(model, theta, tau, mode):
     f = _nodes(100 + model, 20_000)
-    emu, ref = capi.lbm_selftest_collide_f64(model, theta, tau, f)
+    emu, ref = capi.lbm_selftest_collide_f64(model, theta, tau, f, mode)
     bad = ~_same(emu, ref)
     assert not bad.any(), f"model {model}: {bad.any(axis=1).sum()} nodes differ, e.g. node {np.argmax(bad.any(axis=1))}"
     # and the collision conserves mass (and momentum, except the uncorrected model, whose
@@ -121,6 +122,8 @@ def test_selftest_arguments_are_checked():
         capi.lbm_selftest_collide_f64(6, 1 / 3, 0.8, np.ones((2, 9)))
     with pytest.raises(capi.LBMError):
         capi.lbm_selftest_collide_f64(3, 1 / 3, 0.5, np.ones((2, 9)))
+    with pytest.raises(capi.LBMError):
+        capi.lbm_selftest_collide_f64(3, 1 / 3, 0.8, np.ones((2, 9)), mode=3)
     e, r = capi.lbm_selftest_fp64_emu(0, np.array([]), np.array([]))
     assert e.size == r.size == 0
 
