@@ -156,3 +156,28 @@ def test_fp64_step_with_zero_velocities_matches_the_oracle(oracle, flow, model, 
     err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
     assert err.max() <= 1e-12, f"{flow} model {model}: max relative error {err.max():.3e}"
     assert diag[4] == 0 and np.isfinite(diag[:4]).all()
+
+
+@pytest.mark.parametrize("model", [0, 3, 4])
+def test_fp64_result_does_not_depend_on_which_warps_switch_products(model):
+    """Every product mode gives the same bits, so the FP64 state after a flow whose warps switch
+    modes at different rows (a region at rest beside a moving one, zeros on lines) is the same
+    bit for bit under every launch shape and both FP64 kernels."""
+    import torch
+    from paper_2602_21242_gb300.lattice import Lattice
+    nx, ny, theta, tau, steps = 300, 70, 1.0 / 3.0, 0.7, 12
+    rho, ux, uy = flows.shear_wave(nx, ny, 0.05, 0.02)
+    ux[:, : nx // 3] = 0.0  # a third at rest
+    uy[:, : nx // 3] = 0.0
+    uy[ny // 2, :] = 0.0
+    out = []
+    for launch in ((0, 64, 2, 32), (0, 32, 4, 8), (0, 128, 1, 3), (0, 32, 1, 64), (1, 0, 1, 5), (1, 0, 1, 16)):
+        with Lattice(nx, ny, theta, tau, model, "f64") as lat:
+            capi.lbm_set_launch_ex(lat.ctx, *launch)
+            lat.set_diagnostics_interval(1)
+            lat.init(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+            lat.step(steps)
+            out.append((launch, lat.state().cpu().numpy()))
+    ref = out[0][1]
+    for launch, got in out[1:]:
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), f"launch {launch} differs from {out[0][0]}"
