@@ -79,3 +79,46 @@ def test_calls_reject_null_context():
     assert lib.lbm_destroy(None) == capi.LBM_OK
     assert isinstance(capi.last_error(None), str)
     assert capi.lbm_version() >> 16 == 1
+
+
+# Addresses that are never dereferenced: lbm_step_noalloc checks sizes, ranges and
+# overlaps on the host and returns before its first CUDA call when one fails.
+_FAR = 1 << 40
+
+
+@pytest.mark.parametrize("args,fragment", [
+    ((0, 8, 1 / 3, 0.6, 3, _FAR, 2 * _FAR, 3 * _FAR), "invalid size"),
+    ((8, 8, 1.0, 0.6, 3, _FAR, 2 * _FAR, 3 * _FAR), "out of range"),
+    ((8, 8, 1 / 3, 0.5, 3, _FAR, 2 * _FAR, 3 * _FAR), "out of range"),
+    ((8, 8, 1 / 3, 0.6, 6, _FAR, 2 * _FAR, 3 * _FAR), "out of range"),
+    ((8, 8, 1 / 3, 0.6, 3, 0, 2 * _FAR, 3 * _FAR), "NULL"),
+    ((8, 8, 1 / 3, 0.6, 3, _FAR, 0, 3 * _FAR), "NULL"),
+    ((8, 8, 1 / 3, 0.6, 3, _FAR, 2 * _FAR, 0), "NULL"),
+    # 16384 x 16384 needs 16384 blocks at 64 rows per thread: beyond the fixed scratch
+    ((16384, 16384, 1 / 3, 0.6, 3, _FAR, 2 * _FAR, 3 * _FAR), "more than the 8192"),
+    # d_dst starts inside d_src, d_diag5 inside d_src, d_diag5 inside d_dst
+    ((64, 64, 1 / 3, 0.6, 3, _FAR, _FAR + 8, 3 * _FAR), "overlap"),
+    ((64, 64, 1 / 3, 0.6, 3, _FAR, 2 * _FAR, _FAR + 4096), "overlap"),
+    ((64, 64, 1 / 3, 0.6, 3, _FAR, 2 * _FAR, 2 * _FAR - 8), "overlap"),
+])
+def test_noalloc_rejects_bad_arguments_before_touching_the_device(args, fragment):
+    with pytest.raises(capi.LBMError) as e:
+        capi.lbm_step_noalloc(*args)
+    assert e.value.status == capi.LBM_EINVAL
+    assert fragment in str(e.value)
+
+
+def test_product_sources_never_reach_the_oracle():
+    """The package, its CUDA sources and the public header name nothing under oracle/:
+    no import, include, path or library of the checker."""
+    pattern = re.compile(r"\bimport\s+oracle|from\s+oracle\b|liboracle|olbm_oracle|olbm_core|oracle/")
+    hits, scanned = [], 0
+    for sub in ("paper_2602_21242_gb300", "include"):
+        for path in glob.glob(os.path.join(ROOT, sub, "**", "*"), recursive=True):
+            if "_build" in path or not path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                continue
+            scanned += 1
+            for n, line in enumerate(open(path, encoding="utf-8"), 1):
+                if pattern.search(line):
+                    hits.append(f"{os.path.relpath(path, ROOT)}:{n}: {line.strip()}")
+    assert scanned > 20 and not hits, hits
