@@ -74,6 +74,14 @@ class Lattice:
     def ctx(self):
         return self._ctx
 
+    def _after_current(self) -> None:
+        """Order the lattice's stream after the work queued so far on torch's current
+        stream, which produced the tensors handed to the next call (a no-op when the
+        lattice runs on the current stream)."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
     def _fields(self):
         return torch.empty((3, self.ny, self.nx), dtype=torch.float64, device=self.device)
 
@@ -82,6 +90,7 @@ class Lattice:
         shape = (self.ny, self.nx)
         rho, ux, uy = (_dev_f64(t, shape, n) for t, n in ((rho, "rho"), (ux, "ux"), (uy, "uy")))
         with torch.cuda.device(self.device):
+            self._after_current()
             capi.lbm_init(self._ctx, rho.data_ptr(), ux.data_ptr(), uy.data_ptr())
             self._keep = (rho, ux, uy)  # alive until the stream has consumed them
             self.stream.synchronize()
@@ -90,6 +99,7 @@ class Lattice:
     def set_state(self, f: torch.Tensor) -> None:
         f = _dev_f64(f, (9, self.ny, self.nx), "f")
         with torch.cuda.device(self.device):
+            self._after_current()
             capi.lbm_set_state(self._ctx, f.data_ptr())
             self.stream.synchronize()
 
@@ -162,6 +172,7 @@ class _Run(torch.autograd.Function):
             lattice.step(n)
         else:  # the adjoint's forward pass, whose checkpoints the backward pass reuses
             with torch.cuda.device(lattice.device):
+                lattice._after_current()
                 capi.lbm_vjp_forward(lattice.ctx, n, ckpt_every, r0.data_ptr(), u0.data_ptr(), v0.data_ptr())
         rho, ux, uy = lattice.moments()
         fctx.save_for_backward(r0, u0, v0)
@@ -177,6 +188,7 @@ class _Run(torch.autograd.Function):
         args = (lat.ctx, fctx.n, fctx.k, r0.data_ptr(), u0.data_ptr(), v0.data_ptr(),
                 *[g.data_ptr() if g is not None else 0 for g in gs], *[g.data_ptr() for g in grads])
         with torch.cuda.device(lat.device):
+            lat._after_current()  # the incoming gradients and the outputs' allocations
             try:  # the forward pass's checkpoints, unless the lattice changed since
                 capi.lbm_vjp_ex(*args, flags=capi.LBM_VJP_REUSE_FORWARD)
             except capi.LBMError as e:

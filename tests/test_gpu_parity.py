@@ -188,6 +188,37 @@ def test_set_stream_orders_new_work_after_old():
             assert t == steps - 1 and status == capi.LBM_OK
 
 
+def test_inputs_from_the_current_stream_reach_a_lattice_on_its_own_stream():
+    """A lattice bound to a side stream takes fields that torch is still producing on
+    its current stream (queued behind a long matmul chain): init and set_state order
+    the lattice's stream after that work, so the result equals the same run with
+    every input ready."""
+    n, steps = 512, 5
+    rho, ux, uy = flows.shear_wave(n, n, U=0.1, amp=0.01)
+    host = [torch.from_numpy(a) for a in (rho, ux, uy)]
+    with Lattice(n, n, 1 / 3, 0.52, "complete") as ref:
+        ref.init(*(h.cuda() for h in host))
+        ref.step(steps)
+        want = ref.state().cpu()
+    side = torch.cuda.Stream()
+    with Lattice(n, n, 1 / 3, 0.52, "complete", stream=side) as lat:
+        for setter in ("init", "set_state"):
+            torch.cuda.synchronize()
+            busy = torch.randn(2048, 2048, device="cuda")
+            for _ in range(30):
+                busy = torch.tanh(busy @ busy)
+            zero = busy[0, 0] * 0.0  # ready only after the chain
+            if setter == "init":
+                lat.init(*(h.cuda() + zero for h in host))
+            else:
+                with Lattice(n, n, 1 / 3, 0.52, "complete") as tmp:
+                    tmp.init(*(h.cuda() for h in host))
+                    f_eq = tmp.state()
+                lat.set_state(f_eq + zero)
+            lat.step(steps)
+            np.testing.assert_array_equal(lat.state().cpu().numpy(), want.numpy())
+
+
 def test_run_host_matches_device_path(oracle):
     """lbm_run_host (host buffers in and out) equals init + step + moments on the device."""
     n, theta, tau = 48, 1 / 3, 0.56
