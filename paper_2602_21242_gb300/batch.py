@@ -72,6 +72,14 @@ class Batch:
     def set_diagnostics_interval(self, every: int) -> None:
         capi.lbm_batch_set_diagnostics_interval(self._b, every)
 
+    def _after_current(self) -> None:
+        """Order the batch's stream after the work queued so far on torch's current stream,
+        which produced the tensors handed to the next call (a no-op when the batch runs on
+        the current stream)."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
     def _packed(self, fields):
         out = []
         for name, parts in zip(("rho", "ux", "uy"), fields):
@@ -85,6 +93,7 @@ class Batch:
         """rho, ux, uy: sequences of per-domain (ny_k, nx_k) arrays or tensors."""
         r, u, v = self._packed((rho, ux, uy))
         with torch.cuda.device(self.device):
+            self._after_current()
             capi.lbm_batch_init(self._b, r.data_ptr(), u.data_ptr(), v.data_ptr())
             self.stream.synchronize()
 
@@ -93,6 +102,7 @@ class Batch:
         if tuple(f.shape) != (9, self.ny[k], self.nx[k]):
             raise ValueError("state must have shape (9, ny_k, nx_k)")
         with torch.cuda.device(self.device):
+            self._after_current()
             capi.lbm_batch_set_state(self._b, k, f.data_ptr())
             self.stream.synchronize()
 
