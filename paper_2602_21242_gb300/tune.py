@@ -17,7 +17,7 @@ import threading
 
 import torch
 
-from . import capi
+from . import capi, flows
 
 _lock = threading.Lock()
 
@@ -66,6 +66,13 @@ def _key(kind: str, nodes: int, prec: int, model: int, extra: str = "") -> str:
     return f"{gpu}|{kind}|2^{size_class}{extra}|prec{prec}|model{model}"
 
 
+def _timing_fields(nx: int, ny: int):
+    """(rho, ux, uy) host arrays the candidates are timed on: the advected shear wave of the
+    bandwidth benchmark (u_x = 0.1, u_y = 0.01 sin(2 pi x / nx)). A fluid at rest would time
+    another code path of the FP64 form, whose products take zero operands on a slower path."""
+    return flows.shear_wave(nx, ny, U=0.1, amp=0.01)
+
+
 def _time(step, sync, stream, steps: int) -> float:
     step(steps)  # warm-up with the same count (a batch captures its graph here)
     sync()
@@ -79,9 +86,9 @@ def _time(step, sync, stream, steps: int) -> float:
 
 def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, path: str | None = None):
     """Pick and apply the fastest launch (kind, bx, by, rows) for `lat` (a Lattice). Timing
-    runs on a temporary lattice of the same size, storage and model started at rest, so
-    `lat`'s state is untouched. Candidates may be given as (bx, by, rows) for kind 0 or as
-    (kind, bx, by, rows). Returns ((kind, bx, by, rows), ms_per_step or None if cached)."""
+    runs on a temporary lattice of the same size, storage and model started from the
+    advected shear wave of `_timing_fields`, so `lat`'s state is untouched. Candidates may
+    be given as (bx, by, rows) for kind 0 or as (kind, bx, by, rows). Returns ((kind, bx, by, rows), ms_per_step or None if cached)."""
     from .lattice import Lattice
 
     path = path or cache_path()
@@ -98,9 +105,7 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
     best = None
     with Lattice(lat.nx, lat.ny, lat.theta, lat.tau, lat.model, lat.prec, device=lat.device,
                  stream=lat.stream) as tmp:
-        ones = torch.ones((lat.ny, lat.nx), dtype=torch.float64, device=lat.device)
-        zeros = torch.zeros_like(ones)
-        tmp.init(ones, zeros, zeros)
+        tmp.init(*(torch.from_numpy(a).to(lat.device) for a in _timing_fields(lat.nx, lat.ny)))
         tmp.set_diagnostics_interval(1)
         for shape in candidates:
             shape = tuple(shape) if len(shape) == 4 else (0,) + tuple(shape)
@@ -118,7 +123,7 @@ def tune_lattice(lat, candidates=None, steps: int = 10, use_cache: bool = True, 
 
 def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, path: str | None = None):
     """Pick and apply the fastest tile shape for `batch` (a Batch). The timing steps the
-    batch itself from a rest state (rho = 1, u = 0): call it before Batch.init.
+    batch itself from the advected shear wave of `_timing_fields`: call it before Batch.init.
     Candidates are (kind, bx, by, rows) or (bx, by, rows) for kind 0; the default set
     adds the pipeline shapes for the shifted forms. Returns ((kind, bx, by, rows),
     ms_per_step or None if cached)."""
@@ -129,8 +134,7 @@ def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, 
         if hit:
             batch.set_launch(*hit["shape"])
             return tuple(hit["shape"]), None
-    rest = [torch.ones((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
-    zero = [torch.zeros((ny, nx), dtype=torch.float64) for nx, ny in zip(batch.nx, batch.ny)]
+    rho, ux, uy = zip(*(_timing_fields(nx, ny) for nx, ny in zip(batch.nx, batch.ny)))
     best = None
     if candidates is None:
         candidates = BATCH_CANDIDATES + (BATCH_PIPELINE_CANDIDATES + BATCH_TWO_STEP_CANDIDATES
@@ -141,11 +145,11 @@ def tune_batch(batch, candidates=None, steps: int = 10, use_cache: bool = True, 
             batch.set_launch(*shape)
         except capi.LBMError:
             continue
-        batch.init(rest, zero, zero)
+        batch.init(rho, ux, uy)
         ms = _time(batch.step, batch.sync, batch.stream, steps)
         if best is None or ms < best[1]:
             best = (shape, ms)
     batch.set_launch(*best[0])
-    batch.init(rest, zero, zero)
+    batch.init(rho, ux, uy)
     _store(path, key, {"shape": list(best[0]), "ms_per_step": best[1]})
     return tuple(best[0]), best[1]
