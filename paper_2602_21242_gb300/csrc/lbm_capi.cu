@@ -57,7 +57,7 @@ long long nodes_of(const lbm_ctx* c) { return (long long)c->nx * c->ny; }
 // Default launch of the step kernel per storage form, chosen by timing on GB300
 // at the 4096^2 benchmark size: FP64 the column kernel with 64 x 2 threads and
 // 32 rows per thread; the shifted forms the bulk-copy pipeline with one CTA per
-// tile of 32 rows (FP32 90 % of HBM), except on lattices narrower than 32
+// tile of 32 rows (refined per form below), except on lattices narrower than 32
 // columns, where the column kernel with 128 x 4 threads and 16 rows wastes fewer
 // threads. On smaller lattices the rows are halved until the grid has at least
 // 4 CTAs per SM.

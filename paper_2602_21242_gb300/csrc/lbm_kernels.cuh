@@ -364,11 +364,12 @@ __global__ void __maxnreg__(OLBM_DF_MAXNREG) step_kernel_df(const double* __rest
   step_body<MODEL, 3, DIAG, PAIRS>(src, dst, g, c, partials, rows);
 }
 
-// The FP64 form is bound by the FP64 pipe. Capped at 96 registers a thread,
-// five blocks of 128 threads fit an SM (four at the uncapped count); the rate
-// measures the same with caps from 72 (seven blocks, spilling) to 128 registers
-// (4751-4762 MLUPS at 4096^2), so the cap is not critical. Launched with at
-// most 512 threads.
+// The FP64 form is bound by the FP64 pipe. With its products on the integer
+// pipes it is capped at 128 registers a thread (four blocks of 128 threads an
+// SM, a few bytes spilled): the cap raised the 4096^2 rate from 5.57 to 5.77
+// GLUPS when it was set. With every product on the FP64 pipe the rate measured
+// the same for caps from 72 (seven blocks, spilling) to 128 registers
+// (4751-4762 MLUPS). Launched with at most 512 threads.
 #ifndef OLBM_F64_MAXNREG
 #define OLBM_F64_MAXNREG 128
 #endif
