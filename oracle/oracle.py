@@ -37,7 +37,14 @@ CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.int64)
 
 
 def build(force: bool = False) -> str:
-    """Compile olbm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP, no FMA contraction)."""
+    """Compile olbm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP, no FMA contraction).
+
+    Test hook: when OLBM_ORACLE_LIB names a library, that library is loaded instead
+    (tests/test_oracle_mutants_cpu.py runs the pins against copies of the oracle with a
+    planted mistake this way)."""
+    override = os.environ.get("OLBM_ORACLE_LIB")
+    if override:
+        return override
     os.makedirs(_BUILD_DIR, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _SRC)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:

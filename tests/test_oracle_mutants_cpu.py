@@ -1,0 +1,150 @@
+"""Planted mistakes in the oracle: every one must fail a pin.
+
+Each case copies the oracle's C sources (oracle/olbm_oracle.c, oracle/olbm_core.inc)
+to a temporary folder, plants one plausible mistake (a dropped term, a wrong sign,
+a wrong index or axis, a transposed operand, a mixed-up velocity table), compiles
+the copy with the oracle's own flags and runs the CPU pins (tests/test_oracle_pins.py
+and tests/test_golden_cpu.py) against it in a subprocess (OLBM_ORACLE_LIB points the
+oracle's loader at the copy). The pins must fail for every mutant, and must pass
+for the unmodified copy built the same way. The oracle itself is never modified.
+
+Left out because it is not a mistake: dropping the trace term -C_i^2/D delta_ab on
+the i side of Eq. 2's contraction. The k-sum it multiplies is traceless, so that
+term contributes C_i^2/2 (T_xx + T_yy) = 0 and the mutant computes the same values.
+The trace term on the k side is planted (oreg_dropped_trace_k) and caught.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+PINS = [os.path.join("tests", "test_oracle_pins.py"), os.path.join("tests", "test_golden_cpu.py")]
+CORE, MAIN = "olbm_core.inc", "olbm_oracle.c"
+
+# (name, passage, [(file, text in the oracle, planted text), ...])
+MUTANTS = [
+    ("geq_sign_of_cu", "Eq. 10",
+     [(CORE, "(double)c2 - 1.0 + (double)c * u + u * u + theta", "(double)c2 - 1.0 - (double)c * u + u * u + theta")]),
+    ("geq_dropped_u2", "Eq. 10",
+     [(CORE, "(double)c2 - 1.0 + (double)c * u + u * u + theta", "(double)c2 - 1.0 + (double)c * u + theta")]),
+    ("geq_normalisation", "Eq. 10",
+     [(CORE, "(1.0 - 2.0 * (double)c2) / (double)(1 << c2)", "(1.0 - 2.0 * (double)c2) / 2.0")]),
+    ("heq_dropped_theta", "Sec. 5.1, second LBGK reading",
+     [(CORE, "(cu * cu - theta * usq)", "(cu * cu - usq)")]),
+    ("heq_rest_weight", "Sec. 5.1, second LBGK reading",
+     [(CORE, "const double wx = CX[i] == 0 ? 1.0 - theta : 0.5 * theta;",
+       "const double wx = CX[i] == 0 ? 1.0 - theta : theta;")]),
+    ("moments_wrong_axis", "Sec. 1",
+     [(CORE, "*uy = jy / r;", "*uy = jx / r;")]),
+    ("oreg_transposed_index", "Eq. 2",
+     [(CORE, "contraction = contraction + (Ci[a] * Ci[b] - Ci2 / D * dab) * ksum;",
+       "contraction = contraction + (Ci[a] * Ci[a] - Ci2 / D * dab) * ksum;")]),
+    ("oreg_dropped_trace_k", "Eq. 2",
+     [(CORE, "ksum = ksum + ((double)(cka * ckb) - (double)ck2 / D * dab) * fneq[k];",
+       "ksum = ksum + ((double)(cka * ckb)) * fneq[k];")]),
+    ("oreg_f_for_fneq", "Eq. 2",
+     [(CORE, "- (double)ck2 / D * dab) * fneq[k];", "- (double)ck2 / D * dab) * f[k];")]),
+    ("oreg_prefactor", "Eq. 2",
+     [(CORE, "feq[i] / (2.0 * rho * theta * theta) * contraction", "feq[i] / (rho * theta * theta) * contraction")]),
+    ("psi_wrong_axis", "Eq. 6a",
+     [(CORE, "py = py + (double)CY[i] * foreg[i];", "py = py + (double)CX[i] * foreg[i];")]),
+    ("pref_sign", "Eq. 12",
+     [(CORE, "return -1.0 / (4.0 * theta * theta) * s;", "return 1.0 / (4.0 * theta * theta) * s;")]),
+    ("pref_sum_of_axes", "Eq. 12",
+     [(CORE, "(double)(CX[i] * CX[i] - CY[i] * CY[i]) * g[i]", "(double)(CX[i] * CX[i] + CY[i] * CY[i]) * g[i]")]),
+    ("pitilde_xx_sign", "Eq. 11b",
+     [(CORE, "pit[0] = pref * (-(theta * (1.0 - 3.0 * theta)", "pit[0] = pref * ((theta * (1.0 - 3.0 * theta)")]),
+    ("pitilde_yy_theta_term", "Eq. 11b",
+     [(CORE, "pit[1] = pref * (theta * (1.0 - 3.0 * theta)", "pit[1] = pref * (theta * (1.0 - 2.0 * theta)")]),
+    ("pitilde_xy_order", "Eq. 11b",
+     [(CORE, "pit[2] = pref * (ux * uy * (ux * ux - uy * uy));", "pit[2] = pref * (ux * uy * (uy * uy - ux * ux));")]),
+    ("partial_sign", "Eq. 14",
+     [(CORE, "Psi[i] = -0.5 * ((double)CX[i] * psi[0]);", "Psi[i] = 0.5 * ((double)CX[i] * psi[0]);")]),
+    ("partial_axis", "Eq. 14",
+     [(CORE, "Psi[i] = -0.5 * ((double)CY[i] * psi[1]);", "Psi[i] = -0.5 * ((double)CY[i] * psi[0]);")]),
+    ("complete_abar", "Eq. 15",
+     [(CORE, "v = -2.0 * (pit[1] - (double)CX[i] * psi[0]);", "v = -2.0 * (pit[0] - (double)CX[i] * psi[0]);")]),
+    ("complete_psi_sign", "Eq. 15",
+     [(CORE, "v = -2.0 * (pit[0] - (double)CY[i] * psi[1]);", "v = -2.0 * (pit[0] + (double)CY[i] * psi[1]);")]),
+    ("complete_dropped_cc_xy", "Eq. 15",
+     [(CORE, "v = pit[0] + pit[1] + (double)(CX[i] * CY[i]) * pit[2];", "v = pit[0] + pit[1] + pit[2];")]),
+    ("complete_scale", "Eq. 15",
+     [(CORE, "Psi[i] = -0.25 * v;", "Psi[i] = -0.5 * v;")]),
+    ("neq_variant_on_foreg", "Eq. 12, f^neq reading",
+     [(CORE, "FN(pitilde)(FN(pref)(fneq, theta), ux, uy, theta, pit);",
+       "FN(pitilde)(FN(pref)(g, theta), ux, uy, theta, pit);")]),
+    ("relaxation_factor", "Eq. 1a",
+     [(CORE, "const double omega_p = 1.0 - 1.0 / tau;", "const double omega_p = 1.0 / tau;")]),
+    ("poly_lbgk_dispatch", "Eq. 1a, model 5",
+     [(CORE, "if (model == 0 || model == 5) {", "if (model == 0) {")]),
+    ("bounce_back_axis", "Sec. 5.2",
+     [(CORE, "if (CX[j] == -CX[i] && CY[j] == -CY[i]) fs[i] = f[j];",
+       "if (CX[j] == -CX[i] && CY[j] == CY[i]) fs[i] = f[j];")]),
+    ("streaming_direction", "Eq. 1b",
+     [(CORE, "const int xd = (x + CX[i] + nx) % nx;", "const int xd = (x - CX[i] + nx) % nx;")]),
+    ("velocity_numbering", "Fig. 1a",
+     [(MAIN, "static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};",
+       "static const int CX[9] = {0, 1, 0, -1, 0, 1, 1, -1, -1};"),
+      (MAIN, "static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};",
+       "static const int CY[9] = {0, 0, 1, 0, -1, 1, -1, -1, 1};")]),
+    ("diagnostics_energy_half", "diagnostics",
+     [(MAIN, "nsum_add(&ke, 0.5 * (jx * jx + jy * jy) / rho);", "nsum_add(&ke, (jx * jx + jy * jy) / rho);")]),
+    ("diagnostics_momentum_axis", "diagnostics",
+     [(MAIN, "jy += (double)CY[i] * v;", "jy += (double)CX[i] * v;")]),
+]
+
+
+def _build(folder, edits):
+    """Copy the oracle's C sources into `folder`, apply the edits, compile; returns the library."""
+    os.makedirs(folder)
+    for name in (CORE, MAIN):
+        shutil.copy(os.path.join(ORACLE, name), os.path.join(folder, name))
+    for fname, old, new in edits:
+        path = os.path.join(folder, fname)
+        text = open(path).read()
+        assert text.count(old) == 1, f"{fname}: the text to replace must occur once: {old!r}"
+        open(path, "w").write(text.replace(old, new))
+    lib = os.path.join(folder, "liboracle.so")
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", lib,
+                    os.path.join(folder, MAIN), "-lm"], check=True, capture_output=True, cwd=folder)
+    return lib
+
+
+def _pins(lib):
+    """Run the CPU pins against the library; (exit status, last lines of the output)."""
+    env = dict(os.environ, OLBM_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    res = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider",
+                          "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return res.returncode, "\n".join((res.stdout + res.stderr).splitlines()[-15:])
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    base = tmp_path_factory.mktemp("oracle_mutants")
+    cases = [("unmodified", [])] + [(name, edits) for name, _, edits in MUTANTS]
+
+    def one(case):
+        name, edits = case
+        return name, _pins(_build(str(base / name), edits))
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as pool:
+        return dict(pool.map(one, cases))
+
+
+def test_unmodified_copy_passes_the_pins(outcomes):
+    status, tail = outcomes["unmodified"]
+    assert status == 0, tail
+
+
+@pytest.mark.parametrize("name,passage", [(m[0], m[1]) for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(outcomes, name, passage):
+    status, tail = outcomes[name]
+    # exit status 1: tests ran and one failed (not a collection or usage error)
+    assert status == 1, f"{name} ({passage}) was not caught by the pins (status {status}):\n{tail}"
