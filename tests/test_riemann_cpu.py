@@ -37,6 +37,19 @@ def test_rarefaction_invariant_and_characteristics(theta):
     assert ex.isothermal_riemann_sample(rho_l, rho_r, theta, [us - c])[0][0] == pytest.approx(rs, rel=1e-12)
 
 
+@pytest.mark.parametrize("theta", [0.4, 0.55])
+def test_right_rarefaction_invariant_and_characteristics(theta):
+    """Mirror of the left fan (rho_l < rho_r): inside the right rarefaction u + c = xi and
+    u - c ln rho equals its right-state value."""
+    rho_l, rho_r, c = 0.6, 2.4, math.sqrt(theta)
+    rs, us = ex.isothermal_riemann(rho_l, rho_r, theta)
+    xi = np.linspace(us + c + 1e-6, c - 1e-6, 50)
+    rho, u = ex.isothermal_riemann_sample(rho_l, rho_r, theta, xi)
+    np.testing.assert_allclose(u + c, xi, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(u - c * np.log(rho), -c * math.log(rho_r), rtol=1e-14)
+    assert ex.isothermal_riemann_sample(rho_l, rho_r, theta, [us + c])[0][0] == pytest.approx(rs, rel=1e-12)
+
+
 def test_symmetric_problems_have_closed_forms():
     """Equal densities: colliding streams (u_l = -u_r = U) give two shocks with u* = 0 and
     sqrt(rho*/rho) = (U/c + sqrt((U/c)^2 + 4))/2; receding streams give two rarefactions with
@@ -52,10 +65,12 @@ def test_symmetric_problems_have_closed_forms():
 
 
 @pytest.mark.parametrize("theta", [0.4, 0.55])
-def test_integrals_of_mass_and_momentum(theta):
+@pytest.mark.parametrize("rho_l,rho_r", [(1.5, 0.75), (0.6, 2.4)])
+def test_integrals_of_mass_and_momentum(theta, rho_l, rho_r):
     """On a domain wider than the wave pattern: the integral of rho stays at its initial value and the
-    integral of rho u grows at the pressure difference, theta (rho_l - rho_r) per unit time."""
-    rho_l, rho_r, t = 1.5, 0.75, 1.0
+    integral of rho u grows at the pressure difference, theta (rho_l - rho_r) per unit time. Both
+    orientations: a left rarefaction with a right shock, and a left shock with a right rarefaction."""
+    t = 1.0
     x = np.linspace(-2.0, 2.0, 400001)
     rho, u = ex.isothermal_riemann_sample(rho_l, rho_r, theta, x / t)
     h = x[1] - x[0]
@@ -80,6 +95,15 @@ def test_measures_of_the_exact_profile():
     bad = ex.shocktube_measures({"x": x, "rho": rho, "ux": u, "finite": False, "x0": x0, "theta": theta,
                                  "steps": steps, "rho_l": 1.5, "rho_r": 0.75})
     assert not bad["finite"] and "l1_rho" not in bad
+    # a run off the exact profile by +-d at alternate nodes: l1 error exactly d, and the
+    # oscillation shows up as total variation above the exact profile's: each step of the run
+    # is at least 2 d - |exact step|, so the excess is at least 2 d (n - 1) - 2 TV(exact)
+    d = 0.01
+    sign = np.where(x % 2 == 0, 1.0, -1.0)
+    off = ex.shocktube_measures({"x": x, "rho": rho + d * sign, "ux": u - d * sign, "finite": True, "x0": x0,
+                                 "theta": theta, "steps": steps, "rho_l": 1.5, "rho_r": 0.75})
+    assert off["l1_rho"] == pytest.approx(d, rel=1e-9) and off["l1_ux"] == pytest.approx(d, rel=1e-9)
+    assert off["tv_excess"] >= 2 * d * (len(x) - 1) - 2 * np.abs(np.diff(rho)).sum() - 1e-9
 
 
 def test_shocktube_fields_layout():
