@@ -7,6 +7,8 @@ the copy with the oracle's own flags and runs the CPU pins (tests/test_oracle_pi
 and tests/test_golden_cpu.py) against it in a subprocess (OLBM_ORACLE_LIB points the
 oracle's loader at the copy). The pins must fail for every mutant, and must pass
 for the unmodified copy built the same way. The oracle itself is never modified.
+The exact isothermal Riemann solution (oracle/riemann.py) gets the same treatment
+against tests/test_riemann_cpu.py, loaded in place of the original in a subprocess.
 
 Left out because it is not a mistake: dropping the trace term -C_i^2/D delta_ab on
 the i side of Eq. 2's contraction. The k-sum it multiplies is traceless, so that
@@ -148,3 +150,67 @@ def test_planted_mistake_fails_a_pin(outcomes, name, passage):
     status, tail = outcomes[name]
     # exit status 1: tests ran and one failed (not a collection or usage error)
     assert status == 1, f"{name} ({passage}) was not caught by the pins (status {status}):\n{tail}"
+
+
+# The exact isothermal Riemann solution (oracle/riemann.py, the shocktube's checker of Sec. 5.2)
+# against its pins (tests/test_riemann_cpu.py): (name, text in riemann.py, planted text).
+RIEMANN_MUTANTS = [
+    ("shock_curve_denominator", "return c * (rho - rho_k) / s,", "return c * (rho - rho_k) / rho,"),
+    ("rarefaction_curve_sign", "return c * math.log(rho / rho_k), c / rho", "return c * math.log(rho_k / rho), c / rho"),
+    ("middle_velocity_sign", "return rho, u_l - _wave_curve(rho, rho_l, c)[0]",
+     "return rho, u_l + _wave_curve(rho, rho_l, c)[0]"),
+    ("newton_velocity_jump_sign", "step = (fl + fr + u_r - u_l) / (dl + dr)", "step = (fl + fr - u_r + u_l) / (dl + dr)"),
+    ("left_shock_speed", "sl = u_l - c * math.sqrt(rs / rho_l)", "sl = u_l - c * math.sqrt(rho_l / rs)"),
+    ("right_shock_speed", "sr = u_r + c * math.sqrt(rs / rho_r)", "sr = u_r + c * math.sqrt(rho_r / rs)"),
+    ("left_fan_head", "elif z < u_l - c:", "elif z < u_l:"),
+    ("left_fan_invariant", "rho[k] = rho_l * math.exp((u_l - u[k]) / c)", "rho[k] = rho_l * math.exp((u[k] - u_l) / c)"),
+    ("right_fan_characteristic", "u[k] = z - c", "u[k] = z + c"),
+    ("l1_without_abs", "np.mean(np.abs(r - exact_rho))", "np.mean(r - exact_rho)"),
+    ("tv_without_exact_profile", "np.abs(np.diff(r)).sum() - np.abs(np.diff(exact_rho)).sum()",
+     "np.abs(np.diff(r)).sum()"),
+]
+
+_RIEMANN_RUNNER = """
+import importlib.util, sys
+sys.path.insert(0, {root!r})
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.riemann", {path!r})
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.riemann"] = mod
+spec.loader.exec_module(mod)
+oracle.riemann = mod
+import pytest
+sys.exit(pytest.main([{test!r}, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
+"""
+
+
+def _riemann_pins(folder, old, new):
+    os.makedirs(folder)
+    text = open(os.path.join(ORACLE, "riemann.py")).read()
+    if old is not None:
+        assert text.count(old) == 1, f"riemann.py: the text to replace must occur once: {old!r}"
+        text = text.replace(old, new)
+    path = os.path.join(folder, "riemann.py")
+    open(path, "w").write(text)
+    code = _RIEMANN_RUNNER.format(root=ROOT, path=path, test=os.path.join("tests", "test_riemann_cpu.py"))
+    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    return res.returncode, "\n".join((res.stdout + res.stderr).splitlines()[-15:])
+
+
+@pytest.fixture(scope="module")
+def riemann_outcomes(tmp_path_factory):
+    base = tmp_path_factory.mktemp("riemann_mutants")
+    cases = [("unmodified", None, None)] + RIEMANN_MUTANTS
+    with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as pool:
+        return dict(pool.map(lambda c: (c[0], _riemann_pins(str(base / c[0]), c[1], c[2])), cases))
+
+
+def test_unmodified_riemann_checker_passes_its_pins(riemann_outcomes):
+    status, tail = riemann_outcomes["unmodified"]
+    assert status == 0, tail
+
+
+@pytest.mark.parametrize("name", [m[0] for m in RIEMANN_MUTANTS])
+def test_planted_mistake_in_the_riemann_checker_fails_a_pin(riemann_outcomes, name):
+    status, tail = riemann_outcomes[name]
+    assert status == 1, f"{name} was not caught by the Riemann pins (status {status}):\n{tail}"
