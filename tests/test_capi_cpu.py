@@ -5,6 +5,7 @@ import glob
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -122,3 +123,35 @@ def test_product_sources_never_reach_the_oracle():
                 if pattern.search(line):
                     hits.append(f"{os.path.relpath(path, ROOT)}:{n}: {line.strip()}")
     assert scanned > 20 and not hits, hits
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without liblbm.so (and no way to build it) the binding raises: there is no fallback."""
+    code = f"""
+import sys
+sys.path.insert(0, {ROOT!r})
+from paper_2602_21242_gb300 import build, capi
+build.LIB = {str(tmp_path / "absent" / "liblbm.so")!r}
+def no_build(*a, **k):
+    raise RuntimeError("nvcc not found")
+build.build = no_build
+try:
+    capi.load()
+except RuntimeError as e:
+    print("raised:", e)
+    sys.exit(0)
+sys.exit(3)
+"""
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0 and "raised:" in res.stdout, res.stdout + res.stderr
+
+
+def test_lattice_without_a_gpu_raises():
+    """On a host without CUDA the torch wrapper raises instead of computing anywhere else."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2602_21242_gb300.lattice import Lattice
+
+    with pytest.raises(Exception):
+        Lattice(8, 8, 1 / 3, 0.6, "complete")
