@@ -64,6 +64,12 @@ def shear_k2(n: int, orientation: str = "axis") -> float:
     return (2 * math.pi / n) ** 2 * (1.0 if orientation == "axis" else 2.0)
 
 
+def viscosity_from_amplitudes(a1: float, a2: float, dt: int, k2: float) -> float:
+    """Viscosity of a shear wave whose mode amplitude fell from a1 to a2 over dt steps:
+    |a(t)| = |a(0)| exp(-nu k^2 t), so nu = -ln(a2 / a1) / (dt k^2) (negative if it grew)."""
+    return -math.log(a2 / a1) / (dt * k2)
+
+
 def rotated_shear_wave_viscosity(model: str, theta: float, ma: float, n: int = 200, nu: float = 1e-3,
                                  steps: int = 1200, t_fit: int = 200, a0: float = 1e-3, prec: str = "f64",
                                  orientation: str = "axis", device=None):
@@ -84,8 +90,7 @@ def rotated_shear_wave_viscosity(model: str, theta: float, ma: float, n: int = 2
         a2 = abs(shear_mode(u2, v2, n, orientation))
     if not (a2 > 0 and a1 > 0):
         return 0.0
-    nu_num = -math.log(a2 / a1) / ((steps - t_fit) * shear_k2(n, orientation))
-    return nu_num / nu
+    return viscosity_from_amplitudes(a1, a2, steps - t_fit, shear_k2(n, orientation)) / nu
 
 
 def shear_layer_run(model: str, theta: float, n: int, u0: float = 0.04, kappa: float = 80.0, delta: float = 0.05,
