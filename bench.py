@@ -190,6 +190,29 @@ def oracle_mlups(w, model, target_s=12.0, nx=None, ny=None):
     return nx * ny * steps / dt / 1e6, cores, sample
 
 
+def oracle_single_thread_mlups(w, model, target_s=3.0, rows=64):
+    """The FP64 oracle on one host thread over a band of `rows` rows of the workload's flow (the
+    flow depends on x only, so a periodic band is the same flow); returns (mlups, sample)."""
+    from oracle import oracle as O
+    from paper_2602_21242_gb300 import flows
+
+    prev = O.set_threads(0)
+    O.set_threads(1)
+    try:
+        nx, ny = w["nx"], min(rows, w["ny"])
+        m = MODEL_NAMES.index(model)
+        f = O.init(*flows.shear_wave(nx, ny, U=w["U"], amp=w["amp"]), w["theta"])
+        t0 = time.perf_counter()
+        f = O.run(f, w["theta"], w["tau"], m, 1)  # calibration step
+        steps = max(1, int(target_s / max(time.perf_counter() - t0, 1e-6)))
+        t0 = time.perf_counter()
+        f = O.run(f, w["theta"], w["tau"], m, steps)
+        dt = time.perf_counter() - t0
+    finally:
+        O.set_threads(prev)
+    return nx * ny * steps / dt / 1e6, f"{nx}x{ny} periodic band of the same flow, {steps} oracle steps, {dt:.1f} s"
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -334,6 +357,9 @@ def run_gpu(args):
         v, cores, sample = oracle_mlups(w, args.model)
         out["cpu_baseline"] = {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                "sample": sample}
+        v1, sample1 = oracle_single_thread_mlups(w, args.model)
+        out["cpu_baseline"]["single_thread"] = {"value": round(v1, 3), "unit": "MLUPS", "cores": 1,
+                                                "sample": sample1}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -62,3 +62,19 @@ def test_reference_arm_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_cpu_baseline_legs_time_the_oracle():
+    """The GPU arm's CPU-baseline legs: all host threads on the workload's grid, and one thread on
+    a band of rows of the same flow; both positive rates, the thread count restored after."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle as O
+
+    w = bench.workload(256)
+    before = O.set_threads(0)
+    v, cores, sample = bench.oracle_mlups(w, "complete", target_s=0.2)
+    assert v > 0 and cores >= 1 and "256x256" in sample
+    v1, sample1 = bench.oracle_single_thread_mlups(w, "complete", target_s=0.2, rows=16)
+    assert v1 > 0 and "256x16" in sample1
+    assert O.set_threads(0) == before or O.set_threads(0) == cores
