@@ -113,10 +113,6 @@ def tau_from_nu(nu: float, theta: float) -> float:
     return nu / theta + 0.5
 
 
-def nu_from_tau(tau: float, theta: float) -> float:
-    return theta * (tau - 0.5)
-
-
 def set_threads(n: int = 0) -> int:
     """Set the OpenMP thread count used by run() (0 = leave as is); returns the count in use."""
     return int(_load().oracle_set_threads(int(n)))
