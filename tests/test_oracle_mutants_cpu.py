@@ -170,31 +170,37 @@ RIEMANN_MUTANTS = [
      "np.abs(np.diff(r)).sum()"),
 ]
 
-_RIEMANN_RUNNER = """
+_MODULE_RUNNER = """
 import importlib.util, sys
 sys.path.insert(0, {root!r})
 import oracle
-spec = importlib.util.spec_from_file_location("oracle.riemann", {path!r})
+spec = importlib.util.spec_from_file_location("oracle.{name}", {path!r})
 mod = importlib.util.module_from_spec(spec)
-sys.modules["oracle.riemann"] = mod
+sys.modules["oracle.{name}"] = mod
 spec.loader.exec_module(mod)
-oracle.riemann = mod
+setattr(oracle, {name!r}, mod)
 import pytest
-sys.exit(pytest.main([{test!r}, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
+sys.exit(pytest.main([*{tests!r}, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]))
 """
 
 
-def _riemann_pins(folder, old, new):
+def _module_pins(folder, module, old, new, tests, env=None):
+    """Run `tests` in a subprocess with oracle/<module>.py replaced by a copy with `old` -> `new`."""
     os.makedirs(folder)
-    text = open(os.path.join(ORACLE, "riemann.py")).read()
+    text = open(os.path.join(ORACLE, module + ".py")).read()
     if old is not None:
-        assert text.count(old) == 1, f"riemann.py: the text to replace must occur once: {old!r}"
+        assert text.count(old) == 1, f"{module}.py: the text to replace must occur once: {old!r}"
         text = text.replace(old, new)
-    path = os.path.join(folder, "riemann.py")
+    path = os.path.join(folder, module + ".py")
     open(path, "w").write(text)
-    code = _RIEMANN_RUNNER.format(root=ROOT, path=path, test=os.path.join("tests", "test_riemann_cpu.py"))
-    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    code = _MODULE_RUNNER.format(root=ROOT, name=module, path=path, tests=tests)
+    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600,
+                         env=dict(os.environ, **(env or {})))
     return res.returncode, "\n".join((res.stdout + res.stderr).splitlines()[-15:])
+
+
+def _riemann_pins(folder, old, new):
+    return _module_pins(folder, "riemann", old, new, [os.path.join("tests", "test_riemann_cpu.py")])
 
 
 @pytest.fixture(scope="module")
@@ -214,3 +220,18 @@ def test_unmodified_riemann_checker_passes_its_pins(riemann_outcomes):
 def test_planted_mistake_in_the_riemann_checker_fails_a_pin(riemann_outcomes, name):
     status, tail = riemann_outcomes[name]
     assert status == 1, f"{name} was not caught by the Riemann pins (status {status}):\n{tail}"
+
+
+# The oracle's Python face (oracle/oracle.py) is marshalling apart from one formula, the
+# relaxation time of a viscosity (Sec. 1 with the 1/2 of Eq. 5's reading): planted in a copy
+# loaded in place of the original, against the C library built from the unmodified sources.
+def test_planted_mistake_in_the_viscosity_reading_fails_a_pin(tmp_path):
+    from oracle import oracle as O
+
+    lib = O.build()
+    env = {"OLBM_ORACLE_LIB": lib, "OMP_NUM_THREADS": "2"}
+    status, tail = _module_pins(str(tmp_path / "control"), "oracle", None, None, PINS, env=env)
+    assert status == 0, tail  # the unmodified copy, loaded the same way, passes
+    status, tail = _module_pins(str(tmp_path / "tau"), "oracle", "return nu / theta + 0.5", "return nu / theta",
+                                PINS, env=env)
+    assert status == 1, f"tau_from_nu without the 1/2 was not caught (status {status}):\n{tail}"
