@@ -703,7 +703,7 @@ def paper_experiments(args):
     table = {}
     for orientation in ("axis", "diagonal"):
         for t_fit in (200, 600):
-            for theta in (0.25, 1.0 / 3.0, 0.4, 0.5):
+            for theta in experiments.SHEAR_WAVE_THETAS:
                 for model in models + ["lbgk_poly"]:
                     if t_fit != 200 and model not in ("lbgk", "lbgk_poly", "oreg"):
                         continue
@@ -711,15 +711,15 @@ def paper_experiments(args):
                         round(experiments.rotated_shear_wave_viscosity(model, theta, ma, t_fit=t_fit,
                                                                        orientation=orientation), 4) for ma in mas]
     layer = {}
-    for theta in (0.4, 0.6):
-        for n in (128, 256, 512):
+    for theta in experiments.SHEAR_LAYER_THETAS:
+        for n in experiments.SHEAR_LAYER_GRIDS:
             for model in models + ["lbgk_poly"]:
                 finite, steps, w = experiments.shear_layer_run(model, theta, n)
                 layer[f"{model}/theta={theta}/N={n}"] = {
                     "finite": finite, "steps": steps,
                     "max_abs_vorticity": None if w is None else float(abs(w).max())}
     tube = {}
-    for theta, nu in ((0.4, 1e-12), (0.55, 1e-9)):
+    for theta, nu in experiments.SHOCKTUBE_CASES:
         for model in models + ["lbgk_poly"]:
             r = experiments.shocktube_run(model, theta, nu)
             entry = {"finite": r["finite"]}

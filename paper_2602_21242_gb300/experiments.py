@@ -93,18 +93,25 @@ def rotated_shear_wave_viscosity(model: str, theta: float, ma: float, n: int = 2
     return viscosity_from_amplitudes(a1, a2, steps - t_fit, shear_k2(n, orientation)) / nu
 
 
+def shear_layer_fields(n: int, u0: float = 0.04, kappa: float = 80.0, delta: float = 0.05):
+    """(rho, u_x, u_y) of the doubly periodic shear layer on an N x N grid (Sec. 5.3): unit density,
+    u_x = u0 tanh(kappa (y/N - 1/4)) for y <= N/2 and u0 tanh(kappa (3/4 - y/N)) above, and
+    u_y = delta u0 sin(2 pi (x/N + 1/4))."""
+    y = np.arange(n, dtype=np.float64)[:, None]
+    x = np.arange(n, dtype=np.float64)[None, :]
+    ux = np.where(y <= n / 2, u0 * np.tanh(kappa * (y / n - 0.25)), u0 * np.tanh(kappa * (0.75 - y / n)))
+    ux = np.broadcast_to(ux, (n, n)).copy()
+    uy = np.broadcast_to(delta * u0 * np.sin(2 * math.pi * (x / n + 0.25)), (n, n)).copy()
+    return np.ones((n, n)), ux, uy
+
+
 def shear_layer_run(model: str, theta: float, n: int, u0: float = 0.04, kappa: float = 80.0, delta: float = 0.05,
                     re: float = 3.0e4, turnovers: float = 1.0, prec: str = "f64", device=None):
     """Paper's doubly periodic shear layer to `turnovers` x N/u0 steps. Returns (finite, steps,
     vorticity (ny, nx) float64 numpy array or None)."""
     nu = u0 * n / re
     tau = tau_from_nu(nu, theta)
-    y = np.arange(n, dtype=np.float64)[:, None]
-    x = np.arange(n, dtype=np.float64)[None, :]
-    ux = np.where(y <= n / 2, u0 * np.tanh(kappa * (y / n - 0.25)), u0 * np.tanh(kappa * (0.75 - y / n)))
-    ux = np.broadcast_to(ux, (n, n)).copy()
-    uy = np.broadcast_to(delta * u0 * np.sin(2 * math.pi * (x / n + 0.25)), (n, n)).copy()
-    rho = np.ones((n, n))
+    rho, ux, uy = shear_layer_fields(n, u0, kappa, delta)
     steps = int(round(turnovers * n / u0))
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
     with Lattice(n, n, theta, tau, model, prec, device=dev) as lat:
@@ -120,6 +127,14 @@ def shear_layer_run(model: str, theta: float, n: int, u0: float = 0.04, kappa: f
 
 
 SHOCKTUBE_RHO = (1.5, 0.75)
+
+# The runs of Sec. 5 as the paper sets them up: the temperatures of the rotated shear wave
+# (Sec. 5.1, Fig. 2), the (theta, nu) pairs of the shocktube (Sec. 5.2) and the grids and
+# temperatures of the shear layer (Sec. 5.3).
+SHEAR_WAVE_THETAS = (0.25, 1.0 / 3.0, 0.4, 0.5)
+SHOCKTUBE_CASES = ((0.4, 1e-12), (0.55, 1e-9))
+SHEAR_LAYER_GRIDS = (128, 256, 512)
+SHEAR_LAYER_THETAS = (0.4, 0.6)
 
 
 def shocktube_fields(n: int = 800, rho_l: float = SHOCKTUBE_RHO[0], rho_r: float = SHOCKTUBE_RHO[1]):

@@ -1,5 +1,7 @@
-"""The oracle against the one table of values the paper prints: the numbering of the
-D2Q9 velocities in Fig. 1a (tests/golden/d2q9_velocities_fig1a.txt).
+"""Checks against values the paper prints, transcribed under tests/golden/: the
+numbering of the D2Q9 velocities in Fig. 1a (d2q9_velocities_fig1a.txt), which the
+oracle must follow, and the set-ups of the Sec. 5 experiments
+(sec5_experiment_setups.txt), which the experiment harness must run.
 
 The oracle's C core holds its own velocity table. These tests read the figure's
 numbering from the fixture and check that the oracle's populations follow it: the
@@ -66,3 +68,62 @@ def test_population_streams_along_its_figure_velocity(oracle, i):
     y1, x1 = np.unravel_index(np.argmax(bump), bump.shape)
     assert (x1, y1) == ((x0 + cx[i]) % nx, (y0 + cy[i]) % ny)
     assert bump[y1, x1] > 0.9e-3
+
+
+def sec5():
+    out = {}
+    with open(os.path.join(HERE, "golden", "sec5_experiment_setups.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                key, *vals = line.split()
+                out[key] = [float(v) for v in vals]
+    return out
+
+
+def _defaults(fn):
+    import inspect
+
+    return {k: p.default for k, p in inspect.signature(fn).parameters.items() if p.default is not inspect._empty}
+
+
+def test_experiment_set_ups_are_the_papers():
+    """The experiment harness runs Sec. 5's set-ups: its defaults and case lists against the
+    transcription of the values the paper prints."""
+    pytest.importorskip("torch")
+    from paper_2602_21242_gb300 import experiments as X
+
+    g = sec5()
+    sw = _defaults(X.rotated_shear_wave_viscosity)
+    assert (sw["n"], sw["nu"], sw["a0"], sw["steps"]) == (g["shear_wave.N"][0], g["shear_wave.nu"][0],
+                                                          g["shear_wave.A0"][0], g["shear_wave.iterations"][0])
+    np.testing.assert_allclose(X.SHEAR_WAVE_THETAS, g["shear_wave.theta"], rtol=1e-15)
+    rho, ux, uy = X.rotated_shear_wave_fields(int(g["shear_wave.N"][0]), 0.6, sw["a0"])
+    assert (rho == g["shear_wave.rho"][0]).all()
+    assert ux.mean() == pytest.approx(0.6 / np.sqrt(g["shear_wave.mean_flow_divisor_squared"][0]), rel=1e-14)
+    st = _defaults(X.shocktube_run)
+    assert (st["n"], st["steps"]) == (g["shocktube.nx"][0], g["shocktube.steps"][0])
+    assert [list(c) for c in X.SHOCKTUBE_CASES] == [g["shocktube.case1"], g["shocktube.case2"]]
+    sl = _defaults(X.shear_layer_run)
+    assert (sl["kappa"], sl["delta"], sl["u0"], sl["re"], sl["turnovers"]) == (
+        g["shear_layer.kappa"][0], g["shear_layer.delta"][0], g["shear_layer.u0"][0], g["shear_layer.Re"][0],
+        g["shear_layer.turnovers"][0])
+    assert list(X.SHEAR_LAYER_GRIDS) == g["shear_layer.N"] and list(X.SHEAR_LAYER_THETAS) == g["shear_layer.theta"]
+
+
+def test_shear_layer_initial_condition():
+    """Sec. 5.3's initial condition: u_x vanishes at y = N/4 and 3N/4, tends to +-u0 away from the
+    layers and is mirrored about y = N/2; u_y = delta u0 sin(2 pi (x/N + 1/4)) peaks at x = 0."""
+    pytest.importorskip("torch")
+    from paper_2602_21242_gb300 import experiments as X
+
+    g = sec5()
+    n, u0, kappa, delta = 128, g["shear_layer.u0"][0], g["shear_layer.kappa"][0], g["shear_layer.delta"][0]
+    rho, ux, uy = X.shear_layer_fields(n, u0, kappa, delta)
+    assert (rho == 1.0).all() and rho.shape == (n, n)
+    assert abs(ux[n // 4, 0]) < 1e-15 and abs(ux[3 * n // 4, 0]) < 1e-15
+    assert ux[n // 2, 0] == pytest.approx(u0 * np.tanh(kappa / 4), rel=1e-14)
+    assert ux[0, 0] == pytest.approx(-u0 * np.tanh(kappa / 4), rel=1e-14)
+    np.testing.assert_allclose(ux[1:n // 2, 0], ux[n - 1:n // 2:-1, 0], rtol=0, atol=1e-17)
+    assert (ux == ux[:, :1]).all() and (uy == uy[:1, :]).all()
+    assert uy[0, 0] == pytest.approx(delta * u0, rel=1e-14) and abs(uy[0, n // 4]) < 1e-17
