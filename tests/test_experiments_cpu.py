@@ -100,3 +100,40 @@ def test_viscosity_measurement_with_a_stand_in_lattice(monkeypatch, orientation)
     Decaying.blow_up = True
     assert X.rotated_shear_wave_viscosity("complete", 0.4, 0.5, n=40, nu=2e-3, orientation=orientation,
                                           device=cpu) == 0.0
+
+
+def test_shear_layer_run_with_a_stand_in_lattice(monkeypatch):
+    """The shear layer's plumbing (fields, viscosity from Re, one turnover of steps, vorticity) on
+    a stand-in lattice that keeps its initial fields: the vorticity is that of the initial shear."""
+    import torch
+
+    seen = {}
+
+    class Frozen:
+        def __init__(self, nx, ny, theta, tau, model, prec, device=None):
+            seen["tau"], seen["steps"] = tau, 0
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            return False
+
+        def init(self, rho, ux, uy):
+            self.fields = (rho, ux, uy)
+
+        def step(self, n):
+            seen["steps"] += n
+
+        def moments(self):
+            return self.fields
+
+    monkeypatch.setattr(X, "Lattice", Frozen)
+    n, theta = 64, 0.4
+    finite, steps, w = X.shear_layer_run("complete", theta, n, device=torch.device("cpu"))
+    assert finite and steps == seen["steps"] == round(n / 0.04)
+    assert seen["tau"] == pytest.approx(0.04 * n / 3.0e4 / theta + 0.5, rel=1e-15)
+    _, ux, uy = X.shear_layer_fields(n)
+    dudy = (np.roll(ux, -1, axis=0) - np.roll(ux, 1, axis=0)) / 2
+    dvdx = (np.roll(uy, -1, axis=1) - np.roll(uy, 1, axis=1)) / 2
+    np.testing.assert_allclose(w, dvdx - dudy, rtol=0, atol=1e-18)
