@@ -168,5 +168,6 @@ def shocktube_run(model: str, theta: float, nu: float, n: int = 800, steps: int 
             "x0": n // 2 - 0.5, "theta": theta, "steps": steps, "rho_l": rho_l, "rho_r": rho_r}
 
 
-__all__ = ["rotated_shear_wave_fields", "rotated_shear_wave_viscosity", "shear_mode", "shear_k2", "shear_layer_run",
-           "shocktube_fields", "shocktube_run", "SHOCKTUBE_RHO"]
+__all__ = ["rotated_shear_wave_fields", "rotated_shear_wave_viscosity", "shear_mode", "shear_k2",
+           "viscosity_from_amplitudes", "shear_layer_fields", "shear_layer_run", "shocktube_fields", "shocktube_run",
+           "SHOCKTUBE_RHO", "SHEAR_WAVE_THETAS", "SHOCKTUBE_CASES", "SHEAR_LAYER_GRIDS", "SHEAR_LAYER_THETAS"]

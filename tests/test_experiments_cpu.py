@@ -137,3 +137,41 @@ def test_shear_layer_run_with_a_stand_in_lattice(monkeypatch):
     dudy = (np.roll(ux, -1, axis=0) - np.roll(ux, 1, axis=0)) / 2
     dvdx = (np.roll(uy, -1, axis=1) - np.roll(uy, 1, axis=1)) / 2
     np.testing.assert_allclose(w, dvdx - dudy, rtol=0, atol=1e-18)
+
+
+def test_shocktube_run_with_a_stand_in_lattice(monkeypatch):
+    """The shocktube's plumbing (walls at both ends, the density jump, the fluid nodes returned
+    with the jump position and the set-up) on a stand-in lattice that keeps its initial fields."""
+    import torch
+
+    seen = {}
+
+    class Frozen:
+        def __init__(self, nx, ny, theta, tau, model, prec, device=None):
+            seen["shape"], seen["tau"] = (ny, nx), tau
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            return False
+
+        def set_walls(self, mask):
+            seen["walls"] = np.flatnonzero(mask)
+
+        def init(self, rho, ux, uy):
+            self.fields = (rho, ux, uy)
+
+        def step(self, n):
+            seen["steps"] = n
+
+        def moments(self):
+            return self.fields
+
+    monkeypatch.setattr(X, "Lattice", Frozen)
+    r = X.shocktube_run("complete", 0.4, 1e-12, device=torch.device("cpu"))
+    assert seen["shape"] == (1, 800) and list(seen["walls"]) == [0, 799] and seen["steps"] == 400
+    assert seen["tau"] == pytest.approx(1e-12 / 0.4 + 0.5, rel=1e-15)
+    assert r["finite"] and list(r["x"]) == list(range(1, 799)) and r["x0"] == pytest.approx(399.5)
+    assert (r["rho"][r["x"] < 400] == 1.5).all() and (r["rho"][r["x"] >= 400] == 0.75).all()
+    assert (r["theta"], r["steps"], r["rho_l"], r["rho_r"]) == (0.4, 400, 1.5, 0.75)
