@@ -92,12 +92,13 @@ enum lbm_status {
   LBM_ESTATE = -6      /* call out of order (e.g. stepping before lbm_init)      */
 };
 
-/* Library version, (major << 16) | minor. */
+/* Library version, (major << 16) | minor (no counterpart in the paper). */
 int lbm_version(void);
 
 /*
- * Device memory layout of one population buffer for (nx, ny, prec): each of the
- * 9 planes has ny rows of *pitch elements (pitch >= nx, rows 128-byte aligned) and
+ * Device memory layout of one population buffer for (nx, ny, prec) (no
+ * counterpart in the paper, which fixes no storage; the planes hold the nine
+ * f_i of Eq. 1 in Fig. 1a's order): each of the 9 planes has ny rows of *pitch elements (pitch >= nx, rows 128-byte aligned) and
  * planes are *plane elements apart (256-byte aligned). *state_bytes is the size
  * of ONE buffer; a lattice holds two (ping-pong). Any output pointer may be NULL.
  * Errors: LBM_EINVAL for nx, ny < 1, sizes whose buffers exceed 2^40 bytes, or an
@@ -116,7 +117,7 @@ int lbm_layout(int nx, int ny, int prec, long long* pitch, long long* plane,
 int lbm_create(int nx, int ny, double theta, double tau, int model, lbm_ctx** out);
 
 /*
- * As lbm_create with a storage form (enum lbm_prec), a CUDA stream (a
+ * As lbm_create (Sec. 1 / Eq. 1) with a storage form (enum lbm_prec), a CUDA stream (a
  * cudaStream_t cast to void*, NULL = legacy default stream) and, optionally,
  * caller-owned population memory: d_pop_buffers, if not NULL, is a device
  * pointer to 2 * state_bytes bytes (see lbm_layout), 256-byte aligned, that the
@@ -125,12 +126,13 @@ int lbm_create(int nx, int ny, double theta, double tau, int model, lbm_ctx** ou
 int lbm_create_ex(int nx, int ny, double theta, double tau, int model, int prec,
                   void* stream, void* d_pop_buffers, lbm_ctx** out);
 
-/* Release the lattice and the device memory it owns. NULL is accepted. Synchronises its stream. */
+/* Release the lattice and the device memory it owns (no counterpart in the paper).
+ * NULL is accepted. Synchronises its stream. */
 int lbm_destroy(lbm_ctx* ctx);
 
 /*
- * Rebind the lattice to another stream (cudaStream_t as void*, NULL = legacy
- * default). Work already enqueued for the lattice (steps on the old stream and
+ * Rebind the lattice to another stream (no counterpart in the paper;
+ * cudaStream_t as void*, NULL = legacy default). Work already enqueued for the lattice (steps on the old stream and
  * the fused diagnostics' final sums joined into it) is ordered before anything
  * later enqueued on the new stream: the new stream waits for an event recorded
  * on the old one. Does not synchronise the host.
@@ -158,7 +160,8 @@ int lbm_init(lbm_ctx* ctx, const double* d_rho, const double* d_ux, const double
  */
 int lbm_step(lbm_ctx* ctx, int n);
 
-/* Fused diagnostics interval M (0 = off, the default). */
+/* Fused diagnostics interval M (0 = off, the default): the reductions of
+ * lbm_diagnostics taken inside lbm_step (no counterpart in the paper). */
 int lbm_set_diagnostics_interval(lbm_ctx* ctx, int every);
 
 /*
@@ -177,7 +180,7 @@ int lbm_set_diagnostics_interval(lbm_ctx* ctx, int every);
 int lbm_set_walls(lbm_ctx* ctx, const unsigned char* h_mask, long long* h_count);
 
 /*
- * Latest diagnostics reduced inside lbm_step: h_out5 as in lbm_diagnostics,
+ * Latest diagnostics reduced inside lbm_step (no counterpart in the paper): h_out5 as in lbm_diagnostics,
  * *h_time = the time t they describe (-1 if none yet). Synchronises the stream.
  * Returns LBM_ENONFINITE if any fused pass so far met a non-finite population.
  */
@@ -192,7 +195,9 @@ int lbm_step_diagnostics(lbm_ctx* ctx, double* h_out5, long long* h_time);
 int lbm_moments(lbm_ctx* ctx, double* d_rho, double* d_ux, double* d_uy);
 
 /*
- * Global diagnostics of the current state, reduced on the device in a fixed
+ * Global diagnostics of the current state (the moments of Sec. 1 summed over
+ * the grid: mass, momentum and kinetic energy, which Eq. 1a's collision
+ * conserves or the model's viscosity dissipates), reduced on the device in a fixed
  * order (deterministic for a given size) in FP64, written to the HOST array
  * h_out5 = { sum rho, sum rho u_x, sum rho u_y, sum rho |u|^2 / 2,
  * number of nodes with a non-finite population } (sums skip those nodes).
@@ -200,7 +205,8 @@ int lbm_moments(lbm_ctx* ctx, double* d_rho, double* d_ux, double* d_uy);
  */
 int lbm_diagnostics(lbm_ctx* ctx, double* h_out5);
 
-/* Copy the state f(x, t) to / from a device array of 9 * nx * ny doubles ([i][y][x]). */
+/* Copy the state f(x, t) (the populations of Eq. 1 at time t) to / from a device
+ * array of 9 * nx * ny doubles ([i][y][x]). */
 int lbm_get_state(lbm_ctx* ctx, double* d_f);
 int lbm_set_state(lbm_ctx* ctx, const double* d_f);
 
@@ -289,11 +295,12 @@ int lbm_vjp_ex(lbm_ctx* ctx, int n, int ckpt_every, const double* d_rho0, const 
                const double* d_uy0, const double* g_rho, const double* g_ux, const double* g_uy,
                double* g_rho0, double* g_ux0, double* g_uy0, int flags);
 
-/* Current time t (steps since lbm_init / lbm_set_state). */
+/* Current time t of Eq. 1 (steps since lbm_init / lbm_set_state). */
 int lbm_time(const lbm_ctx* ctx, long long* h_t);
 
 /*
- * End-to-end call on HOST memory: copy rho0, u0 (host, nx * ny doubles each;
+ * End-to-end call on HOST memory (no counterpart in the paper; Eq. 10's
+ * initial state and n steps of Eq. 1): copy rho0, u0 (host, nx * ny doubles each;
  * page-locked memory recommended) to the device, lbm_init, run n steps, copy the
  * final moments to h_rho, h_ux, h_uy (host, may be NULL to skip) and the final
  * diagnostics to h_diag5 (host, may be NULL). Synchronous. Device staging
@@ -376,19 +383,20 @@ enum lbm_batch_mode {
   LBM_BATCH_PERSISTENT = 1  /* one cooperative launch for all n steps, bounded-wait grid barrier per step */
 };
 
-/* Create n >= 1 domains (arrays of length n). Errors: LBM_EINVAL for a domain
+/* Create n >= 1 domains (arrays of length n), each the problem of Sec. 1 / Eq. 1
+ * (the batched form itself has no counterpart in the paper). Errors: LBM_EINVAL for a domain
  * outside the lbm_create ranges; LBM_ENOMEM; LBM_ECUDA. Message: lbm_last_error(NULL). */
 int lbm_batch_create(int n, const int* nx, const int* ny, const double* theta, const double* tau,
                      int model, int prec, void* stream, lbm_batch** out);
 int lbm_batch_destroy(lbm_batch* b);
 
-/* Tile shape, launch kind 0 (the column routine): blocks of bx x by threads (bx a
+/* Tile shape (no counterpart in the paper), launch kind 0 (the column routine): blocks of bx x by threads (bx a
  * multiple of 32, bx * by <= 512) updating tiles of bx (node pairs: 2 bx) columns x
  * by * rows rows. Rebuilds the tile list (synchronous). */
 int lbm_batch_set_launch(lbm_batch* b, int bx, int by, int rows);
 int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* ntiles);
 
-/* Launch kind and tile shape. kind 0: as lbm_batch_set_launch. kind 1 (the shifted
+/* Launch kind and tile shape (no counterpart in the paper). kind 0: as lbm_batch_set_launch. kind 1 (the shifted
  * forms only; the FP16 default): the bulk-copy pipeline of the single-lattice
  * kind-1 kernel, one CTA of bx consumer threads (+ one producer warp) per tile of
  * 2 bx columns x rows rows (1..4096), any domain width; bx = 32, 64 or 128 (FP32),
@@ -407,20 +415,22 @@ int lbm_batch_get_launch(const lbm_batch* b, int* bx, int* by, int* rows, int* n
  * tile count). */
 int lbm_batch_set_launch_ex(lbm_batch* b, int kind, int bx, int by, int rows);
 int lbm_batch_get_launch_ex(const lbm_batch* b, int* kind, int* bx, int* by, int* rows, int* ntiles);
-int lbm_batch_set_mode(lbm_batch* b, int mode);  /* enum lbm_batch_mode; default LBM_BATCH_GRAPH */
-/* Fused per-domain diagnostics every M steps in LBM_BATCH_GRAPH mode (0 = off). */
+/* Batch mode, enum lbm_batch_mode; default LBM_BATCH_GRAPH (no counterpart in the paper). */
+int lbm_batch_set_mode(lbm_batch* b, int mode);
+/* Fused per-domain diagnostics every M steps in LBM_BATCH_GRAPH mode (0 = off; no
+ * counterpart in the paper). */
 int lbm_batch_set_diagnostics_interval(lbm_batch* b, int every);
 
 /* f(x, 0) = f^eq(rho0, u0) (Eq. 10) for every domain, from packed device fields. */
 int lbm_batch_init(lbm_batch* b, const double* d_rho, const double* d_ux, const double* d_uy);
-/* Domain k's state f(x, t) to / from a device array of 9 * nx[k] * ny[k] doubles ([i][y][x]). */
+/* Domain k's state f(x, t) (Eq. 1's populations at time t) to / from a device array of 9 * nx[k] * ny[k] doubles ([i][y][x]). */
 int lbm_batch_get_state(lbm_batch* b, int k, double* d_f);
 int lbm_batch_set_state(lbm_batch* b, int k, const double* d_f);
-/* Moments of every domain into packed device fields (asynchronous). */
+/* Moments (Sec. 1) of every domain into packed device fields (asynchronous). */
 int lbm_batch_moments(lbm_batch* b, double* d_rho, double* d_ux, double* d_uy);
 
 /*
- * Advance every domain by n steps. LBM_BATCH_GRAPH: asynchronous; the n launches
+ * Advance every domain by n steps of Eq. 1. LBM_BATCH_GRAPH: asynchronous; the n launches
  * are captured once into a graph (re-captured when n, the buffer parity or the
  * diagnostics phase changes) and replayed; each diagnosed step's final sum is a
  * parallel branch of the graph. LBM_BATCH_PERSISTENT: one cooperative launch
@@ -430,17 +440,19 @@ int lbm_batch_moments(lbm_batch* b, double* d_rho, double* d_ux, double* d_uy);
  * about a second (the state is then undefined).
  */
 int lbm_batch_step(lbm_batch* b, int n);
-/* Latest fused diagnostics, h_out[5 * k + j] as lbm_diagnostics for domain k; *h_time
+/* Latest fused diagnostics (no counterpart in the paper), h_out[5 * k + j] as lbm_diagnostics for domain k; *h_time
  * the time they describe (-1 if none). Synchronises; LBM_ENONFINITE if any pass met one. */
 int lbm_batch_step_diagnostics(lbm_batch* b, double* h_out, long long* h_time);
-/* Diagnostics of every domain's current state into h_out[5 * n] (host). Synchronises. */
+/* Diagnostics of every domain's current state (the moments of Sec. 1 summed per
+ * domain, as lbm_diagnostics) into h_out[5 * n] (host). Synchronises. */
 int lbm_batch_diagnostics(lbm_batch* b, double* h_out);
-/* Total nodes, bytes of the population arena, current time. */
+/* Total nodes, bytes of the population arena, current time; waiting for the
+ * batch's stream; the last error message (no counterpart in the paper). */
 int lbm_batch_info(const lbm_batch* b, long long* total_nodes, long long* arena_bytes, long long* t);
 int lbm_batch_sync(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 
-/* Wait for the lattice's stream; report a pending CUDA error (LBM_ECUDA) or a
+/* Wait for the lattice's stream (no counterpart in the paper); report a pending CUDA error (LBM_ECUDA) or a
  * non-finite population seen by a fused diagnostics pass (LBM_ENONFINITE). */
 int lbm_sync(lbm_ctx* ctx);
 
@@ -545,7 +557,8 @@ int lbm_selftest_fp64_emu(int op, const double* h_a, const double* h_b, long lon
 int lbm_selftest_collide_f64(int model, int mode, double theta, double tau, const double* h_f, long long n,
                              double* h_emu, double* h_ref);
 
-/* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
+/* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL
+ * (no counterpart in the paper). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
 #ifdef __cplusplus

@@ -155,3 +155,21 @@ def test_lattice_without_a_gpu_raises():
 
     with pytest.raises(Exception):
         Lattice(8, 8, 1 / 3, 0.6, "complete")
+
+
+def test_every_declaration_cites_its_passage():
+    """Each function include/*.h declares sits under a comment that names the passage of the
+    paper it implements (an equation, section or figure) or says it has no counterpart there."""
+    cite = re.compile(r"Eqs?\. \d|Sec\. \d|Fig\. \d|no counterpart in the paper")
+    missing = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        comments = [(m.start(), m.end(), re.sub(r"\s*\n\s*\*?\s*", " ", m.group(0)))
+                    for m in re.finditer(r"/\*.*?\*/", text, flags=re.S)]
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            if any(a <= m.start(1) < b for a, b, _ in comments):
+                continue  # a name inside a comment
+            before = [c for a, b, c in comments if b <= m.start()]
+            if not before or not cite.search(before[-1]):
+                missing.append(m.group(1))
+    assert not missing, missing
