@@ -173,3 +173,19 @@ def test_every_declaration_cites_its_passage():
             if not before or not cite.search(before[-1]):
                 missing.append(m.group(1))
     assert not missing, missing
+
+
+@pytest.mark.parametrize("args,fragment", [
+    (([16, 0], [16, 16], [0.3, 0.3], [0.6, 0.6], 3, capi.LBM_F32_SHIFT), "domain 1: invalid size"),
+    (([16], [16], [1.0], [0.6], 3, capi.LBM_F32_SHIFT), "domain 0: theta"),
+    (([16, 8], [16, 8], [0.3, 0.3], [0.6, 0.5], 3, capi.LBM_F64), "domain 1: theta"),
+    (([16], [16], [0.3], [0.6], 7, capi.LBM_F32_SHIFT), "unknown model"),
+    (([16], [16], [0.3], [0.6], 3, capi.LBM_F64_DF), "not available for batches"),
+    (([], [], [], [], 3, capi.LBM_F32_SHIFT), "bad arguments"),
+])
+def test_batch_create_rejects_bad_arguments(args, fragment):
+    """lbm_batch_create checks every domain on the host before touching the device."""
+    with pytest.raises(capi.LBMError) as e:
+        capi.lbm_batch_create(*args)
+    assert e.value.status == capi.LBM_EINVAL
+    assert fragment in str(e.value)
