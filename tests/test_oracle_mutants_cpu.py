@@ -98,6 +98,14 @@ MUTANTS = [
      [(MAIN, "nsum_add(&ke, 0.5 * (jx * jx + jy * jy) / rho);", "nsum_add(&ke, (jx * jx + jy * jy) / rho);")]),
     ("diagnostics_momentum_axis", "diagnostics",
      [(MAIN, "jy += (double)CY[i] * v;", "jy += (double)CX[i] * v;")]),
+    ("run_result_left_in_scratch", "Eq. 1, odd step counts",
+     [(MAIN, "  if (a != f) memcpy(f, a, n9 * sizeof(double));\n", "")]),
+    ("moments_field_transposed_layout", "Sec. 1, [i][y][x] layout",
+     [(MAIN, "    for (int i = 0; i < Q9; ++i) fl[i] = f[(size_t)i * N + n];\n    r_moments(fl, &rho[n], &ux[n], &uy[n]);",
+       "    for (int i = 0; i < Q9; ++i) fl[i] = f[n * Q9 + (size_t)i];\n    r_moments(fl, &rho[n], &ux[n], &uy[n]);")]),
+    ("complex_step_init_axes", "Eq. 10, complex-step twin",
+     [(MAIN, "z_init((const double _Complex*)rho_ri, (const double _Complex*)ux_ri,\n         (const double _Complex*)uy_ri,",
+       "z_init((const double _Complex*)rho_ri, (const double _Complex*)uy_ri,\n         (const double _Complex*)ux_ri,")]),
 ]
 
 
